@@ -1,0 +1,199 @@
+/*
+ * mpm2p.h -- C ABI of the GB300 (sm_103a) MRCM / MPM-2P pressure-update hot path.
+ *
+ * Method: Rocha, Mankad, Sousa, Pereira, "The Multiscale Perturbation Method for
+ * Two-Phase Reservoir Flow Problems", arXiv 2103.11050.
+ *
+ * Problem (Section 2, Eq. Darcy and Eq. BL2D): on the rectangle [0, nx h] x [0, ny h]
+ * with square cells of side h, u = -lambda(s) K grad p, div u = q, with per-side
+ * Dirichlet (p = g) or Neumann (u.n = z) data, coupled with ds/dt + div(f(s) u) = 0.
+ * lambda(s) = M s^2 + (1 - s)^2 and f(s) = M s^2 / lambda(s) (Section 5, k_rw = s^2,
+ * k_ro = (1 - s)^2, M = mu_o / mu_w).  kappa = lambda(s) K (Section 2).
+ *
+ * The fine grid is cell centred with P0 edge fluxes (Section 3): two-point fluxes with
+ * harmonic transmissibilities 2 ka kb / (ka + kb); half-cell transmissibility 2 kc on
+ * Dirichlet faces.  The domain is split into a tensor product of rectangular subdomains
+ * (Section 3); the interface spaces are discontinuous polynomials of degree 0 or 1 on
+ * segments of seg_len fine edges (Section 3.1).
+ *
+ * Conventions shared by all calls
+ *  - Every call returns an int status (MPM_OK on success) and never aborts the process.
+ *    After an error, mpm_last_error(ctx) returns a one-line message.  A CUDA error
+ *    (MPM_ERR_CUDA) leaves the context unusable; destroy it.
+ *  - Arrays are float64, C order.  Cell arrays are [R][ny][nx] (R independent
+ *    realisations, row j = y index).  Face fluxes are INTEGRATED over the face (h times
+ *    the normal velocity): ux is [R][ny][nx+1] (x-face left of cell (i,j), +x positive),
+ *    uy is [R][ny+1][nx] (+y positive).
+ *  - mem = MPM_MEM_HOST: the pointer is host memory (pageable or pinned); the call copies
+ *    synchronously.  mem = MPM_MEM_DEVICE: the pointer is device memory of the context's
+ *    device (for instance a torch CUDA tensor's data_ptr()); the copy is enqueued on the
+ *    context's stream.
+ *  - The caller owns every pointer it passes; setters copy into library-owned device
+ *    memory, getters copy out.  The library allocates its device memory at
+ *    mpm_set_decomposition (and frees it in mpm_destroy); compute calls allocate nothing.
+ *  - All work is enqueued on the stream given to mpm_create; compute calls do not
+ *    synchronise the host unless stated (mpm_get_*, mpm_get_stats and calls that return
+ *    values through host pointers synchronise the stream).
+ */
+#ifndef MPM2P_H
+#define MPM2P_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MPM_OK = 0,
+  MPM_ERR_ARG = 1,            /* invalid argument or inconsistent sizes */
+  MPM_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  MPM_ERR_OOM = 3,            /* device allocation failed */
+  MPM_ERR_NOT_CONVERGED = 4,  /* iterative refinement hit its iteration cap */
+  MPM_ERR_STATE = 5           /* call out of order (e.g. solve before build) */
+};
+
+enum { MPM_MEM_HOST = 0, MPM_MEM_DEVICE = 1 };
+enum { MPM_BC_DIRICHLET = 0, MPM_BC_NEUMANN = 1 };
+enum { MPM_SIDE_LEFT = 0, MPM_SIDE_RIGHT = 1, MPM_SIDE_BOTTOM = 2, MPM_SIDE_TOP = 3 };
+
+/* Precision of the local factorisations and triangular solves.
+ *  FP64:      everything in float64.
+ *  FP32_IR:   local Robin / Neumann factorisations and solves in float32 with
+ *             float64 residuals and iterative refinement to ir_tol; interface
+ *             (skeleton) system, residuals, fluxes and transport stay float64. */
+enum { MPM_PREC_FP64 = 0, MPM_PREC_FP32_IR = 1 };
+
+/* Which pressure mpm_get_pressure returns. */
+enum {
+  MPM_P_MRCM = 0,        /* MRCM-level pressure p^m of the last basis build (Section 3) */
+  MPM_P_DOWNSCALED = 1   /* pressure of the last downscaling, Eq. (mpm_upd) */
+};
+
+typedef struct mpm_ctx mpm_ctx;
+
+typedef struct mpm_stats {
+  long long steps;            /* Algorithm 1 iterations run by mpm_step */
+  long long rebuilds;         /* basis builds (all realisations summed) */
+  long long mpm_updates;      /* MPM-2P reuse updates (all realisations summed) */
+  double last_eps_max;        /* max over realisations of the last epsilon */
+  double last_dt_min;         /* min over realisations of the last transport dt */
+  int ir_iters_max;           /* max refinement sweeps used by any local solve */
+  int interface_dofs;         /* interface unknowns per realisation */
+  int subdomains;             /* subdomains per realisation */
+  int n_hat;                  /* homogeneous BFs per realisation (Section 4.3) */
+} mpm_stats;
+
+/* Create a context for R realisations of an nx x ny grid on [0,Lx]x[0,Ly].
+ * Cells must be square: Lx/nx == Ly/ny (relative 1e-12).  stream is a cudaStream_t
+ * (NULL = legacy default stream) of the current device, which becomes the context's
+ * device.  Defaults: M = 1, left p = 1, right p = 0, top/bottom no flow, s_inflow = 1,
+ * q = 0, FP64.  Errors: MPM_ERR_ARG for non-positive sizes or non-square cells. */
+int mpm_create(mpm_ctx** ctx, int R, int nx, int ny, double Lx, double Ly, void* stream);
+
+/* Free all device memory of ctx (after synchronising its stream). NULL is a no-op. */
+int mpm_destroy(mpm_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none). Owned by ctx. */
+const char* mpm_last_error(const mpm_ctx* ctx);
+
+/* Local solver precision (enum above).  ir_tol: relative FP64 residual target of the
+ * refinement (ignored for FP64), ir_max: sweep cap (>= 1); a local solve that does not
+ * reach ir_tol in ir_max sweeps makes the next mpm_sync / getter return
+ * MPM_ERR_NOT_CONVERGED.  Takes effect at the next basis build. */
+int mpm_set_precision(mpm_ctx* ctx, int mode, double ir_tol, int ir_max);
+
+/* Absolute permeability K [R][ny][nx], every entry > 0 and finite (checked for host
+ * input; device input is trusted). */
+int mpm_set_permeability(mpm_ctx* ctx, const double* K, int mem);
+
+/* Source q [R][ny][nx] per unit area (Eq. Darcy); NULL resets it to zero. */
+int mpm_set_source(mpm_ctx* ctx, const double* q, int mem);
+
+/* Viscosity ratio M = mu_o / mu_w > 0 (Section 5). */
+int mpm_set_fluids(mpm_ctx* ctx, double M);
+
+/* Boundary data per side (MPM_SIDE_*): type[k] is MPM_BC_DIRICHLET (val = pressure g)
+ * or MPM_BC_NEUMANN (val = outward normal velocity z; z < 0 injects).  At least one side
+ * must be Dirichlet (otherwise the pressure is defined up to a constant).  s_inflow is
+ * the saturation carried by inflow through any boundary face (Eq. BL2D). */
+int mpm_set_boundary(mpm_ctx* ctx, const int type[4], const double val[4], double s_inflow);
+
+/* Tensor-product decomposition (Section 3): ncx column widths col_w (cells, summing to
+ * nx) and ncy row heights row_h (summing to ny); every width and height <= 32 and a
+ * multiple of seg_len; degree 0 or 1 (Section 3.1); alpha > 0 is the constant of
+ * Eq. (beta) (beta = alpha H / kappa, H = length of the interface carrying the face).
+ * (Re)allocates every per-subdomain device buffer; invalidates the stored basis. */
+int mpm_set_decomposition(mpm_ctx* ctx, int ncx, const int* col_w, int ncy, const int* row_h,
+                          int seg_len, int degree, double alpha);
+
+/* Water saturation s [R][ny][nx] in [0,1]; also recomputes kappa^n = lambda(s) K. */
+int mpm_set_saturation(mpm_ctx* ctx, const double* s, int mem);
+
+/* MRCM basis build at the current kappa^n (Algorithm 1 lines 2-3 and 13-15; Eqs. mrc1,
+ * mrc_homogeneous, mrc_non_homogeneous, mrc2): factor every local Robin problem, one
+ * local solve per interface DOF plus the non-homogeneous one, assemble and factor the
+ * interface system, solve it, form the MRCM-level pressure p^m and the interface fluxes
+ * (mean of the one-sided traces).  Stores kappa^m := kappa^n.  Enqueued, no host sync.
+ * Needs mpm_set_permeability, mpm_set_decomposition and mpm_set_saturation first. */
+int mpm_build_basis(mpm_ctx* ctx);
+
+/* Recompute kappa^n = lambda(s) K from the current saturation and
+ * epsilon_r = ||kappa^n - kappa^m||_2 / ||kappa^m||_2 per realisation (Section 4.1,
+ * Algorithm 1 line 19).  eps (host, [R]) may be NULL (then no host sync). */
+int mpm_eval_epsilon(mpm_ctx* ctx, double* eps);
+
+/* Algorithm 1 line 11 decision per realisation: rebuild_r = (epsilon_r > eta) with the
+ * epsilon of the last mpm_eval_epsilon.  rebuild (host, [R]) may be NULL (no host sync). */
+int mpm_choose(mpm_ctx* ctx, double eta, int* rebuild);
+
+/* MPM-2P perturbation solve (Section 4.1, Eq. mpm_tf_3): fine residual
+ * r = q h^2 - sum_faces F(kappa^n, p^m), then one local solve per subdomain with the
+ * stored Robin factor of kappa^m (zero Robin data, homogeneous physical data), and the
+ * interface right-hand side from its traces.  Needs a stored basis. */
+int mpm_perturbation_solve(mpm_ctx* ctx);
+
+/* Interface (skeleton) solve with the stored factorisation for the right-hand side of the
+ * last mpm_build_basis or mpm_perturbation_solve, and the interface / boundary fluxes
+ * u_bar: after a build, the mean of the one-sided MRCM traces; after a perturbation
+ * solve, the mean of the one-sided traces of the epsilon^0 problem plus the fine flux
+ * of p^m with kappa^n (Section 4.1, u_bar = u^m + delta u^n). */
+int mpm_interface_solve(mpm_ctx* ctx);
+
+/* Downscaling (Eq. mpm_upd): per subdomain, Neumann problem with kappa^n and u_bar on
+ * all its boundary faces; pressure constant fixed by mean(p~) = mean of the MRCM-level
+ * pressure of the same update over the subdomain.  Writes the conservative fine
+ * fluxes ux, uy and p~. */
+int mpm_downscale(mpm_ctx* ctx);
+
+/* Explicit upwind transport (Section 4, Eq. BL2D): n_sub >= 1 explicit Euler steps with
+ * the current fine fluxes frozen and dt = cfl h^2 / (max f' * max_c max(out_c, in_c)),
+ * out_c / in_c the total integrated outflow / inflow of cell c, 0 < cfl <= 1.  Then
+ * recomputes kappa^n.  dt (host, [R]) may be NULL (no host sync). */
+int mpm_saturation_step(mpm_ctx* ctx, double cfl, int n_sub, double* dt);
+
+/* Algorithm 1 initialisation (lines 1-4): kappa^0, MRCM solve + downscale, store the
+ * basis, epsilon := eta.  Enqueued, no host sync. */
+int mpm_init(mpm_ctx* ctx, double eta);
+
+/* One pass of the while loop of Algorithm 1 (lines 6-20) for every realisation:
+ * n_sub transport steps, kappa^n, MRCM rebuild where epsilon > eta (the epsilon of the
+ * previous pass) else an MPM-2P update, downscaling, new epsilon.  The branch is taken
+ * on the device per realisation; no host synchronisation. */
+int mpm_step(mpm_ctx* ctx, double eta, double cfl, int n_sub);
+
+/* Copy out pressure [R][ny][nx] (which = MPM_P_*), fluxes ux [R][ny][nx+1],
+ * uy [R][ny+1][nx], saturation [R][ny][nx] or conductivity kappa^n.  Synchronise. */
+int mpm_get_pressure(mpm_ctx* ctx, double* p, int which, int mem);
+int mpm_get_flux(mpm_ctx* ctx, double* ux, double* uy, int mem);
+int mpm_get_saturation(mpm_ctx* ctx, double* s, int mem);
+int mpm_get_conductivity(mpm_ctx* ctx, double* kappa, int mem);
+
+/* Counters (synchronises the stream and reports a pending MPM_ERR_NOT_CONVERGED). */
+int mpm_get_stats(mpm_ctx* ctx, mpm_stats* out);
+
+/* Synchronise the context's stream; returns a pending device-side status. */
+int mpm_sync(mpm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPM2P_H */

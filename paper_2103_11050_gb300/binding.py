@@ -1,0 +1,254 @@
+"""ctypes binding of libmpm2p (include/mpm2p.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts NumPy arrays (host)
+and torch CUDA tensors (device) to pointers, forwards the calls with the same names,
+and raises ``MPMError`` on a non-zero status.  If the library is missing it raises at
+import of the handle: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MPM_OK, MPM_ERR_ARG, MPM_ERR_CUDA, MPM_ERR_OOM, MPM_ERR_NOT_CONVERGED, MPM_ERR_STATE = range(6)
+MEM_HOST, MEM_DEVICE = 0, 1
+BC_DIRICHLET, BC_NEUMANN = 0, 1
+PREC_FP64, PREC_FP32_IR = 0, 1
+P_MRCM, P_DOWNSCALED = 0, 1
+
+FUNCTIONS = [
+    "mpm_create", "mpm_destroy", "mpm_last_error", "mpm_set_precision", "mpm_set_permeability",
+    "mpm_set_source", "mpm_set_fluids", "mpm_set_boundary", "mpm_set_decomposition",
+    "mpm_set_saturation", "mpm_build_basis", "mpm_eval_epsilon", "mpm_choose",
+    "mpm_perturbation_solve", "mpm_interface_solve", "mpm_downscale", "mpm_saturation_step",
+    "mpm_init", "mpm_step", "mpm_get_pressure", "mpm_get_flux", "mpm_get_saturation",
+    "mpm_get_conductivity", "mpm_get_stats", "mpm_sync",
+]
+
+
+class MPMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mpm2p error {code}: {msg}")
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_longlong), ("rebuilds", ctypes.c_longlong),
+                ("mpm_updates", ctypes.c_longlong), ("last_eps_max", ctypes.c_double),
+                ("last_dt_min", ctypes.c_double), ("ir_iters_max", ctypes.c_int),
+                ("interface_dofs", ctypes.c_int), ("subdomains", ctypes.c_int), ("n_hat", ctypes.c_int)]
+
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libmpm2p (building it first if its sources are newer)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} is missing: run paper_2103_11050_gb300.build.build() first")
+    L = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    IP, DP = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "mpm_create": ([ctypes.POINTER(P), I, I, I, D, D, P], I),
+        "mpm_destroy": ([P], I),
+        "mpm_last_error": ([P], ctypes.c_char_p),
+        "mpm_set_precision": ([P, I, D, I], I),
+        "mpm_set_permeability": ([P, P, I], I),
+        "mpm_set_source": ([P, P, I], I),
+        "mpm_set_fluids": ([P, D], I),
+        "mpm_set_boundary": ([P, IP, DP, D], I),
+        "mpm_set_decomposition": ([P, I, IP, I, IP, I, I, D], I),
+        "mpm_set_saturation": ([P, P, I], I),
+        "mpm_build_basis": ([P], I),
+        "mpm_eval_epsilon": ([P, DP], I),
+        "mpm_choose": ([P, D, IP], I),
+        "mpm_perturbation_solve": ([P], I),
+        "mpm_interface_solve": ([P], I),
+        "mpm_downscale": ([P], I),
+        "mpm_saturation_step": ([P, D, I, DP], I),
+        "mpm_init": ([P, D], I),
+        "mpm_step": ([P, D, D, I], I),
+        "mpm_get_pressure": ([P, P, I, I], I),
+        "mpm_get_flux": ([P, P, P, I], I),
+        "mpm_get_saturation": ([P, P, I], I),
+        "mpm_get_conductivity": ([P, P, I], I),
+        "mpm_get_stats": ([P, ctypes.POINTER(Stats)], I),
+        "mpm_sync": ([P], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _LIB = L
+    return L
+
+
+def _ptr(x):
+    """(pointer, mem) of a C-contiguous float64 NumPy array or torch CUDA tensor."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a C-contiguous float64 array")
+        return ctypes.c_void_p(x.ctypes.data), MEM_HOST
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError("expected a contiguous float64 tensor")
+        return ctypes.c_void_p(x.data_ptr()), (MEM_DEVICE if x.is_cuda else MEM_HOST)
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+class Context:
+    """One mpm_ctx: R realisations of an nx x ny grid on [0,Lx]x[0,Ly]."""
+
+    def __init__(self, R, nx, ny, Lx=1.0, Ly=None, stream=None):
+        self.L = load()
+        self.R, self.nx, self.ny = int(R), int(nx), int(ny)
+        Ly = Lx * ny / nx if Ly is None else Ly
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(0 if stream is None else int(stream))
+        rc = self.L.mpm_create(ctypes.byref(h), self.R, self.nx, self.ny, float(Lx), float(Ly), st)
+        if rc != MPM_OK:
+            raise MPMError(rc, "mpm_create failed (sizes or non-square cells)")
+        self.h = h
+
+    def _ck(self, rc):
+        if rc != MPM_OK:
+            raise MPMError(rc, self.L.mpm_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mpm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- setters
+    def set_precision(self, mode, ir_tol=1e-13, ir_max=20):
+        self._ck(self.L.mpm_set_precision(self.h, int(mode), float(ir_tol), int(ir_max)))
+
+    def set_permeability(self, K):
+        p, mem = _ptr(K)
+        self._ck(self.L.mpm_set_permeability(self.h, p, mem))
+
+    def set_source(self, q=None):
+        if q is None:
+            self._ck(self.L.mpm_set_source(self.h, None, MEM_HOST))
+        else:
+            p, mem = _ptr(q)
+            self._ck(self.L.mpm_set_source(self.h, p, mem))
+
+    def set_fluids(self, M):
+        self._ck(self.L.mpm_set_fluids(self.h, float(M)))
+
+    def set_boundary(self, types, vals, s_inflow=1.0):
+        t = (ctypes.c_int * 4)(*[int(v) for v in types])
+        v = (ctypes.c_double * 4)(*[float(x) for x in vals])
+        self._ck(self.L.mpm_set_boundary(self.h, t, v, float(s_inflow)))
+
+    def set_decomposition(self, col_w, row_h, seg_len=4, degree=1, alpha=1.0):
+        cw = (ctypes.c_int * len(col_w))(*[int(v) for v in col_w])
+        rh = (ctypes.c_int * len(row_h))(*[int(v) for v in row_h])
+        self._ck(self.L.mpm_set_decomposition(self.h, len(col_w), cw, len(row_h), rh, int(seg_len), int(degree),
+                                              float(alpha)))
+
+    def set_saturation(self, s):
+        p, mem = _ptr(s)
+        self._ck(self.L.mpm_set_saturation(self.h, p, mem))
+
+    # ---- hot path
+    def build_basis(self):
+        self._ck(self.L.mpm_build_basis(self.h))
+
+    def eval_epsilon(self, host=True):
+        if not host:
+            self._ck(self.L.mpm_eval_epsilon(self.h, None))
+            return None
+        out = np.zeros(self.R)
+        self._ck(self.L.mpm_eval_epsilon(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def choose(self, eta, host=True):
+        if not host:
+            self._ck(self.L.mpm_choose(self.h, float(eta), None))
+            return None
+        out = np.zeros(self.R, dtype=np.int32)
+        self._ck(self.L.mpm_choose(self.h, float(eta), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return out
+
+    def perturbation_solve(self):
+        self._ck(self.L.mpm_perturbation_solve(self.h))
+
+    def interface_solve(self):
+        self._ck(self.L.mpm_interface_solve(self.h))
+
+    def downscale(self):
+        self._ck(self.L.mpm_downscale(self.h))
+
+    def saturation_step(self, cfl=0.5, n_sub=1, host=True):
+        if not host:
+            self._ck(self.L.mpm_saturation_step(self.h, float(cfl), int(n_sub), None))
+            return None
+        out = np.zeros(self.R)
+        self._ck(self.L.mpm_saturation_step(self.h, float(cfl), int(n_sub),
+                                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def init(self, eta):
+        self._ck(self.L.mpm_init(self.h, float(eta)))
+
+    def step(self, eta, cfl=0.5, n_sub=1):
+        self._ck(self.L.mpm_step(self.h, float(eta), float(cfl), int(n_sub)))
+
+    def sync(self):
+        self._ck(self.L.mpm_sync(self.h))
+
+    # ---- getters (host NumPy by default, or into a given array / CUDA tensor)
+    def _get(self, fn, shape, out, *extra):
+        if out is None:
+            out = np.zeros(shape)
+        p, mem = _ptr(out)
+        self._ck(fn(self.h, p, *extra, mem))
+        return out
+
+    def get_pressure(self, which=P_DOWNSCALED, out=None):
+        if out is None:
+            out = np.zeros((self.R, self.ny, self.nx))
+        p, mem = _ptr(out)
+        self._ck(self.L.mpm_get_pressure(self.h, p, int(which), mem))
+        return out
+
+    def get_flux(self, ux=None, uy=None):
+        ux = np.zeros((self.R, self.ny, self.nx + 1)) if ux is None else ux
+        uy = np.zeros((self.R, self.ny + 1, self.nx)) if uy is None else uy
+        pu, mem = _ptr(ux)
+        pv, _ = _ptr(uy)
+        self._ck(self.L.mpm_get_flux(self.h, pu, pv, mem))
+        return ux, uy
+
+    def get_saturation(self, out=None):
+        return self._get(self.L.mpm_get_saturation, (self.R, self.ny, self.nx), out)
+
+    def get_conductivity(self, out=None):
+        return self._get(self.L.mpm_get_conductivity, (self.R, self.ny, self.nx), out)
+
+    def get_stats(self):
+        st = Stats()
+        self._ck(self.L.mpm_get_stats(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in Stats._fields_}

@@ -1,0 +1,303 @@
+// Fine-grid stencil kernels of the MPM-2P step (HBM-bound, FP64).
+//
+//  - kappa^n = lambda(s) K and the partial sums of epsilon (Section 4.1, Algorithm 1).
+//  - MPM residual r = q h^2 - sum_faces F(kappa^n, p^m) (Eq. mpm_tf_3).
+//  - interface / boundary fluxes u_bar (mean of one-sided traces, plus F_n(p^m) on
+//    MPM-2P updates: u_bar = uhat_0 - kappa^n grad p^m, Section 4.1).
+//  - CFL time step and explicit upwind transport (Section 4, Eq. BL2D).
+#include "mpm2p_internal.cuh"
+
+namespace mpm {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double mobility(double s, double M) {
+  const double o = 1.0 - s;
+  return M * s * s + o * o;
+}
+
+__device__ __forceinline__ double fracflow(double s, double M) {
+  const double lw = M * s * s;
+  const double o = 1.0 - s;
+  return lw / (lw + o * o);
+}
+
+__device__ __forceinline__ double harm(double a, double b) { return 2.0 * a * b / (a + b); }
+
+
+__device__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  return v;  // valid in thread 0
+}
+
+__device__ double block_max(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  __syncthreads();
+  return v;
+}
+
+// kappa^n = lambda(s) K; optional partial sums of (kappa^n - kappa^m)^2 and (kappa^m)^2.
+__global__ void k_mobility_eps(Grid g, DevState d, int with_eps) {
+  __shared__ double sh[32];
+  const int r = blockIdx.y;
+  const long long n = g.ncell();
+  const long long base = (long long)r * n;
+  double num = 0.0, den = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    const double kn = mobility(d.s[base + c], g.M) * d.K[base + c];
+    d.kap_n[base + c] = kn;
+    if (with_eps) {
+      const double km = d.kap_m[base + c];
+      num += (kn - km) * (kn - km);
+      den += km * km;
+    }
+  }
+  if (!with_eps) return;
+  num = block_sum(num, sh);
+  den = block_sum(den, sh);
+  if (threadIdx.x == 0) {
+    d.eps_part[((long long)r * gridDim.x + blockIdx.x) * 2 + 0] = num;
+    d.eps_part[((long long)r * gridDim.x + blockIdx.x) * 2 + 1] = den;
+  }
+}
+
+__global__ void k_eps_finalize(Grid g, DevState d, int nblk) {
+  __shared__ double sh[32];
+  const int r = blockIdx.x;
+  double num = 0.0, den = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    num += d.eps_part[((long long)r * nblk + b) * 2 + 0];
+    den += d.eps_part[((long long)r * nblk + b) * 2 + 1];
+  }
+  num = block_sum(num, sh);
+  den = block_sum(den, sh);
+  if (threadIdx.x == 0) d.eps[r] = den > 0.0 ? sqrt(num) / sqrt(den) : 0.0;
+}
+
+__global__ void k_choose(Grid g, DevState d, double eta) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < g.R) d.rebuild[r] = d.eps[r] > eta ? 1 : 0;
+}
+
+__global__ void k_fill_flags(Grid g, DevState d, int v) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < g.R) d.rebuild[r] = v;
+}
+
+__global__ void k_copy_kappa_m(Grid g, DevState d) {
+  const int r = blockIdx.y;
+  if (d.rebuild[r] != 1) return;
+  const long long n = g.ncell();
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x)
+    d.kap_m[(long long)r * n + c] = d.kap_n[(long long)r * n + c];
+}
+
+// Outward integrated flux of pressure p through a physical boundary face of cell value
+// (kc, pc) on side `side` (Dirichlet: 2 kc (pc - g); Neumann: z h).
+__device__ __forceinline__ double phys_flux(const Grid& g, int side, double kc, double pc) {
+  return g.bc_type[side] == 0 ? 2.0 * kc * (pc - g.bc_val[side]) : g.bc_val[side] * g.h;
+}
+
+// r_c = q_c h^2 - sum_faces F_out(kappa^n, p^m): residual of the fine system at p^m.
+__global__ void k_residual(Grid g, DevState d) {
+  const int r = blockIdx.y;
+  if (d.rebuild[r] != 0) return;
+  const int nx = g.nx, ny = g.ny;
+  const long long n = g.ncell(), base = (long long)r * n;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
+    const double kc = d.kap_n[base + c], pc = d.p_m[base + c];
+    double out = 0.0;
+    if (i > 0) out += harm(kc, d.kap_n[base + c - 1]) * (pc - d.p_m[base + c - 1]);
+    else out += phys_flux(g, 0, kc, pc);
+    if (i < nx - 1) out += harm(kc, d.kap_n[base + c + 1]) * (pc - d.p_m[base + c + 1]);
+    else out += phys_flux(g, 1, kc, pc);
+    if (j > 0) out += harm(kc, d.kap_n[base + c - nx]) * (pc - d.p_m[base + c - nx]);
+    else out += phys_flux(g, 2, kc, pc);
+    if (j < ny - 1) out += harm(kc, d.kap_n[base + c + nx]) * (pc - d.p_m[base + c + nx]);
+    else out += phys_flux(g, 3, kc, pc);
+    d.resid[base + c] = d.q[base + c] * g.h * g.h - out;
+  }
+}
+
+// u_bar on every subdomain-boundary face, written into ux / uy.  One thread per face of
+// the sides a subdomain owns: its physical sides and its right / top interface sides.
+// branch = 1: after a basis build (mean of the MRCM traces); branch = 0: after a
+// perturbation solve (mean of the epsilon^0 traces plus F_n(p^m)).
+__global__ void k_ubar(Grid g, DevState d, const DevSub* subs, int branch) {
+  const int r = blockIdx.y;
+  if (d.rebuild[r] != branch) return;
+  const int add_fn = branch == 0;
+  const int sidx = blockIdx.x;
+  const DevSub sd = subs[sidx];
+  const int nx = g.nx;
+  const long long cb = (long long)r * g.ncell();
+  const int nface = 2 * (sd.a + sd.b);
+  for (int f = threadIdx.x; f < nface; f += blockDim.x) {
+    int side, t;
+    if (f < sd.b) { side = 0; t = f; }
+    else if (f < 2 * sd.b) { side = 1; t = f - sd.b; }
+    else if (f < 2 * sd.b + sd.a) { side = 2; t = f - 2 * sd.b; }
+    else { side = 3; t = f - 2 * sd.b - sd.a; }
+    const bool iface = sd.side_kind[side] == 1;
+    if (iface && (side == 0 || side == 2)) continue;  // written by the neighbour
+    int ci, cj;  // cell of this subdomain adjacent to the face
+    if (side == 0) { ci = sd.x0; cj = sd.y0 + t; }
+    else if (side == 1) { ci = sd.x0 + sd.a - 1; cj = sd.y0 + t; }
+    else if (side == 2) { ci = sd.x0 + t; cj = sd.y0; }
+    else { ci = sd.x0 + t; cj = sd.y0 + sd.b - 1; }
+    const long long c = (long long)cj * nx + ci;
+    const double Fout = d.trace[(long long)r * d.st_face + sd.face_off + f];
+    double val;  // in +x / +y direction
+    if (iface) {
+      const DevSub nb = subs[sd.side_nbr[side]];
+      const int nf_nb = side == 1 ? face_side_off(0, nb.a, nb.b) + t : face_side_off(2, nb.a, nb.b) + t;
+      const double Fnb = d.trace[(long long)r * d.st_face + nb.face_off + nf_nb];
+      val = 0.5 * (Fout - Fnb);
+      if (add_fn) {
+        const long long cn = side == 1 ? c + 1 : c + nx;
+        val += harm(d.kap_n[cb + c], d.kap_n[cb + cn]) * (d.p_m[cb + c] - d.p_m[cb + cn]);
+      }
+    } else {
+      double out = Fout;
+      if (add_fn) {
+        // the perturbation traces carry homogeneous physical data; add F_n(p^m)
+        out += g.bc_type[side] == 0 ? 2.0 * d.kap_n[cb + c] * (d.p_m[cb + c] - g.bc_val[side])
+                                    : g.bc_val[side] * g.h;
+      }
+      val = (side == 0 || side == 2) ? -out : out;
+    }
+    if (side == 0) d.ux[(long long)r * g.nfx() + (long long)cj * (nx + 1) + ci] = val;
+    else if (side == 1) d.ux[(long long)r * g.nfx() + (long long)cj * (nx + 1) + ci + 1] = val;
+    else if (side == 2) d.uy[(long long)r * g.nfy() + (long long)cj * nx + ci] = val;
+    else d.uy[(long long)r * g.nfy() + (long long)(cj + 1) * nx + ci] = val;
+  }
+}
+
+// max over cells of max(total outflow, total inflow) -> dt per realisation.
+__global__ void k_cfl_part(Grid g, DevState d) {
+  __shared__ double sh[32];
+  const int r = blockIdx.y;
+  const int nx = g.nx;
+  const long long n = g.ncell();
+  double m = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
+    const double* ux = d.ux + (long long)r * g.nfx();
+    const double* uy = d.uy + (long long)r * g.nfy();
+    const double f0 = -ux[(long long)j * (nx + 1) + i], f1 = ux[(long long)j * (nx + 1) + i + 1];
+    const double f2 = -uy[(long long)j * nx + i], f3 = uy[(long long)(j + 1) * nx + i];
+    const double out = fmax(f0, 0.0) + fmax(f1, 0.0) + fmax(f2, 0.0) + fmax(f3, 0.0);
+    const double in = fmax(-f0, 0.0) + fmax(-f1, 0.0) + fmax(-f2, 0.0) + fmax(-f3, 0.0);
+    m = fmax(m, fmax(out, in));
+  }
+  m = block_max(m, sh);
+  if (threadIdx.x == 0) d.rate_part[(long long)r * gridDim.x + blockIdx.x] = m;
+}
+
+__global__ void k_cfl_finalize(Grid g, DevState d, int nblk, double cfl, double fmax_) {
+  __shared__ double sh[32];
+  const int r = blockIdx.x;
+  double m = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) m = fmax(m, d.rate_part[(long long)r * nblk + b]);
+  m = block_max(m, sh);
+  if (threadIdx.x == 0) d.dt[r] = m > 0.0 ? cfl * g.h * g.h / (fmax_ * m) : 0.0;
+}
+
+// s2_c = s_c - dt/h^2 sum_faces F_out f(s_upwind); inflow through the boundary carries s_inflow.
+__global__ void k_upwind(Grid g, DevState d) {
+  const int r = blockIdx.y;
+  const int nx = g.nx, ny = g.ny;
+  const long long n = g.ncell(), base = (long long)r * n;
+  const double lam = d.dt[r] / (g.h * g.h);
+  const double* ux = d.ux + (long long)r * g.nfx();
+  const double* uy = d.uy + (long long)r * g.nfy();
+  const double* s = d.s + base;
+  const double f_in = fracflow(g.s_inflow, g.M);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
+    const double sc = s[c], fc = fracflow(sc, g.M);
+    double acc = 0.0, F;
+    F = -ux[(long long)j * (nx + 1) + i];
+    if (F > 0.0) acc += F * fc;
+    else if (F < 0.0) acc += F * (i > 0 ? fracflow(s[c - 1], g.M) : f_in);
+    F = ux[(long long)j * (nx + 1) + i + 1];
+    if (F > 0.0) acc += F * fc;
+    else if (F < 0.0) acc += F * (i < nx - 1 ? fracflow(s[c + 1], g.M) : f_in);
+    F = -uy[(long long)j * nx + i];
+    if (F > 0.0) acc += F * fc;
+    else if (F < 0.0) acc += F * (j > 0 ? fracflow(s[c - nx], g.M) : f_in);
+    F = uy[(long long)(j + 1) * nx + i];
+    if (F > 0.0) acc += F * fc;
+    else if (F < 0.0) acc += F * (j < ny - 1 ? fracflow(s[c + nx], g.M) : f_in);
+    d.s2[base + c] = sc - lam * acc;
+  }
+}
+
+int cell_blocks(const Grid& g) {
+  long long nb = (g.ncell() + kThreads - 1) / kThreads;
+  return (int)(nb < 1024 ? nb : 1024);
+}
+
+}  // namespace
+
+int grid_cell_blocks(const Grid& g) { return cell_blocks(g); }
+
+void launch_mobility_eps(const Grid& g, const DevState& d, bool with_eps, cudaStream_t st) {
+  dim3 grid(cell_blocks(g), g.R);
+  k_mobility_eps<<<grid, kThreads, 0, st>>>(g, d, with_eps ? 1 : 0);
+  if (with_eps) k_eps_finalize<<<g.R, kThreads, 0, st>>>(g, d, grid.x);
+}
+
+void launch_choose(const Grid& g, const DevState& d, double eta, cudaStream_t st) {
+  k_choose<<<(g.R + 127) / 128, 128, 0, st>>>(g, d, eta);
+}
+
+void launch_fill_flags(const Grid& g, const DevState& d, int v, cudaStream_t st) {
+  k_fill_flags<<<(g.R + 127) / 128, 128, 0, st>>>(g, d, v);
+}
+
+void launch_copy_kappa_m(const Grid& g, const DevState& d, cudaStream_t st) {
+  k_copy_kappa_m<<<dim3(cell_blocks(g), g.R), kThreads, 0, st>>>(g, d);
+}
+
+void launch_residual(const Grid& g, const DevState& d, cudaStream_t st) {
+  k_residual<<<dim3(cell_blocks(g), g.R), kThreads, 0, st>>>(g, d);
+}
+
+void launch_ubar(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int branch,
+                 cudaStream_t st) {
+  k_ubar<<<dim3(nsub, g.R), 128, 0, st>>>(g, d, subs, branch);
+}
+
+void launch_cfl(const Grid& g, const DevState& d, double cfl, double fmax_, cudaStream_t st) {
+  const int nb = cell_blocks(g);
+  k_cfl_part<<<dim3(nb, g.R), kThreads, 0, st>>>(g, d);
+  k_cfl_finalize<<<g.R, kThreads, 0, st>>>(g, d, nb, cfl, fmax_);
+}
+
+void launch_upwind(const Grid& g, const DevState& d, cudaStream_t st) {
+  k_upwind<<<dim3(cell_blocks(g), g.R), kThreads, 0, st>>>(g, d);
+}
+
+}  // namespace mpm

@@ -1,0 +1,703 @@
+// Local problems on the subdomains: Robin problems of the MRCM (Eq. mrc1 with the
+// split Eqs. mrc_homogeneous / mrc_non_homogeneous), the MPM-2P epsilon^0 local solve
+// (Eq. mpm_tf_3 with zero Robin data) and the Neumann downscaling (Eq. mpm_upd).
+//
+// Discretisation (two-point fluxes on the a x b cells of a subdomain, row-major local
+// index c = jl * a + il):
+//   interior face (harmonic):     T = 2 ka kb / (ka + kb)
+//   Robin interface face:         r_e = kappa_c / (1/2 + rho), rho = alpha H / h
+//   Dirichlet physical face:      2 kappa_c          Neumann face: 0
+// The matrix is block tridiagonal over grid rows: A = tridiag(-diag(t_{j-1}), D_j,
+// -diag(t_j)), D_j tridiagonal.  The block LDL^T with explicit inverse pivots
+//   S_0 = D_0,  S_j = D_j - diag(t_{j-1}) Q_{j-1} diag(t_{j-1}),  Q_j = S_j^{-1}
+// only needs elementwise updates between pivots (the coupling blocks are diagonal),
+// and each Q_j comes from an in-place Gauss-Jordan inversion held one entry per thread.
+// Solves are 2b dependent dense a x a block products (GEMV / small GEMM per block row):
+//   forward  W_j = Q_j (f_j + t_{j-1} o W_{j-1})
+//   backward X_j = W_j + Q_j (t_j o X_{j+1})
+// In FP32 mode the factor is built from the Jacobi-scaled matrix S A S,
+// S = diag(A)^{-1/2}, and FP64 iterative refinement against the FP64 stencil recovers
+// FP64 accuracy.
+#include "mpm2p_internal.cuh"
+
+namespace mpm {
+
+namespace {
+
+constexpr int kSmemBudget = 200 * 1024;
+
+__device__ __forceinline__ double harm(double a, double b) { return 2.0 * a * b / (a + b); }
+
+// Value at edge t of a side basis function kk (seg = kk / (degree+1), power = kk % (degree+1)):
+// Legendre {1, 2 xi - 1} on the segment, evaluated at the edge midpoint.
+__device__ __forceinline__ double side_basis(int kk, int t, int seg_len, int degree) {
+  const int nb = degree + 1;
+  const int seg = kk / nb, pw = kk - seg * nb;
+  if (t / seg_len != seg) return 0.0;
+  if (pw == 0) return 1.0;
+  const double xi = ((t % seg_len) + 0.5) / seg_len;
+  return 2.0 * xi - 1.0;
+}
+
+// Local cell adjacent to face f, and the side / position of the face.
+__device__ __forceinline__ void face_info(const DevSub& sd, int f, int& side, int& t, int& cl) {
+  if (f < sd.b) { side = 0; t = f; cl = t * sd.a; }
+  else if (f < 2 * sd.b) { side = 1; t = f - sd.b; cl = t * sd.a + sd.a - 1; }
+  else if (f < 2 * sd.b + sd.a) { side = 2; t = f - 2 * sd.b; cl = t; }
+  else { side = 3; t = f - 2 * sd.b - sd.a; cl = (sd.b - 1) * sd.a + t; }
+}
+
+// Shared-memory layout of one subdomain problem.
+struct Stencil {
+  double* kap;   // m
+  double* dia;   // m   diagonal of A (FP64)
+  double* wE;    // m   transmissibility to the east neighbour (0 on the last column)
+  double* wN;    // m   transmissibility to the north neighbour (0 on the last row)
+  double* sc;    // m   Jacobi scaling (1 in FP64 mode)
+};
+
+// Fill the FP64 stencil of the Robin (neumann = 0) or pinned Neumann (neumann = 1) problem.
+__device__ void build_stencil(const Grid& g, const DevSub& sd, const double* kap_glob, int neumann,
+                              int scale, Stencil S) {
+  const int a = sd.a, b = sd.b, m = a * b;
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    const int jl = c / a, il = c - jl * a;
+    S.kap[c] = kap_glob[(long long)(sd.y0 + jl) * g.nx + sd.x0 + il];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    const int jl = c / a, il = c - jl * a;
+    const double kc = S.kap[c];
+    const double we = il < a - 1 ? harm(kc, S.kap[c + 1]) : 0.0;
+    const double wn = jl < b - 1 ? harm(kc, S.kap[c + a]) : 0.0;
+    double dg = we + wn;
+    if (il > 0) dg += harm(kc, S.kap[c - 1]);
+    if (jl > 0) dg += harm(kc, S.kap[c - a]);
+    if (!neumann) {
+      const int sides[4] = {il == 0 ? 0 : -1, il == a - 1 ? 1 : -1, jl == 0 ? 2 : -1, jl == b - 1 ? 3 : -1};
+      for (int q = 0; q < 4; ++q) {
+        const int sdx = sides[q];
+        if (sdx < 0) continue;
+        if (sd.side_kind[sdx] == 1) dg += kc / (0.5 + sd.side_rho[sdx]);
+        else if (g.bc_type[sdx] == 0) dg += 2.0 * kc;
+      }
+    } else if (c == 0) {
+      dg += kc;  // pin: A + kappa_0 e_0 e_0^T
+    }
+    S.wE[c] = we;
+    S.wN[c] = wn;
+    S.dia[c] = dg;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < m; c += blockDim.x) S.sc[c] = scale ? rsqrt(S.dia[c]) : 1.0;
+  __syncthreads();
+}
+
+// In-place Gauss-Jordan inversion of an a x a matrix held one entry per thread
+// (thread (i, k) holds v = M[i][k]).  pub: 2 * (2 kMaxSide + 1) values of shared memory.
+template <typename T>
+__device__ void gj_invert(T& v, int i, int k, int a, bool active, T* pub) {
+  constexpr int L = 2 * kMaxSide + 1;
+  for (int p = 0; p < a; ++p) {
+    T* buf = pub + (p & 1) * L;
+    if (active) {
+      if (k == p) buf[i] = v;
+      if (i == p) buf[kMaxSide + k] = v;
+      if (i == p && k == p) buf[2 * kMaxSide] = T(1) / v;
+    }
+    __syncthreads();
+    if (active) {
+      const T ip = buf[2 * kMaxSide];
+      const T mip = buf[i], mpk = buf[kMaxSide + k];
+      if (i == p && k == p) v = ip;
+      else if (i == p) v = mpk * ip;
+      else if (k == p) v = -mip * ip;
+      else v = v - mip * (mpk * ip);
+    }
+  }
+  __syncthreads();
+}
+
+// Block factorisation of the (scaled) stencil into Q_0..Q_{b-1} (written to Qout,
+// b*a*a values).  Requires blockDim.x >= a*a.
+template <typename T>
+__device__ void block_factor(const DevSub& sd, Stencil S, T* Qout, T* pub) {
+  const int a = sd.a, b = sd.b;
+  const int tid = threadIdx.x;
+  const bool active = tid < a * a;
+  const int i = active ? tid / a : 0, k = active ? tid - (tid / a) * a : 0;
+  T v = T(0);
+  for (int j = 0; j < b; ++j) {
+    if (active) {
+      const int ci = j * a + i, ck = j * a + k;
+      double dij = 0.0;
+      if (i == k) dij = S.dia[ci] * S.sc[ci] * S.sc[ci];
+      else if (k == i + 1) dij = -S.wE[ci] * S.sc[ci] * S.sc[ck];
+      else if (i == k + 1) dij = -S.wE[ck] * S.sc[ci] * S.sc[ck];
+      T s = T(dij);
+      if (j > 0) {
+        const int pi = ci - a, pk = ck - a;
+        const T ti = T(S.wN[pi] * S.sc[pi] * S.sc[ci]);
+        const T tk = T(S.wN[pk] * S.sc[pk] * S.sc[ck]);
+        s -= ti * v * tk;
+      }
+      v = s;
+    }
+    gj_invert<T>(v, i, k, a, active, pub);
+    if (active) Qout[(long long)j * a * a + i * a + k] = v;
+  }
+  __syncthreads();
+}
+
+// Multi-RHS block solve  (S A S) X = Z  in place on Z ([m][ncol], column stride ncol),
+// W: workspace of the same shape.  Q: b*a*a factor in shared memory.
+template <typename T>
+__device__ void block_solve(const DevSub& sd, Stencil S, const T* Q, T* Z, T* W, int ncol) {
+  const int a = sd.a, b = sd.b;
+  const int nwork = a * ncol;
+  for (int j = 0; j < b; ++j) {
+    const T* Qj = Q + (long long)j * a * a;
+    for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
+      const int i = w / ncol, col = w - (w / ncol) * ncol;
+      T acc = T(0);
+      for (int k = 0; k < a; ++k) {
+        const int ck = j * a + k;
+        T zk = Z[ck * ncol + col];
+        if (j > 0) {
+          const int pk = ck - a;
+          zk += T(S.wN[pk] * S.sc[pk] * S.sc[ck]) * W[pk * ncol + col];
+        }
+        acc += Qj[i * a + k] * zk;
+      }
+      W[(j * a + i) * ncol + col] = acc;
+    }
+    __syncthreads();
+  }
+  // backward: X_{b-1} = W_{b-1}; X_j = W_j + Q_j (t_j o X_{j+1}); X stored in Z
+  for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
+    const int i = w / ncol, col = w - (w / ncol) * ncol;
+    Z[((b - 1) * a + i) * ncol + col] = W[((b - 1) * a + i) * ncol + col];
+  }
+  __syncthreads();
+  for (int j = b - 2; j >= 0; --j) {
+    const T* Qj = Q + (long long)j * a * a;
+    for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
+      const int i = w / ncol, col = w - (w / ncol) * ncol;
+      T acc = W[(j * a + i) * ncol + col];
+      for (int k = 0; k < a; ++k) {
+        const int ck = j * a + k, nk = ck + a;
+        acc += Qj[i * a + k] * (T(S.wN[ck] * S.sc[ck] * S.sc[nk]) * Z[nk * ncol + col]);
+      }
+      Z[(j * a + i) * ncol + col] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// (A x)_c with the FP64 stencil, x with column stride ncol.
+__device__ __forceinline__ double apply_A(const DevSub& sd, const Stencil& S, const double* x, int c,
+                                          int col, int ncol) {
+  const int a = sd.a, b = sd.b;
+  const int jl = c / a, il = c - jl * a;
+  double v = S.dia[c] * x[c * ncol + col];
+  if (il < a - 1) v -= S.wE[c] * x[(c + 1) * ncol + col];
+  if (il > 0) v -= S.wE[c - 1] * x[(c - 1) * ncol + col];
+  if (jl < b - 1) v -= S.wN[c] * x[(c + a) * ncol + col];
+  if (jl > 0) v -= S.wN[c - a] * x[(c - a) * ncol + col];
+  return v;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), __double_as_longlong(v));
+}
+
+// Solve A X = B for ncol right-hand sides (B, X FP64 [m][ncol]).  FP64 mode: one block
+// solve.  FP32 mode: refinement  x += S solve(S r),  r = b - A x, until
+// max|r| <= tol max|b| per column or ir_max sweeps.  R, Zw, Ww: workspaces.
+template <typename T>
+__device__ void solve_refined(const DevSub& sd, Stencil S, const T* Q, const double* B, double* X,
+                              double* Rr, T* Zw, T* Ww, int ncol, bool refine, double tol, int ir_max,
+                              double* colmax /* 2*ncol */, int* status, int* ir_used) {
+  const int m = sd.a * sd.b;
+  const int n = m * ncol;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    X[e] = 0.0;
+    Rr[e] = B[e];
+  }
+  if (refine) {
+    for (int c = threadIdx.x; c < 2 * ncol; c += blockDim.x) colmax[c] = 0.0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) atomic_max_nonneg(&colmax[e % ncol], fabs(B[e]));
+  }
+  __syncthreads();
+  const int sweeps = refine ? ir_max : 1;
+  int it = 0;
+  for (; it < sweeps; ++it) {
+    for (int e = threadIdx.x; e < n; e += blockDim.x) Zw[e] = T(Rr[e] * S.sc[e / ncol]);
+    __syncthreads();
+    block_solve<T>(sd, S, Q, Zw, Ww, ncol);
+    for (int e = threadIdx.x; e < n; e += blockDim.x) X[e] += double(Zw[e]) * S.sc[e / ncol];
+    __syncthreads();
+    if (!refine) break;
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) colmax[ncol + c] = 0.0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int c = e / ncol, col = e - c * ncol;
+      const double r = B[e] - apply_A(sd, S, X, c, col, ncol);
+      Rr[e] = r;
+      atomic_max_nonneg(&colmax[ncol + col], fabs(r));
+    }
+    __syncthreads();
+    bool done = true;
+    for (int col = 0; col < ncol; ++col)
+      if (colmax[ncol + col] > tol * colmax[col]) done = false;
+    __syncthreads();
+    if (done) { ++it; break; }
+  }
+  if (threadIdx.x == 0) {
+    if (refine) {
+      bool ok = true;
+      for (int col = 0; col < ncol; ++col)
+        if (colmax[ncol + col] > tol * colmax[col]) ok = false;
+      if (!ok) atomicOr(status, 1);
+    }
+    atomicMax(ir_used, it);
+  }
+  __syncthreads();
+}
+
+struct SmemPlan {
+  int ncol;
+  size_t bytes;
+};
+
+__host__ __device__ inline size_t stencil_bytes(int m) { return (size_t)5 * m * sizeof(double); }
+
+template <typename T>
+size_t fixed_bytes(int a, int b) {
+  const int m = a * b;
+  return stencil_bytes(m) + (size_t)b * a * a * sizeof(T) + 4 * (2 * kMaxSide + 1) * sizeof(T) +
+         64 * sizeof(double) + 256;
+}
+
+template <typename T>
+SmemPlan plan_smem(int a, int b, int ncol_max) {
+  const int m = a * b;
+  const size_t fixed = fixed_bytes<T>(a, b);
+  const size_t per_col = (size_t)m * (3 * sizeof(double) + 2 * sizeof(T)) + 2 * sizeof(double);
+  int ncol = (int)((kSmemBudget - fixed) / per_col);
+  if (ncol > ncol_max) ncol = ncol_max;
+  if (ncol < 1) ncol = 1;
+  return {ncol, fixed + per_col * ncol};
+}
+
+template <typename T>
+struct Carve {
+  Stencil S;
+  T* Q;
+  T* pub;
+  double* colmax;
+  double *B, *X, *Rr;
+  T *Zw, *Ww;
+};
+
+template <typename T>
+__device__ Carve<T> carve(char* base, int a, int b, int ncol) {
+  const int m = a * b;
+  Carve<T> c;
+  double* p = reinterpret_cast<double*>(base);
+  c.S.kap = p; p += m;
+  c.S.dia = p; p += m;
+  c.S.wE = p; p += m;
+  c.S.wN = p; p += m;
+  c.S.sc = p; p += m;
+  c.colmax = p; p += 64;
+  c.B = p; p += (size_t)m * ncol;
+  c.X = p; p += (size_t)m * ncol;
+  c.Rr = p; p += (size_t)m * ncol;
+  T* q = reinterpret_cast<T*>(p);
+  c.Q = q; q += (size_t)b * a * a;
+  c.Zw = q; q += (size_t)m * ncol;
+  c.Ww = q; q += (size_t)m * ncol;
+  c.pub = q;
+  return c;
+}
+
+int threads_for(int a) {
+  int t = a * a;
+  if (t < 256) t = 256;
+  return (t + 31) / 32 * 32;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Robin factorisation at kappa^n (rebuild realisations), stored for reuse by MPM-2P.
+// Stored per subdomain: Q blocks (factor type) and [dia, wE, wN, sc] (FP64).
+template <typename T>
+__global__ void k_robin_factor(Grid g, DevState d, const DevSub* subs, int scale) {
+  extern __shared__ __align__(16) char smem[];
+  const int r = blockIdx.y;
+  if (d.rebuild[r] != 1) return;
+  const DevSub sd = subs[blockIdx.x];
+  const int a = sd.a, b = sd.b, m = a * b;
+  Carve<T> cv = carve<T>(smem, a, b, 1);
+  build_stencil(g, sd, d.kap_n + (long long)r * g.ncell(), 0, scale, cv.S);
+  T* Qg = reinterpret_cast<T*>(d.fac) + (long long)r * d.st_fac + sd.q_off;
+  block_factor<T>(sd, cv.S, Qg, cv.pub);
+  double* tv = d.tvec + (long long)r * d.st_t + sd.t_off;
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    tv[c] = cv.S.dia[c];
+    tv[m + c] = cv.S.wE[c];
+    tv[2 * m + c] = cv.S.wN[c];
+    tv[3 * m + c] = cv.S.sc[c];
+  }
+}
+
+// Load the stored Robin factor and stencil of kappa^m into shared memory.
+template <typename T>
+__device__ void load_robin(const DevState& d, const DevSub& sd, int r, Carve<T>& cv, const Grid& g) {
+  const int a = sd.a, b = sd.b, m = a * b;
+  const T* Qg = reinterpret_cast<const T*>(d.fac) + (long long)r * d.st_fac + sd.q_off;
+  for (int e = threadIdx.x; e < b * a * a; e += blockDim.x) cv.Q[e] = Qg[e];
+  const double* tv = d.tvec + (long long)r * d.st_t + sd.t_off;
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    cv.S.dia[c] = tv[c];
+    cv.S.wE[c] = tv[m + c];
+    cv.S.wN[c] = tv[2 * m + c];
+    cv.S.sc[c] = tv[3 * m + c];
+    const int jl = c / a, il = c - jl * a;
+    cv.S.kap[c] = d.kap_m[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il];
+  }
+  __syncthreads();
+}
+
+// Right-hand side of the local problem for column `col` of the basis set: col < ndof is the
+// homogeneous BF of local DOF col (Robin datum g = -bh s phi on U-DOFs, g = psi on P-DOFs,
+// entering as r_e g_e; zero source and physical data), col == ndof the non-homogeneous BF
+// (source q h^2 and physical data, zero Robin data).
+__device__ double basis_rhs(const Grid& g, const DevState& d, const DevSub& sd, const Stencil& S, int r,
+                            int c, int col) {
+  const int a = sd.a, b = sd.b;
+  const int jl = c / a, il = c - jl * a;
+  const double kc = S.kap[c];
+  double v = 0.0;
+  if (col == sd.ndof) {
+    v = d.q[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il] * g.h * g.h;
+    const int sides[4] = {il == 0 ? 0 : -1, il == a - 1 ? 1 : -1, jl == 0 ? 2 : -1, jl == b - 1 ? 3 : -1};
+    for (int q = 0; q < 4; ++q) {
+      const int sdx = sides[q];
+      if (sdx < 0 || sd.side_kind[sdx] == 1) continue;
+      if (g.bc_type[sdx] == 0) v += 2.0 * kc * g.bc_val[sdx];
+      else v -= g.bc_val[sdx] * g.h;
+    }
+    return v;
+  }
+  // find the side of DOF col
+  for (int q = 0; q < 4; ++q) {
+    if (sd.side_kind[q] != 1) continue;
+    const int d0 = sd.side_dof0[q], nb = sd.side_nb[q];
+    if (col < d0 || col >= d0 + 2 * nb) continue;
+    const bool on_side = (q == 0 && il == 0) || (q == 1 && il == a - 1) || (q == 2 && jl == 0) ||
+                         (q == 3 && jl == b - 1);
+    if (!on_side) return 0.0;
+    const int t = (q < 2) ? jl : il;
+    const double rho = sd.side_rho[q];
+    const bool isU = col < d0 + nb;
+    const double phi = side_basis(isU ? col - d0 : col - d0 - nb, t, g.seg_len, g.degree);
+    // r_e g_e with r_e = kc/(1/2+rho): U: g = -(rho/kc) s phi -> -rho s phi/(1/2+rho); P: kc phi/(1/2+rho)
+    return isU ? -rho * sd.side_sign[q] * phi / (0.5 + rho) : kc * phi / (0.5 + rho);
+  }
+  return 0.0;
+}
+
+// Robin datum g_e of basis column col on face f (0 for the non-homogeneous column).
+__device__ double basis_g(const Grid& g, const DevSub& sd, const Stencil& S, int f, int col) {
+  if (col == sd.ndof) return 0.0;
+  int side, t, cl;
+  face_info(sd, f, side, t, cl);
+  if (sd.side_kind[side] != 1) return 0.0;
+  const int d0 = sd.side_dof0[side], nb = sd.side_nb[side];
+  if (col < d0 || col >= d0 + 2 * nb) return 0.0;
+  const bool isU = col < d0 + nb;
+  const double phi = side_basis(isU ? col - d0 : col - d0 - nb, t, g.seg_len, g.degree);
+  return isU ? -(sd.side_rho[side] / S.kap[cl]) * sd.side_sign[side] * phi : phi;
+}
+
+// Outward trace on face f of the local solution x (column col of X) of basis column bcol.
+__device__ double basis_trace(const Grid& g, const DevSub& sd, const Stencil& S, const double* X, int ncol,
+                              int f, int col, int bcol, bool homogeneous_phys) {
+  int side, t, cl;
+  face_info(sd, f, side, t, cl);
+  const double kc = S.kap[cl], pc = X[cl * ncol + col];
+  if (sd.side_kind[side] == 1) return kc / (0.5 + sd.side_rho[side]) * (pc - basis_g(g, sd, S, f, bcol));
+  if (g.bc_type[side] == 0) return 2.0 * kc * (pc - (homogeneous_phys ? 0.0 : g.bc_val[side]));
+  return homogeneous_phys ? 0.0 : g.bc_val[side] * g.h;
+}
+
+// All BF solves of a subdomain at once (rebuild): the ndof homogeneous BFs and the
+// non-homogeneous one, in column chunks.  Outputs: traces (tr, fbar), pressures (pf incl.
+// the non-homogeneous column), means (mu_hat, sub_mean).
+template <typename T>
+__global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int ncol_max, int refine,
+                              double tol, int ir_max) {
+  extern __shared__ __align__(16) char smem[];
+  const int r = blockIdx.y;
+  if (d.rebuild[r] != 1) return;
+  const DevSub sd = subs[blockIdx.x];
+  const int a = sd.a, b = sd.b, m = a * b;
+  const int nface = 2 * (a + b);
+  const int ntot = sd.ndof + 1;
+  Carve<T> cv = carve<T>(smem, a, b, ncol_max);
+  load_robin<T>(d, sd, r, cv, g);
+  double* tr = d.tr + (long long)r * d.st_tr + sd.tr_off;       // [nface][ndof]
+  double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;       // [m][ndof+1]
+  double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
+  double* muh = d.mu_hat + (long long)r * d.st_dof + sd.dof_off;
+  for (int c0 = 0; c0 < ntot; c0 += ncol_max) {
+    const int ncol = min(ncol_max, ntot - c0);
+    for (int e = threadIdx.x; e < m * ncol; e += blockDim.x) {
+      const int c = e / ncol, col = e - c * ncol;
+      cv.B[e] = basis_rhs(g, d, sd, cv.S, r, c, c0 + col);
+    }
+    __syncthreads();
+    solve_refined<T>(sd, cv.S, cv.Q, cv.B, cv.X, cv.Rr, cv.Zw, cv.Ww, ncol, refine != 0, tol, ir_max,
+                     cv.colmax, d.status, d.ir_iters);
+    for (int e = threadIdx.x; e < m * ncol; e += blockDim.x) {
+      const int c = e / ncol, col = e - c * ncol;
+      pf[(long long)c * ntot + c0 + col] = cv.X[e];
+    }
+    for (int e = threadIdx.x; e < nface * ncol; e += blockDim.x) {
+      const int f = e / ncol, col = e - f * ncol, bcol = c0 + col;
+      const double v = basis_trace(g, sd, cv.S, cv.X, ncol, f, col, bcol, bcol < sd.ndof);
+      if (bcol < sd.ndof) tr[(long long)f * sd.ndof + bcol] = v;
+      else fbar[f] = v;
+    }
+    // column means
+    for (int col = threadIdx.x >> 5; col < ncol; col += blockDim.x >> 5) {
+      double s = 0.0;
+      for (int c = threadIdx.x & 31; c < m; c += 32) s += cv.X[c * ncol + col];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if ((threadIdx.x & 31) == 0) {
+        const int bcol = c0 + col;
+        if (bcol < sd.ndof) muh[bcol] = s / m;
+        else d.sub_mean[(long long)r * d.st_sub + blockIdx.x] = s / m;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// MPM-2P local solve: A_i(kappa^m) dp = r_i with zero Robin data and homogeneous physical
+// data, using the stored factor.  Outputs the perturbation traces (fbar) and mean(dp).
+template <typename T>
+__global__ void k_mpm_local(Grid g, DevState d, const DevSub* subs, int refine, double tol, int ir_max) {
+  extern __shared__ __align__(16) char smem[];
+  const int r = blockIdx.y;
+  if (d.rebuild[r] != 0) return;
+  const DevSub sd = subs[blockIdx.x];
+  const int a = sd.a, b = sd.b, m = a * b;
+  const int nface = 2 * (a + b);
+  Carve<T> cv = carve<T>(smem, a, b, 1);
+  load_robin<T>(d, sd, r, cv, g);
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    const int jl = c / a, il = c - jl * a;
+    cv.B[c] = d.resid[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il];
+  }
+  __syncthreads();
+  solve_refined<T>(sd, cv.S, cv.Q, cv.B, cv.X, cv.Rr, cv.Zw, cv.Ww, 1, refine != 0, tol, ir_max, cv.colmax,
+                   d.status, d.ir_iters);
+  double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
+  for (int f = threadIdx.x; f < nface; f += blockDim.x)
+    fbar[f] = basis_trace(g, sd, cv.S, cv.X, 1, f, 0, sd.ndof, true);
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int c = threadIdx.x; c < m; c += 32) s += cv.X[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) d.sub_mean[(long long)r * d.st_sub + blockIdx.x] = s / m;
+  }
+}
+
+// Traces (and at a rebuild the MRCM-level pressure p^m) from the interface solution:
+//   rebuild: p^m = pbar + P_hat c, F = Fbar + F_hat c, target mean = mean(p^m)
+//   MPM-2P : F = dFbar + F_hat dc, target mean = mean(p^m) + mean(dpbar) + mu_hat . dc
+__global__ void k_reconstruct(Grid g, DevState d, const DevSub* subs, const DevNode* nodes,
+                              const int* leaf_node, int branch) {
+  __shared__ double cs[4 * kMaxSide * 4];
+  __shared__ double red[32];
+  const int r = blockIdx.y;
+  if (d.rebuild[r] != branch) return;
+  const int sidx = blockIdx.x;
+  const DevSub sd = subs[sidx];
+  const int a = sd.a, b = sd.b, m = a * b, nd = sd.ndof;
+  const int nface = 2 * (a + b);
+  if (nd > 0) {
+    const DevNode nd_leaf = nodes[leaf_node[sidx]];
+    const double* x = d.xvec + (long long)r * d.st_vec + nd_leaf.v_off;
+    for (int l = threadIdx.x; l < nd; l += blockDim.x) cs[l] = x[l];
+  }
+  __syncthreads();
+  const double* tr = d.tr + (long long)r * d.st_tr + sd.tr_off;
+  const double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
+  double* trace = d.trace + (long long)r * d.st_face + sd.face_off;
+  for (int f = threadIdx.x; f < nface; f += blockDim.x) {
+    double v = fbar[f];
+    for (int l = 0; l < nd; ++l) v += tr[(long long)f * nd + l] * cs[l];
+    trace[f] = v;
+  }
+  double part = 0.0;
+  if (branch == 1) {
+    const double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+      double v = pf[(long long)c * (nd + 1) + nd];
+      for (int l = 0; l < nd; ++l) v += pf[(long long)c * (nd + 1) + l] * cs[l];
+      const int jl = c / a, il = c - jl * a;
+      d.p_m[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il] = v;
+      part += v;
+    }
+  } else if (threadIdx.x == 0) {
+    const double* muh = d.mu_hat + (long long)r * d.st_dof + sd.dof_off;
+    part = d.sub_mean[(long long)r * d.st_sub + sidx] * m;
+    for (int l = 0; l < nd; ++l) part += muh[l] * cs[l] * m;
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    const long long si = (long long)r * d.st_sub + sidx;
+    if (branch == 1) {
+      d.pm_mean[si] = s / m;
+      d.sub_target[si] = s / m;
+    } else {
+      d.sub_target[si] = d.pm_mean[si] + s / m;
+    }
+  }
+}
+
+// Downscaling (Eq. mpm_upd): Neumann problem with kappa^n and the fluxes u_bar already
+// written on the subdomain boundary faces of ux / uy; factor + solve + refinement; the
+// pressure constant makes mean(p~) equal the target; writes p~ and the interior fluxes.
+template <typename T>
+__global__ void k_downscale(Grid g, DevState d, const DevSub* subs, int refine, double tol, int ir_max) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ double red[32];
+  const int r = blockIdx.y;
+  const DevSub sd = subs[blockIdx.x];
+  const int a = sd.a, b = sd.b, m = a * b, nx = g.nx;
+  Carve<T> cv = carve<T>(smem, a, b, 1);
+  build_stencil(g, sd, d.kap_n + (long long)r * g.ncell(), 1, refine, cv.S);
+  block_factor<T>(sd, cv.S, cv.Q, cv.pub);
+  const double* ux = d.ux + (long long)r * g.nfx();
+  const double* uy = d.uy + (long long)r * g.nfy();
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    const int jl = c / a, il = c - jl * a;
+    const int i = sd.x0 + il, j = sd.y0 + jl;
+    double v = d.q[(long long)r * g.ncell() + (long long)j * nx + i] * g.h * g.h;
+    if (il == 0) v += ux[(long long)j * (nx + 1) + i];
+    if (il == a - 1) v -= ux[(long long)j * (nx + 1) + i + 1];
+    if (jl == 0) v += uy[(long long)j * nx + i];
+    if (jl == b - 1) v -= uy[(long long)(j + 1) * nx + i];
+    cv.B[c] = v;
+  }
+  __syncthreads();
+  solve_refined<T>(sd, cv.S, cv.Q, cv.B, cv.X, cv.Rr, cv.Zw, cv.Ww, 1, refine != 0, tol, ir_max, cv.colmax,
+                   d.status, d.ir_iters);
+  double part = 0.0;
+  for (int c = threadIdx.x; c < m; c += blockDim.x) part += cv.X[c];
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    red[0] = d.sub_target[(long long)r * d.st_sub + blockIdx.x] - s / m;
+  }
+  __syncthreads();
+  const double shift = red[0];
+  double* uxw = d.ux + (long long)r * g.nfx();
+  double* uyw = d.uy + (long long)r * g.nfy();
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    const int jl = c / a, il = c - jl * a;
+    const int i = sd.x0 + il, j = sd.y0 + jl;
+    d.p_down[(long long)r * g.ncell() + (long long)j * nx + i] = cv.X[c] + shift;
+    if (il < a - 1) uxw[(long long)j * (nx + 1) + i + 1] = cv.S.wE[c] * (cv.X[c] - cv.X[c + 1]);
+    if (jl < b - 1) uyw[(long long)(j + 1) * nx + i] = cv.S.wN[c] * (cv.X[c] - cv.X[c + a]);
+  }
+}
+
+template <typename K>
+void set_smem(K kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+int local_smem_limit() { return kSmemBudget; }
+
+void launch_robin_factor(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
+                         bool fp32, cudaStream_t st) {
+  dim3 grid(nsub, g.R);
+  const int thr = threads_for(max_a);
+  if (fp32) {
+    const SmemPlan pl = plan_smem<float>(max_a, max_b, 1);
+    set_smem(k_robin_factor<float>, pl.bytes);
+    k_robin_factor<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, 1);
+  } else {
+    const SmemPlan pl = plan_smem<double>(max_a, max_b, 1);
+    set_smem(k_robin_factor<double>, pl.bytes);
+    k_robin_factor<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, 0);
+  }
+}
+
+void launch_basis_solve(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
+                        int max_dof, bool fp32, double ir_tol, int ir_max, cudaStream_t st) {
+  dim3 grid(nsub, g.R);
+  const int thr = threads_for(max_a);
+  if (fp32) {
+    const SmemPlan pl = plan_smem<float>(max_a, max_b, 32);
+    set_smem(k_basis_solve<float>, pl.bytes);
+    k_basis_solve<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, pl.ncol, 1, ir_tol, ir_max);
+  } else {
+    const SmemPlan pl = plan_smem<double>(max_a, max_b, 32);
+    set_smem(k_basis_solve<double>, pl.bytes);
+    k_basis_solve<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, pl.ncol, 0, ir_tol, ir_max);
+  }
+  (void)max_dof;
+}
+
+void launch_mpm_local(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
+                      bool fp32, double ir_tol, int ir_max, cudaStream_t st) {
+  dim3 grid(nsub, g.R);
+  const int thr = threads_for(max_a);
+  if (fp32) {
+    const SmemPlan pl = plan_smem<float>(max_a, max_b, 1);
+    set_smem(k_mpm_local<float>, pl.bytes);
+    k_mpm_local<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, 1, ir_tol, ir_max);
+  } else {
+    const SmemPlan pl = plan_smem<double>(max_a, max_b, 1);
+    set_smem(k_mpm_local<double>, pl.bytes);
+    k_mpm_local<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, 0, ir_tol, ir_max);
+  }
+}
+
+void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub, const DevNode* nodes,
+                        const int* leaf_node, int branch, cudaStream_t st) {
+  k_reconstruct<<<dim3(nsub, g.R), 128, 0, st>>>(g, d, subs, nodes, leaf_node, branch);
+}
+
+void launch_downscale(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
+                      bool fp32, double ir_tol, int ir_max, cudaStream_t st) {
+  dim3 grid(nsub, g.R);
+  const int thr = threads_for(max_a);
+  if (fp32) {
+    const SmemPlan pl = plan_smem<float>(max_a, max_b, 1);
+    set_smem(k_downscale<float>, pl.bytes);
+    k_downscale<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, 1, ir_tol, ir_max);
+  } else {
+    const SmemPlan pl = plan_smem<double>(max_a, max_b, 1);
+    set_smem(k_downscale<double>, pl.bytes);
+    k_downscale<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, 0, ir_tol, ir_max);
+  }
+}
+
+}  // namespace mpm

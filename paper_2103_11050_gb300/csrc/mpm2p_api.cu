@@ -1,0 +1,846 @@
+// C ABI of the MRCM / MPM-2P hot path (declarations and argument contracts in
+// include/mpm2p.h).  Host-side context: geometry tables, the nested-dissection tree of
+// the interface system, device pools, and the launch sequences of Algorithm 1.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/mpm2p.h"
+#include "mpm2p_internal.cuh"
+
+using namespace mpm;
+
+struct mpm_ctx {
+  Grid g{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+  int prec = MPM_PREC_FP64;
+  double ir_tol = 1e-13;
+  int ir_max = 20;
+  int fac_prec = -1;  // precision the stored factor was built with
+  bool have_K = false, have_s = false, have_dec = false, have_basis = false;
+  double eta_init = 0.0;
+  // decomposition
+  int ncx = 0, ncy = 0;
+  std::vector<int> col_w, row_h;
+  std::vector<DevSub> subs;
+  int max_a = 0, max_b = 0, max_dof = 0, n_dof = 0, n_hat = 0;
+  // nested dissection
+  std::vector<DevNode> nodes;
+  std::vector<int> leaf_node;
+  std::vector<std::vector<int>> levels;  // node ids per level (level 0 = leaves)
+  std::vector<int> lev_max_nf, lev_max_nsep, lev_max_nbnd;
+  std::vector<int> lev_off;              // offset of each level in d_level_nodes
+  // device tables
+  DevSub* d_subs = nullptr;
+  DevNode* d_nodes = nullptr;
+  int* d_leaf_node = nullptr;
+  int* d_level_nodes = nullptr;
+  int* d_srcmap = nullptr;
+  int* d_pmap = nullptr;
+  DevState d{};
+  std::vector<void*> grid_allocs, dec_allocs;
+  // host staging for flags
+  int* h_flags = nullptr;
+  mpm_stats stats{};
+};
+
+namespace {
+
+int fail(mpm_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                               \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return fail(c, MPM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int dalloc(mpm_ctx* c, std::vector<void*>& list, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(c, MPM_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  list.push_back(*p);
+  cudaMemsetAsync(*p, 0, bytes, c->stream);
+  return MPM_OK;
+}
+
+template <typename T>
+int dalloc_t(mpm_ctx* c, std::vector<void*>& list, T** p, size_t n) {
+  return dalloc(c, list, reinterpret_cast<void**>(p), n * sizeof(T));
+}
+
+void free_list(std::vector<void*>& list) {
+  for (void* p : list) cudaFree(p);
+  list.clear();
+}
+
+int check_launch(mpm_ctx* c) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, MPM_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+  return MPM_OK;
+}
+
+int copy_in(mpm_ctx* c, double* dst, const double* src, size_t n, int mem) {
+  if (!src) return fail(c, MPM_ERR_ARG, "null input pointer");
+  if (mem == MPM_MEM_HOST) {
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  } else if (mem == MPM_MEM_DEVICE) {
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    return fail(c, MPM_ERR_ARG, "mem must be MPM_MEM_HOST or MPM_MEM_DEVICE");
+  }
+  return MPM_OK;
+}
+
+int sync_status(mpm_ctx* c) {
+  CK(cudaStreamSynchronize(c->stream));
+  int st = 0, it = 0;
+  CK(cudaMemcpy(&st, c->d.status, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&it, c->d.ir_iters, sizeof(int), cudaMemcpyDeviceToHost));
+  c->stats.ir_iters_max = std::max(c->stats.ir_iters_max, it);
+  if (st & 1) {
+    CK(cudaMemset(c->d.status, 0, sizeof(int)));
+    return fail(c, MPM_ERR_NOT_CONVERGED, "local iterative refinement did not reach ir_tol=%g in ir_max=%d sweeps",
+                c->ir_tol, c->ir_max);
+  }
+  return MPM_OK;
+}
+
+int copy_out(mpm_ctx* c, double* dst, const double* src, size_t n, int mem) {
+  if (!dst) return fail(c, MPM_ERR_ARG, "null output pointer");
+  if (mem == MPM_MEM_HOST) {
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  } else if (mem == MPM_MEM_DEVICE) {
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    return fail(c, MPM_ERR_ARG, "mem must be MPM_MEM_HOST or MPM_MEM_DEVICE");
+  }
+  return sync_status(c);
+}
+
+// max_s f'(s) of f = M s^2 / (M s^2 + (1-s)^2): the stationary point solves
+// 2(M+1)s^3 - 3(M+1)s^2 + 1 = 0, strictly decreasing on (0,1); bisection.
+double max_fprime(double M) {
+  double lo = 0.0, hi = 1.0;
+  const double cM = M + 1.0;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (2.0 * cM * mid * mid * mid - 3.0 * cM * mid * mid + 1.0 > 0.0) lo = mid;
+    else hi = mid;
+  }
+  const double s = 0.5 * (lo + hi);
+  const double den = M * s * s + (1.0 - s) * (1.0 - s);
+  return 2.0 * M * s * (1.0 - s) / (den * den);
+}
+
+bool fp32(const mpm_ctx* c) { return c->prec == MPM_PREC_FP32_IR; }
+
+// ---------------------------------------------------------------------------------------
+// Nested dissection tree over the subdomain grid.
+struct HostNode {
+  int I0, I1, J0, J1;
+  int child[2] = {-1, -1};
+  int parent = -1;
+  int level = 0;
+  int leaf_sub = -1;
+  std::vector<int> dofs;  // frontal order: separator DOFs, then boundary DOFs
+  int nsep = 0;
+};
+
+struct Iface {
+  int L, dof0, nb;  // length (cells), first global DOF, U DOFs (= P DOFs)
+};
+
+int v_id(const mpm_ctx* c, int I, int J) { return J * (c->ncx - 1) + I; }  // between (I,J) and (I+1,J)
+int h_id(const mpm_ctx* c, int I, int J) { return c->ncy * (c->ncx - 1) + J * c->ncx + I; }  // (I,J)-(I,J+1)
+
+void append_iface(std::vector<int>& out, const Iface& f) {
+  for (int k = 0; k < 2 * f.nb; ++k) out.push_back(f.dof0 + k);
+}
+
+int build_tree(mpm_ctx* c, const std::vector<Iface>& ifs, std::vector<HostNode>& hn, int I0, int I1, int J0,
+               int J1) {
+  const int id = (int)hn.size();
+  hn.push_back(HostNode{I0, I1, J0, J1});
+  std::vector<int> sep;  // interface ids
+  if (I1 - I0 == 1 && J1 - J0 == 1) {
+    hn[id].leaf_sub = J0 * c->ncx + I0;
+  } else {
+    int ch0, ch1;
+    if (I1 - I0 >= J1 - J0) {
+      const int Im = (I0 + I1) / 2;
+      ch0 = build_tree(c, ifs, hn, I0, Im, J0, J1);
+      ch1 = build_tree(c, ifs, hn, Im, I1, J0, J1);
+      for (int J = J0; J < J1; ++J) sep.push_back(v_id(c, Im - 1, J));
+    } else {
+      const int Jm = (J0 + J1) / 2;
+      ch0 = build_tree(c, ifs, hn, I0, I1, J0, Jm);
+      ch1 = build_tree(c, ifs, hn, I0, I1, Jm, J1);
+      for (int I = I0; I < I1; ++I) sep.push_back(h_id(c, I, Jm - 1));
+    }
+    hn[id].child[0] = ch0;
+    hn[id].child[1] = ch1;
+    hn[ch0].parent = id;
+    hn[ch1].parent = id;
+    hn[id].level = 1 + std::max(hn[ch0].level, hn[ch1].level);
+  }
+  // boundary interfaces of the rectangle (interior to the domain)
+  std::vector<int> bnd;
+  if (hn[id].leaf_sub >= 0) {
+    // leaf: subdomain side order left, right, bottom, top
+    if (I0 > 0) bnd.push_back(v_id(c, I0 - 1, J0));
+    if (I1 < c->ncx) bnd.push_back(v_id(c, I0, J0));
+    if (J0 > 0) bnd.push_back(h_id(c, I0, J0 - 1));
+    if (J1 < c->ncy) bnd.push_back(h_id(c, I0, J0));
+  } else {
+    for (int J = J0; J < J1; ++J) {
+      if (I0 > 0) bnd.push_back(v_id(c, I0 - 1, J));
+      if (I1 < c->ncx) bnd.push_back(v_id(c, I1 - 1, J));
+    }
+    for (int I = I0; I < I1; ++I) {
+      if (J0 > 0) bnd.push_back(h_id(c, I, J0 - 1));
+      if (J1 < c->ncy) bnd.push_back(h_id(c, I, J1 - 1));
+    }
+    std::sort(sep.begin(), sep.end());
+    std::sort(bnd.begin(), bnd.end());
+  }
+  std::vector<int> dofs;
+  for (int e : sep) append_iface(dofs, ifs[e]);
+  const int nsep = (int)dofs.size();
+  for (int e : bnd) append_iface(dofs, ifs[e]);
+  hn[id].dofs = dofs;
+  hn[id].nsep = nsep;
+  return id;
+}
+
+int release_decomposition(mpm_ctx* c) {
+  if (!c->dec_allocs.empty()) cudaStreamSynchronize(c->stream);
+  free_list(c->dec_allocs);
+  c->d_subs = nullptr;
+  c->d_nodes = nullptr;
+  c->d_leaf_node = c->d_level_nodes = c->d_srcmap = c->d_pmap = nullptr;
+  c->have_dec = false;
+  c->have_basis = false;
+  return MPM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Launch sequences.
+
+int run_build(mpm_ctx* c) {
+  const Grid& g = c->g;
+  DevState& d = c->d;
+  cudaStream_t st = c->stream;
+  const int nsub = (int)c->subs.size();
+  launch_copy_kappa_m(g, d, st);
+  launch_robin_factor(g, d, c->d_subs, nsub, c->max_a, c->max_b, fp32(c), st);
+  launch_basis_solve(g, d, c->d_subs, nsub, c->max_a, c->max_b, c->max_dof, fp32(c), c->ir_tol, c->ir_max, st);
+  if (c->n_dof > 0) {
+    launch_element_matrix(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, st);
+    for (size_t L = 1; L < c->levels.size(); ++L)
+      launch_nd_factor_level(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(),
+                             c->lev_max_nf[L], c->lev_max_nsep[L], c->d_srcmap, st);
+  }
+  c->fac_prec = c->prec;
+  c->have_basis = true;
+  return check_launch(c);
+}
+
+int run_perturbation(mpm_ctx* c) {
+  const Grid& g = c->g;
+  const int nsub = (int)c->subs.size();
+  launch_residual(g, c->d, c->stream);
+  launch_mpm_local(g, c->d, c->d_subs, nsub, c->max_a, c->max_b, c->fac_prec == MPM_PREC_FP32_IR, c->ir_tol,
+                   c->ir_max, c->stream);
+  return check_launch(c);
+}
+
+int run_interface(mpm_ctx* c) {
+  const Grid& g = c->g;
+  DevState& d = c->d;
+  cudaStream_t st = c->stream;
+  const int nsub = (int)c->subs.size();
+  if (c->n_dof > 0) {
+    launch_element_rhs(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, st);
+    for (size_t L = 1; L < c->levels.size(); ++L)
+      launch_nd_up(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(), c->lev_max_nf[L],
+                   c->lev_max_nsep[L], c->d_srcmap, st);
+    for (int L = (int)c->levels.size() - 1; L >= 0; --L)
+      launch_nd_down(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(),
+                     c->lev_max_nsep[L], c->lev_max_nbnd[L], c->d_pmap, st);
+  }
+  for (int branch = 1; branch >= 0; --branch) {
+    launch_reconstruct(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, branch, st);
+    launch_ubar(g, d, c->d_subs, nsub, branch, st);
+  }
+  return check_launch(c);
+}
+
+int run_downscale(mpm_ctx* c) {
+  launch_downscale(c->g, c->d, c->d_subs, (int)c->subs.size(), c->max_a, c->max_b, fp32(c), c->ir_tol, c->ir_max,
+                   c->stream);
+  return check_launch(c);
+}
+
+int run_transport(mpm_ctx* c, double cfl, int n_sub) {
+  launch_cfl(c->g, c->d, cfl, max_fprime(c->g.M), c->stream);
+  for (int k = 0; k < n_sub; ++k) {
+    launch_upwind(c->g, c->d, c->stream);
+    std::swap(c->d.s, c->d.s2);
+  }
+  launch_mobility_eps(c->g, c->d, false, c->stream);
+  return check_launch(c);
+}
+
+int need_ready(mpm_ctx* c, bool basis) {
+  if (!c->have_K) return fail(c, MPM_ERR_STATE, "permeability not set");
+  if (!c->have_dec) return fail(c, MPM_ERR_STATE, "decomposition not set");
+  if (!c->have_s) return fail(c, MPM_ERR_STATE, "saturation not set");
+  if (basis && !c->have_basis) return fail(c, MPM_ERR_STATE, "no stored basis (call mpm_build_basis or mpm_init)");
+  return MPM_OK;
+}
+
+}  // namespace
+
+// =======================================================================================
+extern "C" {
+
+int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void* stream) {
+  if (!out) return MPM_ERR_ARG;
+  *out = nullptr;
+  if (R < 1 || nx < 1 || ny < 1 || !(Lx > 0) || !(Ly > 0)) return MPM_ERR_ARG;
+  const double hx = Lx / nx, hy = Ly / ny;
+  if (std::fabs(hx - hy) > 1e-12 * std::max(hx, hy)) return MPM_ERR_ARG;
+  mpm_ctx* c = new mpm_ctx();
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  cudaGetDevice(&c->device);
+  Grid& g = c->g;
+  g.R = R;
+  g.nx = nx;
+  g.ny = ny;
+  g.h = hx;
+  g.bc_type[0] = g.bc_type[1] = MPM_BC_DIRICHLET;
+  g.bc_type[2] = g.bc_type[3] = MPM_BC_NEUMANN;
+  g.bc_val[0] = 1.0;
+  g.bc_val[1] = g.bc_val[2] = g.bc_val[3] = 0.0;
+  g.s_inflow = 1.0;
+  g.M = 1.0;
+  g.seg_len = 1;
+  g.degree = 0;
+  g.alpha = 1.0;
+  const size_t nc = (size_t)R * nx * ny;
+  DevState& d = c->d;
+  int rc = MPM_OK;
+  double** cells[] = {&d.K, &d.q, &d.s, &d.s2, &d.kap_n, &d.kap_m, &d.p_m, &d.p_down, &d.resid};
+  for (double** p : cells)
+    if ((rc = dalloc_t(c, c->grid_allocs, p, nc)) != MPM_OK) break;
+  const int nblk = 1024;
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.ux, (size_t)R * g.nfx());
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.uy, (size_t)R * g.nfy());
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.eps, (size_t)R);
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.dt, (size_t)R);
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.eps_part, (size_t)R * nblk * 2);
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.rate_part, (size_t)R * nblk);
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.rebuild, (size_t)R);
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.status, 1);
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.ir_iters, 1);
+  if (rc == MPM_OK && cudaMallocHost(&c->h_flags, sizeof(int) * R) != cudaSuccess) rc = MPM_ERR_OOM;
+  if (rc != MPM_OK) {
+    free_list(c->grid_allocs);
+    delete c;
+    return rc;
+  }
+  cudaStreamSynchronize(c->stream);
+  *out = c;
+  return MPM_OK;
+}
+
+int mpm_destroy(mpm_ctx* c) {
+  if (!c) return MPM_OK;
+  cudaStreamSynchronize(c->stream);
+  release_decomposition(c);
+  free_list(c->grid_allocs);
+  if (c->h_flags) cudaFreeHost(c->h_flags);
+  delete c;
+  return MPM_OK;
+}
+
+const char* mpm_last_error(const mpm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int mpm_set_precision(mpm_ctx* c, int mode, double ir_tol, int ir_max) {
+  if (!c) return MPM_ERR_ARG;
+  if (mode != MPM_PREC_FP64 && mode != MPM_PREC_FP32_IR) return fail(c, MPM_ERR_ARG, "unknown precision mode %d", mode);
+  if (!(ir_tol > 0) || ir_max < 1 || ir_max > 1000) return fail(c, MPM_ERR_ARG, "need ir_tol > 0 and 1 <= ir_max <= 1000");
+  c->prec = mode;
+  c->ir_tol = ir_tol;
+  c->ir_max = ir_max;
+  return MPM_OK;
+}
+
+int mpm_set_permeability(mpm_ctx* c, const double* K, int mem) {
+  if (!c) return MPM_ERR_ARG;
+  const size_t n = (size_t)c->g.R * c->g.nx * c->g.ny;
+  if (mem == MPM_MEM_HOST && K) {
+    for (size_t i = 0; i < n; ++i)
+      if (!(K[i] > 0) || !std::isfinite(K[i])) return fail(c, MPM_ERR_ARG, "permeability must be positive and finite (index %zu)", i);
+  }
+  int rc = copy_in(c, c->d.K, K, n, mem);
+  if (rc) return rc;
+  c->have_K = true;
+  if (c->have_s) launch_mobility_eps(c->g, c->d, false, c->stream);
+  return check_launch(c);
+}
+
+int mpm_set_source(mpm_ctx* c, const double* q, int mem) {
+  if (!c) return MPM_ERR_ARG;
+  const size_t n = (size_t)c->g.R * c->g.nx * c->g.ny;
+  if (!q) {
+    CK(cudaMemsetAsync(c->d.q, 0, n * sizeof(double), c->stream));
+    return MPM_OK;
+  }
+  return copy_in(c, c->d.q, q, n, mem);
+}
+
+int mpm_set_fluids(mpm_ctx* c, double M) {
+  if (!c) return MPM_ERR_ARG;
+  if (!(M > 0) || !std::isfinite(M)) return fail(c, MPM_ERR_ARG, "viscosity ratio must be positive");
+  c->g.M = M;
+  if (c->have_s && c->have_K) launch_mobility_eps(c->g, c->d, false, c->stream);
+  return check_launch(c);
+}
+
+int mpm_set_boundary(mpm_ctx* c, const int type[4], const double val[4], double s_inflow) {
+  if (!c) return MPM_ERR_ARG;
+  if (!type || !val) return fail(c, MPM_ERR_ARG, "null boundary arrays");
+  bool any_d = false;
+  for (int k = 0; k < 4; ++k) {
+    if (type[k] != MPM_BC_DIRICHLET && type[k] != MPM_BC_NEUMANN) return fail(c, MPM_ERR_ARG, "bad boundary type on side %d", k);
+    if (!std::isfinite(val[k])) return fail(c, MPM_ERR_ARG, "boundary value must be finite");
+    any_d |= type[k] == MPM_BC_DIRICHLET;
+  }
+  if (!any_d) return fail(c, MPM_ERR_ARG, "at least one side must be Dirichlet");
+  if (!(s_inflow >= 0 && s_inflow <= 1)) return fail(c, MPM_ERR_ARG, "s_inflow must be in [0,1]");
+  for (int k = 0; k < 4; ++k) {
+    c->g.bc_type[k] = type[k];
+    c->g.bc_val[k] = val[k];
+  }
+  c->g.s_inflow = s_inflow;
+  c->have_basis = false;
+  return MPM_OK;
+}
+
+int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const int* row_h, int seg_len, int degree,
+                          double alpha) {
+  if (!c) return MPM_ERR_ARG;
+  if (ncx < 1 || ncy < 1 || !col_w || !row_h) return fail(c, MPM_ERR_ARG, "bad decomposition arrays");
+  if (seg_len < 1 || (degree != 0 && degree != 1) || !(alpha > 0) || !std::isfinite(alpha))
+    return fail(c, MPM_ERR_ARG, "need seg_len >= 1, degree in {0,1}, alpha > 0");
+  long long sx = 0, sy = 0;
+  for (int I = 0; I < ncx; ++I) {
+    if (col_w[I] < 1 || col_w[I] > kMaxSide || col_w[I] % seg_len)
+      return fail(c, MPM_ERR_ARG, "column width %d must be in [1,%d] and a multiple of seg_len", col_w[I], kMaxSide);
+    sx += col_w[I];
+  }
+  for (int J = 0; J < ncy; ++J) {
+    if (row_h[J] < 1 || row_h[J] > kMaxSide || row_h[J] % seg_len)
+      return fail(c, MPM_ERR_ARG, "row height %d must be in [1,%d] and a multiple of seg_len", row_h[J], kMaxSide);
+    sy += row_h[J];
+  }
+  if (sx != c->g.nx || sy != c->g.ny) return fail(c, MPM_ERR_ARG, "widths/heights must sum to nx/ny");
+  release_decomposition(c);
+  c->ncx = ncx;
+  c->ncy = ncy;
+  c->col_w.assign(col_w, col_w + ncx);
+  c->row_h.assign(row_h, row_h + ncy);
+  Grid& g = c->g;
+  g.seg_len = seg_len;
+  g.degree = degree;
+  g.alpha = alpha;
+  // interfaces
+  const int nv = ncy * (ncx - 1), nh = (ncy - 1) * ncx;
+  std::vector<Iface> ifs(nv + nh);
+  int off = 0;
+  for (int e = 0; e < nv + nh; ++e) {
+    int L;
+    if (e < nv) L = row_h[e / (ncx - 1)];
+    else L = col_w[(e - nv) % ncx];
+    const int nb = (L / seg_len) * (degree + 1);
+    ifs[e] = Iface{L, off, nb};
+    off += 2 * nb;
+  }
+  c->n_dof = off;
+  // subdomains
+  std::vector<int> xo(ncx + 1, 0), yo(ncy + 1, 0);
+  for (int I = 0; I < ncx; ++I) xo[I + 1] = xo[I] + col_w[I];
+  for (int J = 0; J < ncy; ++J) yo[J + 1] = yo[J] + row_h[J];
+  c->subs.assign(ncx * ncy, DevSub{});
+  long long q_off = 0, t_off = 0, tr_off = 0, pf_off = 0;
+  int dof_off = 0, face_off = 0, cell_off = 0;
+  c->max_a = c->max_b = c->max_dof = 0;
+  c->n_hat = 0;
+  for (int J = 0; J < ncy; ++J) {
+    for (int I = 0; I < ncx; ++I) {
+      DevSub& s = c->subs[J * ncx + I];
+      s.x0 = xo[I];
+      s.y0 = yo[J];
+      s.a = col_w[I];
+      s.b = row_h[J];
+      const int ids[4] = {I > 0 ? v_id(c, I - 1, J) : -1, I < ncx - 1 ? v_id(c, I, J) : -1,
+                          J > 0 ? h_id(c, I, J - 1) : -1, J < ncy - 1 ? h_id(c, I, J) : -1};
+      const int nbr[4] = {I > 0 ? J * ncx + I - 1 : -1, I < ncx - 1 ? J * ncx + I + 1 : -1,
+                          J > 0 ? (J - 1) * ncx + I : -1, J < ncy - 1 ? (J + 1) * ncx + I : -1};
+      const double sgn[4] = {-1.0, 1.0, -1.0, 1.0};
+      int nd = 0;
+      for (int q = 0; q < 4; ++q) {
+        s.side_iface[q] = ids[q];
+        s.side_nbr[q] = nbr[q];
+        s.side_sign[q] = sgn[q];
+        if (ids[q] >= 0) {
+          s.side_kind[q] = 1;
+          s.side_dof0[q] = nd;
+          s.side_nb[q] = ifs[ids[q]].nb;
+          s.side_rho[q] = alpha * ifs[ids[q]].L;
+          nd += 2 * ifs[ids[q]].nb;
+        } else {
+          s.side_kind[q] = 0;
+          s.side_dof0[q] = nd;
+          s.side_nb[q] = 0;
+          s.side_rho[q] = 0.0;
+        }
+      }
+      s.ndof = nd;
+      s.dof_off = dof_off;
+      s.face_off = face_off;
+      s.cell_off = cell_off;
+      const int m = s.a * s.b, nface = 2 * (s.a + s.b);
+      s.q_off = q_off;
+      s.t_off = t_off;
+      s.tr_off = tr_off;
+      s.pf_off = pf_off;
+      q_off += (long long)s.b * s.a * s.a;
+      t_off += 4LL * m;
+      tr_off += (long long)nface * nd;
+      pf_off += (long long)m * (nd + 1);
+      dof_off += nd;
+      face_off += nface;
+      cell_off += m;
+      c->max_a = std::max(c->max_a, s.a);
+      c->max_b = std::max(c->max_b, s.b);
+      c->max_dof = std::max(c->max_dof, nd);
+      c->n_hat += nd;
+    }
+  }
+  // nested dissection tree
+  std::vector<HostNode> hn;
+  build_tree(c, ifs, hn, 0, ncx, 0, ncy);
+  const int nn = (int)hn.size();
+  int nlev = 0;
+  for (auto& n : hn) nlev = std::max(nlev, n.level + 1);
+  c->levels.assign(nlev, {});
+  for (int i = 0; i < nn; ++i) c->levels[hn[i].level].push_back(i);
+  c->nodes.assign(nn, DevNode{});
+  c->leaf_node.assign(ncx * ncy, -1);
+  std::vector<int> srcmap, pmap;
+  long long f_off = 0, v_off = 0;
+  for (int i = 0; i < nn; ++i) {
+    DevNode& dn = c->nodes[i];
+    const HostNode& h = hn[i];
+    dn.nf = (int)h.dofs.size();
+    dn.nsep = h.nsep;
+    dn.nbnd = dn.nf - dn.nsep;
+    dn.leaf_sub = h.leaf_sub;
+    dn.child[0] = h.child[0];
+    dn.child[1] = h.child[1];
+    dn.parent = h.parent;
+    dn.f_off = f_off;
+    dn.v_off = v_off;
+    f_off += (long long)dn.nf * dn.nf;
+    v_off += dn.nf;
+    if (h.leaf_sub >= 0) {
+      c->leaf_node[h.leaf_sub] = i;
+      if (dn.nf != c->subs[h.leaf_sub].ndof) return fail(c, MPM_ERR_ARG, "internal: leaf DOF mismatch");
+    }
+    dn.src_off = (int)srcmap.size();
+    if (h.child[0] >= 0) {
+      for (int ch = 0; ch < 2; ++ch) {
+        const HostNode& hc = hn[h.child[ch]];
+        std::map<int, int> pos;
+        for (int k = hc.nsep; k < (int)hc.dofs.size(); ++k) pos[hc.dofs[k]] = k - hc.nsep;
+        for (int k = 0; k < dn.nf; ++k) {
+          auto it = pos.find(h.dofs[k]);
+          srcmap.push_back(it == pos.end() ? -1 : it->second);
+        }
+      }
+    }
+  }
+  for (int i = 0; i < nn; ++i) {
+    DevNode& dn = c->nodes[i];
+    const HostNode& h = hn[i];
+    dn.pmap_off = (int)pmap.size();
+    if (h.parent >= 0) {
+      std::map<int, int> pos;
+      const HostNode& hp = hn[h.parent];
+      for (int k = 0; k < (int)hp.dofs.size(); ++k) pos[hp.dofs[k]] = k;
+      for (int k = h.nsep; k < (int)h.dofs.size(); ++k) {
+        auto it = pos.find(h.dofs[k]);
+        if (it == pos.end()) return fail(c, MPM_ERR_ARG, "internal: boundary DOF missing in parent");
+        pmap.push_back(it->second);
+      }
+    }
+  }
+  std::vector<int> level_nodes;
+  c->lev_off.assign(nlev, 0);
+  c->lev_max_nf.assign(nlev, 0);
+  c->lev_max_nsep.assign(nlev, 0);
+  c->lev_max_nbnd.assign(nlev, 0);
+  long long st_lvl = 1;
+  for (int L = 0; L < nlev; ++L) {
+    c->lev_off[L] = (int)level_nodes.size();
+    for (int i : c->levels[L]) {
+      level_nodes.push_back(i);
+      c->lev_max_nf[L] = std::max(c->lev_max_nf[L], c->nodes[i].nf);
+      c->lev_max_nsep[L] = std::max(c->lev_max_nsep[L], c->nodes[i].nsep);
+      c->lev_max_nbnd[L] = std::max(c->lev_max_nbnd[L], c->nodes[i].nbnd);
+    }
+    st_lvl = std::max(st_lvl, (long long)c->levels[L].size());
+  }
+  if (srcmap.empty()) srcmap.push_back(-1);
+  if (pmap.empty()) pmap.push_back(-1);
+  // device pools
+  DevState& d = c->d;
+  const int R = g.R, nsub = ncx * ncy;
+  d.st_fac = q_off;
+  d.st_t = t_off;
+  d.st_tr = tr_off;
+  d.st_pf = pf_off;
+  d.st_dof = dof_off;
+  d.st_face = face_off;
+  d.st_sub = nsub;
+  d.st_front = f_off;
+  d.st_vec = v_off;
+  d.st_col = v_off * kPivotChunk;
+  d.st_lvl = st_lvl;
+  auto& A = c->dec_allocs;
+  int rc = MPM_OK;
+  if (!rc) rc = dalloc(c, A, &d.fac, (size_t)R * q_off * sizeof(double));
+  if (!rc) rc = dalloc_t(c, A, &d.tvec, (size_t)R * t_off);
+  if (!rc) rc = dalloc_t(c, A, &d.tr, (size_t)R * tr_off);
+  if (!rc) rc = dalloc_t(c, A, &d.pf, (size_t)R * pf_off);
+  if (!rc) rc = dalloc_t(c, A, &d.mu_hat, (size_t)R * dof_off);
+  if (!rc) rc = dalloc_t(c, A, &d.fbar, (size_t)R * face_off);
+  if (!rc) rc = dalloc_t(c, A, &d.trace, (size_t)R * face_off);
+  if (!rc) rc = dalloc_t(c, A, &d.sub_mean, (size_t)R * nsub);
+  if (!rc) rc = dalloc_t(c, A, &d.sub_target, (size_t)R * nsub);
+  if (!rc) rc = dalloc_t(c, A, &d.pm_mean, (size_t)R * nsub);
+  if (!rc) rc = dalloc_t(c, A, &d.front, (size_t)R * f_off);
+  if (!rc) rc = dalloc_t(c, A, &d.gvec, (size_t)R * v_off);
+  if (!rc) rc = dalloc_t(c, A, &d.xvec, (size_t)R * v_off);
+  if (!rc) rc = dalloc_t(c, A, &d.pivinv, (size_t)R * st_lvl * kPivotChunk * kPivotChunk);
+  if (!rc) rc = dalloc_t(c, A, &d.colold, (size_t)R * d.st_col);
+  if (!rc) rc = dalloc_t(c, A, &c->d_subs, (size_t)nsub);
+  if (!rc) rc = dalloc_t(c, A, &c->d_nodes, (size_t)nn);
+  if (!rc) rc = dalloc_t(c, A, &c->d_leaf_node, (size_t)nsub);
+  if (!rc) rc = dalloc_t(c, A, &c->d_level_nodes, level_nodes.size());
+  if (!rc) rc = dalloc_t(c, A, &c->d_srcmap, srcmap.size());
+  if (!rc) rc = dalloc_t(c, A, &c->d_pmap, pmap.size());
+  if (rc) {
+    release_decomposition(c);
+    return rc;
+  }
+  CK(cudaMemcpyAsync(c->d_subs, c->subs.data(), nsub * sizeof(DevSub), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_nodes, c->nodes.data(), nn * sizeof(DevNode), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_leaf_node, c->leaf_node.data(), nsub * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_level_nodes, level_nodes.data(), level_nodes.size() * sizeof(int), cudaMemcpyHostToDevice,
+                     c->stream));
+  CK(cudaMemcpyAsync(c->d_srcmap, srcmap.data(), srcmap.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_pmap, pmap.data(), pmap.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->have_dec = true;
+  c->have_basis = false;
+  c->stats.interface_dofs = c->n_dof;
+  c->stats.subdomains = nsub;
+  c->stats.n_hat = c->n_hat;
+  return MPM_OK;
+}
+
+int mpm_set_saturation(mpm_ctx* c, const double* s, int mem) {
+  if (!c) return MPM_ERR_ARG;
+  const size_t n = (size_t)c->g.R * c->g.nx * c->g.ny;
+  if (mem == MPM_MEM_HOST && s) {
+    for (size_t i = 0; i < n; ++i)
+      if (!(s[i] >= 0 && s[i] <= 1)) return fail(c, MPM_ERR_ARG, "saturation must lie in [0,1] (index %zu)", i);
+  }
+  int rc = copy_in(c, c->d.s, s, n, mem);
+  if (rc) return rc;
+  c->have_s = true;
+  if (c->have_K) launch_mobility_eps(c->g, c->d, false, c->stream);
+  return check_launch(c);
+}
+
+int mpm_build_basis(mpm_ctx* c) {
+  if (!c) return MPM_ERR_ARG;
+  int rc = need_ready(c, false);
+  if (rc) return rc;
+  launch_fill_flags(c->g, c->d, 1, c->stream);
+  return run_build(c);
+}
+
+int mpm_eval_epsilon(mpm_ctx* c, double* eps) {
+  if (!c) return MPM_ERR_ARG;
+  int rc = need_ready(c, true);
+  if (rc) return rc;
+  launch_mobility_eps(c->g, c->d, true, c->stream);
+  if ((rc = check_launch(c))) return rc;
+  if (eps) return copy_out(c, eps, c->d.eps, c->g.R, MPM_MEM_HOST);
+  return MPM_OK;
+}
+
+int mpm_choose(mpm_ctx* c, double eta, int* rebuild) {
+  if (!c) return MPM_ERR_ARG;
+  if (!std::isfinite(eta)) return fail(c, MPM_ERR_ARG, "eta must be finite");
+  launch_choose(c->g, c->d, eta, c->stream);
+  int rc = check_launch(c);
+  if (rc) return rc;
+  if (rebuild) {
+    CK(cudaMemcpyAsync(rebuild, c->d.rebuild, sizeof(int) * c->g.R, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return MPM_OK;
+}
+
+int mpm_perturbation_solve(mpm_ctx* c) {
+  if (!c) return MPM_ERR_ARG;
+  int rc = need_ready(c, true);
+  if (rc) return rc;
+  launch_fill_flags(c->g, c->d, 0, c->stream);
+  return run_perturbation(c);
+}
+
+int mpm_interface_solve(mpm_ctx* c) {
+  if (!c) return MPM_ERR_ARG;
+  int rc = need_ready(c, true);
+  if (rc) return rc;
+  return run_interface(c);
+}
+
+int mpm_downscale(mpm_ctx* c) {
+  if (!c) return MPM_ERR_ARG;
+  int rc = need_ready(c, true);
+  if (rc) return rc;
+  return run_downscale(c);
+}
+
+int mpm_saturation_step(mpm_ctx* c, double cfl, int n_sub, double* dt) {
+  if (!c) return MPM_ERR_ARG;
+  if (!(cfl > 0 && cfl <= 1) || n_sub < 1) return fail(c, MPM_ERR_ARG, "need 0 < cfl <= 1 and n_sub >= 1");
+  int rc = need_ready(c, false);
+  if (rc) return rc;
+  if ((rc = run_transport(c, cfl, n_sub))) return rc;
+  if (dt) return copy_out(c, dt, c->d.dt, c->g.R, MPM_MEM_HOST);
+  return MPM_OK;
+}
+
+int mpm_init(mpm_ctx* c, double eta) {
+  if (!c) return MPM_ERR_ARG;
+  if (!std::isfinite(eta)) return fail(c, MPM_ERR_ARG, "eta must be finite");
+  int rc = need_ready(c, false);
+  if (rc) return rc;
+  launch_mobility_eps(c->g, c->d, false, c->stream);
+  launch_fill_flags(c->g, c->d, 1, c->stream);
+  if ((rc = run_build(c))) return rc;
+  if ((rc = run_interface(c))) return rc;
+  if ((rc = run_downscale(c))) return rc;
+  std::vector<double> e(c->g.R, eta);
+  CK(cudaMemcpyAsync(c->d.eps, e.data(), sizeof(double) * c->g.R, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->stats.rebuilds += c->g.R;
+  return MPM_OK;
+}
+
+int mpm_step(mpm_ctx* c, double eta, double cfl, int n_sub) {
+  if (!c) return MPM_ERR_ARG;
+  if (!(cfl > 0 && cfl <= 1) || n_sub < 1 || !std::isfinite(eta))
+    return fail(c, MPM_ERR_ARG, "need 0 < cfl <= 1, n_sub >= 1 and finite eta");
+  int rc = need_ready(c, true);
+  if (rc) return rc;
+  if ((rc = run_transport(c, cfl, n_sub))) return rc;
+  launch_choose(c->g, c->d, eta, c->stream);
+  CK(cudaMemcpyAsync(c->h_flags, c->d.rebuild, sizeof(int) * c->g.R, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  int nreb = 0;
+  for (int r = 0; r < c->g.R; ++r) nreb += c->h_flags[r] != 0;
+  if (nreb > 0 && (rc = run_build(c))) return rc;
+  if (nreb < c->g.R && (rc = run_perturbation(c))) return rc;
+  if ((rc = run_interface(c))) return rc;
+  if ((rc = run_downscale(c))) return rc;
+  launch_mobility_eps(c->g, c->d, true, c->stream);
+  c->stats.steps += 1;
+  c->stats.rebuilds += nreb;
+  c->stats.mpm_updates += c->g.R - nreb;
+  return check_launch(c);
+}
+
+int mpm_get_pressure(mpm_ctx* c, double* p, int which, int mem) {
+  if (!c) return MPM_ERR_ARG;
+  const size_t n = (size_t)c->g.R * c->g.nx * c->g.ny;
+  if (which == MPM_P_MRCM) return copy_out(c, p, c->d.p_m, n, mem);
+  if (which == MPM_P_DOWNSCALED) return copy_out(c, p, c->d.p_down, n, mem);
+  return fail(c, MPM_ERR_ARG, "which must be MPM_P_MRCM or MPM_P_DOWNSCALED");
+}
+
+int mpm_get_flux(mpm_ctx* c, double* ux, double* uy, int mem) {
+  if (!c) return MPM_ERR_ARG;
+  int rc = copy_out(c, ux, c->d.ux, (size_t)c->g.R * c->g.nfx(), mem);
+  if (rc) return rc;
+  return copy_out(c, uy, c->d.uy, (size_t)c->g.R * c->g.nfy(), mem);
+}
+
+int mpm_get_saturation(mpm_ctx* c, double* s, int mem) {
+  if (!c) return MPM_ERR_ARG;
+  return copy_out(c, s, c->d.s, (size_t)c->g.R * c->g.nx * c->g.ny, mem);
+}
+
+int mpm_get_conductivity(mpm_ctx* c, double* kappa, int mem) {
+  if (!c) return MPM_ERR_ARG;
+  return copy_out(c, kappa, c->d.kap_n, (size_t)c->g.R * c->g.nx * c->g.ny, mem);
+}
+
+int mpm_get_stats(mpm_ctx* c, mpm_stats* out) {
+  if (!c || !out) return MPM_ERR_ARG;
+  int rc = sync_status(c);
+  std::vector<double> e(c->g.R), dt(c->g.R);
+  CK(cudaMemcpy(e.data(), c->d.eps, sizeof(double) * c->g.R, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(dt.data(), c->d.dt, sizeof(double) * c->g.R, cudaMemcpyDeviceToHost));
+  c->stats.last_eps_max = *std::max_element(e.begin(), e.end());
+  c->stats.last_dt_min = *std::min_element(dt.begin(), dt.end());
+  *out = c->stats;
+  return rc;
+}
+
+int mpm_sync(mpm_ctx* c) {
+  if (!c) return MPM_ERR_ARG;
+  return sync_status(c);
+}
+
+}  // extern "C"

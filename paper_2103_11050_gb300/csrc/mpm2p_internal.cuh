@@ -1,0 +1,134 @@
+// Internal declarations shared by the translation units of libmpm2p.
+//
+// Geometry tables (per subdomain, shared by all realisations) and per-realisation
+// pools live in device memory owned by the context.  Kernels are grouped by stage:
+//   k_grid.cu   fine-grid stencils: kappa / epsilon, residual, interface fluxes, transport
+//   k_local.cu  local Robin and Neumann problems (block-tridiagonal factorisation with
+//               explicit inverse pivot blocks, multi-RHS solves, FP64 refinement)
+//   k_iface.cu  interface (skeleton) system: element matrices, nested-dissection sweep
+//               factorisation and solves
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace mpm {
+
+constexpr int kMaxSide = 24;     // largest subdomain width / height in cells
+constexpr int kPivotChunk = 16;  // pivot block of the interface sweeps
+
+// Face numbering inside a subdomain of a x b cells: left side (b faces, bottom to top),
+// right side (b), bottom side (a faces, left to right), top side (a): 2(a+b) faces.
+__host__ __device__ inline int face_side_off(int side, int a, int b) {
+  return side == 0 ? 0 : side == 1 ? b : side == 2 ? 2 * b : 2 * b + a;
+}
+
+struct DevSub {
+  int x0, y0, a, b;
+  int ndof;          // interface DOFs on the sides of this subdomain
+  int dof_off;       // offset in per-DOF tables (sum of ndof of previous subdomains)
+  int face_off;      // offset in per-face tables (sum of 2(a+b))
+  int cell_off;      // offset in per-cell local tables (sum of a*b)
+  int side_kind[4];  // 0 physical boundary, 1 interface
+  int side_iface[4]; // interface id or -1
+  int side_dof0[4];  // first local DOF of this side (U block, then P block)
+  int side_nb[4];    // U DOFs on this side (= P DOFs)
+  int side_nbr[4];   // subdomain on the other side of the interface, or -1
+  double side_sign[4];  // n_check . n_check^i
+  double side_rho[4];   // alpha * (interface length in cells) = alpha H / h
+  long long q_off;   // Robin factor (b*a*a values of the factor type) in the factor pool
+  long long t_off;   // b*a values: vertical transmissibilities + scaling (see k_local.cu)
+  long long tr_off;  // (2(a+b)) x ndof BF traces
+  long long pf_off;  // a*b x ndof BF pressures (temporary, rebuild only)
+};
+
+struct Grid {
+  int R, nx, ny;
+  double h;
+  int bc_type[4];
+  double bc_val[4];
+  double s_inflow;
+  double M;
+  int seg_len, degree;
+  double alpha;
+  __host__ __device__ long long ncell() const { return (long long)nx * ny; }
+  __host__ __device__ long long nfx() const { return (long long)ny * (nx + 1); }
+  __host__ __device__ long long nfy() const { return (long long)(ny + 1) * nx; }
+};
+
+// Nested-dissection node of the interface system.  Leaves are subdomains (no
+// separator, frontal = element matrix over the subdomain's DOFs).
+struct DevNode {
+  int nsep, nbnd, nf;
+  int leaf_sub;        // subdomain id for leaves, -1 otherwise
+  int child[2];        // node ids, -1 for leaves
+  int parent;          // -1 for the root
+  long long f_off;     // frontal matrix (nf x nf, row major) in the frontal pool
+  long long v_off;     // vectors (nf) in the g / x pools
+  int src_off;         // internal nodes: 2*nf ints: child0 / child1 boundary index per frontal index (-1 none)
+  int pmap_off;        // nbnd ints: frontal index in the parent of each boundary DOF
+};
+
+// Per-realisation device state (all pointers are device pointers; pools are indexed
+// r * st_x + offset).
+struct DevState {
+  // cells [R][ny][nx]
+  double *K, *q, *s, *s2, *kap_n, *kap_m, *p_m, *p_down, *resid;
+  // faces
+  double *ux, *uy;
+  // per realisation scalars
+  double *eps, *dt, *eps_part, *rate_part;
+  int* rebuild;        // [R] branch of the current update: 1 = basis build, 0 = MPM-2P reuse
+  int* status;         // [1] bitmask: 1 = a refinement did not reach its tolerance
+  int* ir_iters;       // [1] max refinement sweeps used
+  // per subdomain pools
+  void* fac;           // Robin factors (float or double), st_fac values per realisation
+  double* tvec;        // [dia, wE, wN, sc] per subdomain (4 m), st_t
+  double* tr;          // BF traces (2(a+b) x ndof), st_tr
+  double* pf;          // BF pressures (m x (ndof + 1)), st_pf
+  double* mu_hat;      // BF means, st_dof
+  double* fbar;        // non-homogeneous / perturbation traces, st_face
+  double* trace;       // one-sided traces of the current update, st_face
+  double* sub_mean;    // mean of the non-homogeneous local solution, st_sub
+  double* sub_target;  // target mean of the downscaled pressure, st_sub
+  double* pm_mean;     // mean of p^m over the subdomain, st_sub
+  // interface system
+  double *front, *gvec, *xvec;  // st_front, st_vec, st_vec
+  double *pivinv, *colold;      // st_lvl * 256, st_col
+  long long st_fac, st_t, st_tr, st_pf, st_dof, st_face, st_sub, st_front, st_vec, st_col, st_lvl;
+};
+
+// Host-side launch wrappers (defined in the .cu files).
+int grid_cell_blocks(const Grid& g);
+void launch_mobility_eps(const Grid& g, const DevState& d, bool with_eps, cudaStream_t st);
+void launch_choose(const Grid& g, const DevState& d, double eta, cudaStream_t st);
+void launch_fill_flags(const Grid& g, const DevState& d, int v, cudaStream_t st);
+void launch_copy_kappa_m(const Grid& g, const DevState& d, cudaStream_t st);
+void launch_residual(const Grid& g, const DevState& d, cudaStream_t st);
+void launch_ubar(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int branch, cudaStream_t st);
+void launch_cfl(const Grid& g, const DevState& d, double cfl, double fmax, cudaStream_t st);
+void launch_upwind(const Grid& g, const DevState& d, cudaStream_t st);
+
+int local_smem_limit();
+void launch_robin_factor(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
+                         int max_b, bool fp32, cudaStream_t st);
+void launch_basis_solve(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
+                        int max_b, int max_dof, bool fp32, double ir_tol, int ir_max, cudaStream_t st);
+void launch_mpm_local(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
+                      int max_b, bool fp32, double ir_tol, int ir_max, cudaStream_t st);
+void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub,
+                        const DevNode* nodes, const int* leaf_node, int branch, cudaStream_t st);
+void launch_downscale(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
+                      int max_b, bool fp32, double ir_tol, int ir_max, cudaStream_t st);
+
+void launch_element_matrix(const Grid& g, const DevState& d, const DevSub* subs, int nsub,
+                           const DevNode* nodes, const int* leaf_node, cudaStream_t st);
+void launch_element_rhs(const Grid& g, const DevState& d, const DevSub* subs, int nsub,
+                        const DevNode* nodes, const int* leaf_node, cudaStream_t st);
+void launch_nd_factor_level(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes,
+                            int nlev, int max_nf, int max_nsep, const int* srcmap, cudaStream_t st);
+void launch_nd_up(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
+                  int max_nf, int max_nsep, const int* srcmap, cudaStream_t st);
+void launch_nd_down(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
+                    int max_nsep, int max_nbnd, const int* pmap, cudaStream_t st);
+
+}  // namespace mpm

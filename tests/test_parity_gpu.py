@@ -1,0 +1,158 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element, on the same
+seeded inputs.  Tolerances: relative L2 error <= 1e-10 for the plain FP64 form and
+<= 1e-8 for the FP32 factorisation with FP64 refinement (the accuracy targets of the
+method's GPU forms); discrete quantities (rebuild decisions) exactly."""
+import numpy as np
+import pytest
+
+from oracle import mpm_oracle as O
+from tests.cases import case, rel
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-10, 1: 1e-8}
+
+
+def _oracle_setup(c):
+    prob = O.Problem(c["nx"], c["ny"], c["h"], tuple(c["bc_type"]), tuple(c["bc_val"]), c["M"], 1.0)
+    dec = O.Decomposition(c["nx"], c["ny"], c["col_w"], c["row_h"], c["seg_len"], c["degree"], c["alpha"])
+    return prob, dec
+
+
+def _gpu(c, prec, R=1, K=None, s0=None):
+    from paper_2103_11050_gb300 import binding as B
+    ctx = B.Context(R, c["nx"], c["ny"], c["Lx"], c["Ly"])
+    ctx.set_precision(prec, 1e-13, 30)
+    ctx.set_fluids(c["M"])
+    ctx.set_boundary(c["bc_type"], c["bc_val"], 1.0)
+    ctx.set_decomposition(c["col_w"], c["row_h"], c["seg_len"], c["degree"], c["alpha"])
+    ctx.set_permeability(np.ascontiguousarray(np.broadcast_to(c["K"] if K is None else K, (R, c["ny"], c["nx"]))))
+    ctx.set_saturation(np.ascontiguousarray(np.broadcast_to(c["s0"] if s0 is None else s0, (R, c["ny"], c["nx"]))))
+    return ctx
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_11050_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", ["p1_2x2", "uneven", "const_H", "exact_h", "single", "rate_in", "dirichlet4",
+                                  "contrast64"])
+def test_mrcm_update_parity(name, prec):
+    c = case(name)
+    prob, dec = _oracle_setup(c)
+    kappa = O.mobility(c["s0"], c["M"]) * c["K"]
+    step, _, sol = O.mrcm_step(kappa, prob, dec)
+    ctx = _gpu(c, prec)
+    ctx.init(0.1)
+    pm = ctx.get_pressure(0)[0]
+    pd = ctx.get_pressure(1)[0]
+    ux, uy = ctx.get_flux()
+    tol = TOL[prec]
+    assert rel(pm, sol.p) <= tol, rel(pm, sol.p)
+    assert rel(pd, step.p_down) <= tol, rel(pd, step.p_down)
+    assert rel(ux[0], step.Fx) <= tol, rel(ux[0], step.Fx)
+    assert rel(uy[0], step.Fy) <= tol + 1e-12, rel(uy[0], step.Fy)
+    # conservation of the GPU fluxes in every cell (property at any size)
+    bal = O.cell_balance(ux[0], uy[0], prob)
+    assert np.max(np.abs(bal)) <= 1e-11 * np.max(np.abs(ux[0]))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", ["p1_2x2", "uneven", "rate_in", "dirichlet4", "contrast64"])
+def test_mpm_update_parity(name, prec):
+    c = case(name)
+    prob, dec = _oracle_setup(c)
+    s_m = c["s0"]
+    s_n = np.clip(s_m + 0.05 * np.random.default_rng(c["seed"]).standard_normal(s_m.shape), 0, 1)
+    kap_m = O.mobility(s_m, c["M"]) * c["K"]
+    kap_n = O.mobility(s_n, c["M"]) * c["K"]
+    _, bs, sol = O.mrcm_step(kap_m, prob, dec)
+    step, _ = O.mpm_step(kap_n, bs, sol.p, prob, dec)
+    ctx = _gpu(c, prec)
+    ctx.init(0.1)
+    ctx.set_saturation(np.ascontiguousarray(s_n[None]))
+    eps = ctx.eval_epsilon()
+    assert eps[0] == pytest.approx(O.epsilon(kap_n, kap_m), rel=1e-12)
+    ctx.perturbation_solve()
+    ctx.interface_solve()
+    ctx.downscale()
+    pd = ctx.get_pressure(1)[0]
+    ux, uy = ctx.get_flux()
+    tol = TOL[prec]
+    assert rel(ux[0], step.Fx) <= tol, rel(ux[0], step.Fx)
+    assert rel(uy[0], step.Fy) <= tol + 1e-12, rel(uy[0], step.Fy)
+    assert rel(pd, step.p_down) <= tol, rel(pd, step.p_down)
+    bal = O.cell_balance(ux[0], uy[0], prob)
+    assert np.max(np.abs(bal)) <= 1e-11 * np.max(np.abs(ux[0]))
+
+
+def test_transport_parity():
+    c = case("uneven", "front")
+    prob, dec = _oracle_setup(c)
+    kappa = O.mobility(c["s0"], c["M"]) * c["K"]
+    step, _, _ = O.mrcm_step(kappa, prob, dec)
+    ctx = _gpu(c, 0)
+    ctx.init(0.1)
+    dt = ctx.saturation_step(0.5, 3)
+    dt_o = O.cfl_dt(step.Fx, step.Fy, prob, 0.5)
+    assert dt[0] == pytest.approx(dt_o, rel=1e-12)
+    s = c["s0"]
+    for _ in range(3):
+        s = O.upwind_step(s, step.Fx, step.Fy, dt_o, prob)
+    sg = ctx.get_saturation()[0]
+    assert rel(sg, s) <= 1e-12
+    assert np.all(sg >= -1e-14) and np.all(sg <= 1 + 1e-14)
+    np.testing.assert_allclose(ctx.get_conductivity()[0], O.mobility(s, c["M"]) * c["K"], rtol=1e-12)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name,eta,steps", [("p1_2x2", 0.02, 12), ("uneven", -1.0, 4), ("contrast64", 0.05, 8)])
+def test_algorithm1_parity(name, eta, steps, prec):
+    c = case(name, "zero")
+    prob, dec = _oracle_setup(c)
+    st = O.simulate_init(c["K"], c["s0"], prob, dec, eta)
+    ctx = _gpu(c, prec)
+    ctx.init(eta)
+    tol = TOL[prec]
+    for n in range(steps):
+        O.simulate_step(st, c["K"], prob, dec, eta, 0.5, 1)
+        ctx.step(eta, 0.5, 1)
+    s = ctx.get_saturation()[0]
+    ux, uy = ctx.get_flux()
+    stats = ctx.get_stats()
+    n_reb = sum(1 for h in st.history if h["rebuild"])
+    assert stats["rebuilds"] == n_reb + 1  # plus the initial build
+    assert rel(s, st.s) <= tol * 10, rel(s, st.s)
+    assert rel(ux[0], st.step.Fx) <= tol * 10, rel(ux[0], st.step.Fx)
+    assert rel(uy[0], st.step.Fy) <= tol * 10 + 1e-12
+
+
+def test_realisations_are_independent():
+    c = case("p1_2x2")
+    prob, dec = _oracle_setup(c)
+    from paper_2103_11050_gb300 import fields
+    Ks = np.stack([fields.lognormal_grf(c["nx"], c["ny"], c["h"], 1.0, 0.2, "exponential", 40 + r) for r in range(3)])
+    ctx = _gpu(c, 0, R=3, K=Ks)
+    ctx.init(0.1)
+    ux, uy = ctx.get_flux()
+    for r in range(3):
+        step, _, _ = O.mrcm_step(O.mobility(c["s0"], c["M"]) * Ks[r], prob, dec)
+        assert rel(ux[r], step.Fx) <= 1e-10
+
+
+def test_refinement_cap_reports_not_converged():
+    # one refinement sweep cannot reach 1e-15 with an FP32 factor: the library must say so
+    from paper_2103_11050_gb300 import binding as B
+    c = case("contrast64")
+    ctx = _gpu(c, 1)
+    ctx.set_precision(1, 1e-15, 1)
+    ctx.init(0.1)
+    with pytest.raises(B.MPMError) as ei:
+        ctx.sync()
+    assert ei.value.code == B.MPM_ERR_NOT_CONVERGED
