@@ -80,7 +80,20 @@ typedef struct mpm_stats {
   int interface_dofs;         /* interface unknowns per realisation */
   int subdomains;             /* subdomains per realisation */
   int n_hat;                  /* homogeneous BFs per realisation (Section 4.3) */
+  long long kernel_launches;  /* CUDA kernels launched by this context so far */
 } mpm_stats;
+
+/* Stages timed by the profiler (each is the set of kernels of one step of the path). */
+enum {
+  MPM_STAGE_TRANSPORT = 0,     /* CFL reduction, upwind substeps, kappa^n          */
+  MPM_STAGE_EPSILON = 1,       /* kappa^n, epsilon partial sums and decision         */
+  MPM_STAGE_BASIS = 2,         /* Robin factorisation, BF solves, element matrices   */
+  MPM_STAGE_IFACE_FACTOR = 3,  /* nested-dissection factorisation of the interface   */
+  MPM_STAGE_PERTURB = 4,       /* MPM-2P residual and local solve                    */
+  MPM_STAGE_IFACE_SOLVE = 5,   /* element RHS, interface solve, traces, u_bar        */
+  MPM_STAGE_DOWNSCALE = 6,     /* Neumann downscaling (one kernel)                   */
+  MPM_NSTAGES = 7
+};
 
 /* Create a context for R realisations of an nx x ny grid on [0,Lx]x[0,Ly].
  * Cells must be square: Lx/nx == Ly/ny (relative 1e-12).  stream is a cudaStream_t
@@ -95,10 +108,12 @@ int mpm_destroy(mpm_ctx* ctx);
 /* Message of the last failed call on ctx ("" if none). Owned by ctx. */
 const char* mpm_last_error(const mpm_ctx* ctx);
 
-/* Local solver precision (enum above).  ir_tol: relative FP64 residual target of the
- * refinement (ignored for FP64), ir_max: sweep cap (>= 1); a local solve that does not
- * reach ir_tol in ir_max sweeps makes the next mpm_sync / getter return
- * MPM_ERR_NOT_CONVERGED.  Takes effect at the next basis build. */
+/* Local solver precision (enum above).  ir_tol: target of the refinement, as a backward
+ * error in flux units (max |residual| / max(|rhs| + sum |face fluxes|) over the subdomain;
+ * default 1e-14; ignored for FP64), ir_max: sweep cap (>= 1).  Refinement stops at ir_tol,
+ * or when a sweep no longer halves the error (the FP64 rounding floor of the residual) if
+ * the error is then <= 1e3 ir_tol.  A local solve that ends above that makes the next
+ * mpm_sync / getter return MPM_ERR_NOT_CONVERGED.  Takes effect at the next basis build. */
 int mpm_set_precision(mpm_ctx* ctx, int mode, double ir_tol, int ir_max);
 
 /* Absolute permeability K [R][ny][nx], every entry > 0 and finite (checked for host
@@ -192,6 +207,14 @@ int mpm_get_stats(mpm_ctx* ctx, mpm_stats* out);
 
 /* Synchronise the context's stream; returns a pending device-side status. */
 int mpm_sync(mpm_ctx* ctx);
+
+/* Stage profiler: enable != 0 records a CUDA event pair on the context's stream around
+ * every stage launch (small overhead); 0 disables it.  mpm_profile_read synchronises,
+ * writes per stage the summed device time in ms (ms[MPM_NSTAGES]) and the number of
+ * recorded stage executions (count[MPM_NSTAGES]) since enabling or the last read, and
+ * resets them.  Either output may be NULL. */
+int mpm_profile_enable(mpm_ctx* ctx, int enable);
+int mpm_profile_read(mpm_ctx* ctx, double* ms, long long* count);
 
 #ifdef __cplusplus
 }

@@ -26,8 +26,10 @@ FUNCTIONS = [
     "mpm_set_saturation", "mpm_build_basis", "mpm_eval_epsilon", "mpm_choose",
     "mpm_perturbation_solve", "mpm_interface_solve", "mpm_downscale", "mpm_saturation_step",
     "mpm_init", "mpm_step", "mpm_get_pressure", "mpm_get_flux", "mpm_get_saturation",
-    "mpm_get_conductivity", "mpm_get_stats", "mpm_sync",
+    "mpm_get_conductivity", "mpm_get_stats", "mpm_sync", "mpm_profile_enable", "mpm_profile_read",
 ]
+
+STAGES = ["transport", "epsilon", "basis", "iface_factor", "perturb", "iface_solve", "downscale"]
 
 
 class MPMError(RuntimeError):
@@ -40,7 +42,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("rebuilds", ctypes.c_longlong),
                 ("mpm_updates", ctypes.c_longlong), ("last_eps_max", ctypes.c_double),
                 ("last_dt_min", ctypes.c_double), ("ir_iters_max", ctypes.c_int),
-                ("interface_dofs", ctypes.c_int), ("subdomains", ctypes.c_int), ("n_hat", ctypes.c_int)]
+                ("interface_dofs", ctypes.c_int), ("subdomains", ctypes.c_int), ("n_hat", ctypes.c_int),
+                ("kernel_launches", ctypes.c_longlong)]
 
 
 _LIB = None
@@ -87,6 +90,8 @@ def load(path: str | None = None):
         "mpm_get_conductivity": ([P, P, I], I),
         "mpm_get_stats": ([P, ctypes.POINTER(Stats)], I),
         "mpm_sync": ([P], I),
+        "mpm_profile_enable": ([P, I], I),
+        "mpm_profile_read": ([P, DP, ctypes.POINTER(ctypes.c_longlong)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -140,7 +145,7 @@ class Context:
             pass
 
     # ---- setters
-    def set_precision(self, mode, ir_tol=1e-13, ir_max=20):
+    def set_precision(self, mode, ir_tol=1e-14, ir_max=30):
         self._ck(self.L.mpm_set_precision(self.h, int(mode), float(ir_tol), int(ir_max)))
 
     def set_permeability(self, K):
@@ -247,6 +252,16 @@ class Context:
 
     def get_conductivity(self, out=None):
         return self._get(self.L.mpm_get_conductivity, (self.R, self.ny, self.nx), out)
+
+    def profile_enable(self, on=True):
+        self._ck(self.L.mpm_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        """{stage: (ms, count)} since enabling or the last read."""
+        ms = (ctypes.c_double * len(STAGES))()
+        cnt = (ctypes.c_longlong * len(STAGES))()
+        self._ck(self.L.mpm_profile_read(self.h, ms, cnt))
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(STAGES)}
 
     def get_stats(self):
         st = Stats()

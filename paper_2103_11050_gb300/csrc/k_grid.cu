@@ -266,38 +266,50 @@ int grid_cell_blocks(const Grid& g) { return cell_blocks(g); }
 void launch_mobility_eps(const Grid& g, const DevState& d, bool with_eps, cudaStream_t st) {
   dim3 grid(cell_blocks(g), g.R);
   k_mobility_eps<<<grid, kThreads, 0, st>>>(g, d, with_eps ? 1 : 0);
-  if (with_eps) k_eps_finalize<<<g.R, kThreads, 0, st>>>(g, d, grid.x);
+  ++g_launches;
+  if (with_eps) {
+    k_eps_finalize<<<g.R, kThreads, 0, st>>>(g, d, grid.x);
+    ++g_launches;
+  }
 }
 
 void launch_choose(const Grid& g, const DevState& d, double eta, cudaStream_t st) {
   k_choose<<<(g.R + 127) / 128, 128, 0, st>>>(g, d, eta);
+  ++g_launches;
 }
 
 void launch_fill_flags(const Grid& g, const DevState& d, int v, cudaStream_t st) {
   k_fill_flags<<<(g.R + 127) / 128, 128, 0, st>>>(g, d, v);
+  ++g_launches;
 }
 
 void launch_copy_kappa_m(const Grid& g, const DevState& d, cudaStream_t st) {
   k_copy_kappa_m<<<dim3(cell_blocks(g), g.R), kThreads, 0, st>>>(g, d);
+  ++g_launches;
 }
 
 void launch_residual(const Grid& g, const DevState& d, cudaStream_t st) {
   k_residual<<<dim3(cell_blocks(g), g.R), kThreads, 0, st>>>(g, d);
+  ++g_launches;
 }
 
 void launch_ubar(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int branch,
                  cudaStream_t st) {
   k_ubar<<<dim3(nsub, g.R), 128, 0, st>>>(g, d, subs, branch);
+  ++g_launches;
 }
 
 void launch_cfl(const Grid& g, const DevState& d, double cfl, double fmax_, cudaStream_t st) {
   const int nb = cell_blocks(g);
   k_cfl_part<<<dim3(nb, g.R), kThreads, 0, st>>>(g, d);
+  ++g_launches;
   k_cfl_finalize<<<g.R, kThreads, 0, st>>>(g, d, nb, cfl, fmax_);
+  ++g_launches;
 }
 
 void launch_upwind(const Grid& g, const DevState& d, cudaStream_t st) {
   k_upwind<<<dim3(cell_blocks(g), g.R), kThreads, 0, st>>>(g, d);
+  ++g_launches;
 }
 
 }  // namespace mpm

@@ -340,11 +340,13 @@ __global__ void k_nd_down(Grid g, DevState d, const DevNode* nodes, const int* l
 void launch_element_matrix(const Grid& g, const DevState& d, const DevSub* subs, int nsub, const DevNode* nodes,
                            const int* leaf_node, cudaStream_t st) {
   k_element_matrix<<<dim3(nsub, g.R), 256, 0, st>>>(g, d, subs, nodes, leaf_node);
+  ++g_launches;
 }
 
 void launch_element_rhs(const Grid& g, const DevState& d, const DevSub* subs, int nsub, const DevNode* nodes,
                         const int* leaf_node, cudaStream_t st) {
   k_element_rhs<<<dim3(nsub, g.R), 128, 0, st>>>(g, d, subs, nodes, leaf_node);
+  ++g_launches;
 }
 
 void launch_nd_factor_level(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes,
@@ -353,11 +355,15 @@ void launch_nd_factor_level(const Grid& g, const DevState& d, const DevNode* nod
   const long long per = (long long)thr * 8;
   const int ablk = (int)(((long long)max_nf * max_nf + per - 1) / per);
   k_nd_assemble<<<dim3(nlev, ablk, g.R), thr, 0, st>>>(g, d, nodes, level_nodes, srcmap);
+  ++g_launches;
   const int tiles_x = (max_nf + kTile - 1) / kTile;
   for (int k0 = 0; k0 < max_nsep; k0 += kPivotChunk) {
     k_sweep_pivot<<<dim3(nlev, g.R), kPivotChunk * kPivotChunk, 0, st>>>(g, d, nodes, level_nodes, k0);
+    ++g_launches;
     k_sweep_rowcol<<<dim3(nlev, (max_nf + 127) / 128, g.R), 128, 0, st>>>(g, d, nodes, level_nodes, k0);
+    ++g_launches;
     k_sweep_trailing<<<dim3(nlev, tiles_x * tiles_x, g.R), 256, 0, st>>>(g, d, nodes, level_nodes, k0, tiles_x);
+    ++g_launches;
   }
 }
 
@@ -366,6 +372,7 @@ void launch_nd_up(const Grid& g, const DevState& d, const DevNode* nodes, const 
   const int thr = 128;
   k_nd_up<<<dim3(nlev, (max_nf + thr - 1) / thr, g.R), thr, (size_t)max_nsep * sizeof(double), st>>>(
       g, d, nodes, level_nodes, srcmap);
+  ++g_launches;
 }
 
 void launch_nd_down(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
@@ -374,6 +381,7 @@ void launch_nd_down(const Grid& g, const DevState& d, const DevNode* nodes, cons
   const int ny = max_nsep > 0 ? (max_nsep + thr - 1) / thr : 1;
   k_nd_down<<<dim3(nlev, ny, g.R), thr, (size_t)(max_nbnd > 0 ? max_nbnd : 1) * sizeof(double), st>>>(
       g, d, nodes, level_nodes, pmap);
+  ++g_launches;
 }
 
 }  // namespace mpm

@@ -50,11 +50,21 @@ __device__ __forceinline__ void face_info(const DevSub& sd, int f, int& side, in
 // Shared-memory layout of one subdomain problem.
 struct Stencil {
   double* kap;   // m
-  double* dia;   // m   diagonal of A (FP64)
+  double* ex;    // m   diagonal part not due to interior faces (Robin, Dirichlet, pin)
   double* wE;    // m   transmissibility to the east neighbour (0 on the last column)
   double* wN;    // m   transmissibility to the north neighbour (0 on the last row)
   double* sc;    // m   Jacobi scaling (1 in FP64 mode)
 };
+
+// Full diagonal of A at local cell c.
+__device__ __forceinline__ double diag_of(const DevSub& sd, const Stencil& S, int c) {
+  const int a = sd.a;
+  const int jl = c / a, il = c - jl * a;
+  double d = S.ex[c] + S.wE[c] + S.wN[c];
+  if (il > 0) d += S.wE[c - 1];
+  if (jl > 0) d += S.wN[c - a];
+  return d;
+}
 
 // Fill the FP64 stencil of the Robin (neumann = 0) or pinned Neumann (neumann = 1) problem.
 __device__ void build_stencil(const Grid& g, const DevSub& sd, const double* kap_glob, int neumann,
@@ -70,9 +80,7 @@ __device__ void build_stencil(const Grid& g, const DevSub& sd, const double* kap
     const double kc = S.kap[c];
     const double we = il < a - 1 ? harm(kc, S.kap[c + 1]) : 0.0;
     const double wn = jl < b - 1 ? harm(kc, S.kap[c + a]) : 0.0;
-    double dg = we + wn;
-    if (il > 0) dg += harm(kc, S.kap[c - 1]);
-    if (jl > 0) dg += harm(kc, S.kap[c - a]);
+    double dg = 0.0;
     if (!neumann) {
       const int sides[4] = {il == 0 ? 0 : -1, il == a - 1 ? 1 : -1, jl == 0 ? 2 : -1, jl == b - 1 ? 3 : -1};
       for (int q = 0; q < 4; ++q) {
@@ -86,10 +94,10 @@ __device__ void build_stencil(const Grid& g, const DevSub& sd, const double* kap
     }
     S.wE[c] = we;
     S.wN[c] = wn;
-    S.dia[c] = dg;
+    S.ex[c] = dg;
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < m; c += blockDim.x) S.sc[c] = scale ? rsqrt(S.dia[c]) : 1.0;
+  for (int c = threadIdx.x; c < m; c += blockDim.x) S.sc[c] = scale ? rsqrt(diag_of(sd, S, c)) : 1.0;
   __syncthreads();
 }
 
@@ -131,7 +139,7 @@ __device__ void block_factor(const DevSub& sd, Stencil S, T* Qout, T* pub) {
     if (active) {
       const int ci = j * a + i, ck = j * a + k;
       double dij = 0.0;
-      if (i == k) dij = S.dia[ci] * S.sc[ci] * S.sc[ci];
+      if (i == k) dij = diag_of(sd, S, ci) * S.sc[ci] * S.sc[ci];
       else if (k == i + 1) dij = -S.wE[ci] * S.sc[ci] * S.sc[ck];
       else if (i == k + 1) dij = -S.wE[ck] * S.sc[ci] * S.sc[ck];
       T s = T(dij);
@@ -194,16 +202,21 @@ __device__ void block_solve(const DevSub& sd, Stencil S, const T* Q, T* Z, T* W,
   }
 }
 
-// (A x)_c with the FP64 stencil, x with column stride ncol.
+// (A x)_c in flux form: sum over interior faces of T (x_c - x_nb) plus ex_c x_c, so that
+// b - A x is the mass-balance defect of the cell; absx = sum of the magnitudes of the
+// terms (the flux scale of the cell).  x has column stride ncol.
 __device__ __forceinline__ double apply_A(const DevSub& sd, const Stencil& S, const double* x, int c,
-                                          int col, int ncol) {
+                                          int col, int ncol, double& absx) {
   const int a = sd.a, b = sd.b;
   const int jl = c / a, il = c - jl * a;
-  double v = S.dia[c] * x[c * ncol + col];
-  if (il < a - 1) v -= S.wE[c] * x[(c + 1) * ncol + col];
-  if (il > 0) v -= S.wE[c - 1] * x[(c - 1) * ncol + col];
-  if (jl < b - 1) v -= S.wN[c] * x[(c + a) * ncol + col];
-  if (jl > 0) v -= S.wN[c - a] * x[(c - a) * ncol + col];
+  const double xc = x[c * ncol + col];
+  double t = S.ex[c] * xc;
+  double v = t;
+  absx = fabs(t);
+  if (il < a - 1) { t = S.wE[c] * (xc - x[(c + 1) * ncol + col]); v += t; absx += fabs(t); }
+  if (il > 0) { t = S.wE[c - 1] * (xc - x[(c - 1) * ncol + col]); v += t; absx += fabs(t); }
+  if (jl < b - 1) { t = S.wN[c] * (xc - x[(c + a) * ncol + col]); v += t; absx += fabs(t); }
+  if (jl > 0) { t = S.wN[c - a] * (xc - x[(c - a) * ncol + col]); v += t; absx += fabs(t); }
   return v;
 }
 
@@ -212,8 +225,11 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
 }
 
 // Solve A X = B for ncol right-hand sides (B, X FP64 [m][ncol]).  FP64 mode: one block
-// solve.  FP32 mode: refinement  x += S solve(S r),  r = b - A x, until
-// max|r| <= tol max|b| per column or ir_max sweeps.  R, Zw, Ww: workspaces.
+// solve.  FP32 mode: refinement  x += S solve(S r),  r = b - A x (FP64, flux form), with
+// the backward error in flux units  eta = max_col max|r| / max(|b| + sum|fluxes|).
+// Stops when eta <= tol, or when a sweep no longer halves eta (the FP64 rounding floor of
+// the residual has been reached) provided eta <= 1e3 tol; otherwise, or after ir_max
+// sweeps, the status bit is set.  colmax holds per column [max|r|, max(|b|+sum|fluxes|)].
 template <typename T>
 __device__ void solve_refined(const DevSub& sd, Stencil S, const T* Q, const double* B, double* X,
                               double* Rr, T* Zw, T* Ww, int ncol, bool refine, double tol, int ir_max,
@@ -224,43 +240,39 @@ __device__ void solve_refined(const DevSub& sd, Stencil S, const T* Q, const dou
     X[e] = 0.0;
     Rr[e] = B[e];
   }
-  if (refine) {
-    for (int c = threadIdx.x; c < 2 * ncol; c += blockDim.x) colmax[c] = 0.0;
-    __syncthreads();
-    for (int e = threadIdx.x; e < n; e += blockDim.x) atomic_max_nonneg(&colmax[e % ncol], fabs(B[e]));
-  }
   __syncthreads();
   const int sweeps = refine ? ir_max : 1;
   int it = 0;
+  bool ok = false;
+  double eta_prev = 1e300;
   for (; it < sweeps; ++it) {
     for (int e = threadIdx.x; e < n; e += blockDim.x) Zw[e] = T(Rr[e] * S.sc[e / ncol]);
     __syncthreads();
     block_solve<T>(sd, S, Q, Zw, Ww, ncol);
     for (int e = threadIdx.x; e < n; e += blockDim.x) X[e] += double(Zw[e]) * S.sc[e / ncol];
     __syncthreads();
-    if (!refine) break;
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) colmax[ncol + c] = 0.0;
+    if (!refine) { it = 1; ok = true; break; }
+    for (int c = threadIdx.x; c < 2 * ncol; c += blockDim.x) colmax[c] = 0.0;
     __syncthreads();
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
       const int c = e / ncol, col = e - c * ncol;
-      const double r = B[e] - apply_A(sd, S, X, c, col, ncol);
+      double absx;
+      const double r = B[e] - apply_A(sd, S, X, c, col, ncol, absx);
       Rr[e] = r;
-      atomic_max_nonneg(&colmax[ncol + col], fabs(r));
+      atomic_max_nonneg(&colmax[col], fabs(r));
+      atomic_max_nonneg(&colmax[ncol + col], absx + fabs(B[e]));
     }
     __syncthreads();
-    bool done = true;
+    double eta = 0.0;
     for (int col = 0; col < ncol; ++col)
-      if (colmax[ncol + col] > tol * colmax[col]) done = false;
+      if (colmax[ncol + col] > 0.0) eta = fmax(eta, colmax[col] / colmax[ncol + col]);
     __syncthreads();
-    if (done) { ++it; break; }
+    if (eta <= tol) { ok = true; ++it; break; }
+    if (eta > 0.5 * eta_prev) { ok = eta <= 1e3 * tol; ++it; break; }
+    eta_prev = eta;
   }
   if (threadIdx.x == 0) {
-    if (refine) {
-      bool ok = true;
-      for (int col = 0; col < ncol; ++col)
-        if (colmax[ncol + col] > tol * colmax[col]) ok = false;
-      if (!ok) atomicOr(status, 1);
-    }
+    if (!ok) atomicOr(status, 1);
     atomicMax(ir_used, it);
   }
   __syncthreads();
@@ -307,7 +319,7 @@ __device__ Carve<T> carve(char* base, int a, int b, int ncol) {
   Carve<T> c;
   double* p = reinterpret_cast<double*>(base);
   c.S.kap = p; p += m;
-  c.S.dia = p; p += m;
+  c.S.ex = p; p += m;
   c.S.wE = p; p += m;
   c.S.wN = p; p += m;
   c.S.sc = p; p += m;
@@ -331,7 +343,7 @@ int threads_for(int a) {
 
 // ---------------------------------------------------------------------------------------------
 // Robin factorisation at kappa^n (rebuild realisations), stored for reuse by MPM-2P.
-// Stored per subdomain: Q blocks (factor type) and [dia, wE, wN, sc] (FP64).
+// Stored per subdomain: Q blocks (factor type) and [ex, wE, wN, sc] (FP64).
 template <typename T>
 __global__ void k_robin_factor(Grid g, DevState d, const DevSub* subs, int scale) {
   extern __shared__ __align__(16) char smem[];
@@ -345,7 +357,7 @@ __global__ void k_robin_factor(Grid g, DevState d, const DevSub* subs, int scale
   block_factor<T>(sd, cv.S, Qg, cv.pub);
   double* tv = d.tvec + (long long)r * d.st_t + sd.t_off;
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
-    tv[c] = cv.S.dia[c];
+    tv[c] = cv.S.ex[c];
     tv[m + c] = cv.S.wE[c];
     tv[2 * m + c] = cv.S.wN[c];
     tv[3 * m + c] = cv.S.sc[c];
@@ -360,7 +372,7 @@ __device__ void load_robin(const DevState& d, const DevSub& sd, int r, Carve<T>&
   for (int e = threadIdx.x; e < b * a * a; e += blockDim.x) cv.Q[e] = Qg[e];
   const double* tv = d.tvec + (long long)r * d.st_t + sd.t_off;
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
-    cv.S.dia[c] = tv[c];
+    cv.S.ex[c] = tv[c];
     cv.S.wE[c] = tv[m + c];
     cv.S.wN[c] = tv[2 * m + c];
     cv.S.sc[c] = tv[3 * m + c];
@@ -642,10 +654,12 @@ void launch_robin_factor(const Grid& g, const DevState& d, const DevSub* subs, i
     const SmemPlan pl = plan_smem<float>(max_a, max_b, 1);
     set_smem(k_robin_factor<float>, pl.bytes);
     k_robin_factor<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, 1);
+    ++g_launches;
   } else {
     const SmemPlan pl = plan_smem<double>(max_a, max_b, 1);
     set_smem(k_robin_factor<double>, pl.bytes);
     k_robin_factor<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, 0);
+    ++g_launches;
   }
 }
 
@@ -657,10 +671,12 @@ void launch_basis_solve(const Grid& g, const DevState& d, const DevSub* subs, in
     const SmemPlan pl = plan_smem<float>(max_a, max_b, 32);
     set_smem(k_basis_solve<float>, pl.bytes);
     k_basis_solve<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, pl.ncol, 1, ir_tol, ir_max);
+    ++g_launches;
   } else {
     const SmemPlan pl = plan_smem<double>(max_a, max_b, 32);
     set_smem(k_basis_solve<double>, pl.bytes);
     k_basis_solve<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, pl.ncol, 0, ir_tol, ir_max);
+    ++g_launches;
   }
   (void)max_dof;
 }
@@ -673,16 +689,19 @@ void launch_mpm_local(const Grid& g, const DevState& d, const DevSub* subs, int 
     const SmemPlan pl = plan_smem<float>(max_a, max_b, 1);
     set_smem(k_mpm_local<float>, pl.bytes);
     k_mpm_local<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, 1, ir_tol, ir_max);
+    ++g_launches;
   } else {
     const SmemPlan pl = plan_smem<double>(max_a, max_b, 1);
     set_smem(k_mpm_local<double>, pl.bytes);
     k_mpm_local<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, 0, ir_tol, ir_max);
+    ++g_launches;
   }
 }
 
 void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub, const DevNode* nodes,
                         const int* leaf_node, int branch, cudaStream_t st) {
   k_reconstruct<<<dim3(nsub, g.R), 128, 0, st>>>(g, d, subs, nodes, leaf_node, branch);
+  ++g_launches;
 }
 
 void launch_downscale(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
@@ -693,10 +712,12 @@ void launch_downscale(const Grid& g, const DevState& d, const DevSub* subs, int 
     const SmemPlan pl = plan_smem<float>(max_a, max_b, 1);
     set_smem(k_downscale<float>, pl.bytes);
     k_downscale<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, 1, ir_tol, ir_max);
+    ++g_launches;
   } else {
     const SmemPlan pl = plan_smem<double>(max_a, max_b, 1);
     set_smem(k_downscale<double>, pl.bytes);
     k_downscale<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, 0, ir_tol, ir_max);
+    ++g_launches;
   }
 }
 

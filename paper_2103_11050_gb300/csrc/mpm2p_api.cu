@@ -17,13 +17,17 @@
 
 using namespace mpm;
 
+namespace mpm {
+long long g_launches = 0;
+}
+
 struct mpm_ctx {
   Grid g{};
   cudaStream_t stream = nullptr;
   int device = 0;
   std::string err;
   int prec = MPM_PREC_FP64;
-  double ir_tol = 1e-13;
+  double ir_tol = 1e-14;
   int ir_max = 20;
   int fac_prec = -1;  // precision the stored factor was built with
   bool have_K = false, have_s = false, have_dec = false, have_basis = false;
@@ -51,6 +55,12 @@ struct mpm_ctx {
   // host staging for flags
   int* h_flags = nullptr;
   mpm_stats stats{};
+  long long launches0 = 0;  // g_launches when the context was created
+  // stage profiler
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_rec[MPM_NSTAGES];
+  cudaEvent_t ev_open[MPM_NSTAGES] = {};
 };
 
 namespace {
@@ -121,7 +131,7 @@ int sync_status(mpm_ctx* c) {
   c->stats.ir_iters_max = std::max(c->stats.ir_iters_max, it);
   if (st & 1) {
     CK(cudaMemset(c->d.status, 0, sizeof(int)));
-    return fail(c, MPM_ERR_NOT_CONVERGED, "local iterative refinement did not reach ir_tol=%g in ir_max=%d sweeps",
+    return fail(c, MPM_ERR_NOT_CONVERGED, "local iterative refinement stopped above ir_tol=%g (ir_max=%d sweeps)",
                 c->ir_tol, c->ir_max);
   }
   return MPM_OK;
@@ -155,6 +165,32 @@ double max_fprime(double M) {
 }
 
 bool fp32(const mpm_ctx* c) { return c->prec == MPM_PREC_FP32_IR; }
+
+cudaEvent_t take_event(mpm_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void prof_begin(mpm_ctx* c, int stage) {
+  if (!c->prof) return;
+  cudaEvent_t e = take_event(c);
+  cudaEventRecord(e, c->stream);
+  c->ev_open[stage] = e;
+}
+
+void prof_end(mpm_ctx* c, int stage) {
+  if (!c->prof || !c->ev_open[stage]) return;
+  cudaEvent_t e = take_event(c);
+  cudaEventRecord(e, c->stream);
+  c->ev_rec[stage].push_back({c->ev_open[stage], e});
+  c->ev_open[stage] = nullptr;
+}
 
 // ---------------------------------------------------------------------------------------
 // Nested dissection tree over the subdomain grid.
@@ -253,14 +289,18 @@ int run_build(mpm_ctx* c) {
   DevState& d = c->d;
   cudaStream_t st = c->stream;
   const int nsub = (int)c->subs.size();
+  prof_begin(c, MPM_STAGE_BASIS);
   launch_copy_kappa_m(g, d, st);
   launch_robin_factor(g, d, c->d_subs, nsub, c->max_a, c->max_b, fp32(c), st);
   launch_basis_solve(g, d, c->d_subs, nsub, c->max_a, c->max_b, c->max_dof, fp32(c), c->ir_tol, c->ir_max, st);
+  if (c->n_dof > 0) launch_element_matrix(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, st);
+  prof_end(c, MPM_STAGE_BASIS);
   if (c->n_dof > 0) {
-    launch_element_matrix(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, st);
+    prof_begin(c, MPM_STAGE_IFACE_FACTOR);
     for (size_t L = 1; L < c->levels.size(); ++L)
       launch_nd_factor_level(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(),
                              c->lev_max_nf[L], c->lev_max_nsep[L], c->d_srcmap, st);
+    prof_end(c, MPM_STAGE_IFACE_FACTOR);
   }
   c->fac_prec = c->prec;
   c->have_basis = true;
@@ -270,9 +310,11 @@ int run_build(mpm_ctx* c) {
 int run_perturbation(mpm_ctx* c) {
   const Grid& g = c->g;
   const int nsub = (int)c->subs.size();
+  prof_begin(c, MPM_STAGE_PERTURB);
   launch_residual(g, c->d, c->stream);
   launch_mpm_local(g, c->d, c->d_subs, nsub, c->max_a, c->max_b, c->fac_prec == MPM_PREC_FP32_IR, c->ir_tol,
                    c->ir_max, c->stream);
+  prof_end(c, MPM_STAGE_PERTURB);
   return check_launch(c);
 }
 
@@ -281,6 +323,7 @@ int run_interface(mpm_ctx* c) {
   DevState& d = c->d;
   cudaStream_t st = c->stream;
   const int nsub = (int)c->subs.size();
+  prof_begin(c, MPM_STAGE_IFACE_SOLVE);
   if (c->n_dof > 0) {
     launch_element_rhs(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, st);
     for (size_t L = 1; L < c->levels.size(); ++L)
@@ -294,22 +337,27 @@ int run_interface(mpm_ctx* c) {
     launch_reconstruct(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, branch, st);
     launch_ubar(g, d, c->d_subs, nsub, branch, st);
   }
+  prof_end(c, MPM_STAGE_IFACE_SOLVE);
   return check_launch(c);
 }
 
 int run_downscale(mpm_ctx* c) {
+  prof_begin(c, MPM_STAGE_DOWNSCALE);
   launch_downscale(c->g, c->d, c->d_subs, (int)c->subs.size(), c->max_a, c->max_b, fp32(c), c->ir_tol, c->ir_max,
                    c->stream);
+  prof_end(c, MPM_STAGE_DOWNSCALE);
   return check_launch(c);
 }
 
 int run_transport(mpm_ctx* c, double cfl, int n_sub) {
+  prof_begin(c, MPM_STAGE_TRANSPORT);
   launch_cfl(c->g, c->d, cfl, max_fprime(c->g.M), c->stream);
   for (int k = 0; k < n_sub; ++k) {
     launch_upwind(c->g, c->d, c->stream);
     std::swap(c->d.s, c->d.s2);
   }
   launch_mobility_eps(c->g, c->d, false, c->stream);
+  prof_end(c, MPM_STAGE_TRANSPORT);
   return check_launch(c);
 }
 
@@ -372,6 +420,7 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
     return rc;
   }
   cudaStreamSynchronize(c->stream);
+  c->launches0 = g_launches;
   *out = c;
   return MPM_OK;
 }
@@ -379,6 +428,14 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
 int mpm_destroy(mpm_ctx* c) {
   if (!c) return MPM_OK;
   cudaStreamSynchronize(c->stream);
+  for (int k = 0; k < MPM_NSTAGES; ++k) {
+    for (auto& pr : c->ev_rec[k]) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    if (c->ev_open[k]) cudaEventDestroy(c->ev_open[k]);
+  }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   release_decomposition(c);
   free_list(c->grid_allocs);
   if (c->h_flags) cudaFreeHost(c->h_flags);
@@ -785,7 +842,9 @@ int mpm_step(mpm_ctx* c, double eta, double cfl, int n_sub) {
   int rc = need_ready(c, true);
   if (rc) return rc;
   if ((rc = run_transport(c, cfl, n_sub))) return rc;
+  prof_begin(c, MPM_STAGE_EPSILON);
   launch_choose(c->g, c->d, eta, c->stream);
+  prof_end(c, MPM_STAGE_EPSILON);
   CK(cudaMemcpyAsync(c->h_flags, c->d.rebuild, sizeof(int) * c->g.R, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   int nreb = 0;
@@ -794,7 +853,9 @@ int mpm_step(mpm_ctx* c, double eta, double cfl, int n_sub) {
   if (nreb < c->g.R && (rc = run_perturbation(c))) return rc;
   if ((rc = run_interface(c))) return rc;
   if ((rc = run_downscale(c))) return rc;
+  prof_begin(c, MPM_STAGE_EPSILON);
   launch_mobility_eps(c->g, c->d, true, c->stream);
+  prof_end(c, MPM_STAGE_EPSILON);
   c->stats.steps += 1;
   c->stats.rebuilds += nreb;
   c->stats.mpm_updates += c->g.R - nreb;
@@ -834,6 +895,7 @@ int mpm_get_stats(mpm_ctx* c, mpm_stats* out) {
   CK(cudaMemcpy(dt.data(), c->d.dt, sizeof(double) * c->g.R, cudaMemcpyDeviceToHost));
   c->stats.last_eps_max = *std::max_element(e.begin(), e.end());
   c->stats.last_dt_min = *std::min_element(dt.begin(), dt.end());
+  c->stats.kernel_launches = g_launches - c->launches0;
   *out = c->stats;
   return rc;
 }
@@ -841,6 +903,31 @@ int mpm_get_stats(mpm_ctx* c, mpm_stats* out) {
 int mpm_sync(mpm_ctx* c) {
   if (!c) return MPM_ERR_ARG;
   return sync_status(c);
+}
+
+int mpm_profile_enable(mpm_ctx* c, int enable) {
+  if (!c) return MPM_ERR_ARG;
+  c->prof = enable != 0;
+  return MPM_OK;
+}
+
+int mpm_profile_read(mpm_ctx* c, double* ms, long long* count) {
+  if (!c) return MPM_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < MPM_NSTAGES; ++k) {
+    double tot = 0.0;
+    for (auto& pr : c->ev_rec[k]) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, pr.first, pr.second));
+      tot += t;
+      c->ev_pool.push_back(pr.first);
+      c->ev_pool.push_back(pr.second);
+    }
+    if (ms) ms[k] = tot;
+    if (count) count[k] = (long long)c->ev_rec[k].size();
+    c->ev_rec[k].clear();
+  }
+  return MPM_OK;
 }
 
 }  // extern "C"

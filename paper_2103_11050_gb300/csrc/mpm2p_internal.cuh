@@ -82,7 +82,7 @@ struct DevState {
   int* ir_iters;       // [1] max refinement sweeps used
   // per subdomain pools
   void* fac;           // Robin factors (float or double), st_fac values per realisation
-  double* tvec;        // [dia, wE, wN, sc] per subdomain (4 m), st_t
+  double* tvec;        // [ex, wE, wN, sc] per subdomain (4 m), st_t
   double* tr;          // BF traces (2(a+b) x ndof), st_tr
   double* pf;          // BF pressures (m x (ndof + 1)), st_pf
   double* mu_hat;      // BF means, st_dof
@@ -96,6 +96,9 @@ struct DevState {
   double *pivinv, *colold;      // st_lvl * 256, st_col
   long long st_fac, st_t, st_tr, st_pf, st_dof, st_face, st_sub, st_front, st_vec, st_col, st_lvl;
 };
+
+// Kernels launched by this process through the wrappers below (host side, not thread safe).
+extern long long g_launches;
 
 // Host-side launch wrappers (defined in the .cu files).
 int grid_cell_blocks(const Grid& g);

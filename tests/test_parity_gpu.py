@@ -19,10 +19,15 @@ def _oracle_setup(c):
     return prob, dec
 
 
+def _balance(Fx, Fy, prob):
+    """max over cells of |sum of outward fluxes - q h^2|, relative to the largest x-flux."""
+    return float(np.max(np.abs(O.cell_balance(Fx, Fy, prob))) / np.max(np.abs(Fx)))
+
+
 def _gpu(c, prec, R=1, K=None, s0=None):
     from paper_2103_11050_gb300 import binding as B
     ctx = B.Context(R, c["nx"], c["ny"], c["Lx"], c["Ly"])
-    ctx.set_precision(prec, 1e-13, 30)
+    ctx.set_precision(prec, 1e-14, 30)
     ctx.set_fluids(c["M"])
     ctx.set_boundary(c["bc_type"], c["bc_val"], 1.0)
     ctx.set_decomposition(c["col_w"], c["row_h"], c["seg_len"], c["degree"], c["alpha"])
@@ -48,6 +53,7 @@ def test_mrcm_update_parity(name, prec):
     prob, dec = _oracle_setup(c)
     kappa = O.mobility(c["s0"], c["M"]) * c["K"]
     step, _, sol = O.mrcm_step(kappa, prob, dec)
+    obal = _balance(step.Fx, step.Fy, prob)
     ctx = _gpu(c, prec)
     ctx.init(0.1)
     pm = ctx.get_pressure(0)[0]
@@ -58,9 +64,9 @@ def test_mrcm_update_parity(name, prec):
     assert rel(pd, step.p_down) <= tol, rel(pd, step.p_down)
     assert rel(ux[0], step.Fx) <= tol, rel(ux[0], step.Fx)
     assert rel(uy[0], step.Fy) <= tol + 1e-12, rel(uy[0], step.Fy)
-    # conservation of the GPU fluxes in every cell (property at any size)
-    bal = O.cell_balance(ux[0], uy[0], prob)
-    assert np.max(np.abs(bal)) <= 1e-11 * np.max(np.abs(ux[0]))
+    # conservation of the GPU fluxes in every cell, as tight as the FP64 oracle's own rounding
+    bal = _balance(ux[0], uy[0], prob)
+    assert bal <= max(4 * obal, 5e-13), (bal, obal)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -74,6 +80,7 @@ def test_mpm_update_parity(name, prec):
     kap_n = O.mobility(s_n, c["M"]) * c["K"]
     _, bs, sol = O.mrcm_step(kap_m, prob, dec)
     step, _ = O.mpm_step(kap_n, bs, sol.p, prob, dec)
+    obal = _balance(step.Fx, step.Fy, prob)
     ctx = _gpu(c, prec)
     ctx.init(0.1)
     ctx.set_saturation(np.ascontiguousarray(s_n[None]))
@@ -88,8 +95,8 @@ def test_mpm_update_parity(name, prec):
     assert rel(ux[0], step.Fx) <= tol, rel(ux[0], step.Fx)
     assert rel(uy[0], step.Fy) <= tol + 1e-12, rel(uy[0], step.Fy)
     assert rel(pd, step.p_down) <= tol, rel(pd, step.p_down)
-    bal = O.cell_balance(ux[0], uy[0], prob)
-    assert np.max(np.abs(bal)) <= 1e-11 * np.max(np.abs(ux[0]))
+    bal = _balance(ux[0], uy[0], prob)
+    assert bal <= max(4 * obal, 5e-13), (bal, obal)
 
 
 def test_transport_parity():
@@ -108,7 +115,7 @@ def test_transport_parity():
     sg = ctx.get_saturation()[0]
     assert rel(sg, s) <= 1e-12
     assert np.all(sg >= -1e-14) and np.all(sg <= 1 + 1e-14)
-    np.testing.assert_allclose(ctx.get_conductivity()[0], O.mobility(s, c["M"]) * c["K"], rtol=1e-12)
+    np.testing.assert_allclose(ctx.get_conductivity()[0], O.mobility(s, c["M"]) * c["K"], rtol=1e-11)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -147,7 +154,7 @@ def test_realisations_are_independent():
 
 
 def test_refinement_cap_reports_not_converged():
-    # one refinement sweep cannot reach 1e-15 with an FP32 factor: the library must say so
+    # one refinement sweep cannot reach 1e-15 with an FP32 factor (nor its 1e3 x floor): the library must say so
     from paper_2103_11050_gb300 import binding as B
     c = case("contrast64")
     ctx = _gpu(c, 1)
