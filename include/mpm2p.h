@@ -110,10 +110,12 @@ const char* mpm_last_error(const mpm_ctx* ctx);
 
 /* Local solver precision (enum above).  ir_tol: target of the refinement, as a backward
  * error in flux units (max |residual| / max(|rhs| + sum |face fluxes|) over the subdomain;
- * default 1e-14; ignored for FP64), ir_max: sweep cap (>= 1).  Refinement stops at ir_tol,
- * or when a sweep no longer halves the error (the FP64 rounding floor of the residual) if
- * the error is then <= 1e3 ir_tol.  A local solve that ends above that makes the next
- * mpm_sync / getter return MPM_ERR_NOT_CONVERGED.  Takes effect at the next basis build. */
+ * default 1e-14; ignored for FP64), ir_max: sweep cap (>= 1).  Refinement stops at ir_tol
+ * (1e-3 ir_tol for the basis-function solves, whose traces are combined with the interface
+ * coefficients), or when a sweep no longer halves the error (the FP64 rounding floor of the
+ * residual) if the error is then <= 1e3 ir_tol.  A local solve that reaches neither within
+ * ir_max sweeps makes the next mpm_sync / getter return MPM_ERR_NOT_CONVERGED.  Takes
+ * effect at the next basis build. */
 int mpm_set_precision(mpm_ctx* ctx, int mode, double ir_tol, int ir_max);
 
 /* Absolute permeability K [R][ny][nx], every entry > 0 and finite (checked for host

@@ -56,15 +56,6 @@ __device__ __forceinline__ bool dof_info(const DevSub& sd, int k, int& side, int
 
 __device__ __forceinline__ int side_len(const DevSub& sd, int side) { return side < 2 ? sd.b : sd.a; }
 
-__device__ __forceinline__ int side_cell(const DevSub& sd, int side, int t) {
-  return side == 0 ? t * sd.a : side == 1 ? t * sd.a + sd.a - 1 : side == 2 ? t : (sd.b - 1) * sd.a + t;
-}
-
-__device__ __forceinline__ double kap_at(const Grid& g, const double* kap, const DevSub& sd, int cl) {
-  const int jl = cl / sd.a, il = cl - jl * sd.a;
-  return kap[(long long)(sd.y0 + jl) * g.nx + sd.x0 + il];
-}
-
 __global__ void k_element_matrix(Grid g, DevState d, const DevSub* subs, const DevNode* nodes,
                                  const int* leaf_node) {
   const int r = blockIdx.y;
@@ -76,7 +67,7 @@ __global__ void k_element_matrix(Grid g, DevState d, const DevSub* subs, const D
   const DevNode leaf = nodes[leaf_node[sidx]];
   double* E = d.front + (long long)r * d.st_front + leaf.f_off;
   const double* tr = d.tr + (long long)r * d.st_tr + sd.tr_off;
-  const double* kap = d.kap_m + (long long)r * g.ncell();
+  const double* bhat = d.bhat + (long long)r * d.st_face + sd.face_off;
   for (int e = threadIdx.x; e < nd * nd; e += blockDim.x) {
     const int k = e / nd, l = e - k * nd;
     int side, isP, kk;
@@ -85,7 +76,7 @@ __global__ void k_element_matrix(Grid g, DevState d, const DevSub* subs, const D
     dof_info(sd, l, lside, lisP, ll);
     const int L = side_len(sd, side);
     const int f0 = face_side_off(side, sd.a, sd.b);
-    const double rho = sd.side_rho[side], s = sd.side_sign[side];
+    const double s = sd.side_sign[side];
     double v = 0.0;
     for (int t = 0; t < L; ++t) {
       const double w = side_basis(kk, t, g.seg_len, g.degree);
@@ -94,7 +85,7 @@ __global__ void k_element_matrix(Grid g, DevState d, const DevSub* subs, const D
       if (isP) {
         v += w * F;
       } else {
-        const double bh = rho / kap_at(g, kap, sd, side_cell(sd, side, t));
+        const double bh = bhat[f0 + t];
         v -= bh * s * w * F;
         if (!lisP && lside == side) v += bh * w * side_basis(ll, t, g.seg_len, g.degree);
       }
@@ -115,20 +106,20 @@ __global__ void k_element_rhs(Grid g, DevState d, const DevSub* subs, const DevN
   const DevNode leaf = nodes[leaf_node[sidx]];
   double* gv = d.gvec + (long long)r * d.st_vec + leaf.v_off;
   const double* fb = d.fbar + (long long)r * d.st_face + sd.face_off;
-  const double* kap = d.kap_m + (long long)r * g.ncell();
+  const double* bhat = d.bhat + (long long)r * d.st_face + sd.face_off;
   for (int k = threadIdx.x; k < nd; k += blockDim.x) {
     int side, isP, kk;
     dof_info(sd, k, side, isP, kk);
     const int L = side_len(sd, side);
     const int f0 = face_side_off(side, sd.a, sd.b);
-    const double rho = sd.side_rho[side], s = sd.side_sign[side];
+    const double s = sd.side_sign[side];
     double v = 0.0;
     for (int t = 0; t < L; ++t) {
       const double w = side_basis(kk, t, g.seg_len, g.degree);
       if (w == 0.0) continue;
       const double F = fb[f0 + t];
       if (isP) v -= w * F;
-      else v += rho / kap_at(g, kap, sd, side_cell(sd, side, t)) * s * w * F;
+      else v += bhat[f0 + t] * s * w * F;
     }
     gv[k] = v;
   }
@@ -274,13 +265,22 @@ __global__ void k_sweep_trailing(Grid g, DevState d, const DevNode* nodes, const
   }
 }
 
+constexpr int kRowsPerCta = 32;  // frontal rows per CTA of the solve kernels (8 warps x 4 rows)
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Upward solve at one level: gather g from the children, y_s = M_ss g_s -> x, g_b += M_bs g_s.
+// One warp per frontal row (lane-strided dot product, shuffle reduction).
 __global__ void k_nd_up(Grid g, DevState d, const DevNode* nodes, const int* level_nodes, const int* srcmap) {
   extern __shared__ double gs[];
   const int r = blockIdx.z;
   const DevNode nd = nodes[level_nodes[blockIdx.x]];
   const int nf = nd.nf, ns = nd.nsep;
-  const int row0 = blockIdx.y * blockDim.x;
+  const int row0 = blockIdx.y * kRowsPerCta;
   if (row0 >= nf) return;
   const int* s0 = srcmap + nd.src_off;
   const int* s1 = s0 + nf;
@@ -294,45 +294,54 @@ __global__ void k_nd_up(Grid g, DevState d, const DevNode* nodes, const int* lev
     gs[k] = v;
   }
   __syncthreads();
-  const int row = row0 + threadIdx.x;
-  if (row >= nf) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const double* F = d.front + (long long)r * d.st_front + nd.f_off;
-  double acc = 0.0;
-  for (int k = 0; k < ns; ++k) acc += F[(long long)row * nf + k] * gs[k];
-  if (row < ns) {
-    d.xvec[(long long)r * d.st_vec + nd.v_off + row] = acc;
-  } else {
-    double v = 0.0;
-    if (s0[row] >= 0) v += g0[c0.nsep + s0[row]];
-    if (s1[row] >= 0) v += g1[c1.nsep + s1[row]];
-    d.gvec[(long long)r * d.st_vec + nd.v_off + row] = v + acc;
+  for (int row = row0 + warp; row < min(nf, row0 + kRowsPerCta); row += nw) {
+    const double* Fr = F + (long long)row * nf;
+    double acc = 0.0;
+    for (int k = lane; k < ns; k += 32) acc += Fr[k] * gs[k];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      if (row < ns) {
+        d.xvec[(long long)r * d.st_vec + nd.v_off + row] = acc;
+      } else {
+        double v = 0.0;
+        if (s0[row] >= 0) v += g0[c0.nsep + s0[row]];
+        if (s1[row] >= 0) v += g1[c1.nsep + s1[row]];
+        d.gvec[(long long)r * d.st_vec + nd.v_off + row] = v + acc;
+      }
+    }
   }
 }
 
-// Downward solve at one level: x_b from the parent, x_s = y_s - M_sb x_b.
+// Downward solve at one level: x_b from the parent, x_s = y_s - M_sb x_b (one warp per row).
 __global__ void k_nd_down(Grid g, DevState d, const DevNode* nodes, const int* level_nodes, const int* pmap) {
   extern __shared__ double xb[];
   const int r = blockIdx.z;
   const DevNode nd = nodes[level_nodes[blockIdx.x]];
   const int nf = nd.nf, ns = nd.nsep, nbd = nd.nbnd;
+  if (nd.parent < 0) return;
+  const int row0 = blockIdx.y * kRowsPerCta;
+  if (row0 > 0 && row0 >= ns) return;
   double* x = d.xvec + (long long)r * d.st_vec + nd.v_off;
-  if (nd.parent >= 0) {
-    const DevNode pa = nodes[nd.parent];
-    const double* xp = d.xvec + (long long)r * d.st_vec + pa.v_off;
-    const int* pm = pmap + nd.pmap_off;
-    for (int k = threadIdx.x; k < nbd; k += blockDim.x) {
-      const double v = xp[pm[k]];
-      xb[k] = v;
-      if (blockIdx.y == 0) x[ns + k] = v;
-    }
+  const DevNode pa = nodes[nd.parent];
+  const double* xp = d.xvec + (long long)r * d.st_vec + pa.v_off;
+  const int* pm = pmap + nd.pmap_off;
+  for (int k = threadIdx.x; k < nbd; k += blockDim.x) {
+    const double v = xp[pm[k]];
+    xb[k] = v;
+    if (blockIdx.y == 0) x[ns + k] = v;
   }
   __syncthreads();
-  const int row = blockIdx.y * blockDim.x + threadIdx.x;
-  if (row >= ns || nd.parent < 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const double* F = d.front + (long long)r * d.st_front + nd.f_off;
-  double acc = 0.0;
-  for (int k = 0; k < nbd; ++k) acc += F[(long long)row * nf + ns + k] * xb[k];
-  x[row] -= acc;
+  for (int row = row0 + warp; row < min(ns, row0 + kRowsPerCta); row += nw) {
+    const double* Fr = F + (long long)row * nf + ns;
+    double acc = 0.0;
+    for (int k = lane; k < nbd; k += 32) acc += Fr[k] * xb[k];
+    acc = warp_sum(acc);
+    if (lane == 0) x[row] -= acc;
+  }
 }
 
 }  // namespace
@@ -369,17 +378,15 @@ void launch_nd_factor_level(const Grid& g, const DevState& d, const DevNode* nod
 
 void launch_nd_up(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
                   int max_nf, int max_nsep, const int* srcmap, cudaStream_t st) {
-  const int thr = 128;
-  k_nd_up<<<dim3(nlev, (max_nf + thr - 1) / thr, g.R), thr, (size_t)max_nsep * sizeof(double), st>>>(
+  k_nd_up<<<dim3(nlev, (max_nf + kRowsPerCta - 1) / kRowsPerCta, g.R), 256, (size_t)max_nsep * sizeof(double), st>>>(
       g, d, nodes, level_nodes, srcmap);
   ++g_launches;
 }
 
 void launch_nd_down(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
                     int max_nsep, int max_nbnd, const int* pmap, cudaStream_t st) {
-  const int thr = 128;
-  const int ny = max_nsep > 0 ? (max_nsep + thr - 1) / thr : 1;
-  k_nd_down<<<dim3(nlev, ny, g.R), thr, (size_t)(max_nbnd > 0 ? max_nbnd : 1) * sizeof(double), st>>>(
+  const int ny = max_nsep > 0 ? (max_nsep + kRowsPerCta - 1) / kRowsPerCta : 1;
+  k_nd_down<<<dim3(nlev, ny, g.R), 256, (size_t)(max_nbnd > 0 ? max_nbnd : 1) * sizeof(double), st>>>(
       g, d, nodes, level_nodes, pmap);
   ++g_launches;
 }

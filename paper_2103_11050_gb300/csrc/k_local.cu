@@ -17,8 +17,14 @@
 //   backward X_j = W_j + Q_j (t_j o X_{j+1})
 // In FP32 mode the factor is built from the Jacobi-scaled matrix S A S,
 // S = diag(A)^{-1/2}, and FP64 iterative refinement against the FP64 stencil recovers
-// FP64 accuracy.
+// FP64 accuracy.  Factorisations and single-RHS solves run one warp per subdomain
+// (k_local_warp.cuh); the multi-RHS basis solve runs one CTA per subdomain.  Factors are
+// stored padded as [b][A][A] (A = pad_width(max a)).
 #include "mpm2p_internal.cuh"
+#include "k_local_warp.cuh"
+
+#include <algorithm>
+#include <type_traits>
 
 namespace mpm {
 
@@ -56,126 +62,23 @@ struct Stencil {
   double* sc;    // m   Jacobi scaling (1 in FP64 mode)
 };
 
-// Full diagonal of A at local cell c.
-__device__ __forceinline__ double diag_of(const DevSub& sd, const Stencil& S, int c) {
-  const int a = sd.a;
-  const int jl = c / a, il = c - jl * a;
-  double d = S.ex[c] + S.wE[c] + S.wN[c];
-  if (il > 0) d += S.wE[c - 1];
-  if (jl > 0) d += S.wN[c - a];
-  return d;
-}
-
-// Fill the FP64 stencil of the Robin (neumann = 0) or pinned Neumann (neumann = 1) problem.
-__device__ void build_stencil(const Grid& g, const DevSub& sd, const double* kap_glob, int neumann,
-                              int scale, Stencil S) {
-  const int a = sd.a, b = sd.b, m = a * b;
-  for (int c = threadIdx.x; c < m; c += blockDim.x) {
-    const int jl = c / a, il = c - jl * a;
-    S.kap[c] = kap_glob[(long long)(sd.y0 + jl) * g.nx + sd.x0 + il];
-  }
-  __syncthreads();
-  for (int c = threadIdx.x; c < m; c += blockDim.x) {
-    const int jl = c / a, il = c - jl * a;
-    const double kc = S.kap[c];
-    const double we = il < a - 1 ? harm(kc, S.kap[c + 1]) : 0.0;
-    const double wn = jl < b - 1 ? harm(kc, S.kap[c + a]) : 0.0;
-    double dg = 0.0;
-    if (!neumann) {
-      const int sides[4] = {il == 0 ? 0 : -1, il == a - 1 ? 1 : -1, jl == 0 ? 2 : -1, jl == b - 1 ? 3 : -1};
-      for (int q = 0; q < 4; ++q) {
-        const int sdx = sides[q];
-        if (sdx < 0) continue;
-        if (sd.side_kind[sdx] == 1) dg += kc / (0.5 + sd.side_rho[sdx]);
-        else if (g.bc_type[sdx] == 0) dg += 2.0 * kc;
-      }
-    } else if (c == 0) {
-      dg += kc;  // pin: A + kappa_0 e_0 e_0^T
-    }
-    S.wE[c] = we;
-    S.wN[c] = wn;
-    S.ex[c] = dg;
-  }
-  __syncthreads();
-  for (int c = threadIdx.x; c < m; c += blockDim.x) S.sc[c] = scale ? rsqrt(diag_of(sd, S, c)) : 1.0;
-  __syncthreads();
-}
-
-// In-place Gauss-Jordan inversion of an a x a matrix held one entry per thread
-// (thread (i, k) holds v = M[i][k]).  pub: 2 * (2 kMaxSide + 1) values of shared memory.
-template <typename T>
-__device__ void gj_invert(T& v, int i, int k, int a, bool active, T* pub) {
-  constexpr int L = 2 * kMaxSide + 1;
-  for (int p = 0; p < a; ++p) {
-    T* buf = pub + (p & 1) * L;
-    if (active) {
-      if (k == p) buf[i] = v;
-      if (i == p) buf[kMaxSide + k] = v;
-      if (i == p && k == p) buf[2 * kMaxSide] = T(1) / v;
-    }
-    __syncthreads();
-    if (active) {
-      const T ip = buf[2 * kMaxSide];
-      const T mip = buf[i], mpk = buf[kMaxSide + k];
-      if (i == p && k == p) v = ip;
-      else if (i == p) v = mpk * ip;
-      else if (k == p) v = -mip * ip;
-      else v = v - mip * (mpk * ip);
-    }
-  }
-  __syncthreads();
-}
-
-// Block factorisation of the (scaled) stencil into Q_0..Q_{b-1} (written to Qout,
-// b*a*a values).  Requires blockDim.x >= a*a.
-template <typename T>
-__device__ void block_factor(const DevSub& sd, Stencil S, T* Qout, T* pub) {
-  const int a = sd.a, b = sd.b;
-  const int tid = threadIdx.x;
-  const bool active = tid < a * a;
-  const int i = active ? tid / a : 0, k = active ? tid - (tid / a) * a : 0;
-  T v = T(0);
-  for (int j = 0; j < b; ++j) {
-    if (active) {
-      const int ci = j * a + i, ck = j * a + k;
-      double dij = 0.0;
-      if (i == k) dij = diag_of(sd, S, ci) * S.sc[ci] * S.sc[ci];
-      else if (k == i + 1) dij = -S.wE[ci] * S.sc[ci] * S.sc[ck];
-      else if (i == k + 1) dij = -S.wE[ck] * S.sc[ci] * S.sc[ck];
-      T s = T(dij);
-      if (j > 0) {
-        const int pi = ci - a, pk = ck - a;
-        const T ti = T(S.wN[pi] * S.sc[pi] * S.sc[ci]);
-        const T tk = T(S.wN[pk] * S.sc[pk] * S.sc[ck]);
-        s -= ti * v * tk;
-      }
-      v = s;
-    }
-    gj_invert<T>(v, i, k, a, active, pub);
-    if (active) Qout[(long long)j * a * a + i * a + k] = v;
-  }
-  __syncthreads();
-}
-
 // Multi-RHS block solve  (S A S) X = Z  in place on Z ([m][ncol], column stride ncol),
-// W: workspace of the same shape.  Q: b*a*a factor in shared memory.
+// W: workspace of the same shape.  Q: [b][A][A] factor and th[m] = scaled north
+// couplings (factor type), both in shared memory.
 template <typename T>
-__device__ void block_solve(const DevSub& sd, Stencil S, const T* Q, T* Z, T* W, int ncol) {
+__device__ void block_solve(const DevSub& sd, const T* th, const T* Q, int A, T* Z, T* W, int ncol) {
   const int a = sd.a, b = sd.b;
   const int nwork = a * ncol;
   for (int j = 0; j < b; ++j) {
-    const T* Qj = Q + (long long)j * a * a;
+    const T* Qj = Q + (long long)j * A * A;
     for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
       const int i = w / ncol, col = w - (w / ncol) * ncol;
       T acc = T(0);
       for (int k = 0; k < a; ++k) {
         const int ck = j * a + k;
         T zk = Z[ck * ncol + col];
-        if (j > 0) {
-          const int pk = ck - a;
-          zk += T(S.wN[pk] * S.sc[pk] * S.sc[ck]) * W[pk * ncol + col];
-        }
-        acc += Qj[i * a + k] * zk;
+        if (j > 0) zk += th[ck - a] * W[(ck - a) * ncol + col];
+        acc += Qj[i * A + k] * zk;
       }
       W[(j * a + i) * ncol + col] = acc;
     }
@@ -188,13 +91,13 @@ __device__ void block_solve(const DevSub& sd, Stencil S, const T* Q, T* Z, T* W,
   }
   __syncthreads();
   for (int j = b - 2; j >= 0; --j) {
-    const T* Qj = Q + (long long)j * a * a;
+    const T* Qj = Q + (long long)j * A * A;
     for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
       const int i = w / ncol, col = w - (w / ncol) * ncol;
       T acc = W[(j * a + i) * ncol + col];
       for (int k = 0; k < a; ++k) {
-        const int ck = j * a + k, nk = ck + a;
-        acc += Qj[i * a + k] * (T(S.wN[ck] * S.sc[ck] * S.sc[nk]) * Z[nk * ncol + col]);
+        const int ck = j * a + k;
+        acc += Qj[i * A + k] * (th[ck] * Z[(ck + a) * ncol + col]);
       }
       Z[(j * a + i) * ncol + col] = acc;
     }
@@ -227,13 +130,13 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
 // Solve A X = B for ncol right-hand sides (B, X FP64 [m][ncol]).  FP64 mode: one block
 // solve.  FP32 mode: refinement  x += S solve(S r),  r = b - A x (FP64, flux form), with
 // the backward error in flux units  eta = max_col max|r| / max(|b| + sum|fluxes|).
-// Stops when eta <= tol, or when a sweep no longer halves eta (the FP64 rounding floor of
-// the residual has been reached) provided eta <= 1e3 tol; otherwise, or after ir_max
-// sweeps, the status bit is set.  colmax holds per column [max|r|, max(|b|+sum|fluxes|)].
+// Stops when eta <= target, or when a sweep no longer halves eta (the FP64 rounding floor
+// of the residual) provided eta <= 1e3 tol; after ir_max sweeps without either, the status
+// bit is set.  colmax holds per column [max|r|, max(|b|+sum|fluxes|)].
 template <typename T>
-__device__ void solve_refined(const DevSub& sd, Stencil S, const T* Q, const double* B, double* X,
-                              double* Rr, T* Zw, T* Ww, int ncol, bool refine, double tol, int ir_max,
-                              double* colmax /* 2*ncol */, int* status, int* ir_used) {
+__device__ void solve_refined(const DevSub& sd, Stencil S, const T* th, const T* Q, int A, const double* B,
+                              double* X, double* Rr, T* Zw, T* Ww, int ncol, bool refine, double target, double tol,
+                              int ir_max, double* colmax /* 2*ncol */, int* status, int* ir_used) {
   const int m = sd.a * sd.b;
   const int n = m * ncol;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
@@ -248,7 +151,7 @@ __device__ void solve_refined(const DevSub& sd, Stencil S, const T* Q, const dou
   for (; it < sweeps; ++it) {
     for (int e = threadIdx.x; e < n; e += blockDim.x) Zw[e] = T(Rr[e] * S.sc[e / ncol]);
     __syncthreads();
-    block_solve<T>(sd, S, Q, Zw, Ww, ncol);
+    block_solve<T>(sd, th, Q, A, Zw, Ww, ncol);
     for (int e = threadIdx.x; e < n; e += blockDim.x) X[e] += double(Zw[e]) * S.sc[e / ncol];
     __syncthreads();
     if (!refine) { it = 1; ok = true; break; }
@@ -267,8 +170,8 @@ __device__ void solve_refined(const DevSub& sd, Stencil S, const T* Q, const dou
     for (int col = 0; col < ncol; ++col)
       if (colmax[ncol + col] > 0.0) eta = fmax(eta, colmax[col] / colmax[ncol + col]);
     __syncthreads();
-    if (eta <= tol) { ok = true; ++it; break; }
-    if (eta > 0.5 * eta_prev) { ok = eta <= 1e3 * tol; ++it; break; }
+    if (eta <= target) { ok = true; ++it; break; }
+    if (eta > 0.5 * eta_prev && eta <= 1e3 * tol) { ok = true; ++it; break; }  // FP64 floor reached
     eta_prev = eta;
   }
   if (threadIdx.x == 0) {
@@ -286,16 +189,15 @@ struct SmemPlan {
 __host__ __device__ inline size_t stencil_bytes(int m) { return (size_t)5 * m * sizeof(double); }
 
 template <typename T>
-size_t fixed_bytes(int a, int b) {
+size_t fixed_bytes(int a, int b, int A) {
   const int m = a * b;
-  return stencil_bytes(m) + (size_t)b * a * a * sizeof(T) + 4 * (2 * kMaxSide + 1) * sizeof(T) +
-         64 * sizeof(double) + 256;
+  return stencil_bytes(m) + (size_t)b * A * A * sizeof(T) + (size_t)m * sizeof(T) + 64 * sizeof(double) + 256;
 }
 
 template <typename T>
-SmemPlan plan_smem(int a, int b, int ncol_max) {
+SmemPlan plan_smem(int a, int b, int A, int ncol_max) {
   const int m = a * b;
-  const size_t fixed = fixed_bytes<T>(a, b);
+  const size_t fixed = fixed_bytes<T>(a, b, A);
   const size_t per_col = (size_t)m * (3 * sizeof(double) + 2 * sizeof(T)) + 2 * sizeof(double);
   int ncol = (int)((kSmemBudget - fixed) / per_col);
   if (ncol > ncol_max) ncol = ncol_max;
@@ -307,14 +209,14 @@ template <typename T>
 struct Carve {
   Stencil S;
   T* Q;
-  T* pub;
+  T* th;
   double* colmax;
   double *B, *X, *Rr;
   T *Zw, *Ww;
 };
 
 template <typename T>
-__device__ Carve<T> carve(char* base, int a, int b, int ncol) {
+__device__ Carve<T> carve(char* base, int a, int b, int A, int ncol) {
   const int m = a * b;
   Carve<T> c;
   double* p = reinterpret_cast<double*>(base);
@@ -328,10 +230,10 @@ __device__ Carve<T> carve(char* base, int a, int b, int ncol) {
   c.X = p; p += (size_t)m * ncol;
   c.Rr = p; p += (size_t)m * ncol;
   T* q = reinterpret_cast<T*>(p);
-  c.Q = q; q += (size_t)b * a * a;
+  c.Q = q; q += (size_t)b * A * A;
   c.Zw = q; q += (size_t)m * ncol;
   c.Ww = q; q += (size_t)m * ncol;
-  c.pub = q;
+  c.th = q;
   return c;
 }
 
@@ -341,35 +243,12 @@ int threads_for(int a) {
   return (t + 31) / 32 * 32;
 }
 
-// ---------------------------------------------------------------------------------------------
-// Robin factorisation at kappa^n (rebuild realisations), stored for reuse by MPM-2P.
-// Stored per subdomain: Q blocks (factor type) and [ex, wE, wN, sc] (FP64).
+// Load the stored Robin factor (padded) and FP64 stencil of kappa^m into shared memory (CTA).
 template <typename T>
-__global__ void k_robin_factor(Grid g, DevState d, const DevSub* subs, int scale) {
-  extern __shared__ __align__(16) char smem[];
-  const int r = blockIdx.y;
-  if (d.rebuild[r] != 1) return;
-  const DevSub sd = subs[blockIdx.x];
-  const int a = sd.a, b = sd.b, m = a * b;
-  Carve<T> cv = carve<T>(smem, a, b, 1);
-  build_stencil(g, sd, d.kap_n + (long long)r * g.ncell(), 0, scale, cv.S);
-  T* Qg = reinterpret_cast<T*>(d.fac) + (long long)r * d.st_fac + sd.q_off;
-  block_factor<T>(sd, cv.S, Qg, cv.pub);
-  double* tv = d.tvec + (long long)r * d.st_t + sd.t_off;
-  for (int c = threadIdx.x; c < m; c += blockDim.x) {
-    tv[c] = cv.S.ex[c];
-    tv[m + c] = cv.S.wE[c];
-    tv[2 * m + c] = cv.S.wN[c];
-    tv[3 * m + c] = cv.S.sc[c];
-  }
-}
-
-// Load the stored Robin factor and stencil of kappa^m into shared memory.
-template <typename T>
-__device__ void load_robin(const DevState& d, const DevSub& sd, int r, Carve<T>& cv, const Grid& g) {
+__device__ void load_robin(const DevState& d, const DevSub& sd, int r, Carve<T>& cv, const Grid& g, int A) {
   const int a = sd.a, b = sd.b, m = a * b;
   const T* Qg = reinterpret_cast<const T*>(d.fac) + (long long)r * d.st_fac + sd.q_off;
-  for (int e = threadIdx.x; e < b * a * a; e += blockDim.x) cv.Q[e] = Qg[e];
+  for (int e = threadIdx.x; e < b * A * A; e += blockDim.x) cv.Q[e] = Qg[e];
   const double* tv = d.tvec + (long long)r * d.st_t + sd.t_off;
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
     cv.S.ex[c] = tv[c];
@@ -379,6 +258,9 @@ __device__ void load_robin(const DevState& d, const DevSub& sd, int r, Carve<T>&
     const int jl = c / a, il = c - jl * a;
     cv.S.kap[c] = d.kap_m[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il];
   }
+  __syncthreads();
+  for (int c = threadIdx.x; c < m; c += blockDim.x)
+    cv.th[c] = c + a < m ? T(cv.S.wN[c] * cv.S.sc[c] * cv.S.sc[c + a]) : T(0);
   __syncthreads();
 }
 
@@ -449,7 +331,7 @@ __device__ double basis_trace(const Grid& g, const DevSub& sd, const Stencil& S,
 // non-homogeneous one, in column chunks.  Outputs: traces (tr, fbar), pressures (pf incl.
 // the non-homogeneous column), means (mu_hat, sub_mean).
 template <typename T>
-__global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int ncol_max, int refine,
+__global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int ncol_max, int refine,
                               double tol, int ir_max) {
   extern __shared__ __align__(16) char smem[];
   const int r = blockIdx.y;
@@ -458,8 +340,8 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int ncol_m
   const int a = sd.a, b = sd.b, m = a * b;
   const int nface = 2 * (a + b);
   const int ntot = sd.ndof + 1;
-  Carve<T> cv = carve<T>(smem, a, b, ncol_max);
-  load_robin<T>(d, sd, r, cv, g);
+  Carve<T> cv = carve<T>(smem, a, b, A, ncol_max);
+  load_robin<T>(d, sd, r, cv, g, A);
   double* tr = d.tr + (long long)r * d.st_tr + sd.tr_off;       // [nface][ndof]
   double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;       // [m][ndof+1]
   double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
@@ -471,8 +353,10 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int ncol_m
       cv.B[e] = basis_rhs(g, d, sd, cv.S, r, c, c0 + col);
     }
     __syncthreads();
-    solve_refined<T>(sd, cv.S, cv.Q, cv.B, cv.X, cv.Rr, cv.Zw, cv.Ww, ncol, refine != 0, tol, ir_max,
-                     cv.colmax, d.status, d.ir_iters);
+    // The BF traces are combined with possibly large interface coefficients, so their local
+    // conservation defect (sum of residuals) is driven to the FP64 rounding floor.
+    solve_refined<T>(sd, cv.S, cv.th, cv.Q, A, cv.B, cv.X, cv.Rr, cv.Zw, cv.Ww, ncol, refine != 0, 1e-3 * tol, tol,
+                     ir_max, cv.colmax, d.status, d.ir_iters);
     for (int e = threadIdx.x; e < m * ncol; e += blockDim.x) {
       const int c = e / ncol, col = e - c * ncol;
       pf[(long long)c * ntot + c0 + col] = cv.X[e];
@@ -495,36 +379,6 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int ncol_m
       }
     }
     __syncthreads();
-  }
-}
-
-// MPM-2P local solve: A_i(kappa^m) dp = r_i with zero Robin data and homogeneous physical
-// data, using the stored factor.  Outputs the perturbation traces (fbar) and mean(dp).
-template <typename T>
-__global__ void k_mpm_local(Grid g, DevState d, const DevSub* subs, int refine, double tol, int ir_max) {
-  extern __shared__ __align__(16) char smem[];
-  const int r = blockIdx.y;
-  if (d.rebuild[r] != 0) return;
-  const DevSub sd = subs[blockIdx.x];
-  const int a = sd.a, b = sd.b, m = a * b;
-  const int nface = 2 * (a + b);
-  Carve<T> cv = carve<T>(smem, a, b, 1);
-  load_robin<T>(d, sd, r, cv, g);
-  for (int c = threadIdx.x; c < m; c += blockDim.x) {
-    const int jl = c / a, il = c - jl * a;
-    cv.B[c] = d.resid[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il];
-  }
-  __syncthreads();
-  solve_refined<T>(sd, cv.S, cv.Q, cv.B, cv.X, cv.Rr, cv.Zw, cv.Ww, 1, refine != 0, tol, ir_max, cv.colmax,
-                   d.status, d.ir_iters);
-  double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
-  for (int f = threadIdx.x; f < nface; f += blockDim.x)
-    fbar[f] = basis_trace(g, sd, cv.S, cv.X, 1, f, 0, sd.ndof, true);
-  if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (int c = threadIdx.x; c < m; c += 32) s += cv.X[c];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) d.sub_mean[(long long)r * d.st_sub + blockIdx.x] = s / m;
   }
 }
 
@@ -586,22 +440,120 @@ __global__ void k_reconstruct(Grid g, DevState d, const DevSub* subs, const DevN
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Warp-per-subdomain kernels (k_local_warp.cuh).  WPB warps per CTA, one subdomain each.
+
+__device__ __forceinline__ void load_kappa_warp(const Grid& g, const DevSub& sd, const double* kap, double* dst,
+                                                int lane) {
+  for (int c = lane; c < sd.a * sd.b; c += 32) {
+    const int jl = c / sd.a, il = c - jl * sd.a;
+    dst[c] = kap[(long long)(sd.y0 + jl) * g.nx + sd.x0 + il];
+  }
+  __syncwarp();
+}
+
+// Robin factorisation at kappa^n (rebuild realisations), stored for reuse by MPM-2P:
+// Q blocks [b][A][A] (factor type) and [ex, wE, wN, sc] (FP64).
+template <typename T, int A>
+__global__ void k_robin_factor_w(Grid g, DevState d, const DevSub* subs, int nsub, int wpb, size_t per_warp,
+                                 int scale) {
+  extern __shared__ __align__(16) char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sidx = blockIdx.x * wpb + warp;
+  const int r = blockIdx.y;
+  if (sidx >= nsub || d.rebuild[r] != 1) return;
+  const DevSub sd = subs[sidx];
+  const int m = sd.a * sd.b;
+  warp::Tables<T> t = warp::carve<T, A>(smem + warp * per_warp, m, sd.b);
+  load_kappa_warp(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap, lane);
+  warp::build<T, A>(g, sd, t, 0, scale != 0, lane);
+  T* Qg = reinterpret_cast<T*>(d.fac) + (long long)r * d.st_fac + sd.q_off;
+  warp::factor<T, A>(sd, t, Qg, lane);
+  double* tv = d.tvec + (long long)r * d.st_t + sd.t_off;
+  for (int c = lane; c < m; c += 32) {
+    tv[c] = t.ex[c];
+    tv[m + c] = t.wE[c];
+    tv[2 * m + c] = t.wN[c];
+    tv[3 * m + c] = t.sc[c];
+  }
+  double* bh = d.bhat + (long long)r * d.st_face + sd.face_off;
+  for (int f = lane; f < 2 * (sd.a + sd.b); f += 32) {
+    int side, tt, cl;
+    face_info(sd, f, side, tt, cl);
+    bh[f] = sd.side_kind[side] == 1 ? sd.side_rho[side] / t.kap[cl] : 0.0;
+  }
+}
+
+// MPM-2P local solve: A_i(kappa^m) dp = r_i with zero Robin data and homogeneous physical
+// data, using the stored factor.  Outputs the perturbation traces (fbar) and mean(dp).
+template <typename T, int A>
+__global__ void k_mpm_local_w(Grid g, DevState d, const DevSub* subs, int nsub, int wpb, size_t per_warp,
+                              int refine, double tol, int ir_max) {
+  extern __shared__ __align__(16) char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sidx = blockIdx.x * wpb + warp;
+  const int r = blockIdx.y;
+  if (sidx >= nsub || d.rebuild[r] != 0) return;
+  const DevSub sd = subs[sidx];
+  const int a = sd.a, b = sd.b, m = a * b;
+  warp::Tables<T> t = warp::carve<T, A>(smem + warp * per_warp, m, b);
+  load_kappa_warp(g, sd, d.kap_m + (long long)r * g.ncell(), t.kap, lane);
+  const double* tv = d.tvec + (long long)r * d.st_t + sd.t_off;
+  for (int c = lane; c < m; c += 32) {
+    t.ex[c] = tv[c];
+    t.wE[c] = tv[m + c];
+    t.wN[c] = tv[2 * m + c];
+    t.sc[c] = tv[3 * m + c];
+    const int jl = c / a, il = c - jl * a;
+    t.B[c] = d.resid[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il];
+  }
+  __syncwarp();
+  for (int e = lane; e < b * A; e += 32) {
+    const int j = e / A, i = e - j * A;
+    t.th[e] = (i < a && j < b - 1) ? T(t.wN[j * a + i] * t.sc[j * a + i] * t.sc[j * a + i + a]) : T(0);
+  }
+  __syncwarp();
+  const T* Qg = reinterpret_cast<const T*>(d.fac) + (long long)r * d.st_fac + sd.q_off;
+  warp::solve_refined<T, A>(sd, t, Qg, refine != 0, tol, ir_max, d.status, d.ir_iters, lane);
+  double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
+  const int nface = 2 * (a + b);
+  for (int f = lane; f < nface; f += 32) {
+    int side, tt, cl;
+    face_info(sd, f, side, tt, cl);
+    const double kc = t.kap[cl], pc = t.X[cl];
+    double v;
+    if (sd.side_kind[side] == 1) v = kc / (0.5 + sd.side_rho[side]) * pc;
+    else v = g.bc_type[side] == 0 ? 2.0 * kc * pc : 0.0;
+    fbar[f] = v;
+  }
+  double s = 0.0;
+  for (int c = lane; c < m; c += 32) s += t.X[c];
+  s = warp::warp_sum(s);
+  if (lane == 0) d.sub_mean[(long long)r * d.st_sub + sidx] = s / m;
+}
+
 // Downscaling (Eq. mpm_upd): Neumann problem with kappa^n and the fluxes u_bar already
 // written on the subdomain boundary faces of ux / uy; factor + solve + refinement; the
 // pressure constant makes mean(p~) equal the target; writes p~ and the interior fluxes.
-template <typename T>
-__global__ void k_downscale(Grid g, DevState d, const DevSub* subs, int refine, double tol, int ir_max) {
+template <typename T, int A>
+__global__ void k_downscale_w(Grid g, DevState d, const DevSub* subs, int nsub, int wpb, size_t per_warp,
+                              size_t qoff, int refine, double tol, int ir_max) {
   extern __shared__ __align__(16) char smem[];
-  __shared__ double red[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sidx = blockIdx.x * wpb + warp;
   const int r = blockIdx.y;
-  const DevSub sd = subs[blockIdx.x];
+  if (sidx >= nsub) return;
+  const DevSub sd = subs[sidx];
   const int a = sd.a, b = sd.b, m = a * b, nx = g.nx;
-  Carve<T> cv = carve<T>(smem, a, b, 1);
-  build_stencil(g, sd, d.kap_n + (long long)r * g.ncell(), 1, refine, cv.S);
-  block_factor<T>(sd, cv.S, cv.Q, cv.pub);
+  char* base = smem + warp * per_warp;
+  warp::Tables<T> t = warp::carve<T, A>(base, m, b);
+  T* Q = reinterpret_cast<T*>(base + qoff);
+  load_kappa_warp(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap, lane);
+  warp::build<T, A>(g, sd, t, 1, refine != 0, lane);
+  warp::factor<T, A>(sd, t, Q, lane);
   const double* ux = d.ux + (long long)r * g.nfx();
   const double* uy = d.uy + (long long)r * g.nfy();
-  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+  for (int c = lane; c < m; c += 32) {
     const int jl = c / a, il = c - jl * a;
     const int i = sd.x0 + il, j = sd.y0 + jl;
     double v = d.q[(long long)r * g.ncell() + (long long)j * nx + i] * g.h * g.h;
@@ -609,31 +561,22 @@ __global__ void k_downscale(Grid g, DevState d, const DevSub* subs, int refine, 
     if (il == a - 1) v -= ux[(long long)j * (nx + 1) + i + 1];
     if (jl == 0) v += uy[(long long)j * nx + i];
     if (jl == b - 1) v -= uy[(long long)(j + 1) * nx + i];
-    cv.B[c] = v;
+    t.B[c] = v;
   }
-  __syncthreads();
-  solve_refined<T>(sd, cv.S, cv.Q, cv.B, cv.X, cv.Rr, cv.Zw, cv.Ww, 1, refine != 0, tol, ir_max, cv.colmax,
-                   d.status, d.ir_iters);
-  double part = 0.0;
-  for (int c = threadIdx.x; c < m; c += blockDim.x) part += cv.X[c];
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    red[0] = d.sub_target[(long long)r * d.st_sub + blockIdx.x] - s / m;
-  }
-  __syncthreads();
-  const double shift = red[0];
+  __syncwarp();
+  warp::solve_refined<T, A>(sd, t, Q, refine != 0, tol, ir_max, d.status, d.ir_iters, lane);
+  double s = 0.0;
+  for (int c = lane; c < m; c += 32) s += t.X[c];
+  s = warp::warp_sum(s);
+  const double shift = d.sub_target[(long long)r * d.st_sub + sidx] - s / m;
   double* uxw = d.ux + (long long)r * g.nfx();
   double* uyw = d.uy + (long long)r * g.nfy();
-  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+  for (int c = lane; c < m; c += 32) {
     const int jl = c / a, il = c - jl * a;
     const int i = sd.x0 + il, j = sd.y0 + jl;
-    d.p_down[(long long)r * g.ncell() + (long long)j * nx + i] = cv.X[c] + shift;
-    if (il < a - 1) uxw[(long long)j * (nx + 1) + i + 1] = cv.S.wE[c] * (cv.X[c] - cv.X[c + 1]);
-    if (jl < b - 1) uyw[(long long)(j + 1) * nx + i] = cv.S.wN[c] * (cv.X[c] - cv.X[c + a]);
+    d.p_down[(long long)r * g.ncell() + (long long)j * nx + i] = t.X[c] + shift;
+    if (il < a - 1) uxw[(long long)j * (nx + 1) + i + 1] = t.wE[c] * (t.X[c] - t.X[c + 1]);
+    if (jl < b - 1) uyw[(long long)(j + 1) * nx + i] = t.wN[c] * (t.X[c] - t.X[c + a]);
   }
 }
 
@@ -642,60 +585,93 @@ void set_smem(K kernel, size_t bytes) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+size_t align16(size_t v) { return (v + 15) / 16 * 16; }
+
+// Warp launch geometry: per-warp bytes, warps per CTA (<= 4, within the shared-memory budget).
+template <typename T, int A>
+void warp_geometry(int max_a, int max_b, bool with_q, size_t& per_warp, size_t& qoff, int& wpb) {
+  const int m = max_a * max_b;
+  qoff = align16(warp::table_bytes<T, A>(m, max_b));
+  per_warp = align16(qoff + (with_q ? (size_t)max_b * A * A * sizeof(T) : 0));
+  wpb = (int)std::min<size_t>(4, std::max<size_t>(1, kSmemBudget / per_warp));
+}
+
+template <typename T, int A>
+void robin_factor_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
+                    cudaStream_t st) {
+  size_t per, qoff;
+  int wpb;
+  warp_geometry<T, A>(max_a, max_b, false, per, qoff, wpb);
+  set_smem(k_robin_factor_w<T, A>, per * wpb);
+  k_robin_factor_w<T, A><<<dim3((nsub + wpb - 1) / wpb, g.R), 32 * wpb, per * wpb, st>>>(
+      g, d, subs, nsub, wpb, per, std::is_same<T, float>::value ? 1 : 0);
+  ++g_launches;
+}
+
+template <typename T, int A>
+void mpm_local_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b, int refine,
+                 double tol, int ir_max, cudaStream_t st) {
+  size_t per, qoff;
+  int wpb;
+  warp_geometry<T, A>(max_a, max_b, false, per, qoff, wpb);
+  set_smem(k_mpm_local_w<T, A>, per * wpb);
+  k_mpm_local_w<T, A><<<dim3((nsub + wpb - 1) / wpb, g.R), 32 * wpb, per * wpb, st>>>(g, d, subs, nsub, wpb, per,
+                                                                                      refine, tol, ir_max);
+  ++g_launches;
+}
+
+template <typename T, int A>
+void downscale_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b, int refine,
+                 double tol, int ir_max, cudaStream_t st) {
+  size_t per, qoff;
+  int wpb;
+  warp_geometry<T, A>(max_a, max_b, true, per, qoff, wpb);
+  set_smem(k_downscale_w<T, A>, per * wpb);
+  k_downscale_w<T, A><<<dim3((nsub + wpb - 1) / wpb, g.R), 32 * wpb, per * wpb, st>>>(
+      g, d, subs, nsub, wpb, per, qoff, refine, tol, ir_max);
+  ++g_launches;
+}
+
 }  // namespace
 
 int local_smem_limit() { return kSmemBudget; }
 
+#define MPM_DISPATCH_A(FN, T, ...)                         \
+  do {                                                     \
+    const int A_ = pad_width(max_a);                       \
+    if (A_ == 8) FN<T, 8>(__VA_ARGS__);                    \
+    else if (A_ == 16) FN<T, 16>(__VA_ARGS__);             \
+    else FN<T, 32>(__VA_ARGS__);                           \
+  } while (0)
+
 void launch_robin_factor(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
                          bool fp32, cudaStream_t st) {
-  dim3 grid(nsub, g.R);
-  const int thr = threads_for(max_a);
-  if (fp32) {
-    const SmemPlan pl = plan_smem<float>(max_a, max_b, 1);
-    set_smem(k_robin_factor<float>, pl.bytes);
-    k_robin_factor<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, 1);
-    ++g_launches;
-  } else {
-    const SmemPlan pl = plan_smem<double>(max_a, max_b, 1);
-    set_smem(k_robin_factor<double>, pl.bytes);
-    k_robin_factor<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, 0);
-    ++g_launches;
-  }
+  if (fp32) MPM_DISPATCH_A(robin_factor_t, float, g, d, subs, nsub, max_a, max_b, st);
+  else MPM_DISPATCH_A(robin_factor_t, double, g, d, subs, nsub, max_a, max_b, st);
 }
 
 void launch_basis_solve(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
                         int max_dof, bool fp32, double ir_tol, int ir_max, cudaStream_t st) {
   dim3 grid(nsub, g.R);
-  const int thr = threads_for(max_a);
+  const int thr = 256;
+  const int A = pad_width(max_a);
   if (fp32) {
-    const SmemPlan pl = plan_smem<float>(max_a, max_b, 32);
+    const SmemPlan pl = plan_smem<float>(max_a, max_b, A, 32);
     set_smem(k_basis_solve<float>, pl.bytes);
-    k_basis_solve<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, pl.ncol, 1, ir_tol, ir_max);
-    ++g_launches;
+    k_basis_solve<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, A, pl.ncol, 1, ir_tol, ir_max);
   } else {
-    const SmemPlan pl = plan_smem<double>(max_a, max_b, 32);
+    const SmemPlan pl = plan_smem<double>(max_a, max_b, A, 32);
     set_smem(k_basis_solve<double>, pl.bytes);
-    k_basis_solve<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, pl.ncol, 0, ir_tol, ir_max);
-    ++g_launches;
+    k_basis_solve<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, A, pl.ncol, 0, ir_tol, ir_max);
   }
+  ++g_launches;
   (void)max_dof;
 }
 
 void launch_mpm_local(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
                       bool fp32, double ir_tol, int ir_max, cudaStream_t st) {
-  dim3 grid(nsub, g.R);
-  const int thr = threads_for(max_a);
-  if (fp32) {
-    const SmemPlan pl = plan_smem<float>(max_a, max_b, 1);
-    set_smem(k_mpm_local<float>, pl.bytes);
-    k_mpm_local<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, 1, ir_tol, ir_max);
-    ++g_launches;
-  } else {
-    const SmemPlan pl = plan_smem<double>(max_a, max_b, 1);
-    set_smem(k_mpm_local<double>, pl.bytes);
-    k_mpm_local<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, 0, ir_tol, ir_max);
-    ++g_launches;
-  }
+  if (fp32) MPM_DISPATCH_A(mpm_local_t, float, g, d, subs, nsub, max_a, max_b, 1, ir_tol, ir_max, st);
+  else MPM_DISPATCH_A(mpm_local_t, double, g, d, subs, nsub, max_a, max_b, 0, ir_tol, ir_max, st);
 }
 
 void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub, const DevNode* nodes,
@@ -706,19 +682,8 @@ void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, in
 
 void launch_downscale(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
                       bool fp32, double ir_tol, int ir_max, cudaStream_t st) {
-  dim3 grid(nsub, g.R);
-  const int thr = threads_for(max_a);
-  if (fp32) {
-    const SmemPlan pl = plan_smem<float>(max_a, max_b, 1);
-    set_smem(k_downscale<float>, pl.bytes);
-    k_downscale<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, 1, ir_tol, ir_max);
-    ++g_launches;
-  } else {
-    const SmemPlan pl = plan_smem<double>(max_a, max_b, 1);
-    set_smem(k_downscale<double>, pl.bytes);
-    k_downscale<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, 0, ir_tol, ir_max);
-    ++g_launches;
-  }
+  if (fp32) MPM_DISPATCH_A(downscale_t, float, g, d, subs, nsub, max_a, max_b, 1, ir_tol, ir_max, st);
+  else MPM_DISPATCH_A(downscale_t, double, g, d, subs, nsub, max_a, max_b, 0, ir_tol, ir_max, st);
 }
 
 }  // namespace mpm

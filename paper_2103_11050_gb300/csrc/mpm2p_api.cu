@@ -548,6 +548,7 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   }
   c->n_dof = off;
   // subdomains
+  const int Apad = pad_width(*std::max_element(col_w, col_w + ncx));
   std::vector<int> xo(ncx + 1, 0), yo(ncy + 1, 0);
   for (int I = 0; I < ncx; ++I) xo[I + 1] = xo[I] + col_w[I];
   for (int J = 0; J < ncy; ++J) yo[J + 1] = yo[J] + row_h[J];
@@ -595,7 +596,7 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
       s.t_off = t_off;
       s.tr_off = tr_off;
       s.pf_off = pf_off;
-      q_off += (long long)s.b * s.a * s.a;
+      q_off += (long long)s.b * Apad * Apad;
       t_off += 4LL * m;
       tr_off += (long long)nface * nd;
       pf_off += (long long)m * (nd + 1);
@@ -707,6 +708,7 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   if (!rc) rc = dalloc_t(c, A, &d.mu_hat, (size_t)R * dof_off);
   if (!rc) rc = dalloc_t(c, A, &d.fbar, (size_t)R * face_off);
   if (!rc) rc = dalloc_t(c, A, &d.trace, (size_t)R * face_off);
+  if (!rc) rc = dalloc_t(c, A, &d.bhat, (size_t)R * face_off);
   if (!rc) rc = dalloc_t(c, A, &d.sub_mean, (size_t)R * nsub);
   if (!rc) rc = dalloc_t(c, A, &d.sub_target, (size_t)R * nsub);
   if (!rc) rc = dalloc_t(c, A, &d.pm_mean, (size_t)R * nsub);

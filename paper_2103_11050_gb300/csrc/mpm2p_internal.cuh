@@ -16,6 +16,9 @@ namespace mpm {
 constexpr int kMaxSide = 24;     // largest subdomain width / height in cells
 constexpr int kPivotChunk = 16;  // pivot block of the interface sweeps
 
+// Padded width A of the stored local factors ([b][A][A] per subdomain): 8, 16 or 32.
+__host__ __device__ inline int pad_width(int max_a) { return max_a <= 8 ? 8 : max_a <= 16 ? 16 : 32; }
+
 // Face numbering inside a subdomain of a x b cells: left side (b faces, bottom to top),
 // right side (b), bottom side (a faces, left to right), top side (a): 2(a+b) faces.
 __host__ __device__ inline int face_side_off(int side, int a, int b) {
@@ -35,7 +38,7 @@ struct DevSub {
   int side_nbr[4];   // subdomain on the other side of the interface, or -1
   double side_sign[4];  // n_check . n_check^i
   double side_rho[4];   // alpha * (interface length in cells) = alpha H / h
-  long long q_off;   // Robin factor (b*a*a values of the factor type) in the factor pool
+  long long q_off;   // Robin factor (b*A*A values of the factor type, A = pad_width) in the factor pool
   long long t_off;   // b*a values: vertical transmissibilities + scaling (see k_local.cu)
   long long tr_off;  // (2(a+b)) x ndof BF traces
   long long pf_off;  // a*b x ndof BF pressures (temporary, rebuild only)
@@ -88,6 +91,7 @@ struct DevState {
   double* mu_hat;      // BF means, st_dof
   double* fbar;        // non-homogeneous / perturbation traces, st_face
   double* trace;       // one-sided traces of the current update, st_face
+  double* bhat;        // beta_hat = rho / kappa^m per face (interface faces), st_face
   double* sub_mean;    // mean of the non-homogeneous local solution, st_sub
   double* sub_target;  // target mean of the downscaled pressure, st_sub
   double* pm_mean;     // mean of p^m over the subdomain, st_sub
