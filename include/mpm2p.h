@@ -29,7 +29,8 @@
  *    device (for instance a torch CUDA tensor's data_ptr()); the copy is enqueued on the
  *    context's stream.
  *  - The caller owns every pointer it passes; setters copy into library-owned device
- *    memory, getters copy out.  The library allocates its device memory at
+ *    memory, getters copy out.  Changing the precision, fluids, boundary data or
+ *    decomposition discards the stored basis (call mpm_init or mpm_build_basis again).  The library allocates its device memory at
  *    mpm_set_decomposition (and frees it in mpm_destroy); compute calls allocate nothing.
  *  - All work is enqueued on the stream given to mpm_create; compute calls do not
  *    synchronise the host unless stated (mpm_get_*, mpm_get_stats and calls that return
@@ -193,9 +194,17 @@ int mpm_init(mpm_ctx* ctx, double eta);
 
 /* One pass of the while loop of Algorithm 1 (lines 6-20) for every realisation:
  * n_sub transport steps, kappa^n, MRCM rebuild where epsilon > eta (the epsilon of the
- * previous pass) else an MPM-2P update, downscaling, new epsilon.  The branch is taken
- * on the device per realisation; no host synchronisation. */
+ * previous pass) else an MPM-2P update, downscaling, new epsilon.  By default the pass is
+ * one CUDA graph launch: the decision is taken on the device and selects conditional graph
+ * bodies (rebuild / reuse), with no host synchronisation.  The graph is captured at the
+ * first call and again whenever eta, cfl, n_sub, the fluids, the boundary data, the
+ * precision or the decomposition change. */
 int mpm_step(mpm_ctx* ctx, double eta, double cfl, int n_sub);
+
+/* enable = 0 runs mpm_step eagerly (kernel by kernel; the host reads the decision to skip
+ * the branch no realisation takes; used by the stage profiler); 1 (default) uses the
+ * captured graph. */
+int mpm_set_graph(mpm_ctx* ctx, int enable);
 
 /* Copy out pressure [R][ny][nx] (which = MPM_P_*), fluxes ux [R][ny][nx+1],
  * uy [R][ny+1][nx], saturation [R][ny][nx] or conductivity kappa^n.  Synchronise. */

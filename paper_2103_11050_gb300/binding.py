@@ -27,6 +27,7 @@ FUNCTIONS = [
     "mpm_perturbation_solve", "mpm_interface_solve", "mpm_downscale", "mpm_saturation_step",
     "mpm_init", "mpm_step", "mpm_get_pressure", "mpm_get_flux", "mpm_get_saturation",
     "mpm_get_conductivity", "mpm_get_stats", "mpm_sync", "mpm_profile_enable", "mpm_profile_read",
+    "mpm_set_graph",
 ]
 
 STAGES = ["transport", "epsilon", "basis", "iface_factor", "perturb", "iface_solve", "downscale"]
@@ -91,6 +92,7 @@ def load(path: str | None = None):
         "mpm_get_stats": ([P, ctypes.POINTER(Stats)], I),
         "mpm_sync": ([P], I),
         "mpm_profile_enable": ([P, I], I),
+        "mpm_set_graph": ([P, I], I),
         "mpm_profile_read": ([P, DP, ctypes.POINTER(ctypes.c_longlong)], I),
     }
     for name, (args, res) in sig.items():
@@ -252,6 +254,9 @@ class Context:
 
     def get_conductivity(self, out=None):
         return self._get(self.L.mpm_get_conductivity, (self.R, self.ny, self.nx), out)
+
+    def set_graph(self, on=True):
+        self._ck(self.L.mpm_set_graph(self.h, 1 if on else 0))
 
     def profile_enable(self, on=True):
         self._ck(self.L.mpm_profile_enable(self.h, 1 if on else 0))

@@ -95,6 +95,34 @@ __global__ void k_choose(Grid g, DevState d, double eta) {
   if (r < g.R) d.rebuild[r] = d.eps[r] > eta ? 1 : 0;
 }
 
+// Algorithm 1 decision for every realisation (one CTA): rebuild_r = eps_r > eta; counts
+// the branches taken and, inside a CUDA graph, sets the conditional handles of the
+// rebuild body (any realisation rebuilds) and of the MPM-2P body (any reuses).
+__global__ void k_choose_graph(Grid g, DevState d, double eta, cudaGraphConditionalHandle h_reb,
+                               cudaGraphConditionalHandle h_mpm, int set_handles) {
+  __shared__ int tot;
+  if (threadIdx.x == 0) tot = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int r = threadIdx.x; r < g.R; r += blockDim.x) {
+    const int f = d.eps[r] > eta ? 1 : 0;
+    d.rebuild[r] = f;
+    mine += f;
+  }
+  atomicAdd(&tot, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    d.counts[0] += tot;
+    d.counts[1] += g.R - tot;
+    if (set_handles) {
+      cudaGraphSetConditional(h_reb, tot > 0 ? 1u : 0u);
+      cudaGraphSetConditional(h_mpm, tot < g.R ? 1u : 0u);
+      d.counts[2] += tot > 0;
+      d.counts[3] += tot < g.R;
+    }
+  }
+}
+
 __global__ void k_fill_flags(Grid g, DevState d, int v) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < g.R) d.rebuild[r] = v;
@@ -275,6 +303,12 @@ void launch_mobility_eps(const Grid& g, const DevState& d, bool with_eps, cudaSt
 
 void launch_choose(const Grid& g, const DevState& d, double eta, cudaStream_t st) {
   k_choose<<<(g.R + 127) / 128, 128, 0, st>>>(g, d, eta);
+  ++g_launches;
+}
+
+void launch_choose_graph(const Grid& g, const DevState& d, double eta, cudaGraphConditionalHandle h_reb,
+                         cudaGraphConditionalHandle h_mpm, int set_handles, cudaStream_t st) {
+  k_choose_graph<<<1, 256, 0, st>>>(g, d, eta, h_reb, h_mpm, set_handles);
   ++g_launches;
 }
 

@@ -56,6 +56,18 @@ struct mpm_ctx {
   int* h_flags = nullptr;
   mpm_stats stats{};
   long long launches0 = 0;  // g_launches when the context was created
+  long long init_rebuilds = 0;
+  // kernel nodes of the step graph: always run / rebuild body / MPM-2P body; kernels only
+  // recorded by captures (not executed at that time)
+  long long gk_base = 0, gk_reb = 0, gk_mpm = 0, capture_launches = 0, graph_steps = 0;
+  // CUDA graph of one Algorithm 1 step (conditional bodies for the two branches)
+  bool use_graph = true;
+  bool graph_valid = false;
+  double g_eta = 0.0, g_cfl = 0.0;
+  int g_nsub = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t cap_stream = nullptr, body_stream = nullptr;
   // stage profiler
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -270,8 +282,11 @@ int build_tree(mpm_ctx* c, const std::vector<Iface>& ifs, std::vector<HostNode>&
   return id;
 }
 
+void drop_graph(mpm_ctx* c);
+
 int release_decomposition(mpm_ctx* c) {
   if (!c->dec_allocs.empty()) cudaStreamSynchronize(c->stream);
+  drop_graph(c);
   free_list(c->dec_allocs);
   c->d_subs = nullptr;
   c->d_nodes = nullptr;
@@ -352,13 +367,111 @@ int run_downscale(mpm_ctx* c) {
 int run_transport(mpm_ctx* c, double cfl, int n_sub) {
   prof_begin(c, MPM_STAGE_TRANSPORT);
   launch_cfl(c->g, c->d, cfl, max_fprime(c->g.M), c->stream);
+  double* s_home = c->d.s;
   for (int k = 0; k < n_sub; ++k) {
     launch_upwind(c->g, c->d, c->stream);
+    std::swap(c->d.s, c->d.s2);
+  }
+  if (c->d.s != s_home) {  // odd substep count: bring the result home (graph replays read s_home)
+    CK(cudaMemcpyAsync(s_home, c->d.s, sizeof(double) * c->g.R * c->g.ncell(), cudaMemcpyDeviceToDevice,
+                       c->stream));
     std::swap(c->d.s, c->d.s2);
   }
   launch_mobility_eps(c->g, c->d, false, c->stream);
   prof_end(c, MPM_STAGE_TRANSPORT);
   return check_launch(c);
+}
+
+void drop_graph(mpm_ctx* c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->graph_exec = nullptr;
+  c->graph = nullptr;
+  c->graph_valid = false;
+}
+
+#define CKG(call)                                                                                         \
+  do {                                                                                                    \
+    cudaError_t e_ = (call);                                                                              \
+    if (e_ != cudaSuccess) {                                                                              \
+      c->stream = user;                                                                                   \
+      return fail(c, MPM_ERR_CUDA, "graph capture: %s: %s", #call, cudaGetErrorString(e_));              \
+    }                                                                                                     \
+  } while (0)
+
+// Capture one Algorithm 1 step (lines 6-20) as a CUDA graph: transport, kappa^n, the
+// device-side decision, IF(any rebuild){basis build}, IF(any reuse){perturbation solve},
+// interface solve, downscaling, epsilon.  Kernel arguments (grid data, pointers, eta,
+// cfl, n_sub) are captured by value, so setters that change them drop the graph.
+int build_step_graph(mpm_ctx* c, double eta, double cfl, int n_sub) {
+  drop_graph(c);
+  cudaStream_t user = c->stream;
+  cudaStream_t cs = c->cap_stream, bs = c->body_stream;
+  const bool prof = c->prof;
+  c->prof = false;
+  c->stream = cs;
+  const long long L0 = g_launches;
+  long long Lb[3] = {L0, L0, L0};
+  CKG(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  int rc = run_transport(c, cfl, n_sub);
+  cudaStreamCaptureStatus stt;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndep = 0;
+  cudaGraphConditionalHandle h_reb = 0, h_mpm = 0;
+  if (!rc) {
+    CKG(cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, &deps, nullptr, &ndep));
+    CKG(cudaGraphConditionalHandleCreate(&h_reb, cg, 0, cudaGraphCondAssignDefault));
+    CKG(cudaGraphConditionalHandleCreate(&h_mpm, cg, 0, cudaGraphCondAssignDefault));
+    launch_choose_graph(c->g, c->d, eta, h_reb, h_mpm, 1, cs);
+  }
+  Lb[0] = g_launches;
+  for (int branch = 1; branch >= 0 && !rc; --branch) {
+    CKG(cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, &deps, nullptr, &ndep));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = branch ? h_reb : h_mpm;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CKG(cudaGraphAddNode(&node, cg, deps, nullptr, ndep, &np));
+    CKG(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CKG(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    c->stream = bs;
+    rc = branch ? run_build(c) : run_perturbation(c);
+    c->stream = cs;
+    cudaGraph_t body_out = nullptr;
+    CKG(cudaStreamEndCapture(bs, &body_out));
+    Lb[2 - branch] = g_launches;
+  }
+  if (!rc) rc = run_interface(c);
+  if (!rc) rc = run_downscale(c);
+  if (!rc) launch_mobility_eps(c->g, c->d, true, cs);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  c->stream = user;
+  c->prof = prof;
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(c, MPM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  c->graph = graph;
+  e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+  if (e != cudaSuccess) {
+    drop_graph(c);
+    return fail(c, MPM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  c->graph_valid = true;
+  c->gk_reb = Lb[1] - Lb[0];
+  c->gk_mpm = Lb[2] - Lb[1];
+  c->gk_base = (g_launches - L0) - c->gk_reb - c->gk_mpm;
+  c->capture_launches += g_launches - L0;
+  c->g_eta = eta;
+  c->g_cfl = cfl;
+  c->g_nsub = n_sub;
+  return MPM_OK;
 }
 
 int need_ready(mpm_ctx* c, bool basis) {
@@ -413,6 +526,10 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.rebuild, (size_t)R);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.status, 1);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.ir_iters, 1);
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.counts, 4);
+  if (rc == MPM_OK && (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+                       cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking) != cudaSuccess))
+    rc = MPM_ERR_CUDA;
   if (rc == MPM_OK && cudaMallocHost(&c->h_flags, sizeof(int) * R) != cudaSuccess) rc = MPM_ERR_OOM;
   if (rc != MPM_OK) {
     free_list(c->grid_allocs);
@@ -436,6 +553,9 @@ int mpm_destroy(mpm_ctx* c) {
     if (c->ev_open[k]) cudaEventDestroy(c->ev_open[k]);
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  drop_graph(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->body_stream) cudaStreamDestroy(c->body_stream);
   release_decomposition(c);
   free_list(c->grid_allocs);
   if (c->h_flags) cudaFreeHost(c->h_flags);
@@ -452,6 +572,8 @@ int mpm_set_precision(mpm_ctx* c, int mode, double ir_tol, int ir_max) {
   c->prec = mode;
   c->ir_tol = ir_tol;
   c->ir_max = ir_max;
+  c->have_basis = false;  // the stored factors have the old type
+  drop_graph(c);
   return MPM_OK;
 }
 
@@ -483,6 +605,7 @@ int mpm_set_fluids(mpm_ctx* c, double M) {
   if (!c) return MPM_ERR_ARG;
   if (!(M > 0) || !std::isfinite(M)) return fail(c, MPM_ERR_ARG, "viscosity ratio must be positive");
   c->g.M = M;
+  drop_graph(c);
   if (c->have_s && c->have_K) launch_mobility_eps(c->g, c->d, false, c->stream);
   return check_launch(c);
 }
@@ -504,6 +627,7 @@ int mpm_set_boundary(mpm_ctx* c, const int type[4], const double val[4], double 
   }
   c->g.s_inflow = s_inflow;
   c->have_basis = false;
+  drop_graph(c);
   return MPM_OK;
 }
 
@@ -833,7 +957,7 @@ int mpm_init(mpm_ctx* c, double eta) {
   std::vector<double> e(c->g.R, eta);
   CK(cudaMemcpyAsync(c->d.eps, e.data(), sizeof(double) * c->g.R, cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  c->stats.rebuilds += c->g.R;
+  c->init_rebuilds += c->g.R;
   return MPM_OK;
 }
 
@@ -843,9 +967,19 @@ int mpm_step(mpm_ctx* c, double eta, double cfl, int n_sub) {
     return fail(c, MPM_ERR_ARG, "need 0 < cfl <= 1, n_sub >= 1 and finite eta");
   int rc = need_ready(c, true);
   if (rc) return rc;
+  if (c->use_graph && !c->prof) {
+    if (!c->graph_valid || c->g_eta != eta || c->g_cfl != cfl || c->g_nsub != n_sub) {
+      if ((rc = build_step_graph(c, eta, cfl, n_sub))) return rc;
+    }
+    CK(cudaGraphLaunch(c->graph_exec, c->stream));
+    c->stats.steps += 1;
+    c->graph_steps += 1;
+    return MPM_OK;
+  }
+  // eager path: the host reads the device decision to skip the branch nobody takes
   if ((rc = run_transport(c, cfl, n_sub))) return rc;
   prof_begin(c, MPM_STAGE_EPSILON);
-  launch_choose(c->g, c->d, eta, c->stream);
+  launch_choose_graph(c->g, c->d, eta, 0, 0, 0, c->stream);
   prof_end(c, MPM_STAGE_EPSILON);
   CK(cudaMemcpyAsync(c->h_flags, c->d.rebuild, sizeof(int) * c->g.R, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -859,9 +993,14 @@ int mpm_step(mpm_ctx* c, double eta, double cfl, int n_sub) {
   launch_mobility_eps(c->g, c->d, true, c->stream);
   prof_end(c, MPM_STAGE_EPSILON);
   c->stats.steps += 1;
-  c->stats.rebuilds += nreb;
-  c->stats.mpm_updates += c->g.R - nreb;
   return check_launch(c);
+}
+
+int mpm_set_graph(mpm_ctx* c, int enable) {
+  if (!c) return MPM_ERR_ARG;
+  c->use_graph = enable != 0;
+  if (!c->use_graph) drop_graph(c);
+  return MPM_OK;
 }
 
 int mpm_get_pressure(mpm_ctx* c, double* p, int which, int mem) {
@@ -897,7 +1036,12 @@ int mpm_get_stats(mpm_ctx* c, mpm_stats* out) {
   CK(cudaMemcpy(dt.data(), c->d.dt, sizeof(double) * c->g.R, cudaMemcpyDeviceToHost));
   c->stats.last_eps_max = *std::max_element(e.begin(), e.end());
   c->stats.last_dt_min = *std::min_element(dt.begin(), dt.end());
-  c->stats.kernel_launches = g_launches - c->launches0;
+  long long cnt[4] = {0, 0, 0, 0};
+  CK(cudaMemcpy(cnt, c->d.counts, sizeof(cnt), cudaMemcpyDeviceToHost));
+  c->stats.rebuilds = c->init_rebuilds + cnt[0];
+  c->stats.mpm_updates = cnt[1];
+  c->stats.kernel_launches = g_launches - c->launches0 - c->capture_launches + c->graph_steps * c->gk_base +
+                             cnt[2] * c->gk_reb + cnt[3] * c->gk_mpm;
   *out = c->stats;
   return rc;
 }

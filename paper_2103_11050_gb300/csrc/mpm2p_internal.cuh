@@ -83,6 +83,8 @@ struct DevState {
   int* rebuild;        // [R] branch of the current update: 1 = basis build, 0 = MPM-2P reuse
   int* status;         // [1] bitmask: 1 = a refinement did not reach its tolerance
   int* ir_iters;       // [1] max refinement sweeps used
+  long long* counts;   // [4] rebuild / MPM-2P updates taken by the device-side decision; graph steps
+                       //     that ran the rebuild body / the MPM-2P body
   // per subdomain pools
   void* fac;           // Robin factors (float or double), st_fac values per realisation
   double* tvec;        // [ex, wE, wN, sc] per subdomain (4 m), st_t
@@ -109,6 +111,8 @@ int grid_cell_blocks(const Grid& g);
 void launch_mobility_eps(const Grid& g, const DevState& d, bool with_eps, cudaStream_t st);
 void launch_choose(const Grid& g, const DevState& d, double eta, cudaStream_t st);
 void launch_fill_flags(const Grid& g, const DevState& d, int v, cudaStream_t st);
+void launch_choose_graph(const Grid& g, const DevState& d, double eta, cudaGraphConditionalHandle h_reb,
+                         cudaGraphConditionalHandle h_mpm, int set_handles, cudaStream_t st);
 void launch_copy_kappa_m(const Grid& g, const DevState& d, cudaStream_t st);
 void launch_residual(const Grid& g, const DevState& d, cudaStream_t st);
 void launch_ubar(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int branch, cudaStream_t st);

@@ -118,13 +118,15 @@ def test_transport_parity():
     np.testing.assert_allclose(ctx.get_conductivity()[0], O.mobility(s, c["M"]) * c["K"], rtol=1e-11)
 
 
+@pytest.mark.parametrize("graph", [True, False])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("name,eta,steps", [("p1_2x2", 0.02, 12), ("uneven", -1.0, 4), ("contrast64", 0.05, 8)])
-def test_algorithm1_parity(name, eta, steps, prec):
+def test_algorithm1_parity(name, eta, steps, prec, graph):
     c = case(name, "zero")
     prob, dec = _oracle_setup(c)
     st = O.simulate_init(c["K"], c["s0"], prob, dec, eta)
     ctx = _gpu(c, prec)
+    ctx.set_graph(graph)
     ctx.init(eta)
     tol = TOL[prec]
     for n in range(steps):
@@ -135,9 +137,34 @@ def test_algorithm1_parity(name, eta, steps, prec):
     stats = ctx.get_stats()
     n_reb = sum(1 for h in st.history if h["rebuild"])
     assert stats["rebuilds"] == n_reb + 1  # plus the initial build
+    assert stats["mpm_updates"] == steps - n_reb
     assert rel(s, st.s) <= tol * 10, rel(s, st.s)
     assert rel(ux[0], st.step.Fx) <= tol * 10, rel(ux[0], st.step.Fx)
     assert rel(uy[0], st.step.Fy) <= tol * 10 + 1e-12
+
+
+def test_graph_replay_mixed_branches_across_realisations():
+    # R = 3 realisations whose decisions differ step by step: the graph's two conditional
+    # bodies both run and each kernel acts only on its own realisations.
+    c = case("p1_2x2", "zero")
+    prob, dec = _oracle_setup(c)
+    from paper_2103_11050_gb300 import fields
+    Ks = [fields.lognormal_grf(c["nx"], c["ny"], c["h"], 1.0 + r, 0.2, "exponential", 60 + r) for r in range(3)]
+    etas = 0.03
+    sts = [O.simulate_init(K, c["s0"], prob, dec, etas) for K in Ks]
+    ctx = _gpu(c, 1, R=3, K=np.stack(Ks))
+    ctx.init(etas)
+    for _ in range(10):
+        for r in range(3):
+            O.simulate_step(sts[r], Ks[r], prob, dec, etas, 0.5, 1)
+        ctx.step(etas, 0.5, 1)
+    ux, _ = ctx.get_flux()
+    s = ctx.get_saturation()
+    reb = sum(sum(1 for h in st.history if h["rebuild"]) for st in sts)
+    assert ctx.get_stats()["rebuilds"] == reb + 3
+    for r in range(3):
+        assert rel(ux[r], sts[r].step.Fx) <= 1e-8
+        assert rel(s[r], sts[r].s) <= 1e-8
 
 
 def test_realisations_are_independent():
