@@ -51,10 +51,13 @@ __device__ double block_max(double v, double* sh) {
   return v;
 }
 
-// kappa^n = lambda(s) K; optional partial sums of (kappa^n - kappa^m)^2 and (kappa^m)^2.
+// kappa^n = lambda(s) K and the interior-face transmissibilities of kappa^n (the east and
+// north faces of each cell; the neighbour's kappa is recomputed from its s and K);
+// optional partial sums of (kappa^n - kappa^m)^2 and (kappa^m)^2.
 __global__ void k_mobility_eps(Grid g, DevState d, int with_eps) {
   __shared__ double sh[32];
   const int r = blockIdx.y;
+  const int nx = g.nx, ny = g.ny;
   const long long n = g.ncell();
   const long long base = (long long)r * n;
   double num = 0.0, den = 0.0;
@@ -62,6 +65,15 @@ __global__ void k_mobility_eps(Grid g, DevState d, int with_eps) {
        c += (long long)gridDim.x * blockDim.x) {
     const double kn = mobility(d.s[base + c], g.M) * d.K[base + c];
     d.kap_n[base + c] = kn;
+    const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
+    if (i < nx - 1) {
+      const double ke = mobility(d.s[base + c + 1], g.M) * d.K[base + c + 1];
+      d.tx[(long long)r * g.nfx() + (long long)j * (nx + 1) + i + 1] = harm(kn, ke);
+    }
+    if (j < ny - 1) {
+      const double kt = mobility(d.s[base + c + nx], g.M) * d.K[base + c + nx];
+      d.ty[(long long)r * g.nfy() + (long long)(j + 1) * nx + i] = harm(kn, kt);
+    }
     if (with_eps) {
       const double km = d.kap_m[base + c];
       num += (kn - km) * (kn - km);
@@ -153,14 +165,16 @@ __global__ void k_residual(Grid g, DevState d) {
        c += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
     const double kc = d.kap_n[base + c], pc = d.p_m[base + c];
+    const double* tx = d.tx + (long long)r * g.nfx() + (long long)j * (nx + 1);
+    const double* ty = d.ty + (long long)r * g.nfy();
     double out = 0.0;
-    if (i > 0) out += harm(kc, d.kap_n[base + c - 1]) * (pc - d.p_m[base + c - 1]);
+    if (i > 0) out += tx[i] * (pc - d.p_m[base + c - 1]);
     else out += phys_flux(g, 0, kc, pc);
-    if (i < nx - 1) out += harm(kc, d.kap_n[base + c + 1]) * (pc - d.p_m[base + c + 1]);
+    if (i < nx - 1) out += tx[i + 1] * (pc - d.p_m[base + c + 1]);
     else out += phys_flux(g, 1, kc, pc);
-    if (j > 0) out += harm(kc, d.kap_n[base + c - nx]) * (pc - d.p_m[base + c - nx]);
+    if (j > 0) out += ty[(long long)j * nx + i] * (pc - d.p_m[base + c - nx]);
     else out += phys_flux(g, 2, kc, pc);
-    if (j < ny - 1) out += harm(kc, d.kap_n[base + c + nx]) * (pc - d.p_m[base + c + nx]);
+    if (j < ny - 1) out += ty[(long long)(j + 1) * nx + i] * (pc - d.p_m[base + c + nx]);
     else out += phys_flux(g, 3, kc, pc);
     d.resid[base + c] = d.q[base + c] * g.h * g.h - out;
   }
@@ -202,7 +216,9 @@ __global__ void k_ubar(Grid g, DevState d, const DevSub* subs, int branch) {
       val = 0.5 * (Fout - Fnb);
       if (add_fn) {
         const long long cn = side == 1 ? c + 1 : c + nx;
-        val += harm(d.kap_n[cb + c], d.kap_n[cb + cn]) * (d.p_m[cb + c] - d.p_m[cb + cn]);
+        const double T = side == 1 ? d.tx[(long long)r * g.nfx() + (long long)cj * (nx + 1) + ci + 1]
+                                   : d.ty[(long long)r * g.nfy() + (long long)(cj + 1) * nx + ci];
+        val += T * (d.p_m[cb + c] - d.p_m[cb + cn]);
       }
     } else {
       double out = Fout;

@@ -265,7 +265,7 @@ __global__ void k_sweep_trailing(Grid g, DevState d, const DevNode* nodes, const
   }
 }
 
-constexpr int kRowsPerCta = 32;  // frontal rows per CTA of the solve kernels (8 warps x 4 rows)
+constexpr int kRowsPerCta = 8;  // frontal rows per CTA of the solve kernels (one row per warp)
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

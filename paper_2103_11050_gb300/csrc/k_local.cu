@@ -32,8 +32,6 @@ namespace {
 
 constexpr int kSmemBudget = 200 * 1024;
 
-__device__ __forceinline__ double harm(double a, double b) { return 2.0 * a * b / (a + b); }
-
 // Value at edge t of a side basis function kk (seg = kk / (degree+1), power = kk % (degree+1)):
 // Legendre {1, 2 xi - 1} on the segment, evaluated at the edge midpoint.
 __device__ __forceinline__ double side_basis(int kk, int t, int seg_len, int degree) {
@@ -466,7 +464,7 @@ __global__ void k_robin_factor_w(Grid g, DevState d, const DevSub* subs, int nsu
   const int m = sd.a * sd.b;
   warp::Tables<T> t = warp::carve<T, A>(smem + warp * per_warp, m, sd.b);
   load_kappa_warp(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap, lane);
-  warp::build<T, A>(g, sd, t, 0, scale != 0, lane);
+  warp::build<T, A>(g, sd, t, d.tx + (long long)r * g.nfx(), d.ty + (long long)r * g.nfy(), 0, scale != 0, lane);
   T* Qg = reinterpret_cast<T*>(d.fac) + (long long)r * d.st_fac + sd.q_off;
   warp::factor<T, A>(sd, t, Qg, lane);
   double* tv = d.tvec + (long long)r * d.st_t + sd.t_off;
@@ -549,7 +547,7 @@ __global__ void k_downscale_w(Grid g, DevState d, const DevSub* subs, int nsub, 
   warp::Tables<T> t = warp::carve<T, A>(base, m, b);
   T* Q = reinterpret_cast<T*>(base + qoff);
   load_kappa_warp(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap, lane);
-  warp::build<T, A>(g, sd, t, 1, refine != 0, lane);
+  warp::build<T, A>(g, sd, t, d.tx + (long long)r * g.nfx(), d.ty + (long long)r * g.nfy(), 1, refine != 0, lane);
   warp::factor<T, A>(sd, t, Q, lane);
   const double* ux = d.ux + (long long)r * g.nfx();
   const double* uy = d.uy + (long long)r * g.nfy();
@@ -587,13 +585,14 @@ void set_smem(K kernel, size_t bytes) {
 
 size_t align16(size_t v) { return (v + 15) / 16 * 16; }
 
-// Warp launch geometry: per-warp bytes, warps per CTA (<= 4, within the shared-memory budget).
+// Warp launch geometry: per-warp bytes and warps per CTA.  One subdomain per CTA spreads the
+// subdomains over all SMs, whose FP64 pipes (refinement residuals) are the scarce unit.
 template <typename T, int A>
 void warp_geometry(int max_a, int max_b, bool with_q, size_t& per_warp, size_t& qoff, int& wpb) {
   const int m = max_a * max_b;
   qoff = align16(warp::table_bytes<T, A>(m, max_b));
   per_warp = align16(qoff + (with_q ? (size_t)max_b * A * A * sizeof(T) : 0));
-  wpb = (int)std::min<size_t>(4, std::max<size_t>(1, kSmemBudget / per_warp));
+  wpb = 1;
 }
 
 template <typename T, int A>

@@ -16,8 +16,6 @@
 namespace mpm {
 namespace warp {
 
-__device__ __forceinline__ double harm(double a, double b) { return 2.0 * a * b / (a + b); }
-
 // Per-warp shared-memory tables of one subdomain (a x b cells, m = a b, padded width A).
 template <typename T>
 struct Tables {
@@ -62,16 +60,19 @@ __device__ Tables<T> carve(char* base, int m, int b) {
   return t;
 }
 
-// FP64 stencil of the Robin (neumann = 0) or pinned Neumann (neumann = 1) operator from
-// kappa, and the scaled T tables.  kap must already hold the subdomain's kappa.
+// FP64 stencil of the Robin (neumann = 0) or pinned Neumann (neumann = 1) operator of
+// kappa^n (transmissibilities tx / ty of the current kappa^n, r-th realisation pointers),
+// and the scaled T tables.  kap must already hold the subdomain's kappa^n.
 template <typename T, int A>
-__device__ void build(const Grid& g, const DevSub& sd, Tables<T> t, int neumann, bool scale, int lane) {
+__device__ void build(const Grid& g, const DevSub& sd, Tables<T> t, const double* tx, const double* ty,
+                      int neumann, bool scale, int lane) {
   const int a = sd.a, b = sd.b, m = a * b;
   for (int c = lane; c < m; c += 32) {
     const int jl = c / a, il = c - jl * a;
+    const int i = sd.x0 + il, j = sd.y0 + jl;
     const double kc = t.kap[c];
-    t.wE[c] = il < a - 1 ? harm(kc, t.kap[c + 1]) : 0.0;
-    t.wN[c] = jl < b - 1 ? harm(kc, t.kap[c + a]) : 0.0;
+    t.wE[c] = il < a - 1 ? tx[(long long)j * (g.nx + 1) + i + 1] : 0.0;
+    t.wN[c] = jl < b - 1 ? ty[(long long)(j + 1) * g.nx + i] : 0.0;
     double dg = 0.0;
     if (!neumann) {
       if (il == 0) dg += sd.side_kind[0] == 1 ? kc / (0.5 + sd.side_rho[0]) : (g.bc_type[0] == 0 ? 2.0 * kc : 0.0);

@@ -519,6 +519,8 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   const int nblk = 1024;
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.ux, (size_t)R * g.nfx());
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.uy, (size_t)R * g.nfy());
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.tx, (size_t)R * g.nfx());
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.ty, (size_t)R * g.nfy());
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.eps, (size_t)R);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.dt, (size_t)R);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.eps_part, (size_t)R * nblk * 2);

@@ -78,6 +78,7 @@ struct DevState {
   double *K, *q, *s, *s2, *kap_n, *kap_m, *p_m, *p_down, *resid;
   // faces
   double *ux, *uy;
+  double *tx, *ty;     // transmissibilities of kappa^n: tx [R][ny][nx+1], ty [R][ny+1][nx] (interior faces)
   // per realisation scalars
   double *eps, *dt, *eps_part, *rate_part;
   int* rebuild;        // [R] branch of the current update: 1 = basis build, 0 = MPM-2P reuse
