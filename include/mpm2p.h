@@ -49,7 +49,8 @@ enum {
   MPM_ERR_CUDA = 2,           /* a CUDA runtime call failed */
   MPM_ERR_OOM = 3,            /* device allocation failed */
   MPM_ERR_NOT_CONVERGED = 4,  /* iterative refinement hit its iteration cap */
-  MPM_ERR_STATE = 5           /* call out of order (e.g. solve before build) */
+  MPM_ERR_STATE = 5,          /* call out of order (e.g. solve before build) */
+  MPM_ERR_TOO_LARGE = 6       /* request exceeds a fixed capacity (mpm_cfl_dt_noalloc) */
 };
 
 enum { MPM_MEM_HOST = 0, MPM_MEM_DEVICE = 1 };
@@ -226,6 +227,29 @@ int mpm_sync(mpm_ctx* ctx);
  * resets them.  Either output may be NULL. */
 int mpm_profile_enable(mpm_ctx* ctx, int enable);
 int mpm_profile_read(mpm_ctx* ctx, double* ms, long long* count);
+
+/* Allocation-free transport time step (the paper has no counterpart: this is a service
+ * for callers that cannot allocate device memory).  Some callers cannot call cudaMalloc:
+ * code whose device memory belongs to another runtime's pre-sized pool, or a
+ * latency-critical loop that cannot afford an allocation's implicit device
+ * synchronisation or its failure mid-run.  For them this computes, without any context
+ * and without allocating, the same dt per realisation as mpm_saturation_step:
+ *   dt_r = cfl h^2 / (max f' * max_c max(out_c, in_c))  (0 when there is no flow),
+ * out_c / in_c the total integrated outflow / inflow of cell c, f' for viscosity ratio M.
+ * ux [R][ny][nx+1], uy [R][ny+1][nx] (integrated face fluxes, as mpm_get_flux) and dt [R]
+ * are caller-owned DEVICE pointers of the current device; the work is enqueued on stream
+ * (a cudaStream_t, NULL = legacy default stream) and the call does not synchronise.
+ * Scratch: a fixed 512 KiB device array inside the library (64 partial maxima per
+ * realisation), held by every GPU that loads the library until the process exits; hence
+ * R <= 1024, and larger R returns MPM_ERR_TOO_LARGE without launching anything.  The
+ * first call on a device looks up that array's device address (cudaGetSymbolAddress), so
+ * make the first call on each device before any stream capture, from one host thread.
+ * Every call overwrites the scratch slots it reads, so nothing has to be cleared, but all
+ * calls share the array: calls that may overlap on the GPU (different streams without
+ * ordering) race and must be serialised by the caller.  Returns MPM_ERR_ARG for null
+ * pointers, non-positive sizes, h, M or cfl outside (0,1]; MPM_ERR_CUDA if a CUDA call fails. */
+int mpm_cfl_dt_noalloc(const double* ux, const double* uy, int R, int nx, int ny, double h, double M,
+                       double cfl, double* dt, void* stream);
 
 #ifdef __cplusplus
 }

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-MPM_OK, MPM_ERR_ARG, MPM_ERR_CUDA, MPM_ERR_OOM, MPM_ERR_NOT_CONVERGED, MPM_ERR_STATE = range(6)
+MPM_OK, MPM_ERR_ARG, MPM_ERR_CUDA, MPM_ERR_OOM, MPM_ERR_NOT_CONVERGED, MPM_ERR_STATE, MPM_ERR_TOO_LARGE = range(7)
 MEM_HOST, MEM_DEVICE = 0, 1
 BC_DIRICHLET, BC_NEUMANN = 0, 1
 PREC_FP64, PREC_FP32_IR = 0, 1
@@ -27,7 +27,7 @@ FUNCTIONS = [
     "mpm_perturbation_solve", "mpm_interface_solve", "mpm_downscale", "mpm_saturation_step",
     "mpm_init", "mpm_step", "mpm_get_pressure", "mpm_get_flux", "mpm_get_saturation",
     "mpm_get_conductivity", "mpm_get_stats", "mpm_sync", "mpm_profile_enable", "mpm_profile_read",
-    "mpm_set_graph",
+    "mpm_set_graph", "mpm_cfl_dt_noalloc",
 ]
 
 STAGES = ["transport", "epsilon", "basis", "iface_factor", "perturb", "iface_solve", "downscale"]
@@ -93,6 +93,7 @@ def load(path: str | None = None):
         "mpm_sync": ([P], I),
         "mpm_profile_enable": ([P, I], I),
         "mpm_set_graph": ([P, I], I),
+        "mpm_cfl_dt_noalloc": ([P, P, I, I, I, D, D, D, P, P], I),
         "mpm_profile_read": ([P, DP, ctypes.POINTER(ctypes.c_longlong)], I),
     }
     for name, (args, res) in sig.items():
@@ -101,6 +102,17 @@ def load(path: str | None = None):
         fn.restype = res
     _LIB = L
     return L
+
+
+def cfl_dt_noalloc(ux, uy, dt, h, M, cfl, stream=None):
+    """mpm_cfl_dt_noalloc on torch CUDA tensors ux [R][ny][nx+1], uy [R][ny+1][nx], dt [R]."""
+    L = load()
+    R, ny, nx1 = ux.shape
+    rc = L.mpm_cfl_dt_noalloc(ctypes.c_void_p(ux.data_ptr()), ctypes.c_void_p(uy.data_ptr()), int(R), int(nx1 - 1),
+                              int(ny), float(h), float(M), float(cfl), ctypes.c_void_p(dt.data_ptr()),
+                              ctypes.c_void_p(0 if stream is None else int(stream)))
+    if rc != MPM_OK:
+        raise MPMError(rc, "mpm_cfl_dt_noalloc failed")
 
 
 def _ptr(x):
