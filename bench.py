@@ -114,7 +114,8 @@ def make_inputs(w, R=1):
 
 def setup_ctx(B, w, K, s0, prec, stream, R=1):
     ctx = B.Context(R, w["nx"], w["ny"], 1.0, 1.0, stream=stream)
-    ctx.set_precision(B.PREC_FP32_IR if prec == "fp32" else B.PREC_FP64, 1e-14, 30)
+    mode = {"fp32": B.PREC_FP32_IR, "fp32all": B.PREC_FP32_IR_ALL, "fp64": B.PREC_FP64}[prec]
+    ctx.set_precision(mode, 1e-14, 30)
     ctx.set_fluids(w["M"])
     ctx.set_boundary((0, 0, 1, 1), (1.0, 0.0, 0.0, 0.0), 1.0)
     sd = w["nx"] // w["ncx"]
@@ -194,11 +195,13 @@ def run_gpu(args, w):
     main["prof"] = prof_run["prof"]
     # the plain FP64 GPU form on the same steps, and the accuracy of the main form against it
     other = {}
-    if prec == "fp32" and not args.no_fp64:
+    if prec != "fp64" and not args.no_fp64:
         f64, ux64 = one_run("fp64", args.steps, args.warmup, False)
+        f64p, _ = one_run("fp64", args.steps, args.warmup, True)
         other = {"fp64_form_value": cells * args.steps / (f64["ms"] / 1e3),
                  "rel_flux_err_vs_fp64": float(np.linalg.norm(ux_main - ux64) / np.linalg.norm(ux64)),
-                 "fp64_form_ms_per_step": f64["ms"] / args.steps}
+                 "fp64_form_ms_per_step": f64["ms"] / args.steps,
+                 "fp64_form_stage_ms_per_step_eager": {k: v[0] / args.steps for k, v in f64p["prof"].items()}}
 
     # end to end through the C ABI with host buffers: per step set s (h2d), step, read s (d2h)
     ctx = setup_ctx(B, w, K, s0, prec, stream.cuda_stream)
@@ -224,22 +227,25 @@ def run_gpu(args, w):
     flops, _bytes = algorithmic_downscale(w)
     ds_avg_s = ds_ms / 1e3 / max(ds_n, 1)
     sm_clock = 2070.0
-    fp_peak = (152 * 128 * 2 * sm_clock * 1e6 / 1e12) if prec == "fp32" else (152 * 2 * 2 * sm_clock * 1e6 / 1e12)
+    fp_peak = (152 * 128 * 2 * sm_clock * 1e6 / 1e12) if prec != "fp64" else (152 * 2 * 2 * sm_clock * 1e6 / 1e12)
     roof = {"kernel": "k_downscale", "bound": "alu", "achieved": flops / ds_avg_s / 1e12,
             "peak": fp_peak, "unit": "TFLOP/s", "frac": (flops / ds_avg_s / 1e12) / fp_peak, "traffic": None,
-            "peak_kind": f"derived: 152 SMs x {'128 FP32' if prec == 'fp32' else '2 FP64'} FMA/clk x 2 x 2070 MHz",
+            "peak_kind": f"derived: 152 SMs x {'128 FP32' if prec != 'fp64' else '2 FP64'} FMA/clk x 2 x 2070 MHz",
             "dominant_stage": dom,
             "stage_ms_per_step_eager": {k: v[0] / args.steps for k, v in prof.items()},
             "eager_ms_per_step": prof_run["ms"] / args.steps}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": main["ms"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64ir" if prec == "fp32" else "f64", "data": "synthetic (seeded log-normal field)",
+        "dtype": "f32+f64ir" if prec != "fp64" else "f64", "data": "synthetic (seeded log-normal field)",
         "config": {"workload": f"{WORKLOAD}: {workload_desc(w)}", "realisations": 1,
                    "timed_steps_rebuild": main["rebuilds"], "timed_steps_mpm": main["mpm"],
                    "l2": "flushed between timed steps (256 MB write outside the timed region)",
-                   "precision": "FP32 local factorisations + FP64 refinement; FP64 interface, fluxes, transport"
-                   if prec == "fp32" else "FP64 throughout"},
+                   "precision": {"fp32": "FP32 downscaling factorisations + FP64 refinement; FP64 Robin factors, "
+                                          "interface, fluxes, transport",
+                                 "fp32all": "FP32 local factorisations + FP64 refinement; FP64 interface, fluxes, "
+                                            "transport",
+                                 "fp64": "FP64 throughout"}[prec]},
         "gpu_launches": main["launches"],
         "e2e": {"value": cells * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * cells,
                 "d2h_bytes_per_step": 8 * cells},
@@ -303,7 +309,9 @@ def main():
     ap.add_argument("--steps", type=int, default=197)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp32all", "fp64"],
+                    help="fp32: FP32 downscaling factors + FP64 refinement, FP64 Robin factors; "
+                         "fp32all: every local factor FP32 + FP64 refinement; fp64: all FP64")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=20.0)

@@ -57,12 +57,16 @@ enum { MPM_MEM_HOST = 0, MPM_MEM_DEVICE = 1 };
 enum { MPM_BC_DIRICHLET = 0, MPM_BC_NEUMANN = 1 };
 enum { MPM_SIDE_LEFT = 0, MPM_SIDE_RIGHT = 1, MPM_SIDE_BOTTOM = 2, MPM_SIDE_TOP = 3 };
 
-/* Precision of the local factorisations and triangular solves.
- *  FP64:      everything in float64.
- *  FP32_IR:   local Robin / Neumann factorisations and solves in float32 with
- *             float64 residuals and iterative refinement to ir_tol; interface
- *             (skeleton) system, residuals, fluxes and transport stay float64. */
-enum { MPM_PREC_FP64 = 0, MPM_PREC_FP32_IR = 1 };
+/* Precision of the local factorisations and solves.
+ *  FP64:          everything in float64.
+ *  FP32_IR:       the per-step Neumann downscaling (a new factorisation every step) in
+ *                 float32 with float64 refinement to ir_tol; the Robin factors, built once
+ *                 per basis rebuild and reused by every BF solve and every MPM-2P step, in
+ *                 float64 (on GB300 a float64 solve with a stored factor costs less than
+ *                 float32 solves plus float64 refinement residuals).
+ *  FP32_IR_ALL:   every local factorisation and solve in float32 with float64 refinement.
+ * The interface (skeleton) system, residuals, fluxes and transport are float64 in all modes. */
+enum { MPM_PREC_FP64 = 0, MPM_PREC_FP32_IR = 1, MPM_PREC_FP32_IR_ALL = 2 };
 
 /* Which pressure mpm_get_pressure returns. */
 enum {

@@ -17,7 +17,7 @@ from . import build as _build
 MPM_OK, MPM_ERR_ARG, MPM_ERR_CUDA, MPM_ERR_OOM, MPM_ERR_NOT_CONVERGED, MPM_ERR_STATE, MPM_ERR_TOO_LARGE = range(7)
 MEM_HOST, MEM_DEVICE = 0, 1
 BC_DIRICHLET, BC_NEUMANN = 0, 1
-PREC_FP64, PREC_FP32_IR = 0, 1
+PREC_FP64, PREC_FP32_IR, PREC_FP32_IR_ALL = 0, 1, 2
 P_MRCM, P_DOWNSCALED = 0, 1
 
 FUNCTIONS = [

@@ -110,7 +110,16 @@ __device__ void build(const Grid& g, const DevSub& sd, Tables<T> t, const double
   __syncwarp();
 }
 
-// In-register Gauss-Jordan inversion of the padded A x A block.
+// Reciprocal of a pivot: FP32 uses the hardware approximation (<= 2 ulp), which the FP64
+// refinement absorbs; FP64 keeps the correctly rounded division.
+__device__ __forceinline__ float pivot_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double pivot_rcp(double x) { return 1.0 / x; }
+
+// In-register Gauss-Jordan inversion of the padded A x A block.  Pivot p:
+//   M[p][p] <- 1/M[p][p],  M[p][c] <- M[p][c]/M[p][p],  M[r][p] <- -M[r][p]/M[p][p],
+//   M[r][c] <- M[r][c] - M[r][p] M[p][c]/M[p][p]  otherwise.
+// Row p is held in slot p % NR of the lanes with h == p / NR, so only that slot needs the
+// pivot-row case; the pivot-column case is folded into a per-lane multiplier.
 template <typename T, int A>
 __device__ __forceinline__ void gj_invert(T (&v)[A * A / 32], int lane) {
   constexpr int NR = A * A / 32;
@@ -119,16 +128,15 @@ __device__ __forceinline__ void gj_invert(T (&v)[A * A / 32], int lane) {
   for (int p = 0; p < A; ++p) {
     const T rowv = __shfl_sync(0xffffffffu, v[p % NR], c + A * (p / NR));  // M[p][c]
     const T piv = __shfl_sync(0xffffffffu, rowv, p);                       // M[p][p]
-    const T ip = T(1) / piv;
-    T colv[NR];
-#pragma unroll
-    for (int q = 0; q < NR; ++q) colv[q] = __shfl_sync(0xffffffffu, v[q], p + A * h);  // M[r][p]
+    const T ip = pivot_rcp(piv);
+    const bool pc = c == p;
+    const T keep = pc ? T(0) : T(1);        // the pivot column is replaced, not updated
+    const T sc = pc ? ip : rowv * ip;       // M[p][c] / M[p][p], or 1/M[p][p] in the pivot column
 #pragma unroll
     for (int q = 0; q < NR; ++q) {
-      const int r = h * NR + q;
-      if (r == p) v[q] = (c == p) ? ip : rowv * ip;
-      else if (c == p) v[q] = -colv[q] * ip;
-      else v[q] = v[q] - colv[q] * (rowv * ip);
+      const T colv = __shfl_sync(0xffffffffu, v[q], p + A * h);  // M[r][p]
+      if (q == p % NR && h == p / NR) v[q] = sc;                  // pivot row
+      else v[q] = keep * v[q] - colv * sc;
     }
   }
 }

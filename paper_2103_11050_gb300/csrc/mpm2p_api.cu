@@ -176,7 +176,11 @@ double max_fprime(double M) {
   return 2.0 * M * s * (1.0 - s) / (den * den);
 }
 
-bool fp32(const mpm_ctx* c) { return c->prec == MPM_PREC_FP32_IR; }
+// Factor precision per kernel: the per-step Neumann downscaling factors in FP32 in both
+// mixed modes; the Robin factors (reused by every BF solve and MPM-2P step) only in
+// MPM_PREC_FP32_IR_ALL.
+bool fp32(const mpm_ctx* c) { return c->prec != MPM_PREC_FP64; }
+bool fp32_robin(const mpm_ctx* c) { return c->prec == MPM_PREC_FP32_IR_ALL; }
 
 cudaEvent_t take_event(mpm_ctx* c) {
   if (!c->ev_pool.empty()) {
@@ -306,8 +310,9 @@ int run_build(mpm_ctx* c) {
   const int nsub = (int)c->subs.size();
   prof_begin(c, MPM_STAGE_BASIS);
   launch_copy_kappa_m(g, d, st);
-  launch_robin_factor(g, d, c->d_subs, nsub, c->max_a, c->max_b, fp32(c), st);
-  launch_basis_solve(g, d, c->d_subs, nsub, c->max_a, c->max_b, c->max_dof, fp32(c), c->ir_tol, c->ir_max, st);
+  launch_robin_factor(g, d, c->d_subs, nsub, c->max_a, c->max_b, fp32_robin(c), st);
+  launch_basis_solve(g, d, c->d_subs, nsub, c->max_a, c->max_b, c->max_dof, fp32_robin(c), c->ir_tol, c->ir_max,
+                     st);
   if (c->n_dof > 0) launch_element_matrix(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, st);
   prof_end(c, MPM_STAGE_BASIS);
   if (c->n_dof > 0) {
@@ -327,7 +332,7 @@ int run_perturbation(mpm_ctx* c) {
   const int nsub = (int)c->subs.size();
   prof_begin(c, MPM_STAGE_PERTURB);
   launch_residual(g, c->d, c->stream);
-  launch_mpm_local(g, c->d, c->d_subs, nsub, c->max_a, c->max_b, c->fac_prec == MPM_PREC_FP32_IR, c->ir_tol,
+  launch_mpm_local(g, c->d, c->d_subs, nsub, c->max_a, c->max_b, c->fac_prec == MPM_PREC_FP32_IR_ALL, c->ir_tol,
                    c->ir_max, c->stream);
   prof_end(c, MPM_STAGE_PERTURB);
   return check_launch(c);
@@ -569,7 +574,8 @@ const char* mpm_last_error(const mpm_ctx* c) { return c ? c->err.c_str() : "null
 
 int mpm_set_precision(mpm_ctx* c, int mode, double ir_tol, int ir_max) {
   if (!c) return MPM_ERR_ARG;
-  if (mode != MPM_PREC_FP64 && mode != MPM_PREC_FP32_IR) return fail(c, MPM_ERR_ARG, "unknown precision mode %d", mode);
+  if (mode != MPM_PREC_FP64 && mode != MPM_PREC_FP32_IR && mode != MPM_PREC_FP32_IR_ALL)
+    return fail(c, MPM_ERR_ARG, "unknown precision mode %d", mode);
   if (!(ir_tol > 0) || ir_max < 1 || ir_max > 1000) return fail(c, MPM_ERR_ARG, "need ir_tol > 0 and 1 <= ir_max <= 1000");
   c->prec = mode;
   c->ir_tol = ir_tol;

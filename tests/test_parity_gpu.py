@@ -10,7 +10,7 @@ from tests.cases import case, rel
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-10, 1: 1e-8}
+TOL = {0: 1e-10, 1: 1e-8, 2: 1e-8}
 
 
 def _oracle_setup(c):
@@ -45,7 +45,7 @@ def _built():
     build.build()
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("name", ["p1_2x2", "uneven", "const_H", "exact_h", "single", "rate_in", "dirichlet4",
                                   "contrast64"])
 def test_mrcm_update_parity(name, prec):
@@ -69,7 +69,7 @@ def test_mrcm_update_parity(name, prec):
     assert bal <= max(4 * obal, 5e-13), (bal, obal)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("name", ["p1_2x2", "uneven", "rate_in", "dirichlet4", "contrast64"])
 def test_mpm_update_parity(name, prec):
     c = case(name)
@@ -119,7 +119,7 @@ def test_transport_parity():
 
 
 @pytest.mark.parametrize("graph", [True, False])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("name,eta,steps", [("p1_2x2", 0.02, 12), ("uneven", -1.0, 4), ("contrast64", 0.05, 8)])
 def test_algorithm1_parity(name, eta, steps, prec, graph):
     c = case(name, "zero")
@@ -184,8 +184,8 @@ def test_refinement_cap_reports_not_converged():
     # one refinement sweep cannot reach 1e-15 with an FP32 factor (nor its 1e3 x floor): the library must say so
     from paper_2103_11050_gb300 import binding as B
     c = case("contrast64")
-    ctx = _gpu(c, 1)
-    ctx.set_precision(1, 1e-15, 1)
+    ctx = _gpu(c, 2)
+    ctx.set_precision(2, 1e-15, 1)
     ctx.init(0.1)
     with pytest.raises(B.MPMError) as ei:
         ctx.sync()
