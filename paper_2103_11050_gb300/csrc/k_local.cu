@@ -17,9 +17,10 @@
 //   backward X_j = W_j + Q_j (t_j o X_{j+1})
 // In FP32 mode the factor is built from the Jacobi-scaled matrix S A S,
 // S = diag(A)^{-1/2}, and FP64 iterative refinement against the FP64 stencil recovers
-// FP64 accuracy.  Factorisations and single-RHS solves run one warp per subdomain
-// (k_local_warp.cuh); the multi-RHS basis solve runs one CTA per subdomain.  Factors are
-// stored padded as [b][A][A] (A = pad_width(max a)).
+// FP64 accuracy.  Factorisations and single-RHS solves run two warps per subdomain,
+// factoring from both ends (twisted, k_local_warp.cuh); the multi-RHS basis solve runs one
+// CTA per subdomain with the same twisted sweeps.  Factors are stored padded as
+// [b][A][A] (A = pad_width(max a)).
 #include "mpm2p_internal.cuh"
 #include "k_local_warp.cuh"
 
@@ -60,14 +61,16 @@ struct Stencil {
   double* sc;    // m   Jacobi scaling (1 in FP64 mode)
 };
 
-// Multi-RHS block solve  (S A S) X = Z  in place on Z ([m][ncol], column stride ncol),
-// W: workspace of the same shape.  Q: [b][A][A] factor and th[m] = scaled north
-// couplings (factor type), both in shared memory.
+// Multi-RHS twisted block solve  (S A S) X = Z  in place on Z ([m][ncol], column stride
+// ncol) with the factor of k_local_warp.cuh (top chain j < mid, bottom chain j > mid,
+// middle row mid = b/2).  W: workspace of the same shape.  Q: [b][A][A] factor and
+// th[m] = scaled north couplings (factor type), both in shared memory.
 template <typename T>
 __device__ void block_solve(const DevSub& sd, const T* th, const T* Q, int A, T* Z, T* W, int ncol) {
-  const int a = sd.a, b = sd.b;
+  const int a = sd.a, b = sd.b, mid = b / 2;
   const int nwork = a * ncol;
-  for (int j = 0; j < b; ++j) {
+  // W_j = Q_j (Z_j + th_{jp} o W_{jp}),  jp = previous row of the chain (-1: none)
+  auto fwd = [&](int j, int jp) {
     const T* Qj = Q + (long long)j * A * A;
     for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
       const int i = w / ncol, col = w - (w / ncol) * ncol;
@@ -75,32 +78,50 @@ __device__ void block_solve(const DevSub& sd, const T* th, const T* Q, int A, T*
       for (int k = 0; k < a; ++k) {
         const int ck = j * a + k;
         T zk = Z[ck * ncol + col];
-        if (j > 0) zk += th[ck - a] * W[(ck - a) * ncol + col];
+        if (jp >= 0) zk += th[min(j, jp) * a + k] * W[(jp * a + k) * ncol + col];
         acc += Qj[i * A + k] * zk;
       }
       W[(j * a + i) * ncol + col] = acc;
     }
     __syncthreads();
-  }
-  // backward: X_{b-1} = W_{b-1}; X_j = W_j + Q_j (t_j o X_{j+1}); X stored in Z
-  for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
-    const int i = w / ncol, col = w - (w / ncol) * ncol;
-    Z[((b - 1) * a + i) * ncol + col] = W[((b - 1) * a + i) * ncol + col];
-  }
-  __syncthreads();
-  for (int j = b - 2; j >= 0; --j) {
-    const T* Qj = Q + (long long)j * A * A;
+  };
+  for (int j = 0; j < mid; ++j) fwd(j, j - 1);
+  for (int j = b - 1; j > mid; --j) fwd(j, j + 1 < b ? j + 1 : -1);
+  // middle: X_mid = Q_mid (Z_mid + th_{mid-1} o W_{mid-1} + th_mid o W_{mid+1})
+  {
+    const T* Qm = Q + (long long)mid * A * A;
     for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
       const int i = w / ncol, col = w - (w / ncol) * ncol;
-      T acc = W[(j * a + i) * ncol + col];
+      T acc = T(0);
       for (int k = 0; k < a; ++k) {
-        const int ck = j * a + k;
-        acc += Qj[i * A + k] * (th[ck] * Z[(ck + a) * ncol + col]);
+        const int ck = mid * a + k;
+        T zk = Z[ck * ncol + col];
+        if (mid > 0) zk += th[ck - a] * W[(ck - a) * ncol + col];
+        if (mid < b - 1) zk += th[ck] * W[(ck + a) * ncol + col];
+        acc += Qm[i * A + k] * zk;
       }
-      Z[(j * a + i) * ncol + col] = acc;
+      W[(mid * a + i) * ncol + col] = acc;  // W_mid holds X_mid
     }
     __syncthreads();
   }
+  // backward: X_j = W_j + Q_j (th_{jc} o X_{jn}), jn = the row solved before
+  auto bwd = [&](int j, int jn) {
+    const T* Qj = Q + (long long)j * A * A;
+    for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
+      const int i = w / ncol, col = w - (w / ncol) * ncol;
+      T acc = T(0);
+      for (int k = 0; k < a; ++k) acc += Qj[i * A + k] * (th[min(j, jn) * a + k] * Z[(jn * a + k) * ncol + col]);
+      Z[(j * a + i) * ncol + col] = W[(j * a + i) * ncol + col] + acc;
+    }
+    __syncthreads();
+  };
+  for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
+    const int i = w / ncol, col = w - (w / ncol) * ncol;
+    Z[(mid * a + i) * ncol + col] = W[(mid * a + i) * ncol + col];
+  }
+  __syncthreads();
+  for (int j = mid - 1; j >= 0; --j) bwd(j, j + 1);
+  for (int j = mid + 1; j < b; ++j) bwd(j, j - 1);
 }
 
 // (A x)_c in flux form: sum over interior faces of T (x_c - x_nb) plus ex_c x_c, so that
@@ -235,11 +256,6 @@ __device__ Carve<T> carve(char* base, int a, int b, int A, int ncol) {
   return c;
 }
 
-int threads_for(int a) {
-  int t = a * a;
-  if (t < 256) t = 256;
-  return (t + 31) / 32 * 32;
-}
 
 // Load the stored Robin factor (padded) and FP64 stencil of kappa^m into shared memory (CTA).
 template <typename T>
@@ -441,41 +457,38 @@ __global__ void k_reconstruct(Grid g, DevState d, const DevSub* subs, const DevN
 // ---------------------------------------------------------------------------------------------
 // Warp-per-subdomain kernels (k_local_warp.cuh).  WPB warps per CTA, one subdomain each.
 
-__device__ __forceinline__ void load_kappa_warp(const Grid& g, const DevSub& sd, const double* kap, double* dst,
-                                                int lane) {
-  for (int c = lane; c < sd.a * sd.b; c += 32) {
+__device__ __forceinline__ void load_kappa_cta(const Grid& g, const DevSub& sd, const double* kap, double* dst) {
+  for (int c = threadIdx.x; c < sd.a * sd.b; c += blockDim.x) {
     const int jl = c / sd.a, il = c - jl * sd.a;
     dst[c] = kap[(long long)(sd.y0 + jl) * g.nx + sd.x0 + il];
   }
-  __syncwarp();
+  __syncthreads();
 }
 
 // Robin factorisation at kappa^n (rebuild realisations), stored for reuse by MPM-2P:
-// Q blocks [b][A][A] (factor type) and [ex, wE, wN, sc] (FP64).
+// twisted Q blocks [b][A][A] (factor type), [ex, wE, wN, sc] (FP64) and beta_hat per face.
 template <typename T, int A>
-__global__ void k_robin_factor_w(Grid g, DevState d, const DevSub* subs, int nsub, int wpb, size_t per_warp,
-                                 int scale) {
+__global__ void k_robin_factor_w(Grid g, DevState d, const DevSub* subs, int scale) {
   extern __shared__ __align__(16) char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sidx = blockIdx.x * wpb + warp;
+  const int sidx = blockIdx.x;
   const int r = blockIdx.y;
-  if (sidx >= nsub || d.rebuild[r] != 1) return;
+  if (d.rebuild[r] != 1) return;
   const DevSub sd = subs[sidx];
   const int m = sd.a * sd.b;
-  warp::Tables<T> t = warp::carve<T, A>(smem + warp * per_warp, m, sd.b);
-  load_kappa_warp(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap, lane);
-  warp::build<T, A>(g, sd, t, d.tx + (long long)r * g.nfx(), d.ty + (long long)r * g.nfy(), 0, scale != 0, lane);
+  warp::Tables<T> t = warp::carve<T, A>(smem, m, sd.b);
+  load_kappa_cta(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap);
+  warp::build<T, A>(g, sd, t, d.tx + (long long)r * g.nfx(), d.ty + (long long)r * g.nfy(), 0, scale != 0);
   T* Qg = reinterpret_cast<T*>(d.fac) + (long long)r * d.st_fac + sd.q_off;
-  warp::factor<T, A>(sd, t, Qg, lane);
+  warp::factor<T, A>(sd, t, Qg);
   double* tv = d.tvec + (long long)r * d.st_t + sd.t_off;
-  for (int c = lane; c < m; c += 32) {
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
     tv[c] = t.ex[c];
     tv[m + c] = t.wE[c];
     tv[2 * m + c] = t.wN[c];
     tv[3 * m + c] = t.sc[c];
   }
   double* bh = d.bhat + (long long)r * d.st_face + sd.face_off;
-  for (int f = lane; f < 2 * (sd.a + sd.b); f += 32) {
+  for (int f = threadIdx.x; f < 2 * (sd.a + sd.b); f += blockDim.x) {
     int side, tt, cl;
     face_info(sd, f, side, tt, cl);
     bh[f] = sd.side_kind[side] == 1 ? sd.side_rho[side] / t.kap[cl] : 0.0;
@@ -485,19 +498,18 @@ __global__ void k_robin_factor_w(Grid g, DevState d, const DevSub* subs, int nsu
 // MPM-2P local solve: A_i(kappa^m) dp = r_i with zero Robin data and homogeneous physical
 // data, using the stored factor.  Outputs the perturbation traces (fbar) and mean(dp).
 template <typename T, int A>
-__global__ void k_mpm_local_w(Grid g, DevState d, const DevSub* subs, int nsub, int wpb, size_t per_warp,
-                              int refine, double tol, int ir_max) {
+__global__ void k_mpm_local_w(Grid g, DevState d, const DevSub* subs, int refine, double tol, int ir_max) {
   extern __shared__ __align__(16) char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sidx = blockIdx.x * wpb + warp;
+  __shared__ double red[4];
+  const int sidx = blockIdx.x;
   const int r = blockIdx.y;
-  if (sidx >= nsub || d.rebuild[r] != 0) return;
+  if (d.rebuild[r] != 0) return;
   const DevSub sd = subs[sidx];
   const int a = sd.a, b = sd.b, m = a * b;
-  warp::Tables<T> t = warp::carve<T, A>(smem + warp * per_warp, m, b);
-  load_kappa_warp(g, sd, d.kap_m + (long long)r * g.ncell(), t.kap, lane);
+  warp::Tables<T> t = warp::carve<T, A>(smem, m, b);
+  load_kappa_cta(g, sd, d.kap_m + (long long)r * g.ncell(), t.kap);
   const double* tv = d.tvec + (long long)r * d.st_t + sd.t_off;
-  for (int c = lane; c < m; c += 32) {
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
     t.ex[c] = tv[c];
     t.wE[c] = tv[m + c];
     t.wN[c] = tv[2 * m + c];
@@ -505,17 +517,17 @@ __global__ void k_mpm_local_w(Grid g, DevState d, const DevSub* subs, int nsub, 
     const int jl = c / a, il = c - jl * a;
     t.B[c] = d.resid[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il];
   }
-  __syncwarp();
-  for (int e = lane; e < b * A; e += 32) {
+  __syncthreads();
+  for (int e = threadIdx.x; e < b * A; e += blockDim.x) {
     const int j = e / A, i = e - j * A;
     t.th[e] = (i < a && j < b - 1) ? T(t.wN[j * a + i] * t.sc[j * a + i] * t.sc[j * a + i + a]) : T(0);
   }
-  __syncwarp();
+  __syncthreads();
   const T* Qg = reinterpret_cast<const T*>(d.fac) + (long long)r * d.st_fac + sd.q_off;
-  warp::solve_refined<T, A>(sd, t, Qg, refine != 0, tol, ir_max, d.status, d.ir_iters, lane);
+  warp::solve_refined<T, A>(sd, t, Qg, refine != 0, tol, ir_max, d.status, d.ir_iters, red);
   double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
   const int nface = 2 * (a + b);
-  for (int f = lane; f < nface; f += 32) {
+  for (int f = threadIdx.x; f < nface; f += blockDim.x) {
     int side, tt, cl;
     face_info(sd, f, side, tt, cl);
     const double kc = t.kap[cl], pc = t.X[cl];
@@ -525,33 +537,31 @@ __global__ void k_mpm_local_w(Grid g, DevState d, const DevSub* subs, int nsub, 
     fbar[f] = v;
   }
   double s = 0.0;
-  for (int c = lane; c < m; c += 32) s += t.X[c];
-  s = warp::warp_sum(s);
-  if (lane == 0) d.sub_mean[(long long)r * d.st_sub + sidx] = s / m;
+  for (int c = threadIdx.x; c < m; c += blockDim.x) s += t.X[c];
+  s = warp::cta_sum(s, red);
+  if (threadIdx.x == 0) d.sub_mean[(long long)r * d.st_sub + sidx] = s / m;
 }
 
 // Downscaling (Eq. mpm_upd): Neumann problem with kappa^n and the fluxes u_bar already
 // written on the subdomain boundary faces of ux / uy; factor + solve + refinement; the
 // pressure constant makes mean(p~) equal the target; writes p~ and the interior fluxes.
 template <typename T, int A>
-__global__ void k_downscale_w(Grid g, DevState d, const DevSub* subs, int nsub, int wpb, size_t per_warp,
-                              size_t qoff, int refine, double tol, int ir_max) {
+__global__ void k_downscale_w(Grid g, DevState d, const DevSub* subs, size_t qoff, int refine, double tol,
+                              int ir_max) {
   extern __shared__ __align__(16) char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sidx = blockIdx.x * wpb + warp;
+  __shared__ double red[4];
+  const int sidx = blockIdx.x;
   const int r = blockIdx.y;
-  if (sidx >= nsub) return;
   const DevSub sd = subs[sidx];
   const int a = sd.a, b = sd.b, m = a * b, nx = g.nx;
-  char* base = smem + warp * per_warp;
-  warp::Tables<T> t = warp::carve<T, A>(base, m, b);
-  T* Q = reinterpret_cast<T*>(base + qoff);
-  load_kappa_warp(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap, lane);
-  warp::build<T, A>(g, sd, t, d.tx + (long long)r * g.nfx(), d.ty + (long long)r * g.nfy(), 1, refine != 0, lane);
-  warp::factor<T, A>(sd, t, Q, lane);
+  warp::Tables<T> t = warp::carve<T, A>(smem, m, b);
+  T* Q = reinterpret_cast<T*>(smem + qoff);
+  load_kappa_cta(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap);
+  warp::build<T, A>(g, sd, t, d.tx + (long long)r * g.nfx(), d.ty + (long long)r * g.nfy(), 1, refine != 0);
+  warp::factor<T, A>(sd, t, Q);
   const double* ux = d.ux + (long long)r * g.nfx();
   const double* uy = d.uy + (long long)r * g.nfy();
-  for (int c = lane; c < m; c += 32) {
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
     const int jl = c / a, il = c - jl * a;
     const int i = sd.x0 + il, j = sd.y0 + jl;
     double v = d.q[(long long)r * g.ncell() + (long long)j * nx + i] * g.h * g.h;
@@ -561,15 +571,15 @@ __global__ void k_downscale_w(Grid g, DevState d, const DevSub* subs, int nsub, 
     if (jl == b - 1) v -= uy[(long long)(j + 1) * nx + i];
     t.B[c] = v;
   }
-  __syncwarp();
-  warp::solve_refined<T, A>(sd, t, Q, refine != 0, tol, ir_max, d.status, d.ir_iters, lane);
+  __syncthreads();
+  warp::solve_refined<T, A>(sd, t, Q, refine != 0, tol, ir_max, d.status, d.ir_iters, red);
   double s = 0.0;
-  for (int c = lane; c < m; c += 32) s += t.X[c];
-  s = warp::warp_sum(s);
+  for (int c = threadIdx.x; c < m; c += blockDim.x) s += t.X[c];
+  s = warp::cta_sum(s, red);
   const double shift = d.sub_target[(long long)r * d.st_sub + sidx] - s / m;
   double* uxw = d.ux + (long long)r * g.nfx();
   double* uyw = d.uy + (long long)r * g.nfy();
-  for (int c = lane; c < m; c += 32) {
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
     const int jl = c / a, il = c - jl * a;
     const int i = sd.x0 + il, j = sd.y0 + jl;
     d.p_down[(long long)r * g.ncell() + (long long)j * nx + i] = t.X[c] + shift;
@@ -585,49 +595,43 @@ void set_smem(K kernel, size_t bytes) {
 
 size_t align16(size_t v) { return (v + 15) / 16 * 16; }
 
-// Warp launch geometry: per-warp bytes and warps per CTA.  One subdomain per CTA spreads the
-// subdomains over all SMs, whose FP64 pipes (refinement residuals) are the scarce unit.
+// Launch geometry of the two-warp kernels: one subdomain per CTA of 64 threads (spreads
+// the subdomains over all SMs); dynamic shared memory = tables (+ the factor for the
+// downscaling).
 template <typename T, int A>
-void warp_geometry(int max_a, int max_b, bool with_q, size_t& per_warp, size_t& qoff, int& wpb) {
+void pair_geometry(int max_a, int max_b, bool with_q, size_t& bytes, size_t& qoff) {
   const int m = max_a * max_b;
   qoff = align16(warp::table_bytes<T, A>(m, max_b));
-  per_warp = align16(qoff + (with_q ? (size_t)max_b * A * A * sizeof(T) : 0));
-  wpb = 1;
+  bytes = align16(qoff + (with_q ? (size_t)max_b * A * A * sizeof(T) : 0));
 }
 
 template <typename T, int A>
 void robin_factor_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
                     cudaStream_t st) {
-  size_t per, qoff;
-  int wpb;
-  warp_geometry<T, A>(max_a, max_b, false, per, qoff, wpb);
-  set_smem(k_robin_factor_w<T, A>, per * wpb);
-  k_robin_factor_w<T, A><<<dim3((nsub + wpb - 1) / wpb, g.R), 32 * wpb, per * wpb, st>>>(
-      g, d, subs, nsub, wpb, per, std::is_same<T, float>::value ? 1 : 0);
+  size_t bytes, qoff;
+  pair_geometry<T, A>(max_a, max_b, false, bytes, qoff);
+  set_smem(k_robin_factor_w<T, A>, bytes);
+  k_robin_factor_w<T, A><<<dim3(nsub, g.R), 64, bytes, st>>>(g, d, subs, std::is_same<T, float>::value ? 1 : 0);
   ++g_launches;
 }
 
 template <typename T, int A>
 void mpm_local_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b, int refine,
                  double tol, int ir_max, cudaStream_t st) {
-  size_t per, qoff;
-  int wpb;
-  warp_geometry<T, A>(max_a, max_b, false, per, qoff, wpb);
-  set_smem(k_mpm_local_w<T, A>, per * wpb);
-  k_mpm_local_w<T, A><<<dim3((nsub + wpb - 1) / wpb, g.R), 32 * wpb, per * wpb, st>>>(g, d, subs, nsub, wpb, per,
-                                                                                      refine, tol, ir_max);
+  size_t bytes, qoff;
+  pair_geometry<T, A>(max_a, max_b, false, bytes, qoff);
+  set_smem(k_mpm_local_w<T, A>, bytes);
+  k_mpm_local_w<T, A><<<dim3(nsub, g.R), 64, bytes, st>>>(g, d, subs, refine, tol, ir_max);
   ++g_launches;
 }
 
 template <typename T, int A>
 void downscale_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b, int refine,
                  double tol, int ir_max, cudaStream_t st) {
-  size_t per, qoff;
-  int wpb;
-  warp_geometry<T, A>(max_a, max_b, true, per, qoff, wpb);
-  set_smem(k_downscale_w<T, A>, per * wpb);
-  k_downscale_w<T, A><<<dim3((nsub + wpb - 1) / wpb, g.R), 32 * wpb, per * wpb, st>>>(
-      g, d, subs, nsub, wpb, per, qoff, refine, tol, ir_max);
+  size_t bytes, qoff;
+  pair_geometry<T, A>(max_a, max_b, true, bytes, qoff);
+  set_smem(k_downscale_w<T, A>, bytes);
+  k_downscale_w<T, A><<<dim3(nsub, g.R), 64, bytes, st>>>(g, d, subs, qoff, refine, tol, ir_max);
   ++g_launches;
 }
 

@@ -1,6 +1,6 @@
-// Warp-per-subdomain local solver for single right-hand sides (MPM-2P local solve and
-// downscaling).  Same block-tridiagonal LDL^T with explicit inverse pivots as the
-// CTA-wide path in k_local.cu, but one warp owns one subdomain:
+// Two-warp-per-subdomain local solver for single right-hand sides (Robin factorisation,
+// MPM-2P local solve and downscaling).  Block-tridiagonal LDL^T with explicit inverse
+// pivots, factored from both ends (twisted); each warp owns one chain:
 //   - the a x a pivot block S_j is held in registers, identity-padded to A x A
 //     (A in {8, 16, 32}): lane l holds column c = l % A, rows r = (l / A) * NR + q,
 //     q < NR = A*A/32;
@@ -8,7 +8,8 @@
 //     block barrier (an inverted padded block is [S^-1 0; 0 I]);
 //   - S_j = D_j - t_{j-1} o Q_{j-1} o t_{j-1} is formed in the registers that still hold
 //     Q_{j-1} (the couplings between grid rows are diagonal);
-//   - a solve is 2b dependent A x A products, each lane reducing its rows by shuffles.
+//   - a solve is ~b + 1 dependent A x A products per warp chain, each lane reducing its rows
+//     by shuffles.
 // All inner loops run in the factor type T; the scaled couplings are precomputed once.
 #pragma once
 #include "mpm2p_internal.cuh"
@@ -65,9 +66,10 @@ __device__ Tables<T> carve(char* base, int m, int b) {
 // and the scaled T tables.  kap must already hold the subdomain's kappa^n.
 template <typename T, int A>
 __device__ void build(const Grid& g, const DevSub& sd, Tables<T> t, const double* tx, const double* ty,
-                      int neumann, bool scale, int lane) {
+                      int neumann, bool scale) {
   const int a = sd.a, b = sd.b, m = a * b;
-  for (int c = lane; c < m; c += 32) {
+  const int lane = threadIdx.x;
+  for (int c = lane; c < m; c += blockDim.x) {
     const int jl = c / a, il = c - jl * a;
     const int i = sd.x0 + il, j = sd.y0 + jl;
     const double kc = t.kap[c];
@@ -84,8 +86,8 @@ __device__ void build(const Grid& g, const DevSub& sd, Tables<T> t, const double
     }
     t.ex[c] = dg;
   }
-  __syncwarp();
-  for (int c = lane; c < m; c += 32) {
+  __syncthreads();
+  for (int c = lane; c < m; c += blockDim.x) {
     const int jl = c / a, il = c - jl * a;
     double d = t.ex[c] + t.wE[c] + t.wN[c];
     if (il > 0) d += t.wE[c - 1];
@@ -93,8 +95,8 @@ __device__ void build(const Grid& g, const DevSub& sd, Tables<T> t, const double
     t.sc[c] = scale ? rsqrt(d) : 1.0;
     t.Rr[c] = d;  // full diagonal, consumed below
   }
-  __syncwarp();
-  for (int e = lane; e < b * A; e += 32) {
+  __syncthreads();
+  for (int e = lane; e < b * A; e += blockDim.x) {
     const int j = e / A, i = e - j * A;
     if (i < a) {
       const int c = j * a + i;
@@ -107,7 +109,7 @@ __device__ void build(const Grid& g, const DevSub& sd, Tables<T> t, const double
       t.th[e] = T(0);
     }
   }
-  __syncwarp();
+  __syncthreads();
 }
 
 // Reciprocal of a pivot: FP32 uses the hardware approximation (<= 2 ulp), which the FP64
@@ -141,21 +143,36 @@ __device__ __forceinline__ void gj_invert(T (&v)[A * A / 32], int lane) {
   }
 }
 
-// Factor: Q_j = S_j^-1 for j = 0..b-1, written to Q ([b][A][A], padded).
+// Twisted block factorisation with two warps (warp 0 from the top, warp 1 from the
+// bottom, meeting at block row mid = b/2):
+//   top     S_0 = D_0,        S_j = D_j - t_{j-1} o Q_{j-1} o t_{j-1},  j < mid
+//   bottom  S_{b-1} = D_{b-1}, S_j = D_j - t_j o Q_{j+1} o t_j,          j > mid
+//   middle  S_mid = D_mid - t_{mid-1} o Q_{mid-1} o t_{mid-1} - t_mid o Q_{mid+1} o t_mid
+// with Q_j = S_j^-1 written to Q ([b][A][A], padded).  The critical path is
+// max(mid, b-1-mid) + 1 inversions instead of b.  Requires blockDim.x == 64.
 template <typename T, int A>
-__device__ void factor(const DevSub& sd, Tables<T> t, T* Q, int lane) {
+__device__ void factor(const DevSub& sd, Tables<T> t, T* Q) {
   constexpr int NR = A * A / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = lane % A, h = lane / A;
+  const int b = sd.b, mid = b / 2;
   T v[NR];
 #pragma unroll
   for (int q = 0; q < NR; ++q) v[q] = T(0);
-  for (int j = 0; j < sd.b; ++j) {
-    const T tc = j > 0 ? t.th[(j - 1) * A + c] : T(0);
+  // D_j entry (r, c) of the scaled operator (identity padding)
+  auto dentry = [&](int j, int r) -> T {
+    return r == c ? t.dh[j * A + r] : (c == r + 1 ? t.eh[j * A + r] : (r == c + 1 ? t.eh[j * A + c] : T(0)));
+  };
+  const int nsteps = warp == 0 ? mid : b - 1 - mid;
+  for (int k = 0; k < nsteps; ++k) {
+    const int j = warp == 0 ? k : b - 1 - k;
+    const int jc = warp == 0 ? j - 1 : j;  // coupling row to the previous block (top: j-1, bottom: j)
+    const T tc = k > 0 ? t.th[jc * A + c] : T(0);
 #pragma unroll
     for (int q = 0; q < NR; ++q) {
       const int r = h * NR + q;
-      T s = r == c ? t.dh[j * A + r] : (c == r + 1 ? t.eh[j * A + r] : (r == c + 1 ? t.eh[j * A + c] : T(0)));
-      if (j > 0) s -= t.th[(j - 1) * A + r] * v[q] * tc;
+      T s = dentry(j, r);
+      if (k > 0) s -= t.th[jc * A + r] * v[q] * tc;
       v[q] = s;
     }
     gj_invert<T, A>(v, lane);
@@ -163,7 +180,25 @@ __device__ void factor(const DevSub& sd, Tables<T> t, T* Q, int lane) {
 #pragma unroll
     for (int q = 0; q < NR; ++q) Qj[(h * NR + q) * A + c] = v[q];
   }
-  __syncwarp();
+  __syncthreads();
+  if (warp == 0) {
+    const T* Qb = Q + (size_t)(mid + 1) * A * A;
+    const T ta = mid > 0 ? t.th[(mid - 1) * A + c] : T(0);
+    const T tb = mid < b - 1 ? t.th[mid * A + c] : T(0);
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      const int r = h * NR + q;
+      T s = dentry(mid, r);
+      if (mid > 0) s -= t.th[(mid - 1) * A + r] * v[q] * ta;
+      if (mid < b - 1) s -= t.th[mid * A + r] * Qb[r * A + c] * tb;
+      v[q] = s;
+    }
+    gj_invert<T, A>(v, lane);
+    T* Qm = Q + (size_t)mid * A * A;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) Qm[(h * NR + q) * A + c] = v[q];
+  }
+  __syncthreads();
 }
 
 // y[c] = sum_r Q[r][c] x[r] for the lane's column c (Q symmetric), x held as x[lane % A].
@@ -171,38 +206,56 @@ template <typename T, int A>
 __device__ __forceinline__ T matvec(const T* Qj, T x, int lane) {
   constexpr int NR = A * A / 32;
   const int c = lane % A, h = lane / A;
-  T acc = T(0);
+  T acc0 = T(0), acc1 = T(0);
 #pragma unroll
-  for (int q = 0; q < NR; ++q) {
+  for (int q = 0; q < NR; q += 2) {
     const int r = h * NR + q;
-    acc += Qj[r * A + c] * __shfl_sync(0xffffffffu, x, r);
+    acc0 += Qj[r * A + c] * __shfl_sync(0xffffffffu, x, r);
+    if (q + 1 < NR) acc1 += Qj[(r + 1) * A + c] * __shfl_sync(0xffffffffu, x, r + 1);
   }
+  T acc = acc0 + acc1;
 #pragma unroll
   for (int o = A; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   return acc;
 }
 
-// Solve (S A S) y = V in place (V, W: [b][A] padded, W workspace).
+// Twisted solve (S A S) y = V in place (V, W: [b][A] padded, W workspace), two warps:
+//   forward   W_j = Q_j (V_j + t_{j-1} o W_{j-1}) (top, j < mid),
+//             W_j = Q_j (V_j + t_j o W_{j+1})     (bottom, j > mid),
+//   middle    y_mid = Q_mid (V_mid + t_{mid-1} o W_{mid-1} + t_mid o W_{mid+1}),
+//   backward  y_j = W_j + Q_j (t_j o y_{j+1}) (top),  y_j = W_j + Q_j (t_{j-1} o y_{j-1}) (bottom).
 template <typename T, int A>
-__device__ void solve(const DevSub& sd, Tables<T> t, const T* Q, int lane) {
+__device__ void solve(const DevSub& sd, Tables<T> t, const T* Q) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = lane % A;
-  const int b = sd.b;
+  const int b = sd.b, mid = b / 2;
+  const int nsteps = warp == 0 ? mid : b - 1 - mid;
   T w = T(0);
-  for (int j = 0; j < b; ++j) {
+  for (int k = 0; k < nsteps; ++k) {
+    const int j = warp == 0 ? k : b - 1 - k;
+    const int jc = warp == 0 ? j - 1 : j;
     T u = t.V[j * A + c];
-    if (j > 0) u += t.th[(j - 1) * A + c] * w;
+    if (k > 0) u += t.th[jc * A + c] * w;
     w = matvec<T, A>(Q + (size_t)j * A * A, u, lane);
     if (lane < A) t.W[j * A + c] = w;
   }
-  __syncwarp();
-  T x = w;  // X_{b-1} = W_{b-1}
-  if (lane < A) t.V[(b - 1) * A + c] = x;
-  for (int j = b - 2; j >= 0; --j) {
-    const T u = t.th[j * A + c] * x;
-    x = t.W[j * A + c] + matvec<T, A>(Q + (size_t)j * A * A, u, lane);
+  __syncthreads();
+  if (warp == 0) {
+    T u = t.V[mid * A + c];
+    if (mid > 0) u += t.th[(mid - 1) * A + c] * t.W[(mid - 1) * A + c];
+    if (mid < b - 1) u += t.th[mid * A + c] * t.W[(mid + 1) * A + c];
+    const T x = matvec<T, A>(Q + (size_t)mid * A * A, u, lane);
+    if (lane < A) t.V[mid * A + c] = x;
+  }
+  __syncthreads();
+  T x = t.V[mid * A + c];
+  for (int k = 0; k < nsteps; ++k) {
+    const int j = warp == 0 ? mid - 1 - k : mid + 1 + k;
+    const int jc = warp == 0 ? j : j - 1;  // coupling to the row solved before
+    x = t.W[j * A + c] + matvec<T, A>(Q + (size_t)j * A * A, t.th[jc * A + c] * x, lane);
     if (lane < A) t.V[j * A + c] = x;
   }
-  __syncwarp();
+  __syncthreads();
 }
 
 __device__ __forceinline__ double warp_max(double v) {
@@ -215,6 +268,25 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Sum / max over the 64 threads of the CTA (red: 4 doubles of shared memory).
+__device__ __forceinline__ double cta_sum(double v, double* red) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  const double r = red[0] + red[1];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double cta_max(double v, double* red) {
+  v = warp_max(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  const double r = fmax(red[0], red[1]);
+  __syncthreads();
+  return r;
 }
 
 // (A x)_c in flux form (see k_local.cu) and the cell's flux scale.
@@ -232,56 +304,56 @@ __device__ __forceinline__ double apply_A(const DevSub& sd, const double* ex, co
   return (t0 + t1) + (t2 + t3) + t4;
 }
 
-// Refined solve of A x = B (FP64, t.B) into t.X; same stopping rule as the CTA path
-// with target = tol.
+// Refined solve of A x = B (FP64, t.B) into t.X; same stopping rule as the CTA path with
+// target = tol.  All 64 threads; red: 4 doubles of shared memory.
 template <typename T, int A>
 __device__ void solve_refined(const DevSub& sd, Tables<T> t, const T* Q, bool refine, double tol, int ir_max,
-                              int* status, int* ir_used, int lane) {
+                              int* status, int* ir_used, double* red) {
   const double target = tol;
   const int a = sd.a, b = sd.b, m = a * b;
-  for (int c = lane; c < m; c += 32) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int c = tid; c < m; c += nt) {
     t.X[c] = 0.0;
     t.Rr[c] = t.B[c];
   }
-  __syncwarp();
+  __syncthreads();
   const int sweeps = refine ? ir_max : 1;
   int it = 0;
   bool ok = false;
   double eta_prev = 1e300;
   for (; it < sweeps; ++it) {
-    for (int e = lane; e < b * A; e += 32) {
+    for (int e = tid; e < b * A; e += nt) {
       const int j = e / A, i = e - j * A;
       t.V[e] = i < a ? T(t.Rr[j * a + i] * t.sc[j * a + i]) : T(0);
     }
-    __syncwarp();
-    solve<T, A>(sd, t, Q, lane);
-    for (int c = lane; c < m; c += 32) {
+    __syncthreads();
+    solve<T, A>(sd, t, Q);
+    for (int c = tid; c < m; c += nt) {
       const int j = c / a, i = c - j * a;
       t.X[c] += double(t.V[j * A + i]) * t.sc[c];
     }
-    __syncwarp();
+    __syncthreads();
     if (!refine) { it = 1; ok = true; break; }
     double rmax = 0.0, smax = 0.0;
-    for (int c = lane; c < m; c += 32) {
+    for (int c = tid; c < m; c += nt) {
       double absx;
       const double r = t.B[c] - apply_A(sd, t.ex, t.wE, t.wN, t.X, c, absx);
       t.Rr[c] = r;
       rmax = fmax(rmax, fabs(r));
       smax = fmax(smax, absx + fabs(t.B[c]));
     }
-    rmax = warp_max(rmax);
-    smax = warp_max(smax);
-    __syncwarp();
+    rmax = cta_max(rmax, red);
+    smax = cta_max(smax, red);
     const double eta = smax > 0.0 ? rmax / smax : 0.0;
     if (eta <= target) { ok = true; ++it; break; }
     if (eta > 0.5 * eta_prev && eta <= 1e3 * tol) { ok = true; ++it; break; }  // FP64 floor reached
     eta_prev = eta;
   }
-  if (lane == 0) {
+  if (tid == 0) {
     if (!ok) atomicOr(status, 1);
     atomicMax(ir_used, it);
   }
-  __syncwarp();
+  __syncthreads();
 }
 
 }  // namespace warp
