@@ -156,7 +156,7 @@ def run_gpu(args, w):
 
     def one_run(prec, steps, warmup, profile):
         ctx = setup_ctx(B, w, K, s0, prec, stream.cuda_stream)
-        ctx.set_graph(not profile)  # the stage profiler times the eager launch sequence
+        ctx.set_execution(graph=not profile)  # the stage profiler times the eager launch sequence
         ctx.init(eta)
         for _ in range(warmup):
             ctx.step(eta, CFL, N_SUB)

@@ -206,10 +206,19 @@ int mpm_init(mpm_ctx* ctx, double eta);
  * precision or the decomposition change. */
 int mpm_step(mpm_ctx* ctx, double eta, double cfl, int n_sub);
 
-/* enable = 0 runs mpm_step eagerly (kernel by kernel; the host reads the decision to skip
- * the branch no realisation takes; used by the stage profiler); 1 (default) uses the
- * captured graph. */
-int mpm_set_graph(mpm_ctx* ctx, int enable);
+/* Execution of the path (bitmask, default MPM_EXEC_GRAPH | MPM_EXEC_PERSISTENT):
+ *  MPM_EXEC_GRAPH       mpm_step is one captured CUDA graph launch with device-side
+ *                       branching; without it mpm_step runs kernel by kernel and the host
+ *                       reads the decision to skip the branch no realisation takes (the
+ *                       stage profiler requires this).
+ *  MPM_EXEC_PERSISTENT  the interface-solve stage (element right-hand sides, every
+ *                       nested-dissection level up and down, reconstruction, u_bar) is one
+ *                       persistent cooperative kernel with grid-wide barriers between levels;
+ *                       without it, one kernel per level (also the automatic fallback when
+ *                       the device cannot launch cooperatively).
+ * Results are identical up to rounding order.  Drops a captured graph. */
+enum { MPM_EXEC_GRAPH = 1, MPM_EXEC_PERSISTENT = 2 };
+int mpm_set_execution(mpm_ctx* ctx, int flags);
 
 /* Copy out pressure [R][ny][nx] (which = MPM_P_*), fluxes ux [R][ny][nx+1],
  * uy [R][ny+1][nx], saturation [R][ny][nx] or conductivity kappa^n.  Synchronise. */

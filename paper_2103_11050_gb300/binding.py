@@ -19,6 +19,7 @@ MEM_HOST, MEM_DEVICE = 0, 1
 BC_DIRICHLET, BC_NEUMANN = 0, 1
 PREC_FP64, PREC_FP32_IR, PREC_FP32_IR_ALL = 0, 1, 2
 P_MRCM, P_DOWNSCALED = 0, 1
+EXEC_GRAPH, EXEC_PERSISTENT = 1, 2
 
 FUNCTIONS = [
     "mpm_create", "mpm_destroy", "mpm_last_error", "mpm_set_precision", "mpm_set_permeability",
@@ -27,7 +28,7 @@ FUNCTIONS = [
     "mpm_perturbation_solve", "mpm_interface_solve", "mpm_downscale", "mpm_saturation_step",
     "mpm_init", "mpm_step", "mpm_get_pressure", "mpm_get_flux", "mpm_get_saturation",
     "mpm_get_conductivity", "mpm_get_stats", "mpm_sync", "mpm_profile_enable", "mpm_profile_read",
-    "mpm_set_graph", "mpm_cfl_dt_noalloc",
+    "mpm_set_execution", "mpm_cfl_dt_noalloc",
 ]
 
 STAGES = ["transport", "epsilon", "basis", "iface_factor", "perturb", "iface_solve", "downscale"]
@@ -92,7 +93,7 @@ def load(path: str | None = None):
         "mpm_get_stats": ([P, ctypes.POINTER(Stats)], I),
         "mpm_sync": ([P], I),
         "mpm_profile_enable": ([P, I], I),
-        "mpm_set_graph": ([P, I], I),
+        "mpm_set_execution": ([P, I], I),
         "mpm_cfl_dt_noalloc": ([P, P, I, I, I, D, D, D, P, P], I),
         "mpm_profile_read": ([P, DP, ctypes.POINTER(ctypes.c_longlong)], I),
     }
@@ -267,8 +268,8 @@ class Context:
     def get_conductivity(self, out=None):
         return self._get(self.L.mpm_get_conductivity, (self.R, self.ny, self.nx), out)
 
-    def set_graph(self, on=True):
-        self._ck(self.L.mpm_set_graph(self.h, 1 if on else 0))
+    def set_execution(self, graph=True, persistent=True):
+        self._ck(self.L.mpm_set_execution(self.h, (EXEC_GRAPH if graph else 0) | (EXEC_PERSISTENT if persistent else 0)))
 
     def profile_enable(self, on=True):
         self._ck(self.L.mpm_profile_enable(self.h, 1 if on else 0))

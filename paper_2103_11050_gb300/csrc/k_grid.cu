@@ -180,62 +180,6 @@ __global__ void k_residual(Grid g, DevState d) {
   }
 }
 
-// u_bar on every subdomain-boundary face, written into ux / uy.  One thread per face of
-// the sides a subdomain owns: its physical sides and its right / top interface sides.
-// branch = 1: after a basis build (mean of the MRCM traces); branch = 0: after a
-// perturbation solve (mean of the epsilon^0 traces plus F_n(p^m)).
-__global__ void k_ubar(Grid g, DevState d, const DevSub* subs, int branch) {
-  const int r = blockIdx.y;
-  if (d.rebuild[r] != branch) return;
-  const int add_fn = branch == 0;
-  const int sidx = blockIdx.x;
-  const DevSub sd = subs[sidx];
-  const int nx = g.nx;
-  const long long cb = (long long)r * g.ncell();
-  const int nface = 2 * (sd.a + sd.b);
-  for (int f = threadIdx.x; f < nface; f += blockDim.x) {
-    int side, t;
-    if (f < sd.b) { side = 0; t = f; }
-    else if (f < 2 * sd.b) { side = 1; t = f - sd.b; }
-    else if (f < 2 * sd.b + sd.a) { side = 2; t = f - 2 * sd.b; }
-    else { side = 3; t = f - 2 * sd.b - sd.a; }
-    const bool iface = sd.side_kind[side] == 1;
-    if (iface && (side == 0 || side == 2)) continue;  // written by the neighbour
-    int ci, cj;  // cell of this subdomain adjacent to the face
-    if (side == 0) { ci = sd.x0; cj = sd.y0 + t; }
-    else if (side == 1) { ci = sd.x0 + sd.a - 1; cj = sd.y0 + t; }
-    else if (side == 2) { ci = sd.x0 + t; cj = sd.y0; }
-    else { ci = sd.x0 + t; cj = sd.y0 + sd.b - 1; }
-    const long long c = (long long)cj * nx + ci;
-    const double Fout = d.trace[(long long)r * d.st_face + sd.face_off + f];
-    double val;  // in +x / +y direction
-    if (iface) {
-      const DevSub nb = subs[sd.side_nbr[side]];
-      const int nf_nb = side == 1 ? face_side_off(0, nb.a, nb.b) + t : face_side_off(2, nb.a, nb.b) + t;
-      const double Fnb = d.trace[(long long)r * d.st_face + nb.face_off + nf_nb];
-      val = 0.5 * (Fout - Fnb);
-      if (add_fn) {
-        const long long cn = side == 1 ? c + 1 : c + nx;
-        const double T = side == 1 ? d.tx[(long long)r * g.nfx() + (long long)cj * (nx + 1) + ci + 1]
-                                   : d.ty[(long long)r * g.nfy() + (long long)(cj + 1) * nx + ci];
-        val += T * (d.p_m[cb + c] - d.p_m[cb + cn]);
-      }
-    } else {
-      double out = Fout;
-      if (add_fn) {
-        // the perturbation traces carry homogeneous physical data; add F_n(p^m)
-        out += g.bc_type[side] == 0 ? 2.0 * d.kap_n[cb + c] * (d.p_m[cb + c] - g.bc_val[side])
-                                    : g.bc_val[side] * g.h;
-      }
-      val = (side == 0 || side == 2) ? -out : out;
-    }
-    if (side == 0) d.ux[(long long)r * g.nfx() + (long long)cj * (nx + 1) + ci] = val;
-    else if (side == 1) d.ux[(long long)r * g.nfx() + (long long)cj * (nx + 1) + ci + 1] = val;
-    else if (side == 2) d.uy[(long long)r * g.nfy() + (long long)cj * nx + ci] = val;
-    else d.uy[(long long)r * g.nfy() + (long long)(cj + 1) * nx + ci] = val;
-  }
-}
-
 // max over cells of max(total outflow, total inflow) -> dt per realisation.
 __global__ void k_cfl_part(Grid g, DevState d) {
   __shared__ double sh[32];
@@ -340,12 +284,6 @@ void launch_copy_kappa_m(const Grid& g, const DevState& d, cudaStream_t st) {
 
 void launch_residual(const Grid& g, const DevState& d, cudaStream_t st) {
   k_residual<<<dim3(cell_blocks(g), g.R), kThreads, 0, st>>>(g, d);
-  ++g_launches;
-}
-
-void launch_ubar(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int branch,
-                 cudaStream_t st) {
-  k_ubar<<<dim3(nsub, g.R), 128, 0, st>>>(g, d, subs, branch);
   ++g_launches;
 }
 

@@ -22,6 +22,9 @@
 // side exists), so the sweep needs no pivoting.
 // Solve: upward  y_s = F_ss^-1 g_s, g_b += (-F_bs F_ss^-1) g_s  (g_b -> parent);
 //        downward x_s = y_s - (F_ss^-1 F_sb) x_b  (x_b from the parent).
+#include <cooperative_groups.h>
+
+#include "k_iface_phases.cuh"
 #include "mpm2p_internal.cuh"
 
 namespace mpm {
@@ -30,29 +33,8 @@ namespace {
 
 constexpr int kTile = 32;
 
-__device__ __forceinline__ double side_basis(int kk, int t, int seg_len, int degree) {
-  const int nb = degree + 1;
-  const int seg = kk / nb, pw = kk - seg * nb;
-  if (t / seg_len != seg) return 0.0;
-  if (pw == 0) return 1.0;
-  const double xi = ((t % seg_len) + 0.5) / seg_len;
-  return 2.0 * xi - 1.0;
-}
-
-// Side, kind (0 = U, 1 = P) and index within the side's space of local DOF k.
-__device__ __forceinline__ bool dof_info(const DevSub& sd, int k, int& side, int& isP, int& kk) {
-  for (int q = 0; q < 4; ++q) {
-    if (sd.side_kind[q] != 1) continue;
-    const int d0 = sd.side_dof0[q], nb = sd.side_nb[q];
-    if (k >= d0 && k < d0 + 2 * nb) {
-      side = q;
-      isP = k >= d0 + nb;
-      kk = isP ? k - d0 - nb : k - d0;
-      return true;
-    }
-  }
-  return false;
-}
+using phase::dof_info;
+using phase::side_basis;
 
 __device__ __forceinline__ int side_len(const DevSub& sd, int side) { return side < 2 ? sd.b : sd.a; }
 
@@ -94,35 +76,15 @@ __global__ void k_element_matrix(Grid g, DevState d, const DevSub* subs, const D
   }
 }
 
-// Element right-hand side from the non-homogeneous (rebuild) or perturbation (MPM-2P)
-// traces fbar, moved to the right-hand side: psi rows -sum psi F, phi rows +sum bh s phi F.
+// Element right-hand side of every subdomain (see phase::element_rhs).
 __global__ void k_element_rhs(Grid g, DevState d, const DevSub* subs, const DevNode* nodes,
                               const int* leaf_node) {
   const int r = blockIdx.y;
   const int sidx = blockIdx.x;
   const DevSub sd = subs[sidx];
-  const int nd = sd.ndof;
-  if (nd == 0) return;
+  if (sd.ndof == 0) return;
   const DevNode leaf = nodes[leaf_node[sidx]];
-  double* gv = d.gvec + (long long)r * d.st_vec + leaf.v_off;
-  const double* fb = d.fbar + (long long)r * d.st_face + sd.face_off;
-  const double* bhat = d.bhat + (long long)r * d.st_face + sd.face_off;
-  for (int k = threadIdx.x; k < nd; k += blockDim.x) {
-    int side, isP, kk;
-    dof_info(sd, k, side, isP, kk);
-    const int L = side_len(sd, side);
-    const int f0 = face_side_off(side, sd.a, sd.b);
-    const double s = sd.side_sign[side];
-    double v = 0.0;
-    for (int t = 0; t < L; ++t) {
-      const double w = side_basis(kk, t, g.seg_len, g.degree);
-      if (w == 0.0) continue;
-      const double F = fb[f0 + t];
-      if (isP) v -= w * F;
-      else v += bhat[f0 + t] * s * w * F;
-    }
-    gv[k] = v;
-  }
+  for (int k = threadIdx.x; k < sd.ndof; k += blockDim.x) phase::element_rhs(g, d, sd, leaf, r, k);
 }
 
 // Frontal matrix of an internal node: extend-add of the children's Schur complements.
@@ -265,86 +227,159 @@ __global__ void k_sweep_trailing(Grid g, DevState d, const DevNode* nodes, const
   }
 }
 
-constexpr int kRowsPerCta = 8;  // frontal rows per CTA of the solve kernels (one row per warp)
+constexpr int kRowsPerCta = 8;  // frontal rows per CTA of the per-level solve kernels (one row per warp)
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Upward solve at one level: gather g from the children, y_s = M_ss g_s -> x, g_b += M_bs g_s.
-// One warp per frontal row (lane-strided dot product, shuffle reduction).
+// Upward solve at one level (see phase::nd_up_row).
 __global__ void k_nd_up(Grid g, DevState d, const DevNode* nodes, const int* level_nodes, const int* srcmap) {
-  extern __shared__ double gs[];
   const int r = blockIdx.z;
   const DevNode nd = nodes[level_nodes[blockIdx.x]];
-  const int nf = nd.nf, ns = nd.nsep;
-  const int row0 = blockIdx.y * kRowsPerCta;
-  if (row0 >= nf) return;
-  const int* s0 = srcmap + nd.src_off;
-  const int* s1 = s0 + nf;
-  const DevNode c0 = nodes[nd.child[0]], c1 = nodes[nd.child[1]];
-  const double* g0 = d.gvec + (long long)r * d.st_vec + c0.v_off;
-  const double* g1 = d.gvec + (long long)r * d.st_vec + c1.v_off;
-  for (int k = threadIdx.x; k < ns; k += blockDim.x) {
-    double v = 0.0;
-    if (s0[k] >= 0) v += g0[c0.nsep + s0[k]];
-    if (s1[k] >= 0) v += g1[c1.nsep + s1[k]];
-    gs[k] = v;
-  }
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const double* F = d.front + (long long)r * d.st_front + nd.f_off;
-  for (int row = row0 + warp; row < min(nf, row0 + kRowsPerCta); row += nw) {
-    const double* Fr = F + (long long)row * nf;
-    double acc = 0.0;
-    for (int k = lane; k < ns; k += 32) acc += Fr[k] * gs[k];
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      if (row < ns) {
-        d.xvec[(long long)r * d.st_vec + nd.v_off + row] = acc;
-      } else {
-        double v = 0.0;
-        if (s0[row] >= 0) v += g0[c0.nsep + s0[row]];
-        if (s1[row] >= 0) v += g1[c1.nsep + s1[row]];
-        d.gvec[(long long)r * d.st_vec + nd.v_off + row] = v + acc;
+  const int row0 = blockIdx.y * kRowsPerCta;
+  for (int row = row0 + warp; row < min(nd.nf, row0 + kRowsPerCta); row += nw)
+    phase::nd_up_row(d, nodes, nd, r, row, srcmap, lane);
+}
+
+// Downward solve at one level (see phase::nd_down_row / nd_down_copy).
+__global__ void k_nd_down(Grid g, DevState d, const DevNode* nodes, const int* level_nodes, const int* pmap) {
+  const int r = blockIdx.z;
+  const DevNode nd = nodes[level_nodes[blockIdx.x]];
+  if (nd.parent < 0) return;
+  if (blockIdx.y == 0)
+    for (int k = threadIdx.x; k < nd.nbnd; k += blockDim.x) phase::nd_down_copy(d, nodes, nd, r, pmap, k);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int row0 = blockIdx.y * kRowsPerCta;
+  for (int row = row0 + warp; row < min(nd.nsep, row0 + kRowsPerCta); row += nw)
+    phase::nd_down_row(d, nodes, nd, r, row, pmap, lane);
+}
+
+// Reconstruction of traces / p^m for the realisations of one branch (phase::reconstruct).
+__global__ void k_reconstruct(Grid g, DevState d, const DevSub* subs, const DevNode* nodes, const int* leaf_node,
+                              int branch) {
+  __shared__ double cs[4 * 4 * kMaxSide];
+  __shared__ double red[32];
+  const int r = blockIdx.y;
+  if (d.rebuild[r] != branch) return;
+  phase::reconstruct(g, d, subs, nodes, leaf_node, blockIdx.x, r, branch, cs, red);
+}
+
+// Interface / boundary fluxes u_bar for the realisations of one branch (phase::ubar).
+__global__ void k_ubar(Grid g, DevState d, const DevSub* subs, int branch) {
+  const int r = blockIdx.y;
+  if (d.rebuild[r] != branch) return;
+  phase::ubar(g, d, subs, blockIdx.x, r, branch);
+}
+
+// The whole interface-solve stage in one persistent cooperative launch: element
+// right-hand sides, the upward sweep level by level, the downward sweep level by level,
+// reconstruction and u_bar, with a grid-wide barrier between dependent phases.  Every
+// block reaches every barrier (no early return).  Items are grid-strided; per-level rows
+// are one warp each.
+__global__ void __launch_bounds__(256) k_iface_coop(Grid g, DevState d, const DevSub* subs, int nsub, int max_dof,
+                                                    const DevNode* nodes, const int* leaf_node,
+                                                    const int* level_nodes, const DevLevel* lev, int nlev,
+                                                    const int* srcmap, const int* pmap) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double cs[4 * 4 * kMaxSide];
+  __shared__ double red[32];
+  const long long nthreads = (long long)gridDim.x * blockDim.x;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nwarps = nthreads >> 5, wid = tid >> 5;
+  const int lane = threadIdx.x & 31;
+  if (max_dof > 0) {
+    const long long items = (long long)g.R * nsub * max_dof;
+    for (long long it = tid; it < items; it += nthreads) {
+      const int k = (int)(it % max_dof);
+      const long long rs = it / max_dof;
+      const int sidx = (int)(rs % nsub), r = (int)(rs / nsub);
+      const DevSub& sd = subs[sidx];
+      if (k < sd.ndof) phase::element_rhs(g, d, sd, nodes[leaf_node[sidx]], r, k);
+    }
+    grid.sync();
+    for (int L = 1; L < nlev; ++L) {
+      const DevLevel lv = lev[L];
+      const long long rows = (long long)g.R * lv.cnt * lv.max_nf;
+      for (long long it = wid; it < rows; it += nwarps) {
+        const int row = (int)(it % lv.max_nf);
+        const long long rn = it / lv.max_nf;
+        const int ni = (int)(rn % lv.cnt), r = (int)(rn / lv.cnt);
+        const DevNode& nd = nodes[level_nodes[lv.off + ni]];
+        if (row < nd.nf) phase::nd_up_row(d, nodes, nd, r, row, srcmap, lane);
       }
+      grid.sync();
+    }
+    for (int L = nlev - 1; L >= 0; --L) {
+      const DevLevel lv = lev[L];
+      const long long rows = (long long)g.R * lv.cnt * lv.max_ns;
+      for (long long it = wid; it < rows; it += nwarps) {
+        const int row = (int)(it % lv.max_ns);
+        const long long rn = it / lv.max_ns;
+        const int ni = (int)(rn % lv.cnt), r = (int)(rn / lv.cnt);
+        const DevNode& nd = nodes[level_nodes[lv.off + ni]];
+        if (nd.parent >= 0 && row < nd.nsep) phase::nd_down_row(d, nodes, nd, r, row, pmap, lane);
+      }
+      const long long cps = (long long)g.R * lv.cnt * lv.max_nb;
+      for (long long it = tid; it < cps; it += nthreads) {
+        const int k = (int)(it % lv.max_nb);
+        const long long rn = it / lv.max_nb;
+        const int ni = (int)(rn % lv.cnt), r = (int)(rn / lv.cnt);
+        const DevNode& nd = nodes[level_nodes[lv.off + ni]];
+        if (nd.parent >= 0 && k < nd.nbnd) phase::nd_down_copy(d, nodes, nd, r, pmap, k);
+      }
+      grid.sync();
     }
   }
-}
-
-// Downward solve at one level: x_b from the parent, x_s = y_s - M_sb x_b (one warp per row).
-__global__ void k_nd_down(Grid g, DevState d, const DevNode* nodes, const int* level_nodes, const int* pmap) {
-  extern __shared__ double xb[];
-  const int r = blockIdx.z;
-  const DevNode nd = nodes[level_nodes[blockIdx.x]];
-  const int nf = nd.nf, ns = nd.nsep, nbd = nd.nbnd;
-  if (nd.parent < 0) return;
-  const int row0 = blockIdx.y * kRowsPerCta;
-  if (row0 > 0 && row0 >= ns) return;
-  double* x = d.xvec + (long long)r * d.st_vec + nd.v_off;
-  const DevNode pa = nodes[nd.parent];
-  const double* xp = d.xvec + (long long)r * d.st_vec + pa.v_off;
-  const int* pm = pmap + nd.pmap_off;
-  for (int k = threadIdx.x; k < nbd; k += blockDim.x) {
-    const double v = xp[pm[k]];
-    xb[k] = v;
-    if (blockIdx.y == 0) x[ns + k] = v;
+  for (long long it = blockIdx.x; it < (long long)g.R * nsub; it += gridDim.x) {
+    const int sidx = (int)(it % nsub), r = (int)(it / nsub);
+    phase::reconstruct(g, d, subs, nodes, leaf_node, sidx, r, d.rebuild[r], cs, red);
   }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const double* F = d.front + (long long)r * d.st_front + nd.f_off;
-  for (int row = row0 + warp; row < min(ns, row0 + kRowsPerCta); row += nw) {
-    const double* Fr = F + (long long)row * nf + ns;
-    double acc = 0.0;
-    for (int k = lane; k < nbd; k += 32) acc += Fr[k] * xb[k];
-    acc = warp_sum(acc);
-    if (lane == 0) x[row] -= acc;
+  grid.sync();
+  for (long long it = blockIdx.x; it < (long long)g.R * nsub; it += gridDim.x) {
+    const int sidx = (int)(it % nsub), r = (int)(it / nsub);
+    phase::ubar(g, d, subs, sidx, r, d.rebuild[r]);
   }
 }
 
 }  // namespace
+
+void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub, const DevNode* nodes,
+                        const int* leaf_node, int branch, cudaStream_t st) {
+  k_reconstruct<<<dim3(nsub, g.R), 128, 0, st>>>(g, d, subs, nodes, leaf_node, branch);
+  ++g_launches;
+}
+
+void launch_ubar(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int branch, cudaStream_t st) {
+  k_ubar<<<dim3(nsub, g.R), 128, 0, st>>>(g, d, subs, branch);
+  ++g_launches;
+}
+
+int iface_coop_blocks() {
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iface_coop, 256, 0) != cudaSuccess) return 0;
+  return sms * (per_sm < 2 ? per_sm : 2);
+}
+
+cudaError_t launch_iface_coop(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_dof,
+                              const DevNode* nodes, const int* leaf_node, const int* level_nodes,
+                              const DevLevel* lev, int nlev, const int* srcmap, const int* pmap, int blocks,
+                              cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ++g_launches;
+  return cudaLaunchKernelEx(&cfg, k_iface_coop, g, d, subs, nsub, max_dof, nodes, leaf_node, level_nodes, lev,
+                            nlev, srcmap, pmap);
+}
 
 void launch_element_matrix(const Grid& g, const DevState& d, const DevSub* subs, int nsub, const DevNode* nodes,
                            const int* leaf_node, cudaStream_t st) {

@@ -396,64 +396,6 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
   }
 }
 
-// Traces (and at a rebuild the MRCM-level pressure p^m) from the interface solution:
-//   rebuild: p^m = pbar + P_hat c, F = Fbar + F_hat c, target mean = mean(p^m)
-//   MPM-2P : F = dFbar + F_hat dc, target mean = mean(p^m) + mean(dpbar) + mu_hat . dc
-__global__ void k_reconstruct(Grid g, DevState d, const DevSub* subs, const DevNode* nodes,
-                              const int* leaf_node, int branch) {
-  __shared__ double cs[4 * kMaxSide * 4];
-  __shared__ double red[32];
-  const int r = blockIdx.y;
-  if (d.rebuild[r] != branch) return;
-  const int sidx = blockIdx.x;
-  const DevSub sd = subs[sidx];
-  const int a = sd.a, b = sd.b, m = a * b, nd = sd.ndof;
-  const int nface = 2 * (a + b);
-  if (nd > 0) {
-    const DevNode nd_leaf = nodes[leaf_node[sidx]];
-    const double* x = d.xvec + (long long)r * d.st_vec + nd_leaf.v_off;
-    for (int l = threadIdx.x; l < nd; l += blockDim.x) cs[l] = x[l];
-  }
-  __syncthreads();
-  const double* tr = d.tr + (long long)r * d.st_tr + sd.tr_off;
-  const double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
-  double* trace = d.trace + (long long)r * d.st_face + sd.face_off;
-  for (int f = threadIdx.x; f < nface; f += blockDim.x) {
-    double v = fbar[f];
-    for (int l = 0; l < nd; ++l) v += tr[(long long)f * nd + l] * cs[l];
-    trace[f] = v;
-  }
-  double part = 0.0;
-  if (branch == 1) {
-    const double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;
-    for (int c = threadIdx.x; c < m; c += blockDim.x) {
-      double v = pf[(long long)c * (nd + 1) + nd];
-      for (int l = 0; l < nd; ++l) v += pf[(long long)c * (nd + 1) + l] * cs[l];
-      const int jl = c / a, il = c - jl * a;
-      d.p_m[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il] = v;
-      part += v;
-    }
-  } else if (threadIdx.x == 0) {
-    const double* muh = d.mu_hat + (long long)r * d.st_dof + sd.dof_off;
-    part = d.sub_mean[(long long)r * d.st_sub + sidx] * m;
-    for (int l = 0; l < nd; ++l) part += muh[l] * cs[l] * m;
-  }
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    const long long si = (long long)r * d.st_sub + sidx;
-    if (branch == 1) {
-      d.pm_mean[si] = s / m;
-      d.sub_target[si] = s / m;
-    } else {
-      d.sub_target[si] = d.pm_mean[si] + s / m;
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------------------------
 // Warp-per-subdomain kernels (k_local_warp.cuh).  WPB warps per CTA, one subdomain each.
 
@@ -675,12 +617,6 @@ void launch_mpm_local(const Grid& g, const DevState& d, const DevSub* subs, int 
                       bool fp32, double ir_tol, int ir_max, cudaStream_t st) {
   if (fp32) MPM_DISPATCH_A(mpm_local_t, float, g, d, subs, nsub, max_a, max_b, 1, ir_tol, ir_max, st);
   else MPM_DISPATCH_A(mpm_local_t, double, g, d, subs, nsub, max_a, max_b, 0, ir_tol, ir_max, st);
-}
-
-void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub, const DevNode* nodes,
-                        const int* leaf_node, int branch, cudaStream_t st) {
-  k_reconstruct<<<dim3(nsub, g.R), 128, 0, st>>>(g, d, subs, nodes, leaf_node, branch);
-  ++g_launches;
 }
 
 void launch_downscale(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,

@@ -50,6 +50,8 @@ struct mpm_ctx {
   int* d_level_nodes = nullptr;
   int* d_srcmap = nullptr;
   int* d_pmap = nullptr;
+  DevLevel* d_levels = nullptr;
+  int coop_blocks = -1;  // grid of the persistent interface kernel (0: unavailable), -1: not queried
   DevState d{};
   std::vector<void*> grid_allocs, dec_allocs;
   // host staging for flags
@@ -62,6 +64,7 @@ struct mpm_ctx {
   long long gk_base = 0, gk_reb = 0, gk_mpm = 0, capture_launches = 0, graph_steps = 0;
   // CUDA graph of one Algorithm 1 step (conditional bodies for the two branches)
   bool use_graph = true;
+  bool use_coop = true;  // interface stage as one persistent cooperative kernel
   bool graph_valid = false;
   double g_eta = 0.0, g_cfl = 0.0;
   int g_nsub = 0;
@@ -295,6 +298,7 @@ int release_decomposition(mpm_ctx* c) {
   c->d_subs = nullptr;
   c->d_nodes = nullptr;
   c->d_leaf_node = c->d_level_nodes = c->d_srcmap = c->d_pmap = nullptr;
+  c->d_levels = nullptr;
   c->have_dec = false;
   c->have_basis = false;
   return MPM_OK;
@@ -344,6 +348,15 @@ int run_interface(mpm_ctx* c) {
   cudaStream_t st = c->stream;
   const int nsub = (int)c->subs.size();
   prof_begin(c, MPM_STAGE_IFACE_SOLVE);
+  if (c->use_coop && c->coop_blocks < 0) c->coop_blocks = iface_coop_blocks();
+  if (c->use_coop && c->coop_blocks > 0) {
+    cudaError_t e = launch_iface_coop(g, d, c->d_subs, nsub, c->max_dof, c->d_nodes, c->d_leaf_node,
+                                      c->d_level_nodes, c->d_levels, (int)c->levels.size(), c->d_srcmap, c->d_pmap,
+                                      c->coop_blocks, st);
+    prof_end(c, MPM_STAGE_IFACE_SOLVE);
+    if (e != cudaSuccess) return fail(c, MPM_ERR_CUDA, "persistent interface kernel: %s", cudaGetErrorString(e));
+    return check_launch(c);
+  }
   if (c->n_dof > 0) {
     launch_element_rhs(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, st);
     for (size_t L = 1; L < c->levels.size(); ++L)
@@ -815,6 +828,10 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
     }
     st_lvl = std::max(st_lvl, (long long)c->levels[L].size());
   }
+  std::vector<DevLevel> levtab(nlev);
+  for (int L = 0; L < nlev; ++L)
+    levtab[L] = DevLevel{c->lev_off[L], (int)c->levels[L].size(), c->lev_max_nf[L], c->lev_max_nsep[L],
+                         c->lev_max_nbnd[L]};
   if (srcmap.empty()) srcmap.push_back(-1);
   if (pmap.empty()) pmap.push_back(-1);
   // device pools
@@ -855,6 +872,7 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   if (!rc) rc = dalloc_t(c, A, &c->d_level_nodes, level_nodes.size());
   if (!rc) rc = dalloc_t(c, A, &c->d_srcmap, srcmap.size());
   if (!rc) rc = dalloc_t(c, A, &c->d_pmap, pmap.size());
+  if (!rc) rc = dalloc_t(c, A, &c->d_levels, levtab.size());
   if (rc) {
     release_decomposition(c);
     return rc;
@@ -866,6 +884,8 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
                      c->stream));
   CK(cudaMemcpyAsync(c->d_srcmap, srcmap.data(), srcmap.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->d_pmap, pmap.data(), pmap.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_levels, levtab.data(), levtab.size() * sizeof(DevLevel), cudaMemcpyHostToDevice,
+                     c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->have_dec = true;
   c->have_basis = false;
@@ -1004,10 +1024,12 @@ int mpm_step(mpm_ctx* c, double eta, double cfl, int n_sub) {
   return check_launch(c);
 }
 
-int mpm_set_graph(mpm_ctx* c, int enable) {
+int mpm_set_execution(mpm_ctx* c, int flags) {
   if (!c) return MPM_ERR_ARG;
-  c->use_graph = enable != 0;
-  if (!c->use_graph) drop_graph(c);
+  if (flags & ~(MPM_EXEC_GRAPH | MPM_EXEC_PERSISTENT)) return fail(c, MPM_ERR_ARG, "unknown execution flags %d", flags);
+  c->use_graph = (flags & MPM_EXEC_GRAPH) != 0;
+  c->use_coop = (flags & MPM_EXEC_PERSISTENT) != 0;
+  drop_graph(c);
   return MPM_OK;
 }
 

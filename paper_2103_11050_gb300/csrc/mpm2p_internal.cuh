@@ -71,6 +71,11 @@ struct DevNode {
   int pmap_off;        // nbnd ints: frontal index in the parent of each boundary DOF
 };
 
+// Per-level summary of the nested-dissection tree (node ids level_nodes[off .. off+cnt)).
+struct DevLevel {
+  int off, cnt, max_nf, max_ns, max_nb;
+};
+
 // Per-realisation device state (all pointers are device pointers; pools are indexed
 // r * st_x + offset).
 struct DevState {
@@ -140,6 +145,11 @@ void launch_nd_factor_level(const Grid& g, const DevState& d, const DevNode* nod
                             int nlev, int max_nf, int max_nsep, const int* srcmap, cudaStream_t st);
 void launch_nd_up(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
                   int max_nf, int max_nsep, const int* srcmap, cudaStream_t st);
+int iface_coop_blocks();
+cudaError_t launch_iface_coop(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_dof,
+                              const DevNode* nodes, const int* leaf_node, const int* level_nodes,
+                              const DevLevel* lev, int nlev, const int* srcmap, const int* pmap, int blocks,
+                              cudaStream_t st);
 void launch_nd_down(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
                     int max_nsep, int max_nbnd, const int* pmap, cudaStream_t st);
 
