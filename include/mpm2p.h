@@ -206,7 +206,7 @@ int mpm_init(mpm_ctx* ctx, double eta);
  * precision or the decomposition change. */
 int mpm_step(mpm_ctx* ctx, double eta, double cfl, int n_sub);
 
-/* Execution of the path (bitmask, default MPM_EXEC_GRAPH | MPM_EXEC_PERSISTENT):
+/* Execution of the path (bitmask, default MPM_EXEC_GRAPH):
  *  MPM_EXEC_GRAPH       mpm_step is one captured CUDA graph launch with device-side
  *                       branching; without it mpm_step runs kernel by kernel and the host
  *                       reads the decision to skip the branch no realisation takes (the
@@ -215,7 +215,9 @@ int mpm_step(mpm_ctx* ctx, double eta, double cfl, int n_sub);
  *                       nested-dissection level up and down, reconstruction, u_bar) is one
  *                       persistent cooperative kernel with grid-wide barriers between levels;
  *                       without it, one kernel per level (also the automatic fallback when
- *                       the device cannot launch cooperatively).
+ *                       the device cannot launch cooperatively).  Measured slower than
+ *                       the per-level kernels on the 256^2 workload (the grid-wide barriers
+ *                       cost more than the launches they replace), so it is off by default.
  * Results are identical up to rounding order.  Drops a captured graph. */
 enum { MPM_EXEC_GRAPH = 1, MPM_EXEC_PERSISTENT = 2 };
 int mpm_set_execution(mpm_ctx* ctx, int flags);

@@ -268,7 +268,7 @@ class Context:
     def get_conductivity(self, out=None):
         return self._get(self.L.mpm_get_conductivity, (self.R, self.ny, self.nx), out)
 
-    def set_execution(self, graph=True, persistent=True):
+    def set_execution(self, graph=True, persistent=False):
         self._ck(self.L.mpm_set_execution(self.h, (EXEC_GRAPH if graph else 0) | (EXEC_PERSISTENT if persistent else 0)))
 
     def profile_enable(self, on=True):

@@ -63,8 +63,10 @@ __global__ void k_mobility_eps(Grid g, DevState d, int with_eps) {
   double num = 0.0, den = 0.0;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
-    const double kn = mobility(d.s[base + c], g.M) * d.K[base + c];
+    const double sc = d.s[base + c];
+    const double kn = mobility(sc, g.M) * d.K[base + c];
     d.kap_n[base + c] = kn;
+    d.fs[base + c] = fracflow(sc, g.M);
     const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
     if (i < nx - 1) {
       const double ke = mobility(d.s[base + c + 1], g.M) * d.K[base + c + 1];
@@ -211,7 +213,9 @@ __global__ void k_cfl_finalize(Grid g, DevState d, int nblk, double cfl, double 
   if (threadIdx.x == 0) d.dt[r] = m > 0.0 ? cfl * g.h * g.h / (fmax_ * m) : 0.0;
 }
 
-// s2_c = s_c - dt/h^2 sum_faces F_out f(s_upwind); inflow through the boundary carries s_inflow.
+// s2_c = s_c - dt/h^2 sum_faces F_out f(s_upwind); inflow through the boundary carries
+// s_inflow.  f(s) is read from fs (computed once per cell where s was produced); the
+// kernel writes f(s2) to fs2 for the next substep.
 __global__ void k_upwind(Grid g, DevState d) {
   const int r = blockIdx.y;
   const int nx = g.nx, ny = g.ny;
@@ -219,26 +223,28 @@ __global__ void k_upwind(Grid g, DevState d) {
   const double lam = d.dt[r] / (g.h * g.h);
   const double* ux = d.ux + (long long)r * g.nfx();
   const double* uy = d.uy + (long long)r * g.nfy();
-  const double* s = d.s + base;
+  const double* fs = d.fs + base;
   const double f_in = fracflow(g.s_inflow, g.M);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
-    const double sc = s[c], fc = fracflow(sc, g.M);
+    const double fc = fs[c];
     double acc = 0.0, F;
     F = -ux[(long long)j * (nx + 1) + i];
     if (F > 0.0) acc += F * fc;
-    else if (F < 0.0) acc += F * (i > 0 ? fracflow(s[c - 1], g.M) : f_in);
+    else if (F < 0.0) acc += F * (i > 0 ? fs[c - 1] : f_in);
     F = ux[(long long)j * (nx + 1) + i + 1];
     if (F > 0.0) acc += F * fc;
-    else if (F < 0.0) acc += F * (i < nx - 1 ? fracflow(s[c + 1], g.M) : f_in);
+    else if (F < 0.0) acc += F * (i < nx - 1 ? fs[c + 1] : f_in);
     F = -uy[(long long)j * nx + i];
     if (F > 0.0) acc += F * fc;
-    else if (F < 0.0) acc += F * (j > 0 ? fracflow(s[c - nx], g.M) : f_in);
+    else if (F < 0.0) acc += F * (j > 0 ? fs[c - nx] : f_in);
     F = uy[(long long)(j + 1) * nx + i];
     if (F > 0.0) acc += F * fc;
-    else if (F < 0.0) acc += F * (j < ny - 1 ? fracflow(s[c + nx], g.M) : f_in);
-    d.s2[base + c] = sc - lam * acc;
+    else if (F < 0.0) acc += F * (j < ny - 1 ? fs[c + nx] : f_in);
+    const double s_new = d.s[base + c] - lam * acc;
+    d.s2[base + c] = s_new;
+    d.fs2[base + c] = fracflow(s_new, g.M);
   }
 }
 

@@ -229,14 +229,19 @@ __global__ void k_sweep_trailing(Grid g, DevState d, const DevNode* nodes, const
 
 constexpr int kRowsPerCta = 8;  // frontal rows per CTA of the per-level solve kernels (one row per warp)
 
-// Upward solve at one level (see phase::nd_up_row).
+// Upward solve at one level (see phase::nd_up_row); the separator right-hand side is
+// gathered from the children once per CTA into shared memory.
 __global__ void k_nd_up(Grid g, DevState d, const DevNode* nodes, const int* level_nodes, const int* srcmap) {
+  extern __shared__ double gs[];
   const int r = blockIdx.z;
   const DevNode nd = nodes[level_nodes[blockIdx.x]];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int row0 = blockIdx.y * kRowsPerCta;
+  if (row0 >= nd.nf) return;
+  for (int k = threadIdx.x; k < nd.nsep; k += blockDim.x) gs[k] = phase::gather_g(d, nodes, nd, r, srcmap, k);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int row = row0 + warp; row < min(nd.nf, row0 + kRowsPerCta); row += nw)
-    phase::nd_up_row(d, nodes, nd, r, row, srcmap, lane);
+    phase::nd_up_row(d, nodes, nd, r, row, srcmap, lane, gs);
 }
 
 // Downward solve at one level (see phase::nd_down_row / nd_down_copy).
@@ -252,21 +257,24 @@ __global__ void k_nd_down(Grid g, DevState d, const DevNode* nodes, const int* l
     phase::nd_down_row(d, nodes, nd, r, row, pmap, lane);
 }
 
-// Reconstruction of traces / p^m for the realisations of one branch (phase::reconstruct).
+// Reconstruction of traces / p^m (phase::reconstruct) for the realisations of one branch,
+// or (branch = -1) for every realisation with its own branch.
 __global__ void k_reconstruct(Grid g, DevState d, const DevSub* subs, const DevNode* nodes, const int* leaf_node,
                               int branch) {
   __shared__ double cs[4 * 4 * kMaxSide];
   __shared__ double red[32];
   const int r = blockIdx.y;
-  if (d.rebuild[r] != branch) return;
-  phase::reconstruct(g, d, subs, nodes, leaf_node, blockIdx.x, r, branch, cs, red);
+  const int br = d.rebuild[r];
+  if (branch >= 0 && br != branch) return;
+  phase::reconstruct(g, d, subs, nodes, leaf_node, blockIdx.x, r, br, cs, red);
 }
 
-// Interface / boundary fluxes u_bar for the realisations of one branch (phase::ubar).
+// Interface / boundary fluxes u_bar (phase::ubar), same branch convention.
 __global__ void k_ubar(Grid g, DevState d, const DevSub* subs, int branch) {
   const int r = blockIdx.y;
-  if (d.rebuild[r] != branch) return;
-  phase::ubar(g, d, subs, blockIdx.x, r, branch);
+  const int br = d.rebuild[r];
+  if (branch >= 0 && br != branch) return;
+  phase::ubar(g, d, subs, blockIdx.x, r, br);
 }
 
 // The whole interface-solve stage in one persistent cooperative launch: element
@@ -304,7 +312,7 @@ __global__ void __launch_bounds__(256) k_iface_coop(Grid g, DevState d, const De
         const long long rn = it / lv.max_nf;
         const int ni = (int)(rn % lv.cnt), r = (int)(rn / lv.cnt);
         const DevNode& nd = nodes[level_nodes[lv.off + ni]];
-        if (row < nd.nf) phase::nd_up_row(d, nodes, nd, r, row, srcmap, lane);
+        if (row < nd.nf) phase::nd_up_row(d, nodes, nd, r, row, srcmap, lane, nullptr);
       }
       grid.sync();
     }

@@ -79,13 +79,17 @@ __device__ __forceinline__ double gather_g(const DevState& d, const DevNode* nod
 }
 
 // Upward solve, one frontal row per warp: y_s = M_ss g_s -> x (row < nsep), or
-// g_b = g_b + M_bs g_s (row >= nsep), with g gathered from the children on the fly.
+// g_b = g_b + M_bs g_s (row >= nsep).  gs: the node's gathered separator right-hand side
+// (shared memory), or nullptr to gather from the children on the fly.
 __device__ __forceinline__ void nd_up_row(const DevState& d, const DevNode* nodes, const DevNode& nd, int r, int row,
-                                          const int* srcmap, int lane) {
+                                          const int* srcmap, int lane, const double* gs) {
   const int nf = nd.nf, ns = nd.nsep;
   const double* Fr = d.front + (long long)r * d.st_front + nd.f_off + (long long)row * nf;
   double acc = 0.0;
-  for (int k = lane; k < ns; k += 32) acc += Fr[k] * gather_g(d, nodes, nd, r, srcmap, k);
+  if (gs)
+    for (int k = lane; k < ns; k += 32) acc += Fr[k] * gs[k];
+  else
+    for (int k = lane; k < ns; k += 32) acc += Fr[k] * gather_g(d, nodes, nd, r, srcmap, k);
   acc = warp_sum(acc);
   if (lane == 0) {
     if (row < ns) d.xvec[(long long)r * d.st_vec + nd.v_off + row] = acc;

@@ -64,7 +64,7 @@ struct mpm_ctx {
   long long gk_base = 0, gk_reb = 0, gk_mpm = 0, capture_launches = 0, graph_steps = 0;
   // CUDA graph of one Algorithm 1 step (conditional bodies for the two branches)
   bool use_graph = true;
-  bool use_coop = true;  // interface stage as one persistent cooperative kernel
+  bool use_coop = false;  // interface stage as one persistent cooperative kernel (measured slower)
   bool graph_valid = false;
   double g_eta = 0.0, g_cfl = 0.0;
   int g_nsub = 0;
@@ -366,10 +366,8 @@ int run_interface(mpm_ctx* c) {
       launch_nd_down(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(),
                      c->lev_max_nsep[L], c->lev_max_nbnd[L], c->d_pmap, st);
   }
-  for (int branch = 1; branch >= 0; --branch) {
-    launch_reconstruct(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, branch, st);
-    launch_ubar(g, d, c->d_subs, nsub, branch, st);
-  }
+  launch_reconstruct(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, -1, st);
+  launch_ubar(g, d, c->d_subs, nsub, -1, st);
   prof_end(c, MPM_STAGE_IFACE_SOLVE);
   return check_launch(c);
 }
@@ -386,10 +384,13 @@ int run_transport(mpm_ctx* c, double cfl, int n_sub) {
   prof_begin(c, MPM_STAGE_TRANSPORT);
   launch_cfl(c->g, c->d, cfl, max_fprime(c->g.M), c->stream);
   double* s_home = c->d.s;
+  double* fs_home = c->d.fs;
   for (int k = 0; k < n_sub; ++k) {
     launch_upwind(c->g, c->d, c->stream);
     std::swap(c->d.s, c->d.s2);
+    std::swap(c->d.fs, c->d.fs2);
   }
+  if (c->d.fs != fs_home) std::swap(c->d.fs, c->d.fs2);  // f(s) is recomputed below from the final s
   if (c->d.s != s_home) {  // odd substep count: bring the result home (graph replays read s_home)
     CK(cudaMemcpyAsync(s_home, c->d.s, sizeof(double) * c->g.R * c->g.ncell(), cudaMemcpyDeviceToDevice,
                        c->stream));
@@ -531,7 +532,7 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   const size_t nc = (size_t)R * nx * ny;
   DevState& d = c->d;
   int rc = MPM_OK;
-  double** cells[] = {&d.K, &d.q, &d.s, &d.s2, &d.kap_n, &d.kap_m, &d.p_m, &d.p_down, &d.resid};
+  double** cells[] = {&d.K, &d.q, &d.s, &d.s2, &d.kap_n, &d.kap_m, &d.p_m, &d.p_down, &d.resid, &d.fs, &d.fs2};
   for (double** p : cells)
     if ((rc = dalloc_t(c, c->grid_allocs, p, nc)) != MPM_OK) break;
   const int nblk = 1024;

@@ -81,6 +81,7 @@ struct DevLevel {
 struct DevState {
   // cells [R][ny][nx]
   double *K, *q, *s, *s2, *kap_n, *kap_m, *p_m, *p_down, *resid;
+  double *fs, *fs2;    // fractional flow f(s) of s / s2
   // faces
   double *ux, *uy;
   double *tx, *ty;     // transmissibilities of kappa^n: tx [R][ny][nx+1], ty [R][ny+1][nx] (interior faces)
