@@ -287,6 +287,19 @@ def cpu_baseline(w, budget_s=20.0, max_steps=None):
                       f"{dt:.1f} s of CPU time"}
 
 
+def combine_ranks(ms_per_step, cells_per_rank, device):
+    """Whole-job numbers of replicas on N ranks: the slowest rank's step time and the
+    cell updates of all ranks over that time (weak scaling; the only collective is this
+    max-reduction of one timing, the hot path itself exchanges nothing)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size()
+    t = torch.tensor([ms_per_step], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, world * cells_per_rank / (ms / 1e3)
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -334,10 +347,7 @@ def main():
         torch.cuda.set_device(local)
         args.no_cpu = args.no_cpu or dist.get_rank() != 0
         line = run_gpu(args, w)
-        t = torch.tensor([line["ms_per_step"]], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        line["ms_per_step"] = float(t.item())
-        line["value"] = world * w["nx"] * w["ny"] / (line["ms_per_step"] / 1e3)
+        line["ms_per_step"], line["value"] = combine_ranks(line["ms_per_step"], w["nx"] * w["ny"], "cuda")
         line["n_gpus"] = world
         if dist.get_rank() == 0:
             print(json.dumps(line), flush=True)
