@@ -151,20 +151,20 @@ int mpm_set_decomposition(mpm_ctx* ctx, int ncx, const int* col_w, int ncy, cons
 /* Water saturation s [R][ny][nx] in [0,1]; also recomputes kappa^n = lambda(s) K. */
 int mpm_set_saturation(mpm_ctx* ctx, const double* s, int mem);
 
-/* MRCM basis build at the current kappa^n (Algorithm 1 lines 2-3 and 13-15; Eqs. mrc1,
+/* MRCM basis build at the current kappa^n (Algorithm 1, initialisation and rebuild branch; Eqs. mrc1,
  * mrc_homogeneous, mrc_non_homogeneous, mrc2): factor every local Robin problem, one
  * local solve per interface DOF plus the non-homogeneous one, assemble and factor the
- * interface system, solve it, form the MRCM-level pressure p^m and the interface fluxes
- * (mean of the one-sided traces).  Stores kappa^m := kappa^n.  Enqueued, no host sync.
- * Needs mpm_set_permeability, mpm_set_decomposition and mpm_set_saturation first. */
+ * interface system and form its right-hand side (mpm_interface_solve solves it).  Stores
+ * kappa^m := kappa^n.  Enqueued, no host sync.  Needs mpm_set_permeability,
+ * mpm_set_decomposition and mpm_set_saturation first. */
 int mpm_build_basis(mpm_ctx* ctx);
 
 /* Recompute kappa^n = lambda(s) K from the current saturation and
  * epsilon_r = ||kappa^n - kappa^m||_2 / ||kappa^m||_2 per realisation (Section 4.1,
- * Algorithm 1 line 19).  eps (host, [R]) may be NULL (then no host sync). */
+ * Algorithm 1, update of epsilon).  eps (host, [R]) may be NULL (then no host sync). */
 int mpm_eval_epsilon(mpm_ctx* ctx, double* eps);
 
-/* Algorithm 1 line 11 decision per realisation: rebuild_r = (epsilon_r > eta) with the
+/* Algorithm 1 decision per realisation: rebuild_r = (epsilon_r > eta) with the
  * epsilon of the last mpm_eval_epsilon.  rebuild (host, [R]) may be NULL (no host sync). */
 int mpm_choose(mpm_ctx* ctx, double eta, int* rebuild);
 
@@ -175,29 +175,34 @@ int mpm_choose(mpm_ctx* ctx, double eta, int* rebuild);
 int mpm_perturbation_solve(mpm_ctx* ctx);
 
 /* Interface (skeleton) solve with the stored factorisation for the right-hand side of the
- * last mpm_build_basis or mpm_perturbation_solve, and the interface / boundary fluxes
- * u_bar: after a build, the mean of the one-sided MRCM traces; after a perturbation
- * solve, the mean of the one-sided traces of the epsilon^0 problem plus the fine flux
- * of p^m with kappa^n (Section 4.1, u_bar = u^m + delta u^n). */
+ * last mpm_build_basis or mpm_perturbation_solve, then the one-sided traces of every
+ * subdomain (and, after a build, the MRCM-level pressure p^m).  The interface fluxes
+ * u_bar are formed from these traces by mpm_downscale. */
 int mpm_interface_solve(mpm_ctx* ctx);
 
-/* Downscaling (Eq. mpm_upd): per subdomain, Neumann problem with kappa^n and u_bar on
- * all its boundary faces; pressure constant fixed by mean(p~) = mean of the MRCM-level
- * pressure of the same update over the subdomain.  Writes the conservative fine
- * fluxes ux, uy and p~. */
+/* Downscaling (Eq. mpm_upd).  First the interface / boundary fluxes u_bar from the traces
+ * of the last mpm_interface_solve: after a build, the mean of the one-sided MRCM traces;
+ * after a perturbation solve, the mean of the one-sided traces of the epsilon^0 problem
+ * plus the fine flux of p^m with kappa^n (Section 4.1, u_bar = u^m + delta u^n).  Then per
+ * subdomain the Neumann problem with kappa^n and u_bar on all its boundary faces; pressure
+ * constant fixed by mean(p~) = mean of the MRCM-level pressure of the same update over the
+ * subdomain.  Writes the conservative fine fluxes ux, uy (boundary and interior faces),
+ * p~, and the per-subdomain maxima of cell in/outflow that the next mpm_saturation_step
+ * turns into its time step. */
 int mpm_downscale(mpm_ctx* ctx);
 
 /* Explicit upwind transport (Section 4, Eq. BL2D): n_sub >= 1 explicit Euler steps with
- * the current fine fluxes frozen and dt = cfl h^2 / (max f' * max_c max(out_c, in_c)),
- * out_c / in_c the total integrated outflow / inflow of cell c, 0 < cfl <= 1.  Then
- * recomputes kappa^n.  dt (host, [R]) may be NULL (no host sync). */
+ * the fine fluxes of the last mpm_downscale frozen and
+ * dt = cfl h^2 / (max f' * max_c max(out_c, in_c)), out_c / in_c the total integrated
+ * outflow / inflow of cell c (taken by mpm_downscale; dt = 0 before any downscaling),
+ * 0 < cfl <= 1.  Then recomputes kappa^n.  dt (host, [R]) may be NULL (no host sync). */
 int mpm_saturation_step(mpm_ctx* ctx, double cfl, int n_sub, double* dt);
 
-/* Algorithm 1 initialisation (lines 1-4): kappa^0, MRCM solve + downscale, store the
+/* Algorithm 1 initialisation: kappa^0, MRCM solve + downscale, store the
  * basis, epsilon := eta.  Enqueued, no host sync. */
 int mpm_init(mpm_ctx* ctx, double eta);
 
-/* One pass of the while loop of Algorithm 1 (lines 6-20) for every realisation:
+/* One pass of the while loop of Algorithm 1 for every realisation:
  * n_sub transport steps, kappa^n, MRCM rebuild where epsilon > eta (the epsilon of the
  * previous pass) else an MPM-2P update, downscaling, new epsilon.  By default the pass is
  * one CUDA graph launch: the decision is taken on the device and selects conditional graph

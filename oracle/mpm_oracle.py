@@ -822,7 +822,7 @@ class SimState:
 
 
 def simulate_init(K, s0, prob: Problem, dec: Decomposition, eta: float) -> SimState:
-    """Algorithm 1, lines 1-4: kappa^0, MRCM solution, store the BFs, eps = eta."""
+    """Algorithm 1, initialisation: kappa^0, MRCM solution, store the BFs, eps = eta."""
     kappa0 = mobility(s0, prob.M) * K
     step, bs, sol = mrcm_step(kappa0, prob, dec)
     return SimState(s0.copy(), bs, sol.p.copy(), step, eta)

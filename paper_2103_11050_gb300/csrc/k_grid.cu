@@ -1,10 +1,9 @@
 // Fine-grid stencil kernels of the MPM-2P step (HBM-bound, FP64).
 //
 //  - kappa^n = lambda(s) K and the partial sums of epsilon (Section 4.1, Algorithm 1).
-//  - MPM residual r = q h^2 - sum_faces F(kappa^n, p^m) (Eq. mpm_tf_3).
-//  - interface / boundary fluxes u_bar (mean of one-sided traces, plus F_n(p^m) on
-//    MPM-2P updates: u_bar = uhat_0 - kappa^n grad p^m, Section 4.1).
-//  - CFL time step and explicit upwind transport (Section 4, Eq. BL2D).
+//  - the Algorithm 1 decision and the new epsilon after it.
+//  - CFL time step (from per-subdomain maxima) and explicit upwind transport (Section 4,
+//    Eq. BL2D).
 #include "mpm2p_internal.cuh"
 
 namespace mpm {
@@ -137,6 +136,22 @@ __global__ void k_choose_graph(Grid g, DevState d, double eta, cudaGraphConditio
   }
 }
 
+// New epsilon after the update of this step (Algorithm 1, update of epsilon): 0 where the basis was
+// rebuilt (kappa^m := kappa^n), else ||kappa^n - kappa^m|| / ||kappa^m|| from the partial sums
+// taken in the transport's mobility pass (kappa^m unchanged by an MPM-2P update).
+__global__ void k_eps_after_choose(Grid g, DevState d, int nblk) {
+  __shared__ double sh[32];
+  const int r = blockIdx.x;
+  double num = 0.0, den = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    num += d.eps_part[((long long)r * nblk + b) * 2 + 0];
+    den += d.eps_part[((long long)r * nblk + b) * 2 + 1];
+  }
+  num = block_sum(num, sh);
+  den = block_sum(den, sh);
+  if (threadIdx.x == 0) d.eps[r] = d.rebuild[r] ? 0.0 : (den > 0.0 ? sqrt(num) / sqrt(den) : 0.0);
+}
+
 __global__ void k_fill_flags(Grid g, DevState d, int v) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < g.R) d.rebuild[r] = v;
@@ -151,64 +166,13 @@ __global__ void k_copy_kappa_m(Grid g, DevState d) {
     d.kap_m[(long long)r * n + c] = d.kap_n[(long long)r * n + c];
 }
 
-// Outward integrated flux of pressure p through a physical boundary face of cell value
-// (kc, pc) on side `side` (Dirichlet: 2 kc (pc - g); Neumann: z h).
-__device__ __forceinline__ double phys_flux(const Grid& g, int side, double kc, double pc) {
-  return g.bc_type[side] == 0 ? 2.0 * kc * (pc - g.bc_val[side]) : g.bc_val[side] * g.h;
-}
-
-// r_c = q_c h^2 - sum_faces F_out(kappa^n, p^m): residual of the fine system at p^m.
-__global__ void k_residual(Grid g, DevState d) {
-  const int r = blockIdx.y;
-  if (d.rebuild[r] != 0) return;
-  const int nx = g.nx, ny = g.ny;
-  const long long n = g.ncell(), base = (long long)r * n;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-       c += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
-    const double kc = d.kap_n[base + c], pc = d.p_m[base + c];
-    const double* tx = d.tx + (long long)r * g.nfx() + (long long)j * (nx + 1);
-    const double* ty = d.ty + (long long)r * g.nfy();
-    double out = 0.0;
-    if (i > 0) out += tx[i] * (pc - d.p_m[base + c - 1]);
-    else out += phys_flux(g, 0, kc, pc);
-    if (i < nx - 1) out += tx[i + 1] * (pc - d.p_m[base + c + 1]);
-    else out += phys_flux(g, 1, kc, pc);
-    if (j > 0) out += ty[(long long)j * nx + i] * (pc - d.p_m[base + c - nx]);
-    else out += phys_flux(g, 2, kc, pc);
-    if (j < ny - 1) out += ty[(long long)(j + 1) * nx + i] * (pc - d.p_m[base + c + nx]);
-    else out += phys_flux(g, 3, kc, pc);
-    d.resid[base + c] = d.q[base + c] * g.h * g.h - out;
-  }
-}
-
-// max over cells of max(total outflow, total inflow) -> dt per realisation.
-__global__ void k_cfl_part(Grid g, DevState d) {
-  __shared__ double sh[32];
-  const int r = blockIdx.y;
-  const int nx = g.nx;
-  const long long n = g.ncell();
-  double m = 0.0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-       c += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
-    const double* ux = d.ux + (long long)r * g.nfx();
-    const double* uy = d.uy + (long long)r * g.nfy();
-    const double f0 = -ux[(long long)j * (nx + 1) + i], f1 = ux[(long long)j * (nx + 1) + i + 1];
-    const double f2 = -uy[(long long)j * nx + i], f3 = uy[(long long)(j + 1) * nx + i];
-    const double out = fmax(f0, 0.0) + fmax(f1, 0.0) + fmax(f2, 0.0) + fmax(f3, 0.0);
-    const double in = fmax(-f0, 0.0) + fmax(-f1, 0.0) + fmax(-f2, 0.0) + fmax(-f3, 0.0);
-    m = fmax(m, fmax(out, in));
-  }
-  m = block_max(m, sh);
-  if (threadIdx.x == 0) d.rate_part[(long long)r * gridDim.x + blockIdx.x] = m;
-}
-
-__global__ void k_cfl_finalize(Grid g, DevState d, int nblk, double cfl, double fmax_) {
+// dt per realisation from the per-subdomain maxima of max(total outflow, total inflow)
+// over cells that the downscaling wrote (rate_part[r][subdomain]).
+__global__ void k_cfl_finalize(Grid g, DevState d, int nsub, double cfl, double fmax_) {
   __shared__ double sh[32];
   const int r = blockIdx.x;
   double m = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) m = fmax(m, d.rate_part[(long long)r * nblk + b]);
+  for (int b = threadIdx.x; b < nsub; b += blockDim.x) m = fmax(m, d.rate_part[(long long)r * d.st_sub + b]);
   m = block_max(m, sh);
   if (threadIdx.x == 0) d.dt[r] = m > 0.0 ? cfl * g.h * g.h / (fmax_ * m) : 0.0;
 }
@@ -267,6 +231,16 @@ void launch_mobility_eps(const Grid& g, const DevState& d, bool with_eps, cudaSt
   }
 }
 
+void launch_mobility_partials(const Grid& g, const DevState& d, cudaStream_t st) {
+  k_mobility_eps<<<dim3(cell_blocks(g), g.R), kThreads, 0, st>>>(g, d, 1);
+  ++g_launches;
+}
+
+void launch_eps_after_choose(const Grid& g, const DevState& d, cudaStream_t st) {
+  k_eps_after_choose<<<g.R, kThreads, 0, st>>>(g, d, cell_blocks(g));
+  ++g_launches;
+}
+
 void launch_choose(const Grid& g, const DevState& d, double eta, cudaStream_t st) {
   k_choose<<<(g.R + 127) / 128, 128, 0, st>>>(g, d, eta);
   ++g_launches;
@@ -288,16 +262,8 @@ void launch_copy_kappa_m(const Grid& g, const DevState& d, cudaStream_t st) {
   ++g_launches;
 }
 
-void launch_residual(const Grid& g, const DevState& d, cudaStream_t st) {
-  k_residual<<<dim3(cell_blocks(g), g.R), kThreads, 0, st>>>(g, d);
-  ++g_launches;
-}
-
-void launch_cfl(const Grid& g, const DevState& d, double cfl, double fmax_, cudaStream_t st) {
-  const int nb = cell_blocks(g);
-  k_cfl_part<<<dim3(nb, g.R), kThreads, 0, st>>>(g, d);
-  ++g_launches;
-  k_cfl_finalize<<<g.R, kThreads, 0, st>>>(g, d, nb, cfl, fmax_);
+void launch_cfl(const Grid& g, const DevState& d, double cfl, double fmax_, int nsub, cudaStream_t st) {
+  k_cfl_finalize<<<g.R, kThreads, 0, st>>>(g, d, nsub, cfl, fmax_);
   ++g_launches;
 }
 

@@ -76,17 +76,6 @@ __global__ void k_element_matrix(Grid g, DevState d, const DevSub* subs, const D
   }
 }
 
-// Element right-hand side of every subdomain (see phase::element_rhs).
-__global__ void k_element_rhs(Grid g, DevState d, const DevSub* subs, const DevNode* nodes,
-                              const int* leaf_node) {
-  const int r = blockIdx.y;
-  const int sidx = blockIdx.x;
-  const DevSub sd = subs[sidx];
-  if (sd.ndof == 0) return;
-  const DevNode leaf = nodes[leaf_node[sidx]];
-  for (int k = threadIdx.x; k < sd.ndof; k += blockDim.x) phase::element_rhs(g, d, sd, leaf, r, k);
-}
-
 // Frontal matrix of an internal node: extend-add of the children's Schur complements.
 __global__ void k_nd_assemble(Grid g, DevState d, const DevNode* nodes, const int* level_nodes,
                               const int* srcmap) {
@@ -269,17 +258,10 @@ __global__ void k_reconstruct(Grid g, DevState d, const DevSub* subs, const DevN
   phase::reconstruct(g, d, subs, nodes, leaf_node, blockIdx.x, r, br, cs, red);
 }
 
-// Interface / boundary fluxes u_bar (phase::ubar), same branch convention.
-__global__ void k_ubar(Grid g, DevState d, const DevSub* subs, int branch) {
-  const int r = blockIdx.y;
-  const int br = d.rebuild[r];
-  if (branch >= 0 && br != branch) return;
-  phase::ubar(g, d, subs, blockIdx.x, r, br);
-}
-
-// The whole interface-solve stage in one persistent cooperative launch: element
-// right-hand sides, the upward sweep level by level, the downward sweep level by level,
-// reconstruction and u_bar, with a grid-wide barrier between dependent phases.  Every
+// The whole interface-solve stage in one persistent cooperative launch: the upward sweep
+// level by level, the downward sweep level by level and the reconstruction, with a
+// grid-wide barrier between dependent phases (the leaf right-hand sides come from the
+// local-solve kernels).  Every
 // block reaches every barrier (no early return).  Items are grid-strided; per-level rows
 // are one warp each.
 __global__ void __launch_bounds__(256) k_iface_coop(Grid g, DevState d, const DevSub* subs, int nsub, int max_dof,
@@ -295,15 +277,6 @@ __global__ void __launch_bounds__(256) k_iface_coop(Grid g, DevState d, const De
   const long long nwarps = nthreads >> 5, wid = tid >> 5;
   const int lane = threadIdx.x & 31;
   if (max_dof > 0) {
-    const long long items = (long long)g.R * nsub * max_dof;
-    for (long long it = tid; it < items; it += nthreads) {
-      const int k = (int)(it % max_dof);
-      const long long rs = it / max_dof;
-      const int sidx = (int)(rs % nsub), r = (int)(rs / nsub);
-      const DevSub& sd = subs[sidx];
-      if (k < sd.ndof) phase::element_rhs(g, d, sd, nodes[leaf_node[sidx]], r, k);
-    }
-    grid.sync();
     for (int L = 1; L < nlev; ++L) {
       const DevLevel lv = lev[L];
       const long long rows = (long long)g.R * lv.cnt * lv.max_nf;
@@ -341,11 +314,6 @@ __global__ void __launch_bounds__(256) k_iface_coop(Grid g, DevState d, const De
     const int sidx = (int)(it % nsub), r = (int)(it / nsub);
     phase::reconstruct(g, d, subs, nodes, leaf_node, sidx, r, d.rebuild[r], cs, red);
   }
-  grid.sync();
-  for (long long it = blockIdx.x; it < (long long)g.R * nsub; it += gridDim.x) {
-    const int sidx = (int)(it % nsub), r = (int)(it / nsub);
-    phase::ubar(g, d, subs, sidx, r, d.rebuild[r]);
-  }
 }
 
 }  // namespace
@@ -353,11 +321,6 @@ __global__ void __launch_bounds__(256) k_iface_coop(Grid g, DevState d, const De
 void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub, const DevNode* nodes,
                         const int* leaf_node, int branch, cudaStream_t st) {
   k_reconstruct<<<dim3(nsub, g.R), 128, 0, st>>>(g, d, subs, nodes, leaf_node, branch);
-  ++g_launches;
-}
-
-void launch_ubar(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int branch, cudaStream_t st) {
-  k_ubar<<<dim3(nsub, g.R), 128, 0, st>>>(g, d, subs, branch);
   ++g_launches;
 }
 
@@ -392,12 +355,6 @@ cudaError_t launch_iface_coop(const Grid& g, const DevState& d, const DevSub* su
 void launch_element_matrix(const Grid& g, const DevState& d, const DevSub* subs, int nsub, const DevNode* nodes,
                            const int* leaf_node, cudaStream_t st) {
   k_element_matrix<<<dim3(nsub, g.R), 256, 0, st>>>(g, d, subs, nodes, leaf_node);
-  ++g_launches;
-}
-
-void launch_element_rhs(const Grid& g, const DevState& d, const DevSub* subs, int nsub, const DevNode* nodes,
-                        const int* leaf_node, cudaStream_t st) {
-  k_element_rhs<<<dim3(nsub, g.R), 128, 0, st>>>(g, d, subs, nodes, leaf_node);
   ++g_launches;
 }
 

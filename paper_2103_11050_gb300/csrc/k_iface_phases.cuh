@@ -1,7 +1,9 @@
 // Per-item device functions of the interface-solve stage (Eq. mrc2 right-hand side,
 // nested-dissection up / down sweeps, reconstruction of traces and p^m, interface fluxes
-// u_bar).  They are called both by one-kernel-per-level launches and by the persistent
-// cooperative kernel that runs the whole stage in one launch (k_iface.cu).
+// u_bar).  The sweeps are called both by one-kernel-per-level launches and by the
+// persistent cooperative kernel that runs the whole sweep in one launch (k_iface.cu); the
+// right-hand side is formed by the local-solve kernels that produce the traces, u_bar by
+// the downscaling kernel that consumes it (k_local.cu).
 #pragma once
 #include "mpm2p_internal.cuh"
 
@@ -123,7 +125,7 @@ __device__ __forceinline__ void nd_down_copy(const DevState& d, const DevNode* n
 // interface solution (whole CTA; cs: >= ndof doubles, red: 32 doubles of shared memory):
 //   rebuild: p^m = pbar + P_hat c, F = Fbar + F_hat c, target mean = mean(p^m)
 //   MPM-2P : F = dFbar + F_hat dc, target mean = mean(p^m) + mean(dpbar) + mu_hat . dc
-__device__ void reconstruct(const Grid& g, const DevState& d, const DevSub* subs, const DevNode* nodes,
+__device__ inline void reconstruct(const Grid& g, const DevState& d, const DevSub* subs, const DevNode* nodes,
                             const int* leaf_node, int sidx, int r, int branch, double* cs, double* red) {
   const DevSub& sd = subs[sidx];
   const int a = sd.a, b = sd.b, m = a * b, nd = sd.ndof;
@@ -174,57 +176,46 @@ __device__ void reconstruct(const Grid& g, const DevState& d, const DevSub* subs
   __syncthreads();
 }
 
-// u_bar on the subdomain-boundary faces owned by subdomain sidx (its physical sides and
-// its right / top interface sides), written into ux / uy (whole CTA).
-// branch = 1: after a basis build (mean of the MRCM traces); branch = 0: after a
-// perturbation solve (mean of the epsilon^0 traces plus F_n(p^m) = -kappa^n grad p^m).
-__device__ void ubar(const Grid& g, const DevState& d, const DevSub* subs, int sidx, int r, int branch) {
-  const int add_fn = branch == 0;
-  const DevSub& sd = subs[sidx];
+// u_bar on face t of side `side` of subdomain sd, oriented along +x / +y (Section 4.1,
+// u_bar = uhat_0 + delta u^n).  branch = 1 (after a basis build): the mean of the two
+// one-sided MRCM traces on an interface, the trace itself on a physical side.  branch = 0
+// (after a perturbation solve): the same from the epsilon^0 traces, plus
+// F_n(p^m) = -kappa^n grad p^m.  Both subdomains of an interface face get bit-identical
+// values: the outward flux is formed with explicitly rounded operations whose operands
+// swap sign exactly when the two sides swap.
+__device__ __forceinline__ double ubar_face(const Grid& g, const DevState& d, const DevSub* subs, const DevSub& sd,
+                                            int r, int side, int t, int branch) {
   const int nx = g.nx;
   const long long cb = (long long)r * g.ncell();
-  const int nface = 2 * (sd.a + sd.b);
-  for (int f = threadIdx.x; f < nface; f += blockDim.x) {
-    int side, t;
-    if (f < sd.b) { side = 0; t = f; }
-    else if (f < 2 * sd.b) { side = 1; t = f - sd.b; }
-    else if (f < 2 * sd.b + sd.a) { side = 2; t = f - 2 * sd.b; }
-    else { side = 3; t = f - 2 * sd.b - sd.a; }
-    const bool iface = sd.side_kind[side] == 1;
-    if (iface && (side == 0 || side == 2)) continue;  // written by the neighbour
-    int ci, cj;  // cell of this subdomain adjacent to the face
-    if (side == 0) { ci = sd.x0; cj = sd.y0 + t; }
-    else if (side == 1) { ci = sd.x0 + sd.a - 1; cj = sd.y0 + t; }
-    else if (side == 2) { ci = sd.x0 + t; cj = sd.y0; }
-    else { ci = sd.x0 + t; cj = sd.y0 + sd.b - 1; }
-    const long long c = (long long)cj * nx + ci;
-    const double Fout = d.trace[(long long)r * d.st_face + sd.face_off + f];
-    double val;  // in +x / +y direction
-    if (iface) {
-      const DevSub& nb = subs[sd.side_nbr[side]];
-      const int nf_nb = side == 1 ? face_side_off(0, nb.a, nb.b) + t : face_side_off(2, nb.a, nb.b) + t;
-      const double Fnb = d.trace[(long long)r * d.st_face + nb.face_off + nf_nb];
-      val = 0.5 * (Fout - Fnb);
-      if (add_fn) {
-        const long long cn = side == 1 ? c + 1 : c + nx;
-        const double T = side == 1 ? d.tx[(long long)r * g.nfx() + (long long)cj * (nx + 1) + ci + 1]
-                                   : d.ty[(long long)r * g.nfy() + (long long)(cj + 1) * nx + ci];
-        val += T * (d.p_m[cb + c] - d.p_m[cb + cn]);
-      }
-    } else {
-      double out = Fout;
-      if (add_fn) {
-        // the perturbation traces carry homogeneous physical data; add F_n(p^m)
-        out += g.bc_type[side] == 0 ? 2.0 * d.kap_n[cb + c] * (d.p_m[cb + c] - g.bc_val[side])
-                                    : g.bc_val[side] * g.h;
-      }
-      val = (side == 0 || side == 2) ? -out : out;
+  int ci, cj;  // cell of sd adjacent to the face
+  if (side == 0) { ci = sd.x0; cj = sd.y0 + t; }
+  else if (side == 1) { ci = sd.x0 + sd.a - 1; cj = sd.y0 + t; }
+  else if (side == 2) { ci = sd.x0 + t; cj = sd.y0; }
+  else { ci = sd.x0 + t; cj = sd.y0 + sd.b - 1; }
+  const long long c = (long long)cj * nx + ci;
+  const double Fo = d.trace[(long long)r * d.st_face + sd.face_off + face_side_off(side, sd.a, sd.b) + t];
+  double out;  // outward from sd
+  if (sd.side_kind[side] == 1) {
+    const DevSub& nb = subs[sd.side_nbr[side]];
+    const int opp = side ^ 1;  // 0 <-> 1, 2 <-> 3: the same face seen from the neighbour
+    const double Fn = d.trace[(long long)r * d.st_face + nb.face_off + face_side_off(opp, nb.a, nb.b) + t];
+    out = 0.5 * __dsub_rn(Fo, Fn);
+    if (branch == 0) {
+      long long cn, fi;
+      double T;
+      if (side == 0) { cn = c - 1; fi = (long long)cj * (nx + 1) + ci; }
+      else if (side == 1) { cn = c + 1; fi = (long long)cj * (nx + 1) + ci + 1; }
+      else if (side == 2) { cn = c - nx; fi = (long long)cj * nx + ci; }
+      else { cn = c + nx; fi = (long long)(cj + 1) * nx + ci; }
+      T = side < 2 ? d.tx[(long long)r * g.nfx() + fi] : d.ty[(long long)r * g.nfy() + fi];
+      out = __dadd_rn(out, __dmul_rn(T, __dsub_rn(d.p_m[cb + c], d.p_m[cb + cn])));
     }
-    if (side == 0) d.ux[(long long)r * g.nfx() + (long long)cj * (nx + 1) + ci] = val;
-    else if (side == 1) d.ux[(long long)r * g.nfx() + (long long)cj * (nx + 1) + ci + 1] = val;
-    else if (side == 2) d.uy[(long long)r * g.nfy() + (long long)cj * nx + ci] = val;
-    else d.uy[(long long)r * g.nfy() + (long long)(cj + 1) * nx + ci] = val;
+  } else {
+    out = Fo;
+    // the perturbation traces carry homogeneous physical data; add F_n(p^m)
+    if (branch == 0) out += phys_flux(g, side, d.kap_n[cb + c], d.p_m[cb + c]);
   }
+  return (side == 0 || side == 2) ? -out : out;
 }
 
 }  // namespace phase

@@ -22,6 +22,7 @@
 // CTA per subdomain with the same twisted sweeps.  Factors are stored padded as
 // [b][A][A] (A = pad_width(max a)).
 #include "mpm2p_internal.cuh"
+#include "k_iface_phases.cuh"
 #include "k_local_warp.cuh"
 
 #include <algorithm>
@@ -33,16 +34,7 @@ namespace {
 
 constexpr int kSmemBudget = 200 * 1024;
 
-// Value at edge t of a side basis function kk (seg = kk / (degree+1), power = kk % (degree+1)):
-// Legendre {1, 2 xi - 1} on the segment, evaluated at the edge midpoint.
-__device__ __forceinline__ double side_basis(int kk, int t, int seg_len, int degree) {
-  const int nb = degree + 1;
-  const int seg = kk / nb, pw = kk - seg * nb;
-  if (t / seg_len != seg) return 0.0;
-  if (pw == 0) return 1.0;
-  const double xi = ((t % seg_len) + 0.5) / seg_len;
-  return 2.0 * xi - 1.0;
-}
+using phase::side_basis;
 
 // Local cell adjacent to face f, and the side / position of the face.
 __device__ __forceinline__ void face_info(const DevSub& sd, int f, int& side, int& t, int& cl) {
@@ -346,7 +338,7 @@ __device__ double basis_trace(const Grid& g, const DevSub& sd, const Stencil& S,
 // the non-homogeneous column), means (mu_hat, sub_mean).
 template <typename T>
 __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int ncol_max, int refine,
-                              double tol, int ir_max) {
+                              double tol, int ir_max, const DevNode* nodes, const int* leaf_node) {
   extern __shared__ __align__(16) char smem[];
   const int r = blockIdx.y;
   if (d.rebuild[r] != 1) return;
@@ -394,6 +386,9 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
     }
     __syncthreads();
   }
+  // Interface right-hand side (Eq. mrc2) from the non-homogeneous traces just written.
+  for (int k = threadIdx.x; k < sd.ndof; k += blockDim.x)
+    phase::element_rhs(g, d, sd, nodes[leaf_node[blockIdx.x]], r, k);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -440,7 +435,8 @@ __global__ void k_robin_factor_w(Grid g, DevState d, const DevSub* subs, int sca
 // MPM-2P local solve: A_i(kappa^m) dp = r_i with zero Robin data and homogeneous physical
 // data, using the stored factor.  Outputs the perturbation traces (fbar) and mean(dp).
 template <typename T, int A>
-__global__ void k_mpm_local_w(Grid g, DevState d, const DevSub* subs, int refine, double tol, int ir_max) {
+__global__ void k_mpm_local_w(Grid g, DevState d, const DevSub* subs, int refine, double tol, int ir_max,
+                              const DevNode* nodes, const int* leaf_node) {
   extern __shared__ __align__(16) char smem[];
   __shared__ double red[4];
   const int sidx = blockIdx.x;
@@ -451,13 +447,31 @@ __global__ void k_mpm_local_w(Grid g, DevState d, const DevSub* subs, int refine
   warp::Tables<T> t = warp::carve<T, A>(smem, m, b);
   load_kappa_cta(g, sd, d.kap_m + (long long)r * g.ncell(), t.kap);
   const double* tv = d.tvec + (long long)r * d.st_t + sd.t_off;
+  const int nx = g.nx, ny = g.ny;
+  const long long cb = (long long)r * g.ncell();
+  const double* tx = d.tx + (long long)r * g.nfx();
+  const double* ty = d.ty + (long long)r * g.nfy();
+  const double* pm = d.p_m + cb;
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
     t.ex[c] = tv[c];
     t.wE[c] = tv[m + c];
     t.wN[c] = tv[2 * m + c];
     t.sc[c] = tv[3 * m + c];
+    // fine residual r_c = q_c h^2 - sum_faces F_out(kappa^n, p^m)
     const int jl = c / a, il = c - jl * a;
-    t.B[c] = d.resid[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il];
+    const int i = sd.x0 + il, j = sd.y0 + jl;
+    const long long gc = (long long)j * nx + i;
+    const double kc = d.kap_n[cb + gc], pc = pm[gc];
+    double out = 0.0;
+    if (i > 0) out += tx[(long long)j * (nx + 1) + i] * (pc - pm[gc - 1]);
+    else out += phys_flux(g, 0, kc, pc);
+    if (i < nx - 1) out += tx[(long long)j * (nx + 1) + i + 1] * (pc - pm[gc + 1]);
+    else out += phys_flux(g, 1, kc, pc);
+    if (j > 0) out += ty[gc] * (pc - pm[gc - nx]);
+    else out += phys_flux(g, 2, kc, pc);
+    if (j < ny - 1) out += ty[gc + nx] * (pc - pm[gc + nx]);
+    else out += phys_flux(g, 3, kc, pc);
+    t.B[c] = d.q[cb + gc] * g.h * g.h - out;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < b * A; e += blockDim.x) {
@@ -482,35 +496,57 @@ __global__ void k_mpm_local_w(Grid g, DevState d, const DevSub* subs, int refine
   for (int c = threadIdx.x; c < m; c += blockDim.x) s += t.X[c];
   s = warp::cta_sum(s, red);
   if (threadIdx.x == 0) d.sub_mean[(long long)r * d.st_sub + sidx] = s / m;
+  __syncthreads();  // fbar of the whole subdomain written
+  // Interface right-hand side (Eq. mrc2) from the perturbation traces.
+  for (int k = threadIdx.x; k < sd.ndof; k += blockDim.x) phase::element_rhs(g, d, sd, nodes[leaf_node[sidx]], r, k);
 }
 
-// Downscaling (Eq. mpm_upd): Neumann problem with kappa^n and the fluxes u_bar already
-// written on the subdomain boundary faces of ux / uy; factor + solve + refinement; the
-// pressure constant makes mean(p~) equal the target; writes p~ and the interior fluxes.
+// Downscaling (Eq. mpm_upd): Neumann problem with kappa^n and u_bar on the subdomain
+// boundary faces; factor + solve + refinement; the pressure constant makes mean(p~) equal
+// the target.  u_bar is formed here from the traces of the interface solve (each
+// realisation with the branch it took), written to ux / uy on the faces this subdomain
+// owns (its physical sides, its right and top interfaces) and used as Neumann data; the
+// kernel writes p~ and the interior fluxes, and the subdomain's maximum over its cells of
+// max(total outflow, total inflow) for the CFL step.
 template <typename T, int A>
 __global__ void k_downscale_w(Grid g, DevState d, const DevSub* subs, size_t qoff, int refine, double tol,
                               int ir_max) {
   extern __shared__ __align__(16) char smem[];
   __shared__ double red[4];
+  __shared__ double ub[4 * kMaxSide];  // u_bar per boundary face (face order), +x / +y
   const int sidx = blockIdx.x;
   const int r = blockIdx.y;
   const DevSub sd = subs[sidx];
   const int a = sd.a, b = sd.b, m = a * b, nx = g.nx;
   warp::Tables<T> t = warp::carve<T, A>(smem, m, b);
   T* Q = reinterpret_cast<T*>(smem + qoff);
-  load_kappa_cta(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap);
+  double* uxw = d.ux + (long long)r * g.nfx();
+  double* uyw = d.uy + (long long)r * g.nfy();
+  const int branch = d.rebuild[r] != 0 ? 1 : 0;
+  for (int f = threadIdx.x; f < 2 * (a + b); f += blockDim.x) {
+    int side, tt, cl;
+    face_info(sd, f, side, tt, cl);
+    const double v = phase::ubar_face(g, d, subs, sd, r, side, tt, branch);
+    ub[f] = v;
+    if (sd.side_kind[side] == 1 && (side == 0 || side == 2)) continue;  // written by the neighbour
+    const int il = cl % a, jl = cl / a;
+    const int i = sd.x0 + il, j = sd.y0 + jl;
+    if (side == 0) uxw[(long long)j * (nx + 1) + i] = v;
+    else if (side == 1) uxw[(long long)j * (nx + 1) + i + 1] = v;
+    else if (side == 2) uyw[(long long)j * nx + i] = v;
+    else uyw[(long long)(j + 1) * nx + i] = v;
+  }
+  load_kappa_cta(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap);  // ends with a barrier
   warp::build<T, A>(g, sd, t, d.tx + (long long)r * g.nfx(), d.ty + (long long)r * g.nfy(), 1, refine != 0);
   warp::factor<T, A>(sd, t, Q);
-  const double* ux = d.ux + (long long)r * g.nfx();
-  const double* uy = d.uy + (long long)r * g.nfy();
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
     const int jl = c / a, il = c - jl * a;
     const int i = sd.x0 + il, j = sd.y0 + jl;
     double v = d.q[(long long)r * g.ncell() + (long long)j * nx + i] * g.h * g.h;
-    if (il == 0) v += ux[(long long)j * (nx + 1) + i];
-    if (il == a - 1) v -= ux[(long long)j * (nx + 1) + i + 1];
-    if (jl == 0) v += uy[(long long)j * nx + i];
-    if (jl == b - 1) v -= uy[(long long)(j + 1) * nx + i];
+    if (il == 0) v += ub[jl];
+    if (il == a - 1) v -= ub[b + jl];
+    if (jl == 0) v += ub[2 * b + il];
+    if (jl == b - 1) v -= ub[2 * b + a + il];
     t.B[c] = v;
   }
   __syncthreads();
@@ -519,15 +555,24 @@ __global__ void k_downscale_w(Grid g, DevState d, const DevSub* subs, size_t qof
   for (int c = threadIdx.x; c < m; c += blockDim.x) s += t.X[c];
   s = warp::cta_sum(s, red);
   const double shift = d.sub_target[(long long)r * d.st_sub + sidx] - s / m;
-  double* uxw = d.ux + (long long)r * g.nfx();
-  double* uyw = d.uy + (long long)r * g.nfy();
+  double rate = 0.0;
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
     const int jl = c / a, il = c - jl * a;
     const int i = sd.x0 + il, j = sd.y0 + jl;
     d.p_down[(long long)r * g.ncell() + (long long)j * nx + i] = t.X[c] + shift;
-    if (il < a - 1) uxw[(long long)j * (nx + 1) + i + 1] = t.wE[c] * (t.X[c] - t.X[c + 1]);
-    if (jl < b - 1) uyw[(long long)(j + 1) * nx + i] = t.wN[c] * (t.X[c] - t.X[c + a]);
+    // the four face fluxes of the cell along +x / +y, exactly as stored in ux / uy
+    const double fw = il == 0 ? ub[jl] : t.wE[c - 1] * (t.X[c - 1] - t.X[c]);
+    const double fe = il == a - 1 ? ub[b + jl] : t.wE[c] * (t.X[c] - t.X[c + 1]);
+    const double fs = jl == 0 ? ub[2 * b + il] : t.wN[c - a] * (t.X[c - a] - t.X[c]);
+    const double fn = jl == b - 1 ? ub[2 * b + a + il] : t.wN[c] * (t.X[c] - t.X[c + a]);
+    if (il < a - 1) uxw[(long long)j * (nx + 1) + i + 1] = fe;
+    if (jl < b - 1) uyw[(long long)(j + 1) * nx + i] = fn;
+    const double out = fmax(-fw, 0.0) + fmax(fe, 0.0) + fmax(-fs, 0.0) + fmax(fn, 0.0);
+    const double in = fmax(fw, 0.0) + fmax(-fe, 0.0) + fmax(fs, 0.0) + fmax(-fn, 0.0);
+    rate = fmax(rate, fmax(out, in));
   }
+  rate = warp::cta_max(rate, red);
+  if (threadIdx.x == 0) d.rate_part[(long long)r * d.st_sub + sidx] = rate;
 }
 
 template <typename K>
@@ -559,11 +604,11 @@ void robin_factor_t(const Grid& g, const DevState& d, const DevSub* subs, int ns
 
 template <typename T, int A>
 void mpm_local_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b, int refine,
-                 double tol, int ir_max, cudaStream_t st) {
+                 double tol, int ir_max, const DevNode* nodes, const int* leaf_node, cudaStream_t st) {
   size_t bytes, qoff;
   pair_geometry<T, A>(max_a, max_b, false, bytes, qoff);
   set_smem(k_mpm_local_w<T, A>, bytes);
-  k_mpm_local_w<T, A><<<dim3(nsub, g.R), 64, bytes, st>>>(g, d, subs, refine, tol, ir_max);
+  k_mpm_local_w<T, A><<<dim3(nsub, g.R), 64, bytes, st>>>(g, d, subs, refine, tol, ir_max, nodes, leaf_node);
   ++g_launches;
 }
 
@@ -596,27 +641,30 @@ void launch_robin_factor(const Grid& g, const DevState& d, const DevSub* subs, i
 }
 
 void launch_basis_solve(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
-                        int max_dof, bool fp32, double ir_tol, int ir_max, cudaStream_t st) {
+                        int max_dof, bool fp32, double ir_tol, int ir_max, const DevNode* nodes,
+                        const int* leaf_node, cudaStream_t st) {
   dim3 grid(nsub, g.R);
   const int thr = 256;
   const int A = pad_width(max_a);
   if (fp32) {
     const SmemPlan pl = plan_smem<float>(max_a, max_b, A, 32);
     set_smem(k_basis_solve<float>, pl.bytes);
-    k_basis_solve<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, A, pl.ncol, 1, ir_tol, ir_max);
+    k_basis_solve<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, A, pl.ncol, 1, ir_tol, ir_max, nodes, leaf_node);
   } else {
     const SmemPlan pl = plan_smem<double>(max_a, max_b, A, 32);
     set_smem(k_basis_solve<double>, pl.bytes);
-    k_basis_solve<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, A, pl.ncol, 0, ir_tol, ir_max);
+    k_basis_solve<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, A, pl.ncol, 0, ir_tol, ir_max, nodes,
+                                                         leaf_node);
   }
   ++g_launches;
   (void)max_dof;
 }
 
 void launch_mpm_local(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
-                      bool fp32, double ir_tol, int ir_max, cudaStream_t st) {
-  if (fp32) MPM_DISPATCH_A(mpm_local_t, float, g, d, subs, nsub, max_a, max_b, 1, ir_tol, ir_max, st);
-  else MPM_DISPATCH_A(mpm_local_t, double, g, d, subs, nsub, max_a, max_b, 0, ir_tol, ir_max, st);
+                      bool fp32, double ir_tol, int ir_max, const DevNode* nodes, const int* leaf_node,
+                      cudaStream_t st) {
+  if (fp32) MPM_DISPATCH_A(mpm_local_t, float, g, d, subs, nsub, max_a, max_b, 1, ir_tol, ir_max, nodes, leaf_node, st);
+  else MPM_DISPATCH_A(mpm_local_t, double, g, d, subs, nsub, max_a, max_b, 0, ir_tol, ir_max, nodes, leaf_node, st);
 }
 
 void launch_downscale(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,

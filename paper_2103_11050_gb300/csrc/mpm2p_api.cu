@@ -316,7 +316,7 @@ int run_build(mpm_ctx* c) {
   launch_copy_kappa_m(g, d, st);
   launch_robin_factor(g, d, c->d_subs, nsub, c->max_a, c->max_b, fp32_robin(c), st);
   launch_basis_solve(g, d, c->d_subs, nsub, c->max_a, c->max_b, c->max_dof, fp32_robin(c), c->ir_tol, c->ir_max,
-                     st);
+                     c->d_nodes, c->d_leaf_node, st);
   if (c->n_dof > 0) launch_element_matrix(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, st);
   prof_end(c, MPM_STAGE_BASIS);
   if (c->n_dof > 0) {
@@ -335,9 +335,8 @@ int run_perturbation(mpm_ctx* c) {
   const Grid& g = c->g;
   const int nsub = (int)c->subs.size();
   prof_begin(c, MPM_STAGE_PERTURB);
-  launch_residual(g, c->d, c->stream);
   launch_mpm_local(g, c->d, c->d_subs, nsub, c->max_a, c->max_b, c->fac_prec == MPM_PREC_FP32_IR_ALL, c->ir_tol,
-                   c->ir_max, c->stream);
+                   c->ir_max, c->d_nodes, c->d_leaf_node, c->stream);
   prof_end(c, MPM_STAGE_PERTURB);
   return check_launch(c);
 }
@@ -358,7 +357,6 @@ int run_interface(mpm_ctx* c) {
     return check_launch(c);
   }
   if (c->n_dof > 0) {
-    launch_element_rhs(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, st);
     for (size_t L = 1; L < c->levels.size(); ++L)
       launch_nd_up(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(), c->lev_max_nf[L],
                    c->lev_max_nsep[L], c->d_srcmap, st);
@@ -367,7 +365,6 @@ int run_interface(mpm_ctx* c) {
                      c->lev_max_nsep[L], c->lev_max_nbnd[L], c->d_pmap, st);
   }
   launch_reconstruct(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, -1, st);
-  launch_ubar(g, d, c->d_subs, nsub, -1, st);
   prof_end(c, MPM_STAGE_IFACE_SOLVE);
   return check_launch(c);
 }
@@ -380,9 +377,12 @@ int run_downscale(mpm_ctx* c) {
   return check_launch(c);
 }
 
-int run_transport(mpm_ctx* c, double cfl, int n_sub) {
+// eps_partials: the closing kappa pass also takes the partial sums of
+// ||kappa^n - kappa^m||^2 and ||kappa^m||^2 (needs a stored basis), finalised after the
+// Algorithm 1 decision by launch_eps_after_choose.
+int run_transport(mpm_ctx* c, double cfl, int n_sub, bool eps_partials) {
   prof_begin(c, MPM_STAGE_TRANSPORT);
-  launch_cfl(c->g, c->d, cfl, max_fprime(c->g.M), c->stream);
+  launch_cfl(c->g, c->d, cfl, max_fprime(c->g.M), (int)c->subs.size(), c->stream);
   double* s_home = c->d.s;
   double* fs_home = c->d.fs;
   for (int k = 0; k < n_sub; ++k) {
@@ -396,7 +396,8 @@ int run_transport(mpm_ctx* c, double cfl, int n_sub) {
                        c->stream));
     std::swap(c->d.s, c->d.s2);
   }
-  launch_mobility_eps(c->g, c->d, false, c->stream);
+  if (eps_partials) launch_mobility_partials(c->g, c->d, c->stream);
+  else launch_mobility_eps(c->g, c->d, false, c->stream);
   prof_end(c, MPM_STAGE_TRANSPORT);
   return check_launch(c);
 }
@@ -418,9 +419,10 @@ void drop_graph(mpm_ctx* c) {
     }                                                                                                     \
   } while (0)
 
-// Capture one Algorithm 1 step (lines 6-20) as a CUDA graph: transport, kappa^n, the
-// device-side decision, IF(any rebuild){basis build}, IF(any reuse){perturbation solve},
-// interface solve, downscaling, epsilon.  Kernel arguments (grid data, pointers, eta,
+// Capture one pass of the Algorithm 1 loop as a CUDA graph: transport, kappa^n with the
+// epsilon partial sums, the device-side decision and the new epsilon,
+// IF(any rebuild){basis build}, IF(any reuse){perturbation solve}, interface solve,
+// downscaling.  Kernel arguments (grid data, pointers, eta,
 // cfl, n_sub) are captured by value, so setters that change them drop the graph.
 int build_step_graph(mpm_ctx* c, double eta, double cfl, int n_sub) {
   drop_graph(c);
@@ -432,7 +434,7 @@ int build_step_graph(mpm_ctx* c, double eta, double cfl, int n_sub) {
   const long long L0 = g_launches;
   long long Lb[3] = {L0, L0, L0};
   CKG(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  int rc = run_transport(c, cfl, n_sub);
+  int rc = run_transport(c, cfl, n_sub, true);
   cudaStreamCaptureStatus stt;
   cudaGraph_t cg = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -443,6 +445,7 @@ int build_step_graph(mpm_ctx* c, double eta, double cfl, int n_sub) {
     CKG(cudaGraphConditionalHandleCreate(&h_reb, cg, 0, cudaGraphCondAssignDefault));
     CKG(cudaGraphConditionalHandleCreate(&h_mpm, cg, 0, cudaGraphCondAssignDefault));
     launch_choose_graph(c->g, c->d, eta, h_reb, h_mpm, 1, cs);
+    launch_eps_after_choose(c->g, c->d, cs);
   }
   Lb[0] = g_launches;
   for (int branch = 1; branch >= 0 && !rc; --branch) {
@@ -466,7 +469,6 @@ int build_step_graph(mpm_ctx* c, double eta, double cfl, int n_sub) {
   }
   if (!rc) rc = run_interface(c);
   if (!rc) rc = run_downscale(c);
-  if (!rc) launch_mobility_eps(c->g, c->d, true, cs);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &graph);
   c->stream = user;
@@ -532,7 +534,7 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   const size_t nc = (size_t)R * nx * ny;
   DevState& d = c->d;
   int rc = MPM_OK;
-  double** cells[] = {&d.K, &d.q, &d.s, &d.s2, &d.kap_n, &d.kap_m, &d.p_m, &d.p_down, &d.resid, &d.fs, &d.fs2};
+  double** cells[] = {&d.K, &d.q, &d.s, &d.s2, &d.kap_n, &d.kap_m, &d.p_m, &d.p_down, &d.fs, &d.fs2};
   for (double** p : cells)
     if ((rc = dalloc_t(c, c->grid_allocs, p, nc)) != MPM_OK) break;
   const int nblk = 1024;
@@ -543,7 +545,6 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.eps, (size_t)R);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.dt, (size_t)R);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.eps_part, (size_t)R * nblk * 2);
-  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.rate_part, (size_t)R * nblk);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.rebuild, (size_t)R);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.status, 1);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.ir_iters, 1);
@@ -862,6 +863,7 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   if (!rc) rc = dalloc_t(c, A, &d.sub_mean, (size_t)R * nsub);
   if (!rc) rc = dalloc_t(c, A, &d.sub_target, (size_t)R * nsub);
   if (!rc) rc = dalloc_t(c, A, &d.pm_mean, (size_t)R * nsub);
+  if (!rc) rc = dalloc_t(c, A, &d.rate_part, (size_t)R * nsub);
   if (!rc) rc = dalloc_t(c, A, &d.front, (size_t)R * f_off);
   if (!rc) rc = dalloc_t(c, A, &d.gvec, (size_t)R * v_off);
   if (!rc) rc = dalloc_t(c, A, &d.xvec, (size_t)R * v_off);
@@ -968,7 +970,7 @@ int mpm_saturation_step(mpm_ctx* c, double cfl, int n_sub, double* dt) {
   if (!(cfl > 0 && cfl <= 1) || n_sub < 1) return fail(c, MPM_ERR_ARG, "need 0 < cfl <= 1 and n_sub >= 1");
   int rc = need_ready(c, false);
   if (rc) return rc;
-  if ((rc = run_transport(c, cfl, n_sub))) return rc;
+  if ((rc = run_transport(c, cfl, n_sub, false))) return rc;
   if (dt) return copy_out(c, dt, c->d.dt, c->g.R, MPM_MEM_HOST);
   return MPM_OK;
 }
@@ -1006,9 +1008,10 @@ int mpm_step(mpm_ctx* c, double eta, double cfl, int n_sub) {
     return MPM_OK;
   }
   // eager path: the host reads the device decision to skip the branch nobody takes
-  if ((rc = run_transport(c, cfl, n_sub))) return rc;
+  if ((rc = run_transport(c, cfl, n_sub, true))) return rc;
   prof_begin(c, MPM_STAGE_EPSILON);
   launch_choose_graph(c->g, c->d, eta, 0, 0, 0, c->stream);
+  launch_eps_after_choose(c->g, c->d, c->stream);
   prof_end(c, MPM_STAGE_EPSILON);
   CK(cudaMemcpyAsync(c->h_flags, c->d.rebuild, sizeof(int) * c->g.R, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -1018,9 +1021,6 @@ int mpm_step(mpm_ctx* c, double eta, double cfl, int n_sub) {
   if (nreb < c->g.R && (rc = run_perturbation(c))) return rc;
   if ((rc = run_interface(c))) return rc;
   if ((rc = run_downscale(c))) return rc;
-  prof_begin(c, MPM_STAGE_EPSILON);
-  launch_mobility_eps(c->g, c->d, true, c->stream);
-  prof_end(c, MPM_STAGE_EPSILON);
   c->stats.steps += 1;
   return check_launch(c);
 }

@@ -2,7 +2,7 @@
 //
 // Geometry tables (per subdomain, shared by all realisations) and per-realisation
 // pools live in device memory owned by the context.  Kernels are grouped by stage:
-//   k_grid.cu   fine-grid stencils: kappa / epsilon, residual, interface fluxes, transport
+//   k_grid.cu   fine-grid stencils: kappa / epsilon, decision, CFL, transport
 //   k_local.cu  local Robin and Neumann problems (block-tridiagonal factorisation with
 //               explicit inverse pivot blocks, multi-RHS solves, FP64 refinement)
 //   k_iface.cu  interface (skeleton) system: element matrices, nested-dissection sweep
@@ -58,6 +58,14 @@ struct Grid {
   __host__ __device__ long long nfy() const { return (long long)(ny + 1) * nx; }
 };
 
+#ifdef __CUDACC__
+// Outward integrated flux of pressure p through a physical boundary face of a cell with
+// values (kc, pc) on side `side` (Dirichlet: 2 kc (pc - g); Neumann: z h).
+__device__ __forceinline__ double phys_flux(const Grid& g, int side, double kc, double pc) {
+  return g.bc_type[side] == 0 ? 2.0 * kc * (pc - g.bc_val[side]) : g.bc_val[side] * g.h;
+}
+#endif
+
 // Nested-dissection node of the interface system.  Leaves are subdomains (no
 // separator, frontal = element matrix over the subdomain's DOFs).
 struct DevNode {
@@ -80,13 +88,14 @@ struct DevLevel {
 // r * st_x + offset).
 struct DevState {
   // cells [R][ny][nx]
-  double *K, *q, *s, *s2, *kap_n, *kap_m, *p_m, *p_down, *resid;
+  double *K, *q, *s, *s2, *kap_n, *kap_m, *p_m, *p_down;
   double *fs, *fs2;    // fractional flow f(s) of s / s2
   // faces
   double *ux, *uy;
   double *tx, *ty;     // transmissibilities of kappa^n: tx [R][ny][nx+1], ty [R][ny+1][nx] (interior faces)
   // per realisation scalars
-  double *eps, *dt, *eps_part, *rate_part;
+  double *eps, *dt, *eps_part;
+  double* rate_part;  // [R][st_sub] per subdomain: max over its cells of max(outflow, inflow), by the downscaling
   int* rebuild;        // [R] branch of the current update: 1 = basis build, 0 = MPM-2P reuse
   int* status;         // [1] bitmask: 1 = a refinement did not reach its tolerance
   int* ir_iters;       // [1] max refinement sweeps used
@@ -121,18 +130,21 @@ void launch_fill_flags(const Grid& g, const DevState& d, int v, cudaStream_t st)
 void launch_choose_graph(const Grid& g, const DevState& d, double eta, cudaGraphConditionalHandle h_reb,
                          cudaGraphConditionalHandle h_mpm, int set_handles, cudaStream_t st);
 void launch_copy_kappa_m(const Grid& g, const DevState& d, cudaStream_t st);
-void launch_residual(const Grid& g, const DevState& d, cudaStream_t st);
 void launch_ubar(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int branch, cudaStream_t st);
-void launch_cfl(const Grid& g, const DevState& d, double cfl, double fmax, cudaStream_t st);
+void launch_cfl(const Grid& g, const DevState& d, double cfl, double fmax, int nsub, cudaStream_t st);
+void launch_mobility_partials(const Grid& g, const DevState& d, cudaStream_t st);
+void launch_eps_after_choose(const Grid& g, const DevState& d, cudaStream_t st);
 void launch_upwind(const Grid& g, const DevState& d, cudaStream_t st);
 
 int local_smem_limit();
 void launch_robin_factor(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
                          int max_b, bool fp32, cudaStream_t st);
 void launch_basis_solve(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
-                        int max_b, int max_dof, bool fp32, double ir_tol, int ir_max, cudaStream_t st);
+                        int max_b, int max_dof, bool fp32, double ir_tol, int ir_max, const DevNode* nodes,
+                        const int* leaf_node, cudaStream_t st);
 void launch_mpm_local(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
-                      int max_b, bool fp32, double ir_tol, int ir_max, cudaStream_t st);
+                      int max_b, bool fp32, double ir_tol, int ir_max, const DevNode* nodes, const int* leaf_node,
+                      cudaStream_t st);
 void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub,
                         const DevNode* nodes, const int* leaf_node, int branch, cudaStream_t st);
 void launch_downscale(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
