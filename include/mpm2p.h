@@ -91,13 +91,13 @@ typedef struct mpm_stats {
 
 /* Stages timed by the profiler (each is the set of kernels of one step of the path). */
 enum {
-  MPM_STAGE_TRANSPORT = 0,     /* CFL reduction, upwind substeps, kappa^n          */
-  MPM_STAGE_EPSILON = 1,       /* kappa^n, epsilon partial sums and decision         */
+  MPM_STAGE_TRANSPORT = 0,     /* upwind substeps (CFL step), kappa^n, eps sums   */
+  MPM_STAGE_EPSILON = 1,       /* decision and new epsilon (mpm_step)                */
   MPM_STAGE_BASIS = 2,         /* Robin factorisation, BF solves, element matrices   */
   MPM_STAGE_IFACE_FACTOR = 3,  /* nested-dissection factorisation of the interface   */
-  MPM_STAGE_PERTURB = 4,       /* MPM-2P residual and local solve                    */
-  MPM_STAGE_IFACE_SOLVE = 5,   /* element RHS, interface solve, traces, u_bar        */
-  MPM_STAGE_DOWNSCALE = 6,     /* Neumann downscaling (one kernel)                   */
+  MPM_STAGE_PERTURB = 4,       /* MPM-2P residual, local solve, interface RHS        */
+  MPM_STAGE_IFACE_SOLVE = 5,   /* interface sweeps and traces                        */
+  MPM_STAGE_DOWNSCALE = 6,     /* u_bar, Neumann downscaling, CFL maxima (one kernel) */
   MPM_NSTAGES = 7
 };
 
@@ -211,20 +211,26 @@ int mpm_init(mpm_ctx* ctx, double eta);
  * precision or the decomposition change. */
 int mpm_step(mpm_ctx* ctx, double eta, double cfl, int n_sub);
 
-/* Execution of the path (bitmask, default MPM_EXEC_GRAPH):
+/* Execution of the path (bitmask, default MPM_EXEC_GRAPH | MPM_EXEC_PDL):
  *  MPM_EXEC_GRAPH       mpm_step is one captured CUDA graph launch with device-side
  *                       branching; without it mpm_step runs kernel by kernel and the host
  *                       reads the decision to skip the branch no realisation takes (the
  *                       stage profiler requires this).
- *  MPM_EXEC_PERSISTENT  the interface-solve stage (element right-hand sides, every
- *                       nested-dissection level up and down, reconstruction, u_bar) is one
- *                       persistent cooperative kernel with grid-wide barriers between levels;
- *                       without it, one kernel per level (also the automatic fallback when
- *                       the device cannot launch cooperatively).  Measured slower than
- *                       the per-level kernels on the 256^2 workload (the grid-wide barriers
- *                       cost more than the launches they replace), so it is off by default.
+ *  MPM_EXEC_PDL         inside mpm_step and mpm_init, the kernels after the first one of the
+ *                       interface solve (every nested-dissection level, reconstruction, the
+ *                       downscaling) use programmatic dependent launch: each may start while
+ *                       its predecessor runs and loads its operators (factor rows, index maps)
+ *                       or, for the downscaling, factors its Neumann problems before waiting
+ *                       for the predecessor's results.
+ *  MPM_EXEC_PERSISTENT  the interface sweeps (every nested-dissection level up and down,
+ *                       reconstruction) are one persistent cooperative kernel with
+ *                       grid-wide barriers between levels; without it, one kernel per level
+ *                       (also the automatic fallback when the device cannot launch
+ *                       cooperatively).  Measured slower than the per-level kernels on the
+ *                       256^2 workload (the grid-wide barriers cost more than the launches
+ *                       they replace), so it is off by default.
  * Results are identical up to rounding order.  Drops a captured graph. */
-enum { MPM_EXEC_GRAPH = 1, MPM_EXEC_PERSISTENT = 2 };
+enum { MPM_EXEC_GRAPH = 1, MPM_EXEC_PERSISTENT = 2, MPM_EXEC_PDL = 4 };
 int mpm_set_execution(mpm_ctx* ctx, int flags);
 
 /* Copy out pressure [R][ny][nx] (which = MPM_P_*), fluxes ux [R][ny][nx+1],

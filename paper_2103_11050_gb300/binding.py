@@ -19,7 +19,7 @@ MEM_HOST, MEM_DEVICE = 0, 1
 BC_DIRICHLET, BC_NEUMANN = 0, 1
 PREC_FP64, PREC_FP32_IR, PREC_FP32_IR_ALL = 0, 1, 2
 P_MRCM, P_DOWNSCALED = 0, 1
-EXEC_GRAPH, EXEC_PERSISTENT = 1, 2
+EXEC_GRAPH, EXEC_PERSISTENT, EXEC_PDL = 1, 2, 4
 
 FUNCTIONS = [
     "mpm_create", "mpm_destroy", "mpm_last_error", "mpm_set_precision", "mpm_set_permeability",
@@ -268,8 +268,9 @@ class Context:
     def get_conductivity(self, out=None):
         return self._get(self.L.mpm_get_conductivity, (self.R, self.ny, self.nx), out)
 
-    def set_execution(self, graph=True, persistent=False):
-        self._ck(self.L.mpm_set_execution(self.h, (EXEC_GRAPH if graph else 0) | (EXEC_PERSISTENT if persistent else 0)))
+    def set_execution(self, graph=True, persistent=False, pdl=True):
+        flags = (EXEC_GRAPH if graph else 0) | (EXEC_PERSISTENT if persistent else 0) | (EXEC_PDL if pdl else 0)
+        self._ck(self.L.mpm_set_execution(self.h, flags))
 
     def profile_enable(self, on=True):
         self._ck(self.L.mpm_profile_enable(self.h, 1 if on else 0))

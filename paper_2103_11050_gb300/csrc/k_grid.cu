@@ -1,9 +1,8 @@
 // Fine-grid stencil kernels of the MPM-2P step (HBM-bound, FP64).
 //
 //  - kappa^n = lambda(s) K and the partial sums of epsilon (Section 4.1, Algorithm 1).
-//  - the Algorithm 1 decision and the new epsilon after it.
-//  - CFL time step (from per-subdomain maxima) and explicit upwind transport (Section 4,
-//    Eq. BL2D).
+//  - explicit upwind transport with its CFL time step (Section 4, Eq. BL2D), the last
+//    substep fused with kappa^n, the epsilon partial sums and the Algorithm 1 decision.
 #include "mpm2p_internal.cuh"
 
 namespace mpm {
@@ -36,18 +35,6 @@ __device__ double block_sum(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   __syncthreads();
   return v;  // valid in thread 0
-}
-
-__device__ double block_max(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-  if (w == 0)
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-  __syncthreads();
-  return v;
 }
 
 // kappa^n = lambda(s) K and the interior-face transmissibilities of kappa^n (the east and
@@ -108,21 +95,158 @@ __global__ void k_choose(Grid g, DevState d, double eta) {
   if (r < g.R) d.rebuild[r] = d.eps[r] > eta ? 1 : 0;
 }
 
-// Algorithm 1 decision for every realisation (one CTA): rebuild_r = eps_r > eta; counts
-// the branches taken and, inside a CUDA graph, sets the conditional handles of the
-// rebuild body (any realisation rebuilds) and of the MPM-2P body (any reuses).
-__global__ void k_choose_graph(Grid g, DevState d, double eta, cudaGraphConditionalHandle h_reb,
-                               cudaGraphConditionalHandle h_mpm, int set_handles) {
-  __shared__ int tot;
-  if (threadIdx.x == 0) tot = 0;
-  __syncthreads();
-  int mine = 0;
-  for (int r = threadIdx.x; r < g.R; r += blockDim.x) {
-    const int f = d.eps[r] > eta ? 1 : 0;
-    d.rebuild[r] = f;
-    mine += f;
+__global__ void k_fill_flags(Grid g, DevState d, int v) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < g.R) d.rebuild[r] = v;
+}
+
+// dt = cfl h^2 / (max f' * rate_max) with rate_max the largest total in- or outflow of a
+// cell (reduced by the downscaling); dt = 0 when nothing flows.
+__device__ __forceinline__ double cfl_dt(const Grid& g, const DevState& d, int r, double cfl, double fmax_) {
+  const double rate = d.rate_max[r];
+  return rate > 0.0 ? cfl * g.h * g.h / (fmax_ * rate) : 0.0;
+}
+
+// Explicit upwind update of cell (i, j) (Eq. BL2D): s - dt/h^2 sum_faces F_out f(s_upwind),
+// with f(s) read from fs; inflow through the boundary carries f(s_inflow) = f_in.
+__device__ __forceinline__ double upwind_cell(const Grid& g, const double* ux, const double* uy, const double* fs,
+                                              const double* s, double lam, double f_in, int i, int j) {
+  const int nx = g.nx, ny = g.ny;
+  const long long c = (long long)j * nx + i;
+  const double fc = fs[c];
+  double acc = 0.0, F;
+  F = -ux[(long long)j * (nx + 1) + i];
+  if (F > 0.0) acc += F * fc;
+  else if (F < 0.0) acc += F * (i > 0 ? fs[c - 1] : f_in);
+  F = ux[(long long)j * (nx + 1) + i + 1];
+  if (F > 0.0) acc += F * fc;
+  else if (F < 0.0) acc += F * (i < nx - 1 ? fs[c + 1] : f_in);
+  F = -uy[(long long)j * nx + i];
+  if (F > 0.0) acc += F * fc;
+  else if (F < 0.0) acc += F * (j > 0 ? fs[c - nx] : f_in);
+  F = uy[(long long)(j + 1) * nx + i];
+  if (F > 0.0) acc += F * fc;
+  else if (F < 0.0) acc += F * (j < ny - 1 ? fs[c + nx] : f_in);
+  return s[c] - lam * acc;
+}
+
+// One upwind substep s -> s2 with f(s2) -> fs2 (all substeps but the last).
+__global__ void k_upwind(Grid g, DevState d, double cfl, double fmax_) {
+  const int r = blockIdx.y;
+  const long long n = g.ncell(), base = (long long)r * n;
+  const double dt = cfl_dt(g, d, r, cfl, fmax_);
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.dt[r] = dt;
+  const double lam = dt / (g.h * g.h);
+  const double* ux = d.ux + (long long)r * g.nfx();
+  const double* uy = d.uy + (long long)r * g.nfy();
+  const double f_in = fracflow(g.s_inflow, g.M);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(c / g.nx), i = (int)(c - (long long)j * g.nx);
+    const double s_new = upwind_cell(g, ux, uy, d.fs + base, d.s + base, lam, f_in, i, j);
+    d.s2[base + c] = s_new;
+    d.fs2[base + c] = fracflow(s_new, g.M);
   }
-  atomicAdd(&tot, mine);
+}
+
+constexpr int kTX = 32, kTY = 2;  // cell tile of the last transport substep (one cell per thread; small
+                                  // tiles spread the FP64 work evenly over the SMs)
+
+// Last upwind substep fused with kappa^n (Algorithm 1: transport, then kappa^n): each CTA
+// updates a kTX x kTY tile plus its east column and north row, with kappa^n of each of these
+// cells, into shared memory, then writes s2, f(s2), kappa^n = lambda(s2) K and the east /
+// north transmissibilities of its cells.
+// decide = 1 (mpm_step): also the partial sums of ||kappa^n - kappa^m||^2, ||kappa^m||^2 per
+// CTA; the last CTA to finish takes the Algorithm 1 decision for every realisation with the
+// epsilon of the previous pass (rebuild_r = eps_r > eta), stores the new epsilon (0 where
+// the basis is rebuilt, else sqrt(num / den)), counts the branches and, in a CUDA graph
+// (set_handles), sets the conditional handles of the rebuild and MPM-2P bodies.
+__global__ void __launch_bounds__(kTX * kTY) k_upwind_kappa(Grid g, DevState d, double cfl, double fmax_, int decide,
+                                                            double eta, cudaGraphConditionalHandle h_reb,
+                                                            cudaGraphConditionalHandle h_mpm, int set_handles) {
+  __shared__ double sn[kTY + 1][kTX + 1];  // s2
+  __shared__ double sk[kTY + 1][kTX + 1];  // kappa^n of s2
+  __shared__ double sh[32];
+  __shared__ double lam_s;
+  __shared__ int last, tot;
+  const int r = blockIdx.y;
+  const int nx = g.nx, ny = g.ny;
+  const int ntx = (nx + kTX - 1) / kTX;
+  const int tx0 = (blockIdx.x % ntx) * kTX, ty0 = (blockIdx.x / ntx) * kTY;
+  const long long base = (long long)r * g.ncell();
+  if (threadIdx.x == 0) {
+    const double dt = cfl_dt(g, d, r, cfl, fmax_);
+    if (blockIdx.x == 0) d.dt[r] = dt;
+    lam_s = dt / (g.h * g.h);
+  }
+  __syncthreads();
+  const double lam = lam_s;
+  const double* ux = d.ux + (long long)r * g.nfx();
+  const double* uy = d.uy + (long long)r * g.nfy();
+  const double f_in = fracflow(g.s_inflow, g.M);
+  for (int e = threadIdx.x; e < (kTX + 1) * (kTY + 1); e += blockDim.x) {
+    const int li = e % (kTX + 1), lj = e / (kTX + 1);
+    const int i = tx0 + li, j = ty0 + lj;
+    if (i < nx && j < ny && !(li == kTX && lj == kTY)) {
+      const double v = upwind_cell(g, ux, uy, d.fs + base, d.s + base, lam, f_in, i, j);
+      sn[lj][li] = v;
+      sk[lj][li] = mobility(v, g.M) * d.K[base + (long long)j * nx + i];
+    }
+  }
+  __syncthreads();
+  const int li = threadIdx.x % kTX, lj = threadIdx.x / kTX;
+  const int i = tx0 + li, j = ty0 + lj;
+  double num = 0.0, den = 0.0;
+  if (i < nx && j < ny) {
+    const long long c = base + (long long)j * nx + i;
+    const double s_new = sn[lj][li];
+    d.s2[c] = s_new;
+    d.fs2[c] = fracflow(s_new, g.M);
+    const double kn = sk[lj][li];
+    d.kap_n[c] = kn;
+    if (i < nx - 1) d.tx[(long long)r * g.nfx() + (long long)j * (nx + 1) + i + 1] = harm(kn, sk[lj][li + 1]);
+    if (j < ny - 1) d.ty[(long long)r * g.nfy() + (long long)(j + 1) * nx + i] = harm(kn, sk[lj + 1][li]);
+    if (decide) {
+      const double km = d.kap_m[c];
+      num = (kn - km) * (kn - km);
+      den = km * km;
+    }
+  }
+  if (!decide) return;
+  num = block_sum(num, sh);
+  den = block_sum(den, sh);
+  const int nblk = gridDim.x;
+  if (threadIdx.x == 0) {
+    d.eps_part[((long long)r * nblk + blockIdx.x) * 2 + 0] = num;
+    d.eps_part[((long long)r * nblk + blockIdx.x) * 2 + 1] = den;
+    __threadfence();
+    last = atomicAdd(&d.ticket[1], 1u) == (unsigned int)(nblk * gridDim.y) - 1u;
+    tot = 0;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // one warp per realisation
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int mine = 0;
+  for (int rr = warp; rr < g.R; rr += blockDim.x >> 5) {
+    double a = 0.0, b = 0.0;
+    for (int k = lane; k < nblk; k += 32) {
+      a += __ldcg(&d.eps_part[((long long)rr * nblk + k) * 2 + 0]);
+      b += __ldcg(&d.eps_part[((long long)rr * nblk + k) * 2 + 1]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      const int f = d.eps[rr] > eta ? 1 : 0;
+      d.rebuild[rr] = f;
+      d.eps[rr] = f ? 0.0 : (b > 0.0 ? sqrt(a) / sqrt(b) : 0.0);
+      mine += f;
+    }
+  }
+  if (lane == 0 && mine) atomicAdd(&tot, mine);
   __syncthreads();
   if (threadIdx.x == 0) {
     d.counts[0] += tot;
@@ -133,82 +257,7 @@ __global__ void k_choose_graph(Grid g, DevState d, double eta, cudaGraphConditio
       d.counts[2] += tot > 0;
       d.counts[3] += tot < g.R;
     }
-  }
-}
-
-// New epsilon after the update of this step (Algorithm 1, update of epsilon): 0 where the basis was
-// rebuilt (kappa^m := kappa^n), else ||kappa^n - kappa^m|| / ||kappa^m|| from the partial sums
-// taken in the transport's mobility pass (kappa^m unchanged by an MPM-2P update).
-__global__ void k_eps_after_choose(Grid g, DevState d, int nblk) {
-  __shared__ double sh[32];
-  const int r = blockIdx.x;
-  double num = 0.0, den = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-    num += d.eps_part[((long long)r * nblk + b) * 2 + 0];
-    den += d.eps_part[((long long)r * nblk + b) * 2 + 1];
-  }
-  num = block_sum(num, sh);
-  den = block_sum(den, sh);
-  if (threadIdx.x == 0) d.eps[r] = d.rebuild[r] ? 0.0 : (den > 0.0 ? sqrt(num) / sqrt(den) : 0.0);
-}
-
-__global__ void k_fill_flags(Grid g, DevState d, int v) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < g.R) d.rebuild[r] = v;
-}
-
-__global__ void k_copy_kappa_m(Grid g, DevState d) {
-  const int r = blockIdx.y;
-  if (d.rebuild[r] != 1) return;
-  const long long n = g.ncell();
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-       c += (long long)gridDim.x * blockDim.x)
-    d.kap_m[(long long)r * n + c] = d.kap_n[(long long)r * n + c];
-}
-
-// dt per realisation from the per-subdomain maxima of max(total outflow, total inflow)
-// over cells that the downscaling wrote (rate_part[r][subdomain]).
-__global__ void k_cfl_finalize(Grid g, DevState d, int nsub, double cfl, double fmax_) {
-  __shared__ double sh[32];
-  const int r = blockIdx.x;
-  double m = 0.0;
-  for (int b = threadIdx.x; b < nsub; b += blockDim.x) m = fmax(m, d.rate_part[(long long)r * d.st_sub + b]);
-  m = block_max(m, sh);
-  if (threadIdx.x == 0) d.dt[r] = m > 0.0 ? cfl * g.h * g.h / (fmax_ * m) : 0.0;
-}
-
-// s2_c = s_c - dt/h^2 sum_faces F_out f(s_upwind); inflow through the boundary carries
-// s_inflow.  f(s) is read from fs (computed once per cell where s was produced); the
-// kernel writes f(s2) to fs2 for the next substep.
-__global__ void k_upwind(Grid g, DevState d) {
-  const int r = blockIdx.y;
-  const int nx = g.nx, ny = g.ny;
-  const long long n = g.ncell(), base = (long long)r * n;
-  const double lam = d.dt[r] / (g.h * g.h);
-  const double* ux = d.ux + (long long)r * g.nfx();
-  const double* uy = d.uy + (long long)r * g.nfy();
-  const double* fs = d.fs + base;
-  const double f_in = fracflow(g.s_inflow, g.M);
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-       c += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
-    const double fc = fs[c];
-    double acc = 0.0, F;
-    F = -ux[(long long)j * (nx + 1) + i];
-    if (F > 0.0) acc += F * fc;
-    else if (F < 0.0) acc += F * (i > 0 ? fs[c - 1] : f_in);
-    F = ux[(long long)j * (nx + 1) + i + 1];
-    if (F > 0.0) acc += F * fc;
-    else if (F < 0.0) acc += F * (i < nx - 1 ? fs[c + 1] : f_in);
-    F = -uy[(long long)j * nx + i];
-    if (F > 0.0) acc += F * fc;
-    else if (F < 0.0) acc += F * (j > 0 ? fs[c - nx] : f_in);
-    F = uy[(long long)(j + 1) * nx + i];
-    if (F > 0.0) acc += F * fc;
-    else if (F < 0.0) acc += F * (j < ny - 1 ? fs[c + nx] : f_in);
-    const double s_new = d.s[base + c] - lam * acc;
-    d.s2[base + c] = s_new;
-    d.fs2[base + c] = fracflow(s_new, g.M);
+    d.ticket[1] = 0;
   }
 }
 
@@ -231,24 +280,8 @@ void launch_mobility_eps(const Grid& g, const DevState& d, bool with_eps, cudaSt
   }
 }
 
-void launch_mobility_partials(const Grid& g, const DevState& d, cudaStream_t st) {
-  k_mobility_eps<<<dim3(cell_blocks(g), g.R), kThreads, 0, st>>>(g, d, 1);
-  ++g_launches;
-}
-
-void launch_eps_after_choose(const Grid& g, const DevState& d, cudaStream_t st) {
-  k_eps_after_choose<<<g.R, kThreads, 0, st>>>(g, d, cell_blocks(g));
-  ++g_launches;
-}
-
 void launch_choose(const Grid& g, const DevState& d, double eta, cudaStream_t st) {
   k_choose<<<(g.R + 127) / 128, 128, 0, st>>>(g, d, eta);
-  ++g_launches;
-}
-
-void launch_choose_graph(const Grid& g, const DevState& d, double eta, cudaGraphConditionalHandle h_reb,
-                         cudaGraphConditionalHandle h_mpm, int set_handles, cudaStream_t st) {
-  k_choose_graph<<<1, 256, 0, st>>>(g, d, eta, h_reb, h_mpm, set_handles);
   ++g_launches;
 }
 
@@ -257,18 +290,18 @@ void launch_fill_flags(const Grid& g, const DevState& d, int v, cudaStream_t st)
   ++g_launches;
 }
 
-void launch_copy_kappa_m(const Grid& g, const DevState& d, cudaStream_t st) {
-  k_copy_kappa_m<<<dim3(cell_blocks(g), g.R), kThreads, 0, st>>>(g, d);
+void launch_upwind(const Grid& g, const DevState& d, double cfl, double fmax_, cudaStream_t st) {
+  k_upwind<<<dim3(cell_blocks(g), g.R), kThreads, 0, st>>>(g, d, cfl, fmax_);
   ++g_launches;
 }
 
-void launch_cfl(const Grid& g, const DevState& d, double cfl, double fmax_, int nsub, cudaStream_t st) {
-  k_cfl_finalize<<<g.R, kThreads, 0, st>>>(g, d, nsub, cfl, fmax_);
-  ++g_launches;
-}
+int upwind_kappa_blocks(const Grid& g) { return ((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY); }
 
-void launch_upwind(const Grid& g, const DevState& d, cudaStream_t st) {
-  k_upwind<<<dim3(cell_blocks(g), g.R), kThreads, 0, st>>>(g, d);
+void launch_upwind_kappa(const Grid& g, const DevState& d, double cfl, double fmax_, bool decide, double eta,
+                         cudaGraphConditionalHandle h_reb, cudaGraphConditionalHandle h_mpm, bool set_handles,
+                         cudaStream_t st) {
+  k_upwind_kappa<<<dim3(upwind_kappa_blocks(g), g.R), kTX * kTY, 0, st>>>(g, d, cfl, fmax_, decide ? 1 : 0, eta,
+                                                                        h_reb, h_mpm, set_handles ? 1 : 0);
   ++g_launches;
 }
 

@@ -218,44 +218,211 @@ __global__ void k_sweep_trailing(Grid g, DevState d, const DevNode* nodes, const
 
 constexpr int kRowsPerCta = 8;  // frontal rows per CTA of the per-level solve kernels (one row per warp)
 
-// Upward solve at one level (see phase::nd_up_row); the separator right-hand side is
-// gathered from the children once per CTA into shared memory.
-__global__ void k_nd_up(Grid g, DevState d, const DevNode* nodes, const int* level_nodes, const int* srcmap) {
-  extern __shared__ double gs[];
+// Per-level solve kernels.  Each warp owns one frontal row and holds its part of the row
+// (columns lane + 32 i, i < NR) in registers; these, the node records and the index maps
+// are loaded before pdl_wait(), so under programmatic launch they overlap the previous
+// level, and only the right-hand side / solution gather waits on it.
+
+// Upward solve at one level: y_s = M_ss g_s (rows < nsep, into x) or
+// g_b = g_b + M_bs g_s (rows >= nsep), with g gathered from the children.
+template <int NR>
+__global__ void __launch_bounds__(256) k_nd_up(Grid g, DevState d, const DevNode* nodes, const int* level_nodes,
+                                               const int* srcmap) {
+  extern __shared__ __align__(16) double nd_smem[];
+  pdl_trigger();
   const int r = blockIdx.z;
   const DevNode nd = nodes[level_nodes[blockIdx.x]];
   const int row0 = blockIdx.y * kRowsPerCta;
   if (row0 >= nd.nf) return;
-  for (int k = threadIdx.x; k < nd.nsep; k += blockDim.x) gs[k] = phase::gather_g(d, nodes, nd, r, srcmap, k);
+  const int nf = nd.nf, ns = nd.nsep;
+  double* gs = nd_smem;                              // ns
+  int* i0 = reinterpret_cast<int*>(gs + ns);         // ns
+  int* i1 = i0 + ns;                                 // ns
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = row0 + warp;
+  const bool active = row < nf;
+  const long long vb = (long long)r * d.st_vec;
+  const double* Fr = d.front + (long long)r * d.st_front + nd.f_off + (long long)(active ? row : row0) * nf;
+  double fr[NR];
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    const int k = lane + 32 * i;
+    fr[i] = (active && k < ns) ? Fr[k] : 0.0;
+  }
+  const int* s0 = srcmap + nd.src_off;
+  const int* s1 = s0 + nf;
+  for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+    i0[k] = s0[k];
+    i1[k] = s1[k];
+  }
+  int own0 = -1, own1 = -1;
+  if (active && row >= ns && lane == 0) {
+    own0 = s0[row];
+    own1 = s1[row];
+  }
+  const DevNode& c0 = nodes[nd.child[0]];
+  const DevNode& c1 = nodes[nd.child[1]];
+  const double* g0 = d.gvec + vb + c0.v_off + c0.nsep;
+  const double* g1 = d.gvec + vb + c1.v_off + c1.nsep;
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int row = row0 + warp; row < min(nd.nf, row0 + kRowsPerCta); row += nw)
-    phase::nd_up_row(d, nodes, nd, r, row, srcmap, lane, gs);
+  pdl_wait();
+  for (int k = threadIdx.x; k < ns; k += blockDim.x)
+    gs[k] = (i0[k] >= 0 ? g0[i0[k]] : 0.0) + (i1[k] >= 0 ? g1[i1[k]] : 0.0);
+  __syncthreads();
+  double acc = 0.0;
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    const int k = lane + 32 * i;
+    if (k < ns) acc += fr[i] * gs[k];
+  }
+  if (active)
+    for (int k = lane + 32 * NR; k < ns; k += 32) acc += Fr[k] * gs[k];
+  acc = phase::warp_sum(acc);
+  if (active && lane == 0) {
+    if (row < ns) d.xvec[vb + nd.v_off + row] = acc;
+    else d.gvec[vb + nd.v_off + row] = ((own0 >= 0 ? g0[own0] : 0.0) + (own1 >= 0 ? g1[own1] : 0.0)) + acc;
+  }
 }
 
-// Downward solve at one level (see phase::nd_down_row / nd_down_copy).
-__global__ void k_nd_down(Grid g, DevState d, const DevNode* nodes, const int* level_nodes, const int* pmap) {
+// Downward solve at one level: x_s = y_s - M_sb x_b with x_b gathered from the parent's x;
+// the CTA of row block 0 also stores x_b in the node's own vector for its children.
+// Leaves are not visited: the reconstruction gathers their x from the parent directly.
+template <int NR>
+__global__ void __launch_bounds__(256) k_nd_down(Grid g, DevState d, const DevNode* nodes, const int* level_nodes,
+                                                 const int* pmap) {
+  extern __shared__ __align__(16) double nd_smem[];
+  pdl_trigger();
   const int r = blockIdx.z;
   const DevNode nd = nodes[level_nodes[blockIdx.x]];
   if (nd.parent < 0) return;
-  if (blockIdx.y == 0)
-    for (int k = threadIdx.x; k < nd.nbnd; k += blockDim.x) phase::nd_down_copy(d, nodes, nd, r, pmap, k);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nf = nd.nf, ns = nd.nsep, nbd = nd.nbnd;
   const int row0 = blockIdx.y * kRowsPerCta;
-  for (int row = row0 + warp; row < min(nd.nsep, row0 + kRowsPerCta); row += nw)
-    phase::nd_down_row(d, nodes, nd, r, row, pmap, lane);
+  if (row0 >= ns && blockIdx.y != 0) return;
+  double* xb = nd_smem;                              // nbd
+  int* pidx = reinterpret_cast<int*>(xb + nbd);      // nbd
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = row0 + warp;
+  const bool active = row < ns;
+  const long long vb = (long long)r * d.st_vec;
+  const double* Fr = d.front + (long long)r * d.st_front + nd.f_off + (long long)(active ? row : 0) * nf + ns;
+  double fr[NR];
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    const int k = lane + 32 * i;
+    fr[i] = (active && k < nbd) ? Fr[k] : 0.0;
+  }
+  const int* pm = pmap + nd.pmap_off;
+  for (int k = threadIdx.x; k < nbd; k += blockDim.x) pidx[k] = pm[k];
+  const double* xp = d.xvec + vb + nodes[nd.parent].v_off;
+  double* xo = d.xvec + vb + nd.v_off;
+  __syncthreads();
+  pdl_wait();
+  for (int k = threadIdx.x; k < nbd; k += blockDim.x) {
+    const double v = xp[pidx[k]];
+    xb[k] = v;
+    if (blockIdx.y == 0) xo[ns + k] = v;
+  }
+  __syncthreads();
+  double acc = 0.0;
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    const int k = lane + 32 * i;
+    if (k < nbd) acc += fr[i] * xb[k];
+  }
+  if (active)
+    for (int k = lane + 32 * NR; k < nbd; k += 32) acc += Fr[k] * xb[k];
+  acc = phase::warp_sum(acc);
+  if (active && lane == 0) xo[row] -= acc;
 }
 
-// Reconstruction of traces / p^m (phase::reconstruct) for the realisations of one branch,
-// or (branch = -1) for every realisation with its own branch.
-__global__ void k_reconstruct(Grid g, DevState d, const DevSub* subs, const DevNode* nodes, const int* leaf_node,
-                              int branch) {
-  __shared__ double cs[4 * 4 * kMaxSide];
+// Reconstruction from the interface solution c of one subdomain per CTA (c gathered from the
+// leaf's parent vector): the one-sided traces F = Fbar + F_hat c, one face per warp at a time
+// (rows of F_hat are contiguous), then the target mean of the downscaled pressure, and at a
+// rebuild the MRCM-level pressure p^m = pbar + P_hat c (P_hat stored column by column):
+//   rebuild: target = mean(p^m);  MPM-2P: target = mean(p^m) + mean(dpbar) + mu_hat . dc.
+// branch >= 0 restricts the launch to the realisations that took that branch.
+template <int NR>
+__global__ void __launch_bounds__(256) k_reconstruct(Grid g, DevState d, const DevSub* subs, const DevNode* nodes,
+                                                     const int* leaf_node, const int* pmap, int branch) {
+  extern __shared__ __align__(16) double nd_smem[];
   __shared__ double red[32];
-  const int r = blockIdx.y;
+  pdl_trigger();
+  const int sidx = blockIdx.x, r = blockIdx.y;
   const int br = d.rebuild[r];
   if (branch >= 0 && br != branch) return;
-  phase::reconstruct(g, d, subs, nodes, leaf_node, blockIdx.x, r, br, cs, red);
+  const DevSub& sd = subs[sidx];
+  const int a = sd.a, b = sd.b, m = a * b, nd = sd.ndof, nface = 2 * (a + b);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double* cs = nd_smem;                              // nd
+  int* pidx = reinterpret_cast<int*>(cs + nd);       // nd
+  const double* xp = nullptr;
+  if (nd > 0) {
+    const DevNode& leaf = nodes[leaf_node[sidx]];
+    xp = d.xvec + (long long)r * d.st_vec + nodes[leaf.parent].v_off;
+    const int* pm = pmap + leaf.pmap_off;
+    for (int l = threadIdx.x; l < nd; l += blockDim.x) pidx[l] = pm[l];
+  }
+  __syncthreads();
+  pdl_wait();
+  for (int l = threadIdx.x; l < nd; l += blockDim.x) cs[l] = xp[pidx[l]];
+  __syncthreads();
+  const double* trb = d.tr + (long long)r * d.st_tr + sd.tr_off;
+  const double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
+  double* trace = d.trace + (long long)r * d.st_face + sd.face_off;
+  for (int f0 = warp; f0 < nface; f0 += 2 * nw) {  // two faces per warp per pass
+    const int f1 = f0 + nw;
+    const bool two = f1 < nface;
+    const double* t0 = trb + (long long)f0 * nd;
+    const double* t1 = trb + (long long)(two ? f1 : f0) * nd;
+    double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      const int k = lane + 32 * i;
+      if (k < nd) {
+        acc0 += t0[k] * cs[k];
+        acc1 += t1[k] * cs[k];
+      }
+    }
+    for (int k = lane + 32 * NR; k < nd; k += 32) {
+      acc0 += t0[k] * cs[k];
+      acc1 += t1[k] * cs[k];
+    }
+    acc0 = phase::warp_sum(acc0);
+    acc1 = phase::warp_sum(acc1);
+    if (lane == 0) {
+      trace[f0] = fbar[f0] + acc0;
+      if (two) trace[f1] = fbar[f1] + acc1;
+    }
+  }
+  double part = 0.0;
+  if (br == 1) {
+    const double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;  // [nd + 1][m]
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+      double v = pf[(long long)nd * m + c];
+      for (int l = 0; l < nd; ++l) v += pf[(long long)l * m + c] * cs[l];
+      const int jl = c / a, il = c - jl * a;
+      d.p_m[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il] = v;
+      part += v;
+    }
+  } else {
+    const double* muh = d.mu_hat + (long long)r * d.st_dof + sd.dof_off;
+    for (int l = threadIdx.x; l < nd; l += blockDim.x) part += muh[l] * cs[l];
+    part *= m;
+  }
+  part = phase::warp_sum(part);
+  if (lane == 0) red[warp] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w];
+    const long long si = (long long)r * d.st_sub + sidx;
+    if (br == 1) {
+      d.pm_mean[si] = s / m;
+      d.sub_target[si] = s / m;
+    } else {
+      d.sub_target[si] = d.pm_mean[si] + (d.sub_mean[si] * m + s) / m;
+    }
+  }
 }
 
 // The whole interface-solve stage in one persistent cooperative launch: the upward sweep
@@ -318,12 +485,6 @@ __global__ void __launch_bounds__(256) k_iface_coop(Grid g, DevState d, const De
 
 }  // namespace
 
-void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub, const DevNode* nodes,
-                        const int* leaf_node, int branch, cudaStream_t st) {
-  k_reconstruct<<<dim3(nsub, g.R), 128, 0, st>>>(g, d, subs, nodes, leaf_node, branch);
-  ++g_launches;
-}
-
 int iface_coop_blocks() {
   int dev = 0, sms = 0, per_sm = 0, coop = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -376,19 +537,48 @@ void launch_nd_factor_level(const Grid& g, const DevState& d, const DevNode* nod
   }
 }
 
+namespace {
+// Register chunks per lane for a row of n columns: smallest power of two >= n / 32, at most
+// 16 (longer rows finish with a loop over global memory).
+int row_chunks(int n) {
+  const int q = (n + 31) / 32;
+  return q <= 1 ? 1 : q <= 2 ? 2 : q <= 4 ? 4 : q <= 8 ? 8 : 16;
+}
+}  // namespace
+
+#define MPM_DISPATCH_NR(KERNEL, nr, ...)                        \
+  do {                                                          \
+    switch (nr) {                                               \
+      case 1: launch_ex(KERNEL<1>, __VA_ARGS__); break;         \
+      case 2: launch_ex(KERNEL<2>, __VA_ARGS__); break;         \
+      case 4: launch_ex(KERNEL<4>, __VA_ARGS__); break;         \
+      case 8: launch_ex(KERNEL<8>, __VA_ARGS__); break;         \
+      default: launch_ex(KERNEL<16>, __VA_ARGS__); break;       \
+    }                                                           \
+  } while (0)
+
 void launch_nd_up(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
-                  int max_nf, int max_nsep, const int* srcmap, cudaStream_t st) {
-  k_nd_up<<<dim3(nlev, (max_nf + kRowsPerCta - 1) / kRowsPerCta, g.R), 256, (size_t)max_nsep * sizeof(double), st>>>(
-      g, d, nodes, level_nodes, srcmap);
-  ++g_launches;
+                  int max_nf, int max_nsep, const int* srcmap, bool pdl, cudaStream_t st) {
+  const dim3 grid(nlev, (max_nf + kRowsPerCta - 1) / kRowsPerCta, g.R);
+  const size_t smem = (size_t)max_nsep * (sizeof(double) + 2 * sizeof(int));
+  MPM_DISPATCH_NR(k_nd_up, row_chunks(max_nsep), grid, dim3(256), smem, st, pdl, g, d, nodes, level_nodes, srcmap);
 }
 
 void launch_nd_down(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
-                    int max_nsep, int max_nbnd, const int* pmap, cudaStream_t st) {
-  const int ny = max_nsep > 0 ? (max_nsep + kRowsPerCta - 1) / kRowsPerCta : 1;
-  k_nd_down<<<dim3(nlev, ny, g.R), 256, (size_t)(max_nbnd > 0 ? max_nbnd : 1) * sizeof(double), st>>>(
-      g, d, nodes, level_nodes, pmap);
-  ++g_launches;
+                    int max_nsep, int max_nbnd, const int* pmap, bool pdl, cudaStream_t st) {
+  const dim3 grid(nlev, max_nsep > 0 ? (max_nsep + kRowsPerCta - 1) / kRowsPerCta : 1, g.R);
+  const size_t smem = (size_t)(max_nbnd > 0 ? max_nbnd : 1) * (sizeof(double) + sizeof(int));
+  MPM_DISPATCH_NR(k_nd_down, row_chunks(max_nbnd), grid, dim3(256), smem, st, pdl, g, d, nodes, level_nodes, pmap);
+}
+
+void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_face, int max_dof,
+                        const DevNode* nodes, const int* leaf_node, const int* pmap, int branch, bool pdl,
+                        cudaStream_t st) {
+  (void)max_face;
+  const dim3 grid(nsub, g.R);
+  const size_t smem = (size_t)(max_dof > 0 ? max_dof : 1) * (sizeof(double) + sizeof(int));
+  MPM_DISPATCH_NR(k_reconstruct, row_chunks(max_dof), grid, dim3(256), smem, st, pdl, g, d, subs, nodes, leaf_node,
+                  pmap, branch);
 }
 
 }  // namespace mpm

@@ -148,8 +148,8 @@ __device__ inline void reconstruct(const Grid& g, const DevState& d, const DevSu
   if (branch == 1) {
     const double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
-      double v = pf[(long long)c * (nd + 1) + nd];
-      for (int l = 0; l < nd; ++l) v += pf[(long long)c * (nd + 1) + l] * cs[l];
+      double v = pf[(long long)nd * m + c];
+      for (int l = 0; l < nd; ++l) v += pf[(long long)l * m + c] * cs[l];
       const int jl = c / a, il = c - jl * a;
       d.p_m[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il] = v;
       part += v;

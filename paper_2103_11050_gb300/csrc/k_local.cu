@@ -349,7 +349,7 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
   Carve<T> cv = carve<T>(smem, a, b, A, ncol_max);
   load_robin<T>(d, sd, r, cv, g, A);
   double* tr = d.tr + (long long)r * d.st_tr + sd.tr_off;       // [nface][ndof]
-  double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;       // [m][ndof+1]
+  double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;       // [ndof+1][m]
   double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
   double* muh = d.mu_hat + (long long)r * d.st_dof + sd.dof_off;
   for (int c0 = 0; c0 < ntot; c0 += ncol_max) {
@@ -364,8 +364,8 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
     solve_refined<T>(sd, cv.S, cv.th, cv.Q, A, cv.B, cv.X, cv.Rr, cv.Zw, cv.Ww, ncol, refine != 0, 1e-3 * tol, tol,
                      ir_max, cv.colmax, d.status, d.ir_iters);
     for (int e = threadIdx.x; e < m * ncol; e += blockDim.x) {
-      const int c = e / ncol, col = e - c * ncol;
-      pf[(long long)c * ntot + c0 + col] = cv.X[e];
+      const int col = e / m, c = e - col * m;
+      pf[(long long)(c0 + col) * m + c] = cv.X[c * ncol + col];
     }
     for (int e = threadIdx.x; e < nface * ncol; e += blockDim.x) {
       const int f = e / ncol, col = e - f * ncol, bcol = c0 + col;
@@ -403,7 +403,8 @@ __device__ __forceinline__ void load_kappa_cta(const Grid& g, const DevSub& sd, 
 }
 
 // Robin factorisation at kappa^n (rebuild realisations), stored for reuse by MPM-2P:
-// twisted Q blocks [b][A][A] (factor type), [ex, wE, wN, sc] (FP64) and beta_hat per face.
+// twisted Q blocks [b][A][A] (factor type), [ex, wE, wN, sc] (FP64) and beta_hat per face;
+// also stores kappa^m := kappa^n on the subdomain's cells.
 template <typename T, int A>
 __global__ void k_robin_factor_w(Grid g, DevState d, const DevSub* subs, int scale) {
   extern __shared__ __align__(16) char smem[];
@@ -414,6 +415,10 @@ __global__ void k_robin_factor_w(Grid g, DevState d, const DevSub* subs, int sca
   const int m = sd.a * sd.b;
   warp::Tables<T> t = warp::carve<T, A>(smem, m, sd.b);
   load_kappa_cta(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap);
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {  // kappa^m := kappa^n on this subdomain
+    const int jl = c / sd.a, il = c - jl * sd.a;
+    d.kap_m[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il] = t.kap[c];
+  }
   warp::build<T, A>(g, sd, t, d.tx + (long long)r * g.nfx(), d.ty + (long long)r * g.nfy(), 0, scale != 0);
   T* Qg = reinterpret_cast<T*>(d.fac) + (long long)r * d.st_fac + sd.q_off;
   warp::factor<T, A>(sd, t, Qg);
@@ -501,25 +506,76 @@ __global__ void k_mpm_local_w(Grid g, DevState d, const DevSub* subs, int refine
   for (int k = threadIdx.x; k < sd.ndof; k += blockDim.x) phase::element_rhs(g, d, sd, nodes[leaf_node[sidx]], r, k);
 }
 
-// Downscaling (Eq. mpm_upd): Neumann problem with kappa^n and u_bar on the subdomain
-// boundary faces; factor + solve + refinement; the pressure constant makes mean(p~) equal
-// the target.  u_bar is formed here from the traces of the interface solve (each
-// realisation with the branch it took), written to ux / uy on the faces this subdomain
-// owns (its physical sides, its right and top interfaces) and used as Neumann data; the
-// kernel writes p~ and the interior fluxes, and the subdomain's maximum over its cells of
-// max(total outflow, total inflow) for the CFL step.
+// Downscaling factorisation (Eq. mpm_upd, left-hand side): the pinned Neumann operator of
+// kappa^n of every subdomain, factored (twisted block factorisation) into nfac, with its
+// FP64 stencil [ex, wE, wN, sc] into ntvec.  It depends only on kappa^n, so the step runs it
+// on a side stream concurrently with the perturbation and interface solves.
+template <typename T, int A>
+__global__ void k_downscale_factor_w(Grid g, DevState d, const DevSub* subs, int scale) {
+  extern __shared__ __align__(16) char smem[];
+  const int sidx = blockIdx.x;
+  const int r = blockIdx.y;
+  const DevSub sd = subs[sidx];
+  const int m = sd.a * sd.b;
+  warp::Tables<T> t = warp::carve<T, A>(smem, m, sd.b);
+  load_kappa_cta(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap);
+  warp::build<T, A>(g, sd, t, d.tx + (long long)r * g.nfx(), d.ty + (long long)r * g.nfy(), 1, scale != 0);
+  warp::factor<T, A>(sd, t, reinterpret_cast<T*>(d.nfac) + (long long)r * d.st_fac + sd.q_off);
+  double* tv = d.ntvec + (long long)r * d.st_t + sd.t_off;
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    tv[c] = t.ex[c];
+    tv[m + c] = t.wE[c];
+    tv[2 * m + c] = t.wN[c];
+    tv[3 * m + c] = t.sc[c];
+  }
+}
+
+// Downscaling solve (Eq. mpm_upd) with the factor of k_downscale_factor_w: u_bar is formed
+// from the traces of the interface solve (each realisation with the branch it took), written
+// to ux / uy on the faces this subdomain owns (its physical sides, its right and top
+// interfaces) and used as Neumann data; solve + FP64 refinement; the pressure constant
+// makes mean(p~) equal the target.  Writes p~, the interior fluxes and the subdomain's
+// maximum over its cells of max(total outflow, total inflow); the last block to finish
+// reduces these maxima per realisation into rate_max (CFL step).  The factor and stencil
+// are loaded before pdl_wait() (they come from a stream joined before the launch).
 template <typename T, int A>
 __global__ void k_downscale_w(Grid g, DevState d, const DevSub* subs, size_t qoff, int refine, double tol,
                               int ir_max) {
   extern __shared__ __align__(16) char smem[];
   __shared__ double red[4];
   __shared__ double ub[4 * kMaxSide];  // u_bar per boundary face (face order), +x / +y
+  __shared__ int last;
   const int sidx = blockIdx.x;
   const int r = blockIdx.y;
   const DevSub sd = subs[sidx];
   const int a = sd.a, b = sd.b, m = a * b, nx = g.nx;
   warp::Tables<T> t = warp::carve<T, A>(smem, m, b);
   T* Q = reinterpret_cast<T*>(smem + qoff);
+  {
+    const float4* src = reinterpret_cast<const float4*>(reinterpret_cast<const T*>(d.nfac) +
+                                                        (long long)r * d.st_fac + sd.q_off);
+    float4* dst = reinterpret_cast<float4*>(Q);
+    const int n4 = (int)((size_t)b * A * A * sizeof(T) / sizeof(float4));
+    for (int e = threadIdx.x; e < n4; e += blockDim.x) dst[e] = src[e];
+    const double* tv = d.ntvec + (long long)r * d.st_t + sd.t_off;
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+      t.ex[c] = tv[c];
+      t.wE[c] = tv[m + c];
+      t.wN[c] = tv[2 * m + c];
+      t.sc[c] = tv[3 * m + c];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < b * A; e += blockDim.x) {
+    const int j = e / A, i = e - j * A;
+    t.th[e] = (i < a && j < b - 1) ? T(t.wN[j * a + i] * t.sc[j * a + i] * t.sc[j * a + i + a]) : T(0);
+  }
+  const double* qc = d.q + (long long)r * g.ncell();
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    const int jl = c / a, il = c - jl * a;
+    t.B[c] = qc[(long long)(sd.y0 + jl) * nx + sd.x0 + il] * g.h * g.h;
+  }
+  pdl_wait();
   double* uxw = d.ux + (long long)r * g.nfx();
   double* uyw = d.uy + (long long)r * g.nfy();
   const int branch = d.rebuild[r] != 0 ? 1 : 0;
@@ -536,13 +592,10 @@ __global__ void k_downscale_w(Grid g, DevState d, const DevSub* subs, size_t qof
     else if (side == 2) uyw[(long long)j * nx + i] = v;
     else uyw[(long long)(j + 1) * nx + i] = v;
   }
-  load_kappa_cta(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap);  // ends with a barrier
-  warp::build<T, A>(g, sd, t, d.tx + (long long)r * g.nfx(), d.ty + (long long)r * g.nfy(), 1, refine != 0);
-  warp::factor<T, A>(sd, t, Q);
+  __syncthreads();
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
     const int jl = c / a, il = c - jl * a;
-    const int i = sd.x0 + il, j = sd.y0 + jl;
-    double v = d.q[(long long)r * g.ncell() + (long long)j * nx + i] * g.h * g.h;
+    double v = t.B[c];
     if (il == 0) v += ub[jl];
     if (il == a - 1) v -= ub[b + jl];
     if (jl == 0) v += ub[2 * b + il];
@@ -572,7 +625,25 @@ __global__ void k_downscale_w(Grid g, DevState d, const DevSub* subs, size_t qof
     rate = fmax(rate, fmax(out, in));
   }
   rate = warp::cta_max(rate, red);
-  if (threadIdx.x == 0) d.rate_part[(long long)r * d.st_sub + sidx] = rate;
+  // last-block reduction of the per-subdomain maxima (threadfence-reduction pattern)
+  if (threadIdx.x == 0) {
+    d.rate_part[(long long)r * d.st_sub + sidx] = rate;
+    __threadfence();
+    const unsigned int nblk = gridDim.x * gridDim.y;
+    last = atomicAdd(&d.ticket[0], 1u) == nblk - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int nsub = gridDim.x;
+  for (int rr = 0; rr < (int)gridDim.y; ++rr) {
+    double mx = 0.0;
+    for (int k = threadIdx.x; k < nsub; k += blockDim.x)
+      mx = fmax(mx, __ldcg(&d.rate_part[(long long)rr * d.st_sub + k]));
+    mx = warp::cta_max(mx, red);
+    if (threadIdx.x == 0) d.rate_max[rr] = mx;
+  }
+  if (threadIdx.x == 0) d.ticket[0] = 0;
 }
 
 template <typename K>
@@ -613,13 +684,22 @@ void mpm_local_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub,
 }
 
 template <typename T, int A>
+void downscale_factor_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
+                        cudaStream_t st) {
+  size_t bytes, qoff;
+  pair_geometry<T, A>(max_a, max_b, false, bytes, qoff);
+  set_smem(k_downscale_factor_w<T, A>, bytes);
+  k_downscale_factor_w<T, A><<<dim3(nsub, g.R), 64, bytes, st>>>(g, d, subs, std::is_same<T, float>::value ? 1 : 0);
+  ++g_launches;
+}
+
+template <typename T, int A>
 void downscale_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b, int refine,
-                 double tol, int ir_max, cudaStream_t st) {
+                 double tol, int ir_max, bool pdl, cudaStream_t st) {
   size_t bytes, qoff;
   pair_geometry<T, A>(max_a, max_b, true, bytes, qoff);
   set_smem(k_downscale_w<T, A>, bytes);
-  k_downscale_w<T, A><<<dim3(nsub, g.R), 64, bytes, st>>>(g, d, subs, qoff, refine, tol, ir_max);
-  ++g_launches;
+  launch_ex(k_downscale_w<T, A>, dim3(nsub, g.R), dim3(64), bytes, st, pdl, g, d, subs, qoff, refine, tol, ir_max);
 }
 
 }  // namespace
@@ -667,10 +747,16 @@ void launch_mpm_local(const Grid& g, const DevState& d, const DevSub* subs, int 
   else MPM_DISPATCH_A(mpm_local_t, double, g, d, subs, nsub, max_a, max_b, 0, ir_tol, ir_max, nodes, leaf_node, st);
 }
 
+void launch_downscale_factor(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
+                             bool fp32, cudaStream_t st) {
+  if (fp32) MPM_DISPATCH_A(downscale_factor_t, float, g, d, subs, nsub, max_a, max_b, st);
+  else MPM_DISPATCH_A(downscale_factor_t, double, g, d, subs, nsub, max_a, max_b, st);
+}
+
 void launch_downscale(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
-                      bool fp32, double ir_tol, int ir_max, cudaStream_t st) {
-  if (fp32) MPM_DISPATCH_A(downscale_t, float, g, d, subs, nsub, max_a, max_b, 1, ir_tol, ir_max, st);
-  else MPM_DISPATCH_A(downscale_t, double, g, d, subs, nsub, max_a, max_b, 0, ir_tol, ir_max, st);
+                      bool fp32, double ir_tol, int ir_max, bool pdl, cudaStream_t st) {
+  if (fp32) MPM_DISPATCH_A(downscale_t, float, g, d, subs, nsub, max_a, max_b, 1, ir_tol, ir_max, pdl, st);
+  else MPM_DISPATCH_A(downscale_t, double, g, d, subs, nsub, max_a, max_b, 0, ir_tol, ir_max, pdl, st);
 }
 
 }  // namespace mpm

@@ -36,7 +36,7 @@ struct mpm_ctx {
   int ncx = 0, ncy = 0;
   std::vector<int> col_w, row_h;
   std::vector<DevSub> subs;
-  int max_a = 0, max_b = 0, max_dof = 0, n_dof = 0, n_hat = 0;
+  int max_a = 0, max_b = 0, max_dof = 0, max_face = 0, n_dof = 0, n_hat = 0;
   // nested dissection
   std::vector<DevNode> nodes;
   std::vector<int> leaf_node;
@@ -65,12 +65,21 @@ struct mpm_ctx {
   // CUDA graph of one Algorithm 1 step (conditional bodies for the two branches)
   bool use_graph = true;
   bool use_coop = false;  // interface stage as one persistent cooperative kernel (measured slower)
-  bool graph_valid = false;
+  bool use_pdl = true;    // programmatic dependent launch along the interface-solve chain
+  // The saturation (and f(s)) live in two buffers that swap at every transport substep; a
+  // graph reads and writes fixed buffers, so one graph is kept per buffer parity (slot 0:
+  // the current saturation is in s_buf0).
+  double* s_buf0 = nullptr;
+  bool graph_valid[2] = {false, false};
   double g_eta = 0.0, g_cfl = 0.0;
   int g_nsub = 0;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t graph_exec = nullptr;
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   cudaStream_t cap_stream = nullptr, body_stream = nullptr;
+  // side stream of the downscaling factorisation (forked after kappa^n, joined before the
+  // downscaling solve)
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // stage profiler
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -313,7 +322,6 @@ int run_build(mpm_ctx* c) {
   cudaStream_t st = c->stream;
   const int nsub = (int)c->subs.size();
   prof_begin(c, MPM_STAGE_BASIS);
-  launch_copy_kappa_m(g, d, st);
   launch_robin_factor(g, d, c->d_subs, nsub, c->max_a, c->max_b, fp32_robin(c), st);
   launch_basis_solve(g, d, c->d_subs, nsub, c->max_a, c->max_b, c->max_dof, fp32_robin(c), c->ir_tol, c->ir_max,
                      c->d_nodes, c->d_leaf_node, st);
@@ -341,6 +349,10 @@ int run_perturbation(mpm_ctx* c) {
   return check_launch(c);
 }
 
+// Interface solve: up and down sweeps over the nested-dissection levels, reconstruction.
+// The first sweep kernel is fully ordered after what precedes it; the rest of the chain
+// (and the downscaling after it, see run_downscale) uses programmatic dependent launch when
+// enabled.
 int run_interface(mpm_ctx* c) {
   const Grid& g = c->g;
   DevState& d = c->d;
@@ -356,58 +368,93 @@ int run_interface(mpm_ctx* c) {
     if (e != cudaSuccess) return fail(c, MPM_ERR_CUDA, "persistent interface kernel: %s", cudaGetErrorString(e));
     return check_launch(c);
   }
+  bool chained = false;
   if (c->n_dof > 0) {
-    for (size_t L = 1; L < c->levels.size(); ++L)
+    for (size_t L = 1; L < c->levels.size(); ++L) {
       launch_nd_up(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(), c->lev_max_nf[L],
-                   c->lev_max_nsep[L], c->d_srcmap, st);
-    for (int L = (int)c->levels.size() - 1; L >= 0; --L)
+                   c->lev_max_nsep[L], c->d_srcmap, chained && c->use_pdl, st);
+      chained = true;
+    }
+    for (int L = (int)c->levels.size() - 1; L >= 1; --L)
       launch_nd_down(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(),
-                     c->lev_max_nsep[L], c->lev_max_nbnd[L], c->d_pmap, st);
+                     c->lev_max_nsep[L], c->lev_max_nbnd[L], c->d_pmap, c->use_pdl, st);
   }
-  launch_reconstruct(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, -1, st);
+  launch_reconstruct(g, d, c->d_subs, nsub, c->max_face, c->max_dof, c->d_nodes, c->d_leaf_node, c->d_pmap, -1,
+                     chained && c->use_pdl, st);
   prof_end(c, MPM_STAGE_IFACE_SOLVE);
   return check_launch(c);
 }
 
-int run_downscale(mpm_ctx* c) {
+// Downscaling factorisation of kappa^n on the side stream (fork): it overlaps whatever the
+// main stream runs until join_downscale_factor.
+int fork_downscale_factor(mpm_ctx* c) {
+  CK(cudaEventRecord(c->ev_fork, c->stream));
+  CK(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
+  launch_downscale_factor(c->g, c->d, c->d_subs, (int)c->subs.size(), c->max_a, c->max_b, fp32(c), c->side_stream);
+  CK(cudaEventRecord(c->ev_join, c->side_stream));
+  return check_launch(c);
+}
+
+int join_downscale_factor(mpm_ctx* c) {
+  CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  return MPM_OK;
+}
+
+// Downscaling solve.  after_interface: launched right behind run_interface's chain, so it
+// may use programmatic dependent launch (before waiting it reads only the factor, joined
+// before the launch).  forked: the factor was forked by fork_downscale_factor; otherwise it
+// is computed here on the main stream.
+int run_downscale(mpm_ctx* c, bool after_interface, bool forked) {
   prof_begin(c, MPM_STAGE_DOWNSCALE);
+  if (forked) {
+    int rc = join_downscale_factor(c);
+    if (rc) return rc;
+  } else {
+    launch_downscale_factor(c->g, c->d, c->d_subs, (int)c->subs.size(), c->max_a, c->max_b, fp32(c), c->stream);
+  }
   launch_downscale(c->g, c->d, c->d_subs, (int)c->subs.size(), c->max_a, c->max_b, fp32(c), c->ir_tol, c->ir_max,
-                   c->stream);
+                   after_interface && forked && c->use_pdl, c->stream);
   prof_end(c, MPM_STAGE_DOWNSCALE);
   return check_launch(c);
 }
 
-// eps_partials: the closing kappa pass also takes the partial sums of
-// ||kappa^n - kappa^m||^2 and ||kappa^m||^2 (needs a stored basis), finalised after the
-// Algorithm 1 decision by launch_eps_after_choose.
-int run_transport(mpm_ctx* c, double cfl, int n_sub, bool eps_partials) {
+// n_sub upwind substeps; the last one is fused with kappa^n (and, with decide, with the
+// epsilon partial sums and the Algorithm 1 decision, see launch_upwind_kappa; needs a stored
+// basis).  The saturation buffers swap at every substep: d.s is the new saturation after.
+int run_transport(mpm_ctx* c, double cfl, int n_sub, bool decide, double eta, cudaGraphConditionalHandle h_reb,
+                  cudaGraphConditionalHandle h_mpm, bool set_handles) {
   prof_begin(c, MPM_STAGE_TRANSPORT);
-  launch_cfl(c->g, c->d, cfl, max_fprime(c->g.M), (int)c->subs.size(), c->stream);
-  double* s_home = c->d.s;
-  double* fs_home = c->d.fs;
+  const double fmax_ = max_fprime(c->g.M);
   for (int k = 0; k < n_sub; ++k) {
-    launch_upwind(c->g, c->d, c->stream);
+    if (k + 1 < n_sub) launch_upwind(c->g, c->d, cfl, fmax_, c->stream);
+    else launch_upwind_kappa(c->g, c->d, cfl, fmax_, decide, eta, h_reb, h_mpm, set_handles, c->stream);
     std::swap(c->d.s, c->d.s2);
     std::swap(c->d.fs, c->d.fs2);
   }
-  if (c->d.fs != fs_home) std::swap(c->d.fs, c->d.fs2);  // f(s) is recomputed below from the final s
-  if (c->d.s != s_home) {  // odd substep count: bring the result home (graph replays read s_home)
-    CK(cudaMemcpyAsync(s_home, c->d.s, sizeof(double) * c->g.R * c->g.ncell(), cudaMemcpyDeviceToDevice,
-                       c->stream));
-    std::swap(c->d.s, c->d.s2);
-  }
-  if (eps_partials) launch_mobility_partials(c->g, c->d, c->stream);
-  else launch_mobility_eps(c->g, c->d, false, c->stream);
   prof_end(c, MPM_STAGE_TRANSPORT);
   return check_launch(c);
 }
 
 void drop_graph(mpm_ctx* c) {
-  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-  if (c->graph) cudaGraphDestroy(c->graph);
-  c->graph_exec = nullptr;
-  c->graph = nullptr;
-  c->graph_valid = false;
+  for (int k = 0; k < 2; ++k) {
+    if (c->graph_exec[k]) cudaGraphExecDestroy(c->graph_exec[k]);
+    if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
+    c->graph_exec[k] = nullptr;
+    c->graph[k] = nullptr;
+    c->graph_valid[k] = false;
+  }
+}
+
+int graph_slot(const mpm_ctx* c) { return c->d.s == c->s_buf0 ? 0 : 1; }
+
+void destroy_streams(mpm_ctx* c) {
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->body_stream) cudaStreamDestroy(c->body_stream);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  c->cap_stream = c->body_stream = c->side_stream = nullptr;
+  c->ev_fork = c->ev_join = nullptr;
 }
 
 #define CKG(call)                                                                                         \
@@ -415,38 +462,43 @@ void drop_graph(mpm_ctx* c) {
     cudaError_t e_ = (call);                                                                              \
     if (e_ != cudaSuccess) {                                                                              \
       c->stream = user;                                                                                   \
+      c->d = saved;                                                                                       \
       return fail(c, MPM_ERR_CUDA, "graph capture: %s: %s", #call, cudaGetErrorString(e_));              \
     }                                                                                                     \
   } while (0)
 
-// Capture one pass of the Algorithm 1 loop as a CUDA graph: transport, kappa^n with the
-// epsilon partial sums, the device-side decision and the new epsilon,
+// Capture one pass of the Algorithm 1 loop as a CUDA graph for the current saturation
+// buffer parity: transport with kappa^n, the device-side decision and new epsilon,
 // IF(any rebuild){basis build}, IF(any reuse){perturbation solve}, interface solve,
-// downscaling.  Kernel arguments (grid data, pointers, eta,
-// cfl, n_sub) are captured by value, so setters that change them drop the graph.
+// downscaling.  Kernel arguments (grid data, pointers, eta, cfl, n_sub) are captured by
+// value, so setters that change them drop the graph.  The host-side buffer pointers are
+// restored after the capture (nothing has run yet).
 int build_step_graph(mpm_ctx* c, double eta, double cfl, int n_sub) {
-  drop_graph(c);
+  const int slot = graph_slot(c);
+  if (c->graph_exec[slot]) cudaGraphExecDestroy(c->graph_exec[slot]);
+  if (c->graph[slot]) cudaGraphDestroy(c->graph[slot]);
+  c->graph_exec[slot] = nullptr;
+  c->graph[slot] = nullptr;
+  c->graph_valid[slot] = false;
   cudaStream_t user = c->stream;
   cudaStream_t cs = c->cap_stream, bs = c->body_stream;
   const bool prof = c->prof;
+  const DevState saved = c->d;
   c->prof = false;
   c->stream = cs;
   const long long L0 = g_launches;
   long long Lb[3] = {L0, L0, L0};
-  CKG(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  int rc = run_transport(c, cfl, n_sub, true);
   cudaStreamCaptureStatus stt;
   cudaGraph_t cg = nullptr;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndep = 0;
   cudaGraphConditionalHandle h_reb = 0, h_mpm = 0;
-  if (!rc) {
-    CKG(cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, &deps, nullptr, &ndep));
-    CKG(cudaGraphConditionalHandleCreate(&h_reb, cg, 0, cudaGraphCondAssignDefault));
-    CKG(cudaGraphConditionalHandleCreate(&h_mpm, cg, 0, cudaGraphCondAssignDefault));
-    launch_choose_graph(c->g, c->d, eta, h_reb, h_mpm, 1, cs);
-    launch_eps_after_choose(c->g, c->d, cs);
-  }
+  CKG(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  CKG(cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, &deps, nullptr, &ndep));
+  CKG(cudaGraphConditionalHandleCreate(&h_reb, cg, 0, cudaGraphCondAssignDefault));
+  CKG(cudaGraphConditionalHandleCreate(&h_mpm, cg, 0, cudaGraphCondAssignDefault));
+  int rc = run_transport(c, cfl, n_sub, true, eta, h_reb, h_mpm, true);
+  if (!rc) rc = fork_downscale_factor(c);
   Lb[0] = g_launches;
   for (int branch = 1; branch >= 0 && !rc; --branch) {
     CKG(cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, &deps, nullptr, &ndep));
@@ -468,23 +520,24 @@ int build_step_graph(mpm_ctx* c, double eta, double cfl, int n_sub) {
     Lb[2 - branch] = g_launches;
   }
   if (!rc) rc = run_interface(c);
-  if (!rc) rc = run_downscale(c);
+  if (!rc) rc = run_downscale(c, true, true);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &graph);
   c->stream = user;
   c->prof = prof;
+  c->d = saved;
   if (rc) {
     if (graph) cudaGraphDestroy(graph);
     return rc;
   }
   if (e != cudaSuccess) return fail(c, MPM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-  c->graph = graph;
-  e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+  c->graph[slot] = graph;
+  e = cudaGraphInstantiate(&c->graph_exec[slot], graph, 0);
   if (e != cudaSuccess) {
     drop_graph(c);
     return fail(c, MPM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
   }
-  c->graph_valid = true;
+  c->graph_valid[slot] = true;
   c->gk_reb = Lb[1] - Lb[0];
   c->gk_mpm = Lb[2] - Lb[1];
   c->gk_base = (g_launches - L0) - c->gk_reb - c->gk_mpm;
@@ -537,7 +590,8 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   double** cells[] = {&d.K, &d.q, &d.s, &d.s2, &d.kap_n, &d.kap_m, &d.p_m, &d.p_down, &d.fs, &d.fs2};
   for (double** p : cells)
     if ((rc = dalloc_t(c, c->grid_allocs, p, nc)) != MPM_OK) break;
-  const int nblk = 1024;
+  c->s_buf0 = d.s;
+  const int nblk = std::max(1024, upwind_kappa_blocks(g));
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.ux, (size_t)R * g.nfx());
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.uy, (size_t)R * g.nfy());
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.tx, (size_t)R * g.nfx());
@@ -545,15 +599,20 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.eps, (size_t)R);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.dt, (size_t)R);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.eps_part, (size_t)R * nblk * 2);
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.ticket, (size_t)4);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.rebuild, (size_t)R);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.status, 1);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.ir_iters, 1);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.counts, 4);
   if (rc == MPM_OK && (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-                       cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking) != cudaSuccess))
+                       cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking) != cudaSuccess ||
+                       cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess))
     rc = MPM_ERR_CUDA;
   if (rc == MPM_OK && cudaMallocHost(&c->h_flags, sizeof(int) * R) != cudaSuccess) rc = MPM_ERR_OOM;
   if (rc != MPM_OK) {
+    destroy_streams(c);
     free_list(c->grid_allocs);
     delete c;
     return rc;
@@ -576,8 +635,8 @@ int mpm_destroy(mpm_ctx* c) {
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   drop_graph(c);
-  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-  if (c->body_stream) cudaStreamDestroy(c->body_stream);
+  if (c->side_stream) cudaStreamSynchronize(c->side_stream);
+  destroy_streams(c);
   release_decomposition(c);
   free_list(c->grid_allocs);
   if (c->h_flags) cudaFreeHost(c->h_flags);
@@ -702,7 +761,7 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   c->subs.assign(ncx * ncy, DevSub{});
   long long q_off = 0, t_off = 0, tr_off = 0, pf_off = 0;
   int dof_off = 0, face_off = 0, cell_off = 0;
-  c->max_a = c->max_b = c->max_dof = 0;
+  c->max_a = c->max_b = c->max_dof = c->max_face = 0;
   c->n_hat = 0;
   for (int J = 0; J < ncy; ++J) {
     for (int I = 0; I < ncx; ++I) {
@@ -753,6 +812,7 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
       c->max_a = std::max(c->max_a, s.a);
       c->max_b = std::max(c->max_b, s.b);
       c->max_dof = std::max(c->max_dof, nd);
+      c->max_face = std::max(c->max_face, nface);
       c->n_hat += nd;
     }
   }
@@ -854,6 +914,8 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   int rc = MPM_OK;
   if (!rc) rc = dalloc(c, A, &d.fac, (size_t)R * q_off * sizeof(double));
   if (!rc) rc = dalloc_t(c, A, &d.tvec, (size_t)R * t_off);
+  if (!rc) rc = dalloc(c, A, &d.nfac, (size_t)R * q_off * sizeof(double));
+  if (!rc) rc = dalloc_t(c, A, &d.ntvec, (size_t)R * t_off);
   if (!rc) rc = dalloc_t(c, A, &d.tr, (size_t)R * tr_off);
   if (!rc) rc = dalloc_t(c, A, &d.pf, (size_t)R * pf_off);
   if (!rc) rc = dalloc_t(c, A, &d.mu_hat, (size_t)R * dof_off);
@@ -864,6 +926,7 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   if (!rc) rc = dalloc_t(c, A, &d.sub_target, (size_t)R * nsub);
   if (!rc) rc = dalloc_t(c, A, &d.pm_mean, (size_t)R * nsub);
   if (!rc) rc = dalloc_t(c, A, &d.rate_part, (size_t)R * nsub);
+  if (!rc) rc = dalloc_t(c, A, &d.rate_max, (size_t)R);
   if (!rc) rc = dalloc_t(c, A, &d.front, (size_t)R * f_off);
   if (!rc) rc = dalloc_t(c, A, &d.gvec, (size_t)R * v_off);
   if (!rc) rc = dalloc_t(c, A, &d.xvec, (size_t)R * v_off);
@@ -962,7 +1025,7 @@ int mpm_downscale(mpm_ctx* c) {
   if (!c) return MPM_ERR_ARG;
   int rc = need_ready(c, true);
   if (rc) return rc;
-  return run_downscale(c);
+  return run_downscale(c, false, false);
 }
 
 int mpm_saturation_step(mpm_ctx* c, double cfl, int n_sub, double* dt) {
@@ -970,7 +1033,7 @@ int mpm_saturation_step(mpm_ctx* c, double cfl, int n_sub, double* dt) {
   if (!(cfl > 0 && cfl <= 1) || n_sub < 1) return fail(c, MPM_ERR_ARG, "need 0 < cfl <= 1 and n_sub >= 1");
   int rc = need_ready(c, false);
   if (rc) return rc;
-  if ((rc = run_transport(c, cfl, n_sub, false))) return rc;
+  if ((rc = run_transport(c, cfl, n_sub, false, 0.0, 0, 0, false))) return rc;
   if (dt) return copy_out(c, dt, c->d.dt, c->g.R, MPM_MEM_HOST);
   return MPM_OK;
 }
@@ -982,9 +1045,10 @@ int mpm_init(mpm_ctx* c, double eta) {
   if (rc) return rc;
   launch_mobility_eps(c->g, c->d, false, c->stream);
   launch_fill_flags(c->g, c->d, 1, c->stream);
+  if ((rc = fork_downscale_factor(c))) return rc;
   if ((rc = run_build(c))) return rc;
   if ((rc = run_interface(c))) return rc;
-  if ((rc = run_downscale(c))) return rc;
+  if ((rc = run_downscale(c, true, true))) return rc;
   std::vector<double> e(c->g.R, eta);
   CK(cudaMemcpyAsync(c->d.eps, e.data(), sizeof(double) * c->g.R, cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -999,20 +1063,21 @@ int mpm_step(mpm_ctx* c, double eta, double cfl, int n_sub) {
   int rc = need_ready(c, true);
   if (rc) return rc;
   if (c->use_graph && !c->prof) {
-    if (!c->graph_valid || c->g_eta != eta || c->g_cfl != cfl || c->g_nsub != n_sub) {
-      if ((rc = build_step_graph(c, eta, cfl, n_sub))) return rc;
+    if (c->g_eta != eta || c->g_cfl != cfl || c->g_nsub != n_sub) drop_graph(c);
+    const int slot = graph_slot(c);
+    if (!c->graph_valid[slot] && (rc = build_step_graph(c, eta, cfl, n_sub))) return rc;
+    CK(cudaGraphLaunch(c->graph_exec[slot], c->stream));
+    if (n_sub & 1) {  // the graph left the new saturation in the other buffer
+      std::swap(c->d.s, c->d.s2);
+      std::swap(c->d.fs, c->d.fs2);
     }
-    CK(cudaGraphLaunch(c->graph_exec, c->stream));
     c->stats.steps += 1;
     c->graph_steps += 1;
     return MPM_OK;
   }
   // eager path: the host reads the device decision to skip the branch nobody takes
-  if ((rc = run_transport(c, cfl, n_sub, true))) return rc;
-  prof_begin(c, MPM_STAGE_EPSILON);
-  launch_choose_graph(c->g, c->d, eta, 0, 0, 0, c->stream);
-  launch_eps_after_choose(c->g, c->d, c->stream);
-  prof_end(c, MPM_STAGE_EPSILON);
+  if ((rc = run_transport(c, cfl, n_sub, true, eta, 0, 0, false))) return rc;
+  if ((rc = fork_downscale_factor(c))) return rc;
   CK(cudaMemcpyAsync(c->h_flags, c->d.rebuild, sizeof(int) * c->g.R, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   int nreb = 0;
@@ -1020,16 +1085,18 @@ int mpm_step(mpm_ctx* c, double eta, double cfl, int n_sub) {
   if (nreb > 0 && (rc = run_build(c))) return rc;
   if (nreb < c->g.R && (rc = run_perturbation(c))) return rc;
   if ((rc = run_interface(c))) return rc;
-  if ((rc = run_downscale(c))) return rc;
+  if ((rc = run_downscale(c, true, true))) return rc;
   c->stats.steps += 1;
   return check_launch(c);
 }
 
 int mpm_set_execution(mpm_ctx* c, int flags) {
   if (!c) return MPM_ERR_ARG;
-  if (flags & ~(MPM_EXEC_GRAPH | MPM_EXEC_PERSISTENT)) return fail(c, MPM_ERR_ARG, "unknown execution flags %d", flags);
+  if (flags & ~(MPM_EXEC_GRAPH | MPM_EXEC_PERSISTENT | MPM_EXEC_PDL))
+    return fail(c, MPM_ERR_ARG, "unknown execution flags %d", flags);
   c->use_graph = (flags & MPM_EXEC_GRAPH) != 0;
   c->use_coop = (flags & MPM_EXEC_PERSISTENT) != 0;
+  c->use_pdl = (flags & MPM_EXEC_PDL) != 0;
   drop_graph(c);
   return MPM_OK;
 }

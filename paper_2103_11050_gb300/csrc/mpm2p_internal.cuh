@@ -10,6 +10,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <utility>
 
 namespace mpm {
 
@@ -59,6 +60,16 @@ struct Grid {
 };
 
 #ifdef __CUDACC__
+// Programmatic dependent launch.  A kernel launched with the programmatic-serialisation
+// attribute may start once every block of its predecessor in the stream has called
+// pdl_trigger(), i.e. while the predecessor still runs.  Before pdl_wait() such a kernel
+// reads only data that no kernel of the running chain writes (operators, factors, index
+// maps, and fields finished before the chain's first, fully ordered launch) and writes
+// only registers and shared memory; pdl_wait() returns once the predecessor grid has
+// completed and its memory operations are visible.  Without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Outward integrated flux of pressure p through a physical boundary face of a cell with
 // values (kc, pc) on side `side` (Dirichlet: 2 kc (pc - g); Neumann: z h).
 __device__ __forceinline__ double phys_flux(const Grid& g, int side, double kc, double pc) {
@@ -96,6 +107,8 @@ struct DevState {
   // per realisation scalars
   double *eps, *dt, *eps_part;
   double* rate_part;  // [R][st_sub] per subdomain: max over its cells of max(outflow, inflow), by the downscaling
+  double* rate_max;   // [R] max over rate_part, by the last block of the downscaling
+  unsigned int* ticket;  // [4] block-completion counters (0: downscaling, 1: transport); back to 0 after each launch
   int* rebuild;        // [R] branch of the current update: 1 = basis build, 0 = MPM-2P reuse
   int* status;         // [1] bitmask: 1 = a refinement did not reach its tolerance
   int* ir_iters;       // [1] max refinement sweeps used
@@ -104,8 +117,10 @@ struct DevState {
   // per subdomain pools
   void* fac;           // Robin factors (float or double), st_fac values per realisation
   double* tvec;        // [ex, wE, wN, sc] per subdomain (4 m), st_t
+  void* nfac;          // downscaling (pinned Neumann) factors of kappa^n, same layout as fac
+  double* ntvec;       // their [ex, wE, wN, sc], same layout as tvec
   double* tr;          // BF traces (2(a+b) x ndof), st_tr
-  double* pf;          // BF pressures (m x (ndof + 1)), st_pf
+  double* pf;          // BF pressures, one column of m cells per BF ((ndof + 1) x m), st_pf
   double* mu_hat;      // BF means, st_dof
   double* fbar;        // non-homogeneous / perturbation traces, st_face
   double* trace;       // one-sided traces of the current update, st_face
@@ -122,19 +137,35 @@ struct DevState {
 // Kernels launched by this process through the wrappers below (host side, not thread safe).
 extern long long g_launches;
 
+// cudaLaunchKernelEx with the programmatic-serialisation attribute when pdl is set.
+template <typename... KArgs, typename... Args>
+void launch_ex(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+               Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);  // errors surface via cudaGetLastError
+  ++g_launches;
+}
+
 // Host-side launch wrappers (defined in the .cu files).
 int grid_cell_blocks(const Grid& g);
 void launch_mobility_eps(const Grid& g, const DevState& d, bool with_eps, cudaStream_t st);
 void launch_choose(const Grid& g, const DevState& d, double eta, cudaStream_t st);
 void launch_fill_flags(const Grid& g, const DevState& d, int v, cudaStream_t st);
-void launch_choose_graph(const Grid& g, const DevState& d, double eta, cudaGraphConditionalHandle h_reb,
-                         cudaGraphConditionalHandle h_mpm, int set_handles, cudaStream_t st);
-void launch_copy_kappa_m(const Grid& g, const DevState& d, cudaStream_t st);
-void launch_ubar(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int branch, cudaStream_t st);
-void launch_cfl(const Grid& g, const DevState& d, double cfl, double fmax, int nsub, cudaStream_t st);
-void launch_mobility_partials(const Grid& g, const DevState& d, cudaStream_t st);
-void launch_eps_after_choose(const Grid& g, const DevState& d, cudaStream_t st);
-void launch_upwind(const Grid& g, const DevState& d, cudaStream_t st);
+void launch_upwind(const Grid& g, const DevState& d, double cfl, double fmax, cudaStream_t st);
+int upwind_kappa_blocks(const Grid& g);
+void launch_upwind_kappa(const Grid& g, const DevState& d, double cfl, double fmax, bool decide, double eta,
+                         cudaGraphConditionalHandle h_reb, cudaGraphConditionalHandle h_mpm, bool set_handles,
+                         cudaStream_t st);
 
 int local_smem_limit();
 void launch_robin_factor(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
@@ -145,25 +176,26 @@ void launch_basis_solve(const Grid& g, const DevState& d, const DevSub* subs, in
 void launch_mpm_local(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
                       int max_b, bool fp32, double ir_tol, int ir_max, const DevNode* nodes, const int* leaf_node,
                       cudaStream_t st);
-void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub,
-                        const DevNode* nodes, const int* leaf_node, int branch, cudaStream_t st);
+void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_face,
+                        int max_dof, const DevNode* nodes, const int* leaf_node, const int* pmap, int branch,
+                        bool pdl, cudaStream_t st);
+void launch_downscale_factor(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
+                             int max_b, bool fp32, cudaStream_t st);
 void launch_downscale(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
-                      int max_b, bool fp32, double ir_tol, int ir_max, cudaStream_t st);
+                      int max_b, bool fp32, double ir_tol, int ir_max, bool pdl, cudaStream_t st);
 
 void launch_element_matrix(const Grid& g, const DevState& d, const DevSub* subs, int nsub,
                            const DevNode* nodes, const int* leaf_node, cudaStream_t st);
-void launch_element_rhs(const Grid& g, const DevState& d, const DevSub* subs, int nsub,
-                        const DevNode* nodes, const int* leaf_node, cudaStream_t st);
 void launch_nd_factor_level(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes,
                             int nlev, int max_nf, int max_nsep, const int* srcmap, cudaStream_t st);
 void launch_nd_up(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
-                  int max_nf, int max_nsep, const int* srcmap, cudaStream_t st);
+                  int max_nf, int max_nsep, const int* srcmap, bool pdl, cudaStream_t st);
 int iface_coop_blocks();
 cudaError_t launch_iface_coop(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_dof,
                               const DevNode* nodes, const int* leaf_node, const int* level_nodes,
                               const DevLevel* lev, int nlev, const int* srcmap, const int* pmap, int blocks,
                               cudaStream_t st);
 void launch_nd_down(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
-                    int max_nsep, int max_nbnd, const int* pmap, cudaStream_t st);
+                    int max_nsep, int max_nbnd, const int* pmap, bool pdl, cudaStream_t st);
 
 }  // namespace mpm
