@@ -19,10 +19,10 @@ __device__ __forceinline__ double mobility(double s, double M) {
 __device__ __forceinline__ double fracflow(double s, double M) {
   const double lw = M * s * s;
   const double o = 1.0 - s;
-  return lw / (lw + o * o);
+  return div64(lw, lw + o * o);
 }
 
-__device__ __forceinline__ double harm(double a, double b) { return 2.0 * a * b / (a + b); }
+__device__ __forceinline__ double harm(double a, double b) { return div64(2.0 * a * b, a + b); }
 
 
 __device__ double block_sum(double v, double* sh) {

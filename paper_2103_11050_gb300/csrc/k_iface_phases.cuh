@@ -15,7 +15,7 @@ __device__ __forceinline__ double side_basis(int kk, int t, int seg_len, int deg
   const int seg = kk / nb, pw = kk - seg * nb;
   if (t / seg_len != seg) return 0.0;
   if (pw == 0) return 1.0;
-  const double xi = ((t % seg_len) + 0.5) / seg_len;
+  const double xi = div64((t % seg_len) + 0.5, (double)seg_len);
   return 2.0 * xi - 1.0;
 }
 

@@ -304,7 +304,7 @@ __device__ double basis_rhs(const Grid& g, const DevState& d, const DevSub& sd, 
     const bool isU = col < d0 + nb;
     const double phi = side_basis(isU ? col - d0 : col - d0 - nb, t, g.seg_len, g.degree);
     // r_e g_e with r_e = kc/(1/2+rho): U: g = -(rho/kc) s phi -> -rho s phi/(1/2+rho); P: kc phi/(1/2+rho)
-    return isU ? -rho * sd.side_sign[q] * phi / (0.5 + rho) : kc * phi / (0.5 + rho);
+    return isU ? div64(-rho * sd.side_sign[q] * phi, 0.5 + rho) : div64(kc * phi, 0.5 + rho);
   }
   return 0.0;
 }
@@ -319,7 +319,7 @@ __device__ double basis_g(const Grid& g, const DevSub& sd, const Stencil& S, int
   if (col < d0 || col >= d0 + 2 * nb) return 0.0;
   const bool isU = col < d0 + nb;
   const double phi = side_basis(isU ? col - d0 : col - d0 - nb, t, g.seg_len, g.degree);
-  return isU ? -(sd.side_rho[side] / S.kap[cl]) * sd.side_sign[side] * phi : phi;
+  return isU ? -div64(sd.side_rho[side], S.kap[cl]) * sd.side_sign[side] * phi : phi;
 }
 
 // Outward trace on face f of the local solution x (column col of X) of basis column bcol.
@@ -328,7 +328,7 @@ __device__ double basis_trace(const Grid& g, const DevSub& sd, const Stencil& S,
   int side, t, cl;
   face_info(sd, f, side, t, cl);
   const double kc = S.kap[cl], pc = X[cl * ncol + col];
-  if (sd.side_kind[side] == 1) return kc / (0.5 + sd.side_rho[side]) * (pc - basis_g(g, sd, S, f, bcol));
+  if (sd.side_kind[side] == 1) return div64(kc, 0.5 + sd.side_rho[side]) * (pc - basis_g(g, sd, S, f, bcol));
   if (g.bc_type[side] == 0) return 2.0 * kc * (pc - (homogeneous_phys ? 0.0 : g.bc_val[side]));
   return homogeneous_phys ? 0.0 : g.bc_val[side] * g.h;
 }
@@ -433,7 +433,7 @@ __global__ void k_robin_factor_w(Grid g, DevState d, const DevSub* subs, int sca
   for (int f = threadIdx.x; f < 2 * (sd.a + sd.b); f += blockDim.x) {
     int side, tt, cl;
     face_info(sd, f, side, tt, cl);
-    bh[f] = sd.side_kind[side] == 1 ? sd.side_rho[side] / t.kap[cl] : 0.0;
+    bh[f] = sd.side_kind[side] == 1 ? div64(sd.side_rho[side], t.kap[cl]) : 0.0;
   }
 }
 
@@ -493,7 +493,7 @@ __global__ void k_mpm_local_w(Grid g, DevState d, const DevSub* subs, int refine
     face_info(sd, f, side, tt, cl);
     const double kc = t.kap[cl], pc = t.X[cl];
     double v;
-    if (sd.side_kind[side] == 1) v = kc / (0.5 + sd.side_rho[side]) * pc;
+    if (sd.side_kind[side] == 1) v = div64(kc, 0.5 + sd.side_rho[side]) * pc;
     else v = g.bc_type[side] == 0 ? 2.0 * kc * pc : 0.0;
     fbar[f] = v;
   }

@@ -77,10 +77,10 @@ __device__ void build(const Grid& g, const DevSub& sd, Tables<T> t, const double
     t.wN[c] = jl < b - 1 ? ty[(long long)(j + 1) * g.nx + i] : 0.0;
     double dg = 0.0;
     if (!neumann) {
-      if (il == 0) dg += sd.side_kind[0] == 1 ? kc / (0.5 + sd.side_rho[0]) : (g.bc_type[0] == 0 ? 2.0 * kc : 0.0);
-      if (il == a - 1) dg += sd.side_kind[1] == 1 ? kc / (0.5 + sd.side_rho[1]) : (g.bc_type[1] == 0 ? 2.0 * kc : 0.0);
-      if (jl == 0) dg += sd.side_kind[2] == 1 ? kc / (0.5 + sd.side_rho[2]) : (g.bc_type[2] == 0 ? 2.0 * kc : 0.0);
-      if (jl == b - 1) dg += sd.side_kind[3] == 1 ? kc / (0.5 + sd.side_rho[3]) : (g.bc_type[3] == 0 ? 2.0 * kc : 0.0);
+      if (il == 0) dg += sd.side_kind[0] == 1 ? div64(kc, 0.5 + sd.side_rho[0]) : (g.bc_type[0] == 0 ? 2.0 * kc : 0.0);
+      if (il == a - 1) dg += sd.side_kind[1] == 1 ? div64(kc, 0.5 + sd.side_rho[1]) : (g.bc_type[1] == 0 ? 2.0 * kc : 0.0);
+      if (jl == 0) dg += sd.side_kind[2] == 1 ? div64(kc, 0.5 + sd.side_rho[2]) : (g.bc_type[2] == 0 ? 2.0 * kc : 0.0);
+      if (jl == b - 1) dg += sd.side_kind[3] == 1 ? div64(kc, 0.5 + sd.side_rho[3]) : (g.bc_type[3] == 0 ? 2.0 * kc : 0.0);
     } else if (c == 0) {
       dg += kc;  // pin: A + kappa_0 e_0 e_0^T
     }

@@ -12,6 +12,8 @@
 #include <cstdint>
 #include <utility>
 
+#include "fp64_div.cuh"
+
 namespace mpm {
 
 constexpr int kMaxSide = 24;     // largest subdomain width / height in cells
