@@ -17,7 +17,8 @@
 // Gauss-Jordan sweep, which leaves
 //   [ F_ss^-1          F_ss^-1 F_sb            ]
 //   [ -F_bs F_ss^-1    F_bb - F_bs F_ss^-1 F_sb ]   (Schur complement -> parent)
-// in place.  With the flux rows negated the system is symmetric quasi-definite
+// in place.  The frontal matrices are stored transposed (the sweep then produces the
+// transposes of these blocks), so that the solve reads them along rows.  With the flux rows negated the system is symmetric quasi-definite
 // (Robin-weighted U block positive definite, P block negative definite when a Dirichlet
 // side exists), so the sweep needs no pivoting.
 // Solve: upward  y_s = F_ss^-1 g_s, g_b += (-F_bs F_ss^-1) g_s  (g_b -> parent);
@@ -72,7 +73,7 @@ __global__ void k_element_matrix(Grid g, DevState d, const DevSub* subs, const D
         if (!lisP && lside == side) v += bh * w * side_basis(ll, t, g.seg_len, g.degree);
       }
     }
-    E[e] = v;
+    E[(long long)l * nd + k] = v;  // stored transposed (see the per-level solve kernels)
   }
 }
 
@@ -86,7 +87,7 @@ __global__ void k_nd_assemble(Grid g, DevState d, const DevNode* nodes, const in
   const long long total = (long long)nf * nf;
   const long long start = (long long)blockIdx.y * blockDim.x * 8;
   if (start >= total) return;
-  double* F = d.front + (long long)r * d.st_front + nd.f_off;
+  double* F = d.front + (long long)r * d.st_front + nd.f_off;  // transposed storage, mapped entry by entry
   const int* s0 = srcmap + nd.src_off;
   const int* s1 = s0 + nf;
   const DevNode c0 = nodes[nd.child[0]], c1 = nodes[nd.child[1]];
@@ -216,123 +217,135 @@ __global__ void k_sweep_trailing(Grid g, DevState d, const DevNode* nodes, const
   }
 }
 
-constexpr int kRowsPerCta = 8;  // frontal rows per CTA of the per-level solve kernels (one row per warp)
+// Per-level solve kernels.  Every frontal matrix is stored transposed, G = F^T (the element
+// matrices are written transposed and the extend-add maps entries index by index), and the
+// sweep runs on G, which leaves
+//   [ G_ss^-1 = (F_ss^-1)^T         G_ss^-1 G_sb = (F_bs F_ss^-1)^T      ]
+//   [ -G_bs G_ss^-1 = -(F_ss^-1 F_sb)^T   S_G = (F_bb - F_bs F_ss^-1 F_sb)^T ]
+// so the solve with F reads G along its rows: output r is a sum over k of G[k][r] (up) or
+// G[ns + k][r] (down).  Consecutive threads take consecutive r, so every load is coalesced
+// and no cross-lane reduction is needed (float64 instructions are scarce on this part).  KS
+// threads share a row, each summing every KS-th k (its first kKpt terms held in registers,
+// loaded before pdl_wait()), and combine in shared memory.
+constexpr int kKpt = 16;
 
-// Per-level solve kernels.  Each warp owns one frontal row and holds its part of the row
-// (columns lane + 32 i, i < NR) in registers; these, the node records and the index maps
-// are loaded before pdl_wait(), so under programmatic launch they overlap the previous
-// level, and only the right-hand side / solution gather waits on it.
-
-// Upward solve at one level: y_s = M_ss g_s (rows < nsep, into x) or
-// g_b = g_b + M_bs g_s (rows >= nsep), with g gathered from the children.
-template <int NR>
+// Upward solve at one level: y_s = F_ss^-1 g_s, y_s[r] = sum_k G[k][r] g_s[k] (r < ns, into
+// x), and g_b += -F_bs F_ss^-1 g_s, g_b[r] = gather(r) - sum_k G[k][r] g_s[k] (r >= ns), with
+// g gathered from the children.
+template <int KS>
 __global__ void __launch_bounds__(256) k_nd_up(Grid g, DevState d, const DevNode* nodes, const int* level_nodes,
                                                const int* srcmap) {
+  constexpr int ROWS = 256 / KS;
   extern __shared__ __align__(16) double nd_smem[];
   pdl_trigger();
   const int r = blockIdx.z;
   const DevNode nd = nodes[level_nodes[blockIdx.x]];
-  const int row0 = blockIdx.y * kRowsPerCta;
+  const int row0 = blockIdx.y * ROWS;
   if (row0 >= nd.nf) return;
   const int nf = nd.nf, ns = nd.nsep;
-  double* gs = nd_smem;                              // ns
-  int* i0 = reinterpret_cast<int*>(gs + ns);         // ns
-  int* i1 = i0 + ns;                                 // ns
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = row0 + warp;
-  const bool active = row < nf;
+  double* part = nd_smem;                            // [KS][ROWS]
+  double* gs = nd_smem + KS * ROWS;                  // ns
+  const int i = threadIdx.x % ROWS, q = threadIdx.x / ROWS;
+  const int row = row0 + i;
   const long long vb = (long long)r * d.st_vec;
-  const double* Fr = d.front + (long long)r * d.st_front + nd.f_off + (long long)(active ? row : row0) * nf;
-  double fr[NR];
-#pragma unroll
-  for (int i = 0; i < NR; ++i) {
-    const int k = lane + 32 * i;
-    fr[i] = (active && k < ns) ? Fr[k] : 0.0;
-  }
   const int* s0 = srcmap + nd.src_off;
   const int* s1 = s0 + nf;
-  for (int k = threadIdx.x; k < ns; k += blockDim.x) {
-    i0[k] = s0[k];
-    i1[k] = s1[k];
-  }
-  int own0 = -1, own1 = -1;
-  if (active && row >= ns && lane == 0) {
-    own0 = s0[row];
-    own1 = s1[row];
-  }
   const DevNode& c0 = nodes[nd.child[0]];
   const DevNode& c1 = nodes[nd.child[1]];
   const double* g0 = d.gvec + vb + c0.v_off + c0.nsep;
   const double* g1 = d.gvec + vb + c1.v_off + c1.nsep;
-  __syncthreads();
-  pdl_wait();
-  for (int k = threadIdx.x; k < ns; k += blockDim.x)
-    gs[k] = (i0[k] >= 0 ? g0[i0[k]] : 0.0) + (i1[k] >= 0 ? g1[i1[k]] : 0.0);
-  __syncthreads();
-  double acc = 0.0;
-#pragma unroll
-  for (int i = 0; i < NR; ++i) {
-    const int k = lane + 32 * i;
-    if (k < ns) acc += fr[i] * gs[k];
+  int own0 = -1, own1 = -1;
+  if (q == 0 && row < nf && row >= ns) {
+    own0 = s0[row];
+    own1 = s1[row];
   }
-  if (active)
-    for (int k = lane + 32 * NR; k < ns; k += 32) acc += Fr[k] * gs[k];
-  acc = phase::warp_sum(acc);
-  if (active && lane == 0) {
-    if (row < ns) d.xvec[vb + nd.v_off + row] = acc;
-    else d.gvec[vb + nd.v_off + row] = ((own0 >= 0 ? g0[own0] : 0.0) + (own1 >= 0 ? g1[own1] : 0.0)) + acc;
+  // this thread's first kKpt terms G[q + u KS][row]: operator data, loaded before the wait
+  const double* F = d.front + (long long)r * d.st_front + nd.f_off;
+  double v[kKpt];
+#pragma unroll
+  for (int u = 0; u < kKpt; ++u) {
+    const int k = q + u * KS;
+    v[u] = (row < nf && k < ns) ? F[(long long)k * nf + row] : 0.0;
+  }
+  pdl_wait();
+  for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+    const int a0 = s0[k], a1 = s1[k];
+    gs[k] = (a0 >= 0 ? g0[a0] : 0.0) + (a1 >= 0 ? g1[a1] : 0.0);
+  }
+  __syncthreads();
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int u = 0; u < kKpt; ++u) {
+    const int k = q + u * KS;
+    if (k < ns) acc[u & 3] += v[u] * gs[k];
+  }
+  if (row < nf)
+    for (int k = q + kKpt * KS; k < ns; k += KS) acc[0] += F[(long long)k * nf + row] * gs[k];
+  part[q * ROWS + i] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  __syncthreads();
+  if (q == 0 && row < nf) {
+    double sum = part[i];
+#pragma unroll
+    for (int u = 1; u < KS; ++u) sum += part[u * ROWS + i];
+    if (row < ns) d.xvec[vb + nd.v_off + row] = sum;
+    else d.gvec[vb + nd.v_off + row] = ((own0 >= 0 ? g0[own0] : 0.0) + (own1 >= 0 ? g1[own1] : 0.0)) - sum;
   }
 }
 
-// Downward solve at one level: x_s = y_s - M_sb x_b with x_b gathered from the parent's x;
-// the CTA of row block 0 also stores x_b in the node's own vector for its children.
-// Leaves are not visited: the reconstruction gathers their x from the parent directly.
-template <int NR>
+// Downward solve at one level: x_s = y_s - F_ss^-1 F_sb x_b,
+// x_s[r] = y_s[r] + sum_k G[ns + k][r] x_b[k], with x_b gathered
+// from the parent's x; the CTA of row block 0 also stores x_b in the node's own vector for
+// its children.  Leaves are not visited: the reconstruction gathers their x from the parent.
+template <int KS>
 __global__ void __launch_bounds__(256) k_nd_down(Grid g, DevState d, const DevNode* nodes, const int* level_nodes,
                                                  const int* pmap) {
+  constexpr int ROWS = 256 / KS;
   extern __shared__ __align__(16) double nd_smem[];
   pdl_trigger();
   const int r = blockIdx.z;
   const DevNode nd = nodes[level_nodes[blockIdx.x]];
   if (nd.parent < 0) return;
   const int nf = nd.nf, ns = nd.nsep, nbd = nd.nbnd;
-  const int row0 = blockIdx.y * kRowsPerCta;
+  const int row0 = blockIdx.y * ROWS;
   if (row0 >= ns && blockIdx.y != 0) return;
-  double* xb = nd_smem;                              // nbd
-  int* pidx = reinterpret_cast<int*>(xb + nbd);      // nbd
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = row0 + warp;
-  const bool active = row < ns;
+  double* part = nd_smem;                            // [KS][ROWS]
+  double* xb = nd_smem + KS * ROWS;                  // nbd
+  const int i = threadIdx.x % ROWS, q = threadIdx.x / ROWS;
+  const int row = row0 + i;
   const long long vb = (long long)r * d.st_vec;
-  const double* Fr = d.front + (long long)r * d.st_front + nd.f_off + (long long)(active ? row : 0) * nf + ns;
-  double fr[NR];
-#pragma unroll
-  for (int i = 0; i < NR; ++i) {
-    const int k = lane + 32 * i;
-    fr[i] = (active && k < nbd) ? Fr[k] : 0.0;
-  }
   const int* pm = pmap + nd.pmap_off;
-  for (int k = threadIdx.x; k < nbd; k += blockDim.x) pidx[k] = pm[k];
   const double* xp = d.xvec + vb + nodes[nd.parent].v_off;
   double* xo = d.xvec + vb + nd.v_off;
-  __syncthreads();
+  const double* F = d.front + (long long)r * d.st_front + nd.f_off + (long long)ns * nf;
+  double v[kKpt];
+#pragma unroll
+  for (int u = 0; u < kKpt; ++u) {
+    const int k = q + u * KS;
+    v[u] = (row < ns && k < nbd) ? F[(long long)k * nf + row] : 0.0;
+  }
   pdl_wait();
   for (int k = threadIdx.x; k < nbd; k += blockDim.x) {
-    const double v = xp[pidx[k]];
-    xb[k] = v;
-    if (blockIdx.y == 0) xo[ns + k] = v;
+    const double x = xp[pm[k]];
+    xb[k] = x;
+    if (blockIdx.y == 0) xo[ns + k] = x;
   }
   __syncthreads();
-  double acc = 0.0;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-  for (int i = 0; i < NR; ++i) {
-    const int k = lane + 32 * i;
-    if (k < nbd) acc += fr[i] * xb[k];
+  for (int u = 0; u < kKpt; ++u) {
+    const int k = q + u * KS;
+    if (k < nbd) acc[u & 3] += v[u] * xb[k];
   }
-  if (active)
-    for (int k = lane + 32 * NR; k < nbd; k += 32) acc += Fr[k] * xb[k];
-  acc = phase::warp_sum(acc);
-  if (active && lane == 0) xo[row] -= acc;
+  if (row < ns)
+    for (int k = q + kKpt * KS; k < nbd; k += KS) acc[0] += F[(long long)k * nf + row] * xb[k];
+  part[q * ROWS + i] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  __syncthreads();
+  if (q == 0 && row < ns) {
+    double sum = part[i];
+#pragma unroll
+    for (int u = 1; u < KS; ++u) sum += part[u * ROWS + i];
+    xo[row] += sum;
+  }
 }
 
 // Reconstruction from the interface solution c of one subdomain per CTA (c gathered from the
@@ -557,18 +570,39 @@ int row_chunks(int n) {
     }                                                           \
   } while (0)
 
+namespace {
+// k-chunks per output row: each thread sums at most about 16 terms.
+int k_split(int n) {
+  const int q = (n + 15) / 16;
+  return q <= 1 ? 1 : q <= 2 ? 2 : q <= 4 ? 4 : q <= 8 ? 8 : 16;
+}
+}  // namespace
+
+#define MPM_DISPATCH_KS(KERNEL, ks, ...)                        \
+  do {                                                          \
+    switch (ks) {                                               \
+      case 1: launch_ex(KERNEL<1>, __VA_ARGS__); break;         \
+      case 2: launch_ex(KERNEL<2>, __VA_ARGS__); break;         \
+      case 4: launch_ex(KERNEL<4>, __VA_ARGS__); break;         \
+      case 8: launch_ex(KERNEL<8>, __VA_ARGS__); break;         \
+      default: launch_ex(KERNEL<16>, __VA_ARGS__); break;       \
+    }                                                           \
+  } while (0)
+
 void launch_nd_up(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
                   int max_nf, int max_nsep, const int* srcmap, bool pdl, cudaStream_t st) {
-  const dim3 grid(nlev, (max_nf + kRowsPerCta - 1) / kRowsPerCta, g.R);
-  const size_t smem = (size_t)max_nsep * (sizeof(double) + 2 * sizeof(int));
-  MPM_DISPATCH_NR(k_nd_up, row_chunks(max_nsep), grid, dim3(256), smem, st, pdl, g, d, nodes, level_nodes, srcmap);
+  const int ks = k_split(max_nsep), rows = 256 / ks;
+  const dim3 grid(nlev, (max_nf + rows - 1) / rows, g.R);
+  const size_t smem = (size_t)(256 + max_nsep) * sizeof(double);
+  MPM_DISPATCH_KS(k_nd_up, ks, grid, dim3(256), smem, st, pdl, g, d, nodes, level_nodes, srcmap);
 }
 
 void launch_nd_down(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
                     int max_nsep, int max_nbnd, const int* pmap, bool pdl, cudaStream_t st) {
-  const dim3 grid(nlev, max_nsep > 0 ? (max_nsep + kRowsPerCta - 1) / kRowsPerCta : 1, g.R);
-  const size_t smem = (size_t)(max_nbnd > 0 ? max_nbnd : 1) * (sizeof(double) + sizeof(int));
-  MPM_DISPATCH_NR(k_nd_down, row_chunks(max_nbnd), grid, dim3(256), smem, st, pdl, g, d, nodes, level_nodes, pmap);
+  const int ks = k_split(max_nbnd), rows = 256 / ks;
+  const dim3 grid(nlev, max_nsep > 0 ? (max_nsep + rows - 1) / rows : 1, g.R);
+  const size_t smem = (size_t)(256 + max_nbnd) * sizeof(double);
+  MPM_DISPATCH_KS(k_nd_down, ks, grid, dim3(256), smem, st, pdl, g, d, nodes, level_nodes, pmap);
 }
 
 void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_face, int max_dof,

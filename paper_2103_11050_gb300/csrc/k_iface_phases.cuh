@@ -80,37 +80,39 @@ __device__ __forceinline__ double gather_g(const DevState& d, const DevNode* nod
   return v;
 }
 
-// Upward solve, one frontal row per warp: y_s = M_ss g_s -> x (row < nsep), or
-// g_b = g_b + M_bs g_s (row >= nsep).  gs: the node's gathered separator right-hand side
-// (shared memory), or nullptr to gather from the children on the fly.
+// Upward solve, one frontal row per warp, from the transposed sweep G (k_iface.cu):
+// y_s[row] = sum_k G[k][row] g_s[k] -> x (row < nsep), or
+// g_b[row] = gather(row) - sum_k G[k][row] g_s[k] (row >= nsep).  gs: the node's gathered
+// separator right-hand side (shared memory), or nullptr to gather from the children on the fly.
 __device__ __forceinline__ void nd_up_row(const DevState& d, const DevNode* nodes, const DevNode& nd, int r, int row,
                                           const int* srcmap, int lane, const double* gs) {
   const int nf = nd.nf, ns = nd.nsep;
-  const double* Fr = d.front + (long long)r * d.st_front + nd.f_off + (long long)row * nf;
+  const double* G = d.front + (long long)r * d.st_front + nd.f_off;
   double acc = 0.0;
   if (gs)
-    for (int k = lane; k < ns; k += 32) acc += Fr[k] * gs[k];
+    for (int k = lane; k < ns; k += 32) acc += G[(long long)k * nf + row] * gs[k];
   else
-    for (int k = lane; k < ns; k += 32) acc += Fr[k] * gather_g(d, nodes, nd, r, srcmap, k);
+    for (int k = lane; k < ns; k += 32) acc += G[(long long)k * nf + row] * gather_g(d, nodes, nd, r, srcmap, k);
   acc = warp_sum(acc);
   if (lane == 0) {
     if (row < ns) d.xvec[(long long)r * d.st_vec + nd.v_off + row] = acc;
-    else d.gvec[(long long)r * d.st_vec + nd.v_off + row] = gather_g(d, nodes, nd, r, srcmap, row) + acc;
+    else d.gvec[(long long)r * d.st_vec + nd.v_off + row] = gather_g(d, nodes, nd, r, srcmap, row) - acc;
   }
 }
 
-// Downward solve, one separator row per warp: x_s = y_s - M_sb x_b, x_b read from the parent.
+// Downward solve, one separator row per warp: x_s[row] = y_s[row] + sum_k G[ns + k][row] x_b[k],
+// x_b read from the parent.
 __device__ __forceinline__ void nd_down_row(const DevState& d, const DevNode* nodes, const DevNode& nd, int r,
                                             int row, const int* pmap, int lane) {
   const int nf = nd.nf, ns = nd.nsep, nbd = nd.nbnd;
   const DevNode& pa = nodes[nd.parent];
   const double* xp = d.xvec + (long long)r * d.st_vec + pa.v_off;
   const int* pm = pmap + nd.pmap_off;
-  const double* Fr = d.front + (long long)r * d.st_front + nd.f_off + (long long)row * nf + ns;
+  const double* G = d.front + (long long)r * d.st_front + nd.f_off + (long long)ns * nf;
   double acc = 0.0;
-  for (int k = lane; k < nbd; k += 32) acc += Fr[k] * xp[pm[k]];
+  for (int k = lane; k < nbd; k += 32) acc += G[(long long)k * nf + row] * xp[pm[k]];
   acc = warp_sum(acc);
-  if (lane == 0) d.xvec[(long long)r * d.st_vec + nd.v_off + row] -= acc;
+  if (lane == 0) d.xvec[(long long)r * d.st_vec + nd.v_off + row] += acc;
 }
 
 // Downward solve, boundary copy: x_b[k] = parent's x at the matching frontal index.
