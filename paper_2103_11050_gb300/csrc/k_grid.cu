@@ -160,10 +160,10 @@ constexpr int kTX = 32, kTY = 2;  // cell tile of the last transport substep (on
 // CTA; the last CTA to finish takes the Algorithm 1 decision for every realisation with the
 // epsilon of the previous pass (rebuild_r = eps_r > eta), stores the new epsilon (0 where
 // the basis is rebuilt, else sqrt(num / den)), counts the branches and, in a CUDA graph
-// (set_handles), sets the conditional handles of the rebuild and MPM-2P bodies.
+// (set_handle), sets the conditional handle of the rebuild body.
 __global__ void __launch_bounds__(kTX * kTY) k_upwind_kappa(Grid g, DevState d, double cfl, double fmax_, int decide,
                                                             double eta, cudaGraphConditionalHandle h_reb,
-                                                            cudaGraphConditionalHandle h_mpm, int set_handles) {
+                                                            int set_handle) {
   __shared__ double sn[kTY + 1][kTX + 1];  // s2
   __shared__ double sk[kTY + 1][kTX + 1];  // kappa^n of s2
   __shared__ double sh[32];
@@ -251,9 +251,8 @@ __global__ void __launch_bounds__(kTX * kTY) k_upwind_kappa(Grid g, DevState d, 
   if (threadIdx.x == 0) {
     d.counts[0] += tot;
     d.counts[1] += g.R - tot;
-    if (set_handles) {
+    if (set_handle) {
       cudaGraphSetConditional(h_reb, tot > 0 ? 1u : 0u);
-      cudaGraphSetConditional(h_mpm, tot < g.R ? 1u : 0u);
       d.counts[2] += tot > 0;
       d.counts[3] += tot < g.R;
     }
@@ -298,10 +297,9 @@ void launch_upwind(const Grid& g, const DevState& d, double cfl, double fmax_, c
 int upwind_kappa_blocks(const Grid& g) { return ((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY); }
 
 void launch_upwind_kappa(const Grid& g, const DevState& d, double cfl, double fmax_, bool decide, double eta,
-                         cudaGraphConditionalHandle h_reb, cudaGraphConditionalHandle h_mpm, bool set_handles,
-                         cudaStream_t st) {
+                         cudaGraphConditionalHandle h_reb, bool set_handle, cudaStream_t st) {
   k_upwind_kappa<<<dim3(upwind_kappa_blocks(g), g.R), kTX * kTY, 0, st>>>(g, d, cfl, fmax_, decide ? 1 : 0, eta,
-                                                                        h_reb, h_mpm, set_handles ? 1 : 0);
+                                                                        h_reb, set_handle ? 1 : 0);
   ++g_launches;
 }
 

@@ -41,19 +41,19 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Element right-hand side of local DOF k of subdomain sd from the non-homogeneous
-// (rebuild) or perturbation (MPM-2P) traces fbar, moved to the right-hand side:
-// psi rows -sum psi F, phi rows +sum bh s phi F.  Written to the leaf's g vector.
+// (rebuild) or perturbation (MPM-2P) traces fb (this subdomain's, face order), moved to the
+// right-hand side: psi rows -sum psi F, phi rows +sum bh s phi F, over the edges of the
+// DOF's segment (its support).  Written to the leaf's g vector.
 __device__ __forceinline__ void element_rhs(const Grid& g, const DevState& d, const DevSub& sd, const DevNode& leaf,
-                                            int r, int k) {
+                                            int r, int k, const double* fb) {
   int side, isP, kk;
   dof_info(sd, k, side, isP, kk);
-  const int L = side < 2 ? sd.b : sd.a;
   const int f0 = face_side_off(side, sd.a, sd.b);
   const double s = sd.side_sign[side];
-  const double* fb = d.fbar + (long long)r * d.st_face + sd.face_off;
   const double* bhat = d.bhat + (long long)r * d.st_face + sd.face_off;
+  const int t0 = (kk / (g.degree + 1)) * g.seg_len;
   double v = 0.0;
-  for (int t = 0; t < L; ++t) {
+  for (int t = t0; t < t0 + g.seg_len; ++t) {
     const double w = side_basis(kk, t, g.seg_len, g.degree);
     if (w == 0.0) continue;
     const double F = fb[f0 + t];

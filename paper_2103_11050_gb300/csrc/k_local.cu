@@ -33,6 +33,23 @@ namespace mpm {
 namespace {
 
 constexpr int kSmemBudget = 200 * 1024;
+constexpr int kLocalThreads = 256;  // threads of the single-right-hand-side local kernels (two warps
+                                    // run the twisted chains, all of them the cell-parallel phases)
+
+// Asynchronous 16-byte global -> shared copies (cp.async), completed by cp_async_wait_all().
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+// Stage `bytes` (a multiple of 16, both addresses 16-byte aligned) into shared memory.
+__device__ __forceinline__ void stage_async(void* smem_dst, const void* gsrc, size_t bytes) {
+  char* dst = reinterpret_cast<char*>(smem_dst);
+  const char* src = reinterpret_cast<const char*>(gsrc);
+  for (size_t o = (size_t)threadIdx.x * 16; o < bytes; o += (size_t)blockDim.x * 16) cp_async16(dst + o, src + o);
+}
 
 using phase::side_basis;
 
@@ -388,7 +405,7 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
   }
   // Interface right-hand side (Eq. mrc2) from the non-homogeneous traces just written.
   for (int k = threadIdx.x; k < sd.ndof; k += blockDim.x)
-    phase::element_rhs(g, d, sd, nodes[leaf_node[blockIdx.x]], r, k);
+    phase::element_rhs(g, d, sd, nodes[leaf_node[blockIdx.x]], r, k, fbar);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -438,19 +455,30 @@ __global__ void k_robin_factor_w(Grid g, DevState d, const DevSub* subs, int sca
 }
 
 // MPM-2P local solve: A_i(kappa^m) dp = r_i with zero Robin data and homogeneous physical
-// data, using the stored factor.  Outputs the perturbation traces (fbar) and mean(dp).
+// data, using the stored factor (staged into shared memory when qoff != 0, else read from
+// global memory), with r_i the fine residual q h^2 - sum_faces F(kappa^n, p^m) on the
+// subdomain's cells.  Outputs the perturbation traces (fbar), mean(dp) and the interface
+// right-hand side of the subdomain.
 template <typename T, int A>
-__global__ void k_mpm_local_w(Grid g, DevState d, const DevSub* subs, int refine, double tol, int ir_max,
-                              const DevNode* nodes, const int* leaf_node) {
+__global__ void __launch_bounds__(kLocalThreads) k_mpm_local_w(Grid g, DevState d, const DevSub* subs, size_t qoff,
+                                                               int refine, double tol, int ir_max,
+                                                               const DevNode* nodes, const int* leaf_node) {
   extern __shared__ __align__(16) char smem[];
-  __shared__ double red[4];
+  __shared__ double red[64];
+  __shared__ double fb[4 * kMaxSide];
   const int sidx = blockIdx.x;
   const int r = blockIdx.y;
   if (d.rebuild[r] != 0) return;
   const DevSub sd = subs[sidx];
   const int a = sd.a, b = sd.b, m = a * b;
   warp::Tables<T> t = warp::carve<T, A>(smem, m, b);
-  load_kappa_cta(g, sd, d.kap_m + (long long)r * g.ncell(), t.kap);
+  const T* Qg = reinterpret_cast<const T*>(d.fac) + (long long)r * d.st_fac + sd.q_off;
+  const T* Q = Qg;
+  if (qoff != 0) {
+    T* Qs = reinterpret_cast<T*>(smem + qoff);
+    stage_async(Qs, Qg, (size_t)b * A * A * sizeof(T));
+    Q = Qs;
+  }
   const double* tv = d.tvec + (long long)r * d.st_t + sd.t_off;
   const int nx = g.nx, ny = g.ny;
   const long long cb = (long long)r * g.ncell();
@@ -458,14 +486,15 @@ __global__ void k_mpm_local_w(Grid g, DevState d, const DevSub* subs, int refine
   const double* ty = d.ty + (long long)r * g.nfy();
   const double* pm = d.p_m + cb;
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    const int jl = c / a, il = c - jl * a;
+    const int i = sd.x0 + il, j = sd.y0 + jl;
+    const long long gc = (long long)j * nx + i;
+    t.kap[c] = d.kap_m[cb + gc];
     t.ex[c] = tv[c];
     t.wE[c] = tv[m + c];
     t.wN[c] = tv[2 * m + c];
     t.sc[c] = tv[3 * m + c];
     // fine residual r_c = q_c h^2 - sum_faces F_out(kappa^n, p^m)
-    const int jl = c / a, il = c - jl * a;
-    const int i = sd.x0 + il, j = sd.y0 + jl;
-    const long long gc = (long long)j * nx + i;
     const double kc = d.kap_n[cb + gc], pc = pm[gc];
     double out = 0.0;
     if (i > 0) out += tx[(long long)j * (nx + 1) + i] * (pc - pm[gc - 1]);
@@ -483,9 +512,9 @@ __global__ void k_mpm_local_w(Grid g, DevState d, const DevSub* subs, int refine
     const int j = e / A, i = e - j * A;
     t.th[e] = (i < a && j < b - 1) ? T(t.wN[j * a + i] * t.sc[j * a + i] * t.sc[j * a + i + a]) : T(0);
   }
+  if (qoff != 0) cp_async_wait_all();
   __syncthreads();
-  const T* Qg = reinterpret_cast<const T*>(d.fac) + (long long)r * d.st_fac + sd.q_off;
-  warp::solve_refined<T, A>(sd, t, Qg, refine != 0, tol, ir_max, d.status, d.ir_iters, red);
+  warp::solve_refined<T, A>(sd, t, Q, refine != 0, tol, ir_max, d.status, d.ir_iters, red);
   double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
   const int nface = 2 * (a + b);
   for (int f = threadIdx.x; f < nface; f += blockDim.x) {
@@ -496,14 +525,17 @@ __global__ void k_mpm_local_w(Grid g, DevState d, const DevSub* subs, int refine
     if (sd.side_kind[side] == 1) v = div64(kc, 0.5 + sd.side_rho[side]) * pc;
     else v = g.bc_type[side] == 0 ? 2.0 * kc * pc : 0.0;
     fbar[f] = v;
+    fb[f] = v;
   }
   double s = 0.0;
   for (int c = threadIdx.x; c < m; c += blockDim.x) s += t.X[c];
-  s = warp::cta_sum(s, red);
+  s = warp::cta_sum(s, red);  // also orders the fb writes before the reads below
   if (threadIdx.x == 0) d.sub_mean[(long long)r * d.st_sub + sidx] = s / m;
-  __syncthreads();  // fbar of the whole subdomain written
   // Interface right-hand side (Eq. mrc2) from the perturbation traces.
-  for (int k = threadIdx.x; k < sd.ndof; k += blockDim.x) phase::element_rhs(g, d, sd, nodes[leaf_node[sidx]], r, k);
+  if (sd.ndof > 0) {
+    const DevNode& leaf = nodes[leaf_node[sidx]];
+    for (int k = threadIdx.x; k < sd.ndof; k += blockDim.x) phase::element_rhs(g, d, sd, leaf, r, k, fb);
+  }
 }
 
 // Downscaling factorisation (Eq. mpm_upd, left-hand side): the pinned Neumann operator of
@@ -539,10 +571,10 @@ __global__ void k_downscale_factor_w(Grid g, DevState d, const DevSub* subs, int
 // reduces these maxima per realisation into rate_max (CFL step).  The factor and stencil
 // are loaded before pdl_wait() (they come from a stream joined before the launch).
 template <typename T, int A>
-__global__ void k_downscale_w(Grid g, DevState d, const DevSub* subs, size_t qoff, int refine, double tol,
-                              int ir_max) {
+__global__ void __launch_bounds__(kLocalThreads) k_downscale_w(Grid g, DevState d, const DevSub* subs, size_t qoff,
+                                                               int refine, double tol, int ir_max) {
   extern __shared__ __align__(16) char smem[];
-  __shared__ double red[4];
+  __shared__ double red[64];
   __shared__ double ub[4 * kMaxSide];  // u_bar per boundary face (face order), +x / +y
   __shared__ int last;
   const int sidx = blockIdx.x;
@@ -550,13 +582,14 @@ __global__ void k_downscale_w(Grid g, DevState d, const DevSub* subs, size_t qof
   const DevSub sd = subs[sidx];
   const int a = sd.a, b = sd.b, m = a * b, nx = g.nx;
   warp::Tables<T> t = warp::carve<T, A>(smem, m, b);
-  T* Q = reinterpret_cast<T*>(smem + qoff);
+  const T* Qg = reinterpret_cast<const T*>(d.nfac) + (long long)r * d.st_fac + sd.q_off;
+  const T* Q = Qg;  // staged into shared memory when qoff != 0, else read from global memory
+  if (qoff != 0) {
+    T* Qs = reinterpret_cast<T*>(smem + qoff);
+    stage_async(Qs, Qg, (size_t)b * A * A * sizeof(T));
+    Q = Qs;
+  }
   {
-    const float4* src = reinterpret_cast<const float4*>(reinterpret_cast<const T*>(d.nfac) +
-                                                        (long long)r * d.st_fac + sd.q_off);
-    float4* dst = reinterpret_cast<float4*>(Q);
-    const int n4 = (int)((size_t)b * A * A * sizeof(T) / sizeof(float4));
-    for (int e = threadIdx.x; e < n4; e += blockDim.x) dst[e] = src[e];
     const double* tv = d.ntvec + (long long)r * d.st_t + sd.t_off;
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
       t.ex[c] = tv[c];
@@ -575,6 +608,7 @@ __global__ void k_downscale_w(Grid g, DevState d, const DevSub* subs, size_t qof
     const int jl = c / a, il = c - jl * a;
     t.B[c] = qc[(long long)(sd.y0 + jl) * nx + sd.x0 + il] * g.h * g.h;
   }
+  if (qoff != 0) cp_async_wait_all();
   pdl_wait();
   double* uxw = d.ux + (long long)r * g.nfx();
   double* uyw = d.uy + (long long)r * g.nfy();
@@ -677,9 +711,14 @@ template <typename T, int A>
 void mpm_local_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b, int refine,
                  double tol, int ir_max, const DevNode* nodes, const int* leaf_node, cudaStream_t st) {
   size_t bytes, qoff;
-  pair_geometry<T, A>(max_a, max_b, false, bytes, qoff);
+  pair_geometry<T, A>(max_a, max_b, true, bytes, qoff);  // stored factor staged in shared memory ...
+  if (bytes > (size_t)kSmemBudget) {                      // ... unless it does not fit: read from global
+    pair_geometry<T, A>(max_a, max_b, false, bytes, qoff);
+    qoff = 0;
+  }
   set_smem(k_mpm_local_w<T, A>, bytes);
-  k_mpm_local_w<T, A><<<dim3(nsub, g.R), 64, bytes, st>>>(g, d, subs, refine, tol, ir_max, nodes, leaf_node);
+  k_mpm_local_w<T, A><<<dim3(nsub, g.R), kLocalThreads, bytes, st>>>(g, d, subs, qoff, refine, tol, ir_max, nodes,
+                                                                      leaf_node);
   ++g_launches;
 }
 
@@ -698,8 +737,13 @@ void downscale_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub,
                  double tol, int ir_max, bool pdl, cudaStream_t st) {
   size_t bytes, qoff;
   pair_geometry<T, A>(max_a, max_b, true, bytes, qoff);
+  if (bytes > (size_t)kSmemBudget) {  // factor too large for shared memory: read from global
+    pair_geometry<T, A>(max_a, max_b, false, bytes, qoff);
+    qoff = 0;
+  }
   set_smem(k_downscale_w<T, A>, bytes);
-  launch_ex(k_downscale_w<T, A>, dim3(nsub, g.R), dim3(64), bytes, st, pdl, g, d, subs, qoff, refine, tol, ir_max);
+  launch_ex(k_downscale_w<T, A>, dim3(nsub, g.R), dim3(kLocalThreads), bytes, st, pdl, g, d, subs, qoff, refine, tol,
+            ir_max);
 }
 
 }  // namespace

@@ -149,7 +149,8 @@ __device__ __forceinline__ void gj_invert(T (&v)[A * A / 32], int lane) {
 //   bottom  S_{b-1} = D_{b-1}, S_j = D_j - t_j o Q_{j+1} o t_j,          j > mid
 //   middle  S_mid = D_mid - t_{mid-1} o Q_{mid-1} o t_{mid-1} - t_mid o Q_{mid+1} o t_mid
 // with Q_j = S_j^-1 written to Q ([b][A][A], padded).  The critical path is
-// max(mid, b-1-mid) + 1 inversions instead of b.  Requires blockDim.x == 64.
+// max(mid, b-1-mid) + 1 inversions instead of b.  Warps 0 and 1 work; any further warps of
+// the CTA (blockDim.x a multiple of 64) only join the barriers.
 template <typename T, int A>
 __device__ void factor(const DevSub& sd, Tables<T> t, T* Q) {
   constexpr int NR = A * A / 32;
@@ -163,7 +164,7 @@ __device__ void factor(const DevSub& sd, Tables<T> t, T* Q) {
   auto dentry = [&](int j, int r) -> T {
     return r == c ? t.dh[j * A + r] : (c == r + 1 ? t.eh[j * A + r] : (r == c + 1 ? t.eh[j * A + c] : T(0)));
   };
-  const int nsteps = warp == 0 ? mid : b - 1 - mid;
+  const int nsteps = warp == 0 ? mid : warp == 1 ? b - 1 - mid : 0;  // warps >= 2 idle here
   for (int k = 0; k < nsteps; ++k) {
     const int j = warp == 0 ? k : b - 1 - k;
     const int jc = warp == 0 ? j - 1 : j;  // coupling row to the previous block (top: j-1, bottom: j)
@@ -229,7 +230,7 @@ __device__ void solve(const DevSub& sd, Tables<T> t, const T* Q) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = lane % A;
   const int b = sd.b, mid = b / 2;
-  const int nsteps = warp == 0 ? mid : b - 1 - mid;
+  const int nsteps = warp == 0 ? mid : warp == 1 ? b - 1 - mid : 0;  // warps >= 2 idle here
   T w = T(0);
   for (int k = 0; k < nsteps; ++k) {
     const int j = warp == 0 ? k : b - 1 - k;
@@ -248,7 +249,7 @@ __device__ void solve(const DevSub& sd, Tables<T> t, const T* Q) {
     if (lane < A) t.V[mid * A + c] = x;
   }
   __syncthreads();
-  T x = t.V[mid * A + c];
+  T x = warp < 2 ? t.V[mid * A + c] : T(0);
   for (int k = 0; k < nsteps; ++k) {
     const int j = warp == 0 ? mid - 1 - k : mid + 1 + k;
     const int jc = warp == 0 ? j : j - 1;  // coupling to the row solved before
@@ -270,12 +271,13 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Sum / max over the 64 threads of the CTA (red: 4 doubles of shared memory).
+// Sum / max over the CTA (red: one double of shared memory per warp).
 __device__ __forceinline__ double cta_sum(double v, double* red) {
   v = warp_sum(v);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  const double r = red[0] + red[1];
+  double r = red[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r += red[w];
   __syncthreads();
   return r;
 }
@@ -284,9 +286,30 @@ __device__ __forceinline__ double cta_max(double v, double* red) {
   v = warp_max(v);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  const double r = fmax(red[0], red[1]);
+  double r = red[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[w]);
   __syncthreads();
   return r;
+}
+
+// Max over the CTA of two values at once (one pair of barriers).
+__device__ __forceinline__ void cta_max2(double& v1, double& v2, double* red) {
+  v1 = warp_max(v1);
+  v2 = warp_max(v2);
+  const int nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = v1;
+    red[nw + (threadIdx.x >> 5)] = v2;
+  }
+  __syncthreads();
+  double r1 = red[0], r2 = red[nw];
+  for (int w = 1; w < nw; ++w) {
+    r1 = fmax(r1, red[w]);
+    r2 = fmax(r2, red[nw + w]);
+  }
+  __syncthreads();
+  v1 = r1;
+  v2 = r2;
 }
 
 // (A x)_c in flux form (see k_local.cu) and the cell's flux scale.
@@ -305,7 +328,7 @@ __device__ __forceinline__ double apply_A(const DevSub& sd, const double* ex, co
 }
 
 // Refined solve of A x = B (FP64, t.B) into t.X; same stopping rule as the CTA path with
-// target = tol.  All 64 threads; red: 4 doubles of shared memory.
+// target = tol.  All threads of the CTA; red: two doubles of shared memory per warp.
 template <typename T, int A>
 __device__ void solve_refined(const DevSub& sd, Tables<T> t, const T* Q, bool refine, double tol, int ir_max,
                               int* status, int* ir_used, double* red) {
@@ -342,8 +365,7 @@ __device__ void solve_refined(const DevSub& sd, Tables<T> t, const T* Q, bool re
       rmax = fmax(rmax, fabs(r));
       smax = fmax(smax, absx + fabs(t.B[c]));
     }
-    rmax = cta_max(rmax, red);
-    smax = cta_max(smax, red);
+    cta_max2(rmax, smax, red);
     const double eta = smax > 0.0 ? rmax / smax : 0.0;
     if (eta <= target) { ok = true; ++it; break; }
     if (eta > 0.5 * eta_prev && eta <= 1e3 * tol) { ok = true; ++it; break; }  // FP64 floor reached

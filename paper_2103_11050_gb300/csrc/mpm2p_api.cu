@@ -80,6 +80,12 @@ struct mpm_ctx {
   // downscaling solve)
   cudaStream_t side_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool factor_forked = false;  // a fork not yet joined into the main stream
+  // branch of the rebuild body inside a step graph (forked after the decision, joined
+  // before the interface solve)
+  cudaStream_t reb_stream = nullptr;
+  cudaEvent_t ev_reb_fork = nullptr, ev_reb_join = nullptr;
+  bool reb_forked = false;
   // stage profiler
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -299,6 +305,7 @@ int build_tree(mpm_ctx* c, const std::vector<Iface>& ifs, std::vector<HostNode>&
 }
 
 void drop_graph(mpm_ctx* c);
+int join_branches(mpm_ctx* c);
 
 int release_decomposition(mpm_ctx* c) {
   if (!c->dec_allocs.empty()) cudaStreamSynchronize(c->stream);
@@ -358,6 +365,8 @@ int run_interface(mpm_ctx* c) {
   DevState& d = c->d;
   cudaStream_t st = c->stream;
   const int nsub = (int)c->subs.size();
+  int jrc = join_branches(c);
+  if (jrc) return jrc;
   prof_begin(c, MPM_STAGE_IFACE_SOLVE);
   if (c->use_coop && c->coop_blocks < 0) c->coop_blocks = iface_coop_blocks();
   if (c->use_coop && c->coop_blocks > 0) {
@@ -392,28 +401,33 @@ int fork_downscale_factor(mpm_ctx* c) {
   CK(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
   launch_downscale_factor(c->g, c->d, c->d_subs, (int)c->subs.size(), c->max_a, c->max_b, fp32(c), c->side_stream);
   CK(cudaEventRecord(c->ev_join, c->side_stream));
+  c->factor_forked = true;
   return check_launch(c);
 }
 
-int join_downscale_factor(mpm_ctx* c) {
-  CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+// Join every forked branch into the main stream (no-op when none is pending).
+int join_branches(mpm_ctx* c) {
+  if (c->factor_forked) CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  if (c->reb_forked) CK(cudaStreamWaitEvent(c->stream, c->ev_reb_join, 0));
+  c->factor_forked = c->reb_forked = false;
   return MPM_OK;
 }
 
-// Downscaling solve.  after_interface: launched right behind run_interface's chain, so it
-// may use programmatic dependent launch (before waiting it reads only the factor, joined
-// before the launch).  forked: the factor was forked by fork_downscale_factor; otherwise it
-// is computed here on the main stream.
+// Downscaling solve.  after_interface: launched right behind run_interface's chain, whose
+// first kernel was ordered after the forked factorisation, so it may use programmatic
+// dependent launch (before waiting it reads only the factor).  forked: the factor was forked
+// by fork_downscale_factor; otherwise it is computed here on the main stream.
 int run_downscale(mpm_ctx* c, bool after_interface, bool forked) {
   prof_begin(c, MPM_STAGE_DOWNSCALE);
+  const bool joined_before = forked && !c->factor_forked;  // run_interface joined it
   if (forked) {
-    int rc = join_downscale_factor(c);
+    int rc = join_branches(c);
     if (rc) return rc;
   } else {
     launch_downscale_factor(c->g, c->d, c->d_subs, (int)c->subs.size(), c->max_a, c->max_b, fp32(c), c->stream);
   }
   launch_downscale(c->g, c->d, c->d_subs, (int)c->subs.size(), c->max_a, c->max_b, fp32(c), c->ir_tol, c->ir_max,
-                   after_interface && forked && c->use_pdl, c->stream);
+                   after_interface && joined_before && c->use_pdl, c->stream);
   prof_end(c, MPM_STAGE_DOWNSCALE);
   return check_launch(c);
 }
@@ -422,12 +436,12 @@ int run_downscale(mpm_ctx* c, bool after_interface, bool forked) {
 // epsilon partial sums and the Algorithm 1 decision, see launch_upwind_kappa; needs a stored
 // basis).  The saturation buffers swap at every substep: d.s is the new saturation after.
 int run_transport(mpm_ctx* c, double cfl, int n_sub, bool decide, double eta, cudaGraphConditionalHandle h_reb,
-                  cudaGraphConditionalHandle h_mpm, bool set_handles) {
+                  bool set_handle) {
   prof_begin(c, MPM_STAGE_TRANSPORT);
   const double fmax_ = max_fprime(c->g.M);
   for (int k = 0; k < n_sub; ++k) {
     if (k + 1 < n_sub) launch_upwind(c->g, c->d, cfl, fmax_, c->stream);
-    else launch_upwind_kappa(c->g, c->d, cfl, fmax_, decide, eta, h_reb, h_mpm, set_handles, c->stream);
+    else launch_upwind_kappa(c->g, c->d, cfl, fmax_, decide, eta, h_reb, set_handle, c->stream);
     std::swap(c->d.s, c->d.s2);
     std::swap(c->d.fs, c->d.fs2);
   }
@@ -451,10 +465,13 @@ void destroy_streams(mpm_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->body_stream) cudaStreamDestroy(c->body_stream);
   if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  if (c->reb_stream) cudaStreamDestroy(c->reb_stream);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
-  c->cap_stream = c->body_stream = c->side_stream = nullptr;
-  c->ev_fork = c->ev_join = nullptr;
+  if (c->ev_reb_fork) cudaEventDestroy(c->ev_reb_fork);
+  if (c->ev_reb_join) cudaEventDestroy(c->ev_reb_join);
+  c->cap_stream = c->body_stream = c->side_stream = c->reb_stream = nullptr;
+  c->ev_fork = c->ev_join = c->ev_reb_fork = c->ev_reb_join = nullptr;
 }
 
 #define CKG(call)                                                                                         \
@@ -463,14 +480,16 @@ void destroy_streams(mpm_ctx* c) {
     if (e_ != cudaSuccess) {                                                                              \
       c->stream = user;                                                                                   \
       c->d = saved;                                                                                       \
+      c->factor_forked = c->reb_forked = false;                                                           \
       return fail(c, MPM_ERR_CUDA, "graph capture: %s: %s", #call, cudaGetErrorString(e_));              \
     }                                                                                                     \
   } while (0)
 
 // Capture one pass of the Algorithm 1 loop as a CUDA graph for the current saturation
-// buffer parity: transport with kappa^n, the device-side decision and new epsilon,
-// IF(any rebuild){basis build}, IF(any reuse){perturbation solve}, interface solve,
-// downscaling.  Kernel arguments (grid data, pointers, eta, cfl, n_sub) are captured by
+// buffer parity: transport with kappa^n, the device-side decision and new epsilon; then
+// three branches: the downscaling factorisation, IF(any rebuild){basis build}, and the
+// perturbation solve (a no-op for rebuilding realisations); joined before the interface
+// solve; the downscaling solve.  Kernel arguments (grid data, pointers, eta, cfl, n_sub) are captured by
 // value, so setters that change them drop the graph.  The host-side buffer pointers are
 // restored after the capture (nothing has run yet).
 int build_step_graph(mpm_ctx* c, double eta, double cfl, int n_sub) {
@@ -492,33 +511,42 @@ int build_step_graph(mpm_ctx* c, double eta, double cfl, int n_sub) {
   cudaGraph_t cg = nullptr;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndep = 0;
-  cudaGraphConditionalHandle h_reb = 0, h_mpm = 0;
+  cudaGraphConditionalHandle h_reb = 0;
   CKG(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   CKG(cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, &deps, nullptr, &ndep));
   CKG(cudaGraphConditionalHandleCreate(&h_reb, cg, 0, cudaGraphCondAssignDefault));
-  CKG(cudaGraphConditionalHandleCreate(&h_mpm, cg, 0, cudaGraphCondAssignDefault));
-  int rc = run_transport(c, cfl, n_sub, true, eta, h_reb, h_mpm, true);
+  int rc = run_transport(c, cfl, n_sub, true, eta, h_reb, true);
   if (!rc) rc = fork_downscale_factor(c);
   Lb[0] = g_launches;
-  for (int branch = 1; branch >= 0 && !rc; --branch) {
-    CKG(cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, &deps, nullptr, &ndep));
+  if (!rc) {
+    // rebuild body: IF(any realisation rebuilds) on its own branch, joined before the
+    // interface solve, so that evaluating the condition overlaps the perturbation solve
+    cudaStream_t rs = c->reb_stream;
+    CKG(cudaEventRecord(c->ev_reb_fork, cs));
+    CKG(cudaStreamWaitEvent(rs, c->ev_reb_fork, 0));
+    CKG(cudaStreamGetCaptureInfo(rs, &stt, nullptr, &cg, &deps, nullptr, &ndep));
     cudaGraphNodeParams np{};
     np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = branch ? h_reb : h_mpm;
+    np.conditional.handle = h_reb;
     np.conditional.type = cudaGraphCondTypeIf;
     np.conditional.size = 1;
     cudaGraphNode_t node;
     CKG(cudaGraphAddNode(&node, cg, deps, nullptr, ndep, &np));
-    CKG(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CKG(cudaStreamUpdateCaptureDependencies(rs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
     cudaGraph_t body = np.conditional.phGraph_out[0];
     CKG(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     c->stream = bs;
-    rc = branch ? run_build(c) : run_perturbation(c);
+    rc = run_build(c);
     c->stream = cs;
     cudaGraph_t body_out = nullptr;
     CKG(cudaStreamEndCapture(bs, &body_out));
-    Lb[2 - branch] = g_launches;
+    CKG(cudaEventRecord(c->ev_reb_join, rs));
+    c->reb_forked = true;
   }
+  Lb[1] = g_launches;
+  // perturbation solve: every realisation's kernel returns at once where it rebuilds
+  if (!rc) rc = run_perturbation(c);
+  Lb[2] = Lb[1];
   if (!rc) rc = run_interface(c);
   if (!rc) rc = run_downscale(c, true, true);
   cudaGraph_t graph = nullptr;
@@ -526,6 +554,7 @@ int build_step_graph(mpm_ctx* c, double eta, double cfl, int n_sub) {
   c->stream = user;
   c->prof = prof;
   c->d = saved;
+  c->factor_forked = c->reb_forked = false;
   if (rc) {
     if (graph) cudaGraphDestroy(graph);
     return rc;
@@ -539,8 +568,8 @@ int build_step_graph(mpm_ctx* c, double eta, double cfl, int n_sub) {
   }
   c->graph_valid[slot] = true;
   c->gk_reb = Lb[1] - Lb[0];
-  c->gk_mpm = Lb[2] - Lb[1];
-  c->gk_base = (g_launches - L0) - c->gk_reb - c->gk_mpm;
+  c->gk_mpm = 0;  // the perturbation kernel is launched at every step (counted in gk_base)
+  c->gk_base = (g_launches - L0) - c->gk_reb;
   c->capture_launches += g_launches - L0;
   c->g_eta = eta;
   c->g_cfl = cfl;
@@ -607,8 +636,11 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   if (rc == MPM_OK && (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
                        cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking) != cudaSuccess ||
                        cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+                       cudaStreamCreateWithFlags(&c->reb_stream, cudaStreamNonBlocking) != cudaSuccess ||
                        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-                       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess))
+                       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&c->ev_reb_fork, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&c->ev_reb_join, cudaEventDisableTiming) != cudaSuccess))
     rc = MPM_ERR_CUDA;
   if (rc == MPM_OK && cudaMallocHost(&c->h_flags, sizeof(int) * R) != cudaSuccess) rc = MPM_ERR_OOM;
   if (rc != MPM_OK) {
@@ -1033,7 +1065,7 @@ int mpm_saturation_step(mpm_ctx* c, double cfl, int n_sub, double* dt) {
   if (!(cfl > 0 && cfl <= 1) || n_sub < 1) return fail(c, MPM_ERR_ARG, "need 0 < cfl <= 1 and n_sub >= 1");
   int rc = need_ready(c, false);
   if (rc) return rc;
-  if ((rc = run_transport(c, cfl, n_sub, false, 0.0, 0, 0, false))) return rc;
+  if ((rc = run_transport(c, cfl, n_sub, false, 0.0, 0, false))) return rc;
   if (dt) return copy_out(c, dt, c->d.dt, c->g.R, MPM_MEM_HOST);
   return MPM_OK;
 }
@@ -1076,7 +1108,7 @@ int mpm_step(mpm_ctx* c, double eta, double cfl, int n_sub) {
     return MPM_OK;
   }
   // eager path: the host reads the device decision to skip the branch nobody takes
-  if ((rc = run_transport(c, cfl, n_sub, true, eta, 0, 0, false))) return rc;
+  if ((rc = run_transport(c, cfl, n_sub, true, eta, 0, false))) return rc;
   if ((rc = fork_downscale_factor(c))) return rc;
   CK(cudaMemcpyAsync(c->h_flags, c->d.rebuild, sizeof(int) * c->g.R, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));

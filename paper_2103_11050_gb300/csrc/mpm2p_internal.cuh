@@ -166,8 +166,7 @@ void launch_fill_flags(const Grid& g, const DevState& d, int v, cudaStream_t st)
 void launch_upwind(const Grid& g, const DevState& d, double cfl, double fmax, cudaStream_t st);
 int upwind_kappa_blocks(const Grid& g);
 void launch_upwind_kappa(const Grid& g, const DevState& d, double cfl, double fmax, bool decide, double eta,
-                         cudaGraphConditionalHandle h_reb, cudaGraphConditionalHandle h_mpm, bool set_handles,
-                         cudaStream_t st);
+                         cudaGraphConditionalHandle h_reb, bool set_handle, cudaStream_t st);
 
 int local_smem_limit();
 void launch_robin_factor(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
