@@ -115,7 +115,8 @@ int mpm_destroy(mpm_ctx* ctx);
 const char* mpm_last_error(const mpm_ctx* ctx);
 
 /* Local solver precision (enum above).  ir_tol: target of the refinement, as a backward
- * error in flux units (max |residual| / max(|rhs| + sum |face fluxes|) over the subdomain;
+ * error in flux units (max |residual| / max(|rhs| + sum |face fluxes|) over the subdomain,
+ * the face fluxes of the first iterate;
  * default 1e-14; ignored for FP64), ir_max: sweep cap (>= 1).  Refinement stops at ir_tol
  * (1e-3 ir_tol for the basis-function solves, whose traces are combined with the interface
  * coefficients), or when a sweep no longer halves the error (the FP64 rounding floor of the

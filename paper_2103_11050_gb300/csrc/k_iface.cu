@@ -49,8 +49,9 @@ __global__ void k_element_matrix(Grid g, DevState d, const DevSub* subs, const D
   if (nd == 0) return;
   const DevNode leaf = nodes[leaf_node[sidx]];
   double* E = d.front + (long long)r * d.st_front + leaf.f_off;
-  const double* tr = d.tr + (long long)r * d.st_tr + sd.tr_off;
+  const double* tr = d.tr + (long long)r * d.st_tr + sd.tr_off;  // [nd][nface]
   const double* bhat = d.bhat + (long long)r * d.st_face + sd.face_off;
+  const int nface = 2 * (sd.a + sd.b);
   for (int e = threadIdx.x; e < nd * nd; e += blockDim.x) {
     const int k = e / nd, l = e - k * nd;
     int side, isP, kk;
@@ -64,7 +65,7 @@ __global__ void k_element_matrix(Grid g, DevState d, const DevSub* subs, const D
     for (int t = 0; t < L; ++t) {
       const double w = side_basis(kk, t, g.seg_len, g.degree);
       if (w == 0.0) continue;
-      const double F = tr[(long long)(f0 + t) * nd + l];
+      const double F = tr[(long long)l * nface + f0 + t];
       if (isP) {
         v += w * F;
       } else {
@@ -349,14 +350,17 @@ __global__ void __launch_bounds__(256) k_nd_down(Grid g, DevState d, const DevNo
 }
 
 // Reconstruction from the interface solution c of one subdomain per CTA (c gathered from the
-// leaf's parent vector): the one-sided traces F = Fbar + F_hat c, one face per warp at a time
-// (rows of F_hat are contiguous), then the target mean of the downscaled pressure, and at a
-// rebuild the MRCM-level pressure p^m = pbar + P_hat c (P_hat stored column by column):
+// leaf's parent vector): the one-sided traces F = Fbar + F_hat c, then the target mean of the
+// downscaled pressure, and at a rebuild the MRCM-level pressure p^m = pbar + P_hat c:
 //   rebuild: target = mean(p^m);  MPM-2P: target = mean(p^m) + mean(dpbar) + mu_hat . dc.
-// branch >= 0 restricts the launch to the realisations that took that branch.
-template <int NR>
+// F_hat and P_hat are stored one column per BF, so thread (face f, chunk q) sums F_hat[l][f]
+// c[l] over l = q, q + KS, ... with coalesced loads (its first kKpt terms loaded before
+// pdl_wait()), and the KS chunks combine in shared memory.  branch >= 0 restricts the launch
+// to the realisations that took that branch.
+template <int KS>
 __global__ void __launch_bounds__(256) k_reconstruct(Grid g, DevState d, const DevSub* subs, const DevNode* nodes,
                                                      const int* leaf_node, const int* pmap, int branch) {
+  constexpr int FACES = 256 / KS;
   extern __shared__ __align__(16) double nd_smem[];
   __shared__ double red[32];
   pdl_trigger();
@@ -366,64 +370,60 @@ __global__ void __launch_bounds__(256) k_reconstruct(Grid g, DevState d, const D
   const DevSub& sd = subs[sidx];
   const int a = sd.a, b = sd.b, m = a * b, nd = sd.ndof, nface = 2 * (a + b);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double* cs = nd_smem;                              // nd
-  int* pidx = reinterpret_cast<int*>(cs + nd);       // nd
+  double* part = nd_smem;                            // [KS][FACES]
+  double* cs = nd_smem + 256;                        // nd
+  const int f = threadIdx.x % FACES, q = threadIdx.x / FACES;
+  const double* trb = d.tr + (long long)r * d.st_tr + sd.tr_off;
+  double v[kKpt];
+#pragma unroll
+  for (int u = 0; u < kKpt; ++u) {
+    const int l = q + u * KS;
+    v[u] = (f < nface && l < nd) ? trb[(long long)l * nface + f] : 0.0;
+  }
+  const double fbar = f < nface && q == 0 ? d.fbar[(long long)r * d.st_face + sd.face_off + f] : 0.0;
   const double* xp = nullptr;
+  const int* pm = nullptr;
   if (nd > 0) {
     const DevNode& leaf = nodes[leaf_node[sidx]];
     xp = d.xvec + (long long)r * d.st_vec + nodes[leaf.parent].v_off;
-    const int* pm = pmap + leaf.pmap_off;
-    for (int l = threadIdx.x; l < nd; l += blockDim.x) pidx[l] = pm[l];
+    pm = pmap + leaf.pmap_off;
   }
-  __syncthreads();
   pdl_wait();
-  for (int l = threadIdx.x; l < nd; l += blockDim.x) cs[l] = xp[pidx[l]];
+  for (int l = threadIdx.x; l < nd; l += blockDim.x) cs[l] = xp[pm[l]];
   __syncthreads();
-  const double* trb = d.tr + (long long)r * d.st_tr + sd.tr_off;
-  const double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
-  double* trace = d.trace + (long long)r * d.st_face + sd.face_off;
-  for (int f0 = warp; f0 < nface; f0 += 2 * nw) {  // two faces per warp per pass
-    const int f1 = f0 + nw;
-    const bool two = f1 < nface;
-    const double* t0 = trb + (long long)f0 * nd;
-    const double* t1 = trb + (long long)(two ? f1 : f0) * nd;
-    double acc0 = 0.0, acc1 = 0.0;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-    for (int i = 0; i < NR; ++i) {
-      const int k = lane + 32 * i;
-      if (k < nd) {
-        acc0 += t0[k] * cs[k];
-        acc1 += t1[k] * cs[k];
-      }
-    }
-    for (int k = lane + 32 * NR; k < nd; k += 32) {
-      acc0 += t0[k] * cs[k];
-      acc1 += t1[k] * cs[k];
-    }
-    acc0 = phase::warp_sum(acc0);
-    acc1 = phase::warp_sum(acc1);
-    if (lane == 0) {
-      trace[f0] = fbar[f0] + acc0;
-      if (two) trace[f1] = fbar[f1] + acc1;
-    }
+  for (int u = 0; u < kKpt; ++u) {
+    const int l = q + u * KS;
+    if (l < nd) acc[u & 3] += v[u] * cs[l];
   }
-  double part = 0.0;
+  if (f < nface)
+    for (int l = q + kKpt * KS; l < nd; l += KS) acc[0] += trb[(long long)l * nface + f] * cs[l];
+  part[q * FACES + f] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  __syncthreads();
+  if (q == 0 && f < nface) {
+    double sum = part[f];
+#pragma unroll
+    for (int u = 1; u < KS; ++u) sum += part[u * FACES + f];
+    d.trace[(long long)r * d.st_face + sd.face_off + f] = fbar + sum;
+  }
+  double pt = 0.0;
   if (br == 1) {
     const double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;  // [nd + 1][m]
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
-      double v = pf[(long long)nd * m + c];
-      for (int l = 0; l < nd; ++l) v += pf[(long long)l * m + c] * cs[l];
+      double pv = pf[(long long)nd * m + c];
+      for (int l = 0; l < nd; ++l) pv += pf[(long long)l * m + c] * cs[l];
       const int jl = c / a, il = c - jl * a;
-      d.p_m[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il] = v;
-      part += v;
+      d.p_m[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il] = pv;
+      pt += pv;
     }
   } else {
     const double* muh = d.mu_hat + (long long)r * d.st_dof + sd.dof_off;
-    for (int l = threadIdx.x; l < nd; l += blockDim.x) part += muh[l] * cs[l];
-    part *= m;
+    for (int l = threadIdx.x; l < nd; l += blockDim.x) pt += muh[l] * cs[l];
+    pt *= m;
   }
-  part = phase::warp_sum(part);
-  if (lane == 0) red[warp] = part;
+  pt = phase::warp_sum(pt);
+  if (lane == 0) red[warp] = pt;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
@@ -551,26 +551,6 @@ void launch_nd_factor_level(const Grid& g, const DevState& d, const DevNode* nod
 }
 
 namespace {
-// Register chunks per lane for a row of n columns: smallest power of two >= n / 32, at most
-// 16 (longer rows finish with a loop over global memory).
-int row_chunks(int n) {
-  const int q = (n + 31) / 32;
-  return q <= 1 ? 1 : q <= 2 ? 2 : q <= 4 ? 4 : q <= 8 ? 8 : 16;
-}
-}  // namespace
-
-#define MPM_DISPATCH_NR(KERNEL, nr, ...)                        \
-  do {                                                          \
-    switch (nr) {                                               \
-      case 1: launch_ex(KERNEL<1>, __VA_ARGS__); break;         \
-      case 2: launch_ex(KERNEL<2>, __VA_ARGS__); break;         \
-      case 4: launch_ex(KERNEL<4>, __VA_ARGS__); break;         \
-      case 8: launch_ex(KERNEL<8>, __VA_ARGS__); break;         \
-      default: launch_ex(KERNEL<16>, __VA_ARGS__); break;       \
-    }                                                           \
-  } while (0)
-
-namespace {
 // k-chunks per output row: each thread sums at most about 16 terms.
 int k_split(int n) {
   const int q = (n + 15) / 16;
@@ -608,11 +588,11 @@ void launch_nd_down(const Grid& g, const DevState& d, const DevNode* nodes, cons
 void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_face, int max_dof,
                         const DevNode* nodes, const int* leaf_node, const int* pmap, int branch, bool pdl,
                         cudaStream_t st) {
-  (void)max_face;
-  const dim3 grid(nsub, g.R);
-  const size_t smem = (size_t)(max_dof > 0 ? max_dof : 1) * (sizeof(double) + sizeof(int));
-  MPM_DISPATCH_NR(k_reconstruct, row_chunks(max_dof), grid, dim3(256), smem, st, pdl, g, d, subs, nodes, leaf_node,
-                  pmap, branch);
+  const int faces = max_face <= 16 ? 16 : max_face <= 32 ? 32 : max_face <= 64 ? 64 : 128;
+  const int ks = 256 / faces;
+  const size_t smem = (size_t)(256 + (max_dof > 0 ? max_dof : 1)) * sizeof(double);
+  MPM_DISPATCH_KS(k_reconstruct, ks, dim3(nsub, g.R), dim3(256), smem, st, pdl, g, d, subs, nodes, leaf_node, pmap,
+                  branch);
 }
 
 }  // namespace mpm

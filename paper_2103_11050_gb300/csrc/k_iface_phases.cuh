@@ -143,7 +143,7 @@ __device__ inline void reconstruct(const Grid& g, const DevState& d, const DevSu
   double* trace = d.trace + (long long)r * d.st_face + sd.face_off;
   for (int f = threadIdx.x; f < nface; f += blockDim.x) {
     double v = fbar[f];
-    for (int l = 0; l < nd; ++l) v += tr[(long long)f * nd + l] * cs[l];
+    for (int l = 0; l < nd; ++l) v += tr[(long long)l * nface + f] * cs[l];
     trace[f] = v;
   }
   double part = 0.0;

@@ -365,7 +365,7 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
   const int ntot = sd.ndof + 1;
   Carve<T> cv = carve<T>(smem, a, b, A, ncol_max);
   load_robin<T>(d, sd, r, cv, g, A);
-  double* tr = d.tr + (long long)r * d.st_tr + sd.tr_off;       // [nface][ndof]
+  double* tr = d.tr + (long long)r * d.st_tr + sd.tr_off;       // [ndof][nface]
   double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;       // [ndof+1][m]
   double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
   double* muh = d.mu_hat + (long long)r * d.st_dof + sd.dof_off;
@@ -387,7 +387,7 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
     for (int e = threadIdx.x; e < nface * ncol; e += blockDim.x) {
       const int f = e / ncol, col = e - f * ncol, bcol = c0 + col;
       const double v = basis_trace(g, sd, cv.S, cv.X, ncol, f, col, bcol, bcol < sd.ndof);
-      if (bcol < sd.ndof) tr[(long long)f * sd.ndof + bcol] = v;
+      if (bcol < sd.ndof) tr[(long long)bcol * nface + f] = v;
       else fbar[f] = v;
     }
     // column means

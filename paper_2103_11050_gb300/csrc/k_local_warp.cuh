@@ -312,6 +312,20 @@ __device__ __forceinline__ void cta_max2(double& v1, double& v2, double* red) {
   v2 = r2;
 }
 
+// (A x)_c in flux form (see k_local.cu).
+__device__ __forceinline__ double apply_A(const DevSub& sd, const double* ex, const double* wE, const double* wN,
+                                          const double* x, int c) {
+  const int a = sd.a, b = sd.b;
+  const int jl = c / a, il = c - jl * a;
+  const double xc = x[c];
+  double t0 = ex[c] * xc, t1 = 0.0, t2 = 0.0, t3 = 0.0, t4 = 0.0;
+  if (il < a - 1) t1 = wE[c] * (xc - x[c + 1]);
+  if (il > 0) t2 = wE[c - 1] * (xc - x[c - 1]);
+  if (jl < b - 1) t3 = wN[c] * (xc - x[c + a]);
+  if (jl > 0) t4 = wN[c - a] * (xc - x[c - a]);
+  return (t0 + t1) + (t2 + t3) + t4;
+}
+
 // (A x)_c in flux form (see k_local.cu) and the cell's flux scale.
 __device__ __forceinline__ double apply_A(const DevSub& sd, const double* ex, const double* wE, const double* wN,
                                           const double* x, int c, double& absx) {
@@ -343,7 +357,7 @@ __device__ void solve_refined(const DevSub& sd, Tables<T> t, const T* Q, bool re
   const int sweeps = refine ? ir_max : 1;
   int it = 0;
   bool ok = false;
-  double eta_prev = 1e300;
+  double eta_prev = 1e300, smax = 0.0;
   for (; it < sweeps; ++it) {
     for (int e = tid; e < b * A; e += nt) {
       const int j = e / A, i = e - j * A;
@@ -357,15 +371,26 @@ __device__ void solve_refined(const DevSub& sd, Tables<T> t, const T* Q, bool re
     }
     __syncthreads();
     if (!refine) { it = 1; ok = true; break; }
-    double rmax = 0.0, smax = 0.0;
-    for (int c = tid; c < m; c += nt) {
-      double absx;
-      const double r = t.B[c] - apply_A(sd, t.ex, t.wE, t.wN, t.X, c, absx);
-      t.Rr[c] = r;
-      rmax = fmax(rmax, fabs(r));
-      smax = fmax(smax, absx + fabs(t.B[c]));
+    double rmax = 0.0;
+    if (it == 0) {  // the scale max(|A||x| + |b|) is taken once, at the first iterate
+      double sm = 0.0;
+      for (int c = tid; c < m; c += nt) {
+        double absx;
+        const double r = t.B[c] - apply_A(sd, t.ex, t.wE, t.wN, t.X, c, absx);
+        t.Rr[c] = r;
+        rmax = fmax(rmax, fabs(r));
+        sm = fmax(sm, absx + fabs(t.B[c]));
+      }
+      cta_max2(rmax, sm, red);
+      smax = sm;
+    } else {
+      for (int c = tid; c < m; c += nt) {
+        const double r = t.B[c] - apply_A(sd, t.ex, t.wE, t.wN, t.X, c);
+        t.Rr[c] = r;
+        rmax = fmax(rmax, fabs(r));
+      }
+      rmax = cta_max(rmax, red);
     }
-    cta_max2(rmax, smax, red);
     const double eta = smax > 0.0 ? rmax / smax : 0.0;
     if (eta <= target) { ok = true; ++it; break; }
     if (eta > 0.5 * eta_prev && eta <= 1e3 * tol) { ok = true; ++it; break; }  // FP64 floor reached

@@ -121,7 +121,7 @@ struct DevState {
   double* tvec;        // [ex, wE, wN, sc] per subdomain (4 m), st_t
   void* nfac;          // downscaling (pinned Neumann) factors of kappa^n, same layout as fac
   double* ntvec;       // their [ex, wE, wN, sc], same layout as tvec
-  double* tr;          // BF traces (2(a+b) x ndof), st_tr
+  double* tr;          // BF traces, one column of 2(a+b) faces per BF (ndof x 2(a+b)), st_tr
   double* pf;          // BF pressures, one column of m cells per BF ((ndof + 1) x m), st_pf
   double* mu_hat;      // BF means, st_dof
   double* fbar;        // non-homogeneous / perturbation traces, st_face
