@@ -108,26 +108,32 @@ __device__ __forceinline__ double cfl_dt(const Grid& g, const DevState& d, int r
 }
 
 // Explicit upwind update of cell (i, j) (Eq. BL2D): s - dt/h^2 sum_faces F_out f(s_upwind),
-// with f(s) read from fs; inflow through the boundary carries f(s_inflow) = f_in.
+// with f(s) read from fs; inflow through the boundary carries f(s_inflow) = f_in.  The sign
+// of each face flux is read from its bit pattern (integer compares instead of float64 ones;
+// -0 counts as zero like +0), and the outward flux enters through a fused multiply-add.
+__device__ __forceinline__ bool dpos(double v) { return __double_as_longlong(v) > 0; }
+__device__ __forceinline__ bool dneg(double v) {
+  const long long b = __double_as_longlong(v);
+  return b < 0 && b != (long long)0x8000000000000000ull;
+}
 __device__ __forceinline__ double upwind_cell(const Grid& g, const double* ux, const double* uy, const double* fs,
                                               const double* s, double lam, double f_in, int i, int j) {
   const int nx = g.nx, ny = g.ny;
   const long long c = (long long)j * nx + i;
   const double fc = fs[c];
-  double acc = 0.0, F;
-  F = -ux[(long long)j * (nx + 1) + i];
-  if (F > 0.0) acc += F * fc;
-  else if (F < 0.0) acc += F * (i > 0 ? fs[c - 1] : f_in);
-  F = ux[(long long)j * (nx + 1) + i + 1];
-  if (F > 0.0) acc += F * fc;
-  else if (F < 0.0) acc += F * (i < nx - 1 ? fs[c + 1] : f_in);
-  F = -uy[(long long)j * nx + i];
-  if (F > 0.0) acc += F * fc;
-  else if (F < 0.0) acc += F * (j > 0 ? fs[c - nx] : f_in);
-  F = uy[(long long)(j + 1) * nx + i];
-  if (F > 0.0) acc += F * fc;
-  else if (F < 0.0) acc += F * (j < ny - 1 ? fs[c + nx] : f_in);
-  return s[c] - lam * acc;
+  const double uw = ux[(long long)j * (nx + 1) + i], ue = ux[(long long)j * (nx + 1) + i + 1];
+  const double us = uy[(long long)j * nx + i], un = uy[(long long)(j + 1) * nx + i];
+  double acc = 0.0;
+  // outward fluxes: west -uw, east ue, south -us, north un
+  if (dneg(uw)) acc = fma(-uw, fc, acc);
+  else if (dpos(uw)) acc = fma(-uw, i > 0 ? fs[c - 1] : f_in, acc);
+  if (dpos(ue)) acc = fma(ue, fc, acc);
+  else if (dneg(ue)) acc = fma(ue, i < nx - 1 ? fs[c + 1] : f_in, acc);
+  if (dneg(us)) acc = fma(-us, fc, acc);
+  else if (dpos(us)) acc = fma(-us, j > 0 ? fs[c - nx] : f_in, acc);
+  if (dpos(un)) acc = fma(un, fc, acc);
+  else if (dneg(un)) acc = fma(un, j < ny - 1 ? fs[c + nx] : f_in, acc);
+  return fma(-lam, acc, s[c]);
 }
 
 // One upwind substep s -> s2 with f(s2) -> fs2 (all substeps but the last).

@@ -44,7 +44,10 @@ __global__ void k_element_matrix(Grid g, DevState d, const DevSub* subs, const D
   const int r = blockIdx.y;
   if (d.rebuild[r] != 1) return;
   const int sidx = blockIdx.x;
-  const DevSub sd = subs[sidx];
+  __shared__ DevSub sd_s;  // the subdomain record, staged once per CTA (indexed by side)
+  if (threadIdx.x == 0) sd_s = subs[sidx];
+  __syncthreads();
+  const DevSub& sd = sd_s;
   const int nd = sd.ndof;
   if (nd == 0) return;
   const DevNode leaf = nodes[leaf_node[sidx]];

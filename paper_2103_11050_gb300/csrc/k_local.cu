@@ -359,7 +359,10 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
   extern __shared__ __align__(16) char smem[];
   const int r = blockIdx.y;
   if (d.rebuild[r] != 1) return;
-  const DevSub sd = subs[blockIdx.x];
+  __shared__ DevSub sd_s;  // the subdomain record, staged once per CTA (indexed by side)
+  if (threadIdx.x == 0) sd_s = subs[blockIdx.x];
+  __syncthreads();
+  const DevSub& sd = sd_s;
   const int a = sd.a, b = sd.b, m = a * b;
   const int nface = 2 * (a + b);
   const int ntot = sd.ndof + 1;
@@ -428,7 +431,10 @@ __global__ void k_robin_factor_w(Grid g, DevState d, const DevSub* subs, int sca
   const int sidx = blockIdx.x;
   const int r = blockIdx.y;
   if (d.rebuild[r] != 1) return;
-  const DevSub sd = subs[sidx];
+  __shared__ DevSub sd_s;  // the subdomain record, staged once per CTA (indexed by side)
+  if (threadIdx.x == 0) sd_s = subs[sidx];
+  __syncthreads();
+  const DevSub& sd = sd_s;
   const int m = sd.a * sd.b;
   warp::Tables<T> t = warp::carve<T, A>(smem, m, sd.b);
   load_kappa_cta(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap);
@@ -469,7 +475,10 @@ __global__ void __launch_bounds__(kLocalThreads) k_mpm_local_w(Grid g, DevState 
   const int sidx = blockIdx.x;
   const int r = blockIdx.y;
   if (d.rebuild[r] != 0) return;
-  const DevSub sd = subs[sidx];
+  __shared__ DevSub sd_s;  // the subdomain record, staged once per CTA (indexed by side)
+  if (threadIdx.x == 0) sd_s = subs[sidx];
+  __syncthreads();
+  const DevSub& sd = sd_s;
   const int a = sd.a, b = sd.b, m = a * b;
   warp::Tables<T> t = warp::carve<T, A>(smem, m, b);
   const T* Qg = reinterpret_cast<const T*>(d.fac) + (long long)r * d.st_fac + sd.q_off;
@@ -547,7 +556,10 @@ __global__ void k_downscale_factor_w(Grid g, DevState d, const DevSub* subs, int
   extern __shared__ __align__(16) char smem[];
   const int sidx = blockIdx.x;
   const int r = blockIdx.y;
-  const DevSub sd = subs[sidx];
+  __shared__ DevSub sd_s;  // the subdomain record, staged once per CTA (indexed by side)
+  if (threadIdx.x == 0) sd_s = subs[sidx];
+  __syncthreads();
+  const DevSub& sd = sd_s;
   const int m = sd.a * sd.b;
   warp::Tables<T> t = warp::carve<T, A>(smem, m, sd.b);
   load_kappa_cta(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap);
@@ -579,7 +591,10 @@ __global__ void __launch_bounds__(kLocalThreads) k_downscale_w(Grid g, DevState 
   __shared__ int last;
   const int sidx = blockIdx.x;
   const int r = blockIdx.y;
-  const DevSub sd = subs[sidx];
+  __shared__ DevSub sd_s;  // the subdomain record, staged once per CTA (indexed by side)
+  if (threadIdx.x == 0) sd_s = subs[sidx];
+  __syncthreads();
+  const DevSub& sd = sd_s;
   const int a = sd.a, b = sd.b, m = a * b, nx = g.nx;
   warp::Tables<T> t = warp::carve<T, A>(smem, m, b);
   const T* Qg = reinterpret_cast<const T*>(d.nfac) + (long long)r * d.st_fac + sd.q_off;
