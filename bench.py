@@ -32,6 +32,9 @@ sys.path.insert(0, ROOT)
 from paper_2103_11050_gb300 import fields  # noqa: E402
 
 WORKLOAD = "gaussian256"
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_downscale_w launch (ncu capture of
+# this code, see profiles/); None when the kernel changed since the capture.
+TRAFFIC_DOWNSCALE_SOLVE = None
 METRIC = "fine-cell pressure updates/s (MRCM & MPM-2P) at <=1e-8 rel flux err vs FP64"
 UNIT = "cell-updates/s"
 CFL = 0.5
@@ -125,19 +128,21 @@ def setup_ctx(B, w, K, s0, prec, stream, R=1):
     return ctx
 
 
-def algorithmic_downscale(w):
-    """Useful FP work and bytes of one downscaling launch (all subdomains).
+def algorithmic_downscale_solve(w):
+    """Algorithmic work of one launch of the downscaling solve (all subdomains).
 
-    Per a x b subdomain: block factorisation b Gauss-Jordan inversions of a x a
-    (a^3 FMA each, 2 flops), the two block sweeps (2 b a^2 FMA), the FP64 refinement
-    residual (5 terms per cell); bytes: read kappa^n (8/cell) and the boundary fluxes,
-    write p~ and the interior fluxes (~24/cell)."""
+    Per a x b subdomain: one block-tridiagonal solve with explicit inverse pivots, 2b dense
+    a x a matrix-vector products (4 b a^2 flop); one flux-form residual of the refinement
+    check (14 flop per cell); the interior fine fluxes (2 faces x 2 flop per cell).  Bytes:
+    the stored factor is read once (b a^2 float32), kappa-dependent stencil (32 B/cell), q
+    (8 B/cell), writes p~ and the interior fluxes (24 B/cell)."""
     a = w["nx"] // w["ncx"]
     b = w["ny"] // w["ncy"]
     nsub = w["ncx"] * w["ncy"]
-    flops = nsub * (2.0 * b * a ** 3 + 2.0 * 2 * b * a * a)
-    cells = w["nx"] * w["ny"]
-    return flops, 32.0 * cells
+    m = a * b
+    flops = nsub * (4.0 * b * a * a + 14.0 * m + 4.0 * m)
+    byts = nsub * (4.0 * b * a * a + 64.0 * m)
+    return flops, byts
 
 
 def run_gpu(args, w):
@@ -224,13 +229,16 @@ def run_gpu(args, w):
     prof = main["prof"]
     ds_ms, ds_n = prof["downscale"]
     dom = max(prof, key=lambda k: prof[k][0])
-    flops, _bytes = algorithmic_downscale(w)
+    flops, _bytes = algorithmic_downscale_solve(w)
     ds_avg_s = ds_ms / 1e3 / max(ds_n, 1)
     sm_clock = 2070.0
-    fp_peak = (152 * 128 * 2 * sm_clock * 1e6 / 1e12) if prec != "fp64" else (152 * 2 * 2 * sm_clock * 1e6 / 1e12)
-    roof = {"kernel": "k_downscale", "bound": "alu", "achieved": flops / ds_avg_s / 1e12,
-            "peak": fp_peak, "unit": "TFLOP/s", "frac": (flops / ds_avg_s / 1e12) / fp_peak, "traffic": None,
-            "peak_kind": f"derived: 152 SMs x {'128 FP32' if prec != 'fp64' else '2 FP64'} FMA/clk x 2 x 2070 MHz",
+    fp64_peak = 152 * 2 * 2 * sm_clock * 1e6 / 1e12  # TFLOP/s
+    roof = {"kernel": "k_downscale_w", "bound": "alu", "achieved": flops / ds_avg_s / 1e12,
+            "peak": fp64_peak, "unit": "TFLOP/s", "frac": (flops / ds_avg_s / 1e12) / fp64_peak,
+            "traffic": TRAFFIC_DOWNSCALE_SOLVE,
+            "peak_kind": "derived: float64 pipe, 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (fallback table's "
+                         "nominal 1.25 TFLOP/s; not in MEASURED_PEAKS.json)",
+            "avg_launch_us": ds_avg_s * 1e6,
             "dominant_stage": dom,
             "stage_ms_per_step_eager": {k: v[0] / args.steps for k, v in prof.items()},
             "eager_ms_per_step": prof_run["ms"] / args.steps}

@@ -418,12 +418,13 @@ int join_branches(mpm_ctx* c) {
 // dependent launch (before waiting it reads only the factor).  forked: the factor was forked
 // by fork_downscale_factor; otherwise it is computed here on the main stream.
 int run_downscale(mpm_ctx* c, bool after_interface, bool forked) {
-  prof_begin(c, MPM_STAGE_DOWNSCALE);
   const bool joined_before = forked && !c->factor_forked;  // run_interface joined it
   if (forked) {
     int rc = join_branches(c);
     if (rc) return rc;
-  } else {
+  }
+  prof_begin(c, MPM_STAGE_DOWNSCALE);
+  if (!forked) {
     launch_downscale_factor(c->g, c->d, c->d_subs, (int)c->subs.size(), c->max_a, c->max_b, fp32(c), c->stream);
   }
   launch_downscale(c->g, c->d, c->d_subs, (int)c->subs.size(), c->max_a, c->max_b, fp32(c), c->ir_tol, c->ir_max,
