@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_upwind_kappa(Grid g, DevState d, 
   __shared__ double sn[kTY + 1][kTX + 1];  // s2
   __shared__ double sk[kTY + 1][kTX + 1];  // kappa^n of s2
   __shared__ double sh[32];
-  __shared__ double lam_s;
+  __shared__ double lam_s, fin_s;
   __shared__ int last, tot;
   const int r = blockIdx.y;
   const int nx = g.nx, ny = g.ny;
@@ -184,12 +184,12 @@ __global__ void __launch_bounds__(kTX * kTY) k_upwind_kappa(Grid g, DevState d, 
     const double dt = cfl_dt(g, d, r, cfl, fmax_);
     if (blockIdx.x == 0) d.dt[r] = dt;
     lam_s = dt / (g.h * g.h);
+    fin_s = fracflow(g.s_inflow, g.M);
   }
   __syncthreads();
-  const double lam = lam_s;
+  const double lam = lam_s, f_in = fin_s;
   const double* ux = d.ux + (long long)r * g.nfx();
   const double* uy = d.uy + (long long)r * g.nfy();
-  const double f_in = fracflow(g.s_inflow, g.M);
   for (int e = threadIdx.x; e < (kTX + 1) * (kTY + 1); e += blockDim.x) {
     const int li = e % (kTX + 1), lj = e / (kTX + 1);
     const int i = tx0 + li, j = ty0 + lj;

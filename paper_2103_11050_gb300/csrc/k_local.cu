@@ -656,7 +656,10 @@ __global__ void __launch_bounds__(kLocalThreads) k_downscale_w(Grid g, DevState 
   double s = 0.0;
   for (int c = threadIdx.x; c < m; c += blockDim.x) s += t.X[c];
   s = warp::cta_sum(s, red);
-  const double shift = d.sub_target[(long long)r * d.st_sub + sidx] - s / m;
+  __shared__ double shift_s;
+  if (threadIdx.x == 0) shift_s = d.sub_target[(long long)r * d.st_sub + sidx] - s / m;
+  __syncthreads();
+  const double shift = shift_s;
   double rate = 0.0;
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
     const int jl = c / a, il = c - jl * a;

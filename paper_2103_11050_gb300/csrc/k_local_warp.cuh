@@ -113,9 +113,9 @@ __device__ void build(const Grid& g, const DevSub& sd, Tables<T> t, const double
 }
 
 // Reciprocal of a pivot: FP32 uses the hardware approximation (<= 2 ulp), which the FP64
-// refinement absorbs; FP64 keeps the correctly rounded division.
+// refinement absorbs; FP64 the Newton-Raphson reciprocal of fp64_div.cuh (<= 1 ulp).
 __device__ __forceinline__ float pivot_rcp(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ double pivot_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ double pivot_rcp(double x) { return rcp64(x); }
 
 // In-register Gauss-Jordan inversion of the padded A x A block.  Pivot p:
 //   M[p][p] <- 1/M[p][p],  M[p][c] <- M[p][c]/M[p][p],  M[r][p] <- -M[r][p]/M[p][p],
@@ -357,7 +357,7 @@ __device__ void solve_refined(const DevSub& sd, Tables<T> t, const T* Q, bool re
   const int sweeps = refine ? ir_max : 1;
   int it = 0;
   bool ok = false;
-  double eta_prev = 1e300, smax = 0.0;
+  double rmax_prev = 1e300, smax = 0.0;
   for (; it < sweeps; ++it) {
     for (int e = tid; e < b * A; e += nt) {
       const int j = e / A, i = e - j * A;
@@ -391,10 +391,10 @@ __device__ void solve_refined(const DevSub& sd, Tables<T> t, const T* Q, bool re
       }
       rmax = cta_max(rmax, red);
     }
-    const double eta = smax > 0.0 ? rmax / smax : 0.0;
-    if (eta <= target) { ok = true; ++it; break; }
-    if (eta > 0.5 * eta_prev && eta <= 1e3 * tol) { ok = true; ++it; break; }  // FP64 floor reached
-    eta_prev = eta;
+    // eta = rmax / smax, compared without dividing (every thread evaluates the test)
+    if (rmax <= target * smax) { ok = true; ++it; break; }
+    if (rmax > 0.5 * rmax_prev && rmax <= 1e3 * tol * smax) { ok = true; ++it; break; }  // FP64 floor reached
+    rmax_prev = rmax;
   }
   if (tid == 0) {
     if (!ok) atomicOr(status, 1);
