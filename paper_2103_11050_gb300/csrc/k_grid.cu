@@ -111,11 +111,6 @@ __device__ __forceinline__ double cfl_dt(const Grid& g, const DevState& d, int r
 // with f(s) read from fs; inflow through the boundary carries f(s_inflow) = f_in.  The sign
 // of each face flux is read from its bit pattern (integer compares instead of float64 ones;
 // -0 counts as zero like +0), and the outward flux enters through a fused multiply-add.
-__device__ __forceinline__ bool dpos(double v) { return __double_as_longlong(v) > 0; }
-__device__ __forceinline__ bool dneg(double v) {
-  const long long b = __double_as_longlong(v);
-  return b < 0 && b != (long long)0x8000000000000000ull;
-}
 __device__ __forceinline__ double upwind_cell(const Grid& g, const double* ux, const double* uy, const double* fs,
                                               const double* s, double lam, double f_in, int i, int j) {
   const int nx = g.nx, ny = g.ny;

@@ -271,9 +271,12 @@ __global__ void __launch_bounds__(256) k_nd_up(Grid g, DevState d, const DevNode
     const int k = q + u * KS;
     v[u] = (row < nf && k < ns) ? F[(long long)k * nf + row] : 0.0;
   }
+  // gather indices of the first separator entry of this thread (index maps are static)
+  const int p0 = threadIdx.x < ns ? s0[threadIdx.x] : -1, p1 = threadIdx.x < ns ? s1[threadIdx.x] : -1;
   pdl_wait();
   for (int k = threadIdx.x; k < ns; k += blockDim.x) {
-    const int a0 = s0[k], a1 = s1[k];
+    const bool first = k == (int)threadIdx.x;
+    const int a0 = first ? p0 : s0[k], a1 = first ? p1 : s1[k];
     gs[k] = (a0 >= 0 ? g0[a0] : 0.0) + (a1 >= 0 ? g1[a1] : 0.0);
   }
   __syncthreads();
@@ -327,9 +330,10 @@ __global__ void __launch_bounds__(256) k_nd_down(Grid g, DevState d, const DevNo
     const int k = q + u * KS;
     v[u] = (row < ns && k < nbd) ? F[(long long)k * nf + row] : 0.0;
   }
+  const int p0 = threadIdx.x < nbd ? pm[threadIdx.x] : 0;  // static index map, loaded before the wait
   pdl_wait();
   for (int k = threadIdx.x; k < nbd; k += blockDim.x) {
-    const double x = xp[pm[k]];
+    const double x = xp[k == (int)threadIdx.x ? p0 : pm[k]];
     xb[k] = x;
     if (blockIdx.y == 0) xo[ns + k] = x;
   }
@@ -386,13 +390,15 @@ __global__ void __launch_bounds__(256) k_reconstruct(Grid g, DevState d, const D
   const double fbar = f < nface && q == 0 ? d.fbar[(long long)r * d.st_face + sd.face_off + f] : 0.0;
   const double* xp = nullptr;
   const int* pm = nullptr;
+  int p0 = 0;
   if (nd > 0) {
     const DevNode& leaf = nodes[leaf_node[sidx]];
     xp = d.xvec + (long long)r * d.st_vec + nodes[leaf.parent].v_off;
     pm = pmap + leaf.pmap_off;
+    if ((int)threadIdx.x < nd) p0 = pm[threadIdx.x];  // static index map, loaded before the wait
   }
   pdl_wait();
-  for (int l = threadIdx.x; l < nd; l += blockDim.x) cs[l] = xp[pm[l]];
+  for (int l = threadIdx.x; l < nd; l += blockDim.x) cs[l] = xp[l == (int)threadIdx.x ? p0 : pm[l]];
   __syncthreads();
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll

@@ -660,20 +660,33 @@ __global__ void __launch_bounds__(kLocalThreads) k_downscale_w(Grid g, DevState 
   if (threadIdx.x == 0) shift_s = d.sub_target[(long long)r * d.st_sub + sidx] - s / m;
   __syncthreads();
   const double shift = shift_s;
-  double rate = 0.0;
+  // east / north face fluxes of every cell (along +x / +y, as stored in ux / uy), each
+  // computed once; the residual and right-hand side buffers are free after the solve
+  double* FE = t.Rr;
+  double* FN = t.B;
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
     const int jl = c / a, il = c - jl * a;
     const int i = sd.x0 + il, j = sd.y0 + jl;
     d.p_down[(long long)r * g.ncell() + (long long)j * nx + i] = t.X[c] + shift;
-    // the four face fluxes of the cell along +x / +y, exactly as stored in ux / uy
-    const double fw = il == 0 ? ub[jl] : t.wE[c - 1] * (t.X[c - 1] - t.X[c]);
     const double fe = il == a - 1 ? ub[b + jl] : t.wE[c] * (t.X[c] - t.X[c + 1]);
-    const double fs = jl == 0 ? ub[2 * b + il] : t.wN[c - a] * (t.X[c - a] - t.X[c]);
     const double fn = jl == b - 1 ? ub[2 * b + a + il] : t.wN[c] * (t.X[c] - t.X[c + a]);
     if (il < a - 1) uxw[(long long)j * (nx + 1) + i + 1] = fe;
     if (jl < b - 1) uyw[(long long)(j + 1) * nx + i] = fn;
-    const double out = fmax(-fw, 0.0) + fmax(fe, 0.0) + fmax(-fs, 0.0) + fmax(fn, 0.0);
-    const double in = fmax(fw, 0.0) + fmax(-fe, 0.0) + fmax(fs, 0.0) + fmax(-fn, 0.0);
+    FE[c] = fe;
+    FN[c] = fn;
+  }
+  __syncthreads();
+  // max over the cells of max(total outflow, total inflow); signs from the bit patterns
+  double rate = 0.0;
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    const int jl = c / a, il = c - jl * a;
+    const double o[4] = {-(il == 0 ? ub[jl] : FE[c - 1]), FE[c], -(jl == 0 ? ub[2 * b + il] : FN[c - a]), FN[c]};
+    double out = 0.0, in = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (dpos(o[k])) out += o[k];
+      else if (dneg(o[k])) in -= o[k];
+    }
     rate = fmax(rate, fmax(out, in));
   }
   rate = warp::cta_max(rate, red);

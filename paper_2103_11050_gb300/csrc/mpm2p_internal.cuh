@@ -72,6 +72,13 @@ struct Grid {
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Sign of a float64 from its bit pattern (integer compares; -0 and +0 are neither).
+__device__ __forceinline__ bool dpos(double v) { return __double_as_longlong(v) > 0; }
+__device__ __forceinline__ bool dneg(double v) {
+  const long long b = __double_as_longlong(v);
+  return b < 0 && b != (long long)0x8000000000000000ull;
+}
+
 // Outward integrated flux of pressure p through a physical boundary face of a cell with
 // values (kc, pc) on side `side` (Dirichlet: 2 kc (pc - g); Neumann: z h).
 __device__ __forceinline__ double phys_flux(const Grid& g, int side, double kc, double pc) {
