@@ -356,14 +356,19 @@ __global__ void __launch_bounds__(256) k_nd_down(Grid g, DevState d, const DevNo
   }
 }
 
-// Reconstruction from the interface solution c of one subdomain per CTA (c gathered from the
-// leaf's parent vector): the one-sided traces F = Fbar + F_hat c, then the target mean of the
-// downscaled pressure, and at a rebuild the MRCM-level pressure p^m = pbar + P_hat c:
+// Reconstruction from the interface solution c of one subdomain per CTA: the one-sided
+// traces F = Fbar + F_hat c, then the target mean of the downscaled pressure, and at a
+// rebuild the MRCM-level pressure p^m = pbar + P_hat c:
 //   rebuild: target = mean(p^m);  MPM-2P: target = mean(p^m) + mean(dpbar) + mu_hat . dc.
+// c is gathered from the leaf's parent P.  When P is a level-1 node (two leaf children) its
+// downward step is done here, redundantly by both children, instead of by a sweep kernel:
+// x_P = [y_s + sum_k G[ns + k][r] x_b[k] ; x_b], x_b from P's parent.
 // F_hat and P_hat are stored one column per BF, so thread (face f, chunk q) sums F_hat[l][f]
 // c[l] over l = q, q + KS, ... with coalesced loads (its first kKpt terms loaded before
 // pdl_wait()), and the KS chunks combine in shared memory.  branch >= 0 restricts the launch
 // to the realisations that took that branch.
+constexpr int kKpt1 = 8;  // register-held terms per thread of the fused level-1 step
+
 template <int KS>
 __global__ void __launch_bounds__(256) k_reconstruct(Grid g, DevState d, const DevSub* subs, const DevNode* nodes,
                                                      const int* leaf_node, const int* pmap, int branch) {
@@ -377,9 +382,11 @@ __global__ void __launch_bounds__(256) k_reconstruct(Grid g, DevState d, const D
   const DevSub& sd = subs[sidx];
   const int a = sd.a, b = sd.b, m = a * b, nd = sd.ndof, nface = 2 * (a + b);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double* part = nd_smem;                            // [KS][FACES]
+  double* part = nd_smem;                            // [KS][FACES], then the level-1 partial sums
   double* cs = nd_smem + 256;                        // nd
+  double* xP = cs + nd;                              // the parent's frontal solution (fused case)
   const int f = threadIdx.x % FACES, q = threadIdx.x / FACES;
+  const long long vb = (long long)r * d.st_vec;
   const double* trb = d.tr + (long long)r * d.st_tr + sd.tr_off;
   double v[kKpt];
 #pragma unroll
@@ -388,17 +395,63 @@ __global__ void __launch_bounds__(256) k_reconstruct(Grid g, DevState d, const D
     v[u] = (f < nface && l < nd) ? trb[(long long)l * nface + f] : 0.0;
   }
   const double fbar = f < nface && q == 0 ? d.fbar[(long long)r * d.st_face + sd.face_off + f] : 0.0;
-  const double* xp = nullptr;
   const int* pm = nullptr;
   int p0 = 0;
+  bool fused = false;
+  DevNode P{};
+  // fused level-1 step: thread (row i1, chunk q1) of P's separator rows; its first terms
+  // G[ns + k][i1] and P's boundary index map are operator data, loaded before the wait
+  int rows1 = 1, i1 = 0, q1 = 0, pp0 = 0;
+  double v1[kKpt1];
   if (nd > 0) {
     const DevNode& leaf = nodes[leaf_node[sidx]];
-    xp = d.xvec + (long long)r * d.st_vec + nodes[leaf.parent].v_off;
+    P = nodes[leaf.parent];
     pm = pmap + leaf.pmap_off;
-    if ((int)threadIdx.x < nd) p0 = pm[threadIdx.x];  // static index map, loaded before the wait
+    if ((int)threadIdx.x < nd) p0 = pm[threadIdx.x];
+    fused = P.level == 1;
+    if (fused) {
+      while (rows1 < P.nsep) rows1 <<= 1;
+      const int kc = 256 / rows1;
+      i1 = threadIdx.x % rows1;
+      q1 = threadIdx.x / rows1;
+      const double* G = d.front + (long long)r * d.st_front + P.f_off + (long long)P.nsep * P.nf;
+#pragma unroll
+      for (int u = 0; u < kKpt1; ++u) {
+        const int k = q1 + u * kc;
+        v1[u] = (i1 < P.nsep && k < P.nbnd) ? G[(long long)k * P.nf + i1] : 0.0;
+      }
+      if (P.parent >= 0 && (int)threadIdx.x < P.nbnd) pp0 = pmap[P.pmap_off + threadIdx.x];
+    }
   }
   pdl_wait();
-  for (int l = threadIdx.x; l < nd; l += blockDim.x) cs[l] = xp[l == (int)threadIdx.x ? p0 : pm[l]];
+  if (fused) {
+    const int kc = 256 / rows1;
+    const double* xpp = P.parent >= 0 ? d.xvec + vb + nodes[P.parent].v_off : nullptr;
+    for (int k = threadIdx.x; k < P.nbnd; k += blockDim.x)
+      xP[P.nsep + k] = xpp[k == (int)threadIdx.x ? pp0 : pmap[P.pmap_off + k]];
+    __syncthreads();
+    const double* G = d.front + (long long)r * d.st_front + P.f_off + (long long)P.nsep * P.nf;
+    double a1[2] = {0.0, 0.0};
+#pragma unroll
+    for (int u = 0; u < kKpt1; ++u) {
+      const int k = q1 + u * kc;
+      if (k < P.nbnd) a1[u & 1] += v1[u] * xP[P.nsep + k];
+    }
+    if (i1 < P.nsep)
+      for (int k = q1 + kKpt1 * kc; k < P.nbnd; k += kc) a1[0] += G[(long long)k * P.nf + i1] * xP[P.nsep + k];
+    part[q1 * rows1 + i1] = a1[0] + a1[1];
+    __syncthreads();
+    if (q1 == 0 && i1 < P.nsep) {
+      double sum = d.xvec[vb + P.v_off + i1];  // y_s of the upward sweep
+      for (int u = 0; u < kc; ++u) sum += part[u * rows1 + i1];
+      xP[i1] = sum;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < nd; l += blockDim.x) cs[l] = xP[l == (int)threadIdx.x ? p0 : pm[l]];
+  } else if (nd > 0) {
+    const double* xp = d.xvec + vb + P.v_off;
+    for (int l = threadIdx.x; l < nd; l += blockDim.x) cs[l] = xp[l == (int)threadIdx.x ? p0 : pm[l]];
+  }
   __syncthreads();
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
@@ -595,11 +648,11 @@ void launch_nd_down(const Grid& g, const DevState& d, const DevNode* nodes, cons
 }
 
 void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_face, int max_dof,
-                        const DevNode* nodes, const int* leaf_node, const int* pmap, int branch, bool pdl,
+                        int max_nf1, const DevNode* nodes, const int* leaf_node, const int* pmap, int branch, bool pdl,
                         cudaStream_t st) {
   const int faces = max_face <= 16 ? 16 : max_face <= 32 ? 32 : max_face <= 64 ? 64 : 128;
   const int ks = 256 / faces;
-  const size_t smem = (size_t)(256 + (max_dof > 0 ? max_dof : 1)) * sizeof(double);
+  const size_t smem = (size_t)(256 + (max_dof > 0 ? max_dof : 1) + max_nf1) * sizeof(double);
   MPM_DISPATCH_KS(k_reconstruct, ks, dim3(nsub, g.R), dim3(256), smem, st, pdl, g, d, subs, nodes, leaf_node, pmap,
                   branch);
 }

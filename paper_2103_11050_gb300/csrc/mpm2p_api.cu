@@ -384,12 +384,13 @@ int run_interface(mpm_ctx* c) {
                    c->lev_max_nsep[L], c->d_srcmap, chained && c->use_pdl, st);
       chained = true;
     }
-    for (int L = (int)c->levels.size() - 1; L >= 1; --L)
+    // level 1 (nodes with two leaf children) is done inside the reconstruction
+    for (int L = (int)c->levels.size() - 1; L >= 2; --L)
       launch_nd_down(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(),
                      c->lev_max_nsep[L], c->lev_max_nbnd[L], c->d_pmap, c->use_pdl, st);
   }
-  launch_reconstruct(g, d, c->d_subs, nsub, c->max_face, c->max_dof, c->d_nodes, c->d_leaf_node, c->d_pmap, -1,
-                     chained && c->use_pdl, st);
+  launch_reconstruct(g, d, c->d_subs, nsub, c->max_face, c->max_dof, c->levels.size() > 1 ? c->lev_max_nf[1] : 0,
+                     c->d_nodes, c->d_leaf_node, c->d_pmap, -1, chained && c->use_pdl, st);
   prof_end(c, MPM_STAGE_IFACE_SOLVE);
   return check_launch(c);
 }
@@ -871,6 +872,7 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
     dn.child[0] = h.child[0];
     dn.child[1] = h.child[1];
     dn.parent = h.parent;
+    dn.level = h.level;
     dn.f_off = f_off;
     dn.v_off = v_off;
     f_off += (long long)dn.nf * dn.nf;

@@ -97,6 +97,7 @@ struct DevNode {
   long long v_off;     // vectors (nf) in the g / x pools
   int src_off;         // internal nodes: 2*nf ints: child0 / child1 boundary index per frontal index (-1 none)
   int pmap_off;        // nbnd ints: frontal index in the parent of each boundary DOF
+  int level;           // 0 for leaves, 1 + the larger level of the children otherwise
 };
 
 // Per-level summary of the nested-dissection tree (node ids level_nodes[off .. off+cnt)).
@@ -185,8 +186,8 @@ void launch_mpm_local(const Grid& g, const DevState& d, const DevSub* subs, int 
                       int max_b, bool fp32, double ir_tol, int ir_max, const DevNode* nodes, const int* leaf_node,
                       cudaStream_t st);
 void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_face,
-                        int max_dof, const DevNode* nodes, const int* leaf_node, const int* pmap, int branch,
-                        bool pdl, cudaStream_t st);
+                        int max_dof, int max_nf1, const DevNode* nodes, const int* leaf_node, const int* pmap,
+                        int branch, bool pdl, cudaStream_t st);
 void launch_downscale_factor(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
                              int max_b, bool fp32, cudaStream_t st);
 void launch_downscale(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
