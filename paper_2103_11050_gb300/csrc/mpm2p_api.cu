@@ -305,7 +305,8 @@ int build_tree(mpm_ctx* c, const std::vector<Iface>& ifs, std::vector<HostNode>&
 }
 
 void drop_graph(mpm_ctx* c);
-int join_branches(mpm_ctx* c);
+int join_branches(mpm_ctx* c, bool factor);
+bool late_factor_join(const mpm_ctx* c);
 
 int release_decomposition(mpm_ctx* c) {
   if (!c->dec_allocs.empty()) cudaStreamSynchronize(c->stream);
@@ -365,7 +366,7 @@ int run_interface(mpm_ctx* c) {
   DevState& d = c->d;
   cudaStream_t st = c->stream;
   const int nsub = (int)c->subs.size();
-  int jrc = join_branches(c);
+  int jrc = join_branches(c, !late_factor_join(c));
   if (jrc) return jrc;
   prof_begin(c, MPM_STAGE_IFACE_SOLVE);
   if (c->use_coop && c->coop_blocks < 0) c->coop_blocks = iface_coop_blocks();
@@ -407,12 +408,18 @@ int fork_downscale_factor(mpm_ctx* c) {
 }
 
 // Join every forked branch into the main stream (no-op when none is pending).
-int join_branches(mpm_ctx* c) {
-  if (c->factor_forked) CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+int join_branches(mpm_ctx* c, bool factor = true) {
+  if (factor && c->factor_forked) CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   if (c->reb_forked) CK(cudaStreamWaitEvent(c->stream, c->ev_reb_join, 0));
-  c->factor_forked = c->reb_forked = false;
+  if (factor) c->factor_forked = false;
+  c->reb_forked = false;
   return MPM_OK;
 }
+
+// A float64 downscaling factorisation takes longer than the perturbation solve: it is joined
+// right before the downscaling solve (which then starts without programmatic launch), not
+// before the interface solve.
+bool late_factor_join(const mpm_ctx* c) { return !fp32(c); }
 
 // Downscaling solve.  after_interface: launched right behind run_interface's chain, whose
 // first kernel was ordered after the forked factorisation, so it may use programmatic
@@ -421,7 +428,7 @@ int join_branches(mpm_ctx* c) {
 int run_downscale(mpm_ctx* c, bool after_interface, bool forked) {
   const bool joined_before = forked && !c->factor_forked;  // run_interface joined it
   if (forked) {
-    int rc = join_branches(c);
+    int rc = join_branches(c, true);
     if (rc) return rc;
   }
   prof_begin(c, MPM_STAGE_DOWNSCALE);
