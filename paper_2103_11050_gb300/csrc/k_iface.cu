@@ -127,7 +127,7 @@ __global__ void k_sweep_pivot(Grid g, DevState d, const DevNode* nodes, const in
     if (active) {
       if (k == p) buf[i] = v;
       if (i == p) buf[kPivotChunk + k] = v;
-      if (i == p && k == p) buf[2 * kPivotChunk] = 1.0 / v;
+      if (i == p && k == p) buf[2 * kPivotChunk] = rcp64(v);
     }
     __syncthreads();
     if (active) {
