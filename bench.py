@@ -182,11 +182,13 @@ def run_gpu(args, w):
                 e1.record(stream)
                 evs.append((e0, e1))
         torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in evs)
+        per = [a.elapsed_time(b) for a, b in evs]
+        ms = sum(per)
         prof = ctx.profile_read() if profile else None
         st1 = ctx.get_stats()
-        res = dict(ms=ms, launches=st1["kernel_launches"] - launches0, rebuilds=st1["rebuilds"] - st0["rebuilds"],
-                   mpm=st1["mpm_updates"] - st0["mpm_updates"], prof=prof, ir=st1["ir_iters_max"])
+        res = dict(ms=ms, per=per, launches=st1["kernel_launches"] - launches0,
+                   rebuilds=st1["rebuilds"] - st0["rebuilds"], mpm=st1["mpm_updates"] - st0["mpm_updates"], prof=prof,
+                   ir=st1["ir_iters_max"])
         ux, uy = ctx.get_flux()
         ctx.close()
         return res, ux
@@ -195,6 +197,17 @@ def run_gpu(args, w):
     with ClockSampler(0) as clk:
         main, ux_main = one_run(prec, args.steps, args.warmup, False)
     value = cells * args.steps / (main["ms"] / 1e3)
+    # rebuild and MPM-2P steps separately: a rebuild step costs several times an MPM-2P step,
+    # so the timed rebuild steps are the slowest ones
+    per = sorted(main["per"])
+    n_reb = main["rebuilds"]
+    mpm_part = per[:len(per) - n_reb] if n_reb < len(per) else per
+    reb_part = per[len(per) - n_reb:] if n_reb > 0 else []
+    split = {"mpm_step_ms": sum(mpm_part) / len(mpm_part),
+             "mpm_step_ms_median": statistics.median(mpm_part),
+             "rebuild_step_ms": (sum(reb_part) / len(reb_part)) if reb_part else None,
+             "mpm_steps_rate": cells / (sum(mpm_part) / len(mpm_part) / 1e3),
+             "rebuild_steps_rate": (cells / (sum(reb_part) / len(reb_part) / 1e3)) if reb_part else None}
     # same steps, eager launches with per-stage CUDA events (for the stage split and roofline)
     prof_run, _ = one_run(prec, args.steps, args.warmup, True)
     main["prof"] = prof_run["prof"]
@@ -261,6 +274,7 @@ def run_gpu(args, w):
         "clocks": clk.summary(),
         "peaks_source": pk_kind,
         "ir_sweeps_max": main["ir"],
+        "step_split": split,
     }
     line.update(other)
     if not args.no_cpu:
