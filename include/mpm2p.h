@@ -50,7 +50,8 @@ enum {
   MPM_ERR_OOM = 3,            /* device allocation failed */
   MPM_ERR_NOT_CONVERGED = 4,  /* iterative refinement hit its iteration cap */
   MPM_ERR_STATE = 5,          /* call out of order (e.g. solve before build) */
-  MPM_ERR_TOO_LARGE = 6       /* request exceeds a fixed capacity (mpm_cfl_dt_noalloc) */
+  MPM_ERR_TOO_LARGE = 6,      /* request exceeds a fixed capacity (mpm_cfl_dt_noalloc) */
+  MPM_ERR_TIMEOUT = 7         /* a bounded device-side dependency wait gave up (results invalid) */
 };
 
 enum { MPM_MEM_HOST = 0, MPM_MEM_DEVICE = 1 };
@@ -223,6 +224,15 @@ int mpm_step(mpm_ctx* ctx, double eta, double cfl, int n_sub);
  *                       its predecessor runs and loads its operators (factor rows, index maps)
  *                       or, for the downscaling, factors its Neumann problems before waiting
  *                       for the predecessor's results.
+ *  MPM_EXEC_DATAFLOW    the interface sweeps (all nested-dissection levels above the first) are
+ *                       one cooperative launch whose blocks take work items (node, row block)
+ *                       in topological order and wait, with bounded polling, on per-node
+ *                       completion counters instead of kernel boundaries; without it, one
+ *                       kernel per level.  A wait that gives up makes the next synchronising
+ *                       call return MPM_ERR_TIMEOUT.  Ignored with MPM_EXEC_PERSISTENT.
+ *                       Measured slower than the per-level kernels with programmatic launch
+ *                       on the 256^2 workload (202 vs 190 us per step), so it is off by
+ *                       default.
  *  MPM_EXEC_PERSISTENT  the interface sweeps (every nested-dissection level up and down,
  *                       reconstruction) are one persistent cooperative kernel with
  *                       grid-wide barriers between levels; without it, one kernel per level
@@ -231,7 +241,7 @@ int mpm_step(mpm_ctx* ctx, double eta, double cfl, int n_sub);
  *                       256^2 workload (the grid-wide barriers cost more than the launches
  *                       they replace), so it is off by default.
  * Results are identical up to rounding order.  Drops a captured graph. */
-enum { MPM_EXEC_GRAPH = 1, MPM_EXEC_PERSISTENT = 2, MPM_EXEC_PDL = 4 };
+enum { MPM_EXEC_GRAPH = 1, MPM_EXEC_PERSISTENT = 2, MPM_EXEC_PDL = 4, MPM_EXEC_DATAFLOW = 8 };
 int mpm_set_execution(mpm_ctx* ctx, int flags);
 
 /* Copy out pressure [R][ny][nx] (which = MPM_P_*), fluxes ux [R][ny][nx+1],

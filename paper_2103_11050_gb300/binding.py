@@ -14,12 +14,13 @@ import numpy as np
 
 from . import build as _build
 
-MPM_OK, MPM_ERR_ARG, MPM_ERR_CUDA, MPM_ERR_OOM, MPM_ERR_NOT_CONVERGED, MPM_ERR_STATE, MPM_ERR_TOO_LARGE = range(7)
+(MPM_OK, MPM_ERR_ARG, MPM_ERR_CUDA, MPM_ERR_OOM, MPM_ERR_NOT_CONVERGED, MPM_ERR_STATE, MPM_ERR_TOO_LARGE,
+ MPM_ERR_TIMEOUT) = range(8)
 MEM_HOST, MEM_DEVICE = 0, 1
 BC_DIRICHLET, BC_NEUMANN = 0, 1
 PREC_FP64, PREC_FP32_IR, PREC_FP32_IR_ALL = 0, 1, 2
 P_MRCM, P_DOWNSCALED = 0, 1
-EXEC_GRAPH, EXEC_PERSISTENT, EXEC_PDL = 1, 2, 4
+EXEC_GRAPH, EXEC_PERSISTENT, EXEC_PDL, EXEC_DATAFLOW = 1, 2, 4, 8
 
 FUNCTIONS = [
     "mpm_create", "mpm_destroy", "mpm_last_error", "mpm_set_precision", "mpm_set_permeability",
@@ -268,8 +269,9 @@ class Context:
     def get_conductivity(self, out=None):
         return self._get(self.L.mpm_get_conductivity, (self.R, self.ny, self.nx), out)
 
-    def set_execution(self, graph=True, persistent=False, pdl=True):
+    def set_execution(self, graph=True, persistent=False, pdl=True, dataflow=False):
         flags = (EXEC_GRAPH if graph else 0) | (EXEC_PERSISTENT if persistent else 0) | (EXEC_PDL if pdl else 0)
+        flags |= EXEC_DATAFLOW if dataflow else 0
         self._ck(self.L.mpm_set_execution(self.h, flags))
 
     def profile_enable(self, on=True):

@@ -25,6 +25,8 @@
 //        downward x_s = y_s - (F_ss^-1 F_sb) x_b  (x_b from the parent).
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "k_iface_phases.cuh"
 #include "mpm2p_internal.cuh"
 
@@ -356,6 +358,145 @@ __global__ void __launch_bounds__(256) k_nd_down(Grid g, DevState d, const DevNo
   }
 }
 
+// The interface sweeps as one cooperative launch driven by per-node completion counters
+// instead of one kernel per level: work item = (phase, node, row block), same arithmetic as
+// k_nd_up / k_nd_down.  Items are listed in topological order (upward items by increasing
+// level, then downward items by decreasing level, each for every realisation) and CTA b takes
+// items b, b + gridDim.x, ... in order.  Before an item the CTA loads its operator rows and
+// index maps, then its thread 0 polls the counters of the items it depends on (children's
+// upward items; for a downward item the node's own upward items and the parent's downward
+// items, or the root's upward items) and the CTA proceeds once they are complete.  All CTAs
+// are co-resident (cooperative launch) and take items in increasing order, so the lowest
+// unfinished item can always proceed; every poll loop is bounded (status bit 2 on timeout).
+// Data produced inside the launch is read through L2 (__ldcg).
+constexpr long long kDataflowPolls = 1LL << 22;
+
+__device__ __forceinline__ void wait_counter(const int* cnt, int target, int* status) {
+  const volatile int* v = cnt;
+  long long polls = 0;
+  while (*v < target) {
+    if (++polls > kDataflowPolls) {
+      atomicOr(status, 2);
+      return;
+    }
+    __nanosleep(20);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_nd_dataflow(Grid g, DevState d, const DevNode* nodes, const NdItem* items,
+                                                     int nitems, int nnodes, int* counters, const int* srcmap,
+                                                     const int* pmap) {
+  extern __shared__ __align__(16) double nd_smem[];  // [256] partial sums + gathered vector
+  pdl_trigger();
+  const long long total = (long long)nitems * g.R;
+  for (long long w = blockIdx.x; w < total; w += gridDim.x) {
+    const int it = (int)(w / g.R), r = (int)(w - (long long)it * g.R);
+    const NdItem I = items[it];
+    const DevNode nd = nodes[I.node];
+    const int KS = I.ks, ROWS = 256 / KS;
+    const int i = threadIdx.x % ROWS, q = threadIdx.x / ROWS;
+    const int row = I.row0 + i;
+    const long long vb = (long long)r * d.st_vec;
+    const int nf = nd.nf, ns = nd.nsep, nbd = nd.nbnd;
+    int* cnt = counters + (long long)r * 2 * nnodes;
+    double* part = nd_smem;
+    double* vec = nd_smem + 256;
+    const double* G = d.front + (long long)r * d.st_front + nd.f_off;
+    // operator data of this item, independent of the wait
+    double v[kKpt];
+    int p0 = -1, p1 = -1, own0 = -1, own1 = -1;
+    if (I.phase == 0) {
+#pragma unroll
+      for (int u = 0; u < kKpt; ++u) {
+        const int k = q + u * KS;
+        v[u] = (row < nf && k < ns) ? G[(long long)k * nf + row] : 0.0;
+      }
+      if ((int)threadIdx.x < ns) {
+        p0 = srcmap[nd.src_off + threadIdx.x];
+        p1 = srcmap[nd.src_off + nf + threadIdx.x];
+      }
+      if (q == 0 && row < nf && row >= ns) {
+        own0 = srcmap[nd.src_off + row];
+        own1 = srcmap[nd.src_off + nf + row];
+      }
+    } else {
+      const double* Gb = G + (long long)ns * nf;
+#pragma unroll
+      for (int u = 0; u < kKpt; ++u) {
+        const int k = q + u * KS;
+        v[u] = (row < ns && k < nbd) ? Gb[(long long)k * nf + row] : 0.0;
+      }
+      if ((int)threadIdx.x < nbd) p0 = pmap[nd.pmap_off + threadIdx.x];
+    }
+    if (threadIdx.x == 0) {
+      for (int k = 0; k < 2; ++k)
+        if (I.dep[k] >= 0) wait_counter(cnt + I.dep[k], I.target[k], d.status);
+      __threadfence();
+    }
+    __syncthreads();
+    if (I.phase == 0) {
+      const DevNode& c0 = nodes[nd.child[0]];
+      const DevNode& c1 = nodes[nd.child[1]];
+      const double* g0 = d.gvec + vb + c0.v_off + c0.nsep;
+      const double* g1 = d.gvec + vb + c1.v_off + c1.nsep;
+      for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+        const bool first = k == (int)threadIdx.x;
+        const int a0 = first ? p0 : srcmap[nd.src_off + k], a1 = first ? p1 : srcmap[nd.src_off + nf + k];
+        vec[k] = (a0 >= 0 ? __ldcg(g0 + a0) : 0.0) + (a1 >= 0 ? __ldcg(g1 + a1) : 0.0);
+      }
+      __syncthreads();
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int u = 0; u < kKpt; ++u) {
+        const int k = q + u * KS;
+        if (k < ns) acc[u & 3] += v[u] * vec[k];
+      }
+      if (row < nf)
+        for (int k = q + kKpt * KS; k < ns; k += KS) acc[0] += G[(long long)k * nf + row] * vec[k];
+      part[q * ROWS + i] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+      __syncthreads();
+      if (q == 0 && row < nf) {
+        double sum = part[i];
+        for (int u = 1; u < KS; ++u) sum += part[u * ROWS + i];
+        if (row < ns) d.xvec[vb + nd.v_off + row] = sum;
+        else
+          d.gvec[vb + nd.v_off + row] =
+              ((own0 >= 0 ? __ldcg(g0 + own0) : 0.0) + (own1 >= 0 ? __ldcg(g1 + own1) : 0.0)) - sum;
+      }
+    } else {
+      const double* xp = d.xvec + vb + nodes[nd.parent].v_off;
+      double* xo = d.xvec + vb + nd.v_off;
+      for (int k = threadIdx.x; k < nbd; k += blockDim.x) {
+        const double x = __ldcg(xp + (k == (int)threadIdx.x ? p0 : pmap[nd.pmap_off + k]));
+        vec[k] = x;
+        if (I.row0 == 0) xo[ns + k] = x;
+      }
+      __syncthreads();
+      const double* Gb = G + (long long)ns * nf;
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int u = 0; u < kKpt; ++u) {
+        const int k = q + u * KS;
+        if (k < nbd) acc[u & 3] += v[u] * vec[k];
+      }
+      if (row < ns)
+        for (int k = q + kKpt * KS; k < nbd; k += KS) acc[0] += Gb[(long long)k * nf + row] * vec[k];
+      part[q * ROWS + i] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+      __syncthreads();
+      if (q == 0 && row < ns) {
+        double sum = part[i];
+        for (int u = 1; u < KS; ++u) sum += part[u * ROWS + i];
+        xo[row] = __ldcg(xo + row) + sum;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(cnt + (I.phase == 0 ? I.node : nnodes + I.node), 1);
+    }
+  }
+}
+
 // Reconstruction from the interface solution c of one subdomain per CTA: the one-sided
 // traces F = Fbar + F_hat c, then the target mean of the downscaled pressure, and at a
 // rebuild the MRCM-level pressure p^m = pbar + P_hat c:
@@ -559,6 +700,36 @@ __global__ void __launch_bounds__(256) k_iface_coop(Grid g, DevState d, const De
 }
 
 }  // namespace
+
+int nd_dataflow_blocks(int max_ns, int max_nb) {
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  const size_t smem = (size_t)(256 + std::max(max_ns, max_nb)) * sizeof(double);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nd_dataflow, 256, smem) != cudaSuccess) return 0;
+  return sms * (per_sm < 2 ? per_sm : 2);
+}
+
+cudaError_t launch_nd_dataflow(const Grid& g, const DevState& d, const DevNode* nodes, const NdItem* items,
+                               int nitems, int nnodes, int* counters, int max_ns, int max_nb, const int* srcmap,
+                               const int* pmap, int blocks, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(int) * 2 * (size_t)nnodes * g.R, st);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  const long long total = (long long)nitems * g.R;
+  cfg.gridDim = dim3((unsigned)std::min<long long>(blocks, total));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = (size_t)(256 + std::max(max_ns, max_nb)) * sizeof(double);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ++g_launches;
+  return cudaLaunchKernelEx(&cfg, k_nd_dataflow, g, d, nodes, items, nitems, nnodes, counters, srcmap, pmap);
+}
 
 int iface_coop_blocks() {
   int dev = 0, sms = 0, per_sm = 0, coop = 0;

@@ -118,16 +118,18 @@ def test_transport_parity():
     np.testing.assert_allclose(ctx.get_conductivity()[0], O.mobility(s, c["M"]) * c["K"], rtol=1e-11)
 
 
-@pytest.mark.parametrize("graph,persistent,pdl", [(True, False, True), (False, False, True), (True, False, False),
-                                                  (False, False, False), (True, True, True), (False, True, False)])
+@pytest.mark.parametrize("graph,persistent,pdl,dataflow", [(True, False, True, False), (False, False, True, False),
+                                                           (True, False, True, True), (False, False, True, True),
+                                                           (True, False, False, False), (False, False, False, False),
+                                                           (True, True, True, False), (False, True, False, False)])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("name,eta,steps", [("p1_2x2", 0.02, 12), ("uneven", -1.0, 4), ("contrast64", 0.05, 8)])
-def test_algorithm1_parity(name, eta, steps, prec, graph, persistent, pdl):
+def test_algorithm1_parity(name, eta, steps, prec, graph, persistent, pdl, dataflow):
     c = case(name, "zero")
     prob, dec = _oracle_setup(c)
     st = O.simulate_init(c["K"], c["s0"], prob, dec, eta)
     ctx = _gpu(c, prec)
-    ctx.set_execution(graph, persistent, pdl)
+    ctx.set_execution(graph, persistent, pdl, dataflow)
     ctx.init(eta)
     tol = TOL[prec]
     for n in range(steps):
