@@ -161,9 +161,9 @@ int copy_in(mpm_ctx* c, double* dst, const double* src, size_t n, int mem) {
 
 int sync_status(mpm_ctx* c) {
   CK(cudaStreamSynchronize(c->stream));
-  int st = 0, it = 0;
-  CK(cudaMemcpy(&st, c->d.status, sizeof(int), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(&it, c->d.ir_iters, sizeof(int), cudaMemcpyDeviceToHost));
+  int w[2] = {0, 0};  // status word and refinement sweep count, adjacent on the device
+  CK(cudaMemcpy(w, c->d.status, sizeof(w), cudaMemcpyDeviceToHost));
+  const int st = w[0], it = w[1];
   c->stats.ir_iters_max = std::max(c->stats.ir_iters_max, it);
   if (st & 2) {
     CK(cudaMemset(c->d.status, 0, sizeof(int)));
@@ -661,8 +661,8 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.eps_part, (size_t)R * nblk * 2);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.ticket, (size_t)4);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.rebuild, (size_t)R);
-  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.status, 1);
-  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.ir_iters, 1);
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.status, 2);  // status word, then the sweep count
+  if (rc == MPM_OK) d.ir_iters = d.status + 1;
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.counts, 4);
   if (rc == MPM_OK && (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
                        cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1078,8 +1078,11 @@ int mpm_set_saturation(mpm_ctx* c, const double* s, int mem) {
   if (!c) return MPM_ERR_ARG;
   const size_t n = (size_t)c->g.R * c->g.nx * c->g.ny;
   if (mem == MPM_MEM_HOST && s) {
-    for (size_t i = 0; i < n; ++i)
-      if (!(s[i] >= 0 && s[i] <= 1)) return fail(c, MPM_ERR_ARG, "saturation must lie in [0,1] (index %zu)", i);
+    size_t bad = 0;  // branch-free count first (vectorises), then locate the first offender
+    for (size_t i = 0; i < n; ++i) bad += !(s[i] >= 0 && s[i] <= 1);
+    if (bad)
+      for (size_t i = 0; i < n; ++i)
+        if (!(s[i] >= 0 && s[i] <= 1)) return fail(c, MPM_ERR_ARG, "saturation must lie in [0,1] (index %zu)", i);
   }
   int rc = copy_in(c, c->d.s, s, n, mem);
   if (rc) return rc;
