@@ -34,7 +34,7 @@ from paper_2103_11050_gb300 import fields  # noqa: E402
 WORKLOAD = "gaussian256"
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_downscale_w launch (ncu capture of
 # this code, see profiles/); None when the kernel changed since the capture.
-TRAFFIC_DOWNSCALE_SOLVE = 8.190976e6
+TRAFFIC_DOWNSCALE_SOLVE = None
 METRIC = "fine-cell pressure updates/s (MRCM & MPM-2P) at <=1e-8 rel flux err vs FP64"
 UNIT = "cell-updates/s"
 CFL = 0.5
@@ -135,13 +135,14 @@ def algorithmic_downscale_solve(w):
     a x a matrix-vector products (4 b a^2 flop); one flux-form residual of the refinement
     check (14 flop per cell); the interior fine fluxes (2 faces x 2 flop per cell).  Bytes:
     the stored factor is read once (b a^2 float32), kappa-dependent stencil (32 B/cell), q
-    (8 B/cell), writes p~ and the interior fluxes (24 B/cell)."""
+    (8 B/cell), the previous solution read and the new one written (16 B/cell), writes p~ and
+    the interior fluxes (24 B/cell)."""
     a = w["nx"] // w["ncx"]
     b = w["ny"] // w["ncy"]
     nsub = w["ncx"] * w["ncy"]
     m = a * b
     flops = nsub * (4.0 * b * a * a + 14.0 * m + 4.0 * m)
-    byts = nsub * (4.0 * b * a * a + 64.0 * m)
+    byts = nsub * (4.0 * b * a * a + 80.0 * m)
     return flops, byts
 
 

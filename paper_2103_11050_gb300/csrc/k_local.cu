@@ -604,13 +604,19 @@ __global__ void __launch_bounds__(kLocalThreads) k_downscale_w(Grid g, DevState 
     stage_async(Qs, Qg, (size_t)b * A * A * sizeof(T));
     Q = Qs;
   }
+  const bool warm = refine != 0;  // refined solves start from the previous step's solution
   {
     const double* tv = d.ntvec + (long long)r * d.st_t + sd.t_off;
+    const double* xw = d.x_ds + (long long)r * g.ncell();
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
       t.ex[c] = tv[c];
       t.wE[c] = tv[m + c];
       t.wN[c] = tv[2 * m + c];
       t.sc[c] = tv[3 * m + c];
+      if (warm) {
+        const int jl = c / a, il = c - jl * a;
+        t.X[c] = xw[(long long)(sd.y0 + jl) * g.nx + sd.x0 + il];
+      }
     }
   }
   __syncthreads();
@@ -652,7 +658,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_downscale_w(Grid g, DevState 
     t.B[c] = v;
   }
   __syncthreads();
-  warp::solve_refined<T, A>(sd, t, Q, refine != 0, tol, ir_max, d.status, d.ir_iters, red);
+  warp::solve_refined<T, A>(sd, t, Q, refine != 0, tol, ir_max, d.status, d.ir_iters, red, warm);
   double s = 0.0;
   for (int c = threadIdx.x; c < m; c += blockDim.x) s += t.X[c];
   s = warp::cta_sum(s, red);
@@ -668,6 +674,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_downscale_w(Grid g, DevState 
     const int jl = c / a, il = c - jl * a;
     const int i = sd.x0 + il, j = sd.y0 + jl;
     d.p_down[(long long)r * g.ncell() + (long long)j * nx + i] = t.X[c] + shift;
+    if (warm) d.x_ds[(long long)r * g.ncell() + (long long)j * nx + i] = t.X[c];
     const double fe = il == a - 1 ? ub[b + jl] : t.wE[c] * (t.X[c] - t.X[c + 1]);
     const double fn = jl == b - 1 ? ub[2 * b + a + il] : t.wN[c] * (t.X[c] - t.X[c + a]);
     if (il < a - 1) uxw[(long long)j * (nx + 1) + i + 1] = fe;

@@ -342,16 +342,21 @@ __device__ __forceinline__ double apply_A(const DevSub& sd, const double* ex, co
 }
 
 // Refined solve of A x = B (FP64, t.B) into t.X; same stopping rule as the CTA path with
-// target = tol.  All threads of the CTA; red: two doubles of shared memory per warp.
+// target = tol.  warm: start from the iterate already in t.X (otherwise from zero).  All
+// threads of the CTA; red: two doubles of shared memory per warp.
 template <typename T, int A>
 __device__ void solve_refined(const DevSub& sd, Tables<T> t, const T* Q, bool refine, double tol, int ir_max,
-                              int* status, int* ir_used, double* red) {
+                              int* status, int* ir_used, double* red, bool warm = false) {
   const double target = tol;
   const int a = sd.a, b = sd.b, m = a * b;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int c = tid; c < m; c += nt) {
-    t.X[c] = 0.0;
-    t.Rr[c] = t.B[c];
+  if (warm) {  // t.X holds an initial iterate: start from its residual
+    for (int c = tid; c < m; c += nt) t.Rr[c] = t.B[c] - apply_A(sd, t.ex, t.wE, t.wN, t.X, c);
+  } else {
+    for (int c = tid; c < m; c += nt) {
+      t.X[c] = 0.0;
+      t.Rr[c] = t.B[c];
+    }
   }
   __syncthreads();
   const int sweeps = refine ? ir_max : 1;

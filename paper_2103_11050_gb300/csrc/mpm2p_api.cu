@@ -647,7 +647,7 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   const size_t nc = (size_t)R * nx * ny;
   DevState& d = c->d;
   int rc = MPM_OK;
-  double** cells[] = {&d.K, &d.q, &d.s, &d.s2, &d.kap_n, &d.kap_m, &d.p_m, &d.p_down, &d.fs, &d.fs2};
+  double** cells[] = {&d.K, &d.q, &d.s, &d.s2, &d.kap_n, &d.kap_m, &d.p_m, &d.p_down, &d.fs, &d.fs2, &d.x_ds};
   for (double** p : cells)
     if ((rc = dalloc_t(c, c->grid_allocs, p, nc)) != MPM_OK) break;
   c->s_buf0 = d.s;

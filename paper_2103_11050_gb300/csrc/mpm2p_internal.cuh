@@ -119,6 +119,7 @@ struct DevLevel {
 struct DevState {
   // cells [R][ny][nx]
   double *K, *q, *s, *s2, *kap_n, *kap_m, *p_m, *p_down;
+  double* x_ds;        // pinned Neumann solution of the last refined downscaling (initial iterate of the next)
   double *fs, *fs2;    // fractional flow f(s) of s / s2
   // faces
   double *ux, *uy;
