@@ -92,8 +92,10 @@ typedef struct mpm_stats {
 
 /* Stages timed by the profiler (each is the set of kernels of one step of the path). */
 enum {
-  MPM_STAGE_TRANSPORT = 0,     /* upwind substeps (CFL step), kappa^n, eps sums   */
-  MPM_STAGE_EPSILON = 1,       /* decision and new epsilon (mpm_step)                */
+  MPM_STAGE_TRANSPORT = 0,     /* upwind substeps (CFL step), kappa^n, epsilon and
+                                  the decision (all in the transport kernel)         */
+  MPM_STAGE_EPSILON = 1,       /* kept for layout: nothing is timed here since the
+                                  decision moved into the transport kernel           */
   MPM_STAGE_BASIS = 2,         /* Robin factorisation, BF solves, element matrices   */
   MPM_STAGE_IFACE_FACTOR = 3,  /* nested-dissection factorisation of the interface   */
   MPM_STAGE_PERTURB = 4,       /* MPM-2P residual, local solve, interface RHS        */
