@@ -1,16 +1,21 @@
 // Float64 reciprocal and division for a part whose float64 pipe is narrow (on GB300 the
 // correctly rounded float64 division costs tens of float64 instructions).
 //
-//   rcp64(x): seed y0 = 1/x in float32 (hardware approximation of the reciprocal of x rounded
-//             to float32, relative error < 2^-22), then two Newton-Raphson steps for f(y) =
-//             1/y - x, y <- y + y (1 - x y), each squaring the relative error (2^-44, then
-//             below the float64 rounding of the iteration itself).
+//   rcp64(x): seed y0 = 1/x in float32 (hardware approximation of the reciprocal of x
+//             truncated to float32; relative error below 2^-22 + 2^-23), then two
+//             Newton-Raphson steps for f(y) = 1/y - x, y <- y + y (1 - x y), each squaring the
+//             relative error (below 2^-42, then below the float64 rounding of the iteration).
 //   div64(a, b): q = a rcp64(b), then one residual correction q <- q + rcp64(b) (a - b q)
 //             (Markstein, IBM J. Res. Dev. 34(1), 1990), which leaves q within one ulp of
 //             a / b whenever a / b is a finite normal number.
-// A divisor outside [2^-125, 2^125] in magnitude (where the float32 seed or its reciprocal
-// would not be a normal number), zero, infinite or NaN takes the IEEE division instead.
+// The range test on the divisor, its truncation to float32 and the widening of the seed back
+// to float64 are integer repackings of the bit patterns (fp_bits.cuh): on GB300 the float64
+// conversions would occupy the narrow float64 pipe.  A divisor outside [2^-125, 2^125) in
+// magnitude (where the float32 seed or its reciprocal would not be a normal number), zero,
+// infinite or NaN takes the IEEE division instead.
 #pragma once
+
+#include "fp_bits.cuh"
 
 namespace mpm {
 
@@ -20,15 +25,19 @@ __device__ __forceinline__ float rcp_approx_f32(float x) {
   return y;
 }
 
-// x and 1/x both float32 normal numbers: 2^-125 <= |x| <= 2^125.
+// x and 1/x both float32 normal numbers (2^-125 <= |x| < 2^125, from the biased exponent
+// field: 898 <= e <= 1147); xf = x truncated to float32.
 __device__ __forceinline__ bool f32_seed_ok(double x, float& xf) {
-  xf = __double2float_rn(x);
-  const float ax = fabsf(xf);
-  return ax >= 0x1p-125f && ax <= 0x1p125f;
+  const uint64_t u = dbits(x);
+  const uint32_t hi = (uint32_t)(u >> 32);
+  const uint32_t e = (hi >> 20) & 0x7ffu;
+  if (e - 898u > 249u) return false;  // unsigned: also rejects e < 898
+  xf = f64_normal_to_f32_rz(hi, (uint32_t)u);
+  return true;
 }
 
 __device__ __forceinline__ double newton_rcp(double x, float xf) {
-  double y = (double)rcp_approx_f32(xf);
+  double y = f32_normal_to_f64(rcp_approx_f32(xf));  // a normal float32: exact widening
   y = fma(y, fma(-x, y, 1.0), y);
   return fma(y, fma(-x, y, 1.0), y);
 }

@@ -230,11 +230,25 @@ __global__ void __launch_bounds__(kTX * kTY) k_upwind_kappa(Grid g, DevState d, 
   // one warp per realisation
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int mine = 0;
+  constexpr int kBatch = 8;  // partials loaded together before they are summed (same order)
   for (int rr = warp; rr < g.R; rr += blockDim.x >> 5) {
     double a = 0.0, b = 0.0;
-    for (int k = lane; k < nblk; k += 32) {
-      a += __ldcg(&d.eps_part[((long long)rr * nblk + k) * 2 + 0]);
-      b += __ldcg(&d.eps_part[((long long)rr * nblk + k) * 2 + 1]);
+    const double* ep = d.eps_part + (long long)rr * nblk * 2;
+    for (int k0 = lane; k0 < nblk; k0 += 32 * kBatch) {
+      double va[kBatch], vb[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int k = k0 + 32 * u;
+        va[u] = k < nblk ? __ldcg(&ep[2 * k]) : 0.0;
+        vb[u] = k < nblk ? __ldcg(&ep[2 * k + 1]) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        if (k0 + 32 * u < nblk) {
+          a += va[u];
+          b += vb[u];
+        }
+      }
     }
     for (int o = 16; o > 0; o >>= 1) {
       a += __shfl_xor_sync(0xffffffffu, a, o);

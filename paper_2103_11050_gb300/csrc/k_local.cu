@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_mpm_local_w(Grid g, DevState 
   __syncthreads();
   for (int e = threadIdx.x; e < b * A; e += blockDim.x) {
     const int j = e / A, i = e - j * A;
-    t.th[e] = (i < a && j < b - 1) ? T(t.wN[j * a + i] * t.sc[j * a + i] * t.sc[j * a + i + a]) : T(0);
+    t.th[e] = (i < a && j < b - 1) ? warp::to_T<T>(t.wN[j * a + i] * t.sc[j * a + i] * t.sc[j * a + i + a]) : T(0);
   }
   if (qoff != 0) cp_async_wait_all();
   __syncthreads();
@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_mpm_local_w(Grid g, DevState 
   }
   double s = 0.0;
   for (int c = threadIdx.x; c < m; c += blockDim.x) s += t.X[c];
-  s = warp::cta_sum(s, red);  // also orders the fb writes before the reads below
+  s = warp::cta_sum0(s, red);  // its barrier also orders the fb writes before the reads below
   if (threadIdx.x == 0) d.sub_mean[(long long)r * d.st_sub + sidx] = s / m;
   // Interface right-hand side (Eq. mrc2) from the perturbation traces.
   if (sd.ndof > 0) {
@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_downscale_w(Grid g, DevState 
   __syncthreads();
   for (int e = threadIdx.x; e < b * A; e += blockDim.x) {
     const int j = e / A, i = e - j * A;
-    t.th[e] = (i < a && j < b - 1) ? T(t.wN[j * a + i] * t.sc[j * a + i] * t.sc[j * a + i + a]) : T(0);
+    t.th[e] = (i < a && j < b - 1) ? warp::to_T<T>(t.wN[j * a + i] * t.sc[j * a + i] * t.sc[j * a + i + a]) : T(0);
   }
   const double* qc = d.q + (long long)r * g.ncell();
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
@@ -661,7 +661,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_downscale_w(Grid g, DevState 
   warp::solve_refined<T, A>(sd, t, Q, refine != 0, tol, ir_max, d.status, d.ir_iters, red, warm);
   double s = 0.0;
   for (int c = threadIdx.x; c < m; c += blockDim.x) s += t.X[c];
-  s = warp::cta_sum(s, red);
+  s = warp::cta_sum0(s, red);
   __shared__ double shift_s;
   if (threadIdx.x == 0) shift_s = d.sub_target[(long long)r * d.st_sub + sidx] - s / m;
   __syncthreads();
@@ -683,8 +683,9 @@ __global__ void __launch_bounds__(kLocalThreads) k_downscale_w(Grid g, DevState 
     FN[c] = fn;
   }
   __syncthreads();
-  // max over the cells of max(total outflow, total inflow); signs from the bit patterns
-  double rate = 0.0;
+  // max over the cells of max(total outflow, total inflow); signs from the bit patterns, and
+  // the maxima (of non-negative sums) on the bit patterns too
+  unsigned long long rate_b = 0;
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
     const int jl = c / a, il = c - jl * a;
     const double o[4] = {-(il == 0 ? ub[jl] : FE[c - 1]), FE[c], -(jl == 0 ? ub[2 * b + il] : FN[c - a]), FN[c]};
@@ -694,9 +695,11 @@ __global__ void __launch_bounds__(kLocalThreads) k_downscale_w(Grid g, DevState 
       if (dpos(o[k])) out += o[k];
       else if (dneg(o[k])) in -= o[k];
     }
-    rate = fmax(rate, fmax(out, in));
+    const unsigned long long uo = nn_bits(out), ui = nn_bits(in);
+    const unsigned long long u = uo > ui ? uo : ui;
+    rate_b = u > rate_b ? u : rate_b;
   }
-  rate = warp::cta_max(rate, red);
+  const double rate = nn_from_bits(warp::cta_max_bits(rate_b, red));
   // last-block reduction of the per-subdomain maxima (threadfence-reduction pattern)
   if (threadIdx.x == 0) {
     d.rate_part[(long long)r * d.st_sub + sidx] = rate;
@@ -709,10 +712,12 @@ __global__ void __launch_bounds__(kLocalThreads) k_downscale_w(Grid g, DevState 
   __threadfence();
   const int nsub = gridDim.x;
   for (int rr = 0; rr < (int)gridDim.y; ++rr) {
-    double mx = 0.0;
-    for (int k = threadIdx.x; k < nsub; k += blockDim.x)
-      mx = fmax(mx, __ldcg(&d.rate_part[(long long)rr * d.st_sub + k]));
-    mx = warp::cta_max(mx, red);
+    unsigned long long mb = 0;
+    for (int k = threadIdx.x; k < nsub; k += blockDim.x) {
+      const unsigned long long u = nn_bits(__ldcg(&d.rate_part[(long long)rr * d.st_sub + k]));
+      mb = u > mb ? u : mb;
+    }
+    const double mx = nn_from_bits(warp::cta_max_bits(mb, red));
     if (threadIdx.x == 0) d.rate_max[rr] = mx;
   }
   if (threadIdx.x == 0) d.ticket[0] = 0;

@@ -17,6 +17,19 @@
 namespace mpm {
 namespace warp {
 
+// float64 -> factor type T and back.  For float32 both run on the integer units
+// (fp_bits.cuh): rounding to nearest even, and exact widening, over the float32 normal range,
+// which holds the scaled factors, residuals and corrections; anything smaller than 2^-126
+// becomes zero.
+template <typename T>
+__device__ __forceinline__ T to_T(double x);
+template <>
+__device__ __forceinline__ double to_T<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to_T<float>(double x) { return f64_to_f32_rn(x); }
+__device__ __forceinline__ double from_T(double v) { return v; }
+__device__ __forceinline__ double from_T(float v) { return f32_to_f64(v); }
+
 // Per-warp shared-memory tables of one subdomain (a x b cells, m = a b, padded width A).
 template <typename T>
 struct Tables {
@@ -100,9 +113,9 @@ __device__ void build(const Grid& g, const DevSub& sd, Tables<T> t, const double
     const int j = e / A, i = e - j * A;
     if (i < a) {
       const int c = j * a + i;
-      t.dh[e] = T(t.Rr[c] * t.sc[c] * t.sc[c]);
-      t.eh[e] = i < a - 1 ? T(-t.wE[c] * t.sc[c] * t.sc[c + 1]) : T(0);
-      t.th[e] = j < b - 1 ? T(t.wN[c] * t.sc[c] * t.sc[c + a]) : T(0);
+      t.dh[e] = to_T<T>(t.Rr[c] * t.sc[c] * t.sc[c]);
+      t.eh[e] = i < a - 1 ? to_T<T>(-t.wE[c] * t.sc[c] * t.sc[c + 1]) : T(0);
+      t.th[e] = j < b - 1 ? to_T<T>(t.wN[c] * t.sc[c] * t.sc[c + a]) : T(0);
     } else {
       t.dh[e] = T(1);
       t.eh[e] = T(0);
@@ -259,57 +272,85 @@ __device__ void solve(const DevSub& sd, Tables<T> t, const T* Q) {
   __syncthreads();
 }
 
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Sum / max over the CTA (red: one double of shared memory per warp).
-__device__ __forceinline__ double cta_sum(double v, double* red) {
+// Sum over the CTA, complete in thread 0 only (the other threads return their warp's sum).
+// One barrier, which also orders every shared-memory write issued before the call ahead of
+// every read after it; red (one double per warp) may be reused after the caller's next
+// barrier.
+__device__ __forceinline__ double cta_sum0(double v, double* red) {
   v = warp_sum(v);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double r = red[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r += red[w];
-  __syncthreads();
-  return r;
+  if (threadIdx.x == 0)
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+  return v;
 }
 
+// Maxima of non-negative doubles (+0, never -0) on their bit patterns (fp_bits.cuh): integer
+// compares instead of float64 ones; a NaN propagates.
+__device__ __forceinline__ unsigned long long warp_max_bits(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// Max over the CTA of a non-negative value (red: one double of shared memory per warp).
 __device__ __forceinline__ double cta_max(double v, double* red) {
-  v = warp_max(v);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  unsigned long long* ru = reinterpret_cast<unsigned long long*>(red);
+  const unsigned long long u = warp_max_bits(nn_bits(v));
+  if ((threadIdx.x & 31) == 0) ru[threadIdx.x >> 5] = u;
   __syncthreads();
-  double r = red[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[w]);
+  unsigned long long r = ru[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = ru[w] > r ? ru[w] : r;
   __syncthreads();
-  return r;
+  return nn_from_bits(r);
 }
 
-// Max over the CTA of two values at once (one pair of barriers).
-__device__ __forceinline__ void cta_max2(double& v1, double& v2, double* red) {
-  v1 = warp_max(v1);
-  v2 = warp_max(v2);
+// Max over the CTA of two non-negative values at once (one pair of barriers), as bit patterns.
+__device__ __forceinline__ void cta_max2_bits(unsigned long long& v1, unsigned long long& v2, double* red) {
+  unsigned long long* ru = reinterpret_cast<unsigned long long*>(red);
+  v1 = warp_max_bits(v1);
+  v2 = warp_max_bits(v2);
   const int nw = blockDim.x >> 5;
   if ((threadIdx.x & 31) == 0) {
-    red[threadIdx.x >> 5] = v1;
-    red[nw + (threadIdx.x >> 5)] = v2;
+    ru[threadIdx.x >> 5] = v1;
+    ru[nw + (threadIdx.x >> 5)] = v2;
   }
   __syncthreads();
-  double r1 = red[0], r2 = red[nw];
+  unsigned long long r1 = ru[0], r2 = ru[nw];
   for (int w = 1; w < nw; ++w) {
-    r1 = fmax(r1, red[w]);
-    r2 = fmax(r2, red[nw + w]);
+    r1 = ru[w] > r1 ? ru[w] : r1;
+    r2 = ru[nw + w] > r2 ? ru[nw + w] : r2;
   }
   __syncthreads();
   v1 = r1;
   v2 = r2;
+}
+
+// Max over the CTA of one non-negative value, as a bit pattern.
+__device__ __forceinline__ unsigned long long cta_max_bits(unsigned long long v, double* red) {
+  unsigned long long* ru = reinterpret_cast<unsigned long long*>(red);
+  v = warp_max_bits(v);
+  if ((threadIdx.x & 31) == 0) ru[threadIdx.x >> 5] = v;
+  __syncthreads();
+  unsigned long long r = ru[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = ru[w] > r ? ru[w] : r;
+  __syncthreads();
+  return r;
+}
+
+// Half of a non-negative double, on its bit pattern: the exponent field minus one for normal
+// numbers from 2^-1021 up; a shift of the pattern (exact halving, truncated) below that.
+__device__ __forceinline__ unsigned long long half_bits(unsigned long long u) {
+  return (u >> 52) >= 2ull ? u - (1ull << 52) : u >> 1;
 }
 
 // (A x)_c in flux form (see k_local.cu).
@@ -362,44 +403,50 @@ __device__ void solve_refined(const DevSub& sd, Tables<T> t, const T* Q, bool re
   const int sweeps = refine ? ir_max : 1;
   int it = 0;
   bool ok = false;
-  double rmax_prev = 1e300, smax = 0.0;
+  // The stopping rule on bit patterns of non-negative doubles (integer compares): rmax <=
+  // tol * smax, or stagnation (rmax > rmax_prev / 2) with rmax <= 1e3 tol * smax.  Both
+  // thresholds are fixed by the scale smax of the first iterate.
+  unsigned long long thr_tol = 0, thr_floor = 0, half_prev = nn_bits(0.5e300);
   for (; it < sweeps; ++it) {
     for (int e = tid; e < b * A; e += nt) {
       const int j = e / A, i = e - j * A;
-      t.V[e] = i < a ? T(t.Rr[j * a + i] * t.sc[j * a + i]) : T(0);
+      t.V[e] = i < a ? to_T<T>(t.Rr[j * a + i] * t.sc[j * a + i]) : T(0);
     }
     __syncthreads();
     solve<T, A>(sd, t, Q);
     for (int c = tid; c < m; c += nt) {
       const int j = c / a, i = c - j * a;
-      t.X[c] += double(t.V[j * A + i]) * t.sc[c];
+      t.X[c] += from_T(t.V[j * A + i]) * t.sc[c];
     }
     __syncthreads();
     if (!refine) { it = 1; ok = true; break; }
-    double rmax = 0.0;
+    unsigned long long rb = 0;  // max |r| as a bit pattern
     if (it == 0) {  // the scale max(|A||x| + |b|) is taken once, at the first iterate
-      double sm = 0.0;
+      unsigned long long sb = 0;
       for (int c = tid; c < m; c += nt) {
         double absx;
         const double r = t.B[c] - apply_A(sd, t.ex, t.wE, t.wN, t.X, c, absx);
         t.Rr[c] = r;
-        rmax = fmax(rmax, fabs(r));
-        sm = fmax(sm, absx + fabs(t.B[c]));
+        const unsigned long long ur = nn_bits(fabs(r)), us = nn_bits(absx + fabs(t.B[c]));
+        rb = ur > rb ? ur : rb;
+        sb = us > sb ? us : sb;
       }
-      cta_max2(rmax, sm, red);
-      smax = sm;
+      cta_max2_bits(rb, sb, red);
+      const double smax = nn_from_bits(sb);
+      thr_tol = nn_bits(target * smax);
+      thr_floor = nn_bits(1e3 * tol * smax);
     } else {
       for (int c = tid; c < m; c += nt) {
         const double r = t.B[c] - apply_A(sd, t.ex, t.wE, t.wN, t.X, c);
         t.Rr[c] = r;
-        rmax = fmax(rmax, fabs(r));
+        const unsigned long long ur = nn_bits(fabs(r));
+        rb = ur > rb ? ur : rb;
       }
-      rmax = cta_max(rmax, red);
+      rb = cta_max_bits(rb, red);
     }
-    // eta = rmax / smax, compared without dividing (every thread evaluates the test)
-    if (rmax <= target * smax) { ok = true; ++it; break; }
-    if (rmax > 0.5 * rmax_prev && rmax <= 1e3 * tol * smax) { ok = true; ++it; break; }  // FP64 floor reached
-    rmax_prev = rmax;
+    if (rb <= thr_tol) { ok = true; ++it; break; }
+    if (rb > half_prev && rb <= thr_floor) { ok = true; ++it; break; }  // FP64 floor reached
+    half_prev = half_bits(rb);
   }
   if (tid == 0) {
     if (!ok) atomicOr(status, 1);

@@ -61,6 +61,7 @@ struct mpm_ctx {
   std::vector<void*> grid_allocs, dec_allocs;
   // host staging for flags
   int* h_flags = nullptr;
+  int* h_status = nullptr;  // pinned: status word and refinement sweep count
   mpm_stats stats{};
   long long launches0 = 0;  // g_launches when the context was created
   long long init_rebuilds = 0;
@@ -160,17 +161,18 @@ int copy_in(mpm_ctx* c, double* dst, const double* src, size_t n, int mem) {
 }
 
 int sync_status(mpm_ctx* c) {
+  // status word and refinement sweep count (adjacent on the device), read in stream order
+  // behind the work they report on, so that one host wait covers both
+  CK(cudaMemcpyAsync(c->h_status, c->d.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  int w[2] = {0, 0};  // status word and refinement sweep count, adjacent on the device
-  CK(cudaMemcpy(w, c->d.status, sizeof(w), cudaMemcpyDeviceToHost));
-  const int st = w[0], it = w[1];
+  const int st = c->h_status[0], it = c->h_status[1];
   c->stats.ir_iters_max = std::max(c->stats.ir_iters_max, it);
   if (st & 2) {
-    CK(cudaMemset(c->d.status, 0, sizeof(int)));
+    CK(cudaMemsetAsync(c->d.status, 0, sizeof(int), c->stream));
     return fail(c, MPM_ERR_TIMEOUT, "a dependency wait of the dataflow interface sweep timed out");
   }
   if (st & 1) {
-    CK(cudaMemset(c->d.status, 0, sizeof(int)));
+    CK(cudaMemsetAsync(c->d.status, 0, sizeof(int), c->stream));
     return fail(c, MPM_ERR_NOT_CONVERGED, "local iterative refinement stopped above ir_tol=%g (ir_max=%d sweeps)",
                 c->ir_tol, c->ir_max);
   }
@@ -407,8 +409,10 @@ int run_interface(mpm_ctx* c) {
                    c->lev_max_nsep[L], c->d_srcmap, chained && c->use_pdl, st);
       chained = true;
     }
-    // level 1 (nodes with two leaf children) is done inside the reconstruction
-    for (int L = (int)c->levels.size() - 1; L >= 2; --L)
+    // the top level holds the root alone, whose separator values the upward sweep leaves
+    // final (no launch); level 1 (nodes with two leaf children) is done inside the
+    // reconstruction
+    for (int L = (int)c->levels.size() - 2; L >= 2; --L)
       launch_nd_down(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(),
                      c->lev_max_nsep[L], c->lev_max_nbnd[L], c->d_pmap, c->use_pdl, st);
   }
@@ -674,9 +678,11 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
                        cudaEventCreateWithFlags(&c->ev_reb_join, cudaEventDisableTiming) != cudaSuccess))
     rc = MPM_ERR_CUDA;
   if (rc == MPM_OK && cudaMallocHost(&c->h_flags, sizeof(int) * R) != cudaSuccess) rc = MPM_ERR_OOM;
+  if (rc == MPM_OK && cudaMallocHost(&c->h_status, sizeof(int) * 2) != cudaSuccess) rc = MPM_ERR_OOM;
   if (rc != MPM_OK) {
     destroy_streams(c);
     free_list(c->grid_allocs);
+    if (c->h_flags) cudaFreeHost(c->h_flags);
     delete c;
     return rc;
   }
@@ -703,6 +709,7 @@ int mpm_destroy(mpm_ctx* c) {
   release_decomposition(c);
   free_list(c->grid_allocs);
   if (c->h_flags) cudaFreeHost(c->h_flags);
+  if (c->h_status) cudaFreeHost(c->h_status);
   delete c;
   return MPM_OK;
 }
@@ -1078,14 +1085,21 @@ int mpm_set_saturation(mpm_ctx* c, const double* s, int mem) {
   if (!c) return MPM_ERR_ARG;
   const size_t n = (size_t)c->g.R * c->g.nx * c->g.ny;
   if (mem == MPM_MEM_HOST && s) {
+    // The copy goes to the scratch saturation buffer (every step writes it before reading
+    // it) while the host checks the values; the current saturation is replaced, by a
+    // device copy, only when every value lies in [0,1].
+    CK(cudaMemcpyAsync(c->d.s2, s, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     size_t bad = 0;  // branch-free count first (vectorises), then locate the first offender
     for (size_t i = 0; i < n; ++i) bad += !(s[i] >= 0 && s[i] <= 1);
+    CK(cudaStreamSynchronize(c->stream));  // the caller's buffer is free again
     if (bad)
       for (size_t i = 0; i < n; ++i)
         if (!(s[i] >= 0 && s[i] <= 1)) return fail(c, MPM_ERR_ARG, "saturation must lie in [0,1] (index %zu)", i);
+    CK(cudaMemcpyAsync(c->d.s, c->d.s2, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    int rc = copy_in(c, c->d.s, s, n, mem);
+    if (rc) return rc;
   }
-  int rc = copy_in(c, c->d.s, s, n, mem);
-  if (rc) return rc;
   c->have_s = true;
   if (c->have_K) launch_mobility_eps(c->g, c->d, false, c->stream);
   return check_launch(c);

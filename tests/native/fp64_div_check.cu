@@ -1,7 +1,9 @@
 // Checks mpm::div64 / mpm::rcp64 against the IEEE float64 division on the GPU: seeded
 // log-uniform operands over [1e-30, 1e30] with random signs, the fallback ranges of the
 // divisor (subnormal-as-float32, beyond float32), and exact cases.  Prints the largest
-// difference in ulps and exits non-zero when it exceeds one ulp.
+// difference in ulps and exits non-zero when it exceeds one ulp.  Also compares the
+// integer-unit conversions (fp_bits.cuh) with the hardware conversions on the same device
+// over the float32 normal range: bit-identical, or the program exits non-zero.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -15,6 +17,17 @@ __global__ void k_check(const double* a, const double* b, double* q, double* r, 
   if (i < n) {
     q[i] = mpm::div64(a[i], b[i]);
     r[i] = mpm::rcp64(b[i]);
+  }
+}
+
+// conversions: hardware and integer-unit results side by side
+__global__ void k_conv(const double* x, float* hw_n, float* sw_n, const float* f, double* hw_w, double* sw_w, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    hw_n[i] = __double2float_rn(x[i]);
+    sw_n[i] = mpm::f64_to_f32_rn(x[i]);
+    hw_w[i] = (double)f[i];
+    sw_w[i] = mpm::f32_to_f64(f[i]);
   }
 }
 
@@ -86,13 +99,55 @@ int main() {
       }
     }
   }
-  std::printf("n=%d max_ulp_div=%lld max_ulp_rcp=%lld exact_div=%lld\n", n, (long long)worst_q, (long long)worst_r,
-              exact);
+  // conversions over the float32 normal range (both signs, seeded exponents and mantissas)
+  const int nc = 1 << 20;
+  std::vector<double> cx(nc);
+  std::vector<float> cf(nc);
+  for (int i = 0; i < nc; ++i) {
+    const double m = 1.0 + unif();
+    const int e = -126 + (int)(253.999 * unif());
+    cx[i] = (unif() < 0.5 ? -1 : 1) * std::ldexp(m, e);
+    cf[i] = (float)((unif() < 0.5 ? -1 : 1) * std::ldexp(1.0 + unif(), -126 + (int)(253.999 * unif())));
+  }
+  double *dcx, *dhw_w, *dsw_w;
+  float *dcf, *dhw_n, *dsw_n;
+  cudaMalloc(&dcx, nc * 8);
+  cudaMalloc(&dhw_w, nc * 8);
+  cudaMalloc(&dsw_w, nc * 8);
+  cudaMalloc(&dcf, nc * 4);
+  cudaMalloc(&dhw_n, nc * 4);
+  cudaMalloc(&dsw_n, nc * 4);
+  cudaMemcpy(dcx, cx.data(), nc * 8, cudaMemcpyHostToDevice);
+  cudaMemcpy(dcf, cf.data(), nc * 4, cudaMemcpyHostToDevice);
+  k_conv<<<(nc + 255) / 256, 256>>>(dcx, dhw_n, dsw_n, dcf, dhw_w, dsw_w, nc);
+  std::vector<float> hw_n(nc), sw_n(nc);
+  std::vector<double> hw_w(nc), sw_w(nc);
+  cudaMemcpy(hw_n.data(), dhw_n, nc * 4, cudaMemcpyDeviceToHost);
+  cudaMemcpy(sw_n.data(), dsw_n, nc * 4, cudaMemcpyDeviceToHost);
+  cudaMemcpy(hw_w.data(), dhw_w, nc * 8, cudaMemcpyDeviceToHost);
+  cudaMemcpy(sw_w.data(), dsw_w, nc * 8, cudaMemcpyDeviceToHost);
+  if (cudaGetLastError() != cudaSuccess) {
+    std::printf("cuda error\n");
+    return 2;
+  }
+  long long conv_bad = 0;
+  for (int i = 0; i < nc; ++i) {
+    const bool narrow_ok = std::memcmp(&hw_n[i], &sw_n[i], 4) == 0 || std::fabs(cx[i]) >= 0x1.fffffep127;
+    conv_bad += !narrow_ok || std::memcmp(&hw_w[i], &sw_w[i], 8) != 0;
+  }
+  cudaFree(dcx);
+  cudaFree(dhw_w);
+  cudaFree(dsw_w);
+  cudaFree(dcf);
+  cudaFree(dhw_n);
+  cudaFree(dsw_n);
+  std::printf("n=%d max_ulp_div=%lld max_ulp_rcp=%lld exact_div=%lld conversions=%d conversion_mismatches=%lld\n", n,
+              (long long)worst_q, (long long)worst_r, exact, nc, conv_bad);
   if (iq >= 0) std::printf("worst div: %.17g / %.17g -> %.17g\n", a[iq], b[iq], q[iq]);
   if (ir >= 0) std::printf("worst rcp: 1 / %.17g -> %.17g\n", b[ir], r[ir]);
   cudaFree(da);
   cudaFree(db);
   cudaFree(dq);
   cudaFree(dr);
-  return (worst_q <= 1 && worst_r <= 1) ? 0 : 1;
+  return (worst_q <= 1 && worst_r <= 1 && conv_bad == 0) ? 0 : 1;
 }

@@ -3,7 +3,9 @@ with a Markstein residual correction) against the IEEE division, on the GPU.
 
 The check program (tests/native/fp64_div_check.cu) includes the library's own header, is
 built with nvcc for sm_103a and compares one million seeded log-uniform quotients, the
-fallback ranges of the divisor and exact cases: at most one ulp from the IEEE result.
+fallback ranges of the divisor and exact cases: at most one ulp from the IEEE result.  The
+same program compares the integer-unit float32/float64 conversions with the hardware ones on
+a million seeded values of the float32 normal range: bit-identical.
 """
 import os
 import shutil
@@ -28,3 +30,4 @@ def test_div64_within_one_ulp_of_ieee():
         out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert out.returncode == 0, out.stdout + out.stderr
     assert "max_ulp_div=" in out.stdout
+    assert "conversion_mismatches=0" in out.stdout

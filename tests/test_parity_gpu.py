@@ -193,3 +193,29 @@ def test_refinement_cap_reports_not_converged():
     with pytest.raises(B.MPMError) as ei:
         ctx.sync()
     assert ei.value.code == B.MPM_ERR_NOT_CONVERGED
+
+
+def test_rejected_saturation_leaves_state_unchanged():
+    # a saturation outside [0,1] is refused before it replaces the current one: the state read
+    # back is unchanged and the next steps match, bit for bit, a context that never saw the call
+    from paper_2103_11050_gb300 import binding as B
+    c = case("contrast64")
+    ctxs = [_gpu(c, 1), _gpu(c, 1)]
+    for ctx in ctxs:
+        ctx.init(0.1)
+        ctx.step(0.1, 0.5, 1)
+    before = ctxs[0].get_saturation()
+    bad = before.copy()
+    bad[0, 7, 9] = 1.5
+    with pytest.raises(B.MPMError) as ei:
+        ctxs[0].set_saturation(bad)
+    assert ei.value.code == B.MPM_ERR_ARG
+    assert np.array_equal(ctxs[0].get_saturation(), before)
+    for ctx in ctxs:
+        ctx.set_saturation(before)
+        for _ in range(3):
+            ctx.step(0.1, 0.5, 1)
+    s0, s1 = ctxs[0].get_saturation(), ctxs[1].get_saturation()
+    ux0, _ = ctxs[0].get_flux()
+    ux1, _ = ctxs[1].get_flux()
+    assert np.array_equal(s0, s1) and np.array_equal(ux0, ux1)
