@@ -37,6 +37,7 @@ WORKLOAD = "gaussian256"
 TRAFFIC_DOWNSCALE_SOLVE = 8.724992e6
 METRIC = "fine-cell pressure updates/s (MRCM & MPM-2P) at <=1e-8 rel flux err vs FP64"
 UNIT = "cell-updates/s"
+E2E_PASSES = 3
 CFL = 0.5
 N_SUB = 1
 
@@ -222,22 +223,30 @@ def run_gpu(args, w):
                  "fp64_form_ms_per_step": f64["ms"] / args.steps,
                  "fp64_form_stage_ms_per_step_eager": {k: v[0] / args.steps for k, v in f64p["prof"].items()}}
 
-    # end to end through the C ABI with host buffers: per step set s (h2d), step, read s (d2h)
-    ctx = setup_ctx(B, w, K, s0, prec, stream.cuda_stream)
-    ctx.init(eta)
-    for _ in range(args.warmup):
-        ctx.step(eta, CFL, N_SUB)
-    s_host = torch.empty((1, w["ny"], w["nx"]), dtype=torch.float64).pin_memory().numpy()
-    ctx.get_saturation(s_host)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ctx.set_saturation(s_host)
-        ctx.step(eta, CFL, N_SUB)
+    # end to end through the C ABI with host buffers: per step set s (h2d), step, read s (d2h).
+    # Each pass replays the timed steps of the device measurement on a fresh context (same
+    # initial state, same rebuild steps); the host clock of one pass is exposed to one-off
+    # host stalls, so the median of the passes is reported.
+    def e2e_pass():
+        ctx = setup_ctx(B, w, K, s0, prec, stream.cuda_stream)
+        ctx.init(eta)
+        for _ in range(args.warmup):
+            ctx.step(eta, CFL, N_SUB)
+        s_host = torch.empty((1, w["ny"], w["nx"]), dtype=torch.float64).pin_memory().numpy()
         ctx.get_saturation(s_host)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    ctx.close()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.set_saturation(s_host)
+            ctx.step(eta, CFL, N_SUB)
+            ctx.get_saturation(s_host)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        ctx.close()
+        return t
+
+    e2e_passes = [e2e_pass() for _ in range(E2E_PASSES)]
+    e2e_s = statistics.median(e2e_passes)
 
     pk, pk_kind = peaks()
     prof = main["prof"]
@@ -270,7 +279,8 @@ def run_gpu(args, w):
                                  "fp64": "FP64 throughout"}[prec]},
         "gpu_launches": main["launches"],
         "e2e": {"value": cells * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * cells,
-                "d2h_bytes_per_step": 8 * cells},
+                "d2h_bytes_per_step": 8 * cells, "passes": [cells * args.steps / t for t in e2e_passes],
+                "reported": f"median of {E2E_PASSES} passes, each the timed steps on a fresh context"},
         "roofline": roof,
         "clocks": clk.summary(),
         "peaks_source": pk_kind,

@@ -25,7 +25,10 @@
  *    the normal velocity): ux is [R][ny][nx+1] (x-face left of cell (i,j), +x positive),
  *    uy is [R][ny+1][nx] (+y positive).
  *  - mem = MPM_MEM_HOST: the pointer is host memory (pageable or pinned); the call copies
- *    synchronously.  mem = MPM_MEM_DEVICE: the pointer is device memory of the context's
+ *    synchronously.  Pinned (page-locked, CUDA-registered) host memory is read or written
+ *    directly by a kernel, through the device address CUDA reports for it, instead of a
+ *    copy-engine transfer; pageable memory takes cudaMemcpyAsync.  Either way the buffer is
+ *    free again when the call returns.  mem = MPM_MEM_DEVICE: the pointer is device memory of the context's
  *    device (for instance a torch CUDA tensor's data_ptr()); the copy is enqueued on the
  *    context's stream.
  *  - The caller owns every pointer it passes; setters copy into library-owned device
@@ -152,7 +155,10 @@ int mpm_set_boundary(mpm_ctx* ctx, const int type[4], const double val[4], doubl
 int mpm_set_decomposition(mpm_ctx* ctx, int ncx, const int* col_w, int ncy, const int* row_h,
                           int seg_len, int degree, double alpha);
 
-/* Water saturation s [R][ny][nx] in [0,1]; also recomputes kappa^n = lambda(s) K. */
+/* Water saturation s [R][ny][nx] in [0,1]; also recomputes kappa^n = lambda(s) K.  Host
+ * values are range-checked (on the device for pinned memory, on the host otherwise) before
+ * they replace the current saturation: MPM_ERR_ARG, naming the first index outside [0,1],
+ * leaves the context unchanged. */
 int mpm_set_saturation(mpm_ctx* ctx, const double* s, int mem);
 
 /* MRCM basis build at the current kappa^n (Algorithm 1, initialisation and rebuild branch; Eqs. mrc1,

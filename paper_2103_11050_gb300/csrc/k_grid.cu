@@ -275,6 +275,36 @@ __global__ void __launch_bounds__(kTX * kTY) k_upwind_kappa(Grid g, DevState d, 
   }
 }
 
+// Host-visible transfers without a copy engine: src / dst is pinned host memory addressed
+// from the device (the device address CUDA reports for it).  k_load_checked copies n values
+// in and raises *bad (also pinned host memory) when one lies outside [0,1];
+// k_store_host copies n values out and, from one thread, the two status words after them in
+// stream order.
+__global__ void k_load_checked(const double* __restrict__ src, double* __restrict__ dst, long long n, int* bad) {
+  int found = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = src[i];
+    dst[i] = v;
+    found |= !(v >= 0.0 && v <= 1.0);
+  }
+  if (__syncthreads_or(found) && threadIdx.x == 0) *reinterpret_cast<volatile int*>(bad) = 1;
+}
+
+__global__ void k_store_host(const double* __restrict__ src, double* __restrict__ dst, long long n,
+                             const int* status, int* status_host) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    status_host[0] = status[0];
+    status_host[1] = status[1];
+  }
+}
+
+int transfer_blocks(long long n) {
+  const long long nb = (n + kThreads - 1) / kThreads;
+  return (int)(nb < 1 ? 1 : nb < 1216 ? nb : 1216);  // up to 8 CTAs per SM of 152
+}
+
 int cell_blocks(const Grid& g) {
   long long nb = (g.ncell() + kThreads - 1) / kThreads;
   return (int)(nb < 1024 ? nb : 1024);
@@ -296,6 +326,17 @@ void launch_mobility_eps(const Grid& g, const DevState& d, bool with_eps, cudaSt
 
 void launch_choose(const Grid& g, const DevState& d, double eta, cudaStream_t st) {
   k_choose<<<(g.R + 127) / 128, 128, 0, st>>>(g, d, eta);
+  ++g_launches;
+}
+
+void launch_load_checked(const double* src_dev, double* dst, long long n, int* bad_dev, cudaStream_t st) {
+  k_load_checked<<<transfer_blocks(n), kThreads, 0, st>>>(src_dev, dst, n, bad_dev);
+  ++g_launches;
+}
+
+void launch_store_host(const double* src, double* dst_dev, long long n, const int* status, int* status_host_dev,
+                       cudaStream_t st) {
+  k_store_host<<<transfer_blocks(n), kThreads, 0, st>>>(src, dst_dev, n, status, status_host_dev);
   ++g_launches;
 }
 

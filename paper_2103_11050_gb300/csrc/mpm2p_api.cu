@@ -61,7 +61,8 @@ struct mpm_ctx {
   std::vector<void*> grid_allocs, dec_allocs;
   // host staging for flags
   int* h_flags = nullptr;
-  int* h_status = nullptr;  // pinned: status word and refinement sweep count
+  int* h_status = nullptr;  // pinned: status word and refinement sweep count, then a range flag
+  int* h_status_dev = nullptr;  // the device address of h_status
   mpm_stats stats{};
   long long launches0 = 0;  // g_launches when the context was created
   long long init_rebuilds = 0;
@@ -160,12 +161,31 @@ int copy_in(mpm_ctx* c, double* dst, const double* src, size_t n, int mem) {
   return MPM_OK;
 }
 
+// The device address of pinned (page-locked, registered) host memory, or null for any other
+// pointer; kernels read and write such memory directly, without a copy engine.
+void* pinned_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the query's error: the caller takes the copy path
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+int check_status(mpm_ctx* c);
+
 int sync_status(mpm_ctx* c) {
   // status word and refinement sweep count (adjacent on the device), read in stream order
   // behind the work they report on, so that one host wait covers both
   CK(cudaMemcpyAsync(c->h_status, c->d.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  const int st = c->h_status[0], it = c->h_status[1];
+  return check_status(c);
+}
+
+// Acts on the status words already in h_status (after a host wait).
+int check_status(mpm_ctx* c) {
+  const int st = reinterpret_cast<volatile int*>(c->h_status)[0];
+  const int it = reinterpret_cast<volatile int*>(c->h_status)[1];
   c->stats.ir_iters_max = std::max(c->stats.ir_iters_max, it);
   if (st & 2) {
     CK(cudaMemsetAsync(c->d.status, 0, sizeof(int), c->stream));
@@ -182,6 +202,12 @@ int sync_status(mpm_ctx* c) {
 int copy_out(mpm_ctx* c, double* dst, const double* src, size_t n, int mem) {
   if (!dst) return fail(c, MPM_ERR_ARG, "null output pointer");
   if (mem == MPM_MEM_HOST) {
+    if (void* dd = pinned_device_ptr(dst)) {  // pinned: one kernel writes the values and the status words
+      launch_store_host(src, static_cast<double*>(dd), (long long)n, c->d.status, c->h_status_dev, c->stream);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(c->stream));
+      return check_status(c);
+    }
     CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   } else if (mem == MPM_MEM_DEVICE) {
     CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
@@ -678,7 +704,9 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
                        cudaEventCreateWithFlags(&c->ev_reb_join, cudaEventDisableTiming) != cudaSuccess))
     rc = MPM_ERR_CUDA;
   if (rc == MPM_OK && cudaMallocHost(&c->h_flags, sizeof(int) * R) != cudaSuccess) rc = MPM_ERR_OOM;
-  if (rc == MPM_OK && cudaMallocHost(&c->h_status, sizeof(int) * 2) != cudaSuccess) rc = MPM_ERR_OOM;
+  if (rc == MPM_OK && cudaMallocHost(&c->h_status, sizeof(int) * 4) != cudaSuccess) rc = MPM_ERR_OOM;
+  if (rc == MPM_OK && cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->h_status_dev), c->h_status, 0) != cudaSuccess)
+    rc = MPM_ERR_CUDA;
   if (rc != MPM_OK) {
     destroy_streams(c);
     free_list(c->grid_allocs);
@@ -1086,13 +1114,23 @@ int mpm_set_saturation(mpm_ctx* c, const double* s, int mem) {
   const size_t n = (size_t)c->g.R * c->g.nx * c->g.ny;
   if (mem == MPM_MEM_HOST && s) {
     // The copy goes to the scratch saturation buffer (every step writes it before reading
-    // it) while the host checks the values; the current saturation is replaced, by a
-    // device copy, only when every value lies in [0,1].
-    CK(cudaMemcpyAsync(c->d.s2, s, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    size_t bad = 0;  // branch-free count first (vectorises), then locate the first offender
-    for (size_t i = 0; i < n; ++i) bad += !(s[i] >= 0 && s[i] <= 1);
-    CK(cudaStreamSynchronize(c->stream));  // the caller's buffer is free again
-    if (bad)
+    // it) and is range-checked on the way; the current saturation is replaced, by a device
+    // copy, only when every value lies in [0,1].  Pinned memory is read by a kernel that
+    // also checks the values; other host memory takes a copy while the host checks them.
+    size_t bad = 0;
+    if (void* ds = pinned_device_ptr(s)) {
+      volatile int* flag = reinterpret_cast<volatile int*>(c->h_status) + 2;
+      *flag = 0;
+      launch_load_checked(static_cast<const double*>(ds), c->d.s2, (long long)n, c->h_status_dev + 2, c->stream);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(c->stream));
+      bad = *flag != 0;
+    } else {
+      CK(cudaMemcpyAsync(c->d.s2, s, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      for (size_t i = 0; i < n; ++i) bad += !(s[i] >= 0 && s[i] <= 1);  // branch-free (vectorises)
+      CK(cudaStreamSynchronize(c->stream));  // the caller's buffer is free again
+    }
+    if (bad)  // locate the first offender
       for (size_t i = 0; i < n; ++i)
         if (!(s[i] >= 0 && s[i] <= 1)) return fail(c, MPM_ERR_ARG, "saturation must lie in [0,1] (index %zu)", i);
     CK(cudaMemcpyAsync(c->d.s, c->d.s2, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));

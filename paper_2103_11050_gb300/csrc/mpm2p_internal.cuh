@@ -182,6 +182,10 @@ int grid_cell_blocks(const Grid& g);
 void launch_mobility_eps(const Grid& g, const DevState& d, bool with_eps, cudaStream_t st);
 void launch_choose(const Grid& g, const DevState& d, double eta, cudaStream_t st);
 void launch_fill_flags(const Grid& g, const DevState& d, int v, cudaStream_t st);
+// transfers with pinned host memory addressed from the device (no copy engine)
+void launch_load_checked(const double* src_dev, double* dst, long long n, int* bad_dev, cudaStream_t st);
+void launch_store_host(const double* src, double* dst_dev, long long n, const int* status, int* status_host_dev,
+                       cudaStream_t st);
 void launch_upwind(const Grid& g, const DevState& d, double cfl, double fmax, cudaStream_t st);
 int upwind_kappa_blocks(const Grid& g);
 void launch_upwind_kappa(const Grid& g, const DevState& d, double cfl, double fmax, bool decide, double eta,

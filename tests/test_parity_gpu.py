@@ -219,3 +219,37 @@ def test_rejected_saturation_leaves_state_unchanged():
     ux0, _ = ctxs[0].get_flux()
     ux1, _ = ctxs[1].get_flux()
     assert np.array_equal(s0, s1) and np.array_equal(ux0, ux1)
+
+
+def test_pinned_host_buffers_match_pageable():
+    # pinned host buffers take kernel transfers (no copy engine), pageable ones a copy: the
+    # same values either way, and the same range check on the way in
+    import torch
+    from paper_2103_11050_gb300 import binding as B
+    c = case("contrast64")
+    shape = (1, c["ny"], c["nx"])
+    ctxs = [_gpu(c, 1), _gpu(c, 1)]
+    for ctx in ctxs:
+        ctx.init(0.1)
+        ctx.step(0.1, 0.5, 1)
+    pinned = torch.empty(shape, dtype=torch.float64).pin_memory().numpy()
+    ctxs[0].get_saturation(pinned)
+    pageable = ctxs[1].get_saturation()
+    assert np.array_equal(pinned, pageable)
+    pinned[0, 3, 5] = -0.25
+    with pytest.raises(B.MPMError) as ei:
+        ctxs[0].set_saturation(pinned)
+    assert ei.value.code == B.MPM_ERR_ARG and "index" in str(ei.value)
+    pinned[0, 3, 5] = pageable[0, 3, 5]
+    ctxs[0].set_saturation(pinned)
+    ctxs[1].set_saturation(pageable)
+    for _ in range(3):
+        for ctx in ctxs:
+            ctx.step(0.1, 0.5, 1)
+    ux_p = torch.empty((1, c["ny"], c["nx"] + 1), dtype=torch.float64).pin_memory().numpy()
+    uy_p = torch.empty((1, c["ny"] + 1, c["nx"]), dtype=torch.float64).pin_memory().numpy()
+    ctxs[0].get_flux(ux_p, uy_p)
+    ux, uy = ctxs[1].get_flux()
+    assert np.array_equal(ux_p, ux) and np.array_equal(uy_p, uy)
+    ctxs[0].get_saturation(pinned)
+    assert np.array_equal(pinned, ctxs[1].get_saturation())
