@@ -34,7 +34,7 @@ from paper_2103_11050_gb300 import fields  # noqa: E402
 WORKLOAD = "gaussian256"
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_downscale_w launch (ncu capture of
 # this code, see profiles/); None when the kernel changed since the capture.
-TRAFFIC_DOWNSCALE_SOLVE = 8.724992e6
+TRAFFIC_DOWNSCALE_SOLVE = 8.717824e6
 METRIC = "fine-cell pressure updates/s (MRCM & MPM-2P) at <=1e-8 rel flux err vs FP64"
 UNIT = "cell-updates/s"
 E2E_PASSES = 3
