@@ -93,7 +93,8 @@ def uneven_widths(total: int, parts, seed: int) -> list[int]:
     return [int(v) for v in rng.permutation(parts)]
 
 
-# Workloads used by the tests and the benchmark (see the design doc for the recipe).
+# Workloads used by the tests and the benchmark: grid, subdomain layout, covariance of the
+# log-permeability field, viscosity ratio and rebuild threshold of each, listed per entry.
 WORKLOADS = {
     # 64x64, 4x4 subdomains of 16x16, exponential GRF (ell 0.1, var 1), M = 1,
     # rebuild every step (eta < 0).

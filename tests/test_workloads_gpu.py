@@ -1,4 +1,4 @@
-"""GPU path against the oracle on workload-shaped inputs (inputs):
+"""GPU path against the oracle on workload-shaped inputs (the seeded fields of fields.py):
 the 64^2 rebuild-every-step run in full, the 256^2 benchmark workload at full size, a
 channelised contrast-1e4 field, an ensemble of realisations on an uneven decomposition,
 and a homogeneous fingering run.  Tolerances as in test_parity_gpu (1e-10 FP64, 1e-8 mixed)."""
