@@ -345,6 +345,57 @@ def test_transport_constant_state_preserved():
     np.testing.assert_allclose(s1, 1.0, atol=1e-13)
 
 
+def test_transport_converges_to_buckley_leverett():
+    # 1D strip at unit total velocity, s = 0 initially, water (s = 1) injected at x = 0
+    # (Eq. BL2D in one dimension).  The exact solution at injected pore volume Q is the
+    # Buckley-Leverett profile with the Welge shock: the tangent condition f(s)/s = f'(s)
+    # for f = M s^2 / (M s^2 + (1-s)^2) gives (M + 1) s^2 = 1, so s_f = 1/sqrt(M + 1); behind
+    # the shock s solves f'(s) = x / Q.  First-order upwind converges to it in L1 (at about
+    # half order across the shock), conserving the injected volume exactly.
+    M, Q = 5.0, 0.3
+    f = lambda v: M * v * v / (M * v * v + (1.0 - v) ** 2)
+
+    def fprime(v, d=1e-6):  # central difference of f (independent of the oracle's f')
+        lo, hi = max(v - d, 0.0), min(v + d, 1.0)
+        return (f(hi) - f(lo)) / (hi - lo)
+
+    def bisect(g, lo, hi):
+        glo = g(lo) > 0
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if (g(mid) > 0) == glo:
+                lo = mid
+            else:
+                hi = mid
+        return 0.5 * (lo + hi)
+
+    s_f = 1.0 / np.sqrt(M + 1.0)
+    assert bisect(lambda v: fprime(v) * v - f(v), 1e-3, 1.0) == pytest.approx(s_f, abs=1e-6)
+    xi_f = fprime(s_f)
+
+    def exact(x):
+        xi = x / Q
+        return 0.0 if xi >= xi_f else bisect(lambda v: fprime(v) - xi, s_f, 1.0)
+
+    errs = []
+    for nx in (25, 50, 100, 200):
+        h = 1.0 / nx
+        prob = O.Problem(nx, 1, h, (O.DIRICHLET, O.DIRICHLET, O.NEUMANN, O.NEUMANN), (1, 0, 0, 0), M=M)
+        Fx = np.full((1, nx + 1), h)  # integrated face flux h x unit velocity
+        Fy = np.zeros((2, nx))
+        dt = O.cfl_dt(Fx, Fy, prob, 0.5)
+        s, t = np.zeros((1, nx)), 0.0
+        while t < Q - 1e-15:
+            step = min(dt, Q - t)
+            s = O.upwind_step(s, Fx, Fy, step, prob)
+            t += step
+        assert h * np.sum(s) == pytest.approx(Q, abs=1e-12)  # front still inside: all water stays
+        xc = (np.arange(nx) + 0.5) * h
+        errs.append(h * float(np.sum(np.abs(s[0] - np.array([exact(x) for x in xc])))))
+    assert all(a > b for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < errs[0] / 3.0 and errs[-1] < 0.012, errs
+
+
 # ---------------------------------------------------------------- Algorithm 1
 
 def test_epsilon_relative_l2():
