@@ -27,14 +27,15 @@
  *  - mem = MPM_MEM_HOST: the pointer is host memory (pageable or pinned); the call copies
  *    synchronously.  Pinned (page-locked, CUDA-registered) host memory is read or written
  *    directly by a kernel, through the device address CUDA reports for it, instead of a
- *    copy-engine transfer; pageable memory takes cudaMemcpyAsync.  Either way the buffer is
- *    free again when the call returns.  mem = MPM_MEM_DEVICE: the pointer is device memory of the context's
- *    device (for instance a torch CUDA tensor's data_ptr()); the copy is enqueued on the
- *    context's stream.
+ *    copy-engine transfer; pageable memory takes cudaMemcpyAsync.  Either way the buffer
+ *    is free again when the call returns.  mem = MPM_MEM_DEVICE: the pointer is device
+ *    memory of the context's device (for instance a torch CUDA tensor's data_ptr()); the
+ *    copy is enqueued on the context's stream.
  *  - The caller owns every pointer it passes; setters copy into library-owned device
  *    memory, getters copy out.  Changing the precision, fluids, boundary data or
- *    decomposition discards the stored basis (call mpm_init or mpm_build_basis again).  The library allocates its device memory at
- *    mpm_set_decomposition (and frees it in mpm_destroy); compute calls allocate nothing.
+ *    decomposition discards the stored basis (call mpm_init or mpm_build_basis again).
+ *    The library allocates its device memory at mpm_set_decomposition (and frees it in
+ *    mpm_destroy); compute calls allocate nothing.
  *  - All work is enqueued on the stream given to mpm_create; compute calls do not
  *    synchronise the host unless stated (mpm_get_*, mpm_get_stats and calls that return
  *    values through host pointers synchronise the stream).
