@@ -100,6 +100,52 @@ def test_fine_neumann_rate_bc():
 
 # ---------------------------------------------------------------- MRCM
 
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 4.0])
+def test_local_robin_solve_reproduces_linear_pressure(alpha):
+    # Local problem (Eq. mrc1) in a homogeneous medium with the Robin data of an exact linear
+    # pressure p = 1 + gx x + gy y.  The Robin condition -beta u.n + lambda = g with
+    # beta = alpha H / kappa (Eq. beta) and u = -kappa grad p gives g = p(face) +
+    # alpha H dp/dn on each interface face; two-point fluxes are exact for linear fields, so
+    # the local solve must return the field at the cell centres and the exact integrated
+    # outward fluxes.  The subdomain (bottom middle of 3 x 3) has three interface sides and a
+    # physical Neumann side carrying the field's outward velocity.
+    nx, ny = 24, 18
+    h = 1.0 / nx
+    kap, gx, gy = 2.5, 0.3, -0.7
+    field = lambda x, y: 1.0 + gx * x + gy * y
+    # outward normal derivative of p and outward velocity u.n per side (left, right, bottom, top)
+    dpdn = {O.LEFT: -gx, O.RIGHT: gx, O.BOTTOM: -gy, O.TOP: gy}
+    prob = O.Problem(nx, ny, h, (O.DIRICHLET, O.DIRICHLET, O.NEUMANN, O.NEUMANN),
+                     (1.0, 0.0, -kap * dpdn[O.BOTTOM], -kap * dpdn[O.TOP]), M=1.0)
+    dec = O.Decomposition(nx, ny, [8, 8, 8], [6, 6, 6], 2, 1, alpha)
+    sd = dec.subs[1]
+    assert [side.kind for side in sd.sides] == ["iface", "iface", "phys", "iface"]
+    kappa = np.full((ny, nx), kap)
+    g_faces = []
+    for side in sd.sides:
+        g = []
+        for (j, i) in side.gcells:
+            xf, yf = (i + 0.5) * h, (j + 0.5) * h
+            if side.which == O.LEFT:
+                xf = i * h
+            elif side.which == O.RIGHT:
+                xf = (i + 1) * h
+            elif side.which == O.BOTTOM:
+                yf = j * h
+            else:
+                yf = (j + 1) * h
+            g.append(field(xf, yf) + alpha * side.length * h * dpdn[side.which])
+        g_faces.append(np.array(g))
+    A = O.local_matrix(kappa, prob, dec, sd)
+    rhs = O.local_rhs(kappa, prob, dec, sd, np.zeros(sd.m), g_faces)
+    p_loc = np.linalg.solve(A, rhs)
+    jl, il = np.divmod(np.arange(sd.m), sd.a)
+    exact = field((sd.x0 + il + 0.5) * h, (sd.y0 + jl + 0.5) * h)
+    np.testing.assert_allclose(p_loc, exact, rtol=1e-12, atol=1e-12)
+    for side, tr in zip(sd.sides, O.local_traces(p_loc, kappa, prob, dec, sd, g_faces)):
+        np.testing.assert_allclose(tr, h * (-kap * dpdn[side.which]), rtol=1e-11, atol=1e-13)
+
+
 def test_mrcm_single_subdomain_equals_fine():
     nx, ny = 12, 8
     prob = _prob(nx, ny)
