@@ -39,6 +39,12 @@ Where the paper is silent the reading taken is written next to the code:
   ||kappa^n - kappa^m|| / ||kappa^m|| per realisation.
 * transport (Section 4): explicit Euler, first-order upwind, C_n substeps with
   the flux frozen, dt = cfl h^2 / (max f' * max_c max(sum out, sum in)).
+
+Pins (tests/test_oracle_pins.py) check each building block against closed forms, brute
+force, the paper's special cases and printed numbers, and invariants.  Parity unpinned:
+simulate_init / simulate_step as whole Algorithm 1 trajectories.  Their components and the
+decision logic are pinned one by one, but a multi-step trajectory has no independent
+reference, so the GPU path is compared with it directly.
 """
 from __future__ import annotations
 
