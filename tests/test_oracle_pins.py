@@ -80,6 +80,52 @@ def test_fine_series_resistance_strip():
     assert p[0, 0] == pytest.approx(2.0 - flux / 2.0, rel=1e-13)
 
 
+def test_fine_solve_minimises_discrete_energy():
+    # Brute force on a small heterogeneous grid: the two-point equations are the optimality
+    # conditions of the discrete energy
+    #   E(p) = 1/2 sum_interior T_f (p_a - p_b)^2 + sum_Dirichlet kappa_c (p_c - g)^2
+    #          - sum_c q_c h^2 p_c + sum_Neumann z h p_c,
+    # with T_f the series conductance of the two half cells (each 2 kappa).  The energy is
+    # written here face by face, independently of the oracle's assembly; its gradient (central
+    # differences, exact for a quadratic up to rounding) must vanish at the oracle's solution,
+    # and every perturbation must raise it.
+    nx, ny, h = 5, 4, 0.25
+    rng = np.random.default_rng(11)
+    kappa = np.exp(rng.normal(0.0, 1.5, (ny, nx)))
+    q = rng.normal(0.0, 1.0, (ny, nx))
+    prob = O.Problem(nx, ny, h, (O.DIRICHLET, O.DIRICHLET, O.NEUMANN, O.NEUMANN), (1.3, -0.4, 0.7, -0.2), M=1.0,
+                     q=q)
+    p_star = O.fine_solve(kappa, prob)
+
+    def energy(p):
+        e = 0.0
+        for j in range(ny):
+            for i in range(nx):
+                for (ii, jj) in ((i + 1, j), (i, j + 1)):
+                    if ii < nx and jj < ny:
+                        t = 1.0 / (1.0 / (2.0 * kappa[j, i]) + 1.0 / (2.0 * kappa[jj, ii]))
+                        e += 0.5 * t * (p[j, i] - p[jj, ii]) ** 2
+                e -= q[j, i] * h * h * p[j, i]
+        for j in range(ny):
+            e += kappa[j, 0] * (p[j, 0] - 1.3) ** 2 + kappa[j, nx - 1] * (p[j, nx - 1] + 0.4) ** 2
+        for i in range(nx):
+            e += 0.7 * h * p[0, i] - 0.2 * h * p[ny - 1, i]
+        return e
+
+    step = 1e-3
+    grad = np.zeros((ny, nx))
+    for j in range(ny):
+        for i in range(nx):
+            d = np.zeros((ny, nx))
+            d[j, i] = step
+            grad[j, i] = (energy(p_star + d) - energy(p_star - d)) / (2.0 * step)
+    scale = float(np.max(kappa) * np.max(np.abs(p_star)))
+    assert np.max(np.abs(grad)) <= 1e-9 * scale
+    e0 = energy(p_star)
+    for _ in range(5):
+        assert energy(p_star + 0.05 * rng.normal(size=(ny, nx))) > e0
+
+
 def test_fine_matrix_spd():
     prob = _prob(6, 5)
     A, _ = O.fine_system(_field(6, 5), prob)
