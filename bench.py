@@ -2,17 +2,27 @@
 
 One "step" is one pass of Algorithm 1's loop over the whole workload: upwind transport,
 kappa^n and epsilon, an MRCM basis rebuild or an MPM-2P reuse update, the interface
-solve and the downscaling.  Metric: fine-cell pressure updates per second
-(cells x realisations x timed steps / device time), all on the GPU.
+solve and the downscaling.  Metric: fine-cell pressure updates per second.
 
-Default workload "gaussian256": 256 x 256 cells, 16 x 16 subdomains of 16 x 16, log-normal
-K (Gaussian covariance, variance 4, correlation length 0.05), viscosity ratio 5,
-eta = 0.1, piecewise-linear interface spaces on 4-edge segments, alpha = 1, p = 1 / 0 on
-the left / right, no flow top and bottom; the run continues Algorithm 1 for W + K steps
-after its initial MRCM solve.  Inputs are synthetic and seeded.  The 256^2 working set
-fits in L2, so L2 is flushed (a 256 MB write) between timed steps, outside the timed region.
+Default workload "channel1024": 1024 x 1024 cells, 64 x 64 subdomains of 16 x 16, binary
+permeability with sinusoidal channels (K = 1 in channels of width 8..24 cells covering
+30 % of the cells, 1e-4 elsewhere), viscosity ratio 5, eta = 0.1, piecewise-linear
+interface spaces on 4-edge segments, alpha = 1, p = 1 / 0 on the left / right, no flow
+top and bottom; mixed precision (FP32 downscaling factorisations with FP64 refinement).
+Inputs are synthetic and seeded; L2 is flushed (a 256 MB write) before every timed step,
+outside the timed region.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|fp64] [--impl reference]
+A rebuild step costs many MPM-2P steps, so a short window of K steps says little about the
+workload's real mix.  The reported value is therefore the blended rate over the workload's
+own rebuild mix:
+  t_blend = f t_rebuild + (1 - f) t_mpm,  value = cells x R / t_blend,
+where t_mpm is the mean device time of the MPM-2P steps of the K timed steps, t_rebuild the
+mean of explicitly timed rebuild steps (a context with eta < 0 rebuilds at every step), and
+f the fraction of rebuild steps over the workload's whole trajectory (its `steps`), which
+this run executes and counts.  The K-window rate itself is reported as window_value.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--prec P]
+                  [--impl reference]
 """
 from __future__ import annotations
 
@@ -31,22 +41,60 @@ sys.path.insert(0, ROOT)
 
 from paper_2103_11050_gb300 import fields  # noqa: E402
 
-WORKLOAD = "gaussian256"
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_downscale_w launch (ncu capture of
-# this code, see profiles/); None when the kernel changed since the capture.
-TRAFFIC_DOWNSCALE_SOLVE = 8.717824e6
 METRIC = "fine-cell pressure updates/s (MRCM & MPM-2P) at <=1e-8 rel flux err vs FP64"
 UNIT = "cell-updates/s"
 E2E_PASSES = 3
 CFL = 0.5
 N_SUB = 1
+FORCED_REBUILDS = 3
+# dram__bytes_read.sum + dram__bytes_write.sum of the upward interface sweep of one step
+# (all its launches) from an ncu capture of this code on the default workload; None when
+# the kernels changed since the capture.
+TRAFFIC_IFACE_UP = None
+PREC = {"fp32": "FP32 downscaling factorisations + FP64 refinement; FP64 Robin factors, interface, fluxes, "
+                "transport",
+        "fp32all": "FP32 local factorisations + FP64 refinement; FP64 interface, fluxes, transport",
+        "fp64": "FP64 throughout"}
+DTYPE = {"fp32": "f32+f64ir", "fp32all": "f32+f64ir", "fp64": "f64"}
 
 
-def workload_desc(w):
-    return (f"{w['nx']}x{w['ny']} cells, {w['ncx']}x{w['ncy']} subdomains of {w['nx'] // w['ncx']}x"
-            f"{w['ny'] // w['ncy']}, log-normal K ({w['cov']} covariance, variance {w['sigma2']}, "
-            f"correlation length {w['ell']}), M={w['M']}, eta={w['eta']}, P1 interface spaces on 4-edge "
-            f"segments, alpha=1, C_n={N_SUB}, CFL={CFL}")
+class Workload:
+    """Inputs and run parameters of one benchmark workload (all realisations)."""
+
+    def __init__(self, name):
+        self.name = name
+        if name == "ensemble":
+            Ks, s0, cw, rh, w = fields.make_ensemble()
+            self.R = Ks.shape[0]
+            self.K = Ks
+            self.s0 = np.ascontiguousarray(np.broadcast_to(s0, Ks.shape))
+            self.col_w, self.row_h = cw, rh
+            self.desc = (f"ensemble: {self.R} realisations of {w['nx']}x{w['ny']}, log-normal K (exponential "
+                         f"covariance, variance {w['sigma2']}, correlation length uniform in {w['ell_range']}), "
+                         f"uneven decomposition (column widths {cw}, row heights {rh}), M={w['M']}, "
+                         f"eta={w['eta']}")
+        else:
+            K, s0, w = fields.make_workload(name)
+            self.R = 1
+            self.K = np.ascontiguousarray(K[None])
+            self.s0 = np.ascontiguousarray(s0[None])
+            a, b = w["nx"] // w["ncx"], w["ny"] // w["ncy"]
+            self.col_w, self.row_h = [a] * w["ncx"], [b] * w["ncy"]
+            kind = w.get("field", "grf")
+            if kind == "grf":
+                fdesc = (f"log-normal K ({w['cov']} covariance, variance {w['sigma2']}, correlation length "
+                         f"{w['ell']})")
+            elif kind == "channelised":
+                fdesc = (f"channelised binary K ({w['k_channel']} in sinusoidal channels of width {w['widths'][0]}-"
+                         f"{w['widths'][1]} cells covering {w['coverage']:.0%}, {w['k_matrix']} elsewhere)")
+            else:
+                fdesc = "homogeneous K = 1, fingering initial saturation"
+            self.desc = (f"{name}: {w['nx']}x{w['ny']} cells, {w['ncx']}x{w['ncy']} subdomains of {a}x{b}, {fdesc}, "
+                         f"M={w['M']}, eta={w['eta']}")
+        self.desc += f", P1 interface spaces on 4-edge segments, alpha=1, C_n={N_SUB}, CFL={CFL}"
+        self.nx, self.ny = w["nx"], w["ny"]
+        self.M, self.eta, self.steps = w["M"], w["eta"], w["steps"]
+        self.cells = self.R * self.nx * self.ny
 
 
 def peaks():
@@ -110,72 +158,77 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_inputs(w, R=1):
-    K, s0, _ = fields.make_workload(WORKLOAD)
-    return np.ascontiguousarray(np.broadcast_to(K, (R, w["ny"], w["nx"]))), np.ascontiguousarray(
-        np.broadcast_to(s0, (R, w["ny"], w["nx"])))
-
-
-def setup_ctx(B, w, K, s0, prec, stream, R=1):
-    ctx = B.Context(R, w["nx"], w["ny"], 1.0, 1.0, stream=stream)
+def setup_ctx(B, wl, prec, stream):
+    ctx = B.Context(wl.R, wl.nx, wl.ny, 1.0, wl.ny / wl.nx, stream=stream)
     mode = {"fp32": B.PREC_FP32_IR, "fp32all": B.PREC_FP32_IR_ALL, "fp64": B.PREC_FP64}[prec]
     ctx.set_precision(mode, 1e-14, 30)
-    ctx.set_fluids(w["M"])
+    ctx.set_fluids(wl.M)
     ctx.set_boundary((0, 0, 1, 1), (1.0, 0.0, 0.0, 0.0), 1.0)
-    sd = w["nx"] // w["ncx"]
-    ctx.set_decomposition([sd] * w["ncx"], [w["ny"] // w["ncy"]] * w["ncy"], 4, 1, 1.0)
-    ctx.set_permeability(K)
-    ctx.set_saturation(s0)
+    ctx.set_decomposition(wl.col_w, wl.row_h, 4, 1, 1.0)
+    ctx.set_permeability(wl.K)
+    ctx.set_saturation(wl.s0)
     return ctx
 
 
-def algorithmic_downscale_solve(w):
-    """Algorithmic work of one launch of the downscaling solve (all subdomains).
-
-    Per a x b subdomain: one block-tridiagonal solve with explicit inverse pivots, 2b dense
-    a x a matrix-vector products (4 b a^2 flop); one flux-form residual of the refinement
-    check (14 flop per cell); the interior fine fluxes (2 faces x 2 flop per cell).  Bytes:
-    the stored factor is read once (b a^2 float32), kappa-dependent stencil (32 B/cell), q
-    (8 B/cell), the previous solution read and the new one written (16 B/cell), writes p~ and
-    the interior fluxes (24 B/cell)."""
-    a = w["nx"] // w["ncx"]
-    b = w["ny"] // w["ncy"]
-    nsub = w["ncx"] * w["ncy"]
-    m = a * b
-    flops = nsub * (4.0 * b * a * a + 14.0 * m + 4.0 * m)
-    byts = nsub * (4.0 * b * a * a + 80.0 * m)
-    return flops, byts
+def iface_up_bytes(ctx_stats_nodes):
+    """Algorithmic bytes of one upward interface sweep: every internal node reads its separator
+    rows of the transposed frontal matrix once (nsep x nf float64), plus its gathered right-hand
+    side and its output (2 nf float64)."""
+    return sum(8.0 * ns * nf + 16.0 * nf for ns, nf in ctx_stats_nodes if ns > 0)
 
 
-def run_gpu(args, w):
+def nd_sizes(col_w, row_h, seg_len=4, degree=1):
+    """(nsep, nf) of every nested-dissection node of the interface system, with the bisection
+    the library uses (the longer side of each rectangle of subdomains is split in half)."""
+    ncx, ncy = len(col_w), len(row_h)
+    nb = degree + 1
+    vdofs = [2 * (row_h[J] // seg_len) * nb for J in range(ncy)]
+    hdofs = [2 * (col_w[I] // seg_len) * nb for I in range(ncx)]
+    out = []
+
+    def rec(I0, I1, J0, J1):
+        if I1 - I0 == 1 and J1 - J0 == 1:
+            return
+        if I1 - I0 >= J1 - J0:
+            Im = (I0 + I1) // 2
+            rec(I0, Im, J0, J1)
+            rec(Im, I1, J0, J1)
+            nsep = sum(vdofs[J] for J in range(J0, J1))
+        else:
+            Jm = (J0 + J1) // 2
+            rec(I0, I1, J0, Jm)
+            rec(I0, I1, Jm, J1)
+            nsep = sum(hdofs[I] for I in range(I0, I1))
+        bnd = 0
+        for J in range(J0, J1):
+            bnd += vdofs[J] * ((I0 > 0) + (I1 < ncx))
+        for I in range(I0, I1):
+            bnd += hdofs[I] * ((J0 > 0) + (J1 < ncy))
+        out.append((nsep, nsep + bnd))
+
+    rec(0, ncx, 0, ncy)
+    return out
+
+
+def run_gpu(args, wl):
     import torch
 
     from paper_2103_11050_gb300 import binding as B
     from paper_2103_11050_gb300 import build as Bd
 
     Bd.build()
-    torch.cuda.set_device(0)
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     stream = torch.cuda.Stream()
-    cells = w["nx"] * w["ny"]
-    K, s0 = make_inputs(w)
-    eta = w["eta"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    cells = wl.cells
 
-    def one_run(prec, steps, warmup, profile):
-        ctx = setup_ctx(B, w, K, s0, prec, stream.cuda_stream)
-        ctx.set_execution(graph=not profile)  # the stage profiler times the eager launch sequence
-        ctx.init(eta)
-        for _ in range(warmup):
-            ctx.step(eta, CFL, N_SUB)
-        ctx.sync()
-        if profile:
-            ctx.profile_read()
-            ctx.profile_enable(True)
-        launches0 = ctx.get_stats()["kernel_launches"]
-        st0 = ctx.get_stats()
+    def timed_steps(ctx, n, eta, flags=None):
+        """n steps, each bracketed by CUDA events on the launching stream after an L2 flush;
+        with flags (a list), whether any realisation rebuilt in each step is appended."""
         evs = []
+        last = ctx.get_stats()["rebuilds"] if flags is not None else 0
         with torch.cuda.stream(stream):
-            for _ in range(steps):
+            for _ in range(n):
                 flush.fill_(1.0)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
@@ -183,141 +236,237 @@ def run_gpu(args, w):
                 ctx.step(eta, CFL, N_SUB)
                 e1.record(stream)
                 evs.append((e0, e1))
+                if flags is not None:  # a host read between steps, outside the timed region
+                    now = ctx.get_stats()["rebuilds"]
+                    flags.append(now != last)
+                    last = now
         torch.cuda.synchronize()
-        per = [a.elapsed_time(b) for a, b in evs]
-        ms = sum(per)
-        prof = ctx.profile_read() if profile else None
+        return [a.elapsed_time(b) for a, b in evs]
+
+    def trajectory(prec, profile=False):
+        """init, W warm-up steps, the K timed steps, then the rest of the workload's trajectory."""
+        ctx = setup_ctx(B, wl, prec, stream.cuda_stream)
+        ctx.set_execution(graph=not profile)  # the stage profiler times the eager launch sequence
+        ctx.init(wl.eta)
+        for _ in range(args.warmup):
+            ctx.step(wl.eta, CFL, N_SUB)
+        ctx.sync()
+        if profile:
+            ctx.profile_read()
+            ctx.profile_enable(True)
+        st0 = ctx.get_stats()
+        flags = []
+        per = timed_steps(ctx, args.steps, wl.eta, flags)
         st1 = ctx.get_stats()
-        res = dict(ms=ms, per=per, launches=st1["kernel_launches"] - launches0,
-                   rebuilds=st1["rebuilds"] - st0["rebuilds"], mpm=st1["mpm_updates"] - st0["mpm_updates"], prof=prof,
-                   ir=st1["ir_iters_max"])
+        prof = ctx.profile_read() if profile else None
         ux, uy = ctx.get_flux()
+        res = dict(per=per, flags=flags, launches=st1["kernel_launches"] - st0["kernel_launches"],
+                   rebuild_steps=sum(flags), ir=st1["ir_iters_max"], prof=prof, ux=ux, uy=uy)
+        if not profile:
+            rest = max(0, wl.steps - args.warmup - args.steps) if not args.no_trajectory else 0
+            if rest:
+                timed_steps(ctx, rest, wl.eta)
+            st2 = ctx.get_stats()
+            res["traj_steps"] = args.warmup + args.steps + rest
+            res["traj_rebuilds"] = st2["rebuilds"] - wl.R  # realisation rebuilds, the initial build excluded
         ctx.close()
-        return res, ux
+        return res
+
+    def forced(prec, eta, n, profile=False):
+        """Steps of one kind timed explicitly: eta < 0 makes every step after the first a rebuild,
+        eta = 1e300 makes every step an MPM-2P update."""
+        ctx = setup_ctx(B, wl, prec, stream.cuda_stream)
+        ctx.set_execution(graph=not profile)
+        ctx.init(eta)
+        for _ in range(3):
+            ctx.step(eta, CFL, N_SUB)
+        ctx.sync()
+        if profile:
+            ctx.profile_read()
+            ctx.profile_enable(True)
+        per = timed_steps(ctx, n, eta)
+        prof = ctx.profile_read() if profile else None
+        ctx.close()
+        return per, prof
+
+    def blend(prec, main, reb_per):
+        mpm = [t for t, f in zip(main["per"], main["flags"]) if not f]
+        src = "the MPM-2P steps of the timed window"
+        if not mpm:  # every window step rebuilt some realisation: time MPM-2P steps explicitly
+            mpm, _ = forced(prec, 1e300, args.steps)
+            src = "explicitly timed MPM-2P steps (eta = 1e300)"
+        t_mpm = sum(mpm) / len(mpm)
+        t_reb = sum(reb_per) / len(reb_per)
+        f = main["traj_rebuilds"] / max(wl.R * main["traj_steps"], 1)
+        t = f * t_reb + (1.0 - f) * t_mpm
+        return t, dict(mpm_step_ms=t_mpm, mpm_step_ms_median=statistics.median(mpm), mpm_steps_from=src,
+                       rebuild_step_ms=t_reb, rebuild_steps_from=f"{len(reb_per)} explicitly timed rebuild steps",
+                       rebuild_fraction=f, trajectory_steps=main["traj_steps"],
+                       trajectory_rebuilds=main["traj_rebuilds"], mpm_steps_rate=cells / (t_mpm / 1e3),
+                       rebuild_steps_rate=cells / (t_reb / 1e3))
 
     prec = args.prec
+    if args.window_only:
+        args.no_trajectory = True
+        main = trajectory(prec)
+        return {"metric": METRIC, "window_value": cells * args.steps / (sum(main["per"]) / 1e3), "unit": UNIT,
+                "steps": args.steps, "warmup": args.warmup, "timed_steps_rebuild": main["rebuild_steps"],
+                "gpu_launches": main["launches"], "config": {"workload": wl.desc, "precision": PREC[prec]}}
     with ClockSampler(0) as clk:
-        main, ux_main = one_run(prec, args.steps, args.warmup, False)
-    value = cells * args.steps / (main["ms"] / 1e3)
-    # rebuild and MPM-2P steps separately: a rebuild step costs several times an MPM-2P step,
-    # so the timed rebuild steps are the slowest ones
-    per = sorted(main["per"])
-    n_reb = main["rebuilds"]
-    mpm_part = per[:len(per) - n_reb] if n_reb < len(per) else per
-    reb_part = per[len(per) - n_reb:] if n_reb > 0 else []
-    split = {"mpm_step_ms": sum(mpm_part) / len(mpm_part),
-             "mpm_step_ms_median": statistics.median(mpm_part),
-             "rebuild_step_ms": (sum(reb_part) / len(reb_part)) if reb_part else None,
-             "mpm_steps_rate": cells / (sum(mpm_part) / len(mpm_part) / 1e3),
-             "rebuild_steps_rate": (cells / (sum(reb_part) / len(reb_part) / 1e3)) if reb_part else None}
-    # same steps, eager launches with per-stage CUDA events (for the stage split and roofline)
-    prof_run, _ = one_run(prec, args.steps, args.warmup, True)
-    main["prof"] = prof_run["prof"]
-    # the plain FP64 GPU form on the same steps, and the accuracy of the main form against it
+        main = trajectory(prec)
+        reb_per, _ = forced(prec, -1.0, FORCED_REBUILDS)
+        t_blend, step_split = blend(prec, main, reb_per)
+    value = cells / (t_blend / 1e3)
+    window_ms = sum(main["per"])
+    _, prof_main = forced(prec, 1e300, args.steps, profile=True)
+    _, prof_reb = forced(prec, -1.0, FORCED_REBUILDS, profile=True)
+
     other = {}
     if prec != "fp64" and not args.no_fp64:
-        f64, ux64 = one_run("fp64", args.steps, args.warmup, False)
-        f64p, _ = one_run("fp64", args.steps, args.warmup, True)
-        other = {"fp64_form_value": cells * args.steps / (f64["ms"] / 1e3),
-                 "rel_flux_err_vs_fp64": float(np.linalg.norm(ux_main - ux64) / np.linalg.norm(ux64)),
-                 "fp64_form_ms_per_step": f64["ms"] / args.steps,
-                 "fp64_form_stage_ms_per_step_eager": {k: v[0] / args.steps for k, v in f64p["prof"].items()}}
+        f64 = trajectory("fp64")
+        f64_reb, _ = forced("fp64", -1.0, FORCED_REBUILDS)
+        t64, split64 = blend("fp64", f64, f64_reb)
+        num = np.sqrt(np.sum((main["ux"] - f64["ux"]) ** 2) + np.sum((main["uy"] - f64["uy"]) ** 2))
+        den = np.sqrt(np.sum(f64["ux"] ** 2) + np.sum(f64["uy"] ** 2))
+        other = {"fp64_form_value": cells / (t64 / 1e3), "fp64_form_ms_per_step": t64,
+                 "fp64_form_step_split": split64,
+                 "rel_flux_err_vs_fp64": float(num / den),
+                 "rel_flux_err_vs_fp64_at": f"after init + {args.warmup + args.steps} steps (ux and uy together)"}
 
-    # end to end through the C ABI with host buffers: per step set s (h2d), step, read s (d2h).
-    # Each pass replays the timed steps of the device measurement on a fresh context (same
-    # initial state, same rebuild steps); the host clock of one pass is exposed to one-off
-    # host stalls, so the median of the passes is reported.
-    def e2e_pass():
-        ctx = setup_ctx(B, w, K, s0, prec, stream.cuda_stream)
+    # End to end through the C ABI with host buffers: per step the saturation is copied in from
+    # pinned host memory, the step runs, and the saturation is read back.  MPM-2P steps
+    # (eta = 1e300) and rebuild steps (eta < 0) are timed on fresh contexts and blended like
+    # the device value; the median of E2E_PASSES passes of each is reported.
+    def e2e_pass(eta, nsteps):
+        ctx = setup_ctx(B, wl, prec, stream.cuda_stream)
         ctx.init(eta)
         for _ in range(args.warmup):
             ctx.step(eta, CFL, N_SUB)
-        s_host = torch.empty((1, w["ny"], w["nx"]), dtype=torch.float64).pin_memory().numpy()
+        s_host = torch.empty((wl.R, wl.ny, wl.nx), dtype=torch.float64).pin_memory().numpy()
         ctx.get_saturation(s_host)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(nsteps):
             ctx.set_saturation(s_host)
             ctx.step(eta, CFL, N_SUB)
             ctx.get_saturation(s_host)
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
         ctx.close()
-        return t
+        return t * 1e3 / nsteps
 
-    e2e_passes = [e2e_pass() for _ in range(E2E_PASSES)]
-    e2e_s = statistics.median(e2e_passes)
+    e2e_mpm = [e2e_pass(1e300, args.steps) for _ in range(E2E_PASSES)]
+    e2e_reb = [e2e_pass(-1.0, FORCED_REBUILDS) for _ in range(E2E_PASSES)]
+    f = step_split["rebuild_fraction"]
+    e2e_ms = f * statistics.median(e2e_reb) + (1.0 - f) * statistics.median(e2e_mpm)
 
+    # roofline of the upward interface sweep (the kernels k_nd_up, one per nested-dissection
+    # level): algorithmic bytes per step over its measured device time per step
     pk, pk_kind = peaks()
-    prof = main["prof"]
-    ds_ms, ds_n = prof["downscale"]
-    dom = max(prof, key=lambda k: prof[k][0])
-    flops, _bytes = algorithmic_downscale_solve(w)
-    ds_avg_s = ds_ms / 1e3 / max(ds_n, 1)
-    sm_clock = 2070.0
-    fp64_peak = 152 * 2 * 2 * sm_clock * 1e6 / 1e12  # TFLOP/s
-    roof = {"kernel": "k_downscale_w", "bound": "alu", "achieved": flops / ds_avg_s / 1e12,
-            "peak": fp64_peak, "unit": "TFLOP/s", "frac": (flops / ds_avg_s / 1e12) / fp64_peak,
-            "traffic": TRAFFIC_DOWNSCALE_SOLVE,
-            "peak_kind": "derived: float64 pipe, 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (fallback table's "
-                         "nominal 1.25 TFLOP/s; not in MEASURED_PEAKS.json)",
-            "avg_launch_us": ds_avg_s * 1e6,
-            "dominant_stage": dom,
-            "stage_ms_per_step_eager": {k: v[0] / args.steps for k, v in prof.items()},
-            "eager_ms_per_step": prof_run["ms"] / args.steps}
+    nsteps_prof = args.steps
+    stage = {k: v[0] / max(nsteps_prof, 1) for k, v in prof_main.items()}
+    reb_stage = {k: v[0] / FORCED_REBUILDS for k, v in prof_reb.items()}
+    up_bytes = iface_up_bytes(nd_sizes(wl.col_w, wl.row_h)) * wl.R
+    up_ms = stage.get("iface_up", 0.0)
+    achieved = up_bytes / (up_ms / 1e3) / 1e9 if up_ms > 0 else 0.0
+    roof = {"kernel": "k_nd_up (all levels of one upward interface sweep)", "bound": "hbm",
+            "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+            "traffic": TRAFFIC_IFACE_UP,
+            "algorithmic_bytes_per_step": up_bytes, "ms_per_step": up_ms,
+            "peak_kind": f"{pk_kind} HBM copy bandwidth",
+            "dominant_stage": max(stage, key=lambda k: stage[k] if k != "iface_solve" else -1),
+            "stage_ms_per_mpm_step_eager": stage, "stage_ms_per_rebuild_step_eager": reb_stage}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": main["ms"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64ir" if prec != "fp64" else "f64", "data": "synthetic (seeded log-normal field)",
-        "config": {"workload": f"{WORKLOAD}: {workload_desc(w)}", "realisations": 1,
-                   "timed_steps_rebuild": main["rebuilds"], "timed_steps_mpm": main["mpm"],
-                   "l2": "flushed between timed steps (256 MB write outside the timed region)",
-                   "precision": {"fp32": "FP32 downscaling factorisations + FP64 refinement; FP64 Robin factors, "
-                                          "interface, fluxes, transport",
-                                 "fp32all": "FP32 local factorisations + FP64 refinement; FP64 interface, fluxes, "
-                                            "transport",
-                                 "fp64": "FP64 throughout"}[prec]},
+        "ms_per_step": t_blend, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[prec], "data": "synthetic (seeded permeability field)",
+        "config": {"workload": wl.desc, "realisations": wl.R,
+                   "value": "blended over the workload's rebuild mix: cells / (f t_rebuild + (1-f) t_mpm)",
+                   "timed_steps_rebuild": main["rebuild_steps"], "timed_steps_mpm": args.steps - main["rebuild_steps"],
+                   "l2": "flushed before every timed step (256 MB write outside the timed region)",
+                   "precision": PREC[prec]},
+        "window_value": cells * args.steps / (window_ms / 1e3),
         "gpu_launches": main["launches"],
-        "e2e": {"value": cells * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * cells,
-                "d2h_bytes_per_step": 8 * cells, "passes": [cells * args.steps / t for t in e2e_passes],
-                "reported": f"median of {E2E_PASSES} passes, each the timed steps on a fresh context"},
+        "e2e": {"value": cells / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": 8 * cells,
+                "d2h_bytes_per_step": 8 * cells,
+                "reported": f"blended like value; median of {E2E_PASSES} passes of {args.steps} MPM-2P steps and of "
+                            f"{FORCED_REBUILDS} rebuild steps, each pass on a fresh context",
+                "mpm_step_ms": statistics.median(e2e_mpm), "rebuild_step_ms": statistics.median(e2e_reb)},
         "roofline": roof,
         "clocks": clk.summary(),
         "peaks_source": pk_kind,
         "ir_sweeps_max": main["ir"],
-        "step_split": split,
+        "step_split": step_split,
     }
     line.update(other)
     if not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_budget, gpu_check=(B, stream))
     return line
 
 
-def cpu_baseline(w, budget_s=20.0, max_steps=None):
-    """The oracle, as it stands, timed on this host's cores on a bounded prefix of the
-    workload (its initial MRCM solve is untimed; the timed steps are Algorithm 1 steps)."""
+def oracle_sample(wl):
+    """The bounded sample the oracle runs: the workload itself when its grid is at most 256^2
+    per realisation (first realisation), else its 256 x 256 lower-left window with the same
+    subdomain size, boundary conditions and fluids (the oracle's cost per cell is about
+    constant, so the rate of the window stands for the whole grid)."""
+    n = 256
+    if wl.nx <= n and wl.ny <= n:
+        return wl.K[0], wl.s0[0], wl.col_w, wl.row_h, "the workload's first realisation"
+    a, b = wl.col_w[0], wl.row_h[0]
+    K = np.ascontiguousarray(wl.K[0, :n, :n])
+    s0 = np.ascontiguousarray(wl.s0[0, :n, :n])
+    return K, s0, [a] * (n // a), [b] * (n // b), f"the lower-left {n}x{n} window of the workload"
+
+
+def cpu_baseline(wl, budget_s=20.0, max_steps=None, gpu_check=None):
+    """The oracle, as it stands, timed on this host's cores on a bounded sample of the
+    workload (its initial MRCM solve is untimed; the timed steps are Algorithm 1 steps).
+    With gpu_check, the GPU path runs the same sample for the same steps and its relative
+    flux error against the oracle is reported."""
     from oracle import mpm_oracle as O
     try:
         from threadpoolctl import threadpool_info
         cores = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
     except Exception:
         cores = os.cpu_count() or 1
-    K, s0 = make_inputs(w)
-    nx, ny = w["nx"], w["ny"]
-    prob = O.Problem(nx, ny, 1.0 / nx, (0, 0, 1, 1), (1.0, 0.0, 0.0, 0.0), w["M"], 1.0)
-    dec = O.uniform_decomposition(nx, ny, w["ncx"], w["ncy"], seg_len=4, degree=1)
-    st = O.simulate_init(K[0], s0[0], prob, dec, w["eta"])
+    K, s0, cw, rh, what = oracle_sample(wl)
+    ny, nx = K.shape
+    prob = O.Problem(nx, ny, 1.0 / nx, (0, 0, 1, 1), (1.0, 0.0, 0.0, 0.0), wl.M, 1.0)
+    dec = O.Decomposition(nx, ny, cw, rh, seg_len=4, degree=1)
+    st = O.simulate_init(K, s0, prob, dec, wl.eta)
     n = 0
     t0 = time.perf_counter()
     reb = 0
     while time.perf_counter() - t0 < budget_s and (max_steps is None or n < max_steps):
-        O.simulate_step(st, K[0], prob, dec, w["eta"], CFL, N_SUB)
+        O.simulate_step(st, K, prob, dec, wl.eta, CFL, N_SUB)
         reb += st.history[-1]["rebuild"]
         n += 1
     dt = time.perf_counter() - t0
-    return {"value": nx * ny * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {n} Algorithm 1 steps ({reb} rebuilds) of {WORKLOAD} after its initial MRCM solve, "
-                      f"{dt:.1f} s of CPU time"}
+    out = {"value": nx * ny * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{what}: {n} Algorithm 1 steps ({reb} rebuilds) after its initial MRCM solve, "
+                     f"{dt:.1f} s of CPU time"}
+    if gpu_check is not None:
+        B, stream = gpu_check
+        errs = {}
+        for prec in ("fp32", "fp64"):
+            ctx = B.Context(1, nx, ny, 1.0, ny / nx, stream=stream.cuda_stream)
+            ctx.set_precision({"fp32": B.PREC_FP32_IR, "fp64": B.PREC_FP64}[prec], 1e-14, 30)
+            ctx.set_fluids(wl.M)
+            ctx.set_boundary((0, 0, 1, 1), (1.0, 0.0, 0.0, 0.0), 1.0)
+            ctx.set_decomposition(cw, rh, 4, 1, 1.0)
+            ctx.set_permeability(np.ascontiguousarray(K[None]))
+            ctx.set_saturation(np.ascontiguousarray(s0[None]))
+            ctx.init(wl.eta)
+            for _ in range(n):
+                ctx.step(wl.eta, CFL, N_SUB)
+            ux, uy = ctx.get_flux()
+            ctx.close()
+            num = np.sqrt(np.sum((ux[0] - st.step.Fx) ** 2) + np.sum((uy[0] - st.step.Fy) ** 2))
+            den = np.sqrt(np.sum(st.step.Fx ** 2) + np.sum(st.step.Fy ** 2))
+            errs[prec] = float(num / den)
+        out["gpu_rel_flux_err_vs_oracle"] = {"mixed_fp32_ir": errs["fp32"], "fp64": errs["fp64"],
+                                             "at": f"{what}, after init + {n} steps"}
+    return out
 
 
 def combine_ranks(ms_per_step, cells_per_rank, device):
@@ -333,17 +482,16 @@ def combine_ranks(ms_per_step, cells_per_rank, device):
     return ms, world * cells_per_rank / (ms / 1e3)
 
 
-def run_reference(args, w):
+def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
-    budget = 150.0
-    cb = cpu_baseline(w, budget_s=budget, max_steps=args.steps + args.warmup)
+    cb = cpu_baseline(wl, budget_s=150.0, max_steps=args.steps + args.warmup)
     return {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": w["nx"] * w["ny"] / cb["value"] * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wl.cells / cb["value"] * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded log-normal field)",
-            "config": {"workload": f"{WORKLOAD}: {workload_desc(w)}", "realisations": 1},
+            "data": "synthetic (seeded permeability field)",
+            "config": {"workload": wl.desc, "realisations": wl.R},
             "cpu_baseline": {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
                              "sample": cb["sample"]},
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -355,18 +503,25 @@ def main():
     ap.add_argument("--steps", type=int, default=197)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="channel1024",
+                    choices=["channel1024", "gaussian256", "finger512", "gaussian64", "ensemble"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp32all", "fp64"],
                     help="fp32: FP32 downscaling factors + FP64 refinement, FP64 Robin factors; "
                          "fp32all: every local factor FP32 + FP64 refinement; fp64: all FP64")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-trajectory", action="store_true",
+                    help="do not run the workload's trajectory past the timed window (rebuild mix of the window)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--window-only", action="store_true",
+                    help="run only init, the warm-up and the timed window (graph mode) and print its rate: the "
+                         "command profiled for the kernel launch list")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    w = fields.WORKLOADS[WORKLOAD]
+    wl = Workload(args.workload)
     if args.impl == "reference":
-        line = run_reference(args, w)
+        line = run_reference(args, wl)
         if line is not None:
             print(json.dumps(line), flush=True)
         return
@@ -379,14 +534,14 @@ def main():
         local = int(os.environ.get("LOCAL_RANK", "0"))
         torch.cuda.set_device(local)
         args.no_cpu = args.no_cpu or dist.get_rank() != 0
-        line = run_gpu(args, w)
-        line["ms_per_step"], line["value"] = combine_ranks(line["ms_per_step"], w["nx"] * w["ny"], "cuda")
+        line = run_gpu(args, wl)
+        line["ms_per_step"], line["value"] = combine_ranks(line["ms_per_step"], wl.cells, "cuda")
         line["n_gpus"] = world
         if dist.get_rank() == 0:
             print(json.dumps(line), flush=True)
         dist.destroy_process_group()
         return
-    print(json.dumps(run_gpu(args, w)), flush=True)
+    print(json.dumps(run_gpu(args, wl)), flush=True)
 
 
 if __name__ == "__main__":

@@ -54,8 +54,7 @@ enum {
   MPM_ERR_OOM = 3,            /* device allocation failed */
   MPM_ERR_NOT_CONVERGED = 4,  /* iterative refinement hit its iteration cap */
   MPM_ERR_STATE = 5,          /* call out of order (e.g. solve before build) */
-  MPM_ERR_TOO_LARGE = 6,      /* request exceeds a fixed capacity (mpm_cfl_dt_noalloc) */
-  MPM_ERR_TIMEOUT = 7         /* a bounded device-side dependency wait gave up (results invalid) */
+  MPM_ERR_TOO_LARGE = 6       /* request exceeds a fixed capacity (mpm_cfl_dt_noalloc) */
 };
 
 enum { MPM_MEM_HOST = 0, MPM_MEM_DEVICE = 1 };
@@ -105,7 +104,10 @@ enum {
   MPM_STAGE_PERTURB = 4,       /* MPM-2P residual, local solve, interface RHS        */
   MPM_STAGE_IFACE_SOLVE = 5,   /* interface sweeps and traces                        */
   MPM_STAGE_DOWNSCALE = 6,     /* u_bar, Neumann downscaling, CFL maxima (one kernel) */
-  MPM_NSTAGES = 7
+  MPM_STAGE_IFACE_UP = 7,      /* parts of MPM_STAGE_IFACE_SOLVE: upward sweep ...    */
+  MPM_STAGE_IFACE_DOWN = 8,    /* ... downward sweep ...                              */
+  MPM_STAGE_RECONSTRUCT = 9,   /* ... traces and targets (with the level-1 step)      */
+  MPM_NSTAGES = 10
 };
 
 /* Create a context for R realisations of an nx x ny grid on [0,Lx]x[0,Ly].
@@ -149,7 +151,7 @@ int mpm_set_fluids(mpm_ctx* ctx, double M);
 int mpm_set_boundary(mpm_ctx* ctx, const int type[4], const double val[4], double s_inflow);
 
 /* Tensor-product decomposition (Section 3): ncx column widths col_w (cells, summing to
- * nx) and ncy row heights row_h (summing to ny); every width and height <= 32 and a
+ * nx) and ncy row heights row_h (summing to ny); every width and height <= 24 and a
  * multiple of seg_len; degree 0 or 1 (Section 3.1); alpha > 0 is the constant of
  * Eq. (beta) (beta = alpha H / kappa, H = length of the interface carrying the face).
  * (Re)allocates every per-subdomain device buffer; invalidates the stored basis. */
@@ -233,24 +235,9 @@ int mpm_step(mpm_ctx* ctx, double eta, double cfl, int n_sub);
  *                       its predecessor runs and loads its operators (factor rows, index maps)
  *                       or, for the downscaling, factors its Neumann problems before waiting
  *                       for the predecessor's results.
- *  MPM_EXEC_DATAFLOW    the interface sweeps (all nested-dissection levels above the first) are
- *                       one cooperative launch whose blocks take work items (node, row block)
- *                       in topological order and wait, with bounded polling, on per-node
- *                       completion counters instead of kernel boundaries; without it, one
- *                       kernel per level.  A wait that gives up makes the next synchronising
- *                       call return MPM_ERR_TIMEOUT.  Ignored with MPM_EXEC_PERSISTENT.
- *                       Measured slower than the per-level kernels with programmatic launch
- *                       on the 256^2 workload (202 vs 190 us per step), so it is off by
- *                       default.
- *  MPM_EXEC_PERSISTENT  the interface sweeps (every nested-dissection level up and down,
- *                       reconstruction) are one persistent cooperative kernel with
- *                       grid-wide barriers between levels; without it, one kernel per level
- *                       (also the automatic fallback when the device cannot launch
- *                       cooperatively).  Measured slower than the per-level kernels on the
- *                       256^2 workload (the grid-wide barriers cost more than the launches
- *                       they replace), so it is off by default.
- * Results are identical up to rounding order.  Drops a captured graph. */
-enum { MPM_EXEC_GRAPH = 1, MPM_EXEC_PERSISTENT = 2, MPM_EXEC_PDL = 4, MPM_EXEC_DATAFLOW = 8 };
+ * Results are identical up to rounding order.  Any other bit is MPM_ERR_ARG.  Drops a
+ * captured graph. */
+enum { MPM_EXEC_GRAPH = 1, MPM_EXEC_PDL = 4 };
 int mpm_set_execution(mpm_ctx* ctx, int flags);
 
 /* Copy out pressure [R][ny][nx] (which = MPM_P_*), fluxes ux [R][ny][nx+1],

@@ -14,13 +14,13 @@ import numpy as np
 
 from . import build as _build
 
-(MPM_OK, MPM_ERR_ARG, MPM_ERR_CUDA, MPM_ERR_OOM, MPM_ERR_NOT_CONVERGED, MPM_ERR_STATE, MPM_ERR_TOO_LARGE,
- MPM_ERR_TIMEOUT) = range(8)
+(MPM_OK, MPM_ERR_ARG, MPM_ERR_CUDA, MPM_ERR_OOM, MPM_ERR_NOT_CONVERGED, MPM_ERR_STATE,
+ MPM_ERR_TOO_LARGE) = range(7)
 MEM_HOST, MEM_DEVICE = 0, 1
 BC_DIRICHLET, BC_NEUMANN = 0, 1
 PREC_FP64, PREC_FP32_IR, PREC_FP32_IR_ALL = 0, 1, 2
 P_MRCM, P_DOWNSCALED = 0, 1
-EXEC_GRAPH, EXEC_PERSISTENT, EXEC_PDL, EXEC_DATAFLOW = 1, 2, 4, 8
+EXEC_GRAPH, EXEC_PDL = 1, 4
 
 FUNCTIONS = [
     "mpm_create", "mpm_destroy", "mpm_last_error", "mpm_set_precision", "mpm_set_permeability",
@@ -32,7 +32,8 @@ FUNCTIONS = [
     "mpm_set_execution", "mpm_cfl_dt_noalloc",
 ]
 
-STAGES = ["transport", "epsilon", "basis", "iface_factor", "perturb", "iface_solve", "downscale"]
+STAGES = ["transport", "epsilon", "basis", "iface_factor", "perturb", "iface_solve", "downscale", "iface_up",
+          "iface_down", "reconstruct"]
 
 
 class MPMError(RuntimeError):
@@ -106,13 +107,40 @@ def load(path: str | None = None):
     return L
 
 
+def _stream_handle(stream):
+    """cudaStream_t of a torch.cuda.Stream, a raw handle (int) or None (legacy default stream)."""
+    if stream is None:
+        return 0
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
 def cfl_dt_noalloc(ux, uy, dt, h, M, cfl, stream=None):
-    """mpm_cfl_dt_noalloc on torch CUDA tensors ux [R][ny][nx+1], uy [R][ny+1][nx], dt [R]."""
-    L = load()
+    """mpm_cfl_dt_noalloc on torch CUDA tensors ux [R][ny][nx+1], uy [R][ny+1][nx], dt [R].
+
+    The kernels address the three buffers directly, so every property they rely on is
+    checked here first: float64, contiguous, on the current CUDA device, and shapes that
+    agree (uy is [R][ny+1][nx] for the R, ny, nx of ux; dt holds at least R values)."""
+    import torch
+    for name, t in (("ux", ux), ("uy", uy), ("dt", dt)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float64 tensor")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} is on cuda:{t.device.index}, not on the current device")
+    if ux.dim() != 3:
+        raise ValueError("ux must be [R][ny][nx+1]")
     R, ny, nx1 = ux.shape
+    if tuple(uy.shape) != (R, ny + 1, nx1 - 1):
+        raise ValueError(f"uy must be [R][ny+1][nx] = {(R, ny + 1, nx1 - 1)}, got {tuple(uy.shape)}")
+    if dt.numel() < R:
+        raise ValueError(f"dt must hold at least R = {R} values")
+    L = load()
     rc = L.mpm_cfl_dt_noalloc(ctypes.c_void_p(ux.data_ptr()), ctypes.c_void_p(uy.data_ptr()), int(R), int(nx1 - 1),
                               int(ny), float(h), float(M), float(cfl), ctypes.c_void_p(dt.data_ptr()),
-                              ctypes.c_void_p(0 if stream is None else int(stream)))
+                              ctypes.c_void_p(_stream_handle(stream)))
     if rc != MPM_OK:
         raise MPMError(rc, "mpm_cfl_dt_noalloc failed")
 
@@ -269,9 +297,8 @@ class Context:
     def get_conductivity(self, out=None):
         return self._get(self.L.mpm_get_conductivity, (self.R, self.ny, self.nx), out)
 
-    def set_execution(self, graph=True, persistent=False, pdl=True, dataflow=False):
-        flags = (EXEC_GRAPH if graph else 0) | (EXEC_PERSISTENT if persistent else 0) | (EXEC_PDL if pdl else 0)
-        flags |= EXEC_DATAFLOW if dataflow else 0
+    def set_execution(self, graph=True, pdl=True):
+        flags = (EXEC_GRAPH if graph else 0) | (EXEC_PDL if pdl else 0)
         self._ck(self.L.mpm_set_execution(self.h, flags))
 
     def profile_enable(self, on=True):

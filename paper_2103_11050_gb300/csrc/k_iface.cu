@@ -23,8 +23,6 @@
 // side exists), so the sweep needs no pivoting.
 // Solve: upward  y_s = F_ss^-1 g_s, g_b += (-F_bs F_ss^-1) g_s  (g_b -> parent);
 //        downward x_s = y_s - (F_ss^-1 F_sb) x_b  (x_b from the parent).
-#include <cooperative_groups.h>
-
 #include <algorithm>
 
 #include "k_iface_phases.cuh"
@@ -358,145 +356,6 @@ __global__ void __launch_bounds__(256) k_nd_down(Grid g, DevState d, const DevNo
   }
 }
 
-// The interface sweeps as one cooperative launch driven by per-node completion counters
-// instead of one kernel per level: work item = (phase, node, row block), same arithmetic as
-// k_nd_up / k_nd_down.  Items are listed in topological order (upward items by increasing
-// level, then downward items by decreasing level, each for every realisation) and CTA b takes
-// items b, b + gridDim.x, ... in order.  Before an item the CTA loads its operator rows and
-// index maps, then its thread 0 polls the counters of the items it depends on (children's
-// upward items; for a downward item the node's own upward items and the parent's downward
-// items, or the root's upward items) and the CTA proceeds once they are complete.  All CTAs
-// are co-resident (cooperative launch) and take items in increasing order, so the lowest
-// unfinished item can always proceed; every poll loop is bounded (status bit 2 on timeout).
-// Data produced inside the launch is read through L2 (__ldcg).
-constexpr long long kDataflowPolls = 1LL << 22;
-
-__device__ __forceinline__ void wait_counter(const int* cnt, int target, int* status) {
-  const volatile int* v = cnt;
-  long long polls = 0;
-  while (*v < target) {
-    if (++polls > kDataflowPolls) {
-      atomicOr(status, 2);
-      return;
-    }
-    __nanosleep(20);
-  }
-}
-
-__global__ void __launch_bounds__(256) k_nd_dataflow(Grid g, DevState d, const DevNode* nodes, const NdItem* items,
-                                                     int nitems, int nnodes, int* counters, const int* srcmap,
-                                                     const int* pmap) {
-  extern __shared__ __align__(16) double nd_smem[];  // [256] partial sums + gathered vector
-  pdl_trigger();
-  const long long total = (long long)nitems * g.R;
-  for (long long w = blockIdx.x; w < total; w += gridDim.x) {
-    const int it = (int)(w / g.R), r = (int)(w - (long long)it * g.R);
-    const NdItem I = items[it];
-    const DevNode nd = nodes[I.node];
-    const int KS = I.ks, ROWS = 256 / KS;
-    const int i = threadIdx.x % ROWS, q = threadIdx.x / ROWS;
-    const int row = I.row0 + i;
-    const long long vb = (long long)r * d.st_vec;
-    const int nf = nd.nf, ns = nd.nsep, nbd = nd.nbnd;
-    int* cnt = counters + (long long)r * 2 * nnodes;
-    double* part = nd_smem;
-    double* vec = nd_smem + 256;
-    const double* G = d.front + (long long)r * d.st_front + nd.f_off;
-    // operator data of this item, independent of the wait
-    double v[kKpt];
-    int p0 = -1, p1 = -1, own0 = -1, own1 = -1;
-    if (I.phase == 0) {
-#pragma unroll
-      for (int u = 0; u < kKpt; ++u) {
-        const int k = q + u * KS;
-        v[u] = (row < nf && k < ns) ? G[(long long)k * nf + row] : 0.0;
-      }
-      if ((int)threadIdx.x < ns) {
-        p0 = srcmap[nd.src_off + threadIdx.x];
-        p1 = srcmap[nd.src_off + nf + threadIdx.x];
-      }
-      if (q == 0 && row < nf && row >= ns) {
-        own0 = srcmap[nd.src_off + row];
-        own1 = srcmap[nd.src_off + nf + row];
-      }
-    } else {
-      const double* Gb = G + (long long)ns * nf;
-#pragma unroll
-      for (int u = 0; u < kKpt; ++u) {
-        const int k = q + u * KS;
-        v[u] = (row < ns && k < nbd) ? Gb[(long long)k * nf + row] : 0.0;
-      }
-      if ((int)threadIdx.x < nbd) p0 = pmap[nd.pmap_off + threadIdx.x];
-    }
-    if (threadIdx.x == 0) {
-      for (int k = 0; k < 2; ++k)
-        if (I.dep[k] >= 0) wait_counter(cnt + I.dep[k], I.target[k], d.status);
-      __threadfence();
-    }
-    __syncthreads();
-    if (I.phase == 0) {
-      const DevNode& c0 = nodes[nd.child[0]];
-      const DevNode& c1 = nodes[nd.child[1]];
-      const double* g0 = d.gvec + vb + c0.v_off + c0.nsep;
-      const double* g1 = d.gvec + vb + c1.v_off + c1.nsep;
-      for (int k = threadIdx.x; k < ns; k += blockDim.x) {
-        const bool first = k == (int)threadIdx.x;
-        const int a0 = first ? p0 : srcmap[nd.src_off + k], a1 = first ? p1 : srcmap[nd.src_off + nf + k];
-        vec[k] = (a0 >= 0 ? __ldcg(g0 + a0) : 0.0) + (a1 >= 0 ? __ldcg(g1 + a1) : 0.0);
-      }
-      __syncthreads();
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-      for (int u = 0; u < kKpt; ++u) {
-        const int k = q + u * KS;
-        if (k < ns) acc[u & 3] += v[u] * vec[k];
-      }
-      if (row < nf)
-        for (int k = q + kKpt * KS; k < ns; k += KS) acc[0] += G[(long long)k * nf + row] * vec[k];
-      part[q * ROWS + i] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-      __syncthreads();
-      if (q == 0 && row < nf) {
-        double sum = part[i];
-        for (int u = 1; u < KS; ++u) sum += part[u * ROWS + i];
-        if (row < ns) d.xvec[vb + nd.v_off + row] = sum;
-        else
-          d.gvec[vb + nd.v_off + row] =
-              ((own0 >= 0 ? __ldcg(g0 + own0) : 0.0) + (own1 >= 0 ? __ldcg(g1 + own1) : 0.0)) - sum;
-      }
-    } else {
-      const double* xp = d.xvec + vb + nodes[nd.parent].v_off;
-      double* xo = d.xvec + vb + nd.v_off;
-      for (int k = threadIdx.x; k < nbd; k += blockDim.x) {
-        const double x = __ldcg(xp + (k == (int)threadIdx.x ? p0 : pmap[nd.pmap_off + k]));
-        vec[k] = x;
-        if (I.row0 == 0) xo[ns + k] = x;
-      }
-      __syncthreads();
-      const double* Gb = G + (long long)ns * nf;
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-      for (int u = 0; u < kKpt; ++u) {
-        const int k = q + u * KS;
-        if (k < nbd) acc[u & 3] += v[u] * vec[k];
-      }
-      if (row < ns)
-        for (int k = q + kKpt * KS; k < nbd; k += KS) acc[0] += Gb[(long long)k * nf + row] * vec[k];
-      part[q * ROWS + i] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-      __syncthreads();
-      if (q == 0 && row < ns) {
-        double sum = part[i];
-        for (int u = 1; u < KS; ++u) sum += part[u * ROWS + i];
-        xo[row] = __ldcg(xo + row) + sum;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(cnt + (I.phase == 0 ? I.node : nnodes + I.node), 1);
-    }
-  }
-}
-
 // Reconstruction from the interface solution c of one subdomain per CTA: the one-sided
 // traces F = Fbar + F_hat c, then the target mean of the downscaled pressure, and at a
 // rebuild the MRCM-level pressure p^m = pbar + P_hat c:
@@ -641,123 +500,7 @@ __global__ void __launch_bounds__(256) k_reconstruct(Grid g, DevState d, const D
   }
 }
 
-// The whole interface-solve stage in one persistent cooperative launch: the upward sweep
-// level by level, the downward sweep level by level and the reconstruction, with a
-// grid-wide barrier between dependent phases (the leaf right-hand sides come from the
-// local-solve kernels).  Every
-// block reaches every barrier (no early return).  Items are grid-strided; per-level rows
-// are one warp each.
-__global__ void __launch_bounds__(256) k_iface_coop(Grid g, DevState d, const DevSub* subs, int nsub, int max_dof,
-                                                    const DevNode* nodes, const int* leaf_node,
-                                                    const int* level_nodes, const DevLevel* lev, int nlev,
-                                                    const int* srcmap, const int* pmap) {
-  namespace cg = cooperative_groups;
-  cg::grid_group grid = cg::this_grid();
-  __shared__ double cs[4 * 4 * kMaxSide];
-  __shared__ double red[32];
-  const long long nthreads = (long long)gridDim.x * blockDim.x;
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nwarps = nthreads >> 5, wid = tid >> 5;
-  const int lane = threadIdx.x & 31;
-  if (max_dof > 0) {
-    for (int L = 1; L < nlev; ++L) {
-      const DevLevel lv = lev[L];
-      const long long rows = (long long)g.R * lv.cnt * lv.max_nf;
-      for (long long it = wid; it < rows; it += nwarps) {
-        const int row = (int)(it % lv.max_nf);
-        const long long rn = it / lv.max_nf;
-        const int ni = (int)(rn % lv.cnt), r = (int)(rn / lv.cnt);
-        const DevNode& nd = nodes[level_nodes[lv.off + ni]];
-        if (row < nd.nf) phase::nd_up_row(d, nodes, nd, r, row, srcmap, lane, nullptr);
-      }
-      grid.sync();
-    }
-    for (int L = nlev - 1; L >= 0; --L) {
-      const DevLevel lv = lev[L];
-      const long long rows = (long long)g.R * lv.cnt * lv.max_ns;
-      for (long long it = wid; it < rows; it += nwarps) {
-        const int row = (int)(it % lv.max_ns);
-        const long long rn = it / lv.max_ns;
-        const int ni = (int)(rn % lv.cnt), r = (int)(rn / lv.cnt);
-        const DevNode& nd = nodes[level_nodes[lv.off + ni]];
-        if (nd.parent >= 0 && row < nd.nsep) phase::nd_down_row(d, nodes, nd, r, row, pmap, lane);
-      }
-      const long long cps = (long long)g.R * lv.cnt * lv.max_nb;
-      for (long long it = tid; it < cps; it += nthreads) {
-        const int k = (int)(it % lv.max_nb);
-        const long long rn = it / lv.max_nb;
-        const int ni = (int)(rn % lv.cnt), r = (int)(rn / lv.cnt);
-        const DevNode& nd = nodes[level_nodes[lv.off + ni]];
-        if (nd.parent >= 0 && k < nd.nbnd) phase::nd_down_copy(d, nodes, nd, r, pmap, k);
-      }
-      grid.sync();
-    }
-  }
-  for (long long it = blockIdx.x; it < (long long)g.R * nsub; it += gridDim.x) {
-    const int sidx = (int)(it % nsub), r = (int)(it / nsub);
-    phase::reconstruct(g, d, subs, nodes, leaf_node, sidx, r, d.rebuild[r], cs, red);
-  }
-}
-
 }  // namespace
-
-int nd_dataflow_blocks(int max_ns, int max_nb) {
-  int dev = 0, sms = 0, per_sm = 0, coop = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  const size_t smem = (size_t)(256 + std::max(max_ns, max_nb)) * sizeof(double);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nd_dataflow, 256, smem) != cudaSuccess) return 0;
-  return sms * (per_sm < 2 ? per_sm : 2);
-}
-
-cudaError_t launch_nd_dataflow(const Grid& g, const DevState& d, const DevNode* nodes, const NdItem* items,
-                               int nitems, int nnodes, int* counters, int max_ns, int max_nb, const int* srcmap,
-                               const int* pmap, int blocks, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(int) * 2 * (size_t)nnodes * g.R, st);
-  if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  const long long total = (long long)nitems * g.R;
-  cfg.gridDim = dim3((unsigned)std::min<long long>(blocks, total));
-  cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = (size_t)(256 + std::max(max_ns, max_nb)) * sizeof(double);
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  ++g_launches;
-  return cudaLaunchKernelEx(&cfg, k_nd_dataflow, g, d, nodes, items, nitems, nnodes, counters, srcmap, pmap);
-}
-
-int iface_coop_blocks() {
-  int dev = 0, sms = 0, per_sm = 0, coop = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iface_coop, 256, 0) != cudaSuccess) return 0;
-  return sms * (per_sm < 2 ? per_sm : 2);
-}
-
-cudaError_t launch_iface_coop(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_dof,
-                              const DevNode* nodes, const int* leaf_node, const int* level_nodes,
-                              const DevLevel* lev, int nlev, const int* srcmap, const int* pmap, int blocks,
-                              cudaStream_t st) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(blocks);
-  cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  ++g_launches;
-  return cudaLaunchKernelEx(&cfg, k_iface_coop, g, d, subs, nsub, max_dof, nodes, leaf_node, level_nodes, lev,
-                            nlev, srcmap, pmap);
-}
 
 void launch_element_matrix(const Grid& g, const DevState& d, const DevSub* subs, int nsub, const DevNode* nodes,
                            const int* leaf_node, cudaStream_t st) {

@@ -1,9 +1,7 @@
-// Per-item device functions of the interface-solve stage (Eq. mrc2 right-hand side,
-// nested-dissection up / down sweeps, reconstruction of traces and p^m, interface fluxes
-// u_bar).  The sweeps are called both by one-kernel-per-level launches and by the
-// persistent cooperative kernel that runs the whole sweep in one launch (k_iface.cu); the
-// right-hand side is formed by the local-solve kernels that produce the traces, u_bar by
-// the downscaling kernel that consumes it (k_local.cu).
+// Per-item device functions shared by the interface-solve stage and the local kernels:
+// interface basis values, the element right-hand side of Eq. (mrc2) (formed by the
+// local-solve kernels that produce the traces) and the interface fluxes u_bar (formed by
+// the downscaling kernel that consumes them, k_local.cu).
 #pragma once
 #include "mpm2p_internal.cuh"
 
@@ -61,121 +59,6 @@ __device__ __forceinline__ void element_rhs(const Grid& g, const DevState& d, co
     else v += bhat[f0 + t] * s * w * F;
   }
   d.gvec[(long long)r * d.st_vec + leaf.v_off + k] = v;
-}
-
-// Value of the gathered right-hand side of node nd at frontal index k (children's g).
-__device__ __forceinline__ double gather_g(const DevState& d, const DevNode* nodes, const DevNode& nd, int r,
-                                           const int* srcmap, int k) {
-  const int* s0 = srcmap + nd.src_off;
-  const int* s1 = s0 + nd.nf;
-  double v = 0.0;
-  if (s0[k] >= 0) {
-    const DevNode& c0 = nodes[nd.child[0]];
-    v += d.gvec[(long long)r * d.st_vec + c0.v_off + c0.nsep + s0[k]];
-  }
-  if (s1[k] >= 0) {
-    const DevNode& c1 = nodes[nd.child[1]];
-    v += d.gvec[(long long)r * d.st_vec + c1.v_off + c1.nsep + s1[k]];
-  }
-  return v;
-}
-
-// Upward solve, one frontal row per warp, from the transposed sweep G (k_iface.cu):
-// y_s[row] = sum_k G[k][row] g_s[k] -> x (row < nsep), or
-// g_b[row] = gather(row) - sum_k G[k][row] g_s[k] (row >= nsep).  gs: the node's gathered
-// separator right-hand side (shared memory), or nullptr to gather from the children on the fly.
-__device__ __forceinline__ void nd_up_row(const DevState& d, const DevNode* nodes, const DevNode& nd, int r, int row,
-                                          const int* srcmap, int lane, const double* gs) {
-  const int nf = nd.nf, ns = nd.nsep;
-  const double* G = d.front + (long long)r * d.st_front + nd.f_off;
-  double acc = 0.0;
-  if (gs)
-    for (int k = lane; k < ns; k += 32) acc += G[(long long)k * nf + row] * gs[k];
-  else
-    for (int k = lane; k < ns; k += 32) acc += G[(long long)k * nf + row] * gather_g(d, nodes, nd, r, srcmap, k);
-  acc = warp_sum(acc);
-  if (lane == 0) {
-    if (row < ns) d.xvec[(long long)r * d.st_vec + nd.v_off + row] = acc;
-    else d.gvec[(long long)r * d.st_vec + nd.v_off + row] = gather_g(d, nodes, nd, r, srcmap, row) - acc;
-  }
-}
-
-// Downward solve, one separator row per warp: x_s[row] = y_s[row] + sum_k G[ns + k][row] x_b[k],
-// x_b read from the parent.
-__device__ __forceinline__ void nd_down_row(const DevState& d, const DevNode* nodes, const DevNode& nd, int r,
-                                            int row, const int* pmap, int lane) {
-  const int nf = nd.nf, ns = nd.nsep, nbd = nd.nbnd;
-  const DevNode& pa = nodes[nd.parent];
-  const double* xp = d.xvec + (long long)r * d.st_vec + pa.v_off;
-  const int* pm = pmap + nd.pmap_off;
-  const double* G = d.front + (long long)r * d.st_front + nd.f_off + (long long)ns * nf;
-  double acc = 0.0;
-  for (int k = lane; k < nbd; k += 32) acc += G[(long long)k * nf + row] * xp[pm[k]];
-  acc = warp_sum(acc);
-  if (lane == 0) d.xvec[(long long)r * d.st_vec + nd.v_off + row] += acc;
-}
-
-// Downward solve, boundary copy: x_b[k] = parent's x at the matching frontal index.
-__device__ __forceinline__ void nd_down_copy(const DevState& d, const DevNode* nodes, const DevNode& nd, int r,
-                                             const int* pmap, int k) {
-  const DevNode& pa = nodes[nd.parent];
-  d.xvec[(long long)r * d.st_vec + nd.v_off + nd.nsep + k] =
-      d.xvec[(long long)r * d.st_vec + pa.v_off + pmap[nd.pmap_off + k]];
-}
-
-// Traces (and at a rebuild the MRCM-level pressure p^m) of subdomain sidx from the
-// interface solution (whole CTA; cs: >= ndof doubles, red: 32 doubles of shared memory):
-//   rebuild: p^m = pbar + P_hat c, F = Fbar + F_hat c, target mean = mean(p^m)
-//   MPM-2P : F = dFbar + F_hat dc, target mean = mean(p^m) + mean(dpbar) + mu_hat . dc
-__device__ inline void reconstruct(const Grid& g, const DevState& d, const DevSub* subs, const DevNode* nodes,
-                            const int* leaf_node, int sidx, int r, int branch, double* cs, double* red) {
-  const DevSub& sd = subs[sidx];
-  const int a = sd.a, b = sd.b, m = a * b, nd = sd.ndof;
-  const int nface = 2 * (a + b);
-  if (nd > 0) {
-    const DevNode& leaf = nodes[leaf_node[sidx]];
-    const double* x = d.xvec + (long long)r * d.st_vec + leaf.v_off;
-    for (int l = threadIdx.x; l < nd; l += blockDim.x) cs[l] = x[l];
-  }
-  __syncthreads();
-  const double* tr = d.tr + (long long)r * d.st_tr + sd.tr_off;
-  const double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
-  double* trace = d.trace + (long long)r * d.st_face + sd.face_off;
-  for (int f = threadIdx.x; f < nface; f += blockDim.x) {
-    double v = fbar[f];
-    for (int l = 0; l < nd; ++l) v += tr[(long long)l * nface + f] * cs[l];
-    trace[f] = v;
-  }
-  double part = 0.0;
-  if (branch == 1) {
-    const double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;
-    for (int c = threadIdx.x; c < m; c += blockDim.x) {
-      double v = pf[(long long)nd * m + c];
-      for (int l = 0; l < nd; ++l) v += pf[(long long)l * m + c] * cs[l];
-      const int jl = c / a, il = c - jl * a;
-      d.p_m[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il] = v;
-      part += v;
-    }
-  } else if (threadIdx.x == 0) {
-    const double* muh = d.mu_hat + (long long)r * d.st_dof + sd.dof_off;
-    part = d.sub_mean[(long long)r * d.st_sub + sidx] * m;
-    for (int l = 0; l < nd; ++l) part += muh[l] * cs[l] * m;
-  }
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    const long long si = (long long)r * d.st_sub + sidx;
-    if (branch == 1) {
-      d.pm_mean[si] = s / m;
-      d.sub_target[si] = s / m;
-    } else {
-      d.sub_target[si] = d.pm_mean[si] + s / m;
-    }
-  }
-  __syncthreads();
 }
 
 // u_bar on face t of side `side` of subdomain sd, oriented along +x / +y (Section 4.1,

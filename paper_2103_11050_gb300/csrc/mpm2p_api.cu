@@ -50,13 +50,6 @@ struct mpm_ctx {
   int* d_level_nodes = nullptr;
   int* d_srcmap = nullptr;
   int* d_pmap = nullptr;
-  DevLevel* d_levels = nullptr;
-  // dataflow interface sweep (one cooperative launch, per-node completion counters)
-  std::vector<NdItem> nd_items;
-  NdItem* d_nd_items = nullptr;
-  int* d_nd_counters = nullptr;
-  int nd_max_ns = 0, nd_max_nb = 0, df_blocks = -1;
-  int coop_blocks = -1;  // grid of the persistent interface kernel (0: unavailable), -1: not queried
   DevState d{};
   std::vector<void*> grid_allocs, dec_allocs;
   // host staging for flags
@@ -71,9 +64,7 @@ struct mpm_ctx {
   long long gk_base = 0, gk_reb = 0, gk_mpm = 0, capture_launches = 0, graph_steps = 0;
   // CUDA graph of one Algorithm 1 step (conditional bodies for the two branches)
   bool use_graph = true;
-  bool use_coop = false;  // interface stage as one persistent cooperative kernel (measured slower)
   bool use_pdl = true;    // programmatic dependent launch along the interface-solve chain
-  bool use_dataflow = false;  // interface sweeps as one cooperative dataflow launch (measured slower)
   // The saturation (and f(s)) live in two buffers that swap at every transport substep; a
   // graph reads and writes fixed buffers, so one graph is kept per buffer parity (slot 0:
   // the current saturation is in s_buf0).
@@ -187,10 +178,6 @@ int check_status(mpm_ctx* c) {
   const int st = reinterpret_cast<volatile int*>(c->h_status)[0];
   const int it = reinterpret_cast<volatile int*>(c->h_status)[1];
   c->stats.ir_iters_max = std::max(c->stats.ir_iters_max, it);
-  if (st & 2) {
-    CK(cudaMemsetAsync(c->d.status, 0, sizeof(int), c->stream));
-    return fail(c, MPM_ERR_TIMEOUT, "a dependency wait of the dataflow interface sweep timed out");
-  }
   if (st & 1) {
     CK(cudaMemsetAsync(c->d.status, 0, sizeof(int), c->stream));
     return fail(c, MPM_ERR_NOT_CONVERGED, "local iterative refinement stopped above ir_tol=%g (ir_max=%d sweeps)",
@@ -353,10 +340,6 @@ int release_decomposition(mpm_ctx* c) {
   c->d_subs = nullptr;
   c->d_nodes = nullptr;
   c->d_leaf_node = c->d_level_nodes = c->d_srcmap = c->d_pmap = nullptr;
-  c->d_levels = nullptr;
-  c->d_nd_items = nullptr;
-  c->d_nd_counters = nullptr;
-  c->nd_items.clear();
   c->have_dec = false;
   c->have_basis = false;
   return MPM_OK;
@@ -410,40 +393,28 @@ int run_interface(mpm_ctx* c) {
   int jrc = join_branches(c, !late_factor_join(c));
   if (jrc) return jrc;
   prof_begin(c, MPM_STAGE_IFACE_SOLVE);
-  if (c->use_coop && c->coop_blocks < 0) c->coop_blocks = iface_coop_blocks();
-  if (c->use_coop && c->coop_blocks > 0) {
-    cudaError_t e = launch_iface_coop(g, d, c->d_subs, nsub, c->max_dof, c->d_nodes, c->d_leaf_node,
-                                      c->d_level_nodes, c->d_levels, (int)c->levels.size(), c->d_srcmap, c->d_pmap,
-                                      c->coop_blocks, st);
-    prof_end(c, MPM_STAGE_IFACE_SOLVE);
-    if (e != cudaSuccess) return fail(c, MPM_ERR_CUDA, "persistent interface kernel: %s", cudaGetErrorString(e));
-    return check_launch(c);
-  }
   bool chained = false;
-  if (c->n_dof > 0 && c->use_dataflow) {
-    if (c->df_blocks < 0) c->df_blocks = nd_dataflow_blocks(c->nd_max_ns, c->nd_max_nb);
-  }
-  if (c->n_dof > 0 && c->use_dataflow && c->df_blocks > 0) {
-    cudaError_t e = launch_nd_dataflow(g, d, c->d_nodes, c->d_nd_items, (int)c->nd_items.size(), (int)c->nodes.size(),
-                                       c->d_nd_counters, c->nd_max_ns, c->nd_max_nb, c->d_srcmap, c->d_pmap,
-                                       c->df_blocks, st);
-    if (e != cudaSuccess) return fail(c, MPM_ERR_CUDA, "dataflow interface sweep: %s", cudaGetErrorString(e));
-    chained = true;
-  } else if (c->n_dof > 0) {
+  if (c->n_dof > 0) {
+    prof_begin(c, MPM_STAGE_IFACE_UP);
     for (size_t L = 1; L < c->levels.size(); ++L) {
       launch_nd_up(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(), c->lev_max_nf[L],
                    c->lev_max_nsep[L], c->d_srcmap, chained && c->use_pdl, st);
       chained = true;
     }
+    prof_end(c, MPM_STAGE_IFACE_UP);
     // the top level holds the root alone, whose separator values the upward sweep leaves
     // final (no launch); level 1 (nodes with two leaf children) is done inside the
     // reconstruction
+    prof_begin(c, MPM_STAGE_IFACE_DOWN);
     for (int L = (int)c->levels.size() - 2; L >= 2; --L)
       launch_nd_down(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(),
                      c->lev_max_nsep[L], c->lev_max_nbnd[L], c->d_pmap, c->use_pdl, st);
+    prof_end(c, MPM_STAGE_IFACE_DOWN);
   }
+  prof_begin(c, MPM_STAGE_RECONSTRUCT);
   launch_reconstruct(g, d, c->d_subs, nsub, c->max_face, c->max_dof, c->levels.size() > 1 ? c->lev_max_nf[1] : 0,
                      c->d_nodes, c->d_leaf_node, c->d_pmap, -1, chained && c->use_pdl, st);
+  prof_end(c, MPM_STAGE_RECONSTRUCT);
   prof_end(c, MPM_STAGE_IFACE_SOLVE);
   return check_launch(c);
 }
@@ -989,57 +960,8 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
     }
     st_lvl = std::max(st_lvl, (long long)c->levels[L].size());
   }
-  std::vector<DevLevel> levtab(nlev);
-  for (int L = 0; L < nlev; ++L)
-    levtab[L] = DevLevel{c->lev_off[L], (int)c->levels[L].size(), c->lev_max_nf[L], c->lev_max_nsep[L],
-                         c->lev_max_nbnd[L]};
   if (srcmap.empty()) srcmap.push_back(-1);
   if (pmap.empty()) pmap.push_back(-1);
-  // dataflow work items: upward by increasing level, downward by decreasing level (level 1 is
-  // done inside the reconstruction); each with the counters it waits for
-  {
-    auto ksplit = [](int n) {
-      const int q = (n + 15) / 16;
-      return q <= 1 ? 1 : q <= 2 ? 2 : q <= 4 ? 4 : q <= 8 ? 8 : 16;
-    };
-    std::vector<int> nup(nn, 0), ndn(nn, 0);
-    c->nd_items.clear();
-    c->nd_max_ns = c->nd_max_nb = 0;
-    for (int L = 1; L < nlev; ++L)
-      for (int i : c->levels[L]) {
-        const DevNode& dn = c->nodes[i];
-        const int ks = ksplit(dn.nsep), rows = 256 / ks;
-        c->nd_max_ns = std::max(c->nd_max_ns, dn.nsep);
-        for (int row0 = 0; row0 < dn.nf; row0 += rows) {
-          NdItem it{i, row0, ks, 0, {-1, -1}, {0, 0}};
-          for (int ch = 0; ch < 2; ++ch) {
-            const int cn = dn.child[ch];
-            if (c->nodes[cn].child[0] >= 0) {
-              it.dep[ch] = cn;
-              it.target[ch] = nup[cn];
-            }
-          }
-          c->nd_items.push_back(it);
-          ++nup[i];
-        }
-      }
-    for (int L = nlev - 1; L >= 2; --L)
-      for (int i : c->levels[L]) {
-        const DevNode& dn = c->nodes[i];
-        if (dn.parent < 0) continue;
-        const int ks = ksplit(dn.nbnd), rows = 256 / ks;
-        c->nd_max_nb = std::max(c->nd_max_nb, dn.nbnd);
-        const int P = dn.parent;
-        const bool root = c->nodes[P].parent < 0;
-        const int pdep = root ? P : nn + P, ptarget = root ? nup[P] : ndn[P];
-        const int nblk = std::max(1, (dn.nsep + rows - 1) / rows);
-        for (int bk = 0; bk < nblk; ++bk) {
-          c->nd_items.push_back(NdItem{i, bk * rows, ks, 1, {i, pdep}, {nup[i], ptarget}});
-          ++ndn[i];
-        }
-      }
-    if (c->nd_items.empty()) c->nd_items.push_back(NdItem{0, 0, 1, 0, {-1, -1}, {0, 0}});
-  }
   // device pools
   DevState& d = c->d;
   const int R = g.R, nsub = ncx * ncy;
@@ -1082,9 +1004,6 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   if (!rc) rc = dalloc_t(c, A, &c->d_level_nodes, level_nodes.size());
   if (!rc) rc = dalloc_t(c, A, &c->d_srcmap, srcmap.size());
   if (!rc) rc = dalloc_t(c, A, &c->d_pmap, pmap.size());
-  if (!rc) rc = dalloc_t(c, A, &c->d_levels, levtab.size());
-  if (!rc) rc = dalloc_t(c, A, &c->d_nd_items, c->nd_items.size());
-  if (!rc) rc = dalloc_t(c, A, &c->d_nd_counters, (size_t)2 * nn * R);
   if (rc) {
     release_decomposition(c);
     return rc;
@@ -1096,10 +1015,6 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
                      c->stream));
   CK(cudaMemcpyAsync(c->d_srcmap, srcmap.data(), srcmap.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->d_pmap, pmap.data(), pmap.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemcpyAsync(c->d_levels, levtab.data(), levtab.size() * sizeof(DevLevel), cudaMemcpyHostToDevice,
-                     c->stream));
-  CK(cudaMemcpyAsync(c->d_nd_items, c->nd_items.data(), c->nd_items.size() * sizeof(NdItem), cudaMemcpyHostToDevice,
-                     c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->have_dec = true;
   c->have_basis = false;
@@ -1260,12 +1175,9 @@ int mpm_step(mpm_ctx* c, double eta, double cfl, int n_sub) {
 
 int mpm_set_execution(mpm_ctx* c, int flags) {
   if (!c) return MPM_ERR_ARG;
-  if (flags & ~(MPM_EXEC_GRAPH | MPM_EXEC_PERSISTENT | MPM_EXEC_PDL | MPM_EXEC_DATAFLOW))
-    return fail(c, MPM_ERR_ARG, "unknown execution flags %d", flags);
+  if (flags & ~(MPM_EXEC_GRAPH | MPM_EXEC_PDL)) return fail(c, MPM_ERR_ARG, "unknown execution flags %d", flags);
   c->use_graph = (flags & MPM_EXEC_GRAPH) != 0;
-  c->use_coop = (flags & MPM_EXEC_PERSISTENT) != 0;
   c->use_pdl = (flags & MPM_EXEC_PDL) != 0;
-  c->use_dataflow = (flags & MPM_EXEC_DATAFLOW) != 0;
   drop_graph(c);
   return MPM_OK;
 }

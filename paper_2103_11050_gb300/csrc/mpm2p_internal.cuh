@@ -100,20 +100,6 @@ struct DevNode {
   int level;           // 0 for leaves, 1 + the larger level of the children otherwise
 };
 
-// One work item of the dataflow interface sweep: rows [row0, row0 + 256/ks) of a node's
-// upward (phase 0) or downward (phase 1) step; it may start once the counters dep[k] (index
-// into the per-realisation counter array, -1 for none) have reached target[k].  Completing it
-// increments counter node (upward) or n_nodes + node (downward).
-struct NdItem {
-  int node, row0, ks, phase;
-  int dep[2], target[2];
-};
-
-// Per-level summary of the nested-dissection tree (node ids level_nodes[off .. off+cnt)).
-struct DevLevel {
-  int off, cnt, max_nf, max_ns, max_nb;
-};
-
 // Per-realisation device state (all pointers are device pointers; pools are indexed
 // r * st_x + offset).
 struct DevState {
@@ -130,8 +116,7 @@ struct DevState {
   double* rate_max;   // [R] max over rate_part, by the last block of the downscaling
   unsigned int* ticket;  // [4] block-completion counters (0: downscaling, 1: transport); back to 0 after each launch
   int* rebuild;        // [R] branch of the current update: 1 = basis build, 0 = MPM-2P reuse
-  int* status;         // [1] bitmask: 1 = a refinement did not reach its tolerance, 2 = a dataflow wait
-                       //     of the interface sweep timed out
+  int* status;         // [1] bitmask: 1 = a refinement did not reach its tolerance
   int* ir_iters;       // [1] max refinement sweeps used
   long long* counts;   // [4] rebuild / MPM-2P updates taken by the device-side decision; graph steps
                        //     that ran the rebuild body / the MPM-2P body
@@ -214,15 +199,6 @@ void launch_nd_factor_level(const Grid& g, const DevState& d, const DevNode* nod
                             int nlev, int max_nf, int max_nsep, const int* srcmap, cudaStream_t st);
 void launch_nd_up(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
                   int max_nf, int max_nsep, const int* srcmap, bool pdl, cudaStream_t st);
-int iface_coop_blocks();
-int nd_dataflow_blocks(int max_ns, int max_nb);
-cudaError_t launch_nd_dataflow(const Grid& g, const DevState& d, const DevNode* nodes, const NdItem* items,
-                               int nitems, int nnodes, int* counters, int max_ns, int max_nb, const int* srcmap,
-                               const int* pmap, int blocks, cudaStream_t st);
-cudaError_t launch_iface_coop(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_dof,
-                              const DevNode* nodes, const int* leaf_node, const int* level_nodes,
-                              const DevLevel* lev, int nlev, const int* srcmap, const int* pmap, int blocks,
-                              cudaStream_t st);
 void launch_nd_down(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
                     int max_nsep, int max_nbnd, const int* pmap, bool pdl, cudaStream_t st);
 

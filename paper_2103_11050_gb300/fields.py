@@ -93,17 +93,51 @@ def uneven_widths(total: int, parts, seed: int) -> list[int]:
     return [int(v) for v in rng.permutation(parts)]
 
 
-# Workloads used by the tests and the benchmark: grid, subdomain layout, covariance of the
-# log-permeability field, viscosity ratio and rebuild threshold of each, listed per entry.
+# Workloads used by the tests and the benchmark: grid, subdomain layout, permeability recipe,
+# viscosity ratio, rebuild threshold and trajectory length of each, listed per entry.
+# field: "grf" (log-normal, covariance / variance / correlation length / seed),
+# "channelised" (binary channels: k_channel, k_matrix, coverage, width range, seed),
+# "homogeneous" (K = 1).  s0: "zero" (oil-filled) or "fingering" (fingering_s0).
 WORKLOADS = {
     # 64x64, 4x4 subdomains of 16x16, exponential GRF (ell 0.1, var 1), M = 1,
     # rebuild every step (eta < 0).
-    "gaussian64": dict(nx=64, ny=64, ncx=4, ncy=4, sigma2=1.0, ell=0.1, cov="exponential",
+    "gaussian64": dict(nx=64, ny=64, ncx=4, ncy=4, field="grf", sigma2=1.0, ell=0.1, cov="exponential",
                        seed=1, M=1.0, eta=-1.0, steps=20),
     # 256x256, 16x16 subdomains, Gaussian covariance (ell 0.05, var 4), M = 5, eta = 0.1.
-    "gaussian256": dict(nx=256, ny=256, ncx=16, ncy=16, sigma2=4.0, ell=0.05, cov="gaussian",
+    "gaussian256": dict(nx=256, ny=256, ncx=16, ncy=16, field="grf", sigma2=4.0, ell=0.05, cov="gaussian",
                         seed=2, M=5.0, eta=0.1, steps=500),
+    # 1024x1024, 64x64 subdomains of 16x16; binary K in {1, 1e-4}: sinusoidal channels along x,
+    # widths 8..24 cells, added until 30 % of the cells are channel (contrast 1e4); M = 5,
+    # eta = 0.1 (the values of the 256^2 workload).
+    "channel1024": dict(nx=1024, ny=1024, ncx=64, ncy=64, field="channelised", k_channel=1.0, k_matrix=1e-4,
+                        coverage=0.30, widths=(8, 24), seed=3, M=5.0, eta=0.1, steps=500),
+    # 512x512, 32x32 subdomains of 16x16, K = 1, M = 10, water-filled inlet strip (x < 0.05) with
+    # 1 % seeded noise in the next 8 columns; eta = 0.1 (the runs also take 0.05 and 0.2).
+    "finger512": dict(nx=512, ny=512, ncx=32, ncy=32, field="homogeneous", s0="fingering", seed=5, M=10.0,
+                      eta=0.1, steps=5000),
 }
+
+# The ensemble workload: R independent realisations of a log-normal field (exponential
+# covariance, variance 2, correlation length drawn uniformly in [0.05, 0.2] per realisation
+# with a generator of seed ``seed``, field seed seed + r), all on one uneven tensor-product
+# decomposition whose column widths / row heights are seeded permutations of
+# 8, 8, 12, 12, 16, 16, 16, 20, 20 (sum 128).
+ENSEMBLE = dict(nx=128, ny=128, R=256, parts=(8, 8, 12, 12, 16, 16, 16, 20, 20), col_seed=11, row_seed=12,
+                sigma2=2.0, ell_range=(0.05, 0.2), cov="exponential", seed=4, M=3.0, eta=0.05, steps=500)
+
+
+def make_ensemble(R: int | None = None, **over):
+    """(Ks [R][ny][nx], s0 [ny][nx], col_w, row_h, params) of the ensemble workload; the first
+    R realisations are the same whatever R is."""
+    w = dict(ENSEMBLE)
+    w.update(over)
+    R = w["R"] if R is None else int(R)
+    nx, ny = w["nx"], w["ny"]
+    ells = np.random.default_rng(w["seed"]).uniform(w["ell_range"][0], w["ell_range"][1], max(R, w["R"]))
+    Ks = np.stack([lognormal_grf(nx, ny, 1.0 / nx, w["sigma2"], ells[r], w["cov"], w["seed"] + r) for r in range(R)])
+    cw = uneven_widths(nx, w["parts"], w["col_seed"])
+    rh = uneven_widths(ny, w["parts"], w["row_seed"])
+    return Ks, np.zeros((ny, nx)), cw, rh, w
 
 
 def make_workload(name: str):
@@ -111,6 +145,17 @@ def make_workload(name: str):
     w = dict(WORKLOADS[name])
     nx, ny = w["nx"], w["ny"]
     h = 1.0 / nx
-    K = lognormal_grf(nx, ny, h, w["sigma2"], w["ell"], w["cov"], w["seed"])
-    s0 = np.zeros((ny, nx))
+    kind = w.get("field", "grf")
+    if kind == "grf":
+        K = lognormal_grf(nx, ny, h, w["sigma2"], w["ell"], w["cov"], w["seed"])
+    elif kind == "channelised":
+        K = channelised(nx, ny, w["k_channel"], w["k_matrix"], w["coverage"], w["widths"], w["seed"])
+    elif kind == "homogeneous":
+        K = np.ones((ny, nx))
+    else:
+        raise ValueError(f"unknown field kind {kind!r}")
+    if w.get("s0", "zero") == "fingering":
+        s0 = fingering_s0(nx, ny, 0.05, 8, 0.01, seed=w["seed"])
+    else:
+        s0 = np.zeros((ny, nx))
     return K, s0, w

@@ -118,18 +118,15 @@ def test_transport_parity():
     np.testing.assert_allclose(ctx.get_conductivity()[0], O.mobility(s, c["M"]) * c["K"], rtol=1e-11)
 
 
-@pytest.mark.parametrize("graph,persistent,pdl,dataflow", [(True, False, True, False), (False, False, True, False),
-                                                           (True, False, True, True), (False, False, True, True),
-                                                           (True, False, False, False), (False, False, False, False),
-                                                           (True, True, True, False), (False, True, False, False)])
+@pytest.mark.parametrize("graph,pdl", [(True, True), (False, True), (True, False), (False, False)])
 @pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("name,eta,steps", [("p1_2x2", 0.02, 12), ("uneven", -1.0, 4), ("contrast64", 0.05, 8)])
-def test_algorithm1_parity(name, eta, steps, prec, graph, persistent, pdl, dataflow):
+def test_algorithm1_parity(name, eta, steps, prec, graph, pdl):
     c = case(name, "zero")
     prob, dec = _oracle_setup(c)
     st = O.simulate_init(c["K"], c["s0"], prob, dec, eta)
     ctx = _gpu(c, prec)
-    ctx.set_execution(graph, persistent, pdl, dataflow)
+    ctx.set_execution(graph, pdl)
     ctx.init(eta)
     tol = TOL[prec]
     for n in range(steps):
@@ -141,9 +138,12 @@ def test_algorithm1_parity(name, eta, steps, prec, graph, persistent, pdl, dataf
     n_reb = sum(1 for h in st.history if h["rebuild"])
     assert stats["rebuilds"] == n_reb + 1  # plus the initial build
     assert stats["mpm_updates"] == steps - n_reb
-    assert rel(s, st.s) <= tol * 10, rel(s, st.s)
-    assert rel(ux[0], st.step.Fx) <= tol * 10, rel(ux[0], st.step.Fx)
-    assert rel(uy[0], st.step.Fy) <= tol * 10 + 1e-12
+    assert rel(s, st.s) <= tol, rel(s, st.s)
+    assert rel(ux[0], st.step.Fx) <= tol, rel(ux[0], st.step.Fx)
+    assert rel(uy[0], st.step.Fy) <= tol + 1e-12, rel(uy[0], st.step.Fy)
+    # pressures: the MRCM-level p^m of the last rebuild and the last downscaled pressure
+    assert rel(ctx.get_pressure(0)[0], st.p_m) <= tol, rel(ctx.get_pressure(0)[0], st.p_m)
+    assert rel(ctx.get_pressure(1)[0], st.step.p_down) <= tol, rel(ctx.get_pressure(1)[0], st.step.p_down)
 
 
 def test_graph_replay_mixed_branches_across_realisations():

@@ -55,6 +55,48 @@ def test_noalloc_cfl_matches_saturation_step_on_consecutive_calls(torch_cuda):
     ctx.close()
 
 
+def test_noalloc_calls_take_no_device_memory(torch_cuda):
+    # The point of the entry point: after its first call on the device (which only looks up
+    # the scratch array's address), further calls leave the device's free memory unchanged.
+    torch = torch_cuda
+    from paper_2103_11050_gb300 import binding as B
+    R, nx, ny = 3, 24, 20
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    ux = torch.randn((R, ny, nx + 1), dtype=torch.float64, device="cuda", generator=gen)
+    uy = torch.randn((R, ny + 1, nx), dtype=torch.float64, device="cuda", generator=gen)
+    dt = torch.zeros(R, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    B.cfl_dt_noalloc(ux, uy, dt, 1.0 / nx, 2.0, 0.5, stream)
+    torch.cuda.synchronize()
+    first = dt.clone()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        B.cfl_dt_noalloc(ux, uy, dt, 1.0 / nx, 2.0, 0.5, stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.equal(dt, first)
+
+
+def test_noalloc_binding_checks_shapes_and_types(torch_cuda):
+    torch = torch_cuda
+    from paper_2103_11050_gb300 import binding as B
+    R, nx, ny = 2, 8, 6
+    ux = torch.zeros((R, ny, nx + 1), dtype=torch.float64, device="cuda")
+    uy = torch.zeros((R, ny + 1, nx), dtype=torch.float64, device="cuda")
+    dt = torch.zeros(R, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        B.cfl_dt_noalloc(ux, uy[:, :-1], dt, 0.125, 1.0, 0.5)
+    with pytest.raises(ValueError):
+        B.cfl_dt_noalloc(ux, uy, dt[:1], 0.125, 1.0, 0.5)
+    with pytest.raises(ValueError):
+        B.cfl_dt_noalloc(ux.float(), uy, dt, 0.125, 1.0, 0.5)
+    with pytest.raises(ValueError):
+        B.cfl_dt_noalloc(ux.transpose(1, 2), uy, dt, 0.125, 1.0, 0.5)
+    with pytest.raises(ValueError):
+        B.cfl_dt_noalloc(ux.cpu(), uy, dt, 0.125, 1.0, 0.5)
+
+
 def test_noalloc_refuses_sizes_beyond_its_scratch(torch_cuda):
     torch = torch_cuda
     from paper_2103_11050_gb300 import binding as B
