@@ -17,7 +17,8 @@ Where the paper is silent the reading taken is written next to the code:
   mu_w = 1 / M, so lambda(s) = M s^2 + (1 - s)^2 and f = M s^2 / lambda.
 * Robin faces (Eq. mrc1 with Eq. beta): eliminating the face pressure between the
   half-cell flux and the Robin condition gives the integrated outward flux
-  F_e = r_e (p_c - g_e) with r_e = kappa_c / (1/2 + rho_e), rho_e = alpha H_e / h,
+  F_e = r_e (p_c - g_e) with r_e = kappa_c / (1/2 + rho_e), rho_e = alpha_e H_e / h
+  (alpha constant, or given per interface face: the aMRCM's alpha(x), Section 3.1),
   and the Robin datum g_e = -(rho_e / kappa_c) s U_e + P_e, where U_e is the
   interface flux integrated over the face and s = n_check . n_check^i.
 * H_e (the "characteristic size" in Eq. beta) is the length of the interface
@@ -172,7 +173,10 @@ class Decomposition:
     """Tensor-product decomposition (column widths x row heights) with the
     interface spaces of Section 3.1 (degree 0/1 on segments of seg_len edges)."""
 
-    def __init__(self, nx, ny, col_w, row_h, seg_len=4, degree=1, alpha=1.0):
+    def __init__(self, nx, ny, col_w, row_h, seg_len=4, degree=1, alpha=1.0, alpha_face=None):
+        # alpha_face: None (the constant alpha on every interface face) or a pair
+        # (alpha_x [ny][nx+1], alpha_y [ny+1][nx]) giving alpha(x) of Eq. (beta) per fine face,
+        # read on the interface faces only (the aMRCM's spatially varying alpha, Section 3.1)
         col_w = [int(v) for v in col_w]
         row_h = [int(v) for v in row_h]
         if sum(col_w) != nx or sum(row_h) != ny:
@@ -181,6 +185,12 @@ class Decomposition:
         self.col_w, self.row_h = col_w, row_h
         self.ncx, self.ncy = len(col_w), len(row_h)
         self.seg_len, self.degree, self.alpha = int(seg_len), int(degree), float(alpha)
+        if alpha_face is None:
+            self.alpha_x = np.full((ny, nx + 1), self.alpha)
+            self.alpha_y = np.full((ny + 1, nx), self.alpha)
+        else:
+            self.alpha_x = np.asarray(alpha_face[0], dtype=np.float64).reshape(ny, nx + 1)
+            self.alpha_y = np.asarray(alpha_face[1], dtype=np.float64).reshape(ny + 1, nx)
         xo = np.concatenate([[0], np.cumsum(col_w)]).astype(int)
         yo = np.concatenate([[0], np.cumsum(row_h)]).astype(int)
         self.subs = []
@@ -226,6 +236,16 @@ class Decomposition:
                 else:
                     sd.sides.append(Side("phys", which, cells, gcells))
 
+    def side_alpha(self, side: Side):
+        """alpha of Eq. (beta) on each face of a side (in the side's cell order)."""
+        if side.which == LEFT:
+            return np.array([self.alpha_x[j, i] for (j, i) in side.gcells])
+        if side.which == RIGHT:
+            return np.array([self.alpha_x[j, i + 1] for (j, i) in side.gcells])
+        if side.which == BOTTOM:
+            return np.array([self.alpha_y[j, i] for (j, i) in side.gcells])
+        return np.array([self.alpha_y[j + 1, i] for (j, i) in side.gcells])
+
     def basis(self, itf: Interface, t: int, k: int) -> float:
         """Value at edge t (0-based along the interface) of the k-th basis function of one
         of the two spaces on interface ``itf`` (k = seg * (degree+1) + power)."""
@@ -255,8 +275,8 @@ class Decomposition:
         return sum(len(self.sub_dofs(sd)) for sd in self.subs)
 
 
-def uniform_decomposition(nx, ny, ncx, ncy, seg_len=4, degree=1, alpha=1.0):
-    return Decomposition(nx, ny, [nx // ncx] * ncx, [ny // ncy] * ncy, seg_len, degree, alpha)
+def uniform_decomposition(nx, ny, ncx, ncy, seg_len=4, degree=1, alpha=1.0, alpha_face=None):
+    return Decomposition(nx, ny, [nx // ncx] * ncx, [ny // ncy] * ncy, seg_len, degree, alpha, alpha_face)
 
 
 # ----------------------------------------------------------------------------
@@ -347,8 +367,8 @@ def cell_balance(Fx, Fy, prob: Problem):
 # ----------------------------------------------------------------------------
 
 def _robin_coeffs(dec: Decomposition, side: Side, kappa_cells):
-    """r_e = kappa_c / (1/2 + rho_e) and beta_hat_e = rho_e / kappa_c, rho_e = alpha H_e / h."""
-    rho = dec.alpha * side.length
+    """r_e = kappa_c / (1/2 + rho_e) and beta_hat_e = rho_e / kappa_c, rho_e = alpha_e H_e / h."""
+    rho = dec.side_alpha(side) * side.length
     kc = np.asarray(kappa_cells)
     return kc / (0.5 + rho), rho / kc
 

@@ -146,7 +146,14 @@ def test_fine_neumann_rate_bc():
 
 # ---------------------------------------------------------------- MRCM
 
-@pytest.mark.parametrize("alpha", [0.5, 1.0, 4.0])
+def _alpha_field(nx, ny, seed, lo=0.1, hi=10.0):
+    """A seeded per-face alpha(x) (log-uniform in [lo, hi]): (alpha_x [ny][nx+1], alpha_y [ny+1][nx])."""
+    rng = np.random.default_rng(seed)
+    return (np.exp(rng.uniform(np.log(lo), np.log(hi), (ny, nx + 1))),
+            np.exp(rng.uniform(np.log(lo), np.log(hi), (ny + 1, nx))))
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 4.0, "field"])
 def test_local_robin_solve_reproduces_linear_pressure(alpha):
     # Local problem (Eq. mrc1) in a homogeneous medium with the Robin data of an exact linear
     # pressure p = 1 + gx x + gy y.  The Robin condition -beta u.n + lambda = g with
@@ -163,7 +170,10 @@ def test_local_robin_solve_reproduces_linear_pressure(alpha):
     dpdn = {O.LEFT: -gx, O.RIGHT: gx, O.BOTTOM: -gy, O.TOP: gy}
     prob = O.Problem(nx, ny, h, (O.DIRICHLET, O.DIRICHLET, O.NEUMANN, O.NEUMANN),
                      (1.0, 0.0, -kap * dpdn[O.BOTTOM], -kap * dpdn[O.TOP]), M=1.0)
-    dec = O.Decomposition(nx, ny, [8, 8, 8], [6, 6, 6], 2, 1, alpha)
+    # alpha is a constant, or (aMRCM) varies face by face: the Robin datum then carries each
+    # face's own alpha, and the local solve must still return the linear field
+    af = _alpha_field(nx, ny, 17) if alpha == "field" else None
+    dec = O.Decomposition(nx, ny, [8, 8, 8], [6, 6, 6], 2, 1, 1.0 if af else alpha, af)
     sd = dec.subs[1]
     assert [side.kind for side in sd.sides] == ["iface", "iface", "phys", "iface"]
     kappa = np.full((ny, nx), kap)
@@ -174,13 +184,17 @@ def test_local_robin_solve_reproduces_linear_pressure(alpha):
             xf, yf = (i + 0.5) * h, (j + 0.5) * h
             if side.which == O.LEFT:
                 xf = i * h
+                a_e = af[0][j, i] if af else alpha
             elif side.which == O.RIGHT:
                 xf = (i + 1) * h
+                a_e = af[0][j, i + 1] if af else alpha
             elif side.which == O.BOTTOM:
                 yf = j * h
+                a_e = af[1][j, i] if af else alpha
             else:
                 yf = (j + 1) * h
-            g.append(field(xf, yf) + alpha * side.length * h * dpdn[side.which])
+                a_e = af[1][j + 1, i] if af else alpha
+            g.append(field(xf, yf) + a_e * side.length * h * dpdn[side.which])
         g_faces.append(np.array(g))
     A = O.local_matrix(kappa, prob, dec, sd)
     rhs = O.local_rhs(kappa, prob, dec, sd, np.zeros(sd.m), g_faces)
@@ -205,13 +219,15 @@ def test_mrcm_single_subdomain_equals_fine():
     np.testing.assert_allclose(step.Fy, Fy, atol=1e-12)
 
 
-@pytest.mark.parametrize("alpha", [0.1, 1.0, 10.0])
+@pytest.mark.parametrize("alpha", [0.1, 1.0, 10.0, "field"])
 def test_mrcm_hbar_h_equals_fine(alpha):
-    # Section 5.4: MRCM with H_bar = h and constant spaces equals the undecomposed solution.
+    # Section 5.4: MRCM with H_bar = h and constant spaces equals the undecomposed solution,
+    # for any alpha, also one that varies face by face (aMRCM).
     nx, ny = 12, 10
     prob = _prob(nx, ny, bc_val=(1.0, -0.5, 0.0, 0.0))
     kappa = _field(nx, ny, seed=3, sigma2=2.0)
-    dec = O.Decomposition(nx, ny, [4, 8], [6, 4], seg_len=1, degree=0, alpha=alpha)
+    af = _alpha_field(nx, ny, 23) if alpha == "field" else None
+    dec = O.Decomposition(nx, ny, [4, 8], [6, 4], seg_len=1, degree=0, alpha=1.0 if af else alpha, alpha_face=af)
     step, _, _ = O.mrcm_step(kappa, prob, dec)
     p_ref = O.fine_solve(kappa, prob)
     Fx, Fy = O.fine_fluxes(p_ref, kappa, prob)
@@ -240,12 +256,14 @@ def test_mrcm_p1_reproduces_linear_pressure(direction):
     assert np.max(np.abs(step0.p_level - p_ref)) > 1e-6
 
 
-@pytest.mark.parametrize("alpha,degree,seg", [(1.0, 1, 4), (0.5, 0, 4), (2.0, 1, 2)])
+@pytest.mark.parametrize("alpha,degree,seg", [(1.0, 1, 4), (0.5, 0, 4), (2.0, 1, 2), ("field", 1, 4)])
 def test_mrcm_basis_route_equals_monolithic(alpha, degree, seg):
     nx, ny = 16, 12
     prob = _prob(nx, ny, bc_val=(1.0, 0.0, 0.0, 0.0))
     kappa = _field(nx, ny, seed=11, sigma2=2.0)
-    dec = O.Decomposition(nx, ny, [4, 8, 4], [8, 4], seg_len=seg, degree=degree, alpha=alpha)
+    af = _alpha_field(nx, ny, 29) if alpha == "field" else None
+    dec = O.Decomposition(nx, ny, [4, 8, 4], [8, 4], seg_len=seg, degree=degree, alpha=1.0 if af else alpha,
+                          alpha_face=af)
     sol, _ = O.mrcm_solve(kappa, prob, dec)
     p_mono, c_mono = O.mrcm_monolithic(kappa, prob, dec)
     scale = np.max(np.abs(p_mono))
@@ -253,12 +271,15 @@ def test_mrcm_basis_route_equals_monolithic(alpha, degree, seg):
     np.testing.assert_allclose(sol.coeffs, c_mono, atol=1e-10 * np.max(np.abs(c_mono)))
 
 
-def test_interface_matrix_symmetric():
-    # With the flux-weighted rows negated, Eq. (mrc2) tested with the BFs is symmetric.
+@pytest.mark.parametrize("varying", [False, True])
+def test_interface_matrix_symmetric(varying):
+    # With the flux-weighted rows negated, Eq. (mrc2) tested with the BFs is symmetric (also
+    # with alpha varying face by face: both sides of an interface face share its alpha).
     nx, ny = 16, 16
     prob = _prob(nx, ny)
     kappa = _field(nx, ny, seed=5, sigma2=3.0)
-    dec = O.uniform_decomposition(nx, ny, 2, 2, seg_len=4, degree=1, alpha=1.0)
+    af = _alpha_field(nx, ny, 31) if varying else None
+    dec = O.uniform_decomposition(nx, ny, 2, 2, seg_len=4, degree=1, alpha=1.0, alpha_face=af)
     bs = O.build_basis(kappa, prob, dec)
     K = bs.K.toarray()
     assert np.max(np.abs(K - K.T)) <= 1e-11 * np.max(np.abs(K))
