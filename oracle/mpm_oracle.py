@@ -772,8 +772,22 @@ def mrcm_step(kappa, prob: Problem, dec: Decomposition):
     return StepResult(sol.p, pt, Fx, Fy), bs, sol
 
 
-def mpm_step(kappa_n, bs: BasisSet, p_m, prob: Problem, dec: Decomposition):
-    """One MPM-2P update reusing the BFs of kappa^m = bs.kappa (Section 4.1)."""
+def _homogeneous(prob: Problem):
+    """The same problem with zero source and zero physical boundary data (the data of the
+    perturbation problems, Eq. mpm_tf_4)."""
+    return Problem(prob.nx, prob.ny, prob.h, prob.bc_type, (0.0, 0.0, 0.0, 0.0), prob.M, prob.s_inflow, None)
+
+
+def mpm_step(kappa_n, bs: BasisSet, p_m, prob: Problem, dec: Decomposition, order: int = 0):
+    """One MPM-2P update reusing the BFs of kappa^m = bs.kappa (Section 4.1).
+
+    order = 0 solves the epsilon^0 problem (Eq. mpm_tf_3) only, as the paper does.
+    order = 1 adds the first-order term of the expansion (Eq. mpm_tf_4 with l = 1): its
+    source div(kappa_eps grad delta p_0), with eps kappa_eps = kappa^n - kappa^m, is on the
+    fine grid -(A(kappa^n) - A(kappa^m)) delta p_0 (homogeneous data); it is solved with
+    the same stored BFs, and eps u_hat_1 = eps delta u_1 + (kappa^n - kappa^m) grad delta p_0
+    gives the flux increment u_hat_1 + F_n(delta p_0) - F_m(delta p_0), F_k the fine flux
+    under kappa^k.  delta p_0 is the MRCM-level pressure of the epsilon^0 solve."""
     kappa_m = bs.kappa
     r = fine_residual(kappa_n, p_m, prob)
     pbar, Fbar = _nonhomogeneous(kappa_m, prob, dec, bs, r, True)
@@ -784,6 +798,20 @@ def mpm_step(kappa_n, bs: BasisSet, p_m, prob: Problem, dec: Decomposition):
     ux = dsol.ubar_x + Fnx
     uy = dsol.ubar_y + Fny
     p_level = p_m + dsol.p
+    if order >= 1:
+        hom = _homogeneous(prob)
+        A_n, _ = fine_system(kappa_n, hom)
+        A_m, _ = fine_system(kappa_m, hom)
+        dp0 = dsol.p.reshape(-1)
+        r1 = -((A_n - A_m) @ dp0).reshape(prob.ny, prob.nx)
+        pbar1, Fbar1 = _nonhomogeneous(kappa_m, prob, dec, bs, r1, True)
+        c1 = _solve_interface(bs.K, _interface_rhs(Fbar1, kappa_m, dec))
+        dsol1 = _combine(kappa_m, prob, dec, bs, pbar1, Fbar1, c1)
+        Gnx, Gny = fine_fluxes(dsol.p, kappa_n, hom)
+        Gmx, Gmy = fine_fluxes(dsol.p, kappa_m, hom)
+        ux = ux + dsol1.ubar_x + (Gnx - Gmx)
+        uy = uy + dsol1.ubar_y + (Gny - Gmy)
+        p_level = p_level + dsol1.p
     pt, Fx, Fy = downscale(kappa_n, ux, uy, p_level, prob, dec)
     return StepResult(p_level, pt, Fx, Fy), dsol
 
@@ -854,9 +882,10 @@ def simulate_init(K, s0, prob: Problem, dec: Decomposition, eta: float) -> SimSt
     return SimState(s0.copy(), bs, sol.p.copy(), step, eta)
 
 
-def simulate_step(st: SimState, K, prob: Problem, dec: Decomposition, eta: float, cfl: float, n_sub: int):
+def simulate_step(st: SimState, K, prob: Problem, dec: Decomposition, eta: float, cfl: float, n_sub: int,
+                  order: int = 0):
     """One pass of the while loop of Algorithm 1 (transport substeps, kappa^n,
-    rebuild if eps > eta else MPM, new eps)."""
+    rebuild if eps > eta else MPM of the given perturbation order, new eps)."""
     dt = cfl_dt(st.step.Fx, st.step.Fy, prob, cfl)
     for _ in range(n_sub):
         st.s = upwind_step(st.s, st.step.Fx, st.step.Fy, dt, prob)
@@ -867,7 +896,7 @@ def simulate_step(st: SimState, K, prob: Problem, dec: Decomposition, eta: float
         st.step, st.bs, sol = mrcm_step(kappa_n, prob, dec)
         st.p_m = sol.p.copy()
     else:
-        st.step, _ = mpm_step(kappa_n, st.bs, st.p_m, prob, dec)
+        st.step, _ = mpm_step(kappa_n, st.bs, st.p_m, prob, dec, order)
     st.eps = epsilon(kappa_n, st.bs.kappa)
     st.history.append(dict(n=st.n, rebuild=rebuild, eps=st.eps, dt=dt))
     st.n += 1

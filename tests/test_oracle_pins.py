@@ -408,6 +408,35 @@ def test_mpm_error_order_in_epsilon(seg, degree, order):
         assert 0.9 * 2 ** order < errs[k] / errs[k + 1] < 1.1 * 2 ** order
 
 
+@pytest.mark.parametrize("alpha_field", [False, True])
+def test_mpm_first_order_term_raises_the_order(alpha_field):
+    # Eq. (mpm_tf_4), l = 1: with H_bar = h the MRCM is the exact fine solve, so the epsilon^0
+    # update is one defect-correction sweep with error O(eps^2) (previous pin) and adding the
+    # first-order term (source div(kappa_eps grad delta p_0), flux increment
+    # u_hat_1 + (kappa^n - kappa^m) grad delta p_0) leaves O(eps^3).  A dropped flux increment
+    # or a flipped source sign leaves O(eps^2) and fails the ratio.
+    nx, ny = 16, 16
+    prob = _prob(nx, ny)
+    kap_m = _field(nx, ny, seed=21)
+    af = _alpha_field(nx, ny, 37) if alpha_field else None
+    dec = O.uniform_decomposition(nx, ny, 2, 2, seg_len=1, degree=0, alpha_face=af)
+    _, bs, sol = O.mrcm_step(kap_m, prob, dec)
+    pert = 1.0 + np.sin(np.arange(nx * ny).reshape(ny, nx) * 0.37)
+    errs0, errs1 = [], []
+    for t in (2e-2, 1e-2, 5e-3):
+        kap_n = kap_m * (1.0 + t * pert)
+        p_ref = O.fine_solve(kap_n, prob)
+        Fx, Fy = O.fine_fluxes(p_ref, kap_n, prob)
+        m0, _ = O.mpm_step(kap_n, bs, sol.p, prob, dec, order=0)
+        m1, _ = O.mpm_step(kap_n, bs, sol.p, prob, dec, order=1)
+        errs0.append(np.linalg.norm(m0.Fx - Fx) + np.linalg.norm(m0.Fy - Fy))
+        errs1.append(np.linalg.norm(m1.Fx - Fx) + np.linalg.norm(m1.Fy - Fy))
+    assert errs1[-1] < 1e-2 * errs0[-1]
+    for k in range(2):
+        assert 0.9 * 4 < errs0[k] / errs0[k + 1] < 1.1 * 4
+        assert 0.85 * 8 < errs1[k] / errs1[k + 1] < 1.15 * 8
+
+
 # ---------------------------------------------------------------- transport
 
 def test_upwind_hand_step_strip():
