@@ -158,8 +158,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def setup_ctx(B, wl, prec, stream):
+def setup_ctx(B, wl, prec, stream, tune=None):
     ctx = B.Context(wl.R, wl.nx, wl.ny, 1.0, wl.ny / wl.nx, stream=stream)
+    if tune is not None:
+        ctx.set_tuning(tune)
     mode = {"fp32": B.PREC_FP32_IR, "fp32all": B.PREC_FP32_IR_ALL, "fp64": B.PREC_FP64}[prec]
     ctx.set_precision(mode, 1e-14, 30)
     ctx.set_fluids(wl.M)
@@ -216,11 +218,29 @@ def run_gpu(args, wl):
     from paper_2103_11050_gb300 import binding as B
     from paper_2103_11050_gb300 import build as Bd
 
+    from paper_2103_11050_gb300 import autotune as AT
+
     Bd.build()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     cells = wl.cells
+    tunes = {}
+
+    def tuning(prec):
+        """Launch shapes of this workload and precision: from the cache, or autotuned once on a
+        context that has run its initialisation and three steps."""
+        if args.no_tune:
+            return None
+        if prec not in tunes:
+            key = AT.shape_key(wl.R, wl.nx, wl.ny, wl.col_w, wl.row_h, prec, torch.cuda.get_device_name())
+            ctx = setup_ctx(B, wl, prec, stream.cuda_stream)
+            ctx.init(wl.eta)
+            for _ in range(3):
+                ctx.step(wl.eta, CFL, N_SUB)
+            tunes[prec] = AT.tuned(ctx, key)
+            ctx.close()
+        return tunes[prec][0]
 
     def timed_steps(ctx, n, eta, flags=None):
         """n steps, each bracketed by CUDA events on the launching stream after an L2 flush;
@@ -245,8 +265,9 @@ def run_gpu(args, wl):
 
     def trajectory(prec, profile=False):
         """init, W warm-up steps, the K timed steps, then the rest of the workload's trajectory."""
-        ctx = setup_ctx(B, wl, prec, stream.cuda_stream)
-        ctx.set_execution(graph=not profile)  # the stage profiler times the eager launch sequence
+        ctx = setup_ctx(B, wl, prec, stream.cuda_stream, tuning(prec))
+        # the stage profiler times the eager launch sequence
+        ctx.set_execution(graph=not (profile or args.eager))
         ctx.init(wl.eta)
         for _ in range(args.warmup):
             ctx.step(wl.eta, CFL, N_SUB)
@@ -275,7 +296,7 @@ def run_gpu(args, wl):
     def forced(prec, eta, n, profile=False):
         """Steps of one kind timed explicitly: eta < 0 makes every step after the first a rebuild,
         eta = 1e300 makes every step an MPM-2P update."""
-        ctx = setup_ctx(B, wl, prec, stream.cuda_stream)
+        ctx = setup_ctx(B, wl, prec, stream.cuda_stream, tuning(prec))
         ctx.set_execution(graph=not profile)
         ctx.init(eta)
         for _ in range(3):
@@ -311,7 +332,8 @@ def run_gpu(args, wl):
         main = trajectory(prec)
         return {"metric": METRIC, "window_value": cells * args.steps / (sum(main["per"]) / 1e3), "unit": UNIT,
                 "steps": args.steps, "warmup": args.warmup, "timed_steps_rebuild": main["rebuild_steps"],
-                "gpu_launches": main["launches"], "config": {"workload": wl.desc, "precision": PREC[prec]}}
+                "gpu_launches": main["launches"], "config": {"workload": wl.desc, "precision": PREC[prec],
+                                                             "tuning": tunes.get(prec)}}
     with ClockSampler(0) as clk:
         main = trajectory(prec)
         reb_per, _ = forced(prec, -1.0, FORCED_REBUILDS)
@@ -338,7 +360,7 @@ def run_gpu(args, wl):
     # (eta = 1e300) and rebuild steps (eta < 0) are timed on fresh contexts and blended like
     # the device value; the median of E2E_PASSES passes of each is reported.
     def e2e_pass(eta, nsteps):
-        ctx = setup_ctx(B, wl, prec, stream.cuda_stream)
+        ctx = setup_ctx(B, wl, prec, stream.cuda_stream, tuning(prec))
         ctx.init(eta)
         for _ in range(args.warmup):
             ctx.step(eta, CFL, N_SUB)
@@ -384,7 +406,8 @@ def run_gpu(args, wl):
                    "value": "blended over the workload's rebuild mix: cells / (f t_rebuild + (1-f) t_mpm)",
                    "timed_steps_rebuild": main["rebuild_steps"], "timed_steps_mpm": args.steps - main["rebuild_steps"],
                    "l2": "flushed before every timed step (256 MB write outside the timed region)",
-                   "precision": PREC[prec]},
+                   "precision": PREC[prec],
+                   "tuning": None if args.no_tune else {"values": tunes[prec][0], "source": tunes[prec][1]}},
         "window_value": cells * args.steps / (window_ms / 1e3),
         "gpu_launches": main["launches"],
         "e2e": {"value": cells / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": 8 * cells,
@@ -513,9 +536,13 @@ def main():
     ap.add_argument("--no-trajectory", action="store_true",
                     help="do not run the workload's trajectory past the timed window (rebuild mix of the window)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-tune", action="store_true", help="default launch shapes instead of the autotuned ones")
     ap.add_argument("--window-only", action="store_true",
-                    help="run only init, the warm-up and the timed window (graph mode) and print its rate: the "
-                         "command profiled for the kernel launch list")
+                    help="run only init, the warm-up and the timed window and print its rate: the command "
+                         "profiled for the kernel launch list")
+    ap.add_argument("--eager", action="store_true",
+                    help="with --window-only: launch the steps kernel by kernel instead of as one CUDA graph (ncu "
+                         "does not profile the kernels of graphs with conditional nodes)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

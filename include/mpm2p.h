@@ -152,11 +152,16 @@ int mpm_set_boundary(mpm_ctx* ctx, const int type[4], const double val[4], doubl
 
 /* Tensor-product decomposition (Section 3): ncx column widths col_w (cells, summing to
  * nx) and ncy row heights row_h (summing to ny); every width and height <= 24 and a
- * multiple of seg_len; degree 0 or 1 (Section 3.1); alpha > 0 is the constant of
+ * multiple of seg_len; degree 0 or 1 (Section 3.1).  alpha > 0 is the constant of
  * Eq. (beta) (beta = alpha H / kappa, H = length of the interface carrying the face).
+ * alpha_face (host memory, may be NULL) gives alpha per fine face instead, the aMRCM's
+ * alpha(x) of Section 3.1: ny (nx + 1) values for the x-faces in the layout of ux, then
+ * (ny + 1) nx values for the y-faces in the layout of uy (one field for all realisations);
+ * only its values on interface faces are read, and each of those must be > 0 and finite
+ * (else MPM_ERR_ARG).  NULL means alpha on every face.  The array is copied.
  * (Re)allocates every per-subdomain device buffer; invalidates the stored basis. */
 int mpm_set_decomposition(mpm_ctx* ctx, int ncx, const int* col_w, int ncy, const int* row_h,
-                          int seg_len, int degree, double alpha);
+                          int seg_len, int degree, double alpha, const double* alpha_face);
 
 /* Water saturation s [R][ny][nx] in [0,1]; also recomputes kappa^n = lambda(s) K.  Host
  * values are range-checked (on the device for pinned memory, on the host otherwise) before
@@ -187,8 +192,24 @@ int mpm_choose(mpm_ctx* ctx, double eta, int* rebuild);
  * interface right-hand side from its traces.  Needs a stored basis. */
 int mpm_perturbation_solve(mpm_ctx* ctx);
 
+/* Order of the MPM-2P perturbation expansion (Section 4.1): 0 (default, as in the paper) keeps
+ * the epsilon^0 problem only (Eq. mpm_tf_3); 1 adds the first-order term (Eq. mpm_tf_4 with
+ * l = 1): a second local solve per subdomain with the stored Robin factors, source
+ * div(kappa_eps grad delta p_0) = -(A(kappa^n) - A(kappa^m)) delta p_0 on the fine grid
+ * (delta p_0 the MRCM-level pressure of the epsilon^0 solve, homogeneous data), a second
+ * interface solve, and the flux increment u_hat_1 + (kappa^n - kappa^m) grad delta p_0 in
+ * u_bar.  mpm_step applies it to every MPM-2P update; it roughly doubles the cost of the
+ * perturbation and interface stages.  Drops a captured graph. */
+int mpm_set_mpm_order(mpm_ctx* ctx, int order);
+
+/* The first-order local solves (order 1 only; MPM_ERR_STATE otherwise), for the stand-alone
+ * sequence mpm_perturbation_solve, mpm_interface_solve, mpm_perturbation_correction,
+ * mpm_interface_solve, mpm_downscale.  The interface solve after it solves the first-order
+ * interface problem; the one after mpm_perturbation_solve also forms delta p_0. */
+int mpm_perturbation_correction(mpm_ctx* ctx);
+
 /* Interface (skeleton) solve with the stored factorisation for the right-hand side of the
- * last mpm_build_basis or mpm_perturbation_solve, then the one-sided traces of every
+ * last mpm_build_basis, mpm_perturbation_solve or mpm_perturbation_correction, then the one-sided traces of every
  * subdomain (and, after a build, the MRCM-level pressure p^m).  The interface fluxes
  * u_bar are formed from these traces by mpm_downscale. */
 int mpm_interface_solve(mpm_ctx* ctx);
@@ -240,6 +261,27 @@ int mpm_step(mpm_ctx* ctx, double eta, double cfl, int n_sub);
 enum { MPM_EXEC_GRAPH = 1, MPM_EXEC_PDL = 4 };
 int mpm_set_execution(mpm_ctx* ctx, int flags);
 
+/* Launch shapes that depend on the geometry (the count and size of the subdomains against the
+ * GPU's SM count).  The values, in order (MPM_TUNE_N ints):
+ *   [0] threads per CTA of the MPM-2P local solve (64, 128 or 256)
+ *   [1] 1: that kernel stages the stored Robin factor in shared memory, 0: reads it from global
+ *       memory (smaller CTAs, more subdomains resident per SM)
+ *   [2], [3] the same for the downscaling solve
+ *   [4] rows (2, 4 or 8) of the 32-column cell tile of the fused transport kernel
+ * Defaults: 256, 1, 256, 1, 2.  mpm_get_tuning / mpm_set_tuning read and write them (n >=
+ * MPM_TUNE_N; invalid values: MPM_ERR_ARG); results do not depend on them beyond rounding.
+ * mpm_autotune times every candidate of each kernel on the context's current data (reps
+ * timed launches each, the median taken; 1 <= reps <= 100) and keeps the fastest.  It needs a
+ * stored basis (after mpm_init); it leaves the state of the current step as it was (it
+ * recomputes the downscaled fluxes and pressure of the last update from the same traces, equal
+ * up to refinement rounding), synchronises, and writes the best times (ms: transport, MPM-2P
+ * local solve, downscaling solve) to ms (host, 3 values) unless NULL.  Setting or tuning
+ * drops a captured graph. */
+enum { MPM_TUNE_N = 5 };
+int mpm_get_tuning(mpm_ctx* ctx, int* values, int n);
+int mpm_set_tuning(mpm_ctx* ctx, const int* values, int n);
+int mpm_autotune(mpm_ctx* ctx, int reps, double* ms);
+
 /* Copy out pressure [R][ny][nx] (which = MPM_P_*), fluxes ux [R][ny][nx+1],
  * uy [R][ny+1][nx], saturation [R][ny][nx] or conductivity kappa^n.  Synchronise. */
 int mpm_get_pressure(mpm_ctx* ctx, double* p, int which, int mem);
@@ -249,6 +291,15 @@ int mpm_get_conductivity(mpm_ctx* ctx, double* kappa, int mem);
 
 /* Counters (synchronises the stream and reports a pending MPM_ERR_NOT_CONVERGED). */
 int mpm_get_stats(mpm_ctx* ctx, mpm_stats* out);
+
+/* History of the dimensionless MPM-2P parameter (Section 4.1, Algorithm 1): for each of the
+ * last steps of mpm_step, the epsilon computed at its end (0 after a rebuild) and its
+ * decision (1 = basis rebuilt, 0 = MPM-2P update).  The device keeps the last
+ * MPM_EPS_HISTORY steps per realisation.  eps ([R][cap], host) and rebuilt ([R][cap], host,
+ * may be NULL) receive per realisation the k = min(steps so far, cap, MPM_EPS_HISTORY) most
+ * recent entries in chronological order (row stride cap); *n_out = k.  Synchronises. */
+enum { MPM_EPS_HISTORY = 4096 };
+int mpm_get_eps_history(mpm_ctx* ctx, double* eps, int* rebuilt, int cap, int* n_out);
 
 /* Synchronise the context's stream; returns a pending device-side status. */
 int mpm_sync(mpm_ctx* ctx);

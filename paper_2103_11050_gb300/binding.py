@@ -29,8 +29,10 @@ FUNCTIONS = [
     "mpm_perturbation_solve", "mpm_interface_solve", "mpm_downscale", "mpm_saturation_step",
     "mpm_init", "mpm_step", "mpm_get_pressure", "mpm_get_flux", "mpm_get_saturation",
     "mpm_get_conductivity", "mpm_get_stats", "mpm_sync", "mpm_profile_enable", "mpm_profile_read",
-    "mpm_set_execution", "mpm_cfl_dt_noalloc",
+    "mpm_set_execution", "mpm_cfl_dt_noalloc", "mpm_get_eps_history", "mpm_get_tuning", "mpm_set_tuning",
+    "mpm_autotune", "mpm_set_mpm_order", "mpm_perturbation_correction",
 ]
+TUNE_KEYS = ["local_threads", "local_stage", "ds_threads", "ds_stage", "transport_rows"]
 
 STAGES = ["transport", "epsilon", "basis", "iface_factor", "perturb", "iface_solve", "downscale", "iface_up",
           "iface_down", "reconstruct"]
@@ -77,7 +79,7 @@ def load(path: str | None = None):
         "mpm_set_source": ([P, P, I], I),
         "mpm_set_fluids": ([P, D], I),
         "mpm_set_boundary": ([P, IP, DP, D], I),
-        "mpm_set_decomposition": ([P, I, IP, I, IP, I, I, D], I),
+        "mpm_set_decomposition": ([P, I, IP, I, IP, I, I, D, P], I),
         "mpm_set_saturation": ([P, P, I], I),
         "mpm_build_basis": ([P], I),
         "mpm_eval_epsilon": ([P, DP], I),
@@ -98,6 +100,12 @@ def load(path: str | None = None):
         "mpm_set_execution": ([P, I], I),
         "mpm_cfl_dt_noalloc": ([P, P, I, I, I, D, D, D, P, P], I),
         "mpm_profile_read": ([P, DP, ctypes.POINTER(ctypes.c_longlong)], I),
+        "mpm_get_eps_history": ([P, DP, IP, I, IP], I),
+        "mpm_get_tuning": ([P, IP, I], I),
+        "mpm_set_tuning": ([P, IP, I], I),
+        "mpm_autotune": ([P, I, DP], I),
+        "mpm_set_mpm_order": ([P, I], I),
+        "mpm_perturbation_correction": ([P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -211,11 +219,19 @@ class Context:
         v = (ctypes.c_double * 4)(*[float(x) for x in vals])
         self._ck(self.L.mpm_set_boundary(self.h, t, v, float(s_inflow)))
 
-    def set_decomposition(self, col_w, row_h, seg_len=4, degree=1, alpha=1.0):
+    def set_decomposition(self, col_w, row_h, seg_len=4, degree=1, alpha=1.0, alpha_face=None):
+        """alpha_face: None, or (alpha_x [ny][nx+1], alpha_y [ny+1][nx]) per fine face."""
         cw = (ctypes.c_int * len(col_w))(*[int(v) for v in col_w])
         rh = (ctypes.c_int * len(row_h))(*[int(v) for v in row_h])
+        af = None
+        if alpha_face is not None:
+            ax = np.asarray(alpha_face[0], dtype=np.float64)
+            ay = np.asarray(alpha_face[1], dtype=np.float64)
+            if ax.shape != (self.ny, self.nx + 1) or ay.shape != (self.ny + 1, self.nx):
+                raise ValueError("alpha_face must be (alpha_x [ny][nx+1], alpha_y [ny+1][nx])")
+            af = np.ascontiguousarray(np.concatenate([ax.ravel(), ay.ravel()]))
         self._ck(self.L.mpm_set_decomposition(self.h, len(col_w), cw, len(row_h), rh, int(seg_len), int(degree),
-                                              float(alpha)))
+                                              float(alpha), None if af is None else ctypes.c_void_p(af.ctypes.data)))
 
     def set_saturation(self, s):
         p, mem = _ptr(s)
@@ -243,6 +259,12 @@ class Context:
 
     def perturbation_solve(self):
         self._ck(self.L.mpm_perturbation_solve(self.h))
+
+    def set_mpm_order(self, order):
+        self._ck(self.L.mpm_set_mpm_order(self.h, int(order)))
+
+    def perturbation_correction(self):
+        self._ck(self.L.mpm_perturbation_correction(self.h))
 
     def interface_solve(self):
         self._ck(self.L.mpm_interface_solve(self.h))
@@ -310,6 +332,32 @@ class Context:
         cnt = (ctypes.c_longlong * len(STAGES))()
         self._ck(self.L.mpm_profile_read(self.h, ms, cnt))
         return {name: (ms[i], cnt[i]) for i, name in enumerate(STAGES)}
+
+    def get_eps_history(self, cap=4096):
+        """(eps [R][k], rebuilt [R][k]) of the last k <= cap steps, oldest first."""
+        eps = np.zeros((self.R, cap))
+        reb = np.zeros((self.R, cap), dtype=np.int32)
+        n = ctypes.c_int(0)
+        self._ck(self.L.mpm_get_eps_history(self.h, eps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                            reb.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(cap),
+                                            ctypes.byref(n)))
+        return eps[:, :n.value].copy(), reb[:, :n.value].copy()
+
+    def get_tuning(self):
+        v = (ctypes.c_int * len(TUNE_KEYS))()
+        self._ck(self.L.mpm_get_tuning(self.h, v, len(TUNE_KEYS)))
+        return dict(zip(TUNE_KEYS, list(v)))
+
+    def set_tuning(self, tune):
+        v = (ctypes.c_int * len(TUNE_KEYS))(*[int(tune[k]) for k in TUNE_KEYS])
+        self._ck(self.L.mpm_set_tuning(self.h, v, len(TUNE_KEYS)))
+
+    def autotune(self, reps=5):
+        """Time every launch-shape candidate on this context's data and keep the fastest; returns
+        (tuning dict, best ms of transport / local solve / downscaling solve)."""
+        ms = (ctypes.c_double * 3)()
+        self._ck(self.L.mpm_autotune(self.h, int(reps), ms))
+        return self.get_tuning(), list(ms)
 
     def get_stats(self):
         st = Stats()

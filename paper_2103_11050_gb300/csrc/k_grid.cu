@@ -150,8 +150,9 @@ __global__ void k_upwind(Grid g, DevState d, double cfl, double fmax_) {
   }
 }
 
-constexpr int kTX = 32, kTY = 2;  // cell tile of the last transport substep (one cell per thread; small
-                                  // tiles spread the FP64 work evenly over the SMs)
+constexpr int kTX = 32;  // columns of the cell tile of the last transport substep (one cell per thread); its
+                        // rows kTY are a template parameter: small tiles spread the FP64 work over the SMs,
+                        // tall tiles recompute fewer halo cells
 
 // Last upwind substep fused with kappa^n (Algorithm 1: transport, then kappa^n): each CTA
 // updates a kTX x kTY tile plus its east column and north row, with kappa^n of each of these
@@ -162,6 +163,7 @@ constexpr int kTX = 32, kTY = 2;  // cell tile of the last transport substep (on
 // epsilon of the previous pass (rebuild_r = eps_r > eta), stores the new epsilon (0 where
 // the basis is rebuilt, else sqrt(num / den)), counts the branches and, in a CUDA graph
 // (set_handle), sets the conditional handle of the rebuild body.
+template <int kTY>
 __global__ void __launch_bounds__(kTX * kTY) k_upwind_kappa(Grid g, DevState d, double cfl, double fmax_, int decide,
                                                             double eta, cudaGraphConditionalHandle h_reb,
                                                             int set_handle) {
@@ -229,6 +231,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_upwind_kappa(Grid g, DevState d, 
   __threadfence();
   // one warp per realisation
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slot = (int)(__ldcg(d.hist_n) % kEpsHist);  // history slot of this decision
   int mine = 0;
   constexpr int kBatch = 8;  // partials loaded together before they are summed (same order)
   for (int rr = warp; rr < g.R; rr += blockDim.x >> 5) {
@@ -257,13 +260,17 @@ __global__ void __launch_bounds__(kTX * kTY) k_upwind_kappa(Grid g, DevState d, 
     if (lane == 0) {
       const int f = d.eps[rr] > eta ? 1 : 0;
       d.rebuild[rr] = f;
-      d.eps[rr] = f ? 0.0 : (b > 0.0 ? sqrt(a) / sqrt(b) : 0.0);
+      const double e = f ? 0.0 : (b > 0.0 ? sqrt(a) / sqrt(b) : 0.0);
+      d.eps[rr] = e;
+      d.eps_hist[(long long)rr * kEpsHist + slot] = e;
+      d.reb_hist[(long long)rr * kEpsHist + slot] = f;
       mine += f;
     }
   }
   if (lane == 0 && mine) atomicAdd(&tot, mine);
   __syncthreads();
   if (threadIdx.x == 0) {
+    d.hist_n[0] += 1;
     d.counts[0] += tot;
     d.counts[1] += g.R - tot;
     if (set_handle) {
@@ -350,12 +357,18 @@ void launch_upwind(const Grid& g, const DevState& d, double cfl, double fmax_, c
   ++g_launches;
 }
 
-int upwind_kappa_blocks(const Grid& g) { return ((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY); }
+int upwind_kappa_blocks_rows(const Grid& g, int rows) { return ((g.nx + kTX - 1) / kTX) * ((g.ny + rows - 1) / rows); }
+
+// the largest grid over the tile shapes (sizes the per-block partial sums)
+int upwind_kappa_blocks(const Grid& g) { return upwind_kappa_blocks_rows(g, 2); }
 
 void launch_upwind_kappa(const Grid& g, const DevState& d, double cfl, double fmax_, bool decide, double eta,
-                         cudaGraphConditionalHandle h_reb, bool set_handle, cudaStream_t st) {
-  k_upwind_kappa<<<dim3(upwind_kappa_blocks(g), g.R), kTX * kTY, 0, st>>>(g, d, cfl, fmax_, decide ? 1 : 0, eta,
-                                                                        h_reb, set_handle ? 1 : 0);
+                         cudaGraphConditionalHandle h_reb, bool set_handle, int rows, cudaStream_t st) {
+  const dim3 grid(upwind_kappa_blocks_rows(g, rows), g.R);
+  const int dec = decide ? 1 : 0, sh = set_handle ? 1 : 0;
+  if (rows >= 8) k_upwind_kappa<8><<<grid, kTX * 8, 0, st>>>(g, d, cfl, fmax_, dec, eta, h_reb, sh);
+  else if (rows >= 4) k_upwind_kappa<4><<<grid, kTX * 4, 0, st>>>(g, d, cfl, fmax_, dec, eta, h_reb, sh);
+  else k_upwind_kappa<2><<<grid, kTX * 2, 0, st>>>(g, d, cfl, fmax_, dec, eta, h_reb, sh);
   ++g_launches;
 }
 

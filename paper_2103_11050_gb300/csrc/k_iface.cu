@@ -371,7 +371,7 @@ constexpr int kKpt1 = 8;  // register-held terms per thread of the fused level-1
 
 template <int KS>
 __global__ void __launch_bounds__(256) k_reconstruct(Grid g, DevState d, const DevSub* subs, const DevNode* nodes,
-                                                     const int* leaf_node, const int* pmap, int branch) {
+                                                     const int* leaf_node, const int* pmap, int branch, int pass) {
   constexpr int FACES = 256 / KS;
   extern __shared__ __align__(16) double nd_smem[];
   __shared__ double red[32];
@@ -467,9 +467,22 @@ __global__ void __launch_bounds__(256) k_reconstruct(Grid g, DevState d, const D
     double sum = part[f];
 #pragma unroll
     for (int u = 1; u < KS; ++u) sum += part[u * FACES + f];
-    d.trace[(long long)r * d.st_face + sd.face_off + f] = fbar + sum;
+    (pass == 0 ? d.trace : d.trace1)[(long long)r * d.st_face + sd.face_off + f] = fbar + sum;
   }
   double pt = 0.0;
+  if (br == 0 && pass == 0 && g.order >= 1) {
+    // first-order MPM-2P: the MRCM-level pressure of the epsilon^0 solve, dp0 = dpbar + P_hat c
+    // (dpbar stored in dp0 by the local solve), the source of the first-order problem
+    const double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;
+    double* x = d.dp0 + (long long)r * g.ncell();
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+      const int jl = c / a, il = c - jl * a;
+      const long long gc = (long long)(sd.y0 + jl) * g.nx + sd.x0 + il;
+      double pv = x[gc];
+      for (int l = 0; l < nd; ++l) pv += pf[(long long)l * m + c] * cs[l];
+      x[gc] = pv;
+    }
+  }
   if (br == 1) {
     const double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;  // [nd + 1][m]
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
@@ -494,8 +507,10 @@ __global__ void __launch_bounds__(256) k_reconstruct(Grid g, DevState d, const D
     if (br == 1) {
       d.pm_mean[si] = s / m;
       d.sub_target[si] = s / m;
-    } else {
+    } else if (pass == 0) {
       d.sub_target[si] = d.pm_mean[si] + (d.sub_mean[si] * m + s) / m;
+    } else {  // the first-order term adds its own mean
+      d.sub_target[si] += (d.sub_mean[si] * m + s) / m;
     }
   }
 }
@@ -562,13 +577,13 @@ void launch_nd_down(const Grid& g, const DevState& d, const DevNode* nodes, cons
 }
 
 void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_face, int max_dof,
-                        int max_nf1, const DevNode* nodes, const int* leaf_node, const int* pmap, int branch, bool pdl,
-                        cudaStream_t st) {
+                        int max_nf1, const DevNode* nodes, const int* leaf_node, const int* pmap, int branch, int pass,
+                        bool pdl, cudaStream_t st) {
   const int faces = max_face <= 16 ? 16 : max_face <= 32 ? 32 : max_face <= 64 ? 64 : 128;
   const int ks = 256 / faces;
   const size_t smem = (size_t)(256 + (max_dof > 0 ? max_dof : 1) + max_nf1) * sizeof(double);
   MPM_DISPATCH_KS(k_reconstruct, ks, dim3(nsub, g.R), dim3(256), smem, st, pdl, g, d, subs, nodes, leaf_node, pmap,
-                  branch);
+                  branch, pass);
 }
 
 }  // namespace mpm

@@ -62,7 +62,7 @@ __device__ __forceinline__ void element_rhs(const Grid& g, const DevState& d, co
 }
 
 // u_bar on face t of side `side` of subdomain sd, oriented along +x / +y (Section 4.1,
-// u_bar = uhat_0 + delta u^n).  branch = 1 (after a basis build): the mean of the two
+// u_bar = uhat_0 + delta u^n; with g.order = 1 also the first-order term of Eq. mpm_tf_4).  branch = 1 (after a basis build): the mean of the two
 // one-sided MRCM traces on an interface, the trace itself on a physical side.  branch = 0
 // (after a perturbation solve): the same from the epsilon^0 traces, plus
 // F_n(p^m) = -kappa^n grad p^m.  Both subdomains of an interface face get bit-identical
@@ -94,11 +94,28 @@ __device__ __forceinline__ double ubar_face(const Grid& g, const DevState& d, co
       else { cn = c + nx; fi = (long long)(cj + 1) * nx + ci; }
       T = side < 2 ? d.tx[(long long)r * g.nfx() + fi] : d.ty[(long long)r * g.nfy() + fi];
       out = __dadd_rn(out, __dmul_rn(T, __dsub_rn(d.p_m[cb + c], d.p_m[cb + cn])));
+      if (g.order >= 1) {
+        // first-order term: the mean of the one-sided epsilon^1 traces plus
+        // (T^n - T^m)(dp0_c - dp0_nb), T^m the harmonic transmissibility of kappa^m (symmetric
+        // in its two cells, so both sides round identically)
+        const double F1o = d.trace1[(long long)r * d.st_face + sd.face_off + face_side_off(side, sd.a, sd.b) + t];
+        const double F1n = d.trace1[(long long)r * d.st_face + nb.face_off + face_side_off(opp, nb.a, nb.b) + t];
+        const double km0 = d.kap_m[cb + c], km1 = d.kap_m[cb + cn];
+        const double Tm = div64(2.0 * (km0 * km1), km0 + km1);
+        out = __dadd_rn(out, 0.5 * __dsub_rn(F1o, F1n));
+        out = __dadd_rn(out, __dmul_rn(__dsub_rn(T, Tm), __dsub_rn(d.dp0[cb + c], d.dp0[cb + cn])));
+      }
     }
   } else {
     out = Fo;
     // the perturbation traces carry homogeneous physical data; add F_n(p^m)
     if (branch == 0) out += phys_flux(g, side, d.kap_n[cb + c], d.p_m[cb + c]);
+    if (branch == 0 && g.order >= 1) {
+      // first-order term: its trace (homogeneous data) and, on a Dirichlet face,
+      // 2 (kappa^n - kappa^m)_c dp0_c
+      out += d.trace1[(long long)r * d.st_face + sd.face_off + face_side_off(side, sd.a, sd.b) + t];
+      if (g.bc_type[side] == 0) out += 2.0 * (d.kap_n[cb + c] - d.kap_m[cb + c]) * d.dp0[cb + c];
+    }
   }
   return (side == 0 || side == 2) ? -out : out;
 }

@@ -33,8 +33,6 @@ namespace mpm {
 namespace {
 
 constexpr int kSmemBudget = 200 * 1024;
-constexpr int kLocalThreads = 256;  // threads of the single-right-hand-side local kernels (two warps
-                                    // run the twisted chains, all of them the cell-parallel phases)
 
 // Asynchronous 16-byte global -> shared copies (cp.async), completed by cp_async_wait_all().
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
@@ -317,7 +315,7 @@ __device__ double basis_rhs(const Grid& g, const DevState& d, const DevSub& sd, 
                          (q == 3 && jl == b - 1);
     if (!on_side) return 0.0;
     const int t = (q < 2) ? jl : il;
-    const double rho = sd.side_rho[q];
+    const double rho = d.rho_f[sd.face_off + face_side_off(q, a, b) + t];
     const bool isU = col < d0 + nb;
     const double phi = side_basis(isU ? col - d0 : col - d0 - nb, t, g.seg_len, g.degree);
     // r_e g_e with r_e = kc/(1/2+rho): U: g = -(rho/kc) s phi -> -rho s phi/(1/2+rho); P: kc phi/(1/2+rho)
@@ -327,7 +325,7 @@ __device__ double basis_rhs(const Grid& g, const DevState& d, const DevSub& sd, 
 }
 
 // Robin datum g_e of basis column col on face f (0 for the non-homogeneous column).
-__device__ double basis_g(const Grid& g, const DevSub& sd, const Stencil& S, int f, int col) {
+__device__ double basis_g(const Grid& g, const DevState& d, const DevSub& sd, const Stencil& S, int f, int col) {
   if (col == sd.ndof) return 0.0;
   int side, t, cl;
   face_info(sd, f, side, t, cl);
@@ -336,16 +334,17 @@ __device__ double basis_g(const Grid& g, const DevSub& sd, const Stencil& S, int
   if (col < d0 || col >= d0 + 2 * nb) return 0.0;
   const bool isU = col < d0 + nb;
   const double phi = side_basis(isU ? col - d0 : col - d0 - nb, t, g.seg_len, g.degree);
-  return isU ? -div64(sd.side_rho[side], S.kap[cl]) * sd.side_sign[side] * phi : phi;
+  return isU ? -div64(d.rho_f[sd.face_off + f], S.kap[cl]) * sd.side_sign[side] * phi : phi;
 }
 
 // Outward trace on face f of the local solution x (column col of X) of basis column bcol.
-__device__ double basis_trace(const Grid& g, const DevSub& sd, const Stencil& S, const double* X, int ncol,
-                              int f, int col, int bcol, bool homogeneous_phys) {
+__device__ double basis_trace(const Grid& g, const DevState& d, const DevSub& sd, const Stencil& S, const double* X,
+                              int ncol, int f, int col, int bcol, bool homogeneous_phys) {
   int side, t, cl;
   face_info(sd, f, side, t, cl);
   const double kc = S.kap[cl], pc = X[cl * ncol + col];
-  if (sd.side_kind[side] == 1) return div64(kc, 0.5 + sd.side_rho[side]) * (pc - basis_g(g, sd, S, f, bcol));
+  if (sd.side_kind[side] == 1)
+    return div64(kc, 0.5 + d.rho_f[sd.face_off + f]) * (pc - basis_g(g, d, sd, S, f, bcol));
   if (g.bc_type[side] == 0) return 2.0 * kc * (pc - (homogeneous_phys ? 0.0 : g.bc_val[side]));
   return homogeneous_phys ? 0.0 : g.bc_val[side] * g.h;
 }
@@ -389,7 +388,7 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
     }
     for (int e = threadIdx.x; e < nface * ncol; e += blockDim.x) {
       const int f = e / ncol, col = e - f * ncol, bcol = c0 + col;
-      const double v = basis_trace(g, sd, cv.S, cv.X, ncol, f, col, bcol, bcol < sd.ndof);
+      const double v = basis_trace(g, d, sd, cv.S, cv.X, ncol, f, col, bcol, bcol < sd.ndof);
       if (bcol < sd.ndof) tr[(long long)bcol * nface + f] = v;
       else fbar[f] = v;
     }
@@ -442,7 +441,8 @@ __global__ void k_robin_factor_w(Grid g, DevState d, const DevSub* subs, int sca
     const int jl = c / sd.a, il = c - jl * sd.a;
     d.kap_m[(long long)r * g.ncell() + (long long)(sd.y0 + jl) * g.nx + sd.x0 + il] = t.kap[c];
   }
-  warp::build<T, A>(g, sd, t, d.tx + (long long)r * g.nfx(), d.ty + (long long)r * g.nfy(), 0, scale != 0);
+  warp::build<T, A>(g, sd, t, d.tx + (long long)r * g.nfx(), d.ty + (long long)r * g.nfy(), d.rho_f + sd.face_off,
+                    0, scale != 0);
   T* Qg = reinterpret_cast<T*>(d.fac) + (long long)r * d.st_fac + sd.q_off;
   warp::factor<T, A>(sd, t, Qg);
   double* tv = d.tvec + (long long)r * d.st_t + sd.t_off;
@@ -456,19 +456,25 @@ __global__ void k_robin_factor_w(Grid g, DevState d, const DevSub* subs, int sca
   for (int f = threadIdx.x; f < 2 * (sd.a + sd.b); f += blockDim.x) {
     int side, tt, cl;
     face_info(sd, f, side, tt, cl);
-    bh[f] = sd.side_kind[side] == 1 ? div64(sd.side_rho[side], t.kap[cl]) : 0.0;
+    bh[f] = sd.side_kind[side] == 1 ? div64(d.rho_f[sd.face_off + f], t.kap[cl]) : 0.0;
   }
 }
 
 // MPM-2P local solve: A_i(kappa^m) dp = r_i with zero Robin data and homogeneous physical
 // data, using the stored factor (staged into shared memory when qoff != 0, else read from
-// global memory), with r_i the fine residual q h^2 - sum_faces F(kappa^n, p^m) on the
-// subdomain's cells.  Outputs the perturbation traces (fbar), mean(dp) and the interface
-// right-hand side of the subdomain.
-template <typename T, int A>
-__global__ void __launch_bounds__(kLocalThreads) k_mpm_local_w(Grid g, DevState d, const DevSub* subs, size_t qoff,
-                                                               int refine, double tol, int ir_max,
-                                                               const DevNode* nodes, const int* leaf_node) {
+// global memory).  pass 0 (Eq. mpm_tf_3): r_i is the fine residual
+// q h^2 - sum_faces F(kappa^n, p^m) on the subdomain's cells; with store_x the local solution
+// is also written to dp0 (the reconstruction adds the BF combination to it).  pass 1 (Eq.
+// mpm_tf_4, l = 1): r_i = -(A(kappa^n) - A(kappa^m)) dp0 with homogeneous data, dp0 the
+// MRCM-level pressure of the epsilon^0 solve: minus the sum over the cell's faces of
+// (T^n - T^m)(dp0_c - dp0_nb) (harmonic transmissibilities; the neighbour across an
+// interface from its own subdomain) and, on Dirichlet faces, 2 (kappa^n - kappa^m)_c dp0_c.
+// Outputs the perturbation traces (fbar), mean(dp) and the interface right-hand side of the
+// subdomain.
+template <typename T, int A, int NT>
+__global__ void __launch_bounds__(NT) k_mpm_local_w(Grid g, DevState d, const DevSub* subs, size_t qoff,
+                                                    int refine, double tol, int ir_max, const DevNode* nodes,
+                                                    const int* leaf_node, int pass, int store_x) {
   extern __shared__ __align__(16) char smem[];
   __shared__ double red[64];
   __shared__ double fb[4 * kMaxSide];
@@ -503,18 +509,43 @@ __global__ void __launch_bounds__(kLocalThreads) k_mpm_local_w(Grid g, DevState 
     t.wE[c] = tv[m + c];
     t.wN[c] = tv[2 * m + c];
     t.sc[c] = tv[3 * m + c];
-    // fine residual r_c = q_c h^2 - sum_faces F_out(kappa^n, p^m)
-    const double kc = d.kap_n[cb + gc], pc = pm[gc];
-    double out = 0.0;
-    if (i > 0) out += tx[(long long)j * (nx + 1) + i] * (pc - pm[gc - 1]);
-    else out += phys_flux(g, 0, kc, pc);
-    if (i < nx - 1) out += tx[(long long)j * (nx + 1) + i + 1] * (pc - pm[gc + 1]);
-    else out += phys_flux(g, 1, kc, pc);
-    if (j > 0) out += ty[gc] * (pc - pm[gc - nx]);
-    else out += phys_flux(g, 2, kc, pc);
-    if (j < ny - 1) out += ty[gc + nx] * (pc - pm[gc + nx]);
-    else out += phys_flux(g, 3, kc, pc);
-    t.B[c] = d.q[cb + gc] * g.h * g.h - out;
+    const double kc = d.kap_n[cb + gc];
+    if (pass == 0) {
+      // fine residual r_c = q_c h^2 - sum_faces F_out(kappa^n, p^m)
+      const double pc = pm[gc];
+      double out = 0.0;
+      if (i > 0) out += tx[(long long)j * (nx + 1) + i] * (pc - pm[gc - 1]);
+      else out += phys_flux(g, 0, kc, pc);
+      if (i < nx - 1) out += tx[(long long)j * (nx + 1) + i + 1] * (pc - pm[gc + 1]);
+      else out += phys_flux(g, 1, kc, pc);
+      if (j > 0) out += ty[gc] * (pc - pm[gc - nx]);
+      else out += phys_flux(g, 2, kc, pc);
+      if (j < ny - 1) out += ty[gc + nx] * (pc - pm[gc + nx]);
+      else out += phys_flux(g, 3, kc, pc);
+      t.B[c] = d.q[cb + gc] * g.h * g.h - out;
+    } else {
+      // r_c = -sum_faces (T^n - T^m)(x_c - x_nb) - Dirichlet 2 (kappa^n - kappa^m)_c x_c, x = dp0
+      const double* x = d.dp0 + cb;
+      const double* km = d.kap_m + cb;
+      const double xc = x[gc], kmc = km[gc];
+      double out = 0.0;
+      auto face = [&](double Tn, long long nb) {
+        const double kmn = km[nb];
+        out += (Tn - div64(2.0 * kmc * kmn, kmc + kmn)) * (xc - x[nb]);
+      };
+      auto phys = [&](int side) {
+        if (g.bc_type[side] == 0) out += 2.0 * (kc - kmc) * xc;
+      };
+      if (i > 0) face(tx[(long long)j * (nx + 1) + i], gc - 1);
+      else phys(0);
+      if (i < nx - 1) face(tx[(long long)j * (nx + 1) + i + 1], gc + 1);
+      else phys(1);
+      if (j > 0) face(ty[gc], gc - nx);
+      else phys(2);
+      if (j < ny - 1) face(ty[gc + nx], gc + nx);
+      else phys(3);
+      t.B[c] = -out;
+    }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < b * A; e += blockDim.x) {
@@ -524,6 +555,11 @@ __global__ void __launch_bounds__(kLocalThreads) k_mpm_local_w(Grid g, DevState 
   if (qoff != 0) cp_async_wait_all();
   __syncthreads();
   warp::solve_refined<T, A>(sd, t, Q, refine != 0, tol, ir_max, d.status, d.ir_iters, red);
+  if (store_x)
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+      const int jl = c / a, il = c - jl * a;
+      d.dp0[cb + (long long)(sd.y0 + jl) * nx + sd.x0 + il] = t.X[c];
+    }
   double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
   const int nface = 2 * (a + b);
   for (int f = threadIdx.x; f < nface; f += blockDim.x) {
@@ -531,7 +567,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_mpm_local_w(Grid g, DevState 
     face_info(sd, f, side, tt, cl);
     const double kc = t.kap[cl], pc = t.X[cl];
     double v;
-    if (sd.side_kind[side] == 1) v = div64(kc, 0.5 + sd.side_rho[side]) * pc;
+    if (sd.side_kind[side] == 1) v = div64(kc, 0.5 + d.rho_f[sd.face_off + f]) * pc;
     else v = g.bc_type[side] == 0 ? 2.0 * kc * pc : 0.0;
     fbar[f] = v;
     fb[f] = v;
@@ -563,7 +599,8 @@ __global__ void k_downscale_factor_w(Grid g, DevState d, const DevSub* subs, int
   const int m = sd.a * sd.b;
   warp::Tables<T> t = warp::carve<T, A>(smem, m, sd.b);
   load_kappa_cta(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap);
-  warp::build<T, A>(g, sd, t, d.tx + (long long)r * g.nfx(), d.ty + (long long)r * g.nfy(), 1, scale != 0);
+  warp::build<T, A>(g, sd, t, d.tx + (long long)r * g.nfx(), d.ty + (long long)r * g.nfy(), d.rho_f + sd.face_off,
+                    1, scale != 0);
   warp::factor<T, A>(sd, t, reinterpret_cast<T*>(d.nfac) + (long long)r * d.st_fac + sd.q_off);
   double* tv = d.ntvec + (long long)r * d.st_t + sd.t_off;
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
@@ -582,8 +619,8 @@ __global__ void k_downscale_factor_w(Grid g, DevState d, const DevSub* subs, int
 // maximum over its cells of max(total outflow, total inflow); the last block to finish
 // reduces these maxima per realisation into rate_max (CFL step).  The factor and stencil
 // are loaded before pdl_wait() (they come from a stream joined before the launch).
-template <typename T, int A>
-__global__ void __launch_bounds__(kLocalThreads) k_downscale_w(Grid g, DevState d, const DevSub* subs, size_t qoff,
+template <typename T, int A, int NT>
+__global__ void __launch_bounds__(NT) k_downscale_w(Grid g, DevState d, const DevSub* subs, size_t qoff,
                                                                int refine, double tol, int ir_max) {
   extern __shared__ __align__(16) char smem[];
   __shared__ double red[64];
@@ -750,19 +787,31 @@ void robin_factor_t(const Grid& g, const DevState& d, const DevSub* subs, int ns
   ++g_launches;
 }
 
-template <typename T, int A>
-void mpm_local_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b, int refine,
-                 double tol, int ir_max, const DevNode* nodes, const int* leaf_node, cudaStream_t st) {
+template <typename T, int A, int NT>
+void mpm_local_nt(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b, int refine,
+                  double tol, int ir_max, const DevNode* nodes, const int* leaf_node, int stage, int pass,
+                  cudaStream_t st) {
   size_t bytes, qoff;
-  pair_geometry<T, A>(max_a, max_b, true, bytes, qoff);  // stored factor staged in shared memory ...
-  if (bytes > (size_t)kSmemBudget) {                      // ... unless it does not fit: read from global
+  pair_geometry<T, A>(max_a, max_b, stage != 0, bytes, qoff);  // stored factor staged in shared memory ...
+  if (stage == 0 || bytes > (size_t)kSmemBudget) {              // ... or read from global memory
     pair_geometry<T, A>(max_a, max_b, false, bytes, qoff);
     qoff = 0;
   }
-  set_smem(k_mpm_local_w<T, A>, bytes);
-  k_mpm_local_w<T, A><<<dim3(nsub, g.R), kLocalThreads, bytes, st>>>(g, d, subs, qoff, refine, tol, ir_max, nodes,
-                                                                      leaf_node);
+  set_smem(k_mpm_local_w<T, A, NT>, bytes);
+  k_mpm_local_w<T, A, NT><<<dim3(nsub, g.R), NT, bytes, st>>>(g, d, subs, qoff, refine, tol, ir_max, nodes, leaf_node,
+                                                               pass, pass == 0 && g.order >= 1 ? 1 : 0);
   ++g_launches;
+}
+
+template <typename T, int A>
+void mpm_local_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b, int refine,
+                 double tol, int ir_max, const DevNode* nodes, const int* leaf_node, int threads, int stage, int pass,
+                 cudaStream_t st) {
+  if (threads <= 64)
+    mpm_local_nt<T, A, 64>(g, d, subs, nsub, max_a, max_b, refine, tol, ir_max, nodes, leaf_node, stage, pass, st);
+  else if (threads <= 128)
+    mpm_local_nt<T, A, 128>(g, d, subs, nsub, max_a, max_b, refine, tol, ir_max, nodes, leaf_node, stage, pass, st);
+  else mpm_local_nt<T, A, 256>(g, d, subs, nsub, max_a, max_b, refine, tol, ir_max, nodes, leaf_node, stage, pass, st);
 }
 
 template <typename T, int A>
@@ -775,18 +824,25 @@ void downscale_factor_t(const Grid& g, const DevState& d, const DevSub* subs, in
   ++g_launches;
 }
 
-template <typename T, int A>
-void downscale_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b, int refine,
-                 double tol, int ir_max, bool pdl, cudaStream_t st) {
+template <typename T, int A, int NT>
+void downscale_nt(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b, int refine,
+                  double tol, int ir_max, bool pdl, int stage, cudaStream_t st) {
   size_t bytes, qoff;
-  pair_geometry<T, A>(max_a, max_b, true, bytes, qoff);
-  if (bytes > (size_t)kSmemBudget) {  // factor too large for shared memory: read from global
+  pair_geometry<T, A>(max_a, max_b, stage != 0, bytes, qoff);
+  if (stage == 0 || bytes > (size_t)kSmemBudget) {  // factor read from global memory
     pair_geometry<T, A>(max_a, max_b, false, bytes, qoff);
     qoff = 0;
   }
-  set_smem(k_downscale_w<T, A>, bytes);
-  launch_ex(k_downscale_w<T, A>, dim3(nsub, g.R), dim3(kLocalThreads), bytes, st, pdl, g, d, subs, qoff, refine, tol,
-            ir_max);
+  set_smem(k_downscale_w<T, A, NT>, bytes);
+  launch_ex(k_downscale_w<T, A, NT>, dim3(nsub, g.R), dim3(NT), bytes, st, pdl, g, d, subs, qoff, refine, tol, ir_max);
+}
+
+template <typename T, int A>
+void downscale_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b, int refine,
+                 double tol, int ir_max, bool pdl, int threads, int stage, cudaStream_t st) {
+  if (threads <= 64) downscale_nt<T, A, 64>(g, d, subs, nsub, max_a, max_b, refine, tol, ir_max, pdl, stage, st);
+  else if (threads <= 128) downscale_nt<T, A, 128>(g, d, subs, nsub, max_a, max_b, refine, tol, ir_max, pdl, stage, st);
+  else downscale_nt<T, A, 256>(g, d, subs, nsub, max_a, max_b, refine, tol, ir_max, pdl, stage, st);
 }
 
 }  // namespace
@@ -828,10 +884,14 @@ void launch_basis_solve(const Grid& g, const DevState& d, const DevSub* subs, in
 }
 
 void launch_mpm_local(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
-                      bool fp32, double ir_tol, int ir_max, const DevNode* nodes, const int* leaf_node,
-                      cudaStream_t st) {
-  if (fp32) MPM_DISPATCH_A(mpm_local_t, float, g, d, subs, nsub, max_a, max_b, 1, ir_tol, ir_max, nodes, leaf_node, st);
-  else MPM_DISPATCH_A(mpm_local_t, double, g, d, subs, nsub, max_a, max_b, 0, ir_tol, ir_max, nodes, leaf_node, st);
+                      bool fp32, double ir_tol, int ir_max, const DevNode* nodes, const int* leaf_node, int threads,
+                      int stage, int pass, cudaStream_t st) {
+  if (fp32)
+    MPM_DISPATCH_A(mpm_local_t, float, g, d, subs, nsub, max_a, max_b, 1, ir_tol, ir_max, nodes, leaf_node, threads,
+                   stage, pass, st);
+  else
+    MPM_DISPATCH_A(mpm_local_t, double, g, d, subs, nsub, max_a, max_b, 0, ir_tol, ir_max, nodes, leaf_node, threads,
+                   stage, pass, st);
 }
 
 void launch_downscale_factor(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
@@ -841,9 +901,9 @@ void launch_downscale_factor(const Grid& g, const DevState& d, const DevSub* sub
 }
 
 void launch_downscale(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
-                      bool fp32, double ir_tol, int ir_max, bool pdl, cudaStream_t st) {
-  if (fp32) MPM_DISPATCH_A(downscale_t, float, g, d, subs, nsub, max_a, max_b, 1, ir_tol, ir_max, pdl, st);
-  else MPM_DISPATCH_A(downscale_t, double, g, d, subs, nsub, max_a, max_b, 0, ir_tol, ir_max, pdl, st);
+                      bool fp32, double ir_tol, int ir_max, bool pdl, int threads, int stage, cudaStream_t st) {
+  if (fp32) MPM_DISPATCH_A(downscale_t, float, g, d, subs, nsub, max_a, max_b, 1, ir_tol, ir_max, pdl, threads, stage, st);
+  else MPM_DISPATCH_A(downscale_t, double, g, d, subs, nsub, max_a, max_b, 0, ir_tol, ir_max, pdl, threads, stage, st);
 }
 
 }  // namespace mpm

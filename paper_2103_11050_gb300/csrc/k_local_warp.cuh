@@ -75,11 +75,12 @@ __device__ Tables<T> carve(char* base, int m, int b) {
 }
 
 // FP64 stencil of the Robin (neumann = 0) or pinned Neumann (neumann = 1) operator of
-// kappa^n (transmissibilities tx / ty of the current kappa^n, r-th realisation pointers),
-// and the scaled T tables.  kap must already hold the subdomain's kappa^n.
+// kappa^n (transmissibilities tx / ty of the current kappa^n, r-th realisation pointers;
+// rho: the subdomain's per-face rho_e = alpha_e H_e / h), and the scaled T tables.  kap must
+// already hold the subdomain's kappa^n.
 template <typename T, int A>
 __device__ void build(const Grid& g, const DevSub& sd, Tables<T> t, const double* tx, const double* ty,
-                      int neumann, bool scale) {
+                      const double* rho, int neumann, bool scale) {
   const int a = sd.a, b = sd.b, m = a * b;
   const int lane = threadIdx.x;
   for (int c = lane; c < m; c += blockDim.x) {
@@ -90,10 +91,12 @@ __device__ void build(const Grid& g, const DevSub& sd, Tables<T> t, const double
     t.wN[c] = jl < b - 1 ? ty[(long long)(j + 1) * g.nx + i] : 0.0;
     double dg = 0.0;
     if (!neumann) {
-      if (il == 0) dg += sd.side_kind[0] == 1 ? div64(kc, 0.5 + sd.side_rho[0]) : (g.bc_type[0] == 0 ? 2.0 * kc : 0.0);
-      if (il == a - 1) dg += sd.side_kind[1] == 1 ? div64(kc, 0.5 + sd.side_rho[1]) : (g.bc_type[1] == 0 ? 2.0 * kc : 0.0);
-      if (jl == 0) dg += sd.side_kind[2] == 1 ? div64(kc, 0.5 + sd.side_rho[2]) : (g.bc_type[2] == 0 ? 2.0 * kc : 0.0);
-      if (jl == b - 1) dg += sd.side_kind[3] == 1 ? div64(kc, 0.5 + sd.side_rho[3]) : (g.bc_type[3] == 0 ? 2.0 * kc : 0.0);
+      // rho of this cell's face on each side (face numbering: left, right, bottom, top)
+      if (il == 0) dg += sd.side_kind[0] == 1 ? div64(kc, 0.5 + rho[jl]) : (g.bc_type[0] == 0 ? 2.0 * kc : 0.0);
+      if (il == a - 1) dg += sd.side_kind[1] == 1 ? div64(kc, 0.5 + rho[b + jl]) : (g.bc_type[1] == 0 ? 2.0 * kc : 0.0);
+      if (jl == 0) dg += sd.side_kind[2] == 1 ? div64(kc, 0.5 + rho[2 * b + il]) : (g.bc_type[2] == 0 ? 2.0 * kc : 0.0);
+      if (jl == b - 1)
+        dg += sd.side_kind[3] == 1 ? div64(kc, 0.5 + rho[2 * b + a + il]) : (g.bc_type[3] == 0 ? 2.0 * kc : 0.0);
     } else if (c == 0) {
       dg += kc;  // pin: A + kappa_0 e_0 e_0^T
     }

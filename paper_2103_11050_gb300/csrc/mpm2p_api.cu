@@ -65,6 +65,8 @@ struct mpm_ctx {
   // CUDA graph of one Algorithm 1 step (conditional bodies for the two branches)
   bool use_graph = true;
   bool use_pdl = true;    // programmatic dependent launch along the interface-solve chain
+  Tuning tune;            // launch shapes (defaults, mpm_set_tuning or mpm_autotune)
+  int next_pass = 0;      // pass of the next stand-alone interface solve (1 after mpm_perturbation_correction)
   // The saturation (and f(s)) live in two buffers that swap at every transport substep; a
   // graph reads and writes fixed buffers, so one graph is kept per buffer parity (slot 0:
   // the current saturation is in s_buf0).
@@ -371,13 +373,17 @@ int run_build(mpm_ctx* c) {
   return check_launch(c);
 }
 
-int run_perturbation(mpm_ctx* c) {
+// MPM-2P local solves: pass 0 the epsilon^0 problem (Eq. mpm_tf_3), pass 1 the first-order
+// problem (Eq. mpm_tf_4, l = 1; needs the reconstruction of pass 0).  The interface solve
+// that follows uses the same pass.
+int run_perturbation(mpm_ctx* c, int pass = 0) {
   const Grid& g = c->g;
   const int nsub = (int)c->subs.size();
   prof_begin(c, MPM_STAGE_PERTURB);
   launch_mpm_local(g, c->d, c->d_subs, nsub, c->max_a, c->max_b, c->fac_prec == MPM_PREC_FP32_IR_ALL, c->ir_tol,
-                   c->ir_max, c->d_nodes, c->d_leaf_node, c->stream);
+                   c->ir_max, c->d_nodes, c->d_leaf_node, c->tune.local_threads, c->tune.local_stage, pass, c->stream);
   prof_end(c, MPM_STAGE_PERTURB);
+  c->next_pass = pass;
   return check_launch(c);
 }
 
@@ -385,7 +391,7 @@ int run_perturbation(mpm_ctx* c) {
 // The first sweep kernel is fully ordered after what precedes it; the rest of the chain
 // (and the downscaling after it, see run_downscale) uses programmatic dependent launch when
 // enabled.
-int run_interface(mpm_ctx* c) {
+int run_interface(mpm_ctx* c, int pass = 0) {
   const Grid& g = c->g;
   DevState& d = c->d;
   cudaStream_t st = c->stream;
@@ -412,8 +418,9 @@ int run_interface(mpm_ctx* c) {
     prof_end(c, MPM_STAGE_IFACE_DOWN);
   }
   prof_begin(c, MPM_STAGE_RECONSTRUCT);
+  // the first-order pass concerns the MPM-2P realisations only (branch 0)
   launch_reconstruct(g, d, c->d_subs, nsub, c->max_face, c->max_dof, c->levels.size() > 1 ? c->lev_max_nf[1] : 0,
-                     c->d_nodes, c->d_leaf_node, c->d_pmap, -1, chained && c->use_pdl, st);
+                     c->d_nodes, c->d_leaf_node, c->d_pmap, pass == 0 ? -1 : 0, pass, chained && c->use_pdl, st);
   prof_end(c, MPM_STAGE_RECONSTRUCT);
   prof_end(c, MPM_STAGE_IFACE_SOLVE);
   return check_launch(c);
@@ -459,7 +466,7 @@ int run_downscale(mpm_ctx* c, bool after_interface, bool forked) {
     launch_downscale_factor(c->g, c->d, c->d_subs, (int)c->subs.size(), c->max_a, c->max_b, fp32(c), c->stream);
   }
   launch_downscale(c->g, c->d, c->d_subs, (int)c->subs.size(), c->max_a, c->max_b, fp32(c), c->ir_tol, c->ir_max,
-                   after_interface && joined_before && c->use_pdl, c->stream);
+                   after_interface && joined_before && c->use_pdl, c->tune.ds_threads, c->tune.ds_stage, c->stream);
   prof_end(c, MPM_STAGE_DOWNSCALE);
   return check_launch(c);
 }
@@ -473,7 +480,7 @@ int run_transport(mpm_ctx* c, double cfl, int n_sub, bool decide, double eta, cu
   const double fmax_ = max_fprime(c->g.M);
   for (int k = 0; k < n_sub; ++k) {
     if (k + 1 < n_sub) launch_upwind(c->g, c->d, cfl, fmax_, c->stream);
-    else launch_upwind_kappa(c->g, c->d, cfl, fmax_, decide, eta, h_reb, set_handle, c->stream);
+    else launch_upwind_kappa(c->g, c->d, cfl, fmax_, decide, eta, h_reb, set_handle, c->tune.transport_rows, c->stream);
     std::swap(c->d.s, c->d.s2);
     std::swap(c->d.fs, c->d.fs2);
   }
@@ -580,6 +587,10 @@ int build_step_graph(mpm_ctx* c, double eta, double cfl, int n_sub) {
   if (!rc) rc = run_perturbation(c);
   Lb[2] = Lb[1];
   if (!rc) rc = run_interface(c);
+  if (!rc && c->g.order >= 1) {  // first-order term (its kernels skip rebuilding realisations)
+    rc = run_perturbation(c, 1);
+    if (!rc) rc = run_interface(c, 1);
+  }
   if (!rc) rc = run_downscale(c, true, true);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &graph);
@@ -645,10 +656,11 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   g.seg_len = 1;
   g.degree = 0;
   g.alpha = 1.0;
+  g.order = 0;
   const size_t nc = (size_t)R * nx * ny;
   DevState& d = c->d;
   int rc = MPM_OK;
-  double** cells[] = {&d.K, &d.q, &d.s, &d.s2, &d.kap_n, &d.kap_m, &d.p_m, &d.p_down, &d.fs, &d.fs2, &d.x_ds};
+  double** cells[] = {&d.K, &d.q, &d.s, &d.s2, &d.kap_n, &d.kap_m, &d.p_m, &d.p_down, &d.fs, &d.fs2, &d.x_ds, &d.dp0};
   for (double** p : cells)
     if ((rc = dalloc_t(c, c->grid_allocs, p, nc)) != MPM_OK) break;
   c->s_buf0 = d.s;
@@ -665,6 +677,9 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.status, 2);  // status word, then the sweep count
   if (rc == MPM_OK) d.ir_iters = d.status + 1;
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.counts, 4);
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.eps_hist, (size_t)R * kEpsHist);
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.reb_hist, (size_t)R * kEpsHist);
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.hist_n, 1);
   if (rc == MPM_OK && (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
                        cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking) != cudaSuccess ||
                        cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -783,7 +798,7 @@ int mpm_set_boundary(mpm_ctx* c, const int type[4], const double val[4], double 
 }
 
 int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const int* row_h, int seg_len, int degree,
-                          double alpha) {
+                          double alpha, const double* alpha_face) {
   if (!c) return MPM_ERR_ARG;
   if (ncx < 1 || ncy < 1 || !col_w || !row_h) return fail(c, MPM_ERR_ARG, "bad decomposition arrays");
   if (seg_len < 1 || (degree != 0 && degree != 1) || !(alpha > 0) || !std::isfinite(alpha))
@@ -800,6 +815,23 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
     sy += row_h[J];
   }
   if (sx != c->g.nx || sy != c->g.ny) return fail(c, MPM_ERR_ARG, "widths/heights must sum to nx/ny");
+  // alpha per interface face (x faces [ny][nx+1], then y faces [ny+1][nx]); checked on the
+  // interface faces, the only ones read
+  const long long nfx = (long long)c->g.ny * (c->g.nx + 1);
+  auto alpha_at = [&](bool xface, int j, int i) {
+    if (!alpha_face) return alpha;
+    return xface ? alpha_face[(long long)j * (c->g.nx + 1) + i] : alpha_face[nfx + (long long)j * c->g.nx + i];
+  };
+  if (alpha_face) {
+    for (int I = 1, x = col_w[0]; I < ncx; x += col_w[I], ++I)
+      for (int j = 0; j < c->g.ny; ++j)
+        if (!(alpha_at(true, j, x) > 0) || !std::isfinite(alpha_at(true, j, x)))
+          return fail(c, MPM_ERR_ARG, "alpha must be positive and finite on interface x-face (%d, %d)", x, j);
+    for (int J = 1, y = row_h[0]; J < ncy; y += row_h[J], ++J)
+      for (int i = 0; i < c->g.nx; ++i)
+        if (!(alpha_at(false, y, i) > 0) || !std::isfinite(alpha_at(false, y, i)))
+          return fail(c, MPM_ERR_ARG, "alpha must be positive and finite on interface y-face (%d, %d)", i, y);
+  }
   release_decomposition(c);
   c->ncx = ncx;
   c->ncy = ncy;
@@ -832,6 +864,7 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   int dof_off = 0, face_off = 0, cell_off = 0;
   c->max_a = c->max_b = c->max_dof = c->max_face = 0;
   c->n_hat = 0;
+  std::vector<double> rho_host;  // per subdomain face, in face order (left, right, bottom, top)
   for (int J = 0; J < ncy; ++J) {
     for (int I = 0; I < ncx; ++I) {
       DevSub& s = c->subs[J * ncx + I];
@@ -849,17 +882,25 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
         s.side_iface[q] = ids[q];
         s.side_nbr[q] = nbr[q];
         s.side_sign[q] = sgn[q];
+        const int len = q < 2 ? s.b : s.a;
         if (ids[q] >= 0) {
           s.side_kind[q] = 1;
           s.side_dof0[q] = nd;
           s.side_nb[q] = ifs[ids[q]].nb;
-          s.side_rho[q] = alpha * ifs[ids[q]].L;
           nd += 2 * ifs[ids[q]].nb;
+          // rho_e = alpha_e H_e / h of each face of the side (H_e: the interface length)
+          for (int t = 0; t < len; ++t) {
+            const double ae = q == 0   ? alpha_at(true, s.y0 + t, s.x0)
+                              : q == 1 ? alpha_at(true, s.y0 + t, s.x0 + s.a)
+                              : q == 2 ? alpha_at(false, s.y0, s.x0 + t)
+                                       : alpha_at(false, s.y0 + s.b, s.x0 + t);
+            rho_host.push_back(ae * ifs[ids[q]].L);
+          }
         } else {
           s.side_kind[q] = 0;
           s.side_dof0[q] = nd;
           s.side_nb[q] = 0;
-          s.side_rho[q] = 0.0;
+          for (int t = 0; t < len; ++t) rho_host.push_back(0.0);
         }
       }
       s.ndof = nd;
@@ -987,7 +1028,9 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   if (!rc) rc = dalloc_t(c, A, &d.mu_hat, (size_t)R * dof_off);
   if (!rc) rc = dalloc_t(c, A, &d.fbar, (size_t)R * face_off);
   if (!rc) rc = dalloc_t(c, A, &d.trace, (size_t)R * face_off);
+  if (!rc) rc = dalloc_t(c, A, &d.trace1, (size_t)R * face_off);
   if (!rc) rc = dalloc_t(c, A, &d.bhat, (size_t)R * face_off);
+  if (!rc) rc = dalloc_t(c, A, &d.rho_f, (size_t)face_off);
   if (!rc) rc = dalloc_t(c, A, &d.sub_mean, (size_t)R * nsub);
   if (!rc) rc = dalloc_t(c, A, &d.sub_target, (size_t)R * nsub);
   if (!rc) rc = dalloc_t(c, A, &d.pm_mean, (size_t)R * nsub);
@@ -1009,6 +1052,7 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
     return rc;
   }
   CK(cudaMemcpyAsync(c->d_subs, c->subs.data(), nsub * sizeof(DevSub), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(d.rho_f, rho_host.data(), rho_host.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->d_nodes, c->nodes.data(), nn * sizeof(DevNode), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->d_leaf_node, c->leaf_node.data(), nsub * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->d_level_nodes, level_nodes.data(), level_nodes.size() * sizeof(int), cudaMemcpyHostToDevice,
@@ -1097,11 +1141,30 @@ int mpm_perturbation_solve(mpm_ctx* c) {
   return run_perturbation(c);
 }
 
+int mpm_perturbation_correction(mpm_ctx* c) {
+  if (!c) return MPM_ERR_ARG;
+  int rc = need_ready(c, true);
+  if (rc) return rc;
+  if (c->g.order < 1) return fail(c, MPM_ERR_STATE, "the first-order term needs mpm_set_mpm_order(ctx, 1)");
+  launch_fill_flags(c->g, c->d, 0, c->stream);
+  return run_perturbation(c, 1);
+}
+
+int mpm_set_mpm_order(mpm_ctx* c, int order) {
+  if (!c) return MPM_ERR_ARG;
+  if (order != 0 && order != 1) return fail(c, MPM_ERR_ARG, "order must be 0 or 1");
+  c->g.order = order;
+  drop_graph(c);
+  return MPM_OK;
+}
+
 int mpm_interface_solve(mpm_ctx* c) {
   if (!c) return MPM_ERR_ARG;
   int rc = need_ready(c, true);
   if (rc) return rc;
-  return run_interface(c);
+  const int pass = c->next_pass;
+  c->next_pass = 0;
+  return run_interface(c, pass);
 }
 
 int mpm_downscale(mpm_ctx* c) {
@@ -1168,6 +1231,10 @@ int mpm_step(mpm_ctx* c, double eta, double cfl, int n_sub) {
   if (nreb > 0 && (rc = run_build(c))) return rc;
   if (nreb < c->g.R && (rc = run_perturbation(c))) return rc;
   if ((rc = run_interface(c))) return rc;
+  if (nreb < c->g.R && c->g.order >= 1) {
+    if ((rc = run_perturbation(c, 1))) return rc;
+    if ((rc = run_interface(c, 1))) return rc;
+  }
   if ((rc = run_downscale(c, true, true))) return rc;
   c->stats.steps += 1;
   return check_launch(c);
@@ -1222,6 +1289,147 @@ int mpm_get_stats(mpm_ctx* c, mpm_stats* out) {
   c->stats.kernel_launches = g_launches - c->launches0 - c->capture_launches + c->graph_steps * c->gk_base +
                              cnt[2] * c->gk_reb + cnt[3] * c->gk_mpm;
   *out = c->stats;
+  return rc;
+}
+
+int mpm_get_eps_history(mpm_ctx* c, double* eps, int* rebuilt, int cap, int* n_out) {
+  if (!c || !n_out) return MPM_ERR_ARG;
+  if (cap < 0 || (cap > 0 && !eps)) return fail(c, MPM_ERR_ARG, "need cap >= 0 and an eps array");
+  int rc = sync_status(c);
+  long long n = 0;
+  CK(cudaMemcpy(&n, c->d.hist_n, sizeof(n), cudaMemcpyDeviceToHost));
+  const int R = c->g.R;
+  const long long k = std::min<long long>(std::min<long long>(n, cap), kEpsHist);
+  std::vector<double> eh((size_t)R * kEpsHist);
+  std::vector<int> rh((size_t)R * kEpsHist);
+  CK(cudaMemcpy(eh.data(), c->d.eps_hist, eh.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(rh.data(), c->d.reb_hist, rh.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  for (int r = 0; r < R; ++r)
+    for (long long q = 0; q < k; ++q) {
+      const long long step = n - k + q;  // chronological: the oldest of the k kept decisions first
+      const size_t src = (size_t)r * kEpsHist + (size_t)(step % kEpsHist);
+      eps[(size_t)r * cap + q] = eh[src];
+      if (rebuilt) rebuilt[(size_t)r * cap + q] = rh[src];
+    }
+  *n_out = (int)k;
+  return rc;
+}
+
+}  // extern "C"
+
+namespace {
+
+bool valid_tuning(const Tuning& t) {
+  auto nt = [](int v) { return v == 64 || v == 128 || v == 256; };
+  return nt(t.local_threads) && nt(t.ds_threads) && (t.local_stage == 0 || t.local_stage == 1) &&
+         (t.ds_stage == 0 || t.ds_stage == 1) && (t.transport_rows == 2 || t.transport_rows == 4 || t.transport_rows == 8);
+}
+
+// Median device time (ms) of `reps` launches of fn on the context's stream, after one untimed launch.
+template <typename F>
+double time_launches(mpm_ctx* c, F fn, int reps, cudaEvent_t e0, cudaEvent_t e1) {
+  fn();
+  std::vector<float> t(reps);
+  for (int k = 0; k < reps; ++k) {
+    cudaEventRecord(e0, c->stream);
+    fn();
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&t[k], e0, e1);
+  }
+  std::sort(t.begin(), t.end());
+  return t[reps / 2];
+}
+
+}  // namespace
+
+extern "C" {
+
+int mpm_get_tuning(mpm_ctx* c, int* v, int n) {
+  if (!c || !v || n < MPM_TUNE_N) return MPM_ERR_ARG;
+  const Tuning& t = c->tune;
+  const int vals[MPM_TUNE_N] = {t.local_threads, t.local_stage, t.ds_threads, t.ds_stage, t.transport_rows};
+  for (int k = 0; k < MPM_TUNE_N; ++k) v[k] = vals[k];
+  return MPM_OK;
+}
+
+int mpm_set_tuning(mpm_ctx* c, const int* v, int n) {
+  if (!c || !v || n < MPM_TUNE_N) return MPM_ERR_ARG;
+  Tuning t;
+  t.local_threads = v[0];
+  t.local_stage = v[1];
+  t.ds_threads = v[2];
+  t.ds_stage = v[3];
+  t.transport_rows = v[4];
+  if (!valid_tuning(t)) return fail(c, MPM_ERR_ARG, "invalid tuning values");
+  c->tune = t;
+  drop_graph(c);
+  return MPM_OK;
+}
+
+int mpm_autotune(mpm_ctx* c, int reps, double* ms_out) {
+  if (!c) return MPM_ERR_ARG;
+  if (reps < 1 || reps > 100) return fail(c, MPM_ERR_ARG, "need 1 <= reps <= 100");
+  int rc = need_ready(c, true);
+  if (rc) return rc;
+  const Grid& g = c->g;
+  DevState& d = c->d;
+  const int nsub = (int)c->subs.size();
+  cudaEvent_t e0 = take_event(c), e1 = take_event(c);
+  const bool saved_prof = c->prof;
+  c->prof = false;
+  CK(cudaStreamSynchronize(c->stream));
+  Tuning best = c->tune;
+  double best_ms[3] = {1e300, 1e300, 1e300};
+  // 1. the fused transport tile: without the decision its outputs (s2, f(s2), kappa^n and the
+  //    transmissibilities of s2) depend only on s, f(s) and the fluxes, so repeated launches
+  //    write the same values; kappa^n and the transmissibilities of the current s are restored
+  //    afterwards
+  const double fmax_ = max_fprime(g.M);
+  for (int rows : {2, 4, 8}) {
+    const double ms = time_launches(c, [&] { launch_upwind_kappa(g, d, 0.5, fmax_, false, 0.0, 0, false, rows, c->stream); },
+                                    reps, e0, e1);
+    if (ms < best_ms[0]) { best_ms[0] = ms; best.transport_rows = rows; }
+  }
+  launch_mobility_eps(g, d, false, c->stream);
+  // 2. the MPM-2P local solve (every realisation takes the reuse branch while timed; the
+  //    branch flags of the last update are put back afterwards: the downscaling reads them)
+  std::vector<int> flags(g.R);
+  CK(cudaMemcpyAsync(flags.data(), d.rebuild, sizeof(int) * g.R, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  launch_fill_flags(g, d, 0, c->stream);
+  Grid g0 = g;  // timed as the epsilon^0 solve, which leaves the first-order pressure dp0 alone
+  g0.order = 0;
+  for (int nt : {64, 128, 256})
+    for (int stage : {0, 1}) {
+      const double ms = time_launches(c, [&] {
+        launch_mpm_local(g0, d, c->d_subs, nsub, c->max_a, c->max_b, c->fac_prec == MPM_PREC_FP32_IR_ALL, c->ir_tol,
+                         c->ir_max, c->d_nodes, c->d_leaf_node, nt, stage, 0, c->stream);
+      }, reps, e0, e1);
+      if (ms < best_ms[1]) { best_ms[1] = ms; best.local_threads = nt; best.local_stage = stage; }
+    }
+  CK(cudaMemcpyAsync(d.rebuild, flags.data(), sizeof(int) * g.R, cudaMemcpyHostToDevice, c->stream));
+  // 3. the downscaling solve with the factor of the current kappa^n (its inputs, the traces and
+  //    targets of the last interface solve, are left unchanged; its outputs are recomputed)
+  launch_downscale_factor(g, d, c->d_subs, nsub, c->max_a, c->max_b, fp32(c), c->stream);
+  for (int nt : {64, 128, 256})
+    for (int stage : {0, 1}) {
+      const double ms = time_launches(c, [&] {
+        launch_downscale(g, d, c->d_subs, nsub, c->max_a, c->max_b, fp32(c), c->ir_tol, c->ir_max, false, nt, stage,
+                         c->stream);
+      }, reps, e0, e1);
+      if (ms < best_ms[2]) { best_ms[2] = ms; best.ds_threads = nt; best.ds_stage = stage; }
+    }
+  c->ev_pool.push_back(e0);
+  c->ev_pool.push_back(e1);
+  c->prof = saved_prof;
+  rc = check_launch(c);
+  if (rc) return rc;
+  rc = sync_status(c);
+  c->tune = best;
+  drop_graph(c);
+  if (ms_out)
+    for (int k = 0; k < 3; ++k) ms_out[k] = best_ms[k];
   return rc;
 }
 

@@ -18,6 +18,7 @@ namespace mpm {
 
 constexpr int kMaxSide = 24;     // largest subdomain width / height in cells
 constexpr int kPivotChunk = 16;  // pivot block of the interface sweeps
+constexpr int kEpsHist = 4096;   // steps of epsilon history kept per realisation (MPM_EPS_HISTORY)
 
 // Padded width A of the stored local factors ([b][A][A] per subdomain): 8, 16 or 32.
 __host__ __device__ inline int pad_width(int max_a) { return max_a <= 8 ? 8 : max_a <= 16 ? 16 : 32; }
@@ -40,7 +41,6 @@ struct DevSub {
   int side_nb[4];    // U DOFs on this side (= P DOFs)
   int side_nbr[4];   // subdomain on the other side of the interface, or -1
   double side_sign[4];  // n_check . n_check^i
-  double side_rho[4];   // alpha * (interface length in cells) = alpha H / h
   long long q_off;   // Robin factor (b*A*A values of the factor type, A = pad_width) in the factor pool
   long long t_off;   // b*a values: vertical transmissibilities + scaling (see k_local.cu)
   long long tr_off;  // (2(a+b)) x ndof BF traces
@@ -56,6 +56,7 @@ struct Grid {
   double M;
   int seg_len, degree;
   double alpha;
+  int order;  // MPM-2P perturbation order: 0 (Eq. mpm_tf_3 only) or 1 (plus Eq. mpm_tf_4, l = 1)
   __host__ __device__ long long ncell() const { return (long long)nx * ny; }
   __host__ __device__ long long nfx() const { return (long long)ny * (nx + 1); }
   __host__ __device__ long long nfy() const { return (long long)(ny + 1) * nx; }
@@ -86,6 +87,19 @@ __device__ __forceinline__ double phys_flux(const Grid& g, int side, double kc, 
 }
 #endif
 
+// Launch shapes that depend on the geometry (the number and size of the subdomains against
+// the SM count): defaults below, or the choice of the autotuner (mpm_autotune), which times
+// every candidate on the context's own data.
+struct Tuning {
+  int local_threads = 256;  // threads per CTA of the MPM-2P local solve (64, 128 or 256; warps 0-1 run
+                            // the twisted chains, all warps the cell-parallel phases)
+  int local_stage = 1;      // 1: stage the stored factor in shared memory (cp.async), 0: read it from
+                            // global memory inside the chains (smaller CTAs, more of them per SM)
+  int ds_threads = 256;     // the same two for the downscaling solve
+  int ds_stage = 1;
+  int transport_rows = 2;   // rows of the 32-column tile of the fused transport kernel (2, 4 or 8)
+};
+
 // Nested-dissection node of the interface system.  Leaves are subdomains (no
 // separator, frontal = element matrix over the subdomain's DOFs).
 struct DevNode {
@@ -106,6 +120,7 @@ struct DevState {
   // cells [R][ny][nx]
   double *K, *q, *s, *s2, *kap_n, *kap_m, *p_m, *p_down;
   double* x_ds;        // pinned Neumann solution of the last refined downscaling (initial iterate of the next)
+  double* dp0;         // MRCM-level pressure of the epsilon^0 solve (first-order MPM-2P only)
   double *fs, *fs2;    // fractional flow f(s) of s / s2
   // faces
   double *ux, *uy;
@@ -120,6 +135,9 @@ struct DevState {
   int* ir_iters;       // [1] max refinement sweeps used
   long long* counts;   // [4] rebuild / MPM-2P updates taken by the device-side decision; graph steps
                        //     that ran the rebuild body / the MPM-2P body
+  double* eps_hist;    // [R][kEpsHist] epsilon after each decision (ring, slot = step % kEpsHist)
+  int* reb_hist;       // [R][kEpsHist] the decision of that step (1 = rebuild)
+  long long* hist_n;   // [1] decisions recorded so far
   // per subdomain pools
   void* fac;           // Robin factors (float or double), st_fac values per realisation
   double* tvec;        // [ex, wE, wN, sc] per subdomain (4 m), st_t
@@ -130,7 +148,10 @@ struct DevState {
   double* mu_hat;      // BF means, st_dof
   double* fbar;        // non-homogeneous / perturbation traces, st_face
   double* trace;       // one-sided traces of the current update, st_face
+  double* trace1;      // one-sided traces of the first-order (epsilon^1) solve, st_face
   double* bhat;        // beta_hat = rho / kappa^m per face (interface faces), st_face
+  double* rho_f;       // rho_e = alpha_e H_e / h per subdomain face (0 on physical faces), shared by all
+                       // realisations (indexed face_off + f, no realisation stride)
   double* sub_mean;    // mean of the non-homogeneous local solution, st_sub
   double* sub_target;  // target mean of the downscaled pressure, st_sub
   double* pm_mean;     // mean of p^m over the subdomain, st_sub
@@ -174,7 +195,8 @@ void launch_store_host(const double* src, double* dst_dev, long long n, const in
 void launch_upwind(const Grid& g, const DevState& d, double cfl, double fmax, cudaStream_t st);
 int upwind_kappa_blocks(const Grid& g);
 void launch_upwind_kappa(const Grid& g, const DevState& d, double cfl, double fmax, bool decide, double eta,
-                         cudaGraphConditionalHandle h_reb, bool set_handle, cudaStream_t st);
+                         cudaGraphConditionalHandle h_reb, bool set_handle, int rows, cudaStream_t st);
+int upwind_kappa_blocks_rows(const Grid& g, int rows);
 
 int local_smem_limit();
 void launch_robin_factor(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
@@ -184,14 +206,15 @@ void launch_basis_solve(const Grid& g, const DevState& d, const DevSub* subs, in
                         const int* leaf_node, cudaStream_t st);
 void launch_mpm_local(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
                       int max_b, bool fp32, double ir_tol, int ir_max, const DevNode* nodes, const int* leaf_node,
-                      cudaStream_t st);
+                      int threads, int stage, int pass, cudaStream_t st);
 void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_face,
                         int max_dof, int max_nf1, const DevNode* nodes, const int* leaf_node, const int* pmap,
-                        int branch, bool pdl, cudaStream_t st);
+                        int branch, int pass, bool pdl, cudaStream_t st);
 void launch_downscale_factor(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
                              int max_b, bool fp32, cudaStream_t st);
 void launch_downscale(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
-                      int max_b, bool fp32, double ir_tol, int ir_max, bool pdl, cudaStream_t st);
+                      int max_b, bool fp32, double ir_tol, int ir_max, bool pdl, int threads, int stage,
+                      cudaStream_t st);
 
 void launch_element_matrix(const Grid& g, const DevState& d, const DevSub* subs, int nsub,
                            const DevNode* nodes, const int* leaf_node, cudaStream_t st);

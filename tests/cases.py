@@ -15,7 +15,17 @@ CASES = {
     "rate_in": (32, 16, [16, 16], [16], 4, 1, 2.0, "exponential", 1.0, 0.2, 4.0, (N, D, N, N), (-1.0, 0, 0, 0), 6),
     "dirichlet4": (32, 32, [8, 8, 16], [16, 16], 8, 1, 1.0, "exponential", 1.0, 0.2, 2.0, (D, D, D, D), (1, 0, 0.5, 0.25), 7),
     "contrast64": (64, 64, [16] * 4, [16] * 4, 4, 1, 1.0, "gaussian", 4.0, 0.05, 5.0, (D, D, N, N), (1, 0, 0, 0), 8),
+    # alpha varying face by face (aMRCM, Section 3.1): the alpha argument is replaced by a seeded field
+    "alpha_field": (40, 36, [8, 12, 20], [12, 8, 16], 4, 1, None, "exponential", 2.0, 0.15, 5.0, (D, D, N, N),
+                    (1, 0, 0, 0), 9),
 }
+
+
+def alpha_field(nx, ny, seed, lo=0.1, hi=10.0):
+    """Seeded per-face alpha(x), log-uniform in [lo, hi]: (alpha_x [ny][nx+1], alpha_y [ny+1][nx])."""
+    rng = np.random.default_rng(1000 + seed)
+    return (np.exp(rng.uniform(np.log(lo), np.log(hi), (ny, nx + 1))),
+            np.exp(rng.uniform(np.log(lo), np.log(hi), (ny + 1, nx))))
 
 
 def case(name, s_kind="random"):
@@ -30,8 +40,10 @@ def case(name, s_kind="random"):
         s0 = np.broadcast_to(np.clip(1.0 - x / 0.3, 0, 1), (ny, nx)).copy()
     else:
         s0 = np.zeros((ny, nx))
-    return dict(nx=nx, ny=ny, Lx=1.0, Ly=ny * h, h=h, col_w=cw, row_h=rh, seg_len=seg, degree=deg, alpha=alpha,
-                M=M, bc_type=bct, bc_val=bcv, K=K, s0=np.ascontiguousarray(s0), seed=seed)
+    af = alpha_field(nx, ny, seed) if alpha is None else None
+    return dict(nx=nx, ny=ny, Lx=1.0, Ly=ny * h, h=h, col_w=cw, row_h=rh, seg_len=seg, degree=deg,
+                alpha=1.0 if alpha is None else alpha, alpha_face=af, M=M, bc_type=bct, bc_val=bcv, K=K,
+                s0=np.ascontiguousarray(s0), seed=seed)
 
 
 def rel(a, b):

@@ -15,7 +15,8 @@ TOL = {0: 1e-10, 1: 1e-8, 2: 1e-8}
 
 def _oracle_setup(c):
     prob = O.Problem(c["nx"], c["ny"], c["h"], tuple(c["bc_type"]), tuple(c["bc_val"]), c["M"], 1.0)
-    dec = O.Decomposition(c["nx"], c["ny"], c["col_w"], c["row_h"], c["seg_len"], c["degree"], c["alpha"])
+    dec = O.Decomposition(c["nx"], c["ny"], c["col_w"], c["row_h"], c["seg_len"], c["degree"], c["alpha"],
+                          c["alpha_face"])
     return prob, dec
 
 
@@ -30,7 +31,7 @@ def _gpu(c, prec, R=1, K=None, s0=None):
     ctx.set_precision(prec, 1e-14, 30)
     ctx.set_fluids(c["M"])
     ctx.set_boundary(c["bc_type"], c["bc_val"], 1.0)
-    ctx.set_decomposition(c["col_w"], c["row_h"], c["seg_len"], c["degree"], c["alpha"])
+    ctx.set_decomposition(c["col_w"], c["row_h"], c["seg_len"], c["degree"], c["alpha"], c["alpha_face"])
     ctx.set_permeability(np.ascontiguousarray(np.broadcast_to(c["K"] if K is None else K, (R, c["ny"], c["nx"]))))
     ctx.set_saturation(np.ascontiguousarray(np.broadcast_to(c["s0"] if s0 is None else s0, (R, c["ny"], c["nx"]))))
     return ctx
@@ -47,7 +48,7 @@ def _built():
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("name", ["p1_2x2", "uneven", "const_H", "exact_h", "single", "rate_in", "dirichlet4",
-                                  "contrast64"])
+                                  "contrast64", "alpha_field"])
 def test_mrcm_update_parity(name, prec):
     c = case(name)
     prob, dec = _oracle_setup(c)
@@ -70,7 +71,7 @@ def test_mrcm_update_parity(name, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
-@pytest.mark.parametrize("name", ["p1_2x2", "uneven", "rate_in", "dirichlet4", "contrast64"])
+@pytest.mark.parametrize("name", ["p1_2x2", "uneven", "rate_in", "dirichlet4", "contrast64", "alpha_field"])
 def test_mpm_update_parity(name, prec):
     c = case(name)
     prob, dec = _oracle_setup(c)
@@ -99,6 +100,77 @@ def test_mpm_update_parity(name, prec):
     assert bal <= max(4 * obal, 5e-13), (bal, obal)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", ["p1_2x2", "uneven", "contrast64", "alpha_field"])
+def test_mpm_first_order_update_parity(name, prec):
+    # Eq. (mpm_tf_4), l = 1, through the stand-alone calls: epsilon^0 local + interface solve,
+    # first-order local + interface solve, downscaling
+    c = case(name)
+    prob, dec = _oracle_setup(c)
+    s_m = c["s0"]
+    s_n = np.clip(s_m + 0.05 * np.random.default_rng(c["seed"]).standard_normal(s_m.shape), 0, 1)
+    kap_m = O.mobility(s_m, c["M"]) * c["K"]
+    kap_n = O.mobility(s_n, c["M"]) * c["K"]
+    _, bs, sol = O.mrcm_step(kap_m, prob, dec)
+    step, _ = O.mpm_step(kap_n, bs, sol.p, prob, dec, order=1)
+    step0, _ = O.mpm_step(kap_n, bs, sol.p, prob, dec, order=0)
+    assert rel(step.Fx, step0.Fx) > 1e3 * TOL[prec]  # the first-order term is visible at this tolerance
+    obal = _balance(step.Fx, step.Fy, prob)
+    ctx = _gpu(c, prec)
+    ctx.set_mpm_order(1)
+    ctx.init(0.1)
+    ctx.set_saturation(np.ascontiguousarray(s_n[None]))
+    ctx.eval_epsilon()
+    ctx.perturbation_solve()
+    ctx.interface_solve()
+    ctx.perturbation_correction()
+    ctx.interface_solve()
+    ctx.downscale()
+    pd = ctx.get_pressure(1)[0]
+    ux, uy = ctx.get_flux()
+    tol = TOL[prec]
+    assert rel(ux[0], step.Fx) <= tol, rel(ux[0], step.Fx)
+    assert rel(uy[0], step.Fy) <= tol + 1e-12, rel(uy[0], step.Fy)
+    assert rel(pd, step.p_down) <= tol, rel(pd, step.p_down)
+    bal = _balance(ux[0], uy[0], prob)
+    assert bal <= max(4 * obal, 5e-13), (bal, obal)
+
+
+def test_first_order_correction_needs_order_one():
+    from paper_2103_11050_gb300 import binding as B
+    c = case("p1_2x2")
+    ctx = _gpu(c, 0)
+    ctx.init(0.1)
+    with pytest.raises(B.MPMError) as ei:
+        ctx.perturbation_correction()
+    assert ei.value.code == B.MPM_ERR_STATE
+
+
+@pytest.mark.parametrize("graph", [True, False])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_algorithm1_first_order_parity(prec, graph):
+    c = case("p1_2x2", "zero")
+    prob, dec = _oracle_setup(c)
+    eta, steps = 0.02, 10
+    st = O.simulate_init(c["K"], c["s0"], prob, dec, eta)
+    ctx = _gpu(c, prec)
+    ctx.set_mpm_order(1)
+    ctx.set_execution(graph, True)
+    ctx.init(eta)
+    for _ in range(steps):
+        O.simulate_step(st, c["K"], prob, dec, eta, 0.5, 1, order=1)
+        ctx.step(eta, 0.5, 1)
+    tol = TOL[prec]
+    n_reb = sum(1 for h in st.history if h["rebuild"])
+    assert ctx.get_stats()["rebuilds"] == n_reb + 1
+    assert 0 < n_reb < steps - 1  # both kinds of update occur
+    ux, uy = ctx.get_flux()
+    assert rel(ctx.get_saturation()[0], st.s) <= tol
+    assert rel(ux[0], st.step.Fx) <= tol, rel(ux[0], st.step.Fx)
+    assert rel(uy[0], st.step.Fy) <= tol + 1e-12
+    assert rel(ctx.get_pressure(1)[0], st.step.p_down) <= tol
+
+
 def test_transport_parity():
     c = case("uneven", "front")
     prob, dec = _oracle_setup(c)
@@ -120,7 +192,8 @@ def test_transport_parity():
 
 @pytest.mark.parametrize("graph,pdl", [(True, True), (False, True), (True, False), (False, False)])
 @pytest.mark.parametrize("prec", [0, 1, 2])
-@pytest.mark.parametrize("name,eta,steps", [("p1_2x2", 0.02, 12), ("uneven", -1.0, 4), ("contrast64", 0.05, 8)])
+@pytest.mark.parametrize("name,eta,steps", [("p1_2x2", 0.02, 12), ("uneven", -1.0, 4), ("contrast64", 0.05, 8),
+                                            ("alpha_field", 0.02, 6)])
 def test_algorithm1_parity(name, eta, steps, prec, graph, pdl):
     c = case(name, "zero")
     prob, dec = _oracle_setup(c)
@@ -138,6 +211,13 @@ def test_algorithm1_parity(name, eta, steps, prec, graph, pdl):
     n_reb = sum(1 for h in st.history if h["rebuild"])
     assert stats["rebuilds"] == n_reb + 1  # plus the initial build
     assert stats["mpm_updates"] == steps - n_reb
+    # the epsilon history: every step's epsilon and decision, oldest first
+    eps_h, reb_h = ctx.get_eps_history()
+    assert eps_h.shape == (1, steps)
+    np.testing.assert_array_equal(reb_h[0], [int(h["rebuild"]) for h in st.history])
+    # epsilon is a norm of kappa^n - kappa^m, i.e. of a difference: a relative error of the
+    # saturation of order tol grows by 1/epsilon (~1e2) in it, hence 1e2 tol
+    np.testing.assert_allclose(eps_h[0], [h["eps"] for h in st.history], rtol=1e2 * tol, atol=0)
     assert rel(s, st.s) <= tol, rel(s, st.s)
     assert rel(ux[0], st.step.Fx) <= tol, rel(ux[0], st.step.Fx)
     assert rel(uy[0], st.step.Fy) <= tol + 1e-12, rel(uy[0], st.step.Fy)
@@ -181,6 +261,20 @@ def test_realisations_are_independent():
     for r in range(3):
         step, _, _ = O.mrcm_step(O.mobility(c["s0"], c["M"]) * Ks[r], prob, dec)
         assert rel(ux[r], step.Fx) <= 1e-10
+
+
+def test_alpha_face_rejects_non_positive_values_on_interface_faces():
+    # only interface faces are read: a zero elsewhere is accepted, a zero on an interface face is not
+    from paper_2103_11050_gb300 import binding as B
+    c = case("uneven")
+    ax, ay = np.ones((c["ny"], c["nx"] + 1)), np.ones((c["ny"] + 1, c["nx"]))
+    ax[:, 0] = 0.0  # the left boundary: not an interface
+    ctx = _gpu(c, 0)
+    ctx.set_decomposition(c["col_w"], c["row_h"], c["seg_len"], c["degree"], 1.0, (ax, ay))
+    ax[3, c["col_w"][0]] = -1.0  # a face of the first vertical interface
+    with pytest.raises(B.MPMError) as ei:
+        ctx.set_decomposition(c["col_w"], c["row_h"], c["seg_len"], c["degree"], 1.0, (ax, ay))
+    assert ei.value.code == B.MPM_ERR_ARG
 
 
 def test_refinement_cap_reports_not_converged():
