@@ -471,6 +471,7 @@ class BasisSet:
     P_hat: list       # per subdomain: m x n_dof BF pressures
     F_hat: list       # per subdomain: list per side of (n_side x n_dof) BF traces
     K: sp.csr_matrix  # assembled interface matrix
+    K_lu: object = None  # its sparse LU factorisation, made at the first solve and kept with the BFs
 
 
 def build_basis(kappa, prob: Problem, dec: Decomposition) -> BasisSet:
@@ -566,10 +567,15 @@ def _interface_rhs(Fbar, kappa, dec: Decomposition):
     return f
 
 
-def _solve_interface(K, f):
+def _solve_interface(bs: BasisSet, f):
+    """Solve the interface system of Eq. (mrc2) with matrix bs.K by sparse LU (SuperLU,
+    COLAMD column ordering, partial pivoting).  The factorisation is kept with the BFs, so
+    the MPM-2P updates that reuse them do not factor again (the same LU spsolve would make)."""
     if f.size == 0:
         return f.copy()
-    return spla.spsolve(K.tocsc(), f)
+    if bs.K_lu is None:
+        bs.K_lu = spla.splu(bs.K.tocsc(), permc_spec="COLAMD")
+    return bs.K_lu.solve(f)
 
 
 @dataclass
@@ -640,7 +646,7 @@ def mrcm_solve(kappa, prob: Problem, dec: Decomposition, bs: BasisSet | None = N
     if bs is None:
         bs = build_basis(kappa, prob, dec)
     pbar, Fbar = _nonhomogeneous(kappa, prob, dec, bs, prob.source() * prob.h ** 2, False)
-    c = _solve_interface(bs.K, _interface_rhs(Fbar, kappa, dec))
+    c = _solve_interface(bs, _interface_rhs(Fbar, kappa, dec))
     return _combine(kappa, prob, dec, bs, pbar, Fbar, c), bs
 
 
@@ -791,7 +797,7 @@ def mpm_step(kappa_n, bs: BasisSet, p_m, prob: Problem, dec: Decomposition, orde
     kappa_m = bs.kappa
     r = fine_residual(kappa_n, p_m, prob)
     pbar, Fbar = _nonhomogeneous(kappa_m, prob, dec, bs, r, True)
-    c = _solve_interface(bs.K, _interface_rhs(Fbar, kappa_m, dec))
+    c = _solve_interface(bs, _interface_rhs(Fbar, kappa_m, dec))
     dsol = _combine(kappa_m, prob, dec, bs, pbar, Fbar, c)
     # ubar = u^m + delta u^n = uhat_0 - kappa^n grad p^m  (F_n(p^m) below)
     Fnx, Fny = fine_fluxes(p_m, kappa_n, prob)
@@ -805,7 +811,7 @@ def mpm_step(kappa_n, bs: BasisSet, p_m, prob: Problem, dec: Decomposition, orde
         dp0 = dsol.p.reshape(-1)
         r1 = -((A_n - A_m) @ dp0).reshape(prob.ny, prob.nx)
         pbar1, Fbar1 = _nonhomogeneous(kappa_m, prob, dec, bs, r1, True)
-        c1 = _solve_interface(bs.K, _interface_rhs(Fbar1, kappa_m, dec))
+        c1 = _solve_interface(bs, _interface_rhs(Fbar1, kappa_m, dec))
         dsol1 = _combine(kappa_m, prob, dec, bs, pbar1, Fbar1, c1)
         Gnx, Gny = fine_fluxes(dsol.p, kappa_n, hom)
         Gmx, Gmy = fine_fluxes(dsol.p, kappa_m, hom)
