@@ -162,7 +162,8 @@ def setup_ctx(B, wl, prec, stream, tune=None):
     ctx = B.Context(wl.R, wl.nx, wl.ny, 1.0, wl.ny / wl.nx, stream=stream)
     if tune is not None:
         ctx.set_tuning(tune)
-    mode = {"fp32": B.PREC_FP32_IR, "fp32all": B.PREC_FP32_IR_ALL, "fp64": B.PREC_FP64}[prec]
+    mode = {"fp32": B.PREC_FP32_IR, "fp32all": B.PREC_FP32_IR_ALL, "fp64": B.PREC_FP64, "tf32": B.PREC_TF32_IR,
+            "tf32x3": B.PREC_TF32X3_IR, "bf16": B.PREC_BF16_IR}[prec]
     ctx.set_precision(mode, 1e-14, 30)
     ctx.set_fluids(wl.M)
     ctx.set_boundary((0, 0, 1, 1), (1.0, 0.0, 0.0, 0.0), 1.0)
@@ -355,6 +356,36 @@ def run_gpu(args, wl):
                  "rel_flux_err_vs_fp64": float(num / den),
                  "rel_flux_err_vs_fp64_at": f"after init + {args.warmup + args.steps} steps (ux and uy together)"}
 
+    # Precision study of the rebuild's basis-function solves: a rebuild step (eta < 0) in each
+    # mode, its device time, the refinement sweeps it needed, whether every refinement
+    # converged, and its fluxes against the plain FP64 form after the same steps.
+    def precision_study():
+        out, ref = {}, None
+        for p in ("fp64", "fp32all", "tf32", "tf32x3", "bf16"):
+            ctx = setup_ctx(B, wl, p, stream.cuda_stream)
+            ctx.init(-1.0)
+            ctx.step(-1.0, CFL, N_SUB)
+            ctx.sync()
+            per = timed_steps(ctx, 2, -1.0)
+            try:
+                ctx.sync()
+                conv = True
+            except B.MPMError as e:
+                conv = e.code != B.MPM_ERR_NOT_CONVERGED
+            ux, uy = ctx.get_flux() if conv else (None, None)
+            st = ctx.get_stats()
+            ctx.close()
+            rec = {"rebuild_step_ms": min(per), "ir_sweeps_max": st["ir_iters_max"], "converged": conv}
+            if p == "fp64":
+                ref = (ux, uy)
+            elif conv:
+                num = np.sqrt(np.sum((ux - ref[0]) ** 2) + np.sum((uy - ref[1]) ** 2))
+                rec["rel_flux_err_vs_fp64"] = float(num / np.sqrt(np.sum(ref[0] ** 2) + np.sum(ref[1] ** 2)))
+            out[p] = rec
+        return out
+
+    study = None if args.no_study else precision_study()
+
     # End to end through the C ABI with host buffers: per step the saturation is copied in from
     # pinned host memory, the step runs, and the saturation is read back.  MPM-2P steps
     # (eta = 1e300) and rebuild steps (eta < 0) are timed on fresh contexts and blended like
@@ -420,6 +451,9 @@ def run_gpu(args, wl):
         "peaks_source": pk_kind,
         "ir_sweeps_max": main["ir"],
         "step_split": step_split,
+        "precision_study": {"what": "rebuild steps (init + 3 rebuild steps, the last two timed) per precision mode of "
+                                    "the local solves; basis-function solves on tensor cores in tf32, tf32x3, bf16",
+                            "modes": study},
     }
     line.update(other)
     if not args.no_cpu:
@@ -520,6 +554,45 @@ def run_reference(args, wl):
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def breakthrough_study(args, wl):
+    """The fingering workload run to breakthrough (water saturation above 0.01 in the outlet
+    column, checked every 10 steps, at most the workload's step count) for several rebuild
+    thresholds and both GPU forms: steps to breakthrough, rebuilds, device time per step."""
+    import torch
+
+    from paper_2103_11050_gb300 import binding as B
+    from paper_2103_11050_gb300 import build as Bd
+
+    Bd.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    out = []
+    for prec in ("fp32", "fp64"):
+        for eta in (0.05, 0.1, 0.2):
+            ctx = setup_ctx(B, wl, prec, stream.cuda_stream)
+            ctx.init(eta)
+            ms, n, bt = 0.0, 0, None
+            with torch.cuda.stream(stream):
+                while n < wl.steps and bt is None:
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(10):
+                        ctx.step(eta, CFL, N_SUB)
+                    e1.record(stream)
+                    s = ctx.get_saturation()
+                    ms += e0.elapsed_time(e1)
+                    n += 10
+                    if s[:, :, -1].max() > 0.01:
+                        bt = n
+            st = ctx.get_stats()
+            eps, reb = ctx.get_eps_history(4096)
+            ctx.close()
+            out.append({"prec": prec, "eta": eta, "breakthrough_step": bt, "steps_run": n,
+                        "rebuilds": st["rebuilds"] - 1, "ms_per_step": ms / n,
+                        "eps_max": float(eps.max()) if eps.size else None})
+    return {"study": "fingering to breakthrough", "workload": wl.desc, "unit": "steps, ms", "runs": out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -537,6 +610,9 @@ def main():
                     help="do not run the workload's trajectory past the timed window (rebuild mix of the window)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-tune", action="store_true", help="default launch shapes instead of the autotuned ones")
+    ap.add_argument("--no-study", action="store_true", help="skip the precision study of the rebuild step")
+    ap.add_argument("--breakthrough", action="store_true",
+                    help="run the workload to breakthrough for eta = 0.05, 0.1, 0.2 (fingering study) and print that")
     ap.add_argument("--window-only", action="store_true",
                     help="run only init, the warm-up and the timed window and print its rate: the command "
                          "profiled for the kernel launch list")
@@ -547,6 +623,9 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     wl = Workload(args.workload)
+    if args.breakthrough:
+        print(json.dumps(breakthrough_study(args, wl)), flush=True)
+        return
     if args.impl == "reference":
         line = run_reference(args, wl)
         if line is not None:

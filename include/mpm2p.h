@@ -69,8 +69,23 @@ enum { MPM_SIDE_LEFT = 0, MPM_SIDE_RIGHT = 1, MPM_SIDE_BOTTOM = 2, MPM_SIDE_TOP 
  *                 float64 (on GB300 a float64 solve with a stored factor costs less than
  *                 float32 solves plus float64 refinement residuals).
  *  FP32_IR_ALL:   every local factorisation and solve in float32 with float64 refinement.
+ *  TF32_IR, TF32X3_IR, BF16_IR: as FP32_IR_ALL, with the multi-right-hand-side basis-function
+ *                 solves of a rebuild (all ndof + 1 right-hand sides of a subdomain) on the
+ *                 tensor cores (mma.sync, float32 accumulation) and refined in float64:
+ *                 TF32_IR rounds both operands to tf32; TF32X3_IR splits each operand into two
+ *                 tf32 parts and sums three products (about float32 accuracy); BF16_IR rounds
+ *                 both operands to bf16.  With too little precision for the local conditioning
+ *                 the refinement stalls and the next synchronising call returns
+ *                 MPM_ERR_NOT_CONVERGED.
  * The interface (skeleton) system, residuals, fluxes and transport are float64 in all modes. */
-enum { MPM_PREC_FP64 = 0, MPM_PREC_FP32_IR = 1, MPM_PREC_FP32_IR_ALL = 2 };
+enum {
+  MPM_PREC_FP64 = 0,
+  MPM_PREC_FP32_IR = 1,
+  MPM_PREC_FP32_IR_ALL = 2,
+  MPM_PREC_TF32_IR = 3,
+  MPM_PREC_TF32X3_IR = 4,
+  MPM_PREC_BF16_IR = 5
+};
 
 /* Which pressure mpm_get_pressure returns. */
 enum {

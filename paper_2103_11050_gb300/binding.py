@@ -18,7 +18,7 @@ from . import build as _build
  MPM_ERR_TOO_LARGE) = range(7)
 MEM_HOST, MEM_DEVICE = 0, 1
 BC_DIRICHLET, BC_NEUMANN = 0, 1
-PREC_FP64, PREC_FP32_IR, PREC_FP32_IR_ALL = 0, 1, 2
+PREC_FP64, PREC_FP32_IR, PREC_FP32_IR_ALL, PREC_TF32_IR, PREC_TF32X3_IR, PREC_BF16_IR = 0, 1, 2, 3, 4, 5
 P_MRCM, P_DOWNSCALED = 0, 1
 EXEC_GRAPH, EXEC_PDL = 1, 4
 

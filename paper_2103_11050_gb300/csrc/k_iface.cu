@@ -66,7 +66,7 @@ __global__ void k_element_matrix(Grid g, DevState d, const DevSub* subs, const D
     const double s = sd.side_sign[side];
     double v = 0.0;
     for (int t = 0; t < L; ++t) {
-      const double w = side_basis(kk, t, g.seg_len, g.degree);
+      const double w = side_basis(kk, t, g.seg_len, g.degree, g.inv_seg);
       if (w == 0.0) continue;
       const double F = tr[(long long)l * nface + f0 + t];
       if (isP) {
@@ -74,7 +74,7 @@ __global__ void k_element_matrix(Grid g, DevState d, const DevSub* subs, const D
       } else {
         const double bh = bhat[f0 + t];
         v -= bh * s * w * F;
-        if (!lisP && lside == side) v += bh * w * side_basis(ll, t, g.seg_len, g.degree);
+        if (!lisP && lside == side) v += bh * w * side_basis(ll, t, g.seg_len, g.degree, g.inv_seg);
       }
     }
     E[(long long)l * nd + k] = v;  // stored transposed (see the per-level solve kernels)
@@ -185,17 +185,30 @@ __global__ void k_sweep_rowcol(Grid g, DevState d, const DevNode* nodes, const i
 }
 
 // Sweep step 3: trailing update  M_rc -= Mold_rP M_Pc(new)  for r, c outside P.
+// The frontal matrices are symmetric, and Gauss-Jordan elimination keeps a fixed pattern:
+// with E the pivots eliminated so far and R the rest, M_EE and M_RR stay symmetric and
+// M_ER = -M_RE^T (the partial inverse [A^-1, A^-1 B; -B^T A^-1, C - B^T A^-1 B]).  So only the
+// tiles on and above the diagonal are computed (blockIdx.y enumerates the pairs ty <= tx); an
+// off-diagonal tile also writes its mirror, negated where exactly one of row and column lies in
+// E, i.e. below k0 (through shared memory, so that both writes are coalesced).  This halves the
+// float64 work of the factorisation.
 __global__ void k_sweep_trailing(Grid g, DevState d, const DevNode* nodes, const int* level_nodes, int k0,
                                  int tiles_x) {
   __shared__ double A[kTile][kPivotChunk + 1];
   __shared__ double B[kPivotChunk][kTile + 1];
+  __shared__ double Tn[kTile][kTile + 1];
   const int r = blockIdx.z;
   if (d.rebuild[r] != 1) return;
   const DevNode nd = nodes[level_nodes[blockIdx.x]];
   if (k0 >= nd.nsep) return;
   const int nb = min(kPivotChunk, nd.nsep - k0);
   const int nf = nd.nf;
-  const int ty = blockIdx.y / tiles_x, tx = blockIdx.y - ty * tiles_x;
+  int ty = 0, rem = blockIdx.y;  // (ty, tx) from the upper-triangle index
+  while (rem >= tiles_x - ty) {
+    rem -= tiles_x - ty;
+    ++ty;
+  }
+  const int tx = ty + rem;
   const int r0 = ty * kTile, c0 = tx * kTile;
   if (r0 >= nf || c0 >= nf) return;
   double* F = d.front + (long long)r * d.st_front + nd.f_off;
@@ -217,7 +230,18 @@ __global__ void k_sweep_trailing(Grid g, DevState d, const DevNode* nodes, const
     double acc = 0.0;
 #pragma unroll
     for (int l = 0; l < kPivotChunk; ++l) acc += A[i][l] * B[l][j];
-    F[(long long)row * nf + colx] -= acc;
+    const double v = F[(long long)row * nf + colx] - acc;
+    F[(long long)row * nf + colx] = v;
+    Tn[i][j] = ((row < k0) == (colx < k0)) ? v : -v;
+  }
+  if (tx == ty) return;
+  __syncthreads();
+  for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+    const int j = e / kTile, i = e - j * kTile;  // consecutive threads: consecutive columns of row c0 + j
+    const int row = r0 + i, colx = c0 + j;
+    if (row >= nf || colx >= nf) continue;
+    if ((row >= k0 && row < k0 + nb) || (colx >= k0 && colx < k0 + nb)) continue;
+    F[(long long)colx * nf + row] = Tn[i][j];
   }
 }
 
@@ -536,7 +560,8 @@ void launch_nd_factor_level(const Grid& g, const DevState& d, const DevNode* nod
     ++g_launches;
     k_sweep_rowcol<<<dim3(nlev, (max_nf + 127) / 128, g.R), 128, 0, st>>>(g, d, nodes, level_nodes, k0);
     ++g_launches;
-    k_sweep_trailing<<<dim3(nlev, tiles_x * tiles_x, g.R), 256, 0, st>>>(g, d, nodes, level_nodes, k0, tiles_x);
+    k_sweep_trailing<<<dim3(nlev, tiles_x * (tiles_x + 1) / 2, g.R), 256, 0, st>>>(g, d, nodes, level_nodes, k0,
+                                                                                  tiles_x);
     ++g_launches;
   }
 }

@@ -8,13 +8,16 @@
 namespace mpm {
 namespace phase {
 
-__device__ __forceinline__ double side_basis(int kk, int t, int seg_len, int degree) {
+// Value at edge t of interface basis function kk (Legendre {1, 2 xi - 1} on segments of
+// seg_len edges, xi of the edge midpoint).  2 xi - 1 = (2 (t mod seg_len) + 1 - seg_len) / seg_len:
+// an integer numerator (exact) times inv_seg = 1 / seg_len (computed on the host; exact for
+// powers of two).
+__device__ __forceinline__ double side_basis(int kk, int t, int seg_len, int degree, double inv_seg) {
   const int nb = degree + 1;
   const int seg = kk / nb, pw = kk - seg * nb;
   if (t / seg_len != seg) return 0.0;
   if (pw == 0) return 1.0;
-  const double xi = div64((t % seg_len) + 0.5, (double)seg_len);
-  return 2.0 * xi - 1.0;
+  return (double)(2 * (t % seg_len) + 1 - seg_len) * inv_seg;
 }
 
 // Side, kind (0 = U, 1 = P) and index within the side's space of local DOF k.
@@ -52,7 +55,7 @@ __device__ __forceinline__ void element_rhs(const Grid& g, const DevState& d, co
   const int t0 = (kk / (g.degree + 1)) * g.seg_len;
   double v = 0.0;
   for (int t = t0; t < t0 + g.seg_len; ++t) {
-    const double w = side_basis(kk, t, g.seg_len, g.degree);
+    const double w = side_basis(kk, t, g.seg_len, g.degree, g.inv_seg);
     if (w == 0.0) continue;
     const double F = fb[f0 + t];
     if (isP) v -= w * F;

@@ -23,6 +23,7 @@
 // [b][A][A] (A = pad_width(max a)).
 #include "mpm2p_internal.cuh"
 #include "k_iface_phases.cuh"
+#include "k_local_tc.cuh"
 #include "k_local_warp.cuh"
 
 #include <algorithm>
@@ -317,7 +318,7 @@ __device__ double basis_rhs(const Grid& g, const DevState& d, const DevSub& sd, 
     const int t = (q < 2) ? jl : il;
     const double rho = d.rho_f[sd.face_off + face_side_off(q, a, b) + t];
     const bool isU = col < d0 + nb;
-    const double phi = side_basis(isU ? col - d0 : col - d0 - nb, t, g.seg_len, g.degree);
+    const double phi = side_basis(isU ? col - d0 : col - d0 - nb, t, g.seg_len, g.degree, g.inv_seg);
     // r_e g_e with r_e = kc/(1/2+rho): U: g = -(rho/kc) s phi -> -rho s phi/(1/2+rho); P: kc phi/(1/2+rho)
     return isU ? div64(-rho * sd.side_sign[q] * phi, 0.5 + rho) : div64(kc * phi, 0.5 + rho);
   }
@@ -333,7 +334,7 @@ __device__ double basis_g(const Grid& g, const DevState& d, const DevSub& sd, co
   const int d0 = sd.side_dof0[side], nb = sd.side_nb[side];
   if (col < d0 || col >= d0 + 2 * nb) return 0.0;
   const bool isU = col < d0 + nb;
-  const double phi = side_basis(isU ? col - d0 : col - d0 - nb, t, g.seg_len, g.degree);
+  const double phi = side_basis(isU ? col - d0 : col - d0 - nb, t, g.seg_len, g.degree, g.inv_seg);
   return isU ? -div64(d.rho_f[sd.face_off + f], S.kap[cl]) * sd.side_sign[side] * phi : phi;
 }
 
@@ -406,6 +407,157 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
     __syncthreads();
   }
   // Interface right-hand side (Eq. mrc2) from the non-homogeneous traces just written.
+  for (int k = threadIdx.x; k < sd.ndof; k += blockDim.x)
+    phase::element_rhs(g, d, sd, nodes[leaf_node[blockIdx.x]], r, k, fbar);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Tensor-core basis-function solves (k_local_tc.cuh): the float32 Robin factor, every block
+// product on the tensor cores, float64 refinement with the same residual, scale and stopping
+// rule as solve_refined.  Z / W are [m][ld] floats, ncp = ncol rounded up to 8 (the padding
+// columns hold zeros).
+
+template <int A, int KIND>
+__device__ void solve_refined_tc(const DevSub& sd, Stencil S, const float* th, const float* Q, const double* B,
+                                 double* X, double* Rr, float* Zw, float* Ww, int ncol, int ld, double target, double tol,
+                                 int ir_max, double* colmax, int* status, int* ir_used) {
+  const int m = sd.a * sd.b;
+  const int n = m * ncol, ncp = (ncol + 7) / 8 * 8;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    X[e] = 0.0;
+    Rr[e] = B[e];
+  }
+  __syncthreads();
+  int it = 0;
+  bool ok = false;
+  double eta_prev = 1e300;
+  for (; it < ir_max; ++it) {
+    for (int e = threadIdx.x; e < m * ncp; e += blockDim.x) {
+      const int c = e / ncp, col = e - c * ncp;
+      Zw[c * ld + col] = col < ncol ? (float)(Rr[c * ncol + col] * S.sc[c]) : 0.0f;
+    }
+    __syncthreads();
+    tc::block_solve_tc<A, KIND>(sd, th, Q, Zw, Ww, ld, ncp);
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int c = e / ncol, col = e - c * ncol;
+      X[e] += (double)Zw[c * ld + col] * S.sc[c];
+    }
+    for (int c = threadIdx.x; c < 2 * ncol; c += blockDim.x) colmax[c] = 0.0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int c = e / ncol, col = e - c * ncol;
+      double absx;
+      const double r = B[e] - apply_A(sd, S, X, c, col, ncol, absx);
+      Rr[e] = r;
+      atomic_max_nonneg(&colmax[col], fabs(r));
+      atomic_max_nonneg(&colmax[ncol + col], absx + fabs(B[e]));
+    }
+    __syncthreads();
+    double eta = 0.0;
+    for (int col = 0; col < ncol; ++col)
+      if (colmax[ncol + col] > 0.0) eta = fmax(eta, colmax[col] / colmax[ncol + col]);
+    __syncthreads();
+    if (eta <= target) { ok = true; ++it; break; }
+    if (eta > 0.5 * eta_prev && eta <= 1e3 * tol) { ok = true; ++it; break; }  // float64 floor reached
+    eta_prev = eta;
+  }
+  if (threadIdx.x == 0) {
+    if (!ok) atomicOr(status, 1);
+    atomicMax(ir_used, it);
+  }
+  __syncthreads();
+}
+
+// Shared memory of the tensor-core basis solve: the stencil, colmax, B / X / Rr ([m][ncol]
+// doubles), the factor ([b][A][A] floats), th (m floats), Z / W ([m][ld] floats).
+struct TcPlan {
+  int ncol, ld;
+  size_t bytes;
+};
+
+inline TcPlan plan_tc(int a, int b, int A) {
+  const int m = a * b;
+  for (int ncol = 32; ncol >= 8; ncol -= 8) {
+    const int ld = tc::tc_ld(ncol);
+    const size_t bytes = stencil_bytes(m) + 64 * sizeof(double) + (size_t)3 * m * ncol * sizeof(double) +
+                         (size_t)b * A * A * sizeof(float) + (size_t)m * sizeof(float) +
+                         (size_t)2 * m * ld * sizeof(float) + 256;
+    if (bytes <= (size_t)kSmemBudget || ncol == 8) return {ncol, ld, bytes};
+  }
+  return {8, tc::tc_ld(8), 0};
+}
+
+// All BF solves of a subdomain on the tensor cores (same outputs as k_basis_solve).
+template <int A, int KIND>
+__global__ void __launch_bounds__(256) k_basis_solve_tc(Grid g, DevState d, const DevSub* subs, int ncol_max, int ld,
+                                                        double tol, int ir_max, const DevNode* nodes,
+                                                        const int* leaf_node) {
+  extern __shared__ __align__(16) char smem[];
+  const int r = blockIdx.y;
+  if (d.rebuild[r] != 1) return;
+  __shared__ DevSub sd_s;
+  if (threadIdx.x == 0) sd_s = subs[blockIdx.x];
+  __syncthreads();
+  const DevSub& sd = sd_s;
+  const int a = sd.a, b = sd.b, m = a * b;
+  const int nface = 2 * (a + b);
+  const int ntot = sd.ndof + 1;
+  // carve: the float32 part of the layout (Q, Zw, Ww, th) after the float64 part
+  Carve<float> cv;
+  {
+    double* p = reinterpret_cast<double*>(smem);
+    cv.S.kap = p; p += m;
+    cv.S.ex = p; p += m;
+    cv.S.wE = p; p += m;
+    cv.S.wN = p; p += m;
+    cv.S.sc = p; p += m;
+    cv.colmax = p; p += 64;
+    cv.B = p; p += (size_t)m * ncol_max;
+    cv.X = p; p += (size_t)m * ncol_max;
+    cv.Rr = p; p += (size_t)m * ncol_max;
+    float* q = reinterpret_cast<float*>(p);
+    cv.Q = q; q += (size_t)b * A * A;
+    cv.th = q; q += m;
+    q += (16 - ((uintptr_t)q & 15) / 4) & 3;  // 16-byte alignment of the right-hand-side blocks
+    cv.Zw = q; q += (size_t)m * ld;
+    cv.Ww = q;
+  }
+  load_robin<float>(d, sd, r, cv, g, A);
+  double* tr = d.tr + (long long)r * d.st_tr + sd.tr_off;
+  double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;
+  double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
+  double* muh = d.mu_hat + (long long)r * d.st_dof + sd.dof_off;
+  for (int c0 = 0; c0 < ntot; c0 += ncol_max) {
+    const int ncol = min(ncol_max, ntot - c0);
+    for (int e = threadIdx.x; e < m * ncol; e += blockDim.x) {
+      const int c = e / ncol, col = e - c * ncol;
+      cv.B[e] = basis_rhs(g, d, sd, cv.S, r, c, c0 + col);
+    }
+    __syncthreads();
+    solve_refined_tc<A, KIND>(sd, cv.S, cv.th, cv.Q, cv.B, cv.X, cv.Rr, cv.Zw, cv.Ww, ncol, ld, 1e-3 * tol, tol, ir_max,
+                              cv.colmax, d.status, d.ir_iters);
+    for (int e = threadIdx.x; e < m * ncol; e += blockDim.x) {
+      const int col = e / m, c = e - col * m;
+      pf[(long long)(c0 + col) * m + c] = cv.X[c * ncol + col];
+    }
+    for (int e = threadIdx.x; e < nface * ncol; e += blockDim.x) {
+      const int f = e / ncol, col = e - f * ncol, bcol = c0 + col;
+      const double v = basis_trace(g, d, sd, cv.S, cv.X, ncol, f, col, bcol, bcol < sd.ndof);
+      if (bcol < sd.ndof) tr[(long long)bcol * nface + f] = v;
+      else fbar[f] = v;
+    }
+    for (int col = threadIdx.x >> 5; col < ncol; col += blockDim.x >> 5) {
+      double sum = 0.0;
+      for (int c = threadIdx.x & 31; c < m; c += 32) sum += cv.X[c * ncol + col];
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+      if ((threadIdx.x & 31) == 0) {
+        const int bcol = c0 + col;
+        if (bcol < sd.ndof) muh[bcol] = sum / m;
+        else d.sub_mean[(long long)r * d.st_sub + blockIdx.x] = sum / m;
+      }
+    }
+    __syncthreads();
+  }
   for (int k = threadIdx.x; k < sd.ndof; k += blockDim.x)
     phase::element_rhs(g, d, sd, nodes[leaf_node[blockIdx.x]], r, k, fbar);
 }
@@ -845,6 +997,25 @@ void downscale_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub,
   else downscale_nt<T, A, 256>(g, d, subs, nsub, max_a, max_b, refine, tol, ir_max, pdl, stage, st);
 }
 
+template <int A, int KIND>
+void basis_tc_launch(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b, double tol,
+                     int ir_max, const DevNode* nodes, const int* leaf_node, cudaStream_t st) {
+  const TcPlan pl = plan_tc(max_a, max_b, A);
+  set_smem(k_basis_solve_tc<A, KIND>, pl.bytes);
+  k_basis_solve_tc<A, KIND><<<dim3(nsub, g.R), 256, pl.bytes, st>>>(g, d, subs, pl.ncol, pl.ld, tol, ir_max, nodes,
+                                                                    leaf_node);
+  ++g_launches;
+}
+
+template <int A>
+void basis_tc_kind(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b, int kind,
+                   double tol, int ir_max, const DevNode* nodes, const int* leaf_node, cudaStream_t st) {
+  if (kind == tc::kTf32) basis_tc_launch<A, tc::kTf32>(g, d, subs, nsub, max_a, max_b, tol, ir_max, nodes, leaf_node, st);
+  else if (kind == tc::kTf32x3)
+    basis_tc_launch<A, tc::kTf32x3>(g, d, subs, nsub, max_a, max_b, tol, ir_max, nodes, leaf_node, st);
+  else basis_tc_launch<A, tc::kBf16>(g, d, subs, nsub, max_a, max_b, tol, ir_max, nodes, leaf_node, st);
+}
+
 }  // namespace
 
 int local_smem_limit() { return kSmemBudget; }
@@ -864,11 +1035,17 @@ void launch_robin_factor(const Grid& g, const DevState& d, const DevSub* subs, i
 }
 
 void launch_basis_solve(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
-                        int max_dof, bool fp32, double ir_tol, int ir_max, const DevNode* nodes,
+                        int tc_kind, bool fp32, double ir_tol, int ir_max, const DevNode* nodes,
                         const int* leaf_node, cudaStream_t st) {
   dim3 grid(nsub, g.R);
   const int thr = 256;
   const int A = pad_width(max_a);
+  if (tc_kind != 0) {  // tensor cores (float32 factor)
+    if (A == 8) basis_tc_kind<8>(g, d, subs, nsub, max_a, max_b, tc_kind, ir_tol, ir_max, nodes, leaf_node, st);
+    else if (A == 16) basis_tc_kind<16>(g, d, subs, nsub, max_a, max_b, tc_kind, ir_tol, ir_max, nodes, leaf_node, st);
+    else basis_tc_kind<32>(g, d, subs, nsub, max_a, max_b, tc_kind, ir_tol, ir_max, nodes, leaf_node, st);
+    return;
+  }
   if (fp32) {
     const SmemPlan pl = plan_smem<float>(max_a, max_b, A, 32);
     set_smem(k_basis_solve<float>, pl.bytes);
@@ -880,7 +1057,6 @@ void launch_basis_solve(const Grid& g, const DevState& d, const DevSub* subs, in
                                                          leaf_node);
   }
   ++g_launches;
-  (void)max_dof;
 }
 
 void launch_mpm_local(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,

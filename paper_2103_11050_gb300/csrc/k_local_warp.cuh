@@ -218,17 +218,29 @@ __device__ void factor(const DevSub& sd, Tables<T> t, T* Q) {
   __syncthreads();
 }
 
-// y[c] = sum_r Q[r][c] x[r] for the lane's column c (Q symmetric), x held as x[lane % A].
+// The lane's part of an A x A block (column c = lane % A, rows (lane / A) NR + q): loaded into
+// registers one block row ahead of its use, so that the load latency of the stored factor
+// (shared or global memory) overlaps the previous product of the chain.
 template <typename T, int A>
-__device__ __forceinline__ T matvec(const T* Qj, T x, int lane) {
+__device__ __forceinline__ void load_block(const T* Qj, T (&q)[A * A / 32], int lane) {
   constexpr int NR = A * A / 32;
   const int c = lane % A, h = lane / A;
+#pragma unroll
+  for (int k = 0; k < NR; ++k) q[k] = Qj[(h * NR + k) * A + c];
+}
+
+// y[c] = sum_r Q[r][c] x[r] for the lane's column c (Q symmetric), x held as x[lane % A], Q in
+// the registers of load_block.
+template <typename T, int A>
+__device__ __forceinline__ T matvec_regs(const T (&q)[A * A / 32], T x, int lane) {
+  constexpr int NR = A * A / 32;
+  const int h = lane / A;
   T acc0 = T(0), acc1 = T(0);
 #pragma unroll
-  for (int q = 0; q < NR; q += 2) {
-    const int r = h * NR + q;
-    acc0 += Qj[r * A + c] * __shfl_sync(0xffffffffu, x, r);
-    if (q + 1 < NR) acc1 += Qj[(r + 1) * A + c] * __shfl_sync(0xffffffffu, x, r + 1);
+  for (int k = 0; k < NR; k += 2) {
+    const int r = h * NR + k;
+    acc0 += q[k] * __shfl_sync(0xffffffffu, x, r);
+    if (k + 1 < NR) acc1 += q[k + 1] * __shfl_sync(0xffffffffu, x, r + 1);
   }
   T acc = acc0 + acc1;
 #pragma unroll
@@ -236,25 +248,39 @@ __device__ __forceinline__ T matvec(const T* Qj, T x, int lane) {
   return acc;
 }
 
+template <typename T, int A>
+__device__ __forceinline__ T matvec(const T* Qj, T x, int lane) {
+  T q[A * A / 32];
+  load_block<T, A>(Qj, q, lane);
+  return matvec_regs<T, A>(q, x, lane);
+}
+
 // Twisted solve (S A S) y = V in place (V, W: [b][A] padded, W workspace), two warps:
 //   forward   W_j = Q_j (V_j + t_{j-1} o W_{j-1}) (top, j < mid),
 //             W_j = Q_j (V_j + t_j o W_{j+1})     (bottom, j > mid),
 //   middle    y_mid = Q_mid (V_mid + t_{mid-1} o W_{mid-1} + t_mid o W_{mid+1}),
 //   backward  y_j = W_j + Q_j (t_j o y_{j+1}) (top),  y_j = W_j + Q_j (t_{j-1} o y_{j-1}) (bottom).
+// Each chain prefetches the next block of its factor while it multiplies with the current one.
 template <typename T, int A>
 __device__ void solve(const DevSub& sd, Tables<T> t, const T* Q) {
+  constexpr int NR = A * A / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = lane % A;
   const int b = sd.b, mid = b / 2;
   const int nsteps = warp == 0 ? mid : warp == 1 ? b - 1 - mid : 0;  // warps >= 2 idle here
+  T qc[NR], qn[NR];
   T w = T(0);
+  if (nsteps > 0) load_block<T, A>(Q + (size_t)(warp == 0 ? 0 : b - 1) * A * A, qc, lane);
   for (int k = 0; k < nsteps; ++k) {
     const int j = warp == 0 ? k : b - 1 - k;
     const int jc = warp == 0 ? j - 1 : j;
+    if (k + 1 < nsteps) load_block<T, A>(Q + (size_t)(warp == 0 ? j + 1 : j - 1) * A * A, qn, lane);
     T u = t.V[j * A + c];
     if (k > 0) u += t.th[jc * A + c] * w;
-    w = matvec<T, A>(Q + (size_t)j * A * A, u, lane);
+    w = matvec_regs<T, A>(qc, u, lane);
     if (lane < A) t.W[j * A + c] = w;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) qc[q] = qn[q];
   }
   __syncthreads();
   if (warp == 0) {
@@ -266,11 +292,15 @@ __device__ void solve(const DevSub& sd, Tables<T> t, const T* Q) {
   }
   __syncthreads();
   T x = warp < 2 ? t.V[mid * A + c] : T(0);
+  if (nsteps > 0) load_block<T, A>(Q + (size_t)(warp == 0 ? mid - 1 : mid + 1) * A * A, qc, lane);
   for (int k = 0; k < nsteps; ++k) {
     const int j = warp == 0 ? mid - 1 - k : mid + 1 + k;
     const int jc = warp == 0 ? j : j - 1;  // coupling to the row solved before
-    x = t.W[j * A + c] + matvec<T, A>(Q + (size_t)j * A * A, t.th[jc * A + c] * x, lane);
+    if (k + 1 < nsteps) load_block<T, A>(Q + (size_t)(warp == 0 ? j - 1 : j + 1) * A * A, qn, lane);
+    x = t.W[j * A + c] + matvec_regs<T, A>(qc, t.th[jc * A + c] * x, lane);
     if (lane < A) t.V[j * A + c] = x;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) qc[q] = qn[q];
   }
   __syncthreads();
 }

@@ -225,7 +225,12 @@ double max_fprime(double M) {
 // mixed modes; the Robin factors (reused by every BF solve and MPM-2P step) only in
 // MPM_PREC_FP32_IR_ALL.
 bool fp32(const mpm_ctx* c) { return c->prec != MPM_PREC_FP64; }
-bool fp32_robin(const mpm_ctx* c) { return c->prec == MPM_PREC_FP32_IR_ALL; }
+bool robin_fp32_mode(int prec) { return prec == MPM_PREC_FP32_IR_ALL || prec >= MPM_PREC_TF32_IR; }
+bool fp32_robin(const mpm_ctx* c) { return robin_fp32_mode(c->prec); }
+// Tensor-core kind of the basis-function solves (0: CUDA cores), k_local_tc.cuh.
+int tc_kind(const mpm_ctx* c) {
+  return c->prec == MPM_PREC_TF32_IR ? 1 : c->prec == MPM_PREC_TF32X3_IR ? 2 : c->prec == MPM_PREC_BF16_IR ? 3 : 0;
+}
 
 cudaEvent_t take_event(mpm_ctx* c) {
   if (!c->ev_pool.empty()) {
@@ -357,7 +362,7 @@ int run_build(mpm_ctx* c) {
   const int nsub = (int)c->subs.size();
   prof_begin(c, MPM_STAGE_BASIS);
   launch_robin_factor(g, d, c->d_subs, nsub, c->max_a, c->max_b, fp32_robin(c), st);
-  launch_basis_solve(g, d, c->d_subs, nsub, c->max_a, c->max_b, c->max_dof, fp32_robin(c), c->ir_tol, c->ir_max,
+  launch_basis_solve(g, d, c->d_subs, nsub, c->max_a, c->max_b, tc_kind(c), fp32_robin(c), c->ir_tol, c->ir_max,
                      c->d_nodes, c->d_leaf_node, st);
   if (c->n_dof > 0) launch_element_matrix(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, st);
   prof_end(c, MPM_STAGE_BASIS);
@@ -380,7 +385,7 @@ int run_perturbation(mpm_ctx* c, int pass = 0) {
   const Grid& g = c->g;
   const int nsub = (int)c->subs.size();
   prof_begin(c, MPM_STAGE_PERTURB);
-  launch_mpm_local(g, c->d, c->d_subs, nsub, c->max_a, c->max_b, c->fac_prec == MPM_PREC_FP32_IR_ALL, c->ir_tol,
+  launch_mpm_local(g, c->d, c->d_subs, nsub, c->max_a, c->max_b, robin_fp32_mode(c->fac_prec), c->ir_tol,
                    c->ir_max, c->d_nodes, c->d_leaf_node, c->tune.local_threads, c->tune.local_stage, pass, c->stream);
   prof_end(c, MPM_STAGE_PERTURB);
   c->next_pass = pass;
@@ -654,6 +659,7 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   g.s_inflow = 1.0;
   g.M = 1.0;
   g.seg_len = 1;
+  g.inv_seg = 1.0;
   g.degree = 0;
   g.alpha = 1.0;
   g.order = 0;
@@ -732,7 +738,7 @@ const char* mpm_last_error(const mpm_ctx* c) { return c ? c->err.c_str() : "null
 
 int mpm_set_precision(mpm_ctx* c, int mode, double ir_tol, int ir_max) {
   if (!c) return MPM_ERR_ARG;
-  if (mode != MPM_PREC_FP64 && mode != MPM_PREC_FP32_IR && mode != MPM_PREC_FP32_IR_ALL)
+  if (mode < MPM_PREC_FP64 || mode > MPM_PREC_BF16_IR)
     return fail(c, MPM_ERR_ARG, "unknown precision mode %d", mode);
   if (!(ir_tol > 0) || ir_max < 1 || ir_max > 1000) return fail(c, MPM_ERR_ARG, "need ir_tol > 0 and 1 <= ir_max <= 1000");
   c->prec = mode;
@@ -839,6 +845,7 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   c->row_h.assign(row_h, row_h + ncy);
   Grid& g = c->g;
   g.seg_len = seg_len;
+  g.inv_seg = 1.0 / seg_len;
   g.degree = degree;
   g.alpha = alpha;
   // interfaces
@@ -1403,7 +1410,7 @@ int mpm_autotune(mpm_ctx* c, int reps, double* ms_out) {
   for (int nt : {64, 128, 256})
     for (int stage : {0, 1}) {
       const double ms = time_launches(c, [&] {
-        launch_mpm_local(g0, d, c->d_subs, nsub, c->max_a, c->max_b, c->fac_prec == MPM_PREC_FP32_IR_ALL, c->ir_tol,
+        launch_mpm_local(g0, d, c->d_subs, nsub, c->max_a, c->max_b, robin_fp32_mode(c->fac_prec), c->ir_tol,
                          c->ir_max, c->d_nodes, c->d_leaf_node, nt, stage, 0, c->stream);
       }, reps, e0, e1);
       if (ms < best_ms[1]) { best_ms[1] = ms; best.local_threads = nt; best.local_stage = stage; }

@@ -55,6 +55,7 @@ struct Grid {
   double s_inflow;
   double M;
   int seg_len, degree;
+  double inv_seg;  // 1 / seg_len
   double alpha;
   int order;  // MPM-2P perturbation order: 0 (Eq. mpm_tf_3 only) or 1 (plus Eq. mpm_tf_4, l = 1)
   __host__ __device__ long long ncell() const { return (long long)nx * ny; }
@@ -202,7 +203,7 @@ int local_smem_limit();
 void launch_robin_factor(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
                          int max_b, bool fp32, cudaStream_t st);
 void launch_basis_solve(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
-                        int max_b, int max_dof, bool fp32, double ir_tol, int ir_max, const DevNode* nodes,
+                        int max_b, int tc_kind, bool fp32, double ir_tol, int ir_max, const DevNode* nodes,
                         const int* leaf_node, cudaStream_t st);
 void launch_mpm_local(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
                       int max_b, bool fp32, double ir_tol, int ir_max, const DevNode* nodes, const int* leaf_node,

@@ -26,11 +26,9 @@ from __future__ import annotations
 import numpy as np
 
 
-def lognormal_grf(nx: int, ny: int, h: float, sigma2: float, ell: float,
-                  cov: str = "exponential", seed: int = 0,
-                  mean_log: float = 0.0) -> np.ndarray:
-    """K = exp(mean_log + Y), Y a zero-mean GRF with the named covariance."""
-    rng = np.random.default_rng(seed)
+def _embedding_spectrum(nx, ny, h, sigma2, ell, cov):
+    """Eigenvalues of the circulant embedding of the covariance on the 2nx x 2ny periodic grid
+    (negative ones clipped to zero)."""
     mx, my = 2 * nx, 2 * ny
     dx = np.minimum(np.arange(mx), mx - np.arange(mx)) * h
     dy = np.minimum(np.arange(my), my - np.arange(my)) * h
@@ -42,11 +40,33 @@ def lognormal_grf(nx: int, ny: int, h: float, sigma2: float, ell: float,
     else:
         raise ValueError(f"unknown covariance {cov!r}")
     lam = np.fft.fft2(c).real
-    lam = np.clip(lam, 0.0, None)
-    xi = rng.standard_normal((my, mx)) + 1j * rng.standard_normal((my, mx))
+    return np.clip(lam, 0.0, None)
+
+
+def grf_from_noise(nx: int, ny: int, h: float, sigma2: float, ell: float, cov: str, xi: np.ndarray,
+                   mean_log: float = 0.0) -> np.ndarray:
+    """K = exp(mean_log + Y) for the white noise xi (complex, [2ny][2nx], real and imaginary
+    parts independent standard normals): Y is the real part of the circulant-embedding
+    synthesis, restricted to the grid.  A linear map of xi, so a Gaussian prior on xi is the
+    field's prior (the parametrisation a sampler over permeabilities moves in)."""
+    mx, my = 2 * nx, 2 * ny
+    lam = _embedding_spectrum(nx, ny, h, sigma2, ell, cov)
     y = np.fft.fft2(np.sqrt(lam / (mx * my)) * xi)
-    field = y.real[:ny, :nx]
-    return np.ascontiguousarray(np.exp(mean_log + field))
+    return np.ascontiguousarray(np.exp(mean_log + y.real[:ny, :nx]))
+
+
+def grf_noise(nx: int, ny: int, rng) -> np.ndarray:
+    """The white noise of grf_from_noise, drawn from rng."""
+    mx, my = 2 * nx, 2 * ny
+    return rng.standard_normal((my, mx)) + 1j * rng.standard_normal((my, mx))
+
+
+def lognormal_grf(nx: int, ny: int, h: float, sigma2: float, ell: float,
+                  cov: str = "exponential", seed: int = 0,
+                  mean_log: float = 0.0) -> np.ndarray:
+    """K = exp(mean_log + Y), Y a zero-mean GRF with the named covariance."""
+    rng = np.random.default_rng(seed)
+    return grf_from_noise(nx, ny, h, sigma2, ell, cov, grf_noise(nx, ny, rng), mean_log)
 
 
 def channelised(nx: int, ny: int, k_channel: float = 1.0, k_matrix: float = 1e-4,

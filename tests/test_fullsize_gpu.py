@@ -1,0 +1,148 @@
+"""The benchmark-sized workloads against the oracle, element by element, in the launch
+configuration the benchmark times (graph execution, autotuned launch shapes):
+
+* the 1024^2 channelised workload (64 x 64 subdomains of 16^2, contrast 1e4): the oracle's
+  initial MRCM solve and two Algorithm 1 steps, compared with the plain FP64 form (1e-10) and
+  the FP32 + FP64-refinement form (1e-8);
+* the 256-realisation ensemble of 128^2 fields on the uneven decomposition, all realisations
+  in one context, the first and the last realisation against the oracle;
+* the 512^2 homogeneous fingering workload, four steps.
+
+The oracle runs once per module; its cost (minutes at 1024^2) is why these tests stand apart."""
+import numpy as np
+import pytest
+
+from oracle import mpm_oracle as O
+from paper_2103_11050_gb300 import fields
+from tests.cases import rel
+
+pytestmark = pytest.mark.gpu
+TOL = {0: 1e-10, 1: 1e-8}
+CFL = 0.5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_11050_gb300 import build
+    build.build()
+
+
+def _ctx(R, nx, ny, M, col_w, row_h, K, s0, prec, tune_key=None):
+    from paper_2103_11050_gb300 import binding as B
+    ctx = B.Context(R, nx, ny, 1.0, ny / nx)
+    ctx.set_precision(prec, 1e-14, 30)
+    ctx.set_fluids(M)
+    ctx.set_boundary((0, 0, 1, 1), (1.0, 0, 0, 0), 1.0)
+    ctx.set_decomposition(col_w, row_h, 4, 1, 1.0)
+    ctx.set_permeability(np.ascontiguousarray(np.broadcast_to(K, (R, ny, nx))))
+    ctx.set_saturation(np.ascontiguousarray(np.broadcast_to(s0, (R, ny, nx))))
+    return ctx
+
+
+def _tune(ctx, R, nx, ny, col_w, row_h, prec, eta):
+    """The launch shapes the benchmark uses (cached per shape, autotuned on a miss)."""
+    import torch
+    from paper_2103_11050_gb300 import autotune as AT
+    key = AT.shape_key(R, nx, ny, col_w, row_h, {0: "fp64", 1: "fp32"}[prec], torch.cuda.get_device_name())
+    tmp = _ctx(R, nx, ny, ctx[0], col_w, row_h, ctx[1], ctx[2], prec)
+    tmp.init(eta)
+    for _ in range(3):
+        tmp.step(eta, CFL, 1)
+    tune, _ = AT.tuned(tmp, key)
+    tmp.close()
+    return tune
+
+
+@pytest.fixture(scope="module")
+def channel1024():
+    K, s0, w = fields.make_workload("channel1024")
+    n = w["nx"]
+    prob = O.Problem(n, n, 1.0 / n, (0, 0, 1, 1), (1.0, 0.0, 0.0, 0.0), w["M"], 1.0)
+    dec = O.uniform_decomposition(n, n, w["ncx"], w["ncy"], seg_len=4, degree=1)
+    st = O.simulate_init(K, s0, prob, dec, w["eta"])
+    init = (st.p_m.copy(), st.step.Fx.copy(), st.step.Fy.copy())
+    for _ in range(2):
+        O.simulate_step(st, K, prob, dec, w["eta"], CFL, 1)
+    return K, s0, w, prob, init, st
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_channel1024_against_oracle(channel1024, prec):
+    K, s0, w, prob, (pm0, Fx0, Fy0), st = channel1024
+    n = w["nx"]
+    cw = [n // w["ncx"]] * w["ncx"]
+    tune = _tune((w["M"], K, s0), 1, n, n, cw, cw, prec, w["eta"])
+    ctx = _ctx(1, n, n, w["M"], cw, cw, K, s0, prec)
+    ctx.set_tuning(tune)
+    ctx.init(w["eta"])
+    tol = TOL[prec]
+    ux, uy = ctx.get_flux()
+    assert rel(ctx.get_pressure(0)[0], pm0) <= tol
+    assert rel(ux[0], Fx0) <= tol and rel(uy[0], Fy0) <= tol
+    for _ in range(2):
+        ctx.step(w["eta"], CFL, 1)
+    ux, uy = ctx.get_flux()
+    assert ctx.get_stats()["rebuilds"] == 1 + sum(1 for h in st.history if h["rebuild"])
+    assert rel(ux[0], st.step.Fx) <= tol, rel(ux[0], st.step.Fx)
+    assert rel(uy[0], st.step.Fy) <= tol, rel(uy[0], st.step.Fy)
+    assert rel(ctx.get_saturation()[0], st.s) <= tol
+    assert rel(ctx.get_pressure(1)[0], st.step.p_down) <= tol
+    # per-cell mass balance: the refined form stops at a backward error of ir_tol = 1e-14 or, at
+    # the float64 floor, of at most 1e3 ir_tol in units of the cell's flux scale (|b| + the sum of
+    # its face fluxes, at most four times the largest flux): 4e-11 of the largest flux; the plain
+    # float64 form solves once with its factor, within that form's 1e-10 accuracy
+    bal = np.max(np.abs(O.cell_balance(ux[0], uy[0], prob))) / np.max(np.abs(ux[0]))
+    assert bal <= (4e-11 if prec == 1 else TOL[0]), bal
+    ctx.close()
+
+
+def test_ensemble_256_realisations():
+    Ks, s0, cw, rh, w = fields.make_ensemble()
+    R, nx, ny = Ks.shape
+    assert R == 256
+    eta, steps = w["eta"], 4
+    tune = _tune((w["M"], Ks, s0), R, nx, ny, cw, rh, 1, eta)
+    ctx = _ctx(R, nx, ny, w["M"], cw, rh, Ks, s0, 1)
+    ctx.set_tuning(tune)
+    ctx.init(eta)
+    for _ in range(steps):
+        ctx.step(eta, CFL, 1)
+    ux, uy = ctx.get_flux()
+    s = ctx.get_saturation()
+    prob = O.Problem(nx, ny, 1.0 / nx, (0, 0, 1, 1), (1.0, 0, 0, 0), w["M"], 1.0)
+    dec = O.Decomposition(nx, ny, cw, rh, 4, 1, 1.0)
+    for r in (0, R - 1):
+        st = O.simulate_init(Ks[r], s0, prob, dec, eta)
+        for _ in range(steps):
+            O.simulate_step(st, Ks[r], prob, dec, eta, CFL, 1)
+        assert rel(ux[r], st.step.Fx) <= 1e-8
+        assert rel(uy[r], st.step.Fy) <= 1e-8
+        assert rel(s[r], st.s) <= 1e-8
+    for r in range(R):
+        bal = np.max(np.abs(O.cell_balance(ux[r], uy[r], prob))) / np.max(np.abs(ux[r]))
+        assert bal <= 1e-11
+        assert s[r].min() >= -1e-14 and s[r].max() <= 1 + 1e-14
+    ctx.close()
+
+
+def test_finger512_against_oracle():
+    K, s0, w = fields.make_workload("finger512")
+    n, steps = w["nx"], 4
+    cw = [n // w["ncx"]] * w["ncx"]
+    prob = O.Problem(n, n, 1.0 / n, (0, 0, 1, 1), (1.0, 0.0, 0.0, 0.0), w["M"], 1.0)
+    dec = O.uniform_decomposition(n, n, w["ncx"], w["ncy"], seg_len=4, degree=1)
+    st = O.simulate_init(K, s0, prob, dec, w["eta"])
+    tune = _tune((w["M"], K, s0), 1, n, n, cw, cw, 1, w["eta"])
+    ctx = _ctx(1, n, n, w["M"], cw, cw, K, s0, 1)
+    ctx.set_tuning(tune)
+    ctx.init(w["eta"])
+    for _ in range(steps):
+        O.simulate_step(st, K, prob, dec, w["eta"], CFL, 1)
+        ctx.step(w["eta"], CFL, 1)
+    ux, uy = ctx.get_flux()
+    assert rel(ux[0], st.step.Fx) <= 1e-8 and rel(uy[0], st.step.Fy) <= 1e-8
+    assert rel(ctx.get_saturation()[0], st.s) <= 1e-8
+    ctx.close()

@@ -10,7 +10,7 @@ from tests.cases import case, rel
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-10, 1: 1e-8, 2: 1e-8}
+TOL = {0: 1e-10, 1: 1e-8, 2: 1e-8, 3: 1e-8, 4: 1e-8, 5: 1e-8}
 
 
 def _oracle_setup(c):
@@ -46,7 +46,7 @@ def _built():
     build.build()
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("name", ["p1_2x2", "uneven", "const_H", "exact_h", "single", "rate_in", "dirichlet4",
                                   "contrast64", "alpha_field"])
 def test_mrcm_update_parity(name, prec):
@@ -171,6 +171,28 @@ def test_algorithm1_first_order_parity(prec, graph):
     assert rel(ctx.get_pressure(1)[0], st.step.p_down) <= tol
 
 
+@pytest.mark.parametrize("name", ["p1_2x2", "uneven", "contrast64", "alpha_field"])
+def test_bf16_basis_solves_are_right_or_report(name):
+    # bf16 operands (8 significant bits) leave the refinement a contraction only where the
+    # scaled local problems are well conditioned: the update must then match the oracle, and
+    # otherwise the library must say that it did not converge, never return a silent error.
+    from paper_2103_11050_gb300 import binding as B
+    c = case(name)
+    prob, dec = _oracle_setup(c)
+    kappa = O.mobility(c["s0"], c["M"]) * c["K"]
+    step, _, sol = O.mrcm_step(kappa, prob, dec)
+    ctx = _gpu(c, 5)
+    ctx.init(0.1)
+    try:
+        ctx.sync()
+    except B.MPMError as e:
+        assert e.code == B.MPM_ERR_NOT_CONVERGED
+        return
+    ux, uy = ctx.get_flux()
+    assert rel(ctx.get_pressure(0)[0], sol.p) <= 1e-8
+    assert rel(ux[0], step.Fx) <= 1e-8 and rel(uy[0], step.Fy) <= 1e-8 + 1e-12
+
+
 def test_transport_parity():
     c = case("uneven", "front")
     prob, dec = _oracle_setup(c)
@@ -191,7 +213,7 @@ def test_transport_parity():
 
 
 @pytest.mark.parametrize("graph,pdl", [(True, True), (False, True), (True, False), (False, False)])
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 4])
 @pytest.mark.parametrize("name,eta,steps", [("p1_2x2", 0.02, 12), ("uneven", -1.0, 4), ("contrast64", 0.05, 8),
                                             ("alpha_field", 0.02, 6)])
 def test_algorithm1_parity(name, eta, steps, prec, graph, pdl):
@@ -224,6 +246,28 @@ def test_algorithm1_parity(name, eta, steps, prec, graph, pdl):
     # pressures: the MRCM-level p^m of the last rebuild and the last downscaled pressure
     assert rel(ctx.get_pressure(0)[0], st.p_m) <= tol, rel(ctx.get_pressure(0)[0], st.p_m)
     assert rel(ctx.get_pressure(1)[0], st.step.p_down) <= tol, rel(ctx.get_pressure(1)[0], st.step.p_down)
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_algorithm1_twenty_transport_substeps(graph):
+    # C_n = 20 transport steps between pressure updates (Section 5.1): the pressure step is
+    # Delta t_p = C_n Delta t_s with Delta t_s the CFL step of the current fluxes, so it adapts
+    # to the flow; the trajectory against the oracle's with the same C_n
+    c = case("p1_2x2", "zero")
+    prob, dec = _oracle_setup(c)
+    eta, steps, n_sub = 0.02, 5, 20
+    st = O.simulate_init(c["K"], c["s0"], prob, dec, eta)
+    ctx = _gpu(c, 1)
+    ctx.set_execution(graph, True)
+    ctx.init(eta)
+    for _ in range(steps):
+        O.simulate_step(st, c["K"], prob, dec, eta, 0.5, n_sub)
+        ctx.step(eta, 0.5, n_sub)
+    assert ctx.get_stats()["rebuilds"] == 1 + sum(1 for h in st.history if h["rebuild"])
+    assert ctx.get_stats()["last_dt_min"] == pytest.approx(st.history[-1]["dt"], rel=1e-8)
+    assert rel(ctx.get_saturation()[0], st.s) <= 1e-8
+    ux, uy = ctx.get_flux()
+    assert rel(ux[0], st.step.Fx) <= 1e-8 and rel(uy[0], st.step.Fy) <= 1e-8 + 1e-12
 
 
 def test_graph_replay_mixed_branches_across_realisations():
