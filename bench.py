@@ -47,10 +47,10 @@ E2E_PASSES = 3
 CFL = 0.5
 N_SUB = 1
 FORCED_REBUILDS = 3
-# dram__bytes_read.sum + dram__bytes_write.sum of the upward interface sweep of one step
-# (all its launches) from an ncu capture of this code on the default workload; None when
-# the kernels changed since the capture.
-TRAFFIC_IFACE_UP = None
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the step's kernels on the
+# default workload, from an ncu capture of this code (profiles/); a kernel is left out when
+# it changed since its capture.
+TRAFFIC = {}
 PREC = {"fp32": "FP32 downscaling factorisations + FP64 refinement; FP64 Robin factors, interface, fluxes, "
                 "transport",
         "fp32all": "FP32 local factorisations + FP64 refinement; FP64 interface, fluxes, transport",
@@ -173,16 +173,45 @@ def setup_ctx(B, wl, prec, stream, tune=None):
     return ctx
 
 
-def iface_up_bytes(ctx_stats_nodes):
-    """Algorithmic bytes of one upward interface sweep: every internal node reads its separator
-    rows of the transposed frontal matrix once (nsep x nf float64), plus its gathered right-hand
-    side and its output (2 nf float64)."""
-    return sum(8.0 * ns * nf + 16.0 * nf for ns, nf in ctx_stats_nodes if ns > 0)
+def iface_work(nodes):
+    """Algorithmic work of one interface solve, per sweep: (bytes, flops).  The upward sweep
+    reads every internal node's separator rows of its transposed frontal matrix once
+    (nsep x nf float64) and its gathered right-hand side and output (2 nf float64), one
+    multiply-add per matrix entry; the downward sweep reads the coupling block nbnd x nsep
+    (nodes: nd_sizes)."""
+    up = (sum(8.0 * ns * nf + 16.0 * nf for ns, nf, _ in nodes if ns > 0),
+          sum(2.0 * ns * nf for ns, nf, _ in nodes if ns > 0))
+    # the downward kernels visit the levels between the root (final after the upward sweep) and
+    # level 1 (done inside the reconstruction)
+    inner = [(ns, nf) for ns, nf, lev in nodes[:-1] if lev >= 2 and ns > 0]
+    down = (sum(8.0 * ns * (nf - ns) + 16.0 * ns for ns, nf in inner), sum(2.0 * ns * (nf - ns) for ns, nf in inner))
+    return up, down
+
+
+def local_work(col_w, row_h, R, fp32_factor):
+    """Algorithmic work of the single-right-hand-side local kernels over all subdomains:
+    (bytes, flops) of the MPM-2P local solve (stored float64 factor read once, b a^2 values;
+    the block solve's 2b products of a x a blocks, 4 b a^2 flops; the fine residual, 14 flops
+    and 80 bytes of stencil, pressures, conductivities, transmissibilities and source per
+    cell) and of the downscaling solve (its factor in the factor type; one block solve; one
+    flux-form residual; the interior fluxes; 80 bytes per cell of stencil, source, warm start,
+    outputs)."""
+    mb = md = fm = fd = 0.0
+    fac = 4.0 if fp32_factor else 8.0
+    for b in row_h:
+        for a in col_w:
+            m = a * b
+            mb += 8.0 * b * a * a + 80.0 * m
+            fm += 4.0 * b * a * a + 14.0 * m
+            md += fac * b * a * a + 80.0 * m
+            fd += 4.0 * b * a * a + 18.0 * m
+    return (R * mb, R * fm), (R * md, R * fd)
 
 
 def nd_sizes(col_w, row_h, seg_len=4, degree=1):
-    """(nsep, nf) of every nested-dissection node of the interface system, with the bisection
-    the library uses (the longer side of each rectangle of subdomains is split in half)."""
+    """(nsep, nf, level) of every internal nested-dissection node of the interface system, with
+    the bisection the library uses (the longer side of each rectangle of subdomains is split in
+    half), children before parents (the root last)."""
     ncx, ncy = len(col_w), len(row_h)
     nb = degree + 1
     vdofs = [2 * (row_h[J] // seg_len) * nb for J in range(ncy)]
@@ -191,23 +220,22 @@ def nd_sizes(col_w, row_h, seg_len=4, degree=1):
 
     def rec(I0, I1, J0, J1):
         if I1 - I0 == 1 and J1 - J0 == 1:
-            return
+            return 0
         if I1 - I0 >= J1 - J0:
             Im = (I0 + I1) // 2
-            rec(I0, Im, J0, J1)
-            rec(Im, I1, J0, J1)
+            lev = 1 + max(rec(I0, Im, J0, J1), rec(Im, I1, J0, J1))
             nsep = sum(vdofs[J] for J in range(J0, J1))
         else:
             Jm = (J0 + J1) // 2
-            rec(I0, I1, J0, Jm)
-            rec(I0, I1, Jm, J1)
+            lev = 1 + max(rec(I0, I1, J0, Jm), rec(I0, I1, Jm, J1))
             nsep = sum(hdofs[I] for I in range(I0, I1))
         bnd = 0
         for J in range(J0, J1):
             bnd += vdofs[J] * ((I0 > 0) + (I1 < ncx))
         for I in range(I0, I1):
             bnd += hdofs[I] * ((J0 > 0) + (J1 < ncy))
-        out.append((nsep, nsep + bnd))
+        out.append((nsep, nsep + bnd, lev))
+        return lev
 
     rec(0, ncx, 0, ncy)
     return out
@@ -413,22 +441,41 @@ def run_gpu(args, wl):
     f = step_split["rebuild_fraction"]
     e2e_ms = f * statistics.median(e2e_reb) + (1.0 - f) * statistics.median(e2e_mpm)
 
-    # roofline of the upward interface sweep (the kernels k_nd_up, one per nested-dissection
-    # level): algorithmic bytes per step over its measured device time per step
+    # Roofline of the step's kernels: algorithmic bytes and flops per step (iface_work,
+    # local_work, the transport's 88 bytes and about 30 flops per cell) over the measured
+    # device time per step of each (stage profiler, eager launches, L2 flushed), against the
+    # HBM copy bandwidth and the float64 pipe (152 SMs x 2 FMA per clock x 2 flop x 2070 MHz,
+    # derived: the measured-peaks file has no float64 figure).  Every kernel here is bound by
+    # one of the two; the headline is the kernel with the largest stage time, with the bound
+    # whose fraction is larger.
     pk, pk_kind = peaks()
-    nsteps_prof = args.steps
-    stage = {k: v[0] / max(nsteps_prof, 1) for k, v in prof_main.items()}
+    fp64_peak = 152 * 2 * 2 * 2070e6 / 1e12
+    stage = {k: v[0] / max(args.steps, 1) for k, v in prof_main.items()}
     reb_stage = {k: v[0] / FORCED_REBUILDS for k, v in prof_reb.items()}
-    up_bytes = iface_up_bytes(nd_sizes(wl.col_w, wl.row_h)) * wl.R
-    up_ms = stage.get("iface_up", 0.0)
-    achieved = up_bytes / (up_ms / 1e3) / 1e9 if up_ms > 0 else 0.0
-    roof = {"kernel": "k_nd_up (all levels of one upward interface sweep)", "bound": "hbm",
-            "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-            "traffic": TRAFFIC_IFACE_UP,
-            "algorithmic_bytes_per_step": up_bytes, "ms_per_step": up_ms,
-            "peak_kind": f"{pk_kind} HBM copy bandwidth",
-            "dominant_stage": max(stage, key=lambda k: stage[k] if k != "iface_solve" else -1),
-            "stage_ms_per_mpm_step_eager": stage, "stage_ms_per_rebuild_step_eager": reb_stage}
+    (ub, uf), (db, df) = iface_work(nd_sizes(wl.col_w, wl.row_h))
+    (lb, lf), (dsb, dsf) = local_work(wl.col_w, wl.row_h, wl.R, prec != "fp64")
+    work = {"k_mpm_local_w": ("perturb", lb, lf), "k_downscale_w": ("downscale", dsb, dsf),
+            "k_upwind_kappa": ("transport", 88.0 * cells, 30.0 * cells),
+            "k_nd_up": ("iface_up", ub * wl.R, uf * wl.R), "k_nd_down": ("iface_down", db * wl.R, df * wl.R)}
+    kern = {}
+    for name, (st_name, byts, flops) in work.items():
+        ms = stage.get(st_name, 0.0)
+        if ms <= 0:
+            continue
+        gbs = byts / (ms / 1e3) / 1e9
+        tfs = flops / (ms / 1e3) / 1e12
+        kern[name] = {"ms_per_step": ms, "bytes": byts, "flops": flops, "gbs": gbs, "frac_hbm": gbs / pk["hbm_gbs"],
+                      "tflops": tfs, "frac_fp64": tfs / fp64_peak}
+    dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
+    kd = kern[dom]
+    alu = kd["frac_fp64"] >= kd["frac_hbm"]
+    roof = {"kernel": dom, "bound": "alu" if alu else "hbm",
+            "achieved": kd["tflops"] if alu else kd["gbs"], "peak": fp64_peak if alu else pk["hbm_gbs"],
+            "unit": "TFLOP/s" if alu else "GB/s", "frac": kd["frac_fp64"] if alu else kd["frac_hbm"],
+            "traffic": TRAFFIC.get(dom),
+            "peak_kind": ("derived float64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz" if alu
+                          else f"{pk_kind} HBM copy bandwidth"),
+            "kernels": kern, "stage_ms_per_mpm_step_eager": stage, "stage_ms_per_rebuild_step_eager": reb_stage}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_blend, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -283,16 +283,18 @@ int mpm_set_execution(mpm_ctx* ctx, int flags);
  *       memory (smaller CTAs, more subdomains resident per SM)
  *   [2], [3] the same for the downscaling solve
  *   [4] rows (2, 4 or 8) of the 32-column cell tile of the fused transport kernel
- * Defaults: 256, 1, 256, 1, 2.  mpm_get_tuning / mpm_set_tuning read and write them (n >=
+ *   [5] interface sweeps: terms of a row's sum per thread (4, 8 or 16)
+ * Defaults: 256, 1, 256, 1, 2, 16.  mpm_get_tuning / mpm_set_tuning read and write them (n >=
  * MPM_TUNE_N; invalid values: MPM_ERR_ARG); results do not depend on them beyond rounding.
  * mpm_autotune times every candidate of each kernel on the context's current data (reps
  * timed launches each, the median taken; 1 <= reps <= 100) and keeps the fastest.  It needs a
  * stored basis (after mpm_init); it leaves the state of the current step as it was (it
  * recomputes the downscaled fluxes and pressure of the last update from the same traces, equal
  * up to refinement rounding), synchronises, and writes the best times (ms: transport, MPM-2P
- * local solve, downscaling solve) to ms (host, 3 values) unless NULL.  Setting or tuning
+ * local solve, downscaling solve, interface sweeps; 0 when not timed) to ms (host, 4 values)
+ * unless NULL.  Setting or tuning
  * drops a captured graph. */
-enum { MPM_TUNE_N = 5 };
+enum { MPM_TUNE_N = 6 };
 int mpm_get_tuning(mpm_ctx* ctx, int* values, int n);
 int mpm_set_tuning(mpm_ctx* ctx, const int* values, int n);
 int mpm_autotune(mpm_ctx* ctx, int reps, double* ms);

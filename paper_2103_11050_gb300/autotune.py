@@ -45,12 +45,13 @@ def tuned(ctx, key, path=CACHE, reps=5):
     stored basis, and cache the result.  Returns (tuning dict, source) with source "cache" or
     "autotune"."""
     cache = _load(path)
-    if key in cache:
+    if key in cache and set(cache[key]["tuning"]) == set(ctx.get_tuning()):
         ctx.set_tuning(cache[key]["tuning"])
         return cache[key]["tuning"], "cache"
     tune, ms = ctx.autotune(reps)
     cache = _load(path)  # re-read: another process may have written meanwhile
-    cache[key] = {"tuning": tune, "best_ms": {"transport": ms[0], "local_solve": ms[1], "downscale_solve": ms[2]}}
+    cache[key] = {"tuning": tune, "best_ms": {"transport": ms[0], "local_solve": ms[1], "downscale_solve": ms[2],
+                                              "interface_sweeps": ms[3]}}
     tmp = path + ".tmp"
     with open(tmp, "w") as fh:
         json.dump(cache, fh, indent=1, sort_keys=True)

@@ -32,7 +32,7 @@ FUNCTIONS = [
     "mpm_set_execution", "mpm_cfl_dt_noalloc", "mpm_get_eps_history", "mpm_get_tuning", "mpm_set_tuning",
     "mpm_autotune", "mpm_set_mpm_order", "mpm_perturbation_correction",
 ]
-TUNE_KEYS = ["local_threads", "local_stage", "ds_threads", "ds_stage", "transport_rows"]
+TUNE_KEYS = ["local_threads", "local_stage", "ds_threads", "ds_stage", "transport_rows", "sweep_terms"]
 
 STAGES = ["transport", "epsilon", "basis", "iface_factor", "perturb", "iface_solve", "downscale", "iface_up",
           "iface_down", "reconstruct"]
@@ -354,8 +354,8 @@ class Context:
 
     def autotune(self, reps=5):
         """Time every launch-shape candidate on this context's data and keep the fastest; returns
-        (tuning dict, best ms of transport / local solve / downscaling solve)."""
-        ms = (ctypes.c_double * 3)()
+        (tuning dict, best ms of transport / local solve / downscaling solve / interface sweeps)."""
+        ms = (ctypes.c_double * 4)()
         self._ck(self.L.mpm_autotune(self.h, int(reps), ms))
         return self.get_tuning(), list(ms)
 

@@ -567,9 +567,11 @@ void launch_nd_factor_level(const Grid& g, const DevState& d, const DevNode* nod
 }
 
 namespace {
-// k-chunks per output row: each thread sums at most about 16 terms.
-int k_split(int n) {
-  const int q = (n + 15) / 16;
+// k-chunks per output row: each thread sums about `terms` of the n terms, with at most 16
+// chunks (more chunks mean fewer rows per CTA and more CTAs, but a longer serial combination of
+// the partial sums: 32 and 64 chunks were measured slower on the 1024^2 workload).
+int k_split(int n, int terms) {
+  const int q = (n + terms - 1) / terms;
   return q <= 1 ? 1 : q <= 2 ? 2 : q <= 4 ? 4 : q <= 8 ? 8 : 16;
 }
 }  // namespace
@@ -586,16 +588,16 @@ int k_split(int n) {
   } while (0)
 
 void launch_nd_up(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
-                  int max_nf, int max_nsep, const int* srcmap, bool pdl, cudaStream_t st) {
-  const int ks = k_split(max_nsep), rows = 256 / ks;
+                  int max_nf, int max_nsep, const int* srcmap, bool pdl, int terms, cudaStream_t st) {
+  const int ks = k_split(max_nsep, terms), rows = 256 / ks;
   const dim3 grid(nlev, (max_nf + rows - 1) / rows, g.R);
   const size_t smem = (size_t)(256 + max_nsep) * sizeof(double);
   MPM_DISPATCH_KS(k_nd_up, ks, grid, dim3(256), smem, st, pdl, g, d, nodes, level_nodes, srcmap);
 }
 
 void launch_nd_down(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
-                    int max_nsep, int max_nbnd, const int* pmap, bool pdl, cudaStream_t st) {
-  const int ks = k_split(max_nbnd), rows = 256 / ks;
+                    int max_nsep, int max_nbnd, const int* pmap, bool pdl, int terms, cudaStream_t st) {
+  const int ks = k_split(max_nbnd, terms), rows = 256 / ks;
   const dim3 grid(nlev, max_nsep > 0 ? (max_nsep + rows - 1) / rows : 1, g.R);
   const size_t smem = (size_t)(256 + max_nbnd) * sizeof(double);
   MPM_DISPATCH_KS(k_nd_down, ks, grid, dim3(256), smem, st, pdl, g, d, nodes, level_nodes, pmap);

@@ -222,9 +222,9 @@ size_t fixed_bytes(int a, int b, int A) {
 }
 
 template <typename T>
-SmemPlan plan_smem(int a, int b, int A, int ncol_max) {
+SmemPlan plan_smem(int a, int b, int A, int ncol_max, bool q_global = false) {
   const int m = a * b;
-  const size_t fixed = fixed_bytes<T>(a, b, A);
+  const size_t fixed = fixed_bytes<T>(a, b, A) - (q_global ? (size_t)b * A * A * sizeof(T) : 0);
   const size_t per_col = (size_t)m * (3 * sizeof(double) + 2 * sizeof(T)) + 2 * sizeof(double);
   int ncol = (int)((kSmemBudget - fixed) / per_col);
   if (ncol > ncol_max) ncol = ncol_max;
@@ -243,7 +243,7 @@ struct Carve {
 };
 
 template <typename T>
-__device__ Carve<T> carve(char* base, int a, int b, int A, int ncol) {
+__device__ Carve<T> carve(char* base, int a, int b, int A, int ncol, bool q_global = false) {
   const int m = a * b;
   Carve<T> c;
   double* p = reinterpret_cast<double*>(base);
@@ -257,7 +257,7 @@ __device__ Carve<T> carve(char* base, int a, int b, int A, int ncol) {
   c.X = p; p += (size_t)m * ncol;
   c.Rr = p; p += (size_t)m * ncol;
   T* q = reinterpret_cast<T*>(p);
-  c.Q = q; q += (size_t)b * A * A;
+  c.Q = q; q += q_global ? 0 : (size_t)b * A * A;  // the factor stays in global memory when q_global
   c.Zw = q; q += (size_t)m * ncol;
   c.Ww = q; q += (size_t)m * ncol;
   c.th = q;
@@ -267,10 +267,13 @@ __device__ Carve<T> carve(char* base, int a, int b, int A, int ncol) {
 
 // Load the stored Robin factor (padded) and FP64 stencil of kappa^m into shared memory (CTA).
 template <typename T>
-__device__ void load_robin(const DevState& d, const DevSub& sd, int r, Carve<T>& cv, const Grid& g, int A) {
+__device__ void load_robin(const DevState& d, const DevSub& sd, int r, Carve<T>& cv, const Grid& g, int A,
+                           bool q_global = false) {
   const int a = sd.a, b = sd.b, m = a * b;
   const T* Qg = reinterpret_cast<const T*>(d.fac) + (long long)r * d.st_fac + sd.q_off;
-  for (int e = threadIdx.x; e < b * A * A; e += blockDim.x) cv.Q[e] = Qg[e];
+  if (q_global) cv.Q = const_cast<T*>(Qg);  // read in place (only read by the solves)
+  else
+    for (int e = threadIdx.x; e < b * A * A; e += blockDim.x) cv.Q[e] = Qg[e];
   const double* tv = d.tvec + (long long)r * d.st_t + sd.t_off;
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
     cv.S.ex[c] = tv[c];
@@ -355,7 +358,7 @@ __device__ double basis_trace(const Grid& g, const DevState& d, const DevSub& sd
 // the non-homogeneous column), means (mu_hat, sub_mean).
 template <typename T>
 __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int ncol_max, int refine,
-                              double tol, int ir_max, const DevNode* nodes, const int* leaf_node) {
+                              double tol, int ir_max, const DevNode* nodes, const int* leaf_node, int q_global) {
   extern __shared__ __align__(16) char smem[];
   const int r = blockIdx.y;
   if (d.rebuild[r] != 1) return;
@@ -366,8 +369,8 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
   const int a = sd.a, b = sd.b, m = a * b;
   const int nface = 2 * (a + b);
   const int ntot = sd.ndof + 1;
-  Carve<T> cv = carve<T>(smem, a, b, A, ncol_max);
-  load_robin<T>(d, sd, r, cv, g, A);
+  Carve<T> cv = carve<T>(smem, a, b, A, ncol_max, q_global != 0);
+  load_robin<T>(d, sd, r, cv, g, A, q_global != 0);
   double* tr = d.tr + (long long)r * d.st_tr + sd.tr_off;       // [ndof][nface]
   double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;       // [ndof+1][m]
   double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
@@ -702,7 +705,8 @@ __global__ void __launch_bounds__(NT) k_mpm_local_w(Grid g, DevState d, const De
   __syncthreads();
   for (int e = threadIdx.x; e < b * A; e += blockDim.x) {
     const int j = e / A, i = e - j * A;
-    t.th[e] = (i < a && j < b - 1) ? warp::to_T<T>(t.wN[j * a + i] * t.sc[j * a + i] * t.sc[j * a + i + a]) : T(0);
+    t.th[e] = (i < a && j < b - 1) ? warp::scaled_coupling<T>(t.wN[j * a + i], t.sc[j * a + i], t.sc[j * a + i + a])
+                                   : T(0);
   }
   if (qoff != 0) cp_async_wait_all();
   __syncthreads();
@@ -751,8 +755,20 @@ __global__ void k_downscale_factor_w(Grid g, DevState d, const DevSub* subs, int
   const int m = sd.a * sd.b;
   warp::Tables<T> t = warp::carve<T, A>(smem, m, sd.b);
   load_kappa_cta(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap);
+  // the pinned cell: the one of largest kappa^n (first on ties).  The pin fixes the pressure
+  // constant only (the mean is shifted afterwards), so its place changes no result, but a pin in
+  // a low-conductivity cell of a high-contrast field leaves a badly conditioned system that the
+  // float32 factor then refines slowly.
+  __shared__ int pin_s;
+  if (threadIdx.x == 0) {
+    int p = 0;
+    for (int c = 1; c < m; ++c)
+      if (__double_as_longlong(t.kap[c]) > __double_as_longlong(t.kap[p])) p = c;  // positive doubles
+    pin_s = p;
+  }
+  __syncthreads();
   warp::build<T, A>(g, sd, t, d.tx + (long long)r * g.nfx(), d.ty + (long long)r * g.nfy(), d.rho_f + sd.face_off,
-                    1, scale != 0);
+                    1 + pin_s, scale != 0);
   warp::factor<T, A>(sd, t, reinterpret_cast<T*>(d.nfac) + (long long)r * d.st_fac + sd.q_off);
   double* tv = d.ntvec + (long long)r * d.st_t + sd.t_off;
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
@@ -811,7 +827,8 @@ __global__ void __launch_bounds__(NT) k_downscale_w(Grid g, DevState d, const De
   __syncthreads();
   for (int e = threadIdx.x; e < b * A; e += blockDim.x) {
     const int j = e / A, i = e - j * A;
-    t.th[e] = (i < a && j < b - 1) ? warp::to_T<T>(t.wN[j * a + i] * t.sc[j * a + i] * t.sc[j * a + i + a]) : T(0);
+    t.th[e] = (i < a && j < b - 1) ? warp::scaled_coupling<T>(t.wN[j * a + i], t.sc[j * a + i], t.sc[j * a + i + a])
+                                   : T(0);
   }
   const double* qc = d.q + (long long)r * g.ncell();
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
@@ -1046,15 +1063,22 @@ void launch_basis_solve(const Grid& g, const DevState& d, const DevSub* subs, in
     else basis_tc_kind<32>(g, d, subs, nsub, max_a, max_b, tc_kind, ir_tol, ir_max, nodes, leaf_node, st);
     return;
   }
+  // the stored factor is staged in shared memory unless that leaves room for fewer than 8
+  // right-hand-side columns per pass (large padded blocks): then it is read in place
   if (fp32) {
-    const SmemPlan pl = plan_smem<float>(max_a, max_b, A, 32);
+    SmemPlan pl = plan_smem<float>(max_a, max_b, A, 32);
+    const bool qg = pl.ncol < 8;
+    if (qg) pl = plan_smem<float>(max_a, max_b, A, 32, true);
     set_smem(k_basis_solve<float>, pl.bytes);
-    k_basis_solve<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, A, pl.ncol, 1, ir_tol, ir_max, nodes, leaf_node);
+    k_basis_solve<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, A, pl.ncol, 1, ir_tol, ir_max, nodes, leaf_node,
+                                                       qg ? 1 : 0);
   } else {
-    const SmemPlan pl = plan_smem<double>(max_a, max_b, A, 32);
+    SmemPlan pl = plan_smem<double>(max_a, max_b, A, 32);
+    const bool qg = pl.ncol < 8;
+    if (qg) pl = plan_smem<double>(max_a, max_b, A, 32, true);
     set_smem(k_basis_solve<double>, pl.bytes);
     k_basis_solve<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, A, pl.ncol, 0, ir_tol, ir_max, nodes,
-                                                         leaf_node);
+                                                         leaf_node, qg ? 1 : 0);
   }
   ++g_launches;
 }

@@ -30,6 +30,17 @@ __device__ __forceinline__ float to_T<float>(double x) { return f64_to_f32_rn(x)
 __device__ __forceinline__ double from_T(double v) { return v; }
 __device__ __forceinline__ double from_T(float v) { return f32_to_f64(v); }
 
+// Float64 factors are built from the unscaled operator (Jacobi scaling only for float32).
+template <typename T>
+constexpr bool kUnscaled = sizeof(T) == sizeof(double);
+
+// The scaled north coupling t_j sc_c sc_c+a of the padded tables (T = float), or t_j itself.
+template <typename T>
+__device__ __forceinline__ T scaled_coupling(double wN, double sc0, double sc1) {
+  if constexpr (kUnscaled<T>) return wN;
+  else return to_T<T>(wN * sc0 * sc1);
+}
+
 // Per-warp shared-memory tables of one subdomain (a x b cells, m = a b, padded width A).
 template <typename T>
 struct Tables {
@@ -74,7 +85,7 @@ __device__ Tables<T> carve(char* base, int m, int b) {
   return t;
 }
 
-// FP64 stencil of the Robin (neumann = 0) or pinned Neumann (neumann = 1) operator of
+// FP64 stencil of the Robin (neumann = 0) or pinned Neumann (neumann = 1 + the pinned cell) operator of
 // kappa^n (transmissibilities tx / ty of the current kappa^n, r-th realisation pointers;
 // rho: the subdomain's per-face rho_e = alpha_e H_e / h), and the scaled T tables.  kap must
 // already hold the subdomain's kappa^n.
@@ -97,8 +108,8 @@ __device__ void build(const Grid& g, const DevSub& sd, Tables<T> t, const double
       if (jl == 0) dg += sd.side_kind[2] == 1 ? div64(kc, 0.5 + rho[2 * b + il]) : (g.bc_type[2] == 0 ? 2.0 * kc : 0.0);
       if (jl == b - 1)
         dg += sd.side_kind[3] == 1 ? div64(kc, 0.5 + rho[2 * b + a + il]) : (g.bc_type[3] == 0 ? 2.0 * kc : 0.0);
-    } else if (c == 0) {
-      dg += kc;  // pin: A + kappa_0 e_0 e_0^T
+    } else if (c == neumann - 1) {
+      dg += kc;  // pin: A + kappa_p e_p e_p^T at the pinned cell p = neumann - 1
     }
     t.ex[c] = dg;
   }
@@ -443,13 +454,16 @@ __device__ void solve_refined(const DevSub& sd, Tables<T> t, const T* Q, bool re
   for (; it < sweeps; ++it) {
     for (int e = tid; e < b * A; e += nt) {
       const int j = e / A, i = e - j * A;
-      t.V[e] = i < a ? to_T<T>(t.Rr[j * a + i] * t.sc[j * a + i]) : T(0);
+      // float64 factors are built unscaled (sc = 1): no multiplication by the scaling there
+      if constexpr (kUnscaled<T>) t.V[e] = i < a ? t.Rr[j * a + i] : T(0);
+      else t.V[e] = i < a ? to_T<T>(t.Rr[j * a + i] * t.sc[j * a + i]) : T(0);
     }
     __syncthreads();
     solve<T, A>(sd, t, Q);
     for (int c = tid; c < m; c += nt) {
       const int j = c / a, i = c - j * a;
-      t.X[c] += from_T(t.V[j * A + i]) * t.sc[c];
+      if constexpr (kUnscaled<T>) t.X[c] += t.V[j * A + i];
+      else t.X[c] += from_T(t.V[j * A + i]) * t.sc[c];
     }
     __syncthreads();
     if (!refine) { it = 1; ok = true; break; }

@@ -409,7 +409,7 @@ int run_interface(mpm_ctx* c, int pass = 0) {
     prof_begin(c, MPM_STAGE_IFACE_UP);
     for (size_t L = 1; L < c->levels.size(); ++L) {
       launch_nd_up(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(), c->lev_max_nf[L],
-                   c->lev_max_nsep[L], c->d_srcmap, chained && c->use_pdl, st);
+                   c->lev_max_nsep[L], c->d_srcmap, chained && c->use_pdl, c->tune.sweep_terms, st);
       chained = true;
     }
     prof_end(c, MPM_STAGE_IFACE_UP);
@@ -419,7 +419,7 @@ int run_interface(mpm_ctx* c, int pass = 0) {
     prof_begin(c, MPM_STAGE_IFACE_DOWN);
     for (int L = (int)c->levels.size() - 2; L >= 2; --L)
       launch_nd_down(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(),
-                     c->lev_max_nsep[L], c->lev_max_nbnd[L], c->d_pmap, c->use_pdl, st);
+                     c->lev_max_nsep[L], c->lev_max_nbnd[L], c->d_pmap, c->use_pdl, c->tune.sweep_terms, st);
     prof_end(c, MPM_STAGE_IFACE_DOWN);
   }
   prof_begin(c, MPM_STAGE_RECONSTRUCT);
@@ -1329,7 +1329,8 @@ namespace {
 bool valid_tuning(const Tuning& t) {
   auto nt = [](int v) { return v == 64 || v == 128 || v == 256; };
   return nt(t.local_threads) && nt(t.ds_threads) && (t.local_stage == 0 || t.local_stage == 1) &&
-         (t.ds_stage == 0 || t.ds_stage == 1) && (t.transport_rows == 2 || t.transport_rows == 4 || t.transport_rows == 8);
+         (t.ds_stage == 0 || t.ds_stage == 1) && (t.transport_rows == 2 || t.transport_rows == 4 || t.transport_rows == 8) &&
+         (t.sweep_terms == 4 || t.sweep_terms == 8 || t.sweep_terms == 16);
 }
 
 // Median device time (ms) of `reps` launches of fn on the context's stream, after one untimed launch.
@@ -1355,7 +1356,8 @@ extern "C" {
 int mpm_get_tuning(mpm_ctx* c, int* v, int n) {
   if (!c || !v || n < MPM_TUNE_N) return MPM_ERR_ARG;
   const Tuning& t = c->tune;
-  const int vals[MPM_TUNE_N] = {t.local_threads, t.local_stage, t.ds_threads, t.ds_stage, t.transport_rows};
+  const int vals[MPM_TUNE_N] = {t.local_threads, t.local_stage, t.ds_threads, t.ds_stage, t.transport_rows,
+                                t.sweep_terms};
   for (int k = 0; k < MPM_TUNE_N; ++k) v[k] = vals[k];
   return MPM_OK;
 }
@@ -1368,6 +1370,7 @@ int mpm_set_tuning(mpm_ctx* c, const int* v, int n) {
   t.ds_threads = v[2];
   t.ds_stage = v[3];
   t.transport_rows = v[4];
+  t.sweep_terms = v[5];
   if (!valid_tuning(t)) return fail(c, MPM_ERR_ARG, "invalid tuning values");
   c->tune = t;
   drop_graph(c);
@@ -1387,7 +1390,7 @@ int mpm_autotune(mpm_ctx* c, int reps, double* ms_out) {
   c->prof = false;
   CK(cudaStreamSynchronize(c->stream));
   Tuning best = c->tune;
-  double best_ms[3] = {1e300, 1e300, 1e300};
+  double best_ms[4] = {1e300, 1e300, 1e300, 1e300};
   // 1. the fused transport tile: without the decision its outputs (s2, f(s2), kappa^n and the
   //    transmissibilities of s2) depend only on s, f(s) and the fluxes, so repeated launches
   //    write the same values; kappa^n and the transmissibilities of the current s are restored
@@ -1427,6 +1430,20 @@ int mpm_autotune(mpm_ctx* c, int reps, double* ms_out) {
       }, reps, e0, e1);
       if (ms < best_ms[2]) { best_ms[2] = ms; best.ds_threads = nt; best.ds_stage = stage; }
     }
+  // 4. the interface sweeps (up and down, every level; they only read the leaves' right-hand
+  //    sides and rewrite the internal nodes' vectors, so repeating them changes nothing)
+  if (c->n_dof > 0)
+    for (int terms : {4, 8, 16}) {
+      const double ms = time_launches(c, [&] {
+        for (size_t L = 1; L < c->levels.size(); ++L)
+          launch_nd_up(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(),
+                       c->lev_max_nf[L], c->lev_max_nsep[L], c->d_srcmap, false, terms, c->stream);
+        for (int L = (int)c->levels.size() - 2; L >= 2; --L)
+          launch_nd_down(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(),
+                         c->lev_max_nsep[L], c->lev_max_nbnd[L], c->d_pmap, false, terms, c->stream);
+      }, reps, e0, e1);
+      if (ms < best_ms[3]) { best_ms[3] = ms; best.sweep_terms = terms; }
+    }
   c->ev_pool.push_back(e0);
   c->ev_pool.push_back(e1);
   c->prof = saved_prof;
@@ -1436,7 +1453,7 @@ int mpm_autotune(mpm_ctx* c, int reps, double* ms_out) {
   c->tune = best;
   drop_graph(c);
   if (ms_out)
-    for (int k = 0; k < 3; ++k) ms_out[k] = best_ms[k];
+    for (int k = 0; k < 4; ++k) ms_out[k] = best_ms[k] < 1e300 ? best_ms[k] : 0.0;
   return rc;
 }
 

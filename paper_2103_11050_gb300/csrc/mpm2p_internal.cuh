@@ -99,6 +99,8 @@ struct Tuning {
   int ds_threads = 256;     // the same two for the downscaling solve
   int ds_stage = 1;
   int transport_rows = 2;   // rows of the 32-column tile of the fused transport kernel (2, 4 or 8)
+  int sweep_terms = 16;     // interface sweeps: terms of a row's sum per thread (4, 8 or 16; fewer terms,
+                            // more threads per row and more CTAs per level)
 };
 
 // Nested-dissection node of the interface system.  Leaves are subdomains (no
@@ -222,8 +224,8 @@ void launch_element_matrix(const Grid& g, const DevState& d, const DevSub* subs,
 void launch_nd_factor_level(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes,
                             int nlev, int max_nf, int max_nsep, const int* srcmap, cudaStream_t st);
 void launch_nd_up(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
-                  int max_nf, int max_nsep, const int* srcmap, bool pdl, cudaStream_t st);
+                  int max_nf, int max_nsep, const int* srcmap, bool pdl, int terms, cudaStream_t st);
 void launch_nd_down(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
-                    int max_nsep, int max_nbnd, const int* pmap, bool pdl, cudaStream_t st);
+                    int max_nsep, int max_nbnd, const int* pmap, bool pdl, int terms, cudaStream_t st);
 
 }  // namespace mpm

@@ -8,10 +8,10 @@ from tests.cases import case, rel
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [dict(local_threads=64, local_stage=0, ds_threads=64, ds_stage=0, transport_rows=8),
-          dict(local_threads=128, local_stage=1, ds_threads=128, ds_stage=1, transport_rows=4),
-          dict(local_threads=256, local_stage=0, ds_threads=256, ds_stage=0, transport_rows=2),
-          dict(local_threads=64, local_stage=1, ds_threads=128, ds_stage=0, transport_rows=4)]
+SHAPES = [dict(local_threads=64, local_stage=0, ds_threads=64, ds_stage=0, transport_rows=8, sweep_terms=4),
+          dict(local_threads=128, local_stage=1, ds_threads=128, ds_stage=1, transport_rows=4, sweep_terms=8),
+          dict(local_threads=256, local_stage=0, ds_threads=256, ds_stage=0, transport_rows=2, sweep_terms=16),
+          dict(local_threads=64, local_stage=1, ds_threads=128, ds_stage=0, transport_rows=4, sweep_terms=4)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -63,7 +63,8 @@ def test_launch_shapes_agree(prec):
 def test_invalid_tuning_rejected():
     from paper_2103_11050_gb300 import binding as B
     ctx = _ctx(case("p1_2x2"), 0)
-    for bad in (dict(SHAPES[0], local_threads=96), dict(SHAPES[0], ds_stage=2), dict(SHAPES[0], transport_rows=3)):
+    for bad in (dict(SHAPES[0], local_threads=96), dict(SHAPES[0], ds_stage=2), dict(SHAPES[0], transport_rows=3),
+                dict(SHAPES[0], sweep_terms=12)):
         with pytest.raises(B.MPMError) as ei:
             ctx.set_tuning(bad)
         assert ei.value.code == B.MPM_ERR_ARG
@@ -83,7 +84,7 @@ def test_autotune_keeps_the_state(prec):
     ux0, uy0 = a.get_flux()
     tune, ms = a.autotune(3)
     assert tune["local_threads"] in (64, 128, 256) and tune["transport_rows"] in (2, 4, 8)
-    assert all(m > 0 for m in ms)
+    assert all(m > 0 for m in ms) and tune["sweep_terms"] in (4, 8, 16)
     ux1, uy1 = a.get_flux()
     assert rel(ux1, ux0) <= 1e-12 and rel(uy1, uy0) <= 1e-12 + 1e-14
     np.testing.assert_array_equal(a.get_saturation(), b.get_saturation())
