@@ -363,7 +363,8 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
   const int r = blockIdx.y;
   if (d.rebuild[r] != 1) return;
   __shared__ DevSub sd_s;  // the subdomain record, staged once per CTA (indexed by side)
-  if (threadIdx.x == 0) sd_s = subs[blockIdx.x];
+  const int sidx = sub_index(g);
+  if (threadIdx.x == 0) sd_s = subs[sidx];
   __syncthreads();
   const DevSub& sd = sd_s;
   const int a = sd.a, b = sd.b, m = a * b;
@@ -404,14 +405,14 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
       if ((threadIdx.x & 31) == 0) {
         const int bcol = c0 + col;
         if (bcol < sd.ndof) muh[bcol] = s / m;
-        else d.sub_mean[(long long)r * d.st_sub + blockIdx.x] = s / m;
+        else d.sub_mean[(long long)r * d.st_sub + sidx] = s / m;
       }
     }
     __syncthreads();
   }
   // Interface right-hand side (Eq. mrc2) from the non-homogeneous traces just written.
   for (int k = threadIdx.x; k < sd.ndof; k += blockDim.x)
-    phase::element_rhs(g, d, sd, nodes[leaf_node[blockIdx.x]], r, k, fbar);
+    phase::element_rhs(g, d, sd, nodes[leaf_node[sidx]], r, k, fbar);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -499,7 +500,8 @@ __global__ void __launch_bounds__(256) k_basis_solve_tc(Grid g, DevState d, cons
   const int r = blockIdx.y;
   if (d.rebuild[r] != 1) return;
   __shared__ DevSub sd_s;
-  if (threadIdx.x == 0) sd_s = subs[blockIdx.x];
+  const int sidx = sub_index(g);
+  if (threadIdx.x == 0) sd_s = subs[sidx];
   __syncthreads();
   const DevSub& sd = sd_s;
   const int a = sd.a, b = sd.b, m = a * b;
@@ -556,13 +558,13 @@ __global__ void __launch_bounds__(256) k_basis_solve_tc(Grid g, DevState d, cons
       if ((threadIdx.x & 31) == 0) {
         const int bcol = c0 + col;
         if (bcol < sd.ndof) muh[bcol] = sum / m;
-        else d.sub_mean[(long long)r * d.st_sub + blockIdx.x] = sum / m;
+        else d.sub_mean[(long long)r * d.st_sub + sidx] = sum / m;
       }
     }
     __syncthreads();
   }
   for (int k = threadIdx.x; k < sd.ndof; k += blockDim.x)
-    phase::element_rhs(g, d, sd, nodes[leaf_node[blockIdx.x]], r, k, fbar);
+    phase::element_rhs(g, d, sd, nodes[leaf_node[sidx]], r, k, fbar);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -582,7 +584,7 @@ __device__ __forceinline__ void load_kappa_cta(const Grid& g, const DevSub& sd, 
 template <typename T, int A>
 __global__ void k_robin_factor_w(Grid g, DevState d, const DevSub* subs, int scale) {
   extern __shared__ __align__(16) char smem[];
-  const int sidx = blockIdx.x;
+  const int sidx = sub_index(g);
   const int r = blockIdx.y;
   if (d.rebuild[r] != 1) return;
   __shared__ DevSub sd_s;  // the subdomain record, staged once per CTA (indexed by side)
@@ -633,7 +635,7 @@ __global__ void __launch_bounds__(NT) k_mpm_local_w(Grid g, DevState d, const De
   extern __shared__ __align__(16) char smem[];
   __shared__ double red[64];
   __shared__ double fb[4 * kMaxSide];
-  const int sidx = blockIdx.x;
+  const int sidx = sub_index(g);
   const int r = blockIdx.y;
   if (d.rebuild[r] != 0) return;
   __shared__ DevSub sd_s;  // the subdomain record, staged once per CTA (indexed by side)
@@ -746,7 +748,7 @@ __global__ void __launch_bounds__(NT) k_mpm_local_w(Grid g, DevState d, const De
 template <typename T, int A>
 __global__ void k_downscale_factor_w(Grid g, DevState d, const DevSub* subs, int scale) {
   extern __shared__ __align__(16) char smem[];
-  const int sidx = blockIdx.x;
+  const int sidx = sub_index(g);
   const int r = blockIdx.y;
   __shared__ DevSub sd_s;  // the subdomain record, staged once per CTA (indexed by side)
   if (threadIdx.x == 0) sd_s = subs[sidx];
@@ -794,7 +796,7 @@ __global__ void __launch_bounds__(NT) k_downscale_w(Grid g, DevState d, const De
   __shared__ double red[64];
   __shared__ double ub[4 * kMaxSide];  // u_bar per boundary face (face order), +x / +y
   __shared__ int last;
-  const int sidx = blockIdx.x;
+  const int sidx = sub_index(g);
   const int r = blockIdx.y;
   __shared__ DevSub sd_s;  // the subdomain record, staged once per CTA (indexed by side)
   if (threadIdx.x == 0) sd_s = subs[sidx];
@@ -910,13 +912,13 @@ __global__ void __launch_bounds__(NT) k_downscale_w(Grid g, DevState d, const De
   if (threadIdx.x == 0) {
     d.rate_part[(long long)r * d.st_sub + sidx] = rate;
     __threadfence();
-    const unsigned int nblk = gridDim.x * gridDim.y;
+    const unsigned int nblk = (unsigned int)d.st_sub * gridDim.y;  // every subdomain, over all launches
     last = atomicAdd(&d.ticket[0], 1u) == nblk - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  const int nsub = gridDim.x;
+  const int nsub = d.st_sub;
   for (int rr = 0; rr < (int)gridDim.y; ++rr) {
     unsigned long long mb = 0;
     for (int k = threadIdx.x; k < nsub; k += blockDim.x) {

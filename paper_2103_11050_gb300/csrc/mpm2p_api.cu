@@ -21,6 +21,13 @@ namespace mpm {
 long long g_launches = 0;
 }
 
+// The subdomains of one padded factor width A: one launch of each local kernel, over the
+// device list d_list (null when every subdomain has this width).
+struct SubClass {
+  int A, count, max_a, max_b;
+  int* d_list;
+};
+
 struct mpm_ctx {
   Grid g{};
   cudaStream_t stream = nullptr;
@@ -66,6 +73,7 @@ struct mpm_ctx {
   bool use_graph = true;
   bool use_pdl = true;    // programmatic dependent launch along the interface-solve chain
   Tuning tune;            // launch shapes (defaults, mpm_set_tuning or mpm_autotune)
+  std::vector<SubClass> classes;  // subdomains by padded factor width (one launch of a local kernel each)
   int next_pass = 0;      // pass of the next stand-alone interface solve (1 after mpm_perturbation_correction)
   // The saturation (and f(s)) live in two buffers that swap at every transport substep; a
   // graph reads and writes fixed buffers, so one graph is kept per buffer parity (slot 0:
@@ -347,6 +355,7 @@ int release_decomposition(mpm_ctx* c) {
   c->d_subs = nullptr;
   c->d_nodes = nullptr;
   c->d_leaf_node = c->d_level_nodes = c->d_srcmap = c->d_pmap = nullptr;
+  c->classes.clear();
   c->have_dec = false;
   c->have_basis = false;
   return MPM_OK;
@@ -355,15 +364,30 @@ int release_decomposition(mpm_ctx* c) {
 // ---------------------------------------------------------------------------------------
 // Launch sequences.
 
+// Calls f(grid, count, max_a, max_b) once per width class: the local kernels run one launch
+// per padded factor width, each over its class's subdomains (Grid::sub_list).
+template <typename F>
+void per_class(const mpm_ctx* c, F f) {
+  for (const SubClass& k : c->classes) {
+    Grid gk = c->g;
+    gk.sub_list = c->classes.size() > 1 ? k.d_list : nullptr;
+    f(gk, k.count, k.max_a, k.max_b);
+  }
+}
+
 int run_build(mpm_ctx* c) {
   const Grid& g = c->g;
   DevState& d = c->d;
   cudaStream_t st = c->stream;
   const int nsub = (int)c->subs.size();
   prof_begin(c, MPM_STAGE_BASIS);
-  launch_robin_factor(g, d, c->d_subs, nsub, c->max_a, c->max_b, fp32_robin(c), st);
-  launch_basis_solve(g, d, c->d_subs, nsub, c->max_a, c->max_b, tc_kind(c), fp32_robin(c), c->ir_tol, c->ir_max,
-                     c->d_nodes, c->d_leaf_node, st);
+  per_class(c, [&](const Grid& gk, int n, int ma, int mb) {
+    launch_robin_factor(gk, d, c->d_subs, n, ma, mb, fp32_robin(c), st);
+  });
+  per_class(c, [&](const Grid& gk, int n, int ma, int mb) {
+    launch_basis_solve(gk, d, c->d_subs, n, ma, mb, tc_kind(c), fp32_robin(c), c->ir_tol, c->ir_max, c->d_nodes,
+                       c->d_leaf_node, st);
+  });
   if (c->n_dof > 0) launch_element_matrix(g, d, c->d_subs, nsub, c->d_nodes, c->d_leaf_node, st);
   prof_end(c, MPM_STAGE_BASIS);
   if (c->n_dof > 0) {
@@ -385,8 +409,10 @@ int run_perturbation(mpm_ctx* c, int pass = 0) {
   const Grid& g = c->g;
   const int nsub = (int)c->subs.size();
   prof_begin(c, MPM_STAGE_PERTURB);
-  launch_mpm_local(g, c->d, c->d_subs, nsub, c->max_a, c->max_b, robin_fp32_mode(c->fac_prec), c->ir_tol,
-                   c->ir_max, c->d_nodes, c->d_leaf_node, c->tune.local_threads, c->tune.local_stage, pass, c->stream);
+  per_class(c, [&](const Grid& gk, int n, int ma, int mb) {
+    launch_mpm_local(gk, c->d, c->d_subs, n, ma, mb, robin_fp32_mode(c->fac_prec), c->ir_tol, c->ir_max, c->d_nodes,
+                     c->d_leaf_node, c->tune.local_threads, c->tune.local_stage, pass, c->stream);
+  });
   prof_end(c, MPM_STAGE_PERTURB);
   c->next_pass = pass;
   return check_launch(c);
@@ -436,7 +462,9 @@ int run_interface(mpm_ctx* c, int pass = 0) {
 int fork_downscale_factor(mpm_ctx* c) {
   CK(cudaEventRecord(c->ev_fork, c->stream));
   CK(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
-  launch_downscale_factor(c->g, c->d, c->d_subs, (int)c->subs.size(), c->max_a, c->max_b, fp32(c), c->side_stream);
+  per_class(c, [&](const Grid& gk, int n, int ma, int mb) {
+    launch_downscale_factor(gk, c->d, c->d_subs, n, ma, mb, fp32(c), c->side_stream);
+  });
   CK(cudaEventRecord(c->ev_join, c->side_stream));
   c->factor_forked = true;
   return check_launch(c);
@@ -468,10 +496,14 @@ int run_downscale(mpm_ctx* c, bool after_interface, bool forked) {
   }
   prof_begin(c, MPM_STAGE_DOWNSCALE);
   if (!forked) {
-    launch_downscale_factor(c->g, c->d, c->d_subs, (int)c->subs.size(), c->max_a, c->max_b, fp32(c), c->stream);
+    per_class(c, [&](const Grid& gk, int n, int ma, int mb) {
+      launch_downscale_factor(gk, c->d, c->d_subs, n, ma, mb, fp32(c), c->stream);
+    });
   }
-  launch_downscale(c->g, c->d, c->d_subs, (int)c->subs.size(), c->max_a, c->max_b, fp32(c), c->ir_tol, c->ir_max,
-                   after_interface && joined_before && c->use_pdl, c->tune.ds_threads, c->tune.ds_stage, c->stream);
+  per_class(c, [&](const Grid& gk, int n, int ma, int mb) {
+    launch_downscale(gk, c->d, c->d_subs, n, ma, mb, fp32(c), c->ir_tol, c->ir_max,
+                     after_interface && joined_before && c->use_pdl, c->tune.ds_threads, c->tune.ds_stage, c->stream);
+  });
   prof_end(c, MPM_STAGE_DOWNSCALE);
   return check_launch(c);
 }
@@ -663,6 +695,7 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   g.degree = 0;
   g.alpha = 1.0;
   g.order = 0;
+  g.sub_list = nullptr;
   const size_t nc = (size_t)R * nx * ny;
   DevState& d = c->d;
   int rc = MPM_OK;
@@ -862,7 +895,6 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   }
   c->n_dof = off;
   // subdomains
-  const int Apad = pad_width(*std::max_element(col_w, col_w + ncx));
   std::vector<int> xo(ncx + 1, 0), yo(ncy + 1, 0);
   for (int I = 0; I < ncx; ++I) xo[I + 1] = xo[I] + col_w[I];
   for (int J = 0; J < ncy; ++J) yo[J + 1] = yo[J] + row_h[J];
@@ -919,7 +951,8 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
       s.t_off = t_off;
       s.tr_off = tr_off;
       s.pf_off = pf_off;
-      q_off += (long long)s.b * Apad * Apad;
+      s.A = pad_width(s.a);
+      q_off += (long long)s.b * s.A * s.A;
       t_off += 4LL * m;
       tr_off += (long long)nface * nd;
       pf_off += (long long)m * (nd + 1);
@@ -932,6 +965,23 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
       c->max_face = std::max(c->max_face, nface);
       c->n_hat += nd;
     }
+  }
+  // width classes of the local kernels (Grid::sub_list): one per padded width present
+  std::vector<std::vector<int>> cls_lists;
+  c->classes.clear();
+  for (int A : {8, 16, 32}) {
+    SubClass k{A, 0, 0, 0, nullptr};
+    std::vector<int> lst;
+    for (int i = 0; i < (int)c->subs.size(); ++i)
+      if (c->subs[i].A == A) {
+        lst.push_back(i);
+        k.max_a = std::max(k.max_a, c->subs[i].a);
+        k.max_b = std::max(k.max_b, c->subs[i].b);
+      }
+    if (lst.empty()) continue;
+    k.count = (int)lst.size();
+    c->classes.push_back(k);
+    cls_lists.push_back(lst);
   }
   // nested dissection tree
   std::vector<HostNode> hn;
@@ -1054,12 +1104,18 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   if (!rc) rc = dalloc_t(c, A, &c->d_level_nodes, level_nodes.size());
   if (!rc) rc = dalloc_t(c, A, &c->d_srcmap, srcmap.size());
   if (!rc) rc = dalloc_t(c, A, &c->d_pmap, pmap.size());
+  if (c->classes.size() > 1)
+    for (size_t k = 0; k < c->classes.size() && !rc; ++k) rc = dalloc_t(c, A, &c->classes[k].d_list, cls_lists[k].size());
   if (rc) {
     release_decomposition(c);
     return rc;
   }
   CK(cudaMemcpyAsync(c->d_subs, c->subs.data(), nsub * sizeof(DevSub), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(d.rho_f, rho_host.data(), rho_host.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (c->classes.size() > 1)
+    for (size_t k = 0; k < c->classes.size(); ++k)
+      CK(cudaMemcpyAsync(c->classes[k].d_list, cls_lists[k].data(), cls_lists[k].size() * sizeof(int),
+                         cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->d_nodes, c->nodes.data(), nn * sizeof(DevNode), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->d_leaf_node, c->leaf_node.data(), nsub * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->d_level_nodes, level_nodes.data(), level_nodes.size() * sizeof(int), cudaMemcpyHostToDevice,
@@ -1408,25 +1464,31 @@ int mpm_autotune(mpm_ctx* c, int reps, double* ms_out) {
   CK(cudaMemcpyAsync(flags.data(), d.rebuild, sizeof(int) * g.R, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   launch_fill_flags(g, d, 0, c->stream);
-  Grid g0 = g;  // timed as the epsilon^0 solve, which leaves the first-order pressure dp0 alone
-  g0.order = 0;
+  // (timed as the epsilon^0 solve, which leaves the first-order pressure dp0 alone)
   for (int nt : {64, 128, 256})
     for (int stage : {0, 1}) {
       const double ms = time_launches(c, [&] {
-        launch_mpm_local(g0, d, c->d_subs, nsub, c->max_a, c->max_b, robin_fp32_mode(c->fac_prec), c->ir_tol,
-                         c->ir_max, c->d_nodes, c->d_leaf_node, nt, stage, 0, c->stream);
+        per_class(c, [&](const Grid& gk, int n, int ma, int mb) {
+          Grid g0k = gk;
+          g0k.order = 0;
+          launch_mpm_local(g0k, d, c->d_subs, n, ma, mb, robin_fp32_mode(c->fac_prec), c->ir_tol, c->ir_max,
+                           c->d_nodes, c->d_leaf_node, nt, stage, 0, c->stream);
+        });
       }, reps, e0, e1);
       if (ms < best_ms[1]) { best_ms[1] = ms; best.local_threads = nt; best.local_stage = stage; }
     }
   CK(cudaMemcpyAsync(d.rebuild, flags.data(), sizeof(int) * g.R, cudaMemcpyHostToDevice, c->stream));
   // 3. the downscaling solve with the factor of the current kappa^n (its inputs, the traces and
   //    targets of the last interface solve, are left unchanged; its outputs are recomputed)
-  launch_downscale_factor(g, d, c->d_subs, nsub, c->max_a, c->max_b, fp32(c), c->stream);
+  per_class(c, [&](const Grid& gk, int n, int ma, int mb) {
+    launch_downscale_factor(gk, d, c->d_subs, n, ma, mb, fp32(c), c->stream);
+  });
   for (int nt : {64, 128, 256})
     for (int stage : {0, 1}) {
       const double ms = time_launches(c, [&] {
-        launch_downscale(g, d, c->d_subs, nsub, c->max_a, c->max_b, fp32(c), c->ir_tol, c->ir_max, false, nt, stage,
-                         c->stream);
+        per_class(c, [&](const Grid& gk, int n, int ma, int mb) {
+          launch_downscale(gk, d, c->d_subs, n, ma, mb, fp32(c), c->ir_tol, c->ir_max, false, nt, stage, c->stream);
+        });
       }, reps, e0, e1);
       if (ms < best_ms[2]) { best_ms[2] = ms; best.ds_threads = nt; best.ds_stage = stage; }
     }

@@ -31,6 +31,7 @@ __host__ __device__ inline int face_side_off(int side, int a, int b) {
 
 struct DevSub {
   int x0, y0, a, b;
+  int A;             // padded width of this subdomain's factor blocks, pad_width(a)
   int ndof;          // interface DOFs on the sides of this subdomain
   int dof_off;       // offset in per-DOF tables (sum of ndof of previous subdomains)
   int face_off;      // offset in per-face tables (sum of 2(a+b))
@@ -58,12 +59,20 @@ struct Grid {
   double inv_seg;  // 1 / seg_len
   double alpha;
   int order;  // MPM-2P perturbation order: 0 (Eq. mpm_tf_3 only) or 1 (plus Eq. mpm_tf_4, l = 1)
+  // The subdomains of one launch of a local kernel: blockIdx.x indexes this list (device
+  // memory), or the subdomains themselves when it is null.  Decompositions with subdomain
+  // widths of more than one padded width (8, 16, 32) launch the local kernels once per width,
+  // each over its own list, so that every factor is padded to its own width only.
+  const int* sub_list;
   __host__ __device__ long long ncell() const { return (long long)nx * ny; }
   __host__ __device__ long long nfx() const { return (long long)ny * (nx + 1); }
   __host__ __device__ long long nfy() const { return (long long)(ny + 1) * nx; }
 };
 
 #ifdef __CUDACC__
+// Subdomain handled by this CTA of a local kernel (see Grid::sub_list).
+__device__ __forceinline__ int sub_index(const Grid& g) { return g.sub_list ? g.sub_list[blockIdx.x] : (int)blockIdx.x; }
+
 // Programmatic dependent launch.  A kernel launched with the programmatic-serialisation
 // attribute may start once every block of its predecessor in the stream has called
 // pdl_trigger(), i.e. while the predecessor still runs.  Before pdl_wait() such a kernel
