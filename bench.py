@@ -414,6 +414,51 @@ def run_gpu(args, wl):
 
     study = None if args.no_study else precision_study()
 
+    # Other workloads of the same path, for context: config 1 (64^2, a rebuild at every step:
+    # the MRCM cost the RCR model counts), config 2 (256^2) and config 4 (the ensemble):
+    # device time per step of each kind (graph launches, L2 flushed before each step).
+    # The ensemble (config 4: 256 realisations of 128^2 on the uneven decomposition) gets its
+    # own autotuned shapes and its blended rate over its own 500-step trajectory.
+    def secondary():
+        out = {}
+        for name in ("gaussian64", "gaussian256", "ensemble"):
+            w2 = Workload(name)
+            tune = None
+            if name == "ensemble" and not args.no_tune:
+                key = AT.shape_key(w2.R, w2.nx, w2.ny, w2.col_w, w2.row_h, prec, torch.cuda.get_device_name())
+                ctx = setup_ctx(B, w2, prec, stream.cuda_stream)
+                ctx.init(w2.eta)
+                for _ in range(3):
+                    ctx.step(w2.eta, CFL, N_SUB)
+                tune, _ = AT.tuned(ctx, key)
+                ctx.close()
+            per = {}
+            for kind, eta in (("rebuild", -1.0), ("mpm", 1e300)):
+                ctx = setup_ctx(B, w2, prec, stream.cuda_stream, tune)
+                ctx.init(eta)
+                for _ in range(3):
+                    ctx.step(eta, CFL, N_SUB)
+                t = timed_steps(ctx, 10 if name != "ensemble" else 4, eta)
+                ctx.close()
+                per[kind] = statistics.median(t)
+            rec = {"cells": w2.cells, "rebuild_step_ms": per["rebuild"], "mpm_step_ms": per["mpm"],
+                   "rebuild_steps_rate": w2.cells / (per["rebuild"] / 1e3),
+                   "mpm_steps_rate": w2.cells / (per["mpm"] / 1e3)}
+            if name == "ensemble":
+                ctx = setup_ctx(B, w2, prec, stream.cuda_stream, tune)
+                ctx.init(w2.eta)
+                for _ in range(w2.steps):
+                    ctx.step(w2.eta, CFL, N_SUB)
+                f = (ctx.get_stats()["rebuilds"] - w2.R) / (w2.R * w2.steps)
+                ctx.close()
+                t_bl = f * per["rebuild"] + (1 - f) * per["mpm"]
+                rec.update({"workload": w2.desc, "rebuild_fraction": f, "blended_rate": w2.cells / (t_bl / 1e3),
+                            "tuning": tune})
+            out[name] = rec
+        return out
+
+    small = None if args.no_study else secondary()
+
     # End to end through the C ABI with host buffers: per step the saturation is copied in from
     # pinned host memory, the step runs, and the saturation is read back.  MPM-2P steps
     # (eta = 1e300) and rebuild steps (eta < 0) are timed on fresh contexts and blended like
@@ -498,6 +543,7 @@ def run_gpu(args, wl):
         "peaks_source": pk_kind,
         "ir_sweeps_max": main["ir"],
         "step_split": step_split,
+        "other_workloads": small,
         "precision_study": {"what": "rebuild steps (init + 3 rebuild steps, the last two timed) per precision mode of "
                                     "the local solves; basis-function solves on tensor cores in tf32, tf32x3, bf16",
                             "modes": study},
