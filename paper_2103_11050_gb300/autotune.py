@@ -40,6 +40,14 @@ def _load(path):
         return {}
 
 
+def cached(key, names, path=CACHE):
+    """The cached tuning of `key` when it holds exactly the parameters `names`, else None."""
+    entry = _load(path).get(key)
+    if entry is not None and set(entry["tuning"]) == set(names):
+        return dict(entry["tuning"])
+    return None
+
+
 def tuned(ctx, key, path=CACHE, reps=5):
     """Apply the cached tuning of `key` to ctx, or (cache miss) autotune ctx, which must hold a
     stored basis, and cache the result.  Returns (tuning dict, source) with source "cache" or
