@@ -47,6 +47,7 @@ E2E_PASSES = 3
 CFL = 0.5
 N_SUB = 1
 FORCED_REBUILDS = 3
+IR_TOL = 1e-14  # backward-error target of the FP64 refinement of float32 factors (--ir-tol)
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the step's kernels on the
 # default workload, from an ncu capture of this code (profiles/); a kernel is left out when
 # it changed since its capture.
@@ -164,7 +165,7 @@ def setup_ctx(B, wl, prec, stream, tune=None):
         ctx.set_tuning(tune)
     mode = {"fp32": B.PREC_FP32_IR, "fp32all": B.PREC_FP32_IR_ALL, "fp64": B.PREC_FP64, "tf32": B.PREC_TF32_IR,
             "tf32x3": B.PREC_TF32X3_IR, "bf16": B.PREC_BF16_IR}[prec]
-    ctx.set_precision(mode, 1e-14, 30)
+    ctx.set_precision(mode, IR_TOL, 30)
     ctx.set_fluids(wl.M)
     ctx.set_boundary((0, 0, 1, 1), (1.0, 0.0, 0.0, 0.0), 1.0)
     ctx.set_decomposition(wl.col_w, wl.row_h, 4, 1, 1.0)
@@ -365,7 +366,7 @@ def run_gpu(args, wl):
         main = trajectory(prec)
         return {"metric": METRIC, "window_value": cells * args.steps / (sum(main["per"]) / 1e3), "unit": UNIT,
                 "steps": args.steps, "warmup": args.warmup, "timed_steps_rebuild": main["rebuild_steps"],
-                "gpu_launches": main["launches"], "config": {"workload": wl.desc, "precision": PREC[prec],
+                "gpu_launches": main["launches"], "config": {"workload": wl.desc, "precision": PREC[prec], "ir_tol": IR_TOL,
                                                              "tuning": tunes.get(prec)}}
     with ClockSampler(0) as clk:
         main = trajectory(prec)
@@ -533,7 +534,7 @@ def run_gpu(args, wl):
                    "value": "blended over the workload's rebuild mix: cells / (f t_rebuild + (1-f) t_mpm)",
                    "timed_steps_rebuild": main["rebuild_steps"], "timed_steps_mpm": args.steps - main["rebuild_steps"],
                    "l2": "flushed before every timed step (256 MB write outside the timed region)",
-                   "precision": PREC[prec],
+                   "precision": PREC[prec], "ir_tol": IR_TOL,
                    "tuning": None if args.no_tune else {"values": tunes[prec][0], "source": tunes[prec][1]}},
         "window_value": cells * args.steps / (window_ms / 1e3),
         "gpu_launches": main["launches"],
@@ -604,7 +605,7 @@ def cpu_baseline(wl, budget_s=20.0, max_steps=None, gpu_check=None):
         errs = {}
         for prec in ("fp32", "fp64"):
             ctx = B.Context(1, nx, ny, 1.0, ny / nx, stream=stream.cuda_stream)
-            ctx.set_precision({"fp32": B.PREC_FP32_IR, "fp64": B.PREC_FP64}[prec], 1e-14, 30)
+            ctx.set_precision({"fp32": B.PREC_FP32_IR, "fp64": B.PREC_FP64}[prec], IR_TOL, 30)
             ctx.set_fluids(wl.M)
             ctx.set_boundary((0, 0, 1, 1), (1.0, 0.0, 0.0, 0.0), 1.0)
             ctx.set_decomposition(cw, rh, 4, 1, 1.0)
@@ -691,6 +692,7 @@ def breakthrough_study(args, wl):
 
 
 def main():
+    global IR_TOL
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=197)
@@ -716,7 +718,10 @@ def main():
     ap.add_argument("--eager", action="store_true",
                     help="with --window-only: launch the steps kernel by kernel instead of as one CUDA graph (ncu "
                          "does not profile the kernels of graphs with conditional nodes)")
+    ap.add_argument("--ir-tol", type=float, default=IR_TOL,
+                    help="backward-error target of the FP64 refinement of the float32 factors")
     args = ap.parse_args()
+    IR_TOL = args.ir_tol
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     wl = Workload(args.workload)

@@ -112,8 +112,10 @@ typedef struct mpm_stats {
 enum {
   MPM_STAGE_TRANSPORT = 0,     /* upwind substeps (CFL step), kappa^n, epsilon and
                                   the decision (all in the transport kernel)         */
-  MPM_STAGE_EPSILON = 1,       /* kept for layout: nothing is timed here since the
-                                  decision moved into the transport kernel           */
+  MPM_STAGE_DS_FACTOR = 1,     /* downscaling factorisation of kappa^n (Eq. mpm_upd);
+                                  a step overlaps it with the perturbation and
+                                  interface solves on a second stream, the profiler
+                                  runs it alone on the context's stream              */
   MPM_STAGE_BASIS = 2,         /* Robin factorisation, BF solves, element matrices   */
   MPM_STAGE_IFACE_FACTOR = 3,  /* nested-dissection factorisation of the interface   */
   MPM_STAGE_PERTURB = 4,       /* MPM-2P residual, local solve, interface RHS        */
@@ -282,9 +284,10 @@ int mpm_set_execution(mpm_ctx* ctx, int flags);
  *   [1] 1: that kernel stages the stored Robin factor in shared memory, 0: reads it from global
  *       memory (smaller CTAs, more subdomains resident per SM)
  *   [2], [3] the same for the downscaling solve
- *   [4] rows (2, 4 or 8) of the 32-column cell tile of the fused transport kernel
+ *   [4] rows (4, 8 or 16) of the 32-column cell tile of the fused transport kernel (two rows
+ *       per thread)
  *   [5] interface sweeps: terms of a row's sum per thread (4, 8 or 16)
- * Defaults: 256, 1, 256, 1, 2, 16.  mpm_get_tuning / mpm_set_tuning read and write them (n >=
+ * Defaults: 256, 1, 256, 1, 8, 16.  mpm_get_tuning / mpm_set_tuning read and write them (n >=
  * MPM_TUNE_N; invalid values: MPM_ERR_ARG); results do not depend on them beyond rounding.
  * mpm_autotune times every candidate of each kernel on the context's current data (reps
  * timed launches each, the median taken; 1 <= reps <= 100) and keeps the fastest.  It needs a

@@ -34,7 +34,7 @@ FUNCTIONS = [
 ]
 TUNE_KEYS = ["local_threads", "local_stage", "ds_threads", "ds_stage", "transport_rows", "sweep_terms"]
 
-STAGES = ["transport", "epsilon", "basis", "iface_factor", "perturb", "iface_solve", "downscale", "iface_up",
+STAGES = ["transport", "ds_factor", "basis", "iface_factor", "perturb", "iface_solve", "downscale", "iface_up",
           "iface_down", "reconstruct"]
 
 

@@ -17,7 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libmpm2p.so")
 SOURCES = ["mpm2p_api.cu", "k_grid.cu", "k_local.cu", "k_iface.cu", "k_noalloc.cu"]
-HEADERS = ["mpm2p_internal.cuh", "k_local_warp.cuh", "k_iface_phases.cuh", "fp64_div.cuh", "fp_bits.cuh"]
+HEADERS = ["mpm2p_internal.cuh", "k_local_warp.cuh", "k_local_tc.cuh", "k_iface_phases.cuh", "fp64_div.cuh",
+           "fp_bits.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -1,13 +1,16 @@
 // Float64 reciprocal and division for a part whose float64 pipe is narrow (on GB300 the
 // correctly rounded float64 division costs tens of float64 instructions).
 //
-//   rcp64(x): seed y0 = 1/x in float32 (hardware approximation of the reciprocal of x
-//             truncated to float32; relative error below 2^-22 + 2^-23), then two
-//             Newton-Raphson steps for f(y) = 1/y - x, y <- y + y (1 - x y), each squaring the
-//             relative error (below 2^-42, then below the float64 rounding of the iteration).
-//   div64(a, b): q = a rcp64(b), then one residual correction q <- q + rcp64(b) (a - b q)
-//             (Markstein, IBM J. Res. Dev. 34(1), 1990), which leaves q within one ulp of
-//             a / b whenever a / b is a finite normal number.
+//   Seed y0 = 1/x in float32 (hardware approximation of the reciprocal of x truncated to
+//   float32; relative error e0 below 2^-22 + 2^-23).  A Newton-Raphson step for
+//   f(y) = 1/y - x, y <- y + y (1 - x y), squares the relative error (e1 <= e0^2 + 2^-53,
+//   about 2^-44).
+//   rcp64(x): two steps (error below the float64 rounding of the iteration).
+//   div64(a, b): one step, q = a y1, then one residual correction q <- q + y1 (a - b q)
+//             (Markstein, IBM J. Res. Dev. 34(1), 1990): with r = a - b q from one fused
+//             multiply-add, the corrected quotient is off by about |r / b| e1, i.e. 2^-88
+//             |a / b|, before its final rounding, so q is within one ulp of a / b whenever
+//             a / b is a finite normal number.
 // The range test on the divisor, its truncation to float32 and the widening of the seed back
 // to float64 are integer repackings of the bit patterns (fp_bits.cuh): on GB300 the float64
 // conversions would occupy the narrow float64 pipe.  A divisor outside [2^-125, 2^125) in
@@ -36,9 +39,14 @@ __device__ __forceinline__ bool f32_seed_ok(double x, float& xf) {
   return true;
 }
 
+// seed and one Newton-Raphson step (relative error about 2^-44)
+__device__ __forceinline__ double newton_rcp1(double x, float xf) {
+  const double y = f32_normal_to_f64(rcp_approx_f32(xf));  // a normal float32: exact widening
+  return fma(y, fma(-x, y, 1.0), y);
+}
+
 __device__ __forceinline__ double newton_rcp(double x, float xf) {
-  double y = f32_normal_to_f64(rcp_approx_f32(xf));  // a normal float32: exact widening
-  y = fma(y, fma(-x, y, 1.0), y);
+  const double y = newton_rcp1(x, xf);
   return fma(y, fma(-x, y, 1.0), y);
 }
 
@@ -51,7 +59,7 @@ __device__ __forceinline__ double rcp64(double x) {
 __device__ __forceinline__ double div64(double a, double b) {
   float bf;
   if (!f32_seed_ok(b, bf)) return a / b;
-  const double y = newton_rcp(b, bf);
+  const double y = newton_rcp1(b, bf);
   const double q = a * y;
   return fma(fma(-b, q, a), y, q);
 }

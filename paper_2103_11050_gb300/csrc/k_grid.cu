@@ -150,24 +150,28 @@ __global__ void k_upwind(Grid g, DevState d, double cfl, double fmax_) {
   }
 }
 
-constexpr int kTX = 32;  // columns of the cell tile of the last transport substep (one cell per thread); its
-                        // rows kTY are a template parameter: small tiles spread the FP64 work over the SMs,
-                        // tall tiles recompute fewer halo cells
+constexpr int kTX = 32;  // columns of the cell tile of the last transport substep; its rows kTY are a
+                        // template parameter (4, 8 or 16), two rows per thread: small tiles spread the
+                        // FP64 work over the SMs, tall tiles recompute fewer halo cells
 
 // Last upwind substep fused with kappa^n (Algorithm 1: transport, then kappa^n): each CTA
-// updates a kTX x kTY tile plus its east column and north row, with kappa^n of each of these
-// cells, into shared memory, then writes s2, f(s2), kappa^n = lambda(s2) K and the east /
-// north transmissibilities of its cells.
+// updates a kTX x kTY tile plus its east column and north row, with the water mobility
+// M s^2, the total mobility lambda(s) and kappa^n = lambda(s) K of each of these cells, into
+// shared memory, then writes s2, f(s2) = M s^2 / lambda(s) (from the stored mobilities),
+// kappa^n and the east / north transmissibilities of its cells.  A thread takes two cells of
+// one column (rows lj and lj + kTY / 2).
 // decide = 1 (mpm_step): also the partial sums of ||kappa^n - kappa^m||^2, ||kappa^m||^2 per
 // CTA; the last CTA to finish takes the Algorithm 1 decision for every realisation with the
 // epsilon of the previous pass (rebuild_r = eps_r > eta), stores the new epsilon (0 where
 // the basis is rebuilt, else sqrt(num / den)), counts the branches and, in a CUDA graph
 // (set_handle), sets the conditional handle of the rebuild body.
 template <int kTY>
-__global__ void __launch_bounds__(kTX * kTY) k_upwind_kappa(Grid g, DevState d, double cfl, double fmax_, int decide,
-                                                            double eta, cudaGraphConditionalHandle h_reb,
-                                                            int set_handle) {
+__global__ void __launch_bounds__(kTX * kTY / 2) k_upwind_kappa(Grid g, DevState d, double cfl, double fmax_,
+                                                                int decide, double eta,
+                                                                cudaGraphConditionalHandle h_reb, int set_handle) {
   __shared__ double sn[kTY + 1][kTX + 1];  // s2
+  __shared__ double sw[kTY + 1][kTX + 1];  // M s2^2
+  __shared__ double sl[kTY + 1][kTX + 1];  // lambda(s2)
   __shared__ double sk[kTY + 1][kTX + 1];  // kappa^n of s2
   __shared__ double sh[32];
   __shared__ double lam_s, fin_s;
@@ -192,27 +196,34 @@ __global__ void __launch_bounds__(kTX * kTY) k_upwind_kappa(Grid g, DevState d, 
     const int i = tx0 + li, j = ty0 + lj;
     if (i < nx && j < ny && !(li == kTX && lj == kTY)) {
       const double v = upwind_cell(g, ux, uy, d.fs + base, d.s + base, lam, f_in, i, j);
+      const double o = 1.0 - v;
+      const double lw = g.M * v * v;
+      const double lt = lw + o * o;  // lambda(v), as mobility()
       sn[lj][li] = v;
-      sk[lj][li] = mobility(v, g.M) * d.K[base + (long long)j * nx + i];
+      sw[lj][li] = lw;
+      sl[lj][li] = lt;
+      sk[lj][li] = lt * d.K[base + (long long)j * nx + i];
     }
   }
   __syncthreads();
-  const int li = threadIdx.x % kTX, lj = threadIdx.x / kTX;
-  const int i = tx0 + li, j = ty0 + lj;
   double num = 0.0, den = 0.0;
-  if (i < nx && j < ny) {
-    const long long c = base + (long long)j * nx + i;
-    const double s_new = sn[lj][li];
-    d.s2[c] = s_new;
-    d.fs2[c] = fracflow(s_new, g.M);
-    const double kn = sk[lj][li];
-    d.kap_n[c] = kn;
-    if (i < nx - 1) d.tx[(long long)r * g.nfx() + (long long)j * (nx + 1) + i + 1] = harm(kn, sk[lj][li + 1]);
-    if (j < ny - 1) d.ty[(long long)r * g.nfy() + (long long)(j + 1) * nx + i] = harm(kn, sk[lj + 1][li]);
-    if (decide) {
-      const double km = d.kap_m[c];
-      num = (kn - km) * (kn - km);
-      den = km * km;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int li = threadIdx.x % kTX, lj = threadIdx.x / kTX + half * (kTY / 2);
+    const int i = tx0 + li, j = ty0 + lj;
+    if (i < nx && j < ny) {
+      const long long c = base + (long long)j * nx + i;
+      d.s2[c] = sn[lj][li];
+      d.fs2[c] = div64(sw[lj][li], sl[lj][li]);  // fracflow(s2)
+      const double kn = sk[lj][li];
+      d.kap_n[c] = kn;
+      if (i < nx - 1) d.tx[(long long)r * g.nfx() + (long long)j * (nx + 1) + i + 1] = harm(kn, sk[lj][li + 1]);
+      if (j < ny - 1) d.ty[(long long)r * g.nfy() + (long long)(j + 1) * nx + i] = harm(kn, sk[lj + 1][li]);
+      if (decide) {
+        const double km = d.kap_m[c];
+        num += (kn - km) * (kn - km);
+        den += km * km;
+      }
     }
   }
   if (!decide) return;
@@ -360,15 +371,15 @@ void launch_upwind(const Grid& g, const DevState& d, double cfl, double fmax_, c
 int upwind_kappa_blocks_rows(const Grid& g, int rows) { return ((g.nx + kTX - 1) / kTX) * ((g.ny + rows - 1) / rows); }
 
 // the largest grid over the tile shapes (sizes the per-block partial sums)
-int upwind_kappa_blocks(const Grid& g) { return upwind_kappa_blocks_rows(g, 2); }
+int upwind_kappa_blocks(const Grid& g) { return upwind_kappa_blocks_rows(g, 4); }
 
 void launch_upwind_kappa(const Grid& g, const DevState& d, double cfl, double fmax_, bool decide, double eta,
                          cudaGraphConditionalHandle h_reb, bool set_handle, int rows, cudaStream_t st) {
   const dim3 grid(upwind_kappa_blocks_rows(g, rows), g.R);
   const int dec = decide ? 1 : 0, sh = set_handle ? 1 : 0;
-  if (rows >= 8) k_upwind_kappa<8><<<grid, kTX * 8, 0, st>>>(g, d, cfl, fmax_, dec, eta, h_reb, sh);
-  else if (rows >= 4) k_upwind_kappa<4><<<grid, kTX * 4, 0, st>>>(g, d, cfl, fmax_, dec, eta, h_reb, sh);
-  else k_upwind_kappa<2><<<grid, kTX * 2, 0, st>>>(g, d, cfl, fmax_, dec, eta, h_reb, sh);
+  if (rows >= 16) k_upwind_kappa<16><<<grid, kTX * 8, 0, st>>>(g, d, cfl, fmax_, dec, eta, h_reb, sh);
+  else if (rows >= 8) k_upwind_kappa<8><<<grid, kTX * 4, 0, st>>>(g, d, cfl, fmax_, dec, eta, h_reb, sh);
+  else k_upwind_kappa<4><<<grid, kTX * 2, 0, st>>>(g, d, cfl, fmax_, dec, eta, h_reb, sh);
   ++g_launches;
 }
 

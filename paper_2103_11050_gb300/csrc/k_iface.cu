@@ -26,6 +26,7 @@
 #include <algorithm>
 
 #include "k_iface_phases.cuh"
+#include "k_local_warp.cuh"
 #include "mpm2p_internal.cuh"
 
 namespace mpm {
@@ -108,90 +109,112 @@ __global__ void k_nd_assemble(Grid g, DevState d, const DevNode* nodes, const in
   }
 }
 
-// Sweep step 1: invert the pivot block P = [k0, k0+nb) of every node (one CTA per node).
-__global__ void k_sweep_pivot(Grid g, DevState d, const DevNode* nodes, const int* level_nodes, int k0) {
-  __shared__ double piv[2][2 * kPivotChunk + 1];
-  const int r = blockIdx.y;
-  if (d.rebuild[r] != 1) return;
-  const int nid = level_nodes[blockIdx.x];
-  const DevNode nd = nodes[nid];
-  if (k0 >= nd.nsep) return;
-  const int nb = min(kPivotChunk, nd.nsep - k0);
-  double* F = d.front + (long long)r * d.st_front + nd.f_off;
-  const int tid = threadIdx.x;
-  const int i = tid / kPivotChunk, k = tid - i * kPivotChunk;
-  const bool active = i < nb && k < nb;
-  double v = active ? F[(long long)(k0 + i) * nd.nf + k0 + k] : 0.0;
-  for (int p = 0; p < nb; ++p) {
-    double* buf = piv[p & 1];
-    if (active) {
-      if (k == p) buf[i] = v;
-      if (i == p) buf[kPivotChunk + k] = v;
-      if (i == p && k == p) buf[2 * kPivotChunk] = rcp64(v);
-    }
-    __syncthreads();
-    if (active) {
-      const double ip = buf[2 * kPivotChunk];
-      const double mip = buf[i], mpk = buf[kPivotChunk + k];
-      if (i == p && k == p) v = ip;
-      else if (i == p) v = mpk * ip;
-      else if (k == p) v = -mip * ip;
-      else v = v - mip * (mpk * ip);
-    }
+// The factorisation of one level runs, for every pivot chunk P = [k0, k0 + nb) (nb <= 16),
+// two launches: k_sweep_rowcol (pivot rows and columns) and k_sweep_trailing (the rest).  The
+// inverse of the chunk's pivot block is ready before k_sweep_rowcol: the first chunk's from
+// k_sweep_pivot0, every later chunk's from the k_sweep_trailing launch of the chunk before,
+// whose diagonal tile holding that block finishes it and inverts it at once.  The inverse is
+// written into the front (where the solve reads it) and to pivinv (read by k_sweep_rowcol).
+
+// One warp inverts the pivot block [k1, k1 + nb) of a front in registers (Gauss-Jordan, the
+// block padded with the identity to 16 x 16), src(i, k) giving its entries.
+template <typename Src>
+__device__ __forceinline__ void invert_pivot(Src src, double* F, int nf, int k1, int nb, double* pv, int lane) {
+  constexpr int A = kPivotChunk, NR = A * A / 32;
+  const int c = lane % A, h = lane / A;
+  double v[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    const int i = h * NR + q;
+    v[q] = (i < nb && c < nb) ? src(i, c) : (i == c ? 1.0 : 0.0);
   }
-  if (active) {
-    F[(long long)(k0 + i) * nd.nf + k0 + k] = v;
-    d.pivinv[((long long)r * d.st_lvl + blockIdx.x) * kPivotChunk * kPivotChunk + i * kPivotChunk + k] = v;
+  warp::gj_invert<double, A>(v, lane);
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    const int i = h * NR + q;
+    if (i < nb && c < nb) F[(long long)(k1 + i) * nf + k1 + c] = v[q];
+    pv[i * A + c] = v[q];
   }
 }
 
-// Sweep step 2: pivot rows  M_Pc <- Pinv M_Pc  and pivot columns  M_rP <- -M_rP Pinv
-// (old M_rP saved for step 3), for every index outside P.
-__global__ void k_sweep_rowcol(Grid g, DevState d, const DevNode* nodes, const int* level_nodes, int k0) {
-  __shared__ double P[kPivotChunk][kPivotChunk];
+// Inverse of the first pivot block of every front of a level (one warp per front).
+__global__ void __launch_bounds__(32) k_sweep_pivot0(Grid g, DevState d, const DevNode* nodes, const int* level_nodes) {
+  const int r = blockIdx.y;
+  if (d.rebuild[r] != 1) return;
+  const DevNode nd = nodes[level_nodes[blockIdx.x]];
+  if (nd.nsep <= 0) return;
+  const int nf = nd.nf;
+  double* F = d.front + (long long)r * d.st_front + nd.f_off;
+  double* pv = d.pivinv + ((long long)r * d.st_lvl + blockIdx.x) * kPivotChunk * kPivotChunk;
+  invert_pivot([&](int i, int k) { return F[(long long)i * nf + k]; }, F, nf, 0, min(kPivotChunk, nd.nsep), pv,
+               threadIdx.x);
+}
+
+constexpr int kRcIdx = 32;  // front indices per CTA of k_sweep_rowcol
+
+// Pivot rows and columns of chunk P for every index c outside P:  M_Pc <- Pinv M_Pc  and
+// M_cP <- -M_cP Pinv, the old M_cP saved to colold for k_sweep_trailing.  The symmetric
+// pattern of the partial inverse (see k_sweep_trailing) gives the column from the row:
+// before the step M_cP = s M_Pc^T with s = +1 for c not yet eliminated (c >= k0 + nb) and
+// s = -1 for c < k0, so with Pinv symmetric the new column is -s (Pinv M_Pc)^T and the old
+// one s M_Pc^T: one product of Pinv with the CTA's 16 x 32 slab of pivot rows, staged in
+// shared memory.  The pivot rows are read and written along rows (coalesced), the columns
+// 16 consecutive entries per index.
+__global__ void __launch_bounds__(256) k_sweep_rowcol(Grid g, DevState d, const DevNode* nodes,
+                                                       const int* level_nodes, int k0) {
+  __shared__ double P[kPivotChunk][kPivotChunk + 1];
+  __shared__ double S[kPivotChunk][kRcIdx + 1];  // old pivot rows of the CTA's indices
+  __shared__ double Y[kPivotChunk][kRcIdx + 1];  // new pivot rows
   const int r = blockIdx.z;
   if (d.rebuild[r] != 1) return;
   const DevNode nd = nodes[level_nodes[blockIdx.x]];
   if (k0 >= nd.nsep) return;
   const int nb = min(kPivotChunk, nd.nsep - k0);
   const int nf = nd.nf;
-  const int idx = blockIdx.y * blockDim.x + threadIdx.x;
+  const int i0 = blockIdx.y * kRcIdx;
+  if (i0 >= nf) return;
+  const int tid = threadIdx.x;
   const double* Pg = d.pivinv + ((long long)r * d.st_lvl + blockIdx.x) * kPivotChunk * kPivotChunk;
-  for (int e = threadIdx.x; e < kPivotChunk * kPivotChunk; e += blockDim.x) P[e / kPivotChunk][e % kPivotChunk] = Pg[e];
-  __syncthreads();
-  if (idx >= nf || (idx >= k0 && idx < k0 + nb)) return;
   double* F = d.front + (long long)r * d.st_front + nd.f_off;
-  double* Cold = d.colold + (long long)r * d.st_col + (long long)nd.v_off * kPivotChunk;
-  double col[kPivotChunk], row[kPivotChunk];
-#pragma unroll
-  for (int l = 0; l < kPivotChunk; ++l) {
-    col[l] = l < nb ? F[(long long)(k0 + l) * nf + idx] : 0.0;
-    row[l] = l < nb ? F[(long long)idx * nf + k0 + l] : 0.0;
+  for (int e = tid; e < kPivotChunk * kPivotChunk; e += blockDim.x) P[e / kPivotChunk][e % kPivotChunk] = Pg[e];
+  for (int e = tid; e < kPivotChunk * kRcIdx; e += blockDim.x) {
+    const int l = e / kRcIdx, j = e - l * kRcIdx, idx = i0 + j;
+    S[l][j] = (l < nb && idx < nf) ? F[(long long)(k0 + l) * nf + idx] : 0.0;
   }
+  __syncthreads();
+  auto outside = [&](int idx) { return idx < nf && !(idx >= k0 && idx < k0 + nb); };
+  for (int e = tid; e < kPivotChunk * kRcIdx; e += blockDim.x) {
+    const int l = e / kRcIdx, j = e - l * kRcIdx, idx = i0 + j;
+    if (l >= nb || !outside(idx)) continue;
+    double a = 0.0;
 #pragma unroll
-  for (int l = 0; l < kPivotChunk; ++l) {
-    if (l >= nb) break;
-    double a = 0.0, c = 0.0;
-#pragma unroll
-    for (int q = 0; q < kPivotChunk; ++q) {
-      if (q >= nb) break;
-      a += P[l][q] * col[q];
-      c += row[q] * P[q][l];
-    }
+    for (int q = 0; q < kPivotChunk; ++q) a += P[l][q] * S[q][j];  // S is 0 past nb
+    Y[l][j] = a;
     F[(long long)(k0 + l) * nf + idx] = a;
-    F[(long long)idx * nf + k0 + l] = -c;
-    Cold[(long long)idx * kPivotChunk + l] = row[l];
+  }
+  __syncthreads();
+  double* Cold = d.colold + (long long)r * d.st_col + (long long)nd.v_off * kPivotChunk;
+  for (int e = tid; e < kPivotChunk * kRcIdx; e += blockDim.x) {
+    const int j = e / kPivotChunk, l = e - j * kPivotChunk, idx = i0 + j;
+    if (!outside(idx)) continue;
+    // sign flips on the bit pattern (no float64 instruction): s = -1 below k0
+    const unsigned long long sflip = idx < k0 ? 0x8000000000000000ull : 0ull;
+    if (l < nb)
+      F[(long long)idx * nf + k0 + l] =
+          __longlong_as_double(__double_as_longlong(Y[l][j]) ^ sflip ^ 0x8000000000000000ull);
+    Cold[(long long)idx * kPivotChunk + l] = l < nb ? __longlong_as_double(__double_as_longlong(S[l][j]) ^ sflip) : 0.0;
   }
 }
 
-// Sweep step 3: trailing update  M_rc -= Mold_rP M_Pc(new)  for r, c outside P.
+// Trailing update of chunk P:  M_rc -= Mold_rP M_Pc(new)  for r, c outside P.
 // The frontal matrices are symmetric, and Gauss-Jordan elimination keeps a fixed pattern:
 // with E the pivots eliminated so far and R the rest, M_EE and M_RR stay symmetric and
 // M_ER = -M_RE^T (the partial inverse [A^-1, A^-1 B; -B^T A^-1, C - B^T A^-1 B]).  So only the
 // tiles on and above the diagonal are computed (blockIdx.y enumerates the pairs ty <= tx); an
 // off-diagonal tile also writes its mirror, negated where exactly one of row and column lies in
 // E, i.e. below k0 (through shared memory, so that both writes are coalesced).  This halves the
-// float64 work of the factorisation.
+// float64 work of the factorisation.  The diagonal tile that holds the next chunk's pivot
+// block (final once this update is done) also inverts it (invert_pivot).
 __global__ void k_sweep_trailing(Grid g, DevState d, const DevNode* nodes, const int* level_nodes, int k0,
                                  int tiles_x) {
   __shared__ double A[kTile][kPivotChunk + 1];
@@ -234,7 +257,19 @@ __global__ void k_sweep_trailing(Grid g, DevState d, const DevNode* nodes, const
     F[(long long)row * nf + colx] = v;
     Tn[i][j] = ((row < k0) == (colx < k0)) ? v : -v;
   }
-  if (tx == ty) return;
+  if (tx == ty) {
+    const int k1 = k0 + kPivotChunk;  // the next chunk: its pivot block lies inside tile k1 / kTile
+    if (k1 < nd.nsep && ty == k1 / kTile) {
+      __syncthreads();  // the tile's values complete, its writes to F ordered before the inverse's
+      if (threadIdx.x < 32) {
+        const int o = k1 - r0;
+        double* pv = d.pivinv + ((long long)r * d.st_lvl + blockIdx.x) * kPivotChunk * kPivotChunk;
+        invert_pivot([&](int i, int k) { return Tn[o + i][o + k]; }, F, nf, k1, min(kPivotChunk, nd.nsep - k1), pv,
+                     threadIdx.x);
+      }
+    }
+    return;
+  }
   __syncthreads();
   for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
     const int j = e / kTile, i = e - j * kTile;  // consecutive threads: consecutive columns of row c0 + j
@@ -555,10 +590,10 @@ void launch_nd_factor_level(const Grid& g, const DevState& d, const DevNode* nod
   k_nd_assemble<<<dim3(nlev, ablk, g.R), thr, 0, st>>>(g, d, nodes, level_nodes, srcmap);
   ++g_launches;
   const int tiles_x = (max_nf + kTile - 1) / kTile;
+  k_sweep_pivot0<<<dim3(nlev, g.R), 32, 0, st>>>(g, d, nodes, level_nodes);
+  ++g_launches;
   for (int k0 = 0; k0 < max_nsep; k0 += kPivotChunk) {
-    k_sweep_pivot<<<dim3(nlev, g.R), kPivotChunk * kPivotChunk, 0, st>>>(g, d, nodes, level_nodes, k0);
-    ++g_launches;
-    k_sweep_rowcol<<<dim3(nlev, (max_nf + 127) / 128, g.R), 128, 0, st>>>(g, d, nodes, level_nodes, k0);
+    k_sweep_rowcol<<<dim3(nlev, (max_nf + kRcIdx - 1) / kRcIdx, g.R), 256, 0, st>>>(g, d, nodes, level_nodes, k0);
     ++g_launches;
     k_sweep_trailing<<<dim3(nlev, tiles_x * (tiles_x + 1) / 2, g.R), 256, 0, st>>>(g, d, nodes, level_nodes, k0,
                                                                                   tiles_x);

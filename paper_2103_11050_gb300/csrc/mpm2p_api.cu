@@ -460,6 +460,14 @@ int run_interface(mpm_ctx* c, int pass = 0) {
 // Downscaling factorisation of kappa^n on the side stream (fork): it overlaps whatever the
 // main stream runs until join_downscale_factor.
 int fork_downscale_factor(mpm_ctx* c) {
+  if (c->prof) {  // the stage profiler times the factorisation alone, on the main stream
+    prof_begin(c, MPM_STAGE_DS_FACTOR);
+    per_class(c, [&](const Grid& gk, int n, int ma, int mb) {
+      launch_downscale_factor(gk, c->d, c->d_subs, n, ma, mb, fp32(c), c->stream);
+    });
+    prof_end(c, MPM_STAGE_DS_FACTOR);
+    return check_launch(c);
+  }
   CK(cudaEventRecord(c->ev_fork, c->stream));
   CK(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
   per_class(c, [&](const Grid& gk, int n, int ma, int mb) {
@@ -1385,7 +1393,7 @@ namespace {
 bool valid_tuning(const Tuning& t) {
   auto nt = [](int v) { return v == 64 || v == 128 || v == 256; };
   return nt(t.local_threads) && nt(t.ds_threads) && (t.local_stage == 0 || t.local_stage == 1) &&
-         (t.ds_stage == 0 || t.ds_stage == 1) && (t.transport_rows == 2 || t.transport_rows == 4 || t.transport_rows == 8) &&
+         (t.ds_stage == 0 || t.ds_stage == 1) && (t.transport_rows == 4 || t.transport_rows == 8 || t.transport_rows == 16) &&
          (t.sweep_terms == 4 || t.sweep_terms == 8 || t.sweep_terms == 16);
 }
 
@@ -1452,7 +1460,7 @@ int mpm_autotune(mpm_ctx* c, int reps, double* ms_out) {
   //    write the same values; kappa^n and the transmissibilities of the current s are restored
   //    afterwards
   const double fmax_ = max_fprime(g.M);
-  for (int rows : {2, 4, 8}) {
+  for (int rows : {4, 8, 16}) {
     const double ms = time_launches(c, [&] { launch_upwind_kappa(g, d, 0.5, fmax_, false, 0.0, 0, false, rows, c->stream); },
                                     reps, e0, e1);
     if (ms < best_ms[0]) { best_ms[0] = ms; best.transport_rows = rows; }

@@ -107,7 +107,7 @@ struct Tuning {
                             // global memory inside the chains (smaller CTAs, more of them per SM)
   int ds_threads = 256;     // the same two for the downscaling solve
   int ds_stage = 1;
-  int transport_rows = 2;   // rows of the 32-column tile of the fused transport kernel (2, 4 or 8)
+  int transport_rows = 8;   // rows of the 32-column tile of the fused transport kernel (4, 8 or 16)
   int sweep_terms = 16;     // interface sweeps: terms of a row's sum per thread (4, 8 or 16; fewer terms,
                             // more threads per row and more CTAs per level)
 };

@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 
 SHAPES = [dict(local_threads=64, local_stage=0, ds_threads=64, ds_stage=0, transport_rows=8, sweep_terms=4),
           dict(local_threads=128, local_stage=1, ds_threads=128, ds_stage=1, transport_rows=4, sweep_terms=8),
-          dict(local_threads=256, local_stage=0, ds_threads=256, ds_stage=0, transport_rows=2, sweep_terms=16),
+          dict(local_threads=256, local_stage=0, ds_threads=256, ds_stage=0, transport_rows=16, sweep_terms=16),
           dict(local_threads=64, local_stage=1, ds_threads=128, ds_stage=0, transport_rows=4, sweep_terms=4)]
 
 
@@ -83,7 +83,7 @@ def test_autotune_keeps_the_state(prec):
             ctx.step(eta, 0.5, 1)
     ux0, uy0 = a.get_flux()
     tune, ms = a.autotune(3)
-    assert tune["local_threads"] in (64, 128, 256) and tune["transport_rows"] in (2, 4, 8)
+    assert tune["local_threads"] in (64, 128, 256) and tune["transport_rows"] in (4, 8, 16)
     assert all(m > 0 for m in ms) and tune["sweep_terms"] in (4, 8, 16)
     ux1, uy1 = a.get_flux()
     assert rel(ux1, ux0) <= 1e-12 and rel(uy1, uy0) <= 1e-12 + 1e-14
