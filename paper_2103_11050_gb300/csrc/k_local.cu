@@ -628,8 +628,15 @@ __global__ void k_robin_factor_w(Grid g, DevState d, const DevSub* subs, int sca
 // interface from its own subdomain) and, on Dirichlet faces, 2 (kappa^n - kappa^m)_c dp0_c.
 // Outputs the perturbation traces (fbar), mean(dp) and the interface right-hand side of the
 // subdomain.
+// Resident CTAs per SM that the register allocation of the MPM-2P local solve must allow: 768
+// threads per SM for factor widths up to 16 (at most 80 registers a thread, no spills; the
+// chains of more subdomains in flight hide the latency of the factor loads and shuffles), no
+// bound for width 32 (its register-held blocks would spill).
+template <int A, int NT>
+constexpr int kLocalMinBlocks = A <= 16 ? 768 / NT : 1;
+
 template <typename T, int A, int NT>
-__global__ void __launch_bounds__(NT) k_mpm_local_w(Grid g, DevState d, const DevSub* subs, size_t qoff,
+__global__ void __launch_bounds__(NT, kLocalMinBlocks<A, NT>) k_mpm_local_w(Grid g, DevState d, const DevSub* subs, size_t qoff,
                                                     int refine, double tol, int ir_max, const DevNode* nodes,
                                                     const int* leaf_node, int pass, int store_x) {
   extern __shared__ __align__(16) char smem[];
@@ -934,6 +941,9 @@ __global__ void __launch_bounds__(NT) k_downscale_w(Grid g, DevState d, const De
 template <typename K>
 void set_smem(K kernel, size_t bytes) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  // all of the unified L1 / shared storage that shared memory may take: the occupancy of these
+  // kernels is bounded by their shared tables, and their global loads are read-once streams
+  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
 }
 
 size_t align16(size_t v) { return (v + 15) / 16 * 16; }

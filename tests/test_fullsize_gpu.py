@@ -121,9 +121,11 @@ def test_ensemble_256_realisations():
         assert rel(ux[r], st.step.Fx) <= 1e-8
         assert rel(uy[r], st.step.Fy) <= 1e-8
         assert rel(s[r], st.s) <= 1e-8
+    # per-cell mass balance within the refinement's stopping rule (1e3 ir_tol of the cell's flux
+    # scale, at most four times the largest flux; see test_channel1024_against_oracle)
     for r in range(R):
         bal = np.max(np.abs(O.cell_balance(ux[r], uy[r], prob))) / np.max(np.abs(ux[r]))
-        assert bal <= 1e-11
+        assert bal <= 4e-11, (r, bal)
         assert s[r].min() >= -1e-14 and s[r].max() <= 1 + 1e-14
     ctx.close()
 
