@@ -353,9 +353,12 @@ __device__ double basis_trace(const Grid& g, const DevState& d, const DevSub& sd
   return homogeneous_phys ? 0.0 : g.bc_val[side] * g.h;
 }
 
-// All BF solves of a subdomain at once (rebuild): the ndof homogeneous BFs and the
-// non-homogeneous one, in column chunks.  Outputs: traces (tr, fbar), pressures (pf incl.
-// the non-homogeneous column), means (mu_hat, sub_mean).
+// All BF solves of a subdomain (rebuild): the ndof homogeneous BFs and the non-homogeneous
+// one, in column chunks of ncol_max; chunk k goes to the CTA with blockIdx.z = k mod gridDim.z
+// (on grids with few subdomains several CTAs share a subdomain's columns, each with its own
+// copy of the factor).  Outputs: traces (tr, fbar), pressures (pf incl. the
+// non-homogeneous column), means (mu_hat, sub_mean); the CTA of the non-homogeneous column
+// also writes the subdomain's interface right-hand side.
 template <typename T>
 __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int ncol_max, int refine,
                               double tol, int ir_max, const DevNode* nodes, const int* leaf_node, int q_global) {
@@ -370,13 +373,14 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
   const int a = sd.a, b = sd.b, m = a * b;
   const int nface = 2 * (a + b);
   const int ntot = sd.ndof + 1;
+  if ((int)blockIdx.z * ncol_max >= ntot) return;  // no chunk for this CTA
   Carve<T> cv = carve<T>(smem, a, b, A, ncol_max, q_global != 0);
   load_robin<T>(d, sd, r, cv, g, A, q_global != 0);
   double* tr = d.tr + (long long)r * d.st_tr + sd.tr_off;       // [ndof][nface]
   double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;       // [ndof+1][m]
   double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
   double* muh = d.mu_hat + (long long)r * d.st_dof + sd.dof_off;
-  for (int c0 = 0; c0 < ntot; c0 += ncol_max) {
+  for (int c0 = blockIdx.z * ncol_max; c0 < ntot; c0 += gridDim.z * ncol_max) {
     const int ncol = min(ncol_max, ntot - c0);
     for (int e = threadIdx.x; e < m * ncol; e += blockDim.x) {
       const int c = e / ncol, col = e - c * ncol;
@@ -411,8 +415,9 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
     __syncthreads();
   }
   // Interface right-hand side (Eq. mrc2) from the non-homogeneous traces just written.
-  for (int k = threadIdx.x; k < sd.ndof; k += blockDim.x)
-    phase::element_rhs(g, d, sd, nodes[leaf_node[sidx]], r, k, fbar);
+  if ((ntot - 1) / ncol_max % (int)gridDim.z == (int)blockIdx.z)
+    for (int k = threadIdx.x; k < sd.ndof; k += blockDim.x)
+      phase::element_rhs(g, d, sd, nodes[leaf_node[sidx]], r, k, fbar);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -532,7 +537,7 @@ __global__ void __launch_bounds__(256) k_basis_solve_tc(Grid g, DevState d, cons
   double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;
   double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
   double* muh = d.mu_hat + (long long)r * d.st_dof + sd.dof_off;
-  for (int c0 = 0; c0 < ntot; c0 += ncol_max) {
+  for (int c0 = blockIdx.z * ncol_max; c0 < ntot; c0 += gridDim.z * ncol_max) {
     const int ncol = min(ncol_max, ntot - c0);
     for (int e = threadIdx.x; e < m * ncol; e += blockDim.x) {
       const int c = e / ncol, col = e - c * ncol;
@@ -1076,7 +1081,10 @@ void launch_basis_solve(const Grid& g, const DevState& d, const DevSub* subs, in
     return;
   }
   // the stored factor is staged in shared memory unless that leaves room for fewer than 8
-  // right-hand-side columns per pass (large padded blocks): then it is read in place
+  // right-hand-side columns per pass (large padded blocks): then it is read in place.  With
+  // fewer than 4 CTAs per SM, the column chunks of a subdomain are spread over up to 4 CTAs.
+  const int per = nsub * g.R;
+  grid.z = per >= 4 * sm_count() ? 1 : std::min(4, (4 * sm_count() + per - 1) / per);
   if (fp32) {
     SmemPlan pl = plan_smem<float>(max_a, max_b, A, 32);
     const bool qg = pl.ncol < 8;

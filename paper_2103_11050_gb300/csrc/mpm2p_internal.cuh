@@ -196,6 +196,19 @@ void launch_ex(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cud
 }
 
 // Host-side launch wrappers (defined in the .cu files).
+// SMs of the current device (queried once per device).
+inline int sm_count() {
+  static int n[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (n[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    n[dev] = v > 0 ? v : 1;
+  }
+  return n[dev];
+}
+
 int grid_cell_blocks(const Grid& g);
 void launch_mobility_eps(const Grid& g, const DevState& d, bool with_eps, cudaStream_t st);
 void launch_choose(const Grid& g, const DevState& d, double eta, cudaStream_t st);
