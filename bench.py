@@ -316,7 +316,8 @@ def run_gpu(args, wl):
         prof = ctx.profile_read() if profile else None
         ux, uy = ctx.get_flux()
         res = dict(per=per, flags=flags, launches=st1["kernel_launches"] - st0["kernel_launches"],
-                   rebuild_steps=sum(flags), ir=st1["ir_iters_max"], prof=prof, ux=ux, uy=uy)
+                   rebuild_steps=sum(flags), ir=st1["ir_iters_max"], prof=prof, ux=ux, uy=uy,
+                   ds_fact=st1["ds_factorisations"] - st0["ds_factorisations"])
         if not profile:
             rest = max(0, wl.steps - args.warmup - args.steps) if not args.no_trajectory else 0
             if rest:
@@ -372,6 +373,10 @@ def run_gpu(args, wl):
         main = trajectory(prec)
         reb_per, _ = forced(prec, -1.0, FORCED_REBUILDS)
         t_blend, step_split = blend(prec, main, reb_per)
+        # downscaling factorisations computed in the window, as a fraction of subdomains x steps
+        # (the rest kept their stored float32 factor, mpm_set_downscale_reuse)
+        step_split["downscale_factorised_fraction"] = main["ds_fact"] / (
+            len(wl.col_w) * len(wl.row_h) * wl.R * args.steps)
     value = cells / (t_blend / 1e3)
     window_ms = sum(main["per"])
     _, prof_main = forced(prec, 1e300, args.steps, profile=True)

@@ -106,6 +106,8 @@ typedef struct mpm_stats {
   int subdomains;             /* subdomains per realisation */
   int n_hat;                  /* homogeneous BFs per realisation (Section 4.3) */
   long long kernel_launches;  /* CUDA kernels launched by this context so far */
+  long long ds_factorisations; /* downscaling factorisations computed (subdomains, all
+                                  realisations summed); see mpm_set_downscale_reuse */
 } mpm_stats;
 
 /* Stages timed by the profiler (each is the set of kernels of one step of the path). */
@@ -150,6 +152,17 @@ const char* mpm_last_error(const mpm_ctx* ctx);
  * ir_max sweeps makes the next mpm_sync / getter return MPM_ERR_NOT_CONVERGED.  Takes
  * effect at the next basis build. */
 int mpm_set_precision(mpm_ctx* ctx, int mode, double ir_tol, int ir_max);
+
+/* Reuse of float32 downscaling factors (Eq. mpm_upd, left-hand side; the refined precision
+ * modes only).  The pinned Neumann operator of kappa^n changes every step, but little in most
+ * subdomains (the premise of MPM-2P, Section 4).  A subdomain whose stored float32 factor was
+ * computed from transmissibilities within a relative tol of the current ones on every face
+ * (and with the pinned cell's kappa within tol) keeps it: its float64 refinement runs against
+ * the current operator, so the solution is that of the current operator to the same ir_tol,
+ * and the refinement's contraction per sweep grows by at most about tol.  0 <= tol <= 0.5;
+ * 0 refactors every subdomain every step; default 0.02.  mpm_stats.ds_factorisations counts
+ * the factorisations computed.  MPM_ERR_ARG outside the range.  Drops a captured graph. */
+int mpm_set_downscale_reuse(mpm_ctx* ctx, double tol);
 
 /* Absolute permeability K [R][ny][nx], every entry > 0 and finite (checked for host
  * input; device input is trusted). */

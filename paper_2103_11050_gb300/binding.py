@@ -29,7 +29,7 @@ FUNCTIONS = [
     "mpm_perturbation_solve", "mpm_interface_solve", "mpm_downscale", "mpm_saturation_step",
     "mpm_init", "mpm_step", "mpm_get_pressure", "mpm_get_flux", "mpm_get_saturation",
     "mpm_get_conductivity", "mpm_get_stats", "mpm_sync", "mpm_profile_enable", "mpm_profile_read",
-    "mpm_set_execution", "mpm_cfl_dt_noalloc", "mpm_get_eps_history", "mpm_get_tuning", "mpm_set_tuning",
+    "mpm_set_execution", "mpm_set_downscale_reuse", "mpm_cfl_dt_noalloc", "mpm_get_eps_history", "mpm_get_tuning", "mpm_set_tuning",
     "mpm_autotune", "mpm_set_mpm_order", "mpm_perturbation_correction",
 ]
 TUNE_KEYS = ["local_threads", "local_stage", "ds_threads", "ds_stage", "transport_rows", "sweep_terms"]
@@ -49,7 +49,7 @@ class Stats(ctypes.Structure):
                 ("mpm_updates", ctypes.c_longlong), ("last_eps_max", ctypes.c_double),
                 ("last_dt_min", ctypes.c_double), ("ir_iters_max", ctypes.c_int),
                 ("interface_dofs", ctypes.c_int), ("subdomains", ctypes.c_int), ("n_hat", ctypes.c_int),
-                ("kernel_launches", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong), ("ds_factorisations", ctypes.c_longlong)]
 
 
 _LIB = None
@@ -98,6 +98,7 @@ def load(path: str | None = None):
         "mpm_sync": ([P], I),
         "mpm_profile_enable": ([P, I], I),
         "mpm_set_execution": ([P, I], I),
+        "mpm_set_downscale_reuse": ([P, D], I),
         "mpm_cfl_dt_noalloc": ([P, P, I, I, I, D, D, D, P, P], I),
         "mpm_profile_read": ([P, DP, ctypes.POINTER(ctypes.c_longlong)], I),
         "mpm_get_eps_history": ([P, DP, IP, I, IP], I),
@@ -322,6 +323,11 @@ class Context:
     def set_execution(self, graph=True, pdl=True):
         flags = (EXEC_GRAPH if graph else 0) | (EXEC_PDL if pdl else 0)
         self._ck(self.L.mpm_set_execution(self.h, flags))
+
+    def set_downscale_reuse(self, tol):
+        """Keep float32 downscaling factors while the transmissibilities stay within a relative
+        tol of those they were computed from (0: refactor every step)."""
+        self._ck(self.L.mpm_set_downscale_reuse(self.h, float(tol)))
 
     def profile_enable(self, on=True):
         self._ck(self.L.mpm_profile_enable(self.h, 1 if on else 0))

@@ -757,8 +757,15 @@ __global__ void __launch_bounds__(NT, kLocalMinBlocks<A, NT>) k_mpm_local_w(Grid
 // kappa^n of every subdomain, factored (twisted block factorisation) into nfac, with its
 // FP64 stencil [ex, wE, wN, sc] into ntvec.  It depends only on kappa^n, so the step runs it
 // on a side stream concurrently with the perturbation and interface solves.
+// reuse_tol > 0 (float32 factors, which the downscaling solve refines in float64 against the
+// current operator anyway): a subdomain whose stored factor was computed from transmissibilities
+// within a relative reuse_tol of the current ones on every face (and the pinned cell's kappa
+// likewise) keeps that factor, its scaling and its pinned cell; only the float64 stencil of
+// the current kappa^n is written.  The generalised eigenvalues of the current operator
+// against the stored one then lie within 1 -+ reuse_tol, so the refinement's contraction per
+// sweep grows by at most about reuse_tol.
 template <typename T, int A>
-__global__ void k_downscale_factor_w(Grid g, DevState d, const DevSub* subs, int scale) {
+__global__ void k_downscale_factor_w(Grid g, DevState d, const DevSub* subs, int scale, double reuse_tol) {
   extern __shared__ __align__(16) char smem[];
   const int sidx = sub_index(g);
   const int r = blockIdx.y;
@@ -769,6 +776,34 @@ __global__ void k_downscale_factor_w(Grid g, DevState d, const DevSub* subs, int
   const int m = sd.a * sd.b;
   warp::Tables<T> t = warp::carve<T, A>(smem, m, sd.b);
   load_kappa_cta(g, sd, d.kap_n + (long long)r * g.ncell(), t.kap);
+  const double* txr = d.tx + (long long)r * g.nfx();
+  const double* tyr = d.ty + (long long)r * g.nfy();
+  double* tv = d.ntvec + (long long)r * d.st_t + sd.t_off;
+  double* fw = d.nfw + (long long)r * d.st_t + sd.t_off;
+  const long long si = (long long)r * d.st_sub + sidx;
+  const int pin_old = reuse_tol > 0.0 ? d.npin[si] : -1;
+  if (pin_old >= 0) {
+    // |T - T_factor| > reuse_tol T_factor on some face?  (non-negative values compared as bit
+    // patterns: integer compares)
+    bool far = false;
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+      const int jl = c / sd.a, il = c - jl * sd.a;
+      const int i = sd.x0 + il, j = sd.y0 + jl;
+      const double we = il < sd.a - 1 ? txr[(long long)j * (g.nx + 1) + i + 1] : 0.0;
+      const double wn = jl < sd.b - 1 ? tyr[(long long)(j + 1) * g.nx + i] : 0.0;
+      const double fe = fw[c], fn = fw[m + c];
+      far |= nn_bits(fabs(we - fe)) > nn_bits(reuse_tol * fe);
+      far |= nn_bits(fabs(wn - fn)) > nn_bits(reuse_tol * fn);
+      tv[c] = c == pin_old ? t.kap[c] : 0.0;  // ex of the pinned operator, pinned where the factor was
+      tv[m + c] = we;
+      tv[2 * m + c] = wn;
+    }
+    if (threadIdx.x == 0) {
+      const double kp = d.npin_k[si];
+      far |= nn_bits(fabs(t.kap[pin_old] - kp)) > nn_bits(reuse_tol * kp);
+    }
+    if (!__syncthreads_or(far)) return;  // reused: ntvec holds the current stencil, the stored scaling
+  }
   // the pinned cell: the one of largest kappa^n (first on ties).  The pin fixes the pressure
   // constant only (the mean is shifted afterwards), so its place changes no result, but a pin in
   // a low-conductivity cell of a high-contrast field leaves a badly conditioned system that the
@@ -784,12 +819,18 @@ __global__ void k_downscale_factor_w(Grid g, DevState d, const DevSub* subs, int
   warp::build<T, A>(g, sd, t, d.tx + (long long)r * g.nfx(), d.ty + (long long)r * g.nfy(), d.rho_f + sd.face_off,
                     1 + pin_s, scale != 0);
   warp::factor<T, A>(sd, t, reinterpret_cast<T*>(d.nfac) + (long long)r * d.st_fac + sd.q_off);
-  double* tv = d.ntvec + (long long)r * d.st_t + sd.t_off;
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
     tv[c] = t.ex[c];
     tv[m + c] = t.wE[c];
     tv[2 * m + c] = t.wN[c];
     tv[3 * m + c] = t.sc[c];
+    fw[c] = t.wE[c];
+    fw[m + c] = t.wN[c];
+  }
+  if (threadIdx.x == 0) {
+    d.npin[si] = pin_s;
+    d.npin_k[si] = t.kap[pin_s];
+    atomicAdd(reinterpret_cast<unsigned long long*>(&d.counts[4]), 1ull);
   }
 }
 
@@ -839,9 +880,12 @@ __global__ void __launch_bounds__(NT) k_downscale_w(Grid g, DevState d, const De
     }
   }
   __syncthreads();
+  // the factor's own couplings: the north transmissibilities it was computed from (equal to the
+  // current ones unless the factor was kept, see k_downscale_factor_w)
+  const double* fwN = d.nfw + (long long)r * d.st_t + sd.t_off + m;
   for (int e = threadIdx.x; e < b * A; e += blockDim.x) {
     const int j = e / A, i = e - j * A;
-    t.th[e] = (i < a && j < b - 1) ? warp::scaled_coupling<T>(t.wN[j * a + i], t.sc[j * a + i], t.sc[j * a + i + a])
+    t.th[e] = (i < a && j < b - 1) ? warp::scaled_coupling<T>(fwN[j * a + i], t.sc[j * a + i], t.sc[j * a + i + a])
                                    : T(0);
   }
   const double* qc = d.q + (long long)r * g.ncell();
@@ -1002,11 +1046,12 @@ void mpm_local_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub,
 
 template <typename T, int A>
 void downscale_factor_t(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
-                        cudaStream_t st) {
+                        double reuse_tol, cudaStream_t st) {
   size_t bytes, qoff;
   pair_geometry<T, A>(max_a, max_b, false, bytes, qoff);
   set_smem(k_downscale_factor_w<T, A>, bytes);
-  k_downscale_factor_w<T, A><<<dim3(nsub, g.R), 64, bytes, st>>>(g, d, subs, std::is_same<T, float>::value ? 1 : 0);
+  k_downscale_factor_w<T, A><<<dim3(nsub, g.R), 64, bytes, st>>>(g, d, subs, std::is_same<T, float>::value ? 1 : 0,
+                                                                   reuse_tol);
   ++g_launches;
 }
 
@@ -1115,9 +1160,9 @@ void launch_mpm_local(const Grid& g, const DevState& d, const DevSub* subs, int 
 }
 
 void launch_downscale_factor(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,
-                             bool fp32, cudaStream_t st) {
-  if (fp32) MPM_DISPATCH_A(downscale_factor_t, float, g, d, subs, nsub, max_a, max_b, st);
-  else MPM_DISPATCH_A(downscale_factor_t, double, g, d, subs, nsub, max_a, max_b, st);
+                             bool fp32, double reuse_tol, cudaStream_t st) {
+  if (fp32) MPM_DISPATCH_A(downscale_factor_t, float, g, d, subs, nsub, max_a, max_b, reuse_tol, st);
+  else MPM_DISPATCH_A(downscale_factor_t, double, g, d, subs, nsub, max_a, max_b, 0.0, st);
 }
 
 void launch_downscale(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a, int max_b,

@@ -35,6 +35,7 @@ struct mpm_ctx {
   std::string err;
   int prec = MPM_PREC_FP64;
   double ir_tol = 1e-14;
+  double ds_reuse = 0.02;  // relative transmissibility change up to which a float32 downscaling factor is kept
   int ir_max = 20;
   int fac_prec = -1;  // precision the stored factor was built with
   bool have_K = false, have_s = false, have_dec = false, have_basis = false;
@@ -233,6 +234,9 @@ double max_fprime(double M) {
 // mixed modes; the Robin factors (reused by every BF solve and MPM-2P step) only in
 // MPM_PREC_FP32_IR_ALL.
 bool fp32(const mpm_ctx* c) { return c->prec != MPM_PREC_FP64; }
+// Relative change of the transmissibilities up to which a stored float32 downscaling factor is
+// kept (0: refactor every step; float64 factors are never kept: nothing refines them).
+double ds_reuse_tol(const mpm_ctx* c) { return fp32(c) ? c->ds_reuse : 0.0; }
 bool robin_fp32_mode(int prec) { return prec == MPM_PREC_FP32_IR_ALL || prec >= MPM_PREC_TF32_IR; }
 bool fp32_robin(const mpm_ctx* c) { return robin_fp32_mode(c->prec); }
 // Tensor-core kind of the basis-function solves (0: CUDA cores), k_local_tc.cuh.
@@ -463,7 +467,7 @@ int fork_downscale_factor(mpm_ctx* c) {
   if (c->prof) {  // the stage profiler times the factorisation alone, on the main stream
     prof_begin(c, MPM_STAGE_DS_FACTOR);
     per_class(c, [&](const Grid& gk, int n, int ma, int mb) {
-      launch_downscale_factor(gk, c->d, c->d_subs, n, ma, mb, fp32(c), c->stream);
+      launch_downscale_factor(gk, c->d, c->d_subs, n, ma, mb, fp32(c), ds_reuse_tol(c), c->stream);
     });
     prof_end(c, MPM_STAGE_DS_FACTOR);
     return check_launch(c);
@@ -471,7 +475,7 @@ int fork_downscale_factor(mpm_ctx* c) {
   CK(cudaEventRecord(c->ev_fork, c->stream));
   CK(cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
   per_class(c, [&](const Grid& gk, int n, int ma, int mb) {
-    launch_downscale_factor(gk, c->d, c->d_subs, n, ma, mb, fp32(c), c->side_stream);
+    launch_downscale_factor(gk, c->d, c->d_subs, n, ma, mb, fp32(c), ds_reuse_tol(c), c->side_stream);
   });
   CK(cudaEventRecord(c->ev_join, c->side_stream));
   c->factor_forked = true;
@@ -505,7 +509,7 @@ int run_downscale(mpm_ctx* c, bool after_interface, bool forked) {
   prof_begin(c, MPM_STAGE_DOWNSCALE);
   if (!forked) {
     per_class(c, [&](const Grid& gk, int n, int ma, int mb) {
-      launch_downscale_factor(gk, c->d, c->d_subs, n, ma, mb, fp32(c), c->stream);
+      launch_downscale_factor(gk, c->d, c->d_subs, n, ma, mb, fp32(c), ds_reuse_tol(c), c->stream);
     });
   }
   per_class(c, [&](const Grid& gk, int n, int ma, int mb) {
@@ -723,7 +727,7 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.rebuild, (size_t)R);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.status, 2);  // status word, then the sweep count
   if (rc == MPM_OK) d.ir_iters = d.status + 1;
-  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.counts, 4);
+  if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.counts, 5);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.eps_hist, (size_t)R * kEpsHist);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.reb_hist, (size_t)R * kEpsHist);
   if (rc == MPM_OK) rc = dalloc_t(c, c->grid_allocs, &d.hist_n, 1);
@@ -786,6 +790,8 @@ int mpm_set_precision(mpm_ctx* c, int mode, double ir_tol, int ir_max) {
   c->ir_tol = ir_tol;
   c->ir_max = ir_max;
   c->have_basis = false;  // the stored factors have the old type
+  if (c->have_dec && c->d.npin)  // so do the stored downscaling factors
+    CK(cudaMemsetAsync(c->d.npin, 0xff, (size_t)c->g.R * c->subs.size() * sizeof(int), c->stream));
   drop_graph(c);
   return MPM_OK;
 }
@@ -1088,6 +1094,9 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   if (!rc) rc = dalloc_t(c, A, &d.tvec, (size_t)R * t_off);
   if (!rc) rc = dalloc(c, A, &d.nfac, (size_t)R * q_off * sizeof(double));
   if (!rc) rc = dalloc_t(c, A, &d.ntvec, (size_t)R * t_off);
+  if (!rc) rc = dalloc_t(c, A, &d.nfw, (size_t)R * t_off);
+  if (!rc) rc = dalloc_t(c, A, &d.npin, (size_t)R * nsub);
+  if (!rc) rc = dalloc_t(c, A, &d.npin_k, (size_t)R * nsub);
   if (!rc) rc = dalloc_t(c, A, &d.tr, (size_t)R * tr_off);
   if (!rc) rc = dalloc_t(c, A, &d.pf, (size_t)R * pf_off);
   if (!rc) rc = dalloc_t(c, A, &d.mu_hat, (size_t)R * dof_off);
@@ -1118,6 +1127,7 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
     release_decomposition(c);
     return rc;
   }
+  CK(cudaMemsetAsync(d.npin, 0xff, (size_t)R * nsub * sizeof(int), c->stream));  // no stored factor: -1
   CK(cudaMemcpyAsync(c->d_subs, c->subs.data(), nsub * sizeof(DevSub), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(d.rho_f, rho_host.data(), rho_host.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   if (c->classes.size() > 1)
@@ -1262,6 +1272,8 @@ int mpm_init(mpm_ctx* c, double eta) {
   if (rc) return rc;
   launch_mobility_eps(c->g, c->d, false, c->stream);
   launch_fill_flags(c->g, c->d, 1, c->stream);
+  // a fresh start: no stored downscaling factor is kept (their type may have changed)
+  CK(cudaMemsetAsync(c->d.npin, 0xff, (size_t)c->g.R * c->subs.size() * sizeof(int), c->stream));
   if ((rc = fork_downscale_factor(c))) return rc;
   if ((rc = run_build(c))) return rc;
   if ((rc = run_interface(c))) return rc;
@@ -1311,6 +1323,14 @@ int mpm_step(mpm_ctx* c, double eta, double cfl, int n_sub) {
   return check_launch(c);
 }
 
+int mpm_set_downscale_reuse(mpm_ctx* c, double tol) {
+  if (!c) return MPM_ERR_ARG;
+  if (!(tol >= 0.0 && tol <= 0.5)) return fail(c, MPM_ERR_ARG, "need 0 <= tol <= 0.5");
+  c->ds_reuse = tol;
+  drop_graph(c);
+  return MPM_OK;
+}
+
 int mpm_set_execution(mpm_ctx* c, int flags) {
   if (!c) return MPM_ERR_ARG;
   if (flags & ~(MPM_EXEC_GRAPH | MPM_EXEC_PDL)) return fail(c, MPM_ERR_ARG, "unknown execution flags %d", flags);
@@ -1353,8 +1373,9 @@ int mpm_get_stats(mpm_ctx* c, mpm_stats* out) {
   CK(cudaMemcpy(dt.data(), c->d.dt, sizeof(double) * c->g.R, cudaMemcpyDeviceToHost));
   c->stats.last_eps_max = *std::max_element(e.begin(), e.end());
   c->stats.last_dt_min = *std::min_element(dt.begin(), dt.end());
-  long long cnt[4] = {0, 0, 0, 0};
+  long long cnt[5] = {0, 0, 0, 0, 0};
   CK(cudaMemcpy(cnt, c->d.counts, sizeof(cnt), cudaMemcpyDeviceToHost));
+  c->stats.ds_factorisations = cnt[4];
   c->stats.rebuilds = c->init_rebuilds + cnt[0];
   c->stats.mpm_updates = cnt[1];
   c->stats.kernel_launches = g_launches - c->launches0 - c->capture_launches + c->graph_steps * c->gk_base +
@@ -1489,7 +1510,7 @@ int mpm_autotune(mpm_ctx* c, int reps, double* ms_out) {
   // 3. the downscaling solve with the factor of the current kappa^n (its inputs, the traces and
   //    targets of the last interface solve, are left unchanged; its outputs are recomputed)
   per_class(c, [&](const Grid& gk, int n, int ma, int mb) {
-    launch_downscale_factor(gk, d, c->d_subs, n, ma, mb, fp32(c), c->stream);
+    launch_downscale_factor(gk, d, c->d_subs, n, ma, mb, fp32(c), ds_reuse_tol(c), c->stream);
   });
   for (int nt : {64, 128, 256})
     for (int stage : {0, 1}) {

@@ -145,8 +145,9 @@ struct DevState {
   int* rebuild;        // [R] branch of the current update: 1 = basis build, 0 = MPM-2P reuse
   int* status;         // [1] bitmask: 1 = a refinement did not reach its tolerance
   int* ir_iters;       // [1] max refinement sweeps used
-  long long* counts;   // [4] rebuild / MPM-2P updates taken by the device-side decision; graph steps
-                       //     that ran the rebuild body / the MPM-2P body
+  long long* counts;   // [5] rebuild / MPM-2P updates taken by the device-side decision; graph steps
+                       //     that ran the rebuild body / the MPM-2P body; downscaling factorisations
+                       //     computed (subdomains, all realisations)
   double* eps_hist;    // [R][kEpsHist] epsilon after each decision (ring, slot = step % kEpsHist)
   int* reb_hist;       // [R][kEpsHist] the decision of that step (1 = rebuild)
   long long* hist_n;   // [1] decisions recorded so far
@@ -154,7 +155,12 @@ struct DevState {
   void* fac;           // Robin factors (float or double), st_fac values per realisation
   double* tvec;        // [ex, wE, wN, sc] per subdomain (4 m), st_t
   void* nfac;          // downscaling (pinned Neumann) factors of kappa^n, same layout as fac
-  double* ntvec;       // their [ex, wE, wN, sc], same layout as tvec
+  double* ntvec;       // their [ex, wE, wN, sc] of the current kappa^n (sc: of the stored factor), same
+                       // layout as tvec
+  double* nfw;         // [wE, wN] of kappa^n when the stored downscaling factor was computed (first 2 m of
+                       // each subdomain's tvec-layout block)
+  int* npin;           // [R][st_sub] pinned cell of the stored downscaling factor, -1: none stored
+  double* npin_k;      // [R][st_sub] kappa^n of that cell when the factor was computed
   double* tr;          // BF traces, one column of 2(a+b) faces per BF (ndof x 2(a+b)), st_tr
   double* pf;          // BF pressures, one column of m cells per BF ((ndof + 1) x m), st_pf
   double* mu_hat;      // BF means, st_dof
@@ -236,7 +242,7 @@ void launch_reconstruct(const Grid& g, const DevState& d, const DevSub* subs, in
                         int max_dof, int max_nf1, const DevNode* nodes, const int* leaf_node, const int* pmap,
                         int branch, int pass, bool pdl, cudaStream_t st);
 void launch_downscale_factor(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
-                             int max_b, bool fp32, cudaStream_t st);
+                             int max_b, bool fp32, double reuse_tol, cudaStream_t st);
 void launch_downscale(const Grid& g, const DevState& d, const DevSub* subs, int nsub, int max_a,
                       int max_b, bool fp32, double ir_tol, int ir_max, bool pdl, int threads, int stage,
                       cudaStream_t st);

@@ -248,6 +248,49 @@ def test_algorithm1_parity(name, eta, steps, prec, graph, pdl):
     assert rel(ctx.get_pressure(1)[0], st.step.p_down) <= tol, rel(ctx.get_pressure(1)[0], st.step.p_down)
 
 
+@pytest.mark.parametrize("name,eta,steps", [("contrast64", 0.05, 20), ("uneven", 0.02, 12)])
+def test_downscale_factor_reuse(name, eta, steps):
+    """Kept float32 downscaling factors (mpm_set_downscale_reuse): the float64 refinement runs
+    against the current operator, so the trajectory matches the oracle at the mixed form's
+    tolerance and the every-step refactorisation to the refinement's accuracy, with fewer
+    factorisations (the front has not reached most subdomains, whose kappa^n does not change)."""
+    c = case(name, "zero")
+    prob, dec = _oracle_setup(c)
+    st = O.simulate_init(c["K"], c["s0"], prob, dec, eta)
+    for _ in range(steps):
+        O.simulate_step(st, c["K"], prob, dec, eta, 0.5, 1)
+    nsub = len(c["col_w"]) * len(c["row_h"])
+    runs = {}
+    for tol in (0.0, 0.05):
+        ctx = _gpu(c, 1)
+        ctx.set_downscale_reuse(tol)
+        ctx.init(eta)
+        for _ in range(steps):
+            ctx.step(eta, 0.5, 1)
+        ux, uy = ctx.get_flux()
+        runs[tol] = (ux[0], uy[0], ctx.get_saturation()[0], ctx.get_stats())
+        ctx.close()
+    assert runs[0.0][3]["ds_factorisations"] == nsub * (steps + 1)
+    assert runs[0.05][3]["ds_factorisations"] < nsub * (steps + 1)
+    for ux, uy, s, _ in runs.values():
+        assert rel(ux, st.step.Fx) <= TOL[1], rel(ux, st.step.Fx)
+        assert rel(uy, st.step.Fy) <= TOL[1] + 1e-12, rel(uy, st.step.Fy)
+        assert rel(s, st.s) <= TOL[1], rel(s, st.s)
+        # per-cell balance within the refinement's stopping rule (1e3 ir_tol of the flux scale)
+        assert _balance(ux, uy, prob) <= 4e-11
+    assert rel(runs[0.05][0], runs[0.0][0]) <= 1e-10
+    assert rel(runs[0.05][1], runs[0.0][1]) <= 1e-10
+
+
+def test_downscale_reuse_rejects_out_of_range():
+    c = case("single")
+    ctx = _gpu(c, 1)
+    for bad in (-0.1, 0.6, float("nan")):
+        with pytest.raises(RuntimeError):
+            ctx.set_downscale_reuse(bad)
+    ctx.close()
+
+
 @pytest.mark.parametrize("graph", [True, False])
 def test_algorithm1_twenty_transport_substeps(graph):
     # C_n = 20 transport steps between pressure updates (Section 5.1): the pressure step is
