@@ -159,9 +159,11 @@ int mpm_set_precision(mpm_ctx* ctx, int mode, double ir_tol, int ir_max);
  * computed from transmissibilities within a relative tol of the current ones on every face
  * (and with the pinned cell's kappa within tol) keeps it: its float64 refinement runs against
  * the current operator, so the solution is that of the current operator to the same ir_tol,
- * and the refinement's contraction per sweep grows by at most about tol.  0 <= tol <= 0.5;
- * 0 refactors every subdomain every step; default 0.02.  mpm_stats.ds_factorisations counts
- * the factorisations computed.  MPM_ERR_ARG outside the range.  Drops a captured graph. */
+ * and the refinement's contraction per sweep grows by at most about tol.  tol <= 0.5; 0
+ * refactors every subdomain every step; negative (the default) means 0.005 on decompositions
+ * with at least 4 subdomains per SM (realisations included), where the factorisation competes
+ * with the rest of the step for the SMs, else 0.  mpm_stats.ds_factorisations counts the
+ * factorisations computed.  MPM_ERR_ARG above 0.5 or NaN.  Drops a captured graph. */
 int mpm_set_downscale_reuse(mpm_ctx* ctx, double tol);
 
 /* Absolute permeability K [R][ny][nx], every entry > 0 and finite (checked for host

@@ -326,7 +326,7 @@ class Context:
 
     def set_downscale_reuse(self, tol):
         """Keep float32 downscaling factors while the transmissibilities stay within a relative
-        tol of those they were computed from (0: refactor every step)."""
+        tol of those they were computed from (0: refactor every step, negative: the default)."""
         self._ck(self.L.mpm_set_downscale_reuse(self.h, float(tol)))
 
     def profile_enable(self, on=True):
