@@ -842,8 +842,14 @@ __global__ void k_downscale_factor_w(Grid g, DevState d, const DevSub* subs, int
 // maximum over its cells of max(total outflow, total inflow); the last block to finish
 // reduces these maxima per realisation into rate_max (CFL step).  The factor and stencil
 // are loaded before pdl_wait() (they come from a stream joined before the launch).
+// Resident CTAs per SM that the register allocation of the downscaling solve must allow, for
+// factor widths up to 16: 896 threads per SM with float32 factors (at most 72 registers a
+// thread), 640 with float64 ones (at most 102); no bound for 32-wide blocks (they would spill).
 template <typename T, int A, int NT>
-__global__ void __launch_bounds__(NT) k_downscale_w(Grid g, DevState d, const DevSub* subs, size_t qoff,
+constexpr int kDownscaleMinBlocks = A > 16 ? 1 : (std::is_same<T, float>::value ? 896 : 640) / NT;
+
+template <typename T, int A, int NT>
+__global__ void __launch_bounds__(NT, kDownscaleMinBlocks<T, A, NT>) k_downscale_w(Grid g, DevState d, const DevSub* subs, size_t qoff,
                                                                int refine, double tol, int ir_max) {
   extern __shared__ __align__(16) char smem[];
   __shared__ double red[64];

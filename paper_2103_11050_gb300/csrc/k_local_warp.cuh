@@ -52,6 +52,8 @@ struct Tables {
   double* X;    // m  FP64 solution
   double* B;    // m  FP64 right-hand side
   double* Rr;   // m  FP64 residual
+  double* fE;   // m  east face flux wE (x_c - x_east) of the current iterate (0 on the last column)
+  double* fN;   // m  north face flux wN (x_c - x_north) (0 on the last row)
   T* dh;        // b*A  scaled diagonal (padding: 1)
   T* eh;        // b*A  scaled coupling to the east neighbour (padding: 0)
   T* th;        // b*A  scaled coupling to the north neighbour, positive (padding: 0)
@@ -61,7 +63,7 @@ struct Tables {
 
 template <typename T, int A>
 __host__ __device__ constexpr size_t table_bytes(int m, int b) {
-  return (size_t)8 * m * sizeof(double) + (size_t)5 * b * A * sizeof(T);
+  return (size_t)10 * m * sizeof(double) + (size_t)5 * b * A * sizeof(T);
 }
 
 template <typename T, int A>
@@ -76,6 +78,8 @@ __device__ Tables<T> carve(char* base, int m, int b) {
   t.X = p; p += m;
   t.B = p; p += m;
   t.Rr = p; p += m;
+  t.fE = p; p += m;
+  t.fN = p; p += m;
   T* q = reinterpret_cast<T*>(p);
   t.dh = q; q += b * A;
   t.eh = q; q += b * A;
@@ -397,32 +401,38 @@ __device__ __forceinline__ unsigned long long half_bits(unsigned long long u) {
   return (u >> 52) >= 2ull ? u - (1ull << 52) : u >> 1;
 }
 
-// (A x)_c in flux form (see k_local.cu).
-__device__ __forceinline__ double apply_A(const DevSub& sd, const double* ex, const double* wE, const double* wN,
-                                          const double* x, int c) {
-  const int a = sd.a, b = sd.b;
+// East and north face fluxes of the iterate x, each face computed once: fE[c] = wE_c (x_c -
+// x_east), fN[c] = wN_c (x_c - x_north), 0 on the subdomain's last column / row.  All threads
+// of the CTA; a barrier must follow before apply_A reads them.
+__device__ __forceinline__ void face_fluxes(const DevSub& sd, const double* wE, const double* wN, const double* x,
+                                            double* fE, double* fN) {
+  const int a = sd.a, b = sd.b, m = a * b;
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    const int jl = c / a, il = c - jl * a;
+    fE[c] = il < a - 1 ? wE[c] * (x[c] - x[c + 1]) : 0.0;
+    fN[c] = jl < b - 1 ? wN[c] * (x[c] - x[c + a]) : 0.0;
+  }
+}
+
+// (A x)_c in flux form (see k_local.cu) from the face fluxes of face_fluxes: ex_c x_c plus the
+// cell's four outward face fluxes (the west and south ones are the neighbours' east / north
+// fluxes negated, which is exact), summed in a fixed order; absx: the cell's flux scale.
+__device__ __forceinline__ double apply_A(const DevSub& sd, const double* ex, const double* fE, const double* fN,
+                                          const double* x, int c, double& absx) {
+  const int a = sd.a;
   const int jl = c / a, il = c - jl * a;
-  const double xc = x[c];
-  double t0 = ex[c] * xc, t1 = 0.0, t2 = 0.0, t3 = 0.0, t4 = 0.0;
-  if (il < a - 1) t1 = wE[c] * (xc - x[c + 1]);
-  if (il > 0) t2 = wE[c - 1] * (xc - x[c - 1]);
-  if (jl < b - 1) t3 = wN[c] * (xc - x[c + a]);
-  if (jl > 0) t4 = wN[c - a] * (xc - x[c - a]);
+  const double t0 = ex[c] * x[c], t1 = fE[c], t3 = fN[c];
+  const double t2 = il > 0 ? -fE[c - 1] : 0.0, t4 = jl > 0 ? -fN[c - a] : 0.0;
+  absx = fabs(t0) + fabs(t1) + fabs(t2) + fabs(t3) + fabs(t4);
   return (t0 + t1) + (t2 + t3) + t4;
 }
 
-// (A x)_c in flux form (see k_local.cu) and the cell's flux scale.
-__device__ __forceinline__ double apply_A(const DevSub& sd, const double* ex, const double* wE, const double* wN,
-                                          const double* x, int c, double& absx) {
-  const int a = sd.a, b = sd.b;
+__device__ __forceinline__ double apply_A(const DevSub& sd, const double* ex, const double* fE, const double* fN,
+                                          const double* x, int c) {
+  const int a = sd.a;
   const int jl = c / a, il = c - jl * a;
-  const double xc = x[c];
-  double t0 = ex[c] * xc, t1 = 0.0, t2 = 0.0, t3 = 0.0, t4 = 0.0;
-  if (il < a - 1) t1 = wE[c] * (xc - x[c + 1]);
-  if (il > 0) t2 = wE[c - 1] * (xc - x[c - 1]);
-  if (jl < b - 1) t3 = wN[c] * (xc - x[c + a]);
-  if (jl > 0) t4 = wN[c - a] * (xc - x[c - a]);
-  absx = fabs(t0) + fabs(t1) + fabs(t2) + fabs(t3) + fabs(t4);
+  const double t0 = ex[c] * x[c], t1 = fE[c], t3 = fN[c];
+  const double t2 = il > 0 ? -fE[c - 1] : 0.0, t4 = jl > 0 ? -fN[c - a] : 0.0;
   return (t0 + t1) + (t2 + t3) + t4;
 }
 
@@ -436,7 +446,9 @@ __device__ void solve_refined(const DevSub& sd, Tables<T> t, const T* Q, bool re
   const int a = sd.a, b = sd.b, m = a * b;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (warm) {  // t.X holds an initial iterate: start from its residual
-    for (int c = tid; c < m; c += nt) t.Rr[c] = t.B[c] - apply_A(sd, t.ex, t.wE, t.wN, t.X, c);
+    face_fluxes(sd, t.wE, t.wN, t.X, t.fE, t.fN);
+    __syncthreads();
+    for (int c = tid; c < m; c += nt) t.Rr[c] = t.B[c] - apply_A(sd, t.ex, t.fE, t.fN, t.X, c);
   } else {
     for (int c = tid; c < m; c += nt) {
       t.X[c] = 0.0;
@@ -467,12 +479,14 @@ __device__ void solve_refined(const DevSub& sd, Tables<T> t, const T* Q, bool re
     }
     __syncthreads();
     if (!refine) { it = 1; ok = true; break; }
+    face_fluxes(sd, t.wE, t.wN, t.X, t.fE, t.fN);
+    __syncthreads();
     unsigned long long rb = 0;  // max |r| as a bit pattern
     if (it == 0) {  // the scale max(|A||x| + |b|) is taken once, at the first iterate
       unsigned long long sb = 0;
       for (int c = tid; c < m; c += nt) {
         double absx;
-        const double r = t.B[c] - apply_A(sd, t.ex, t.wE, t.wN, t.X, c, absx);
+        const double r = t.B[c] - apply_A(sd, t.ex, t.fE, t.fN, t.X, c, absx);
         t.Rr[c] = r;
         const unsigned long long ur = nn_bits(fabs(r)), us = nn_bits(absx + fabs(t.B[c]));
         rb = ur > rb ? ur : rb;
@@ -484,7 +498,7 @@ __device__ void solve_refined(const DevSub& sd, Tables<T> t, const T* Q, bool re
       thr_floor = nn_bits(1e3 * tol * smax);
     } else {
       for (int c = tid; c < m; c += nt) {
-        const double r = t.B[c] - apply_A(sd, t.ex, t.wE, t.wN, t.X, c);
+        const double r = t.B[c] - apply_A(sd, t.ex, t.fE, t.fN, t.X, c);
         t.Rr[c] = r;
         const unsigned long long ur = nn_bits(fabs(r));
         rb = ur > rb ? ur : rb;
