@@ -308,6 +308,20 @@ __global__ void k_load_checked(const double* __restrict__ src, double* __restric
   if (__syncthreads_or(found) && threadIdx.x == 0) *reinterpret_cast<volatile int*>(bad) = 1;
 }
 
+// k_load_checked that also writes the fractional flow f(s) of every value loaded (the one
+// quantity of the saturation that the next transport step reads besides s itself).
+__global__ void k_load_checked_fs(const double* __restrict__ src, double* __restrict__ dst,
+                                  double* __restrict__ fs_dst, long long n, double M, int* bad) {
+  int found = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = src[i];
+    dst[i] = v;
+    fs_dst[i] = fracflow(v, M);
+    found |= !(v >= 0.0 && v <= 1.0);
+  }
+  if (__syncthreads_or(found) && threadIdx.x == 0) *reinterpret_cast<volatile int*>(bad) = 1;
+}
+
 __global__ void k_store_host(const double* __restrict__ src, double* __restrict__ dst, long long n,
                              const int* status, int* status_host) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -349,6 +363,12 @@ void launch_choose(const Grid& g, const DevState& d, double eta, cudaStream_t st
 
 void launch_load_checked(const double* src_dev, double* dst, long long n, int* bad_dev, cudaStream_t st) {
   k_load_checked<<<transfer_blocks(n), kThreads, 0, st>>>(src_dev, dst, n, bad_dev);
+  ++g_launches;
+}
+
+void launch_load_checked_fs(const double* src_dev, double* dst, double* fs_dst, long long n, double M, int* bad_dev,
+                            cudaStream_t st) {
+  k_load_checked_fs<<<transfer_blocks(n), kThreads, 0, st>>>(src_dev, dst, fs_dst, n, M, bad_dev);
   ++g_launches;
 }
 

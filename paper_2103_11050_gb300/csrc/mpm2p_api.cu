@@ -40,6 +40,10 @@ struct mpm_ctx {
   int ir_max = 20;
   int fac_prec = -1;  // precision the stored factor was built with
   bool have_K = false, have_s = false, have_dec = false, have_basis = false;
+  // kappa^n, f(s) and the transmissibilities of kappa^n lag the current saturation: set by a
+  // pinned-memory mpm_set_saturation, which computes f(s) only (all a step needs); the other
+  // entry points bring them up to date first (ensure_derived)
+  bool derived_stale = false;
   double eta_init = 0.0;
   // decomposition
   int ncx = 0, ncy = 0;
@@ -242,6 +246,17 @@ bool fp32(const mpm_ctx* c) { return c->prec != MPM_PREC_FP64; }
 // for the SMs; on smaller ones it runs beside them for free and a kept factor would only add
 // refinement sweeps (measured: 1024^2 and the 256-realisation ensemble 10-13 % faster per
 // MPM-2P step, 256^2 6 % slower).
+// kappa^n, f(s) and the transmissibilities of the current saturation (k_mobility_eps).
+void recompute_derived(mpm_ctx* c) {
+  launch_mobility_eps(c->g, c->d, false, c->stream);
+  c->derived_stale = false;
+}
+
+// Brings them up to date when a pinned-memory mpm_set_saturation left them behind.
+void ensure_derived(mpm_ctx* c) {
+  if (c->derived_stale && c->have_s && c->have_K) recompute_derived(c);
+}
+
 double ds_reuse_tol(const mpm_ctx* c) {
   if (!fp32(c)) return 0.0;
   if (c->ds_reuse >= 0.0) return c->ds_reuse;
@@ -536,6 +551,7 @@ int run_downscale(mpm_ctx* c, bool after_interface, bool forked) {
 int run_transport(mpm_ctx* c, double cfl, int n_sub, bool decide, double eta, cudaGraphConditionalHandle h_reb,
                   bool set_handle) {
   prof_begin(c, MPM_STAGE_TRANSPORT);
+  c->derived_stale = false;  // the transport writes kappa^n and its transmissibilities of the new saturation
   const double fmax_ = max_fprime(c->g.M);
   for (int k = 0; k < n_sub; ++k) {
     if (k + 1 < n_sub) launch_upwind(c->g, c->d, cfl, fmax_, c->stream);
@@ -816,7 +832,7 @@ int mpm_set_permeability(mpm_ctx* c, const double* K, int mem) {
   int rc = copy_in(c, c->d.K, K, n, mem);
   if (rc) return rc;
   c->have_K = true;
-  if (c->have_s) launch_mobility_eps(c->g, c->d, false, c->stream);
+  if (c->have_s) recompute_derived(c);
   return check_launch(c);
 }
 
@@ -835,7 +851,7 @@ int mpm_set_fluids(mpm_ctx* c, double M) {
   if (!(M > 0) || !std::isfinite(M)) return fail(c, MPM_ERR_ARG, "viscosity ratio must be positive");
   c->g.M = M;
   drop_graph(c);
-  if (c->have_s && c->have_K) launch_mobility_eps(c->g, c->d, false, c->stream);
+  if (c->have_s && c->have_K) recompute_derived(c);
   return check_launch(c);
 }
 
@@ -1162,6 +1178,27 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
 int mpm_set_saturation(mpm_ctx* c, const double* s, int mem) {
   if (!c) return MPM_ERR_ARG;
   const size_t n = (size_t)c->g.R * c->g.nx * c->g.ny;
+  if (mem == MPM_MEM_HOST && s && c->have_K && pinned_device_ptr(s)) {
+    // Pinned memory: one kernel loads the values into the scratch saturation, range-checks
+    // them and writes their f(s) into the scratch f buffer; when every value lies in [0,1] the
+    // current and scratch buffers swap (the step graph of the other buffer parity serves
+    // from then on).  kappa^n and the transmissibilities are left for the next step's
+    // transport (which recomputes them from the new saturation) or for ensure_derived.
+    volatile int* flag = reinterpret_cast<volatile int*>(c->h_status) + 2;
+    *flag = 0;
+    launch_load_checked_fs(static_cast<const double*>(pinned_device_ptr(s)), c->d.s2, c->d.fs2, (long long)n, c->g.M,
+                           c->h_status_dev + 2, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    if (*flag != 0)
+      for (size_t i = 0; i < n; ++i)
+        if (!(s[i] >= 0 && s[i] <= 1)) return fail(c, MPM_ERR_ARG, "saturation must lie in [0,1] (index %zu)", i);
+    std::swap(c->d.s, c->d.s2);
+    std::swap(c->d.fs, c->d.fs2);
+    c->have_s = true;
+    c->derived_stale = true;
+    return MPM_OK;
+  }
   if (mem == MPM_MEM_HOST && s) {
     // The copy goes to the scratch saturation buffer (every step writes it before reading
     // it) and is range-checked on the way; the current saturation is replaced, by a device
@@ -1189,7 +1226,7 @@ int mpm_set_saturation(mpm_ctx* c, const double* s, int mem) {
     if (rc) return rc;
   }
   c->have_s = true;
-  if (c->have_K) launch_mobility_eps(c->g, c->d, false, c->stream);
+  if (c->have_K) recompute_derived(c);
   return check_launch(c);
 }
 
@@ -1197,6 +1234,7 @@ int mpm_build_basis(mpm_ctx* c) {
   if (!c) return MPM_ERR_ARG;
   int rc = need_ready(c, false);
   if (rc) return rc;
+  ensure_derived(c);
   launch_fill_flags(c->g, c->d, 1, c->stream);
   return run_build(c);
 }
@@ -1206,6 +1244,7 @@ int mpm_eval_epsilon(mpm_ctx* c, double* eps) {
   int rc = need_ready(c, true);
   if (rc) return rc;
   launch_mobility_eps(c->g, c->d, true, c->stream);
+  c->derived_stale = false;
   if ((rc = check_launch(c))) return rc;
   if (eps) return copy_out(c, eps, c->d.eps, c->g.R, MPM_MEM_HOST);
   return MPM_OK;
@@ -1228,6 +1267,7 @@ int mpm_perturbation_solve(mpm_ctx* c) {
   if (!c) return MPM_ERR_ARG;
   int rc = need_ready(c, true);
   if (rc) return rc;
+  ensure_derived(c);
   launch_fill_flags(c->g, c->d, 0, c->stream);
   return run_perturbation(c);
 }
@@ -1236,6 +1276,7 @@ int mpm_perturbation_correction(mpm_ctx* c) {
   if (!c) return MPM_ERR_ARG;
   int rc = need_ready(c, true);
   if (rc) return rc;
+  ensure_derived(c);
   if (c->g.order < 1) return fail(c, MPM_ERR_STATE, "the first-order term needs mpm_set_mpm_order(ctx, 1)");
   launch_fill_flags(c->g, c->d, 0, c->stream);
   return run_perturbation(c, 1);
@@ -1253,6 +1294,7 @@ int mpm_interface_solve(mpm_ctx* c) {
   if (!c) return MPM_ERR_ARG;
   int rc = need_ready(c, true);
   if (rc) return rc;
+  ensure_derived(c);
   const int pass = c->next_pass;
   c->next_pass = 0;
   return run_interface(c, pass);
@@ -1262,6 +1304,7 @@ int mpm_downscale(mpm_ctx* c) {
   if (!c) return MPM_ERR_ARG;
   int rc = need_ready(c, true);
   if (rc) return rc;
+  ensure_derived(c);
   return run_downscale(c, false, false);
 }
 
@@ -1280,7 +1323,7 @@ int mpm_init(mpm_ctx* c, double eta) {
   if (!std::isfinite(eta)) return fail(c, MPM_ERR_ARG, "eta must be finite");
   int rc = need_ready(c, false);
   if (rc) return rc;
-  launch_mobility_eps(c->g, c->d, false, c->stream);
+  recompute_derived(c);
   launch_fill_flags(c->g, c->d, 1, c->stream);
   // a fresh start: no stored downscaling factor is kept (their type may have changed)
   CK(cudaMemsetAsync(c->d.npin, 0xff, (size_t)c->g.R * c->subs.size() * sizeof(int), c->stream));
@@ -1306,6 +1349,7 @@ int mpm_step(mpm_ctx* c, double eta, double cfl, int n_sub) {
     const int slot = graph_slot(c);
     if (!c->graph_valid[slot] && (rc = build_step_graph(c, eta, cfl, n_sub))) return rc;
     CK(cudaGraphLaunch(c->graph_exec[slot], c->stream));
+    c->derived_stale = false;  // its transport wrote kappa^n and the transmissibilities
     if (n_sub & 1) {  // the graph left the new saturation in the other buffer
       std::swap(c->d.s, c->d.s2);
       std::swap(c->d.fs, c->d.fs2);
@@ -1372,6 +1416,7 @@ int mpm_get_saturation(mpm_ctx* c, double* s, int mem) {
 
 int mpm_get_conductivity(mpm_ctx* c, double* kappa, int mem) {
   if (!c) return MPM_ERR_ARG;
+  ensure_derived(c);
   return copy_out(c, kappa, c->d.kap_n, (size_t)c->g.R * c->g.nx * c->g.ny, mem);
 }
 
@@ -1477,6 +1522,7 @@ int mpm_autotune(mpm_ctx* c, int reps, double* ms_out) {
   if (reps < 1 || reps > 100) return fail(c, MPM_ERR_ARG, "need 1 <= reps <= 100");
   int rc = need_ready(c, true);
   if (rc) return rc;
+  ensure_derived(c);
   const Grid& g = c->g;
   DevState& d = c->d;
   const int nsub = (int)c->subs.size();
@@ -1496,7 +1542,7 @@ int mpm_autotune(mpm_ctx* c, int reps, double* ms_out) {
                                     reps, e0, e1);
     if (ms < best_ms[0]) { best_ms[0] = ms; best.transport_rows = rows; }
   }
-  launch_mobility_eps(g, d, false, c->stream);
+  recompute_derived(c);
   // 2. the MPM-2P local solve (every realisation takes the reuse branch while timed; the
   //    branch flags of the last update are put back afterwards: the downscaling reads them)
   std::vector<int> flags(g.R);

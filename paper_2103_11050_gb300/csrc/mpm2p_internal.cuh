@@ -221,6 +221,8 @@ void launch_choose(const Grid& g, const DevState& d, double eta, cudaStream_t st
 void launch_fill_flags(const Grid& g, const DevState& d, int v, cudaStream_t st);
 // transfers with pinned host memory addressed from the device (no copy engine)
 void launch_load_checked(const double* src_dev, double* dst, long long n, int* bad_dev, cudaStream_t st);
+void launch_load_checked_fs(const double* src_dev, double* dst, double* fs_dst, long long n, double M, int* bad_dev,
+                            cudaStream_t st);
 void launch_store_host(const double* src, double* dst_dev, long long n, const int* status, int* status_host_dev,
                        cudaStream_t st);
 void launch_upwind(const Grid& g, const DevState& d, double cfl, double fmax, cudaStream_t st);
