@@ -48,10 +48,11 @@ CFL = 0.5
 N_SUB = 1
 FORCED_REBUILDS = 3
 IR_TOL = 1e-14  # backward-error target of the FP64 refinement of float32 factors (--ir-tol)
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the step's kernels on the
-# default workload, from an ncu capture of this code (profiles/); a kernel is left out when
-# it changed since its capture.
-TRAFFIC = {}
+# dram__bytes_read.sum + dram__bytes_write.sum of the step's kernels on the default workload
+# (per launch; the interface sweeps: all levels of one solve), from an ncu capture of this
+# code (profiles/counters_channel1024.md); a kernel is left out when it changed since.
+TRAFFIC = {"k_downscale_w": 172.0e6, "k_mpm_local_w": 239.2e6, "k_upwind_kappa": 55.6e6, "k_nd_up": 342.9e6,
+           "k_nd_down": 234.1e6}
 PREC = {"fp32": "FP32 downscaling factorisations + FP64 refinement; FP64 Robin factors, interface, fluxes, "
                 "transport",
         "fp32all": "FP32 local factorisations + FP64 refinement; FP64 interface, fluxes, transport",
@@ -520,14 +521,15 @@ def run_gpu(args, wl):
         gbs = byts / (ms / 1e3) / 1e9
         tfs = flops / (ms / 1e3) / 1e12
         kern[name] = {"ms_per_step": ms, "bytes": byts, "flops": flops, "gbs": gbs, "frac_hbm": gbs / pk["hbm_gbs"],
-                      "tflops": tfs, "frac_fp64": tfs / fp64_peak}
+                      "tflops": tfs, "frac_fp64": tfs / fp64_peak,
+                      "traffic": TRAFFIC.get(name) if wl.name == "channel1024" and prec == "fp32" else None}
     dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
     kd = kern[dom]
     alu = kd["frac_fp64"] >= kd["frac_hbm"]
     roof = {"kernel": dom, "bound": "alu" if alu else "hbm",
             "achieved": kd["tflops"] if alu else kd["gbs"], "peak": fp64_peak if alu else pk["hbm_gbs"],
             "unit": "TFLOP/s" if alu else "GB/s", "frac": kd["frac_fp64"] if alu else kd["frac_hbm"],
-            "traffic": TRAFFIC.get(dom),
+            "traffic": kern[dom]["traffic"],
             "peak_kind": ("derived float64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz" if alu
                           else f"{pk_kind} HBM copy bandwidth"),
             "kernels": kern, "stage_ms_per_mpm_step_eager": stage, "stage_ms_per_rebuild_step_eager": reb_stage}
