@@ -100,11 +100,11 @@ __global__ void k_fill_flags(Grid g, DevState d, int v) {
   if (r < g.R) d.rebuild[r] = v;
 }
 
-// dt = cfl h^2 / (max f' * rate_max) with rate_max the largest total in- or outflow of a
-// cell (reduced by the downscaling); dt = 0 when nothing flows.
-__device__ __forceinline__ double cfl_dt(const Grid& g, const DevState& d, int r, double cfl, double fmax_) {
-  const double rate = d.rate_max[r];
-  return rate > 0.0 ? cfl * g.h * g.h / (fmax_ * rate) : 0.0;
+// lambda = dt / h^2 = (cfl / max f') / rate_max with rate_max the largest total in- or outflow
+// of a cell (reduced by the downscaling, which also stores its reciprocal); cfl_fmax = cfl /
+// max f' from the host; 0 when nothing flows.
+__device__ __forceinline__ double cfl_lambda(const DevState& d, int r, double cfl_fmax) {
+  return cfl_fmax * d.inv_rate[r];
 }
 
 // Explicit upwind update of cell (i, j) (Eq. BL2D): s - dt/h^2 sum_faces F_out f(s_upwind),
@@ -132,15 +132,14 @@ __device__ __forceinline__ double upwind_cell(const Grid& g, const double* ux, c
 }
 
 // One upwind substep s -> s2 with f(s2) -> fs2 (all substeps but the last).
-__global__ void k_upwind(Grid g, DevState d, double cfl, double fmax_) {
+__global__ void k_upwind(Grid g, DevState d, double cfl_fmax) {
   const int r = blockIdx.y;
   const long long n = g.ncell(), base = (long long)r * n;
-  const double dt = cfl_dt(g, d, r, cfl, fmax_);
-  if (blockIdx.x == 0 && threadIdx.x == 0) d.dt[r] = dt;
-  const double lam = dt / (g.h * g.h);
+  const double lam = cfl_lambda(d, r, cfl_fmax);
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.dt[r] = lam * g.h * g.h;
   const double* ux = d.ux + (long long)r * g.nfx();
   const double* uy = d.uy + (long long)r * g.nfy();
-  const double f_in = fracflow(g.s_inflow, g.M);
+  const double f_in = g.f_in;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(c / g.nx), i = (int)(c - (long long)j * g.nx);
@@ -166,29 +165,22 @@ constexpr int kTX = 32;  // columns of the cell tile of the last transport subst
 // the basis is rebuilt, else sqrt(num / den)), counts the branches and, in a CUDA graph
 // (set_handle), sets the conditional handle of the rebuild body.
 template <int kTY>
-__global__ void __launch_bounds__(kTX * kTY / 2) k_upwind_kappa(Grid g, DevState d, double cfl, double fmax_,
-                                                                int decide, double eta,
-                                                                cudaGraphConditionalHandle h_reb, int set_handle) {
+__global__ void __launch_bounds__(kTX * kTY / 2) k_upwind_kappa(Grid g, DevState d, double cfl_fmax, int decide,
+                                                                double eta, cudaGraphConditionalHandle h_reb,
+                                                                int set_handle) {
   __shared__ double sn[kTY + 1][kTX + 1];  // s2
   __shared__ double sw[kTY + 1][kTX + 1];  // M s2^2
   __shared__ double sl[kTY + 1][kTX + 1];  // lambda(s2)
   __shared__ double sk[kTY + 1][kTX + 1];  // kappa^n of s2
   __shared__ double sh[32];
-  __shared__ double lam_s, fin_s;
   __shared__ int last, tot;
   const int r = blockIdx.y;
   const int nx = g.nx, ny = g.ny;
   const int ntx = (nx + kTX - 1) / kTX;
   const int tx0 = (blockIdx.x % ntx) * kTX, ty0 = (blockIdx.x / ntx) * kTY;
   const long long base = (long long)r * g.ncell();
-  if (threadIdx.x == 0) {
-    const double dt = cfl_dt(g, d, r, cfl, fmax_);
-    if (blockIdx.x == 0) d.dt[r] = dt;
-    lam_s = dt / (g.h * g.h);
-    fin_s = fracflow(g.s_inflow, g.M);
-  }
-  __syncthreads();
-  const double lam = lam_s, f_in = fin_s;
+  const double lam = cfl_lambda(d, r, cfl_fmax), f_in = g.f_in;  // every thread: two loads, one multiply
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.dt[r] = lam * g.h * g.h;
   const double* ux = d.ux + (long long)r * g.nfx();
   const double* uy = d.uy + (long long)r * g.nfy();
   for (int e = threadIdx.x; e < (kTX + 1) * (kTY + 1); e += blockDim.x) {
@@ -384,7 +376,7 @@ void launch_fill_flags(const Grid& g, const DevState& d, int v, cudaStream_t st)
 }
 
 void launch_upwind(const Grid& g, const DevState& d, double cfl, double fmax_, cudaStream_t st) {
-  k_upwind<<<dim3(cell_blocks(g), g.R), kThreads, 0, st>>>(g, d, cfl, fmax_);
+  k_upwind<<<dim3(cell_blocks(g), g.R), kThreads, 0, st>>>(g, d, cfl / fmax_);
   ++g_launches;
 }
 
@@ -397,9 +389,10 @@ void launch_upwind_kappa(const Grid& g, const DevState& d, double cfl, double fm
                          cudaGraphConditionalHandle h_reb, bool set_handle, int rows, cudaStream_t st) {
   const dim3 grid(upwind_kappa_blocks_rows(g, rows), g.R);
   const int dec = decide ? 1 : 0, sh = set_handle ? 1 : 0;
-  if (rows >= 16) k_upwind_kappa<16><<<grid, kTX * 8, 0, st>>>(g, d, cfl, fmax_, dec, eta, h_reb, sh);
-  else if (rows >= 8) k_upwind_kappa<8><<<grid, kTX * 4, 0, st>>>(g, d, cfl, fmax_, dec, eta, h_reb, sh);
-  else k_upwind_kappa<4><<<grid, kTX * 2, 0, st>>>(g, d, cfl, fmax_, dec, eta, h_reb, sh);
+  const double cf = cfl / fmax_;
+  if (rows >= 16) k_upwind_kappa<16><<<grid, kTX * 8, 0, st>>>(g, d, cf, dec, eta, h_reb, sh);
+  else if (rows >= 8) k_upwind_kappa<8><<<grid, kTX * 4, 0, st>>>(g, d, cf, dec, eta, h_reb, sh);
+  else k_upwind_kappa<4><<<grid, kTX * 2, 0, st>>>(g, d, cf, dec, eta, h_reb, sh);
   ++g_launches;
 }
 

@@ -297,11 +297,12 @@ constexpr int kKpt = 16;
 // g gathered from the children.
 template <int KS>
 __global__ void __launch_bounds__(256) k_nd_up(Grid g, DevState d, const DevNode* nodes, const int* level_nodes,
-                                               const int* srcmap) {
+                                               const int* srcmap, int branch) {
   constexpr int ROWS = 256 / KS;
   extern __shared__ __align__(16) double nd_smem[];
   pdl_trigger();
   const int r = blockIdx.z;
+  if (branch >= 0 && d.rebuild[r] != branch) return;  // branch >= 0: only the realisations that took it
   const DevNode nd = nodes[level_nodes[blockIdx.x]];
   const int row0 = blockIdx.y * ROWS;
   if (row0 >= nd.nf) return;
@@ -623,11 +624,11 @@ int k_split(int n, int terms) {
   } while (0)
 
 void launch_nd_up(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
-                  int max_nf, int max_nsep, const int* srcmap, bool pdl, int terms, cudaStream_t st) {
+                  int max_nf, int max_nsep, const int* srcmap, bool pdl, int terms, cudaStream_t st, int branch) {
   const int ks = k_split(max_nsep, terms), rows = 256 / ks;
   const dim3 grid(nlev, (max_nf + rows - 1) / rows, g.R);
   const size_t smem = (size_t)(256 + max_nsep) * sizeof(double);
-  MPM_DISPATCH_KS(k_nd_up, ks, grid, dim3(256), smem, st, pdl, g, d, nodes, level_nodes, srcmap);
+  MPM_DISPATCH_KS(k_nd_up, ks, grid, dim3(256), smem, st, pdl, g, d, nodes, level_nodes, srcmap, branch);
 }
 
 void launch_nd_down(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,

@@ -123,5 +123,67 @@ __device__ __forceinline__ double ubar_face(const Grid& g, const DevState& d, co
   return (side == 0 || side == 2) ? -out : out;
 }
 
+// Upward step of the nested-dissection solve at one level-1 node nid (two leaf children) for
+// realisation r, by all threads of one CTA: g_s gathered from the children's right-hand sides,
+// then for every frontal row y[row] = sum_k G[k][row] g_s[k] into x (separator rows) or
+// g_b[row] = gather(row) - y[row] into g (boundary rows), as the level kernels do (k_iface.cu).
+// The children's vectors were written by other CTAs: read past L1.
+__device__ __forceinline__ void nd_up_leaf_parent(const DevState& d, const DevNode* nodes, int nid, int r) {
+  __shared__ double gs[4 * kMaxSide];  // a level-1 separator is one interface: at most 4 kMaxSide DOFs
+  const DevNode nd = nodes[nid];
+  const int nf = nd.nf, ns = nd.nsep;
+  const long long vb = (long long)r * d.st_vec;
+  const int* s0 = d.srcmap + nd.src_off;
+  const int* s1 = s0 + nf;
+  const double* g0 = d.gvec + vb + nodes[nd.child[0]].v_off;  // leaves: no separator part
+  const double* g1 = d.gvec + vb + nodes[nd.child[1]].v_off;
+  for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+    const int a0 = s0[k], a1 = s1[k];
+    gs[k] = (a0 >= 0 ? __ldcg(g0 + a0) : 0.0) + (a1 >= 0 ? __ldcg(g1 + a1) : 0.0);
+  }
+  __syncthreads();
+  const double* F = d.front + (long long)r * d.st_front + nd.f_off;
+  for (int row = threadIdx.x; row < nf; row += blockDim.x) {
+    double acc0 = 0.0, acc1 = 0.0;
+    int k = 0;
+    for (; k + 1 < ns; k += 2) {
+      acc0 += F[(long long)k * nf + row] * gs[k];
+      acc1 += F[(long long)(k + 1) * nf + row] * gs[k + 1];
+    }
+    if (k < ns) acc0 += F[(long long)k * nf + row] * gs[k];
+    const double y = acc0 + acc1;
+    if (row < ns) {
+      d.xvec[vb + nd.v_off + row] = y;
+    } else {
+      const int a0 = s0[row], a1 = s1[row];
+      d.gvec[vb + nd.v_off + row] = ((a0 >= 0 ? __ldcg(g0 + a0) : 0.0) + (a1 >= 0 ? __ldcg(g1 + a1) : 0.0)) - y;
+    }
+  }
+}
+
+// Called by every thread of a CTA of the MPM-2P local solve right after it wrote leaf lid's
+// interface right-hand side (realisation r): the CTA that completes the second child of a
+// level-1 node does that node's upward step (nd_up_leaf_parent), so the level-1 sweep of an
+// MPM-2P update needs no launch of its own.  (After a basis build the level-1 step is launched
+// behind the new factorisation instead, for the rebuilding realisations only.)  A ticket
+// per node and realisation counts the completed children (last-arriving-block pattern: no CTA
+// waits for another); the second arrival resets it for the next solve.
+__device__ __forceinline__ void fold_up(const DevState& d, const DevNode* nodes, int lid, int r) {
+  __shared__ int last;
+  const int p = nodes[lid].parent;
+  if (p < 0 || nodes[p].level != 1) return;
+  __syncthreads();  // every write of this leaf's right-hand side issued
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned int* t = d.nd_ticket + (long long)r * d.st_nodes + p;
+    last = atomicAdd(t, 1u) == 1u;
+    if (last) *t = 0u;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  nd_up_leaf_parent(d, nodes, p, r);
+}
+
 }  // namespace phase
 }  // namespace mpm

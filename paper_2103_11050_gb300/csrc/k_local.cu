@@ -750,6 +750,7 @@ __global__ void __launch_bounds__(NT, kLocalMinBlocks<A, NT>) k_mpm_local_w(Grid
   if (sd.ndof > 0) {
     const DevNode& leaf = nodes[leaf_node[sidx]];
     for (int k = threadIdx.x; k < sd.ndof; k += blockDim.x) phase::element_rhs(g, d, sd, leaf, r, k, fb);
+    phase::fold_up(d, nodes, leaf_node[sidx], r);
   }
 }
 
@@ -988,7 +989,10 @@ __global__ void __launch_bounds__(NT, kDownscaleMinBlocks<T, A, NT>) k_downscale
       mb = u > mb ? u : mb;
     }
     const double mx = nn_from_bits(warp::cta_max_bits(mb, red));
-    if (threadIdx.x == 0) d.rate_max[rr] = mx;
+    if (threadIdx.x == 0) {
+      d.rate_max[rr] = mx;
+      d.inv_rate[rr] = mx > 0.0 ? 1.0 / mx : 0.0;
+    }
   }
   if (threadIdx.x == 0) d.ticket[0] = 0;
 }

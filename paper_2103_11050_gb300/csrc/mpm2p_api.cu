@@ -239,6 +239,12 @@ double max_fprime(double M) {
 // mixed modes; the Robin factors (reused by every BF solve and MPM-2P step) only in
 // MPM_PREC_FP32_IR_ALL.
 bool fp32(const mpm_ctx* c) { return c->prec != MPM_PREC_FP64; }
+
+// Fractional flow f(s) = M s^2 / (M s^2 + (1 - s)^2) (Eq. BL2D) on the host (inflow boundary).
+double host_fracflow(double s, double M) {
+  const double lw = M * s * s, o = 1.0 - s;
+  return lw / (lw + o * o);
+}
 // Relative change of the transmissibilities up to which a stored float32 downscaling factor is
 // kept (0: refactor every step; float64 factors are never kept: nothing refines them).  The
 // default keeps factors within 0.5 % on decompositions with at least 4 subdomains per SM
@@ -425,6 +431,11 @@ int run_build(mpm_ctx* c) {
       launch_nd_factor_level(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(),
                              c->lev_max_nf[L], c->lev_max_nsep[L], c->d_srcmap, st);
     prof_end(c, MPM_STAGE_IFACE_FACTOR);
+    // level 1 of the upward sweep with the new fronts, for the rebuilding realisations (the
+    // MPM-2P local solve does it for the others, phase::fold_up)
+    if (c->levels.size() > 1)
+      launch_nd_up(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[1], (int)c->levels[1].size(), c->lev_max_nf[1],
+                   c->lev_max_nsep[1], c->d_srcmap, false, c->tune.sweep_terms, st, 1);
   }
   c->fac_prec = c->prec;
   c->have_basis = true;
@@ -462,7 +473,9 @@ int run_interface(mpm_ctx* c, int pass = 0) {
   bool chained = false;
   if (c->n_dof > 0) {
     prof_begin(c, MPM_STAGE_IFACE_UP);
-    for (size_t L = 1; L < c->levels.size(); ++L) {
+    // level 1 (nodes with two leaf children) was done by the local kernels that wrote the
+    // leaves' right-hand sides (phase::fold_up)
+    for (size_t L = 2; L < c->levels.size(); ++L) {
       launch_nd_up(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(), c->lev_max_nf[L],
                    c->lev_max_nsep[L], c->d_srcmap, chained && c->use_pdl, c->tune.sweep_terms, st);
       chained = true;
@@ -728,6 +741,7 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   g.bc_val[1] = g.bc_val[2] = g.bc_val[3] = 0.0;
   g.s_inflow = 1.0;
   g.M = 1.0;
+  g.f_in = host_fracflow(g.s_inflow, g.M);
   g.seg_len = 1;
   g.inv_seg = 1.0;
   g.degree = 0;
@@ -850,6 +864,7 @@ int mpm_set_fluids(mpm_ctx* c, double M) {
   if (!c) return MPM_ERR_ARG;
   if (!(M > 0) || !std::isfinite(M)) return fail(c, MPM_ERR_ARG, "viscosity ratio must be positive");
   c->g.M = M;
+  c->g.f_in = host_fracflow(c->g.s_inflow, M);
   drop_graph(c);
   if (c->have_s && c->have_K) recompute_derived(c);
   return check_launch(c);
@@ -871,6 +886,7 @@ int mpm_set_boundary(mpm_ctx* c, const int type[4], const double val[4], double 
     c->g.bc_val[k] = val[k];
   }
   c->g.s_inflow = s_inflow;
+  c->g.f_in = host_fracflow(s_inflow, c->g.M);
   c->have_basis = false;
   drop_graph(c);
   return MPM_OK;
@@ -1114,6 +1130,7 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   d.st_vec = v_off;
   d.st_col = v_off * kPivotChunk;
   d.st_lvl = st_lvl;
+  d.st_nodes = nn;
   auto& A = c->dec_allocs;
   int rc = MPM_OK;
   if (!rc) rc = dalloc(c, A, &d.fac, (size_t)R * q_off * sizeof(double));
@@ -1136,6 +1153,7 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   if (!rc) rc = dalloc_t(c, A, &d.pm_mean, (size_t)R * nsub);
   if (!rc) rc = dalloc_t(c, A, &d.rate_part, (size_t)R * nsub);
   if (!rc) rc = dalloc_t(c, A, &d.rate_max, (size_t)R);
+  if (!rc) rc = dalloc_t(c, A, &d.inv_rate, (size_t)R);
   if (!rc) rc = dalloc_t(c, A, &d.front, (size_t)R * f_off);
   if (!rc) rc = dalloc_t(c, A, &d.gvec, (size_t)R * v_off);
   if (!rc) rc = dalloc_t(c, A, &d.xvec, (size_t)R * v_off);
@@ -1143,9 +1161,11 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   if (!rc) rc = dalloc_t(c, A, &d.colold, (size_t)R * d.st_col);
   if (!rc) rc = dalloc_t(c, A, &c->d_subs, (size_t)nsub);
   if (!rc) rc = dalloc_t(c, A, &c->d_nodes, (size_t)nn);
+  if (!rc) rc = dalloc_t(c, A, &d.nd_ticket, (size_t)R * nn);  // zeroed
   if (!rc) rc = dalloc_t(c, A, &c->d_leaf_node, (size_t)nsub);
   if (!rc) rc = dalloc_t(c, A, &c->d_level_nodes, level_nodes.size());
   if (!rc) rc = dalloc_t(c, A, &c->d_srcmap, srcmap.size());
+  if (!rc) d.srcmap = c->d_srcmap;
   if (!rc) rc = dalloc_t(c, A, &c->d_pmap, pmap.size());
   if (c->classes.size() > 1)
     for (size_t k = 0; k < c->classes.size() && !rc; ++k) rc = dalloc_t(c, A, &c->classes[k].d_list, cls_lists[k].size());
@@ -1582,7 +1602,7 @@ int mpm_autotune(mpm_ctx* c, int reps, double* ms_out) {
   if (c->n_dof > 0)
     for (int terms : {4, 8, 16}) {
       const double ms = time_launches(c, [&] {
-        for (size_t L = 1; L < c->levels.size(); ++L)
+        for (size_t L = 2; L < c->levels.size(); ++L)
           launch_nd_up(g, d, c->d_nodes, c->d_level_nodes + c->lev_off[L], (int)c->levels[L].size(),
                        c->lev_max_nf[L], c->lev_max_nsep[L], c->d_srcmap, false, terms, c->stream);
         for (int L = (int)c->levels.size() - 2; L >= 2; --L)

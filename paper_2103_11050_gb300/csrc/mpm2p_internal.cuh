@@ -55,6 +55,7 @@ struct Grid {
   double bc_val[4];
   double s_inflow;
   double M;
+  double f_in;  // f(s_inflow) = M s_inflow^2 / (M s_inflow^2 + (1 - s_inflow)^2), set with s_inflow and M
   int seg_len, degree;
   double inv_seg;  // 1 / seg_len
   double alpha;
@@ -141,6 +142,7 @@ struct DevState {
   double *eps, *dt, *eps_part;
   double* rate_part;  // [R][st_sub] per subdomain: max over its cells of max(outflow, inflow), by the downscaling
   double* rate_max;   // [R] max over rate_part, by the last block of the downscaling
+  double* inv_rate;   // [R] 1 / rate_max (0 when nothing flows), by the same block
   unsigned int* ticket;  // [4] block-completion counters (0: downscaling, 1: transport); back to 0 after each launch
   int* rebuild;        // [R] branch of the current update: 1 = basis build, 0 = MPM-2P reuse
   int* status;         // [1] bitmask: 1 = a refinement did not reach its tolerance
@@ -176,7 +178,9 @@ struct DevState {
   // interface system
   double *front, *gvec, *xvec;  // st_front, st_vec, st_vec
   double *pivinv, *colold;      // st_lvl * 256, st_col
-  long long st_fac, st_t, st_tr, st_pf, st_dof, st_face, st_sub, st_front, st_vec, st_col, st_lvl;
+  const int* srcmap;         // extend-add maps of the internal nodes (DevNode::src_off)
+  unsigned int* nd_ticket;   // [R][st_nodes] children of each level-1 node done so far (see phase::fold_up)
+  long long st_fac, st_t, st_tr, st_pf, st_dof, st_face, st_sub, st_front, st_vec, st_col, st_lvl, st_nodes;
 };
 
 // Kernels launched by this process through the wrappers below (host side, not thread safe).
@@ -254,7 +258,8 @@ void launch_element_matrix(const Grid& g, const DevState& d, const DevSub* subs,
 void launch_nd_factor_level(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes,
                             int nlev, int max_nf, int max_nsep, const int* srcmap, cudaStream_t st);
 void launch_nd_up(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
-                  int max_nf, int max_nsep, const int* srcmap, bool pdl, int terms, cudaStream_t st);
+                  int max_nf, int max_nsep, const int* srcmap, bool pdl, int terms, cudaStream_t st,
+                  int branch = -1);
 void launch_nd_down(const Grid& g, const DevState& d, const DevNode* nodes, const int* level_nodes, int nlev,
                     int max_nsep, int max_nbnd, const int* pmap, bool pdl, int terms, cudaStream_t st);
 
