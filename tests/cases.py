@@ -18,6 +18,9 @@ CASES = {
     # alpha varying face by face (aMRCM, Section 3.1): the alpha argument is replaced by a seeded field
     "alpha_field": (40, 36, [8, 12, 20], [12, 8, 16], 4, 1, None, "exponential", 2.0, 0.15, 5.0, (D, D, N, N),
                     (1, 0, 0, 0), 9),
+    # 9 x 9 subdomains with 32 interface DOFs per side: the top separator (9 interfaces, 288
+    # DOFs) and the boundaries of the level below it are longer than 256
+    "long_sep": (144, 144, [16] * 9, [16] * 9, 2, 1, 1.0, "exponential", 1.0, 0.2, 3.0, (D, D, N, N), (1, 0, 0, 0), 10),
 }
 
 

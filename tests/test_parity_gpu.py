@@ -248,6 +248,48 @@ def test_algorithm1_parity(name, eta, steps, prec, graph, pdl):
     assert rel(ctx.get_pressure(1)[0], st.step.p_down) <= tol, rel(ctx.get_pressure(1)[0], st.step.p_down)
 
 
+_LONG_SEP = {}
+
+
+def _long_sep_trajectory(eta, steps):
+    """Oracle trajectory of the long-separator case (computed once per module)."""
+    if not _LONG_SEP:
+        c = case("long_sep", "zero")
+        prob, dec = _oracle_setup(c)
+        st = O.simulate_init(c["K"], c["s0"], prob, dec, eta)
+        for _ in range(steps):
+            O.simulate_step(st, c["K"], prob, dec, eta, 0.5, 1)
+        _LONG_SEP.update(c=c, st=st)
+    return _LONG_SEP["c"], _LONG_SEP["st"]
+
+
+@pytest.mark.parametrize("graph", [True, False])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_long_separator_levels(prec, graph):
+    """Sweep levels longer than the sweep kernels' register-held terms (the top separator of
+    288 DOFs and the boundaries of the level below it take the kernels that stage their
+    operator tile in shared memory), in the rebuild and the MPM-2P interface solves: 144^2,
+    9 x 9 subdomains, init and 6 Algorithm 1 steps with a rebuild among them, against the
+    oracle."""
+    eta, steps = 0.003, 6
+    c, st = _long_sep_trajectory(eta, steps)
+    ctx = _gpu(c, prec)
+    ctx.set_execution(graph, True)
+    ctx.init(eta)
+    for _ in range(steps):
+        ctx.step(eta, 0.5, 1)
+    n_reb = sum(1 for h in st.history if h["rebuild"])
+    assert n_reb >= 1
+    assert ctx.get_stats()["rebuilds"] == n_reb + 1
+    tol = TOL[prec]
+    ux, uy = ctx.get_flux()
+    assert rel(ctx.get_saturation()[0], st.s) <= tol
+    assert rel(ux[0], st.step.Fx) <= tol, rel(ux[0], st.step.Fx)
+    assert rel(uy[0], st.step.Fy) <= tol + 1e-12, rel(uy[0], st.step.Fy)
+    assert rel(ctx.get_pressure(0)[0], st.p_m) <= tol, rel(ctx.get_pressure(0)[0], st.p_m)
+    assert rel(ctx.get_pressure(1)[0], st.step.p_down) <= tol, rel(ctx.get_pressure(1)[0], st.step.p_down)
+
+
 @pytest.mark.parametrize("name,eta,steps", [("contrast64", 0.05, 20), ("uneven", 0.02, 12)])
 def test_downscale_factor_reuse(name, eta, steps):
     """Kept float32 downscaling factors (mpm_set_downscale_reuse): the float64 refinement runs
