@@ -51,8 +51,8 @@ IR_TOL = 1e-14  # backward-error target of the FP64 refinement of float32 factor
 # dram__bytes_read.sum + dram__bytes_write.sum of the step's kernels on the default workload
 # (per launch; the interface sweeps: all levels of one solve), from an ncu capture of this
 # code (profiles/counters_channel1024.md); a kernel is left out when it changed since.
-TRAFFIC = {"k_downscale_w": 172.0e6, "k_mpm_local_w": 239.2e6, "k_upwind_kappa": 55.6e6, "k_nd_up": 342.9e6,
-           "k_nd_down": 234.1e6}
+TRAFFIC = {"k_downscale_w": 161.8e6, "k_mpm_local_w": 260.7e6, "k_upwind_kappa": 55.3e6, "k_nd_up": 309.7e6,
+           "k_nd_down": 234.2e6}
 PREC = {"fp32": "FP32 downscaling factorisations + FP64 refinement; FP64 Robin factors, interface, fluxes, "
                 "transport",
         "fp32all": "FP32 local factorisations + FP64 refinement; FP64 interface, fluxes, transport",
@@ -176,18 +176,20 @@ def setup_ctx(B, wl, prec, stream, tune=None):
 
 
 def iface_work(nodes):
-    """Algorithmic work of one interface solve, per sweep: (bytes, flops).  The upward sweep
-    reads every internal node's separator rows of its transposed frontal matrix once
-    (nsep x nf float64) and its gathered right-hand side and output (2 nf float64), one
-    multiply-add per matrix entry; the downward sweep reads the coupling block nbnd x nsep
-    (nodes: nd_sizes)."""
-    up = (sum(8.0 * ns * nf + 16.0 * nf for ns, nf, _ in nodes if ns > 0),
-          sum(2.0 * ns * nf for ns, nf, _ in nodes if ns > 0))
+    """Algorithmic work of one interface solve: (bytes, flops) of the upward step of the level-1
+    nodes (done inside the MPM-2P local solve), of the upward sweep kernels (levels 2 and up) and
+    of the downward sweep kernels.  An upward step reads the node's separator rows of its
+    transposed frontal matrix once (nsep x nf float64) and its gathered right-hand side and
+    output (2 nf float64), one multiply-add per matrix entry; a downward step reads the coupling
+    block nbnd x nsep (nodes: nd_sizes)."""
+    def up(levels):
+        sel = [(ns, nf) for ns, nf, lev in nodes if ns > 0 and levels(lev)]
+        return sum(8.0 * ns * nf + 16.0 * nf for ns, nf in sel), sum(2.0 * ns * nf for ns, nf in sel)
     # the downward kernels visit the levels between the root (final after the upward sweep) and
     # level 1 (done inside the reconstruction)
     inner = [(ns, nf) for ns, nf, lev in nodes[:-1] if lev >= 2 and ns > 0]
     down = (sum(8.0 * ns * (nf - ns) + 16.0 * ns for ns, nf in inner), sum(2.0 * ns * (nf - ns) for ns, nf in inner))
-    return up, down
+    return up(lambda lev: lev == 1), up(lambda lev: lev >= 2), down
 
 
 def local_work(col_w, row_h, R, fp32_factor):
@@ -508,8 +510,10 @@ def run_gpu(args, wl):
     fp64_peak = 152 * 2 * 2 * 2070e6 / 1e12
     stage = {k: v[0] / max(args.steps, 1) for k, v in prof_main.items()}
     reb_stage = {k: v[0] / FORCED_REBUILDS for k, v in prof_reb.items()}
-    (ub, uf), (db, df) = iface_work(nd_sizes(wl.col_w, wl.row_h))
+    (u1b, u1f), (ub, uf), (db, df) = iface_work(nd_sizes(wl.col_w, wl.row_h))
     (lb, lf), (dsb, dsf) = local_work(wl.col_w, wl.row_h, wl.R, prec != "fp64")
+    # the MPM-2P local solve also does the upward step of the level-1 nodes
+    lb, lf = lb + u1b * wl.R, lf + u1f * wl.R
     work = {"k_mpm_local_w": ("perturb", lb, lf), "k_downscale_w": ("downscale", dsb, dsf),
             "k_upwind_kappa": ("transport", 88.0 * cells, 30.0 * cells),
             "k_nd_up": ("iface_up", ub * wl.R, uf * wl.R), "k_nd_down": ("iface_down", db * wl.R, df * wl.R)}
