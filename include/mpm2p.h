@@ -76,7 +76,9 @@ enum { MPM_SIDE_LEFT = 0, MPM_SIDE_RIGHT = 1, MPM_SIDE_BOTTOM = 2, MPM_SIDE_TOP 
  *                 tf32 parts and sums three products (about float32 accuracy); BF16_IR rounds
  *                 both operands to bf16.  With too little precision for the local conditioning
  *                 the refinement stalls and the next synchronising call returns
- *                 MPM_ERR_NOT_CONVERGED.
+ *                 MPM_ERR_NOT_CONVERGED.  Subdomains whose tensor-core tables do not fit in
+ *                 shared memory (sides of 20 x 24 cells and larger) take the float32
+ *                 CUDA-core basis solve of FP32_IR_ALL instead.
  * The interface (skeleton) system, residuals, fluxes and transport are float64 in all modes. */
 enum {
   MPM_PREC_FP64 = 0,

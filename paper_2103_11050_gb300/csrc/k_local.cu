@@ -226,7 +226,10 @@ SmemPlan plan_smem(int a, int b, int A, int ncol_max, bool q_global = false) {
   const int m = a * b;
   const size_t fixed = fixed_bytes<T>(a, b, A) - (q_global ? (size_t)b * A * A * sizeof(T) : 0);
   const size_t per_col = (size_t)m * (3 * sizeof(double) + 2 * sizeof(T)) + 2 * sizeof(double);
-  int ncol = (int)((kSmemBudget - fixed) / per_col);
+  // signed: the fixed part alone may exceed the budget (a staged 32-wide float64 factor of
+  // 24 block rows), which leaves no column and sends the caller to the in-place factor
+  const long long room = (long long)kSmemBudget - (long long)fixed;
+  int ncol = room > 0 ? (int)(room / (long long)per_col) : 0;
   if (ncol > ncol_max) ncol = ncol_max;
   if (ncol < 1) ncol = 1;
   return {ncol, fixed + per_col * ncol};
@@ -1129,7 +1132,9 @@ void launch_basis_solve(const Grid& g, const DevState& d, const DevSub* subs, in
   dim3 grid(nsub, g.R);
   const int thr = 256;
   const int A = pad_width(max_a);
-  if (tc_kind != 0) {  // tensor cores (float32 factor)
+  // tensor cores (float32 factor), unless the class's tables exceed shared memory (sides of
+  // 20 x 24 cells and up): those take the float32 CUDA-core solve below, same factor and outputs
+  if (tc_kind != 0 && plan_tc(max_a, max_b, A).bytes <= (size_t)kSmemBudget) {
     if (A == 8) basis_tc_kind<8>(g, d, subs, nsub, max_a, max_b, tc_kind, ir_tol, ir_max, nodes, leaf_node, st);
     else if (A == 16) basis_tc_kind<16>(g, d, subs, nsub, max_a, max_b, tc_kind, ir_tol, ir_max, nodes, leaf_node, st);
     else basis_tc_kind<32>(g, d, subs, nsub, max_a, max_b, tc_kind, ir_tol, ir_max, nodes, leaf_node, st);

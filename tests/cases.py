@@ -21,6 +21,8 @@ CASES = {
     # 9 x 9 subdomains with 32 interface DOFs per side: the top separator (9 interfaces, 288
     # DOFs) and the boundaries of the level below it are longer than 256
     "long_sep": (144, 144, [16] * 9, [16] * 9, 2, 1, 1.0, "exponential", 1.0, 0.2, 3.0, (D, D, N, N), (1, 0, 0, 0), 10),
+    # subdomain sides at the library's maximum (24 cells) beside narrower ones
+    "max_side": (56, 48, [24, 8, 24], [24, 24], 4, 1, 1.0, "exponential", 2.0, 0.15, 4.0, (D, D, N, N), (1, 0, 0, 0), 11),
 }
 
 

@@ -48,7 +48,7 @@ def _built():
 
 @pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("name", ["p1_2x2", "uneven", "const_H", "exact_h", "single", "rate_in", "dirichlet4",
-                                  "contrast64", "alpha_field"])
+                                  "contrast64", "alpha_field", "max_side"])
 def test_mrcm_update_parity(name, prec):
     c = case(name)
     prob, dec = _oracle_setup(c)
@@ -71,7 +71,8 @@ def test_mrcm_update_parity(name, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
-@pytest.mark.parametrize("name", ["p1_2x2", "uneven", "rate_in", "dirichlet4", "contrast64", "alpha_field"])
+@pytest.mark.parametrize("name", ["p1_2x2", "uneven", "rate_in", "dirichlet4", "contrast64", "alpha_field",
+                                  "max_side"])
 def test_mpm_update_parity(name, prec):
     c = case(name)
     prob, dec = _oracle_setup(c)
@@ -280,6 +281,33 @@ def test_long_separator_levels(prec, graph):
         ctx.step(eta, 0.5, 1)
     n_reb = sum(1 for h in st.history if h["rebuild"])
     assert n_reb >= 1
+    assert ctx.get_stats()["rebuilds"] == n_reb + 1
+    tol = TOL[prec]
+    ux, uy = ctx.get_flux()
+    assert rel(ctx.get_saturation()[0], st.s) <= tol
+    assert rel(ux[0], st.step.Fx) <= tol, rel(ux[0], st.step.Fx)
+    assert rel(uy[0], st.step.Fy) <= tol + 1e-12, rel(uy[0], st.step.Fy)
+    assert rel(ctx.get_pressure(0)[0], st.p_m) <= tol, rel(ctx.get_pressure(0)[0], st.p_m)
+    assert rel(ctx.get_pressure(1)[0], st.step.p_down) <= tol, rel(ctx.get_pressure(1)[0], st.step.p_down)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 3])
+def test_max_side_trajectory(prec):
+    """Subdomains with sides at the library's maximum (24 x 24 cells: a 32-wide padded factor of
+    24 block rows, read in place because staged it would not fit in shared memory; in the
+    tensor-core mode their basis solves take the float32 CUDA-core path) through the step graph:
+    init and 8 Algorithm 1 steps with both kinds of update, against the oracle."""
+    c = case("max_side", "zero")
+    prob, dec = _oracle_setup(c)
+    eta, steps = 0.02, 8
+    st = O.simulate_init(c["K"], c["s0"], prob, dec, eta)
+    ctx = _gpu(c, prec)
+    ctx.init(eta)
+    for _ in range(steps):
+        O.simulate_step(st, c["K"], prob, dec, eta, 0.5, 1)
+        ctx.step(eta, 0.5, 1)
+    n_reb = sum(1 for h in st.history if h["rebuild"])
+    assert 0 < n_reb < steps - 1  # both kinds of update occur
     assert ctx.get_stats()["rebuilds"] == n_reb + 1
     tol = TOL[prec]
     ux, uy = ctx.get_flux()
