@@ -186,7 +186,9 @@ int mpm_set_boundary(mpm_ctx* ctx, const int type[4], const double val[4], doubl
 
 /* Tensor-product decomposition (Section 3): ncx column widths col_w (cells, summing to
  * nx) and ncy row heights row_h (summing to ny); every width and height <= 24 and a
- * multiple of seg_len; degree 0 or 1 (Section 3.1).  alpha > 0 is the constant of
+ * multiple of seg_len; degree 0 or 1 (Section 3.1), degree 1 with seg_len >= 2 (its linear
+ * basis function, sampled at the midpoint of a single edge, would vanish and leave the
+ * interface system singular); MPM_ERR_ARG otherwise.  alpha > 0 is the constant of
  * Eq. (beta) (beta = alpha H / kappa, H = length of the interface carrying the face).
  * alpha_face (host memory, may be NULL) gives alpha per fine face instead, the aMRCM's
  * alpha(x) of Section 3.1: ny (nx + 1) values for the x-faces in the layout of ux, then

@@ -898,6 +898,8 @@ int mpm_set_decomposition(mpm_ctx* c, int ncx, const int* col_w, int ncy, const 
   if (ncx < 1 || ncy < 1 || !col_w || !row_h) return fail(c, MPM_ERR_ARG, "bad decomposition arrays");
   if (seg_len < 1 || (degree != 0 && degree != 1) || !(alpha > 0) || !std::isfinite(alpha))
     return fail(c, MPM_ERR_ARG, "need seg_len >= 1, degree in {0,1}, alpha > 0");
+  if (degree == 1 && seg_len < 2)  // a linear function sampled at one edge midpoint vanishes
+    return fail(c, MPM_ERR_ARG, "degree 1 needs seg_len >= 2");
   long long sx = 0, sy = 0;
   for (int I = 0; I < ncx; ++I) {
     if (col_w[I] < 1 || col_w[I] > kMaxSide || col_w[I] % seg_len)

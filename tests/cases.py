@@ -23,6 +23,9 @@ CASES = {
     "long_sep": (144, 144, [16] * 9, [16] * 9, 2, 1, 1.0, "exponential", 1.0, 0.2, 3.0, (D, D, N, N), (1, 0, 0, 0), 10),
     # subdomain sides at the library's maximum (24 cells) beside narrower ones
     "max_side": (56, 48, [24, 8, 24], [24, 24], 4, 1, 1.0, "exponential", 2.0, 0.15, 4.0, (D, D, N, N), (1, 0, 0, 0), 11),
+    # short sides: one to four block rows per subdomain, two-cell interfaces
+    "small_sides": (16, 12, [4, 8, 4], [2, 6, 4], 2, 1, 1.0, "exponential", 1.0, 0.2, 2.0, (D, D, N, N), (1, 0, 0, 0),
+                    12),
 }
 
 

@@ -48,7 +48,7 @@ def _built():
 
 @pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("name", ["p1_2x2", "uneven", "const_H", "exact_h", "single", "rate_in", "dirichlet4",
-                                  "contrast64", "alpha_field", "max_side"])
+                                  "contrast64", "alpha_field", "max_side", "small_sides"])
 def test_mrcm_update_parity(name, prec):
     c = case(name)
     prob, dec = _oracle_setup(c)
@@ -72,7 +72,7 @@ def test_mrcm_update_parity(name, prec):
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("name", ["p1_2x2", "uneven", "rate_in", "dirichlet4", "contrast64", "alpha_field",
-                                  "max_side"])
+                                  "max_side", "small_sides"])
 def test_mpm_update_parity(name, prec):
     c = case(name)
     prob, dec = _oracle_setup(c)
@@ -433,6 +433,19 @@ def test_alpha_face_rejects_non_positive_values_on_interface_faces():
     with pytest.raises(B.MPMError) as ei:
         ctx.set_decomposition(c["col_w"], c["row_h"], c["seg_len"], c["degree"], 1.0, (ax, ay))
     assert ei.value.code == B.MPM_ERR_ARG
+
+
+def test_decomposition_rejects_out_of_range_geometry():
+    # sides beyond 24 cells, sides that are not multiples of seg_len, and linear interface
+    # spaces on one-edge segments (whose linear basis function vanishes at the edge midpoint)
+    from paper_2103_11050_gb300 import binding as B
+    c = case("max_side")
+    ctx = _gpu(c, 0)
+    for cw, rh, seg, deg in (([28, 28], [24, 24], 4, 1), ([26, 30], [24, 24], 4, 1), (c["col_w"], c["row_h"], 1, 1)):
+        with pytest.raises(B.MPMError) as ei:
+            ctx.set_decomposition(cw, rh, seg, deg, 1.0)
+        assert ei.value.code == B.MPM_ERR_ARG
+    ctx.set_decomposition(c["col_w"], c["row_h"], 1, 0, 1.0)  # one-edge constant segments are fine
 
 
 def test_refinement_cap_reports_not_converged():
