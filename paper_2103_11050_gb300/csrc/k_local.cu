@@ -72,54 +72,77 @@ struct Stencil {
 // Multi-RHS twisted block solve  (S A S) X = Z  in place on Z ([m][ncol], column stride
 // ncol) with the factor of k_local_warp.cuh (top chain j < mid, bottom chain j > mid,
 // middle row mid = b/2).  W: workspace of the same shape.  Q: [b][A][A] factor and
-// th[m] = scaled north couplings (factor type), both in shared memory.
+// th[m] = scaled north couplings (factor type), both in shared memory.  The coupling of a
+// block row to its neighbour (an elementwise product, the inter-row blocks of a 5-point
+// operator being diagonal) is formed once per entry in shared memory before the row's
+// products with its a x a block, not once per output row inside them.
 template <typename T>
 __device__ void block_solve(const DevSub& sd, const T* th, const T* Q, int A, T* Z, T* W, int ncol) {
   const int a = sd.a, b = sd.b, mid = b / 2;
   const int nwork = a * ncol;
-  // W_j = Q_j (Z_j + th_{jp} o W_{jp}),  jp = previous row of the chain (-1: none)
-  auto fwd = [&](int j, int jp) {
+  // W_j = Q_j Y_j,  Y_j = Z_j + th_{jp} o W_{jp} (formed in place in Z_j),  jp = previous
+  // row of the chain (-1: none)
+  auto product = [&](int j, const T* Y) {  // W_j = Q_j Y
     const T* Qj = Q + (long long)j * A * A;
     for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
       const int i = w / ncol, col = w - (w / ncol) * ncol;
       T acc = T(0);
-      for (int k = 0; k < a; ++k) {
-        const int ck = j * a + k;
-        T zk = Z[ck * ncol + col];
-        if (jp >= 0) zk += th[min(j, jp) * a + k] * W[(jp * a + k) * ncol + col];
-        acc += Qj[i * A + k] * zk;
-      }
+      for (int k = 0; k < a; ++k) acc += Qj[i * A + k] * Y[k * ncol + col];
       W[(j * a + i) * ncol + col] = acc;
     }
     __syncthreads();
   };
+  auto fwd = [&](int j, int jp) {
+    if (jp >= 0) {
+      const T* tj = th + min(j, jp) * a;
+      for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
+        const int k = w / ncol, col = w - (w / ncol) * ncol;
+        Z[(j * a + k) * ncol + col] += tj[k] * W[(jp * a + k) * ncol + col];
+      }
+      __syncthreads();
+    }
+    product(j, Z + (long long)j * a * ncol);
+  };
   for (int j = 0; j < mid; ++j) fwd(j, j - 1);
   for (int j = b - 1; j > mid; --j) fwd(j, j + 1 < b ? j + 1 : -1);
   // middle: X_mid = Q_mid (Z_mid + th_{mid-1} o W_{mid-1} + th_mid o W_{mid+1})
-  {
-    const T* Qm = Q + (long long)mid * A * A;
+  if (mid > 0 || mid < b - 1) {
     for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
-      const int i = w / ncol, col = w - (w / ncol) * ncol;
-      T acc = T(0);
-      for (int k = 0; k < a; ++k) {
-        const int ck = mid * a + k;
-        T zk = Z[ck * ncol + col];
-        if (mid > 0) zk += th[ck - a] * W[(ck - a) * ncol + col];
-        if (mid < b - 1) zk += th[ck] * W[(ck + a) * ncol + col];
-        acc += Qm[i * A + k] * zk;
-      }
-      W[(mid * a + i) * ncol + col] = acc;  // W_mid holds X_mid
+      const int k = w / ncol, col = w - (w / ncol) * ncol;
+      const int ck = mid * a + k;
+      T zk = Z[ck * ncol + col];
+      if (mid > 0) zk += th[ck - a] * W[(ck - a) * ncol + col];
+      if (mid < b - 1) zk += th[ck] * W[(ck + a) * ncol + col];
+      Z[ck * ncol + col] = zk;
     }
     __syncthreads();
   }
-  // backward: X_j = W_j + Q_j (th_{jc} o X_{jn}), jn = the row solved before
+  product(mid, Z + (long long)mid * a * ncol);  // W_mid holds X_mid
+  // backward: X_j = W_j + Q_j (th_{jc} o X_{jn}), jn = the row solved before.  The products
+  // th_{jc} o X_{jn} go into W_{jn} (no longer needed once X_{jn} is final), except for
+  // jn = mid, whose row serves both chains with different couplings.
   auto bwd = [&](int j, int jn) {
     const T* Qj = Q + (long long)j * A * A;
-    for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
-      const int i = w / ncol, col = w - (w / ncol) * ncol;
-      T acc = T(0);
-      for (int k = 0; k < a; ++k) acc += Qj[i * A + k] * (th[min(j, jn) * a + k] * Z[(jn * a + k) * ncol + col]);
-      Z[(j * a + i) * ncol + col] = W[(j * a + i) * ncol + col] + acc;
+    const T* tj = th + min(j, jn) * a;
+    if (jn != mid) {
+      for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
+        const int k = w / ncol, col = w - (w / ncol) * ncol;
+        W[(jn * a + k) * ncol + col] = tj[k] * Z[(jn * a + k) * ncol + col];
+      }
+      __syncthreads();
+      for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
+        const int i = w / ncol, col = w - (w / ncol) * ncol;
+        T acc = T(0);
+        for (int k = 0; k < a; ++k) acc += Qj[i * A + k] * W[(jn * a + k) * ncol + col];
+        Z[(j * a + i) * ncol + col] = W[(j * a + i) * ncol + col] + acc;
+      }
+    } else {
+      for (int w = threadIdx.x; w < nwork; w += blockDim.x) {
+        const int i = w / ncol, col = w - (w / ncol) * ncol;
+        T acc = T(0);
+        for (int k = 0; k < a; ++k) acc += Qj[i * A + k] * (tj[k] * Z[(jn * a + k) * ncol + col]);
+        Z[(j * a + i) * ncol + col] = W[(j * a + i) * ncol + col] + acc;
+      }
     }
     __syncthreads();
   };
