@@ -189,6 +189,17 @@ __device__ void solve_refined(const DevSub& sd, Stencil S, const T* th, const T*
                               int ir_max, double* colmax /* 2*ncol */, int* status, int* ir_used) {
   const int m = sd.a * sd.b;
   const int n = m * ncol;
+  if (std::is_same<T, double>::value && !refine) {
+    // float64 factor, unscaled (S.sc = 1): one block solve, without the scaling products
+    for (int e = threadIdx.x; e < n; e += blockDim.x) Zw[e] = T(B[e]);
+    __syncthreads();
+    block_solve<T>(sd, th, Q, A, Zw, Ww, ncol);
+    for (int e = threadIdx.x; e < n; e += blockDim.x) X[e] = double(Zw[e]);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(ir_used, 1);
+    __syncthreads();
+    return;
+  }
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
     X[e] = 0.0;
     Rr[e] = B[e];
@@ -367,14 +378,25 @@ __device__ double basis_g(const Grid& g, const DevState& d, const DevSub& sd, co
   return isU ? -div64(d.rho_f[sd.face_off + f], S.kap[cl]) * sd.side_sign[side] * phi : phi;
 }
 
-// Outward trace on face f of the local solution x (column col of X) of basis column bcol.
+// Robin coefficient r_e = kappa_c / (1/2 + rho_e) of every interface face of the subdomain
+// (unused on physical faces), formed once per CTA for the traces of all its basis columns.
+__device__ void robin_coeffs(const DevState& d, const DevSub& sd, const Stencil& S, double* rface) {
+  const int nface = 2 * (sd.a + sd.b);
+  for (int f = threadIdx.x; f < nface; f += blockDim.x) {
+    int side, t, cl;
+    face_info(sd, f, side, t, cl);
+    rface[f] = sd.side_kind[side] == 1 ? div64(S.kap[cl], 0.5 + d.rho_f[sd.face_off + f]) : 0.0;
+  }
+}
+
+// Outward trace on face f of the local solution x (column col of X) of basis column bcol;
+// rface from robin_coeffs.
 __device__ double basis_trace(const Grid& g, const DevState& d, const DevSub& sd, const Stencil& S, const double* X,
-                              int ncol, int f, int col, int bcol, bool homogeneous_phys) {
+                              const double* rface, int ncol, int f, int col, int bcol, bool homogeneous_phys) {
   int side, t, cl;
   face_info(sd, f, side, t, cl);
   const double kc = S.kap[cl], pc = X[cl * ncol + col];
-  if (sd.side_kind[side] == 1)
-    return div64(kc, 0.5 + d.rho_f[sd.face_off + f]) * (pc - basis_g(g, d, sd, S, f, bcol));
+  if (sd.side_kind[side] == 1) return rface[f] * (pc - basis_g(g, d, sd, S, f, bcol));
   if (g.bc_type[side] == 0) return 2.0 * kc * (pc - (homogeneous_phys ? 0.0 : g.bc_val[side]));
   return homogeneous_phys ? 0.0 : g.bc_val[side] * g.h;
 }
@@ -402,6 +424,8 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
   if ((int)blockIdx.z * ncol_max >= ntot) return;  // no chunk for this CTA
   Carve<T> cv = carve<T>(smem, a, b, A, ncol_max, q_global != 0);
   load_robin<T>(d, sd, r, cv, g, A, q_global != 0);
+  __shared__ double rface[4 * kMaxSide];
+  robin_coeffs(d, sd, cv.S, rface);  // read after the barriers of the first chunk's solve
   double* tr = d.tr + (long long)r * d.st_tr + sd.tr_off;       // [ndof][nface]
   double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;       // [ndof+1][m]
   double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
@@ -423,7 +447,7 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
     }
     for (int e = threadIdx.x; e < nface * ncol; e += blockDim.x) {
       const int f = e / ncol, col = e - f * ncol, bcol = c0 + col;
-      const double v = basis_trace(g, d, sd, cv.S, cv.X, ncol, f, col, bcol, bcol < sd.ndof);
+      const double v = basis_trace(g, d, sd, cv.S, cv.X, rface, ncol, f, col, bcol, bcol < sd.ndof);
       if (bcol < sd.ndof) tr[(long long)bcol * nface + f] = v;
       else fbar[f] = v;
     }
@@ -559,6 +583,8 @@ __global__ void __launch_bounds__(256) k_basis_solve_tc(Grid g, DevState d, cons
     cv.Ww = q;
   }
   load_robin<float>(d, sd, r, cv, g, A);
+  __shared__ double rface[4 * kMaxSide];
+  robin_coeffs(d, sd, cv.S, rface);  // read after the barriers of the first chunk's solve
   double* tr = d.tr + (long long)r * d.st_tr + sd.tr_off;
   double* pf = d.pf + (long long)r * d.st_pf + sd.pf_off;
   double* fbar = d.fbar + (long long)r * d.st_face + sd.face_off;
@@ -578,7 +604,7 @@ __global__ void __launch_bounds__(256) k_basis_solve_tc(Grid g, DevState d, cons
     }
     for (int e = threadIdx.x; e < nface * ncol; e += blockDim.x) {
       const int f = e / ncol, col = e - f * ncol, bcol = c0 + col;
-      const double v = basis_trace(g, d, sd, cv.S, cv.X, ncol, f, col, bcol, bcol < sd.ndof);
+      const double v = basis_trace(g, d, sd, cv.S, cv.X, rface, ncol, f, col, bcol, bcol < sd.ndof);
       if (bcol < sd.ndof) tr[(long long)bcol * nface + f] = v;
       else fbar[f] = v;
     }
