@@ -190,11 +190,15 @@ __device__ void solve_refined(const DevSub& sd, Stencil S, const T* th, const T*
   const int m = sd.a * sd.b;
   const int n = m * ncol;
   if (std::is_same<T, double>::value && !refine) {
-    // float64 factor, unscaled (S.sc = 1): one block solve, without the scaling products
-    for (int e = threadIdx.x; e < n; e += blockDim.x) Zw[e] = T(B[e]);
+    // float64 factor, unscaled (S.sc = 1): one block solve, without the scaling products (in
+    // place when B and X are the workspace Zw itself)
+    const bool in_place = reinterpret_cast<const void*>(B) == reinterpret_cast<const void*>(Zw);
+    if (!in_place)
+      for (int e = threadIdx.x; e < n; e += blockDim.x) Zw[e] = T(B[e]);
     __syncthreads();
     block_solve<T>(sd, th, Q, A, Zw, Ww, ncol);
-    for (int e = threadIdx.x; e < n; e += blockDim.x) X[e] = double(Zw[e]);
+    if (!in_place)
+      for (int e = threadIdx.x; e < n; e += blockDim.x) X[e] = double(Zw[e]);
     __syncthreads();
     if (threadIdx.x == 0) atomicMax(ir_used, 1);
     __syncthreads();
@@ -255,11 +259,15 @@ size_t fixed_bytes(int a, int b, int A) {
   return stencil_bytes(m) + (size_t)b * A * A * sizeof(T) + (size_t)m * sizeof(T) + 64 * sizeof(double) + 256;
 }
 
+// direct: the float64 solve without refinement, whose right-hand side is built in the block
+// solve's workspace and whose solution is read from it (no separate right-hand-side, solution
+// and residual blocks: 16 instead of 40 bytes per cell and column).
 template <typename T>
-SmemPlan plan_smem(int a, int b, int A, int ncol_max, bool q_global = false) {
+SmemPlan plan_smem(int a, int b, int A, int ncol_max, bool q_global = false, bool direct = false) {
   const int m = a * b;
   const size_t fixed = fixed_bytes<T>(a, b, A) - (q_global ? (size_t)b * A * A * sizeof(T) : 0);
-  const size_t per_col = (size_t)m * (3 * sizeof(double) + 2 * sizeof(T)) + 2 * sizeof(double);
+  const size_t per_col = direct ? (size_t)m * 2 * sizeof(T) + 2 * sizeof(double)
+                                : (size_t)m * (3 * sizeof(double) + 2 * sizeof(T)) + 2 * sizeof(double);
   // signed: the fixed part alone may exceed the budget (a staged 32-wide float64 factor of
   // 24 block rows), which leaves no column and sends the caller to the in-place factor
   const long long room = (long long)kSmemBudget - (long long)fixed;
@@ -280,7 +288,7 @@ struct Carve {
 };
 
 template <typename T>
-__device__ Carve<T> carve(char* base, int a, int b, int A, int ncol, bool q_global = false) {
+__device__ Carve<T> carve(char* base, int a, int b, int A, int ncol, bool q_global = false, bool direct = false) {
   const int m = a * b;
   Carve<T> c;
   double* p = reinterpret_cast<double*>(base);
@@ -290,14 +298,20 @@ __device__ Carve<T> carve(char* base, int a, int b, int A, int ncol, bool q_glob
   c.S.wN = p; p += m;
   c.S.sc = p; p += m;
   c.colmax = p; p += 64;
-  c.B = p; p += (size_t)m * ncol;
-  c.X = p; p += (size_t)m * ncol;
-  c.Rr = p; p += (size_t)m * ncol;
+  if (!direct) {
+    c.B = p; p += (size_t)m * ncol;
+    c.X = p; p += (size_t)m * ncol;
+    c.Rr = p; p += (size_t)m * ncol;
+  }
   T* q = reinterpret_cast<T*>(p);
   c.Q = q; q += q_global ? 0 : (size_t)b * A * A;  // the factor stays in global memory when q_global
   c.Zw = q; q += (size_t)m * ncol;
   c.Ww = q; q += (size_t)m * ncol;
   c.th = q;
+  if (direct) {  // float64 only (plan_smem): right-hand side and solution live in Zw
+    c.B = c.X = reinterpret_cast<double*>(c.Zw);
+    c.Rr = nullptr;
+  }
   return c;
 }
 
@@ -422,7 +436,8 @@ __global__ void k_basis_solve(Grid g, DevState d, const DevSub* subs, int A, int
   const int nface = 2 * (a + b);
   const int ntot = sd.ndof + 1;
   if ((int)blockIdx.z * ncol_max >= ntot) return;  // no chunk for this CTA
-  Carve<T> cv = carve<T>(smem, a, b, A, ncol_max, q_global != 0);
+  const bool direct = std::is_same<T, double>::value && refine == 0;  // the layout of plan_smem
+  Carve<T> cv = carve<T>(smem, a, b, A, ncol_max, q_global != 0, direct);
   load_robin<T>(d, sd, r, cv, g, A, q_global != 0);
   __shared__ double rface[4 * kMaxSide];
   robin_coeffs(d, sd, cv.S, rface);  // read after the barriers of the first chunk's solve
@@ -1202,9 +1217,15 @@ void launch_basis_solve(const Grid& g, const DevState& d, const DevSub* subs, in
     k_basis_solve<float><<<grid, thr, pl.bytes, st>>>(g, d, subs, A, pl.ncol, 1, ir_tol, ir_max, nodes, leaf_node,
                                                        qg ? 1 : 0);
   } else {
-    SmemPlan pl = plan_smem<double>(max_a, max_b, A, 32);
-    const bool qg = pl.ncol < 8;
-    if (qg) pl = plan_smem<double>(max_a, max_b, A, 32, true);
+    // float64 without refinement: the direct layout (right-hand side and solution in the
+    // workspace), up to 64 columns per pass, or as many as spread the columns of the widest
+    // subdomain (2 (a + b) / seg_len segments of degree + 1 functions, U and P, plus the
+    // non-homogeneous column) evenly over the CTAs of a subdomain
+    const int ntot = 2 * (g.degree + 1) * (2 * max_a + 2 * max_b) / g.seg_len + 1;
+    const int cap = grid.z > 1 ? std::min(64, ((int)(ntot + grid.z - 1) / (int)grid.z)) : 64;
+    SmemPlan pl = plan_smem<double>(max_a, max_b, A, cap, false, true);
+    const bool qg = pl.ncol < 8 && pl.ncol < cap;
+    if (qg) pl = plan_smem<double>(max_a, max_b, A, cap, true, true);
     set_smem(k_basis_solve<double>, pl.bytes);
     k_basis_solve<double><<<grid, thr, pl.bytes, st>>>(g, d, subs, A, pl.ncol, 0, ir_tol, ir_max, nodes,
                                                          leaf_node, qg ? 1 : 0);
