@@ -154,16 +154,25 @@ def cfl_dt_noalloc(ux, uy, dt, h, M, cfl, stream=None):
         raise MPMError(rc, "mpm_cfl_dt_noalloc failed")
 
 
-def _ptr(x):
-    """(pointer, mem) of a C-contiguous float64 NumPy array or torch CUDA tensor."""
+def _ptr(x, n=None):
+    """(pointer, mem) of a C-contiguous float64 NumPy array or torch tensor holding exactly n
+    values (when n is given): the library reads or writes that many through the pointer, so
+    a smaller buffer would be overrun.  A CUDA tensor must be on the current device (the
+    context's)."""
     if isinstance(x, np.ndarray):
         if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
             raise ValueError("expected a C-contiguous float64 array")
+        if n is not None and x.size != n:
+            raise ValueError(f"expected {n} values, got an array of {x.size}")
         return ctypes.c_void_p(x.ctypes.data), MEM_HOST
     if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
         import torch
         if x.dtype != torch.float64 or not x.is_contiguous():
             raise ValueError("expected a contiguous float64 tensor")
+        if n is not None and x.numel() != n:
+            raise ValueError(f"expected {n} values, got a tensor of {x.numel()}")
+        if x.is_cuda and x.device.index != torch.cuda.current_device():
+            raise ValueError(f"tensor on cuda:{x.device.index}, not on the current device")
         return ctypes.c_void_p(x.data_ptr()), (MEM_DEVICE if x.is_cuda else MEM_HOST)
     raise TypeError(f"unsupported array type {type(x)}")
 
@@ -201,15 +210,18 @@ class Context:
     def set_precision(self, mode, ir_tol=1e-14, ir_max=30):
         self._ck(self.L.mpm_set_precision(self.h, int(mode), float(ir_tol), int(ir_max)))
 
+    def _ncell(self):
+        return self.R * self.ny * self.nx
+
     def set_permeability(self, K):
-        p, mem = _ptr(K)
+        p, mem = _ptr(K, self._ncell())
         self._ck(self.L.mpm_set_permeability(self.h, p, mem))
 
     def set_source(self, q=None):
         if q is None:
             self._ck(self.L.mpm_set_source(self.h, None, MEM_HOST))
         else:
-            p, mem = _ptr(q)
+            p, mem = _ptr(q, self._ncell())
             self._ck(self.L.mpm_set_source(self.h, p, mem))
 
     def set_fluids(self, M):
@@ -235,7 +247,7 @@ class Context:
                                               float(alpha), None if af is None else ctypes.c_void_p(af.ctypes.data)))
 
     def set_saturation(self, s):
-        p, mem = _ptr(s)
+        p, mem = _ptr(s, self._ncell())
         self._ck(self.L.mpm_set_saturation(self.h, p, mem))
 
     # ---- hot path
@@ -295,22 +307,24 @@ class Context:
     def _get(self, fn, shape, out, *extra):
         if out is None:
             out = np.zeros(shape)
-        p, mem = _ptr(out)
+        p, mem = _ptr(out, int(np.prod(shape)))
         self._ck(fn(self.h, p, *extra, mem))
         return out
 
     def get_pressure(self, which=P_DOWNSCALED, out=None):
         if out is None:
             out = np.zeros((self.R, self.ny, self.nx))
-        p, mem = _ptr(out)
+        p, mem = _ptr(out, self._ncell())
         self._ck(self.L.mpm_get_pressure(self.h, p, int(which), mem))
         return out
 
     def get_flux(self, ux=None, uy=None):
         ux = np.zeros((self.R, self.ny, self.nx + 1)) if ux is None else ux
         uy = np.zeros((self.R, self.ny + 1, self.nx)) if uy is None else uy
-        pu, mem = _ptr(ux)
-        pv, _ = _ptr(uy)
+        pu, mem = _ptr(ux, self.R * self.ny * (self.nx + 1))
+        pv, mem_v = _ptr(uy, self.R * (self.ny + 1) * self.nx)
+        if mem_v != mem:
+            raise ValueError("ux and uy must both be host memory or both device memory")
         self._ck(self.L.mpm_get_flux(self.h, pu, pv, mem))
         return ux, uy
 
