@@ -135,7 +135,8 @@ enum {
  * Cells must be square: Lx/nx == Ly/ny (relative 1e-12).  stream is a cudaStream_t
  * (NULL = legacy default stream) of the current device, which becomes the context's
  * device.  Defaults: M = 1, left p = 1, right p = 0, top/bottom no flow, s_inflow = 1,
- * q = 0, FP64.  Errors: MPM_ERR_ARG for non-positive sizes or non-square cells. */
+ * q = 0, FP64.  Errors: MPM_ERR_ARG for non-positive sizes, R > 65535 or non-square
+ * cells. */
 int mpm_create(mpm_ctx** ctx, int R, int nx, int ny, double Lx, double Ly, void* stream);
 
 /* Free all device memory of ctx (after synchronising its stream). NULL is a no-op. */

@@ -725,6 +725,7 @@ int mpm_create(mpm_ctx** out, int R, int nx, int ny, double Lx, double Ly, void*
   if (!out) return MPM_ERR_ARG;
   *out = nullptr;
   if (R < 1 || nx < 1 || ny < 1 || !(Lx > 0) || !(Ly > 0)) return MPM_ERR_ARG;
+  if (R > kMaxRealisations) return MPM_ERR_ARG;  // realisations index grid y / z of the launches
   const double hx = Lx / nx, hy = Ly / ny;
   if (std::fabs(hx - hy) > 1e-12 * std::max(hx, hy)) return MPM_ERR_ARG;
   mpm_ctx* c = new mpm_ctx();

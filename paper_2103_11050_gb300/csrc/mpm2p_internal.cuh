@@ -16,6 +16,7 @@
 
 namespace mpm {
 
+constexpr int kMaxRealisations = 65535;  // realisations per context (a grid y / z dimension)
 constexpr int kMaxSide = 24;     // largest subdomain width / height in cells
 constexpr int kPivotChunk = 16;  // pivot block of the interface sweeps
 constexpr int kEpsHist = 4096;   // steps of epsilon history kept per realisation (MPM_EPS_HISTORY)

@@ -47,3 +47,4 @@ def test_create_rejects_bad_sizes_without_gpu_work(lib):
     assert L.mpm_create(ctypes.byref(h), 1, 4, 4, 1.0, 2.0, None) == binding.MPM_ERR_ARG
     assert L.mpm_create(ctypes.byref(h), 0, 4, 4, 1.0, 1.0, None) == binding.MPM_ERR_ARG
     assert L.mpm_create(ctypes.byref(h), 1, -4, 4, 1.0, 1.0, None) == binding.MPM_ERR_ARG
+    assert L.mpm_create(ctypes.byref(h), 65536, 4, 4, 1.0, 1.0, None) == binding.MPM_ERR_ARG
