@@ -271,6 +271,20 @@ def test_mrcm_basis_route_equals_monolithic(alpha, degree, seg):
     np.testing.assert_allclose(sol.coeffs, c_mono, atol=1e-10 * np.max(np.abs(c_mono)))
 
 
+@pytest.mark.parametrize("col_w,row_h,seg", [([24, 8], [24], 4), ([4, 8, 4], [2, 6, 4], 2)])
+def test_mrcm_basis_route_equals_monolithic_extreme_sides(col_w, row_h, seg):
+    # the subdomain sides at the extremes of the GPU parity cases (24 cells; 2 cells, one block
+    # row pair): the basis-function route still equals the monolithic solve of Eqs. (mrc1)+(mrc2)
+    nx, ny = sum(col_w), sum(row_h)
+    prob = _prob(nx, ny, bc_val=(1.0, 0.0, 0.0, 0.0))
+    kappa = _field(nx, ny, seed=13, sigma2=2.0)
+    dec = O.Decomposition(nx, ny, col_w, row_h, seg_len=seg, degree=1, alpha=1.0)
+    sol, _ = O.mrcm_solve(kappa, prob, dec)
+    p_mono, c_mono = O.mrcm_monolithic(kappa, prob, dec)
+    np.testing.assert_allclose(sol.p, p_mono, atol=1e-12 * np.max(np.abs(p_mono)))
+    np.testing.assert_allclose(sol.coeffs, c_mono, atol=1e-10 * np.max(np.abs(c_mono)))
+
+
 @pytest.mark.parametrize("varying", [False, True])
 def test_interface_matrix_symmetric(varying):
     # With the flux-weighted rows negated, Eq. (mrc2) tested with the BFs is symmetric (also
